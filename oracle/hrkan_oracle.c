@@ -1,0 +1,473 @@
+/*
+ * HRKAN FP64 CPU oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path links, loads or
+ * calls this file: only the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark use it.  It shares no code, header, table or constant with
+ * the CUDA path.
+ *
+ * Every routine is the plain definition from the paper, written for
+ * readability, in double precision, with no blocking, no active-set
+ * shortcut and no fusion:
+ *
+ *   support    Section 2.1/2.2: the HR basis uses "the same support as the
+ *              B-spline basis" of grid size g and order k, i.e. n = g + k
+ *              intervals [s_i, e_i] with s_i = lo + (i-k)h, e_i = lo + (i+1)h,
+ *              h = (hi-lo)/g.
+ *   basis      Section 3, Eq. 2: v_{m,i}(x) = ReLU(e_i-x)^m ReLU(x-s_i)^m c_m,
+ *              c_m = (2/(e_i-s_i))^{2m}; first to third derivatives are the
+ *              derivatives of that polynomial inside (s_i, e_i), zero outside.
+ *   layer      Sections 1-3 (KAN layer as a matrix operation): output unit o of
+ *              a layer is sum_j sum_i W[o][j][i] v_i(z_j), summed densely over
+ *              all n bases; no bias, no base branch, no normalisation.
+ *   jets       the input derivatives the PDE residuals need (Eq. 3: Laplacian;
+ *              Eq. 6-8: u_t, u_x, u_xx) by the forward-mode chain rule.
+ *   loss       Eq. 4 (Poisson) and Eq. 8 (Burgers): L = alpha L_pde + L_bnd,
+ *              L_bnd the pooled mean over all boundary/initial points.
+ *   backward   hand-written reverse mode of the above.
+ *   adam       the Adam update used for training (Section 4), bias-corrected.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+
+/* ---------------------------------------------------------------- support */
+
+void orc_support(int G, int k, double lo, double hi, double* s, double* e)
+{
+    double h = (hi - lo) / (double)G;
+    for (int i = 0; i < G + k; ++i) {
+        s[i] = lo + (double)(i - k) * h;
+        e[i] = lo + (double)(i + 1) * h;
+    }
+}
+
+/* ------------------------------------------------------------------ basis */
+
+static double relu(double x) { return x > 0.0 ? x : 0.0; }
+
+/* b^p for integer p; a negative power only ever multiplies a zero
+ * coefficient in the formulas below, so it is returned as 0. */
+static double ipow(double b, int p)
+{
+    if (p < 0) return 0.0;
+    double r = 1.0;
+    for (int t = 0; t < p; ++t) r *= b;
+    return r;
+}
+
+/*
+ * out[0..3] = v, v', v'', v''' of the order-m HR basis on [s, e] at x.
+ * With p(x) = (e-x)(x-s), p' = e+s-2x, p'' = -2, inside (s, e):
+ *   v    = c p^m
+ *   v'   = c m p^{m-1} p'
+ *   v''  = c [m(m-1) p^{m-2} p'^2 - 2m p^{m-1}]
+ *   v''' = c [m(m-1)(m-2) p^{m-3} p'^3 - 6m(m-1) p^{m-2} p']
+ * The value is the literal ReLU product of Eq. 2 everywhere; the derivatives
+ * are taken as 0 at and outside the end points.
+ */
+void orc_hr_basis(int m, double s, double e, double x, double* out)
+{
+    double c = pow(2.0 / (e - s), 2.0 * m);
+    double A = relu(e - x), B = relu(x - s);
+    out[0] = ipow(A, m) * ipow(B, m) * c;
+    if (!(x > s && x < e)) {
+        out[1] = out[2] = out[3] = 0.0;
+        return;
+    }
+    double p = A * B, dp = e + s - 2.0 * x;
+    double md = (double)m;
+    out[1] = c * md * ipow(p, m - 1) * dp;
+    out[2] = c * (md * (md - 1.0) * ipow(p, m - 2) * dp * dp - 2.0 * md * ipow(p, m - 1));
+    out[3] = c * (md * (md - 1.0) * (md - 2.0) * ipow(p, m - 3) * dp * dp * dp
+                  - 6.0 * md * (md - 1.0) * ipow(p, m - 2) * dp);
+}
+
+/* ---------------------------------------------------------------- network */
+
+typedef struct {
+    int n_widths;      /* layers + 1 */
+    const int* widths; /* widths[0] = D input dims, widths[n_widths-1] = 1 */
+    int G, k, m;
+    double lo, hi;
+} orc_net;
+
+static int orc_nbasis(const orc_net* net) { return net->G + net->k; }
+
+long orc_param_count(int n_widths, const int* widths, int G, int k)
+{
+    long P = 0;
+    for (int l = 0; l + 1 < n_widths; ++l) P += (long)widths[l] * widths[l + 1] * (G + k);
+    return P;
+}
+
+static long layer_offset(const orc_net* net, int l)
+{
+    long off = 0, n = orc_nbasis(net);
+    for (int t = 0; t < l; ++t) off += (long)net->widths[t] * net->widths[t + 1] * n;
+    return off;
+}
+
+static int max_width(const orc_net* net)
+{
+    int w = 0;
+    for (int l = 0; l < net->n_widths; ++l) if (net->widths[l] > w) w = net->widths[l];
+    return w;
+}
+
+/*
+ * One layer, one point, full jets over D input dims.
+ * z[j], dz[j*D+d] = dz_j/dx_d, d2z[j*D+d] = d2z_j/dx_d^2  ->  y, dy, d2y.
+ */
+static void layer_forward(const orc_net* net, int l, const double* Wl, int D,
+                          const double* s, const double* e,
+                          const double* z, const double* dz, const double* d2z,
+                          double* y, double* dy, double* d2y)
+{
+    int I = net->widths[l], O = net->widths[l + 1], n = orc_nbasis(net);
+    for (int o = 0; o < O; ++o) {
+        y[o] = 0.0;
+        for (int d = 0; d < D; ++d) dy[o * D + d] = d2y[o * D + d] = 0.0;
+    }
+    for (int j = 0; j < I; ++j) {
+        for (int i = 0; i < n; ++i) {
+            double b[4];
+            orc_hr_basis(net->m, s[i], e[i], z[j], b);
+            for (int o = 0; o < O; ++o) {
+                double w = Wl[((long)o * I + j) * n + i];
+                y[o] += w * b[0];
+                for (int d = 0; d < D; ++d) {
+                    double zd = dz[j * D + d];
+                    dy[o * D + d] += w * b[1] * zd;
+                    d2y[o * D + d] += w * (b[2] * zd * zd + b[1] * d2z[j * D + d]);
+                }
+            }
+        }
+    }
+}
+
+/* jet rows selected by mask: bit 0 = u, bit 1+d = du/dx_d, bit 1+D+d = d2u/dx_d^2 */
+static int mask_rows(unsigned mask, int D, int* bit_of_row)
+{
+    int J = 0;
+    for (int b = 0; b < 1 + 2 * D; ++b)
+        if (mask & (1u << b)) bit_of_row[J++] = b;
+    return J;
+}
+
+/* Scratch holding the per-layer input jets of one point. */
+typedef struct {
+    double *z, *dz, *d2z; /* [layer][maxw], [layer][maxw*D] */
+    double *y, *dy, *d2y;
+    int stride;           /* maxw */
+} point_tape;
+
+static int tape_alloc(point_tape* t, const orc_net* net, int D)
+{
+    int L = net->n_widths - 1, w = max_width(net);
+    t->stride = w;
+    t->z = calloc((size_t)(L + 1) * w, sizeof(double));
+    t->dz = calloc((size_t)(L + 1) * w * D, sizeof(double));
+    t->d2z = calloc((size_t)(L + 1) * w * D, sizeof(double));
+    t->y = calloc((size_t)w, sizeof(double));
+    t->dy = calloc((size_t)w * D, sizeof(double));
+    t->d2y = calloc((size_t)w * D, sizeof(double));
+    return (t->z && t->dz && t->d2z && t->y && t->dy && t->d2y) ? 0 : -1;
+}
+
+static void tape_free(point_tape* t)
+{
+    free(t->z); free(t->dz); free(t->d2z); free(t->y); free(t->dy); free(t->d2y);
+}
+
+/* Forward of one point through all layers; layer l's input jets land in the tape row l,
+ * the network output in row L. */
+static void point_forward(const orc_net* net, const double* W, int D, const double* s,
+                          const double* e, const double* xp, point_tape* t)
+{
+    int L = net->n_widths - 1, w = t->stride;
+    for (int j = 0; j < D; ++j) {
+        t->z[j] = xp[j];
+        for (int d = 0; d < D; ++d) {
+            t->dz[j * D + d] = (j == d) ? 1.0 : 0.0;
+            t->d2z[j * D + d] = 0.0;
+        }
+    }
+    for (int l = 0; l < L; ++l) {
+        const double* Wl = W + layer_offset(net, l);
+        layer_forward(net, l, Wl, D, s, e, t->z + (long)l * w, t->dz + (long)l * w * D,
+                      t->d2z + (long)l * w * D, t->z + (long)(l + 1) * w,
+                      t->dz + (long)(l + 1) * w * D, t->d2z + (long)(l + 1) * w * D);
+    }
+}
+
+/*
+ * jets[J][N] of the network output at N points x[D][N] (structure of arrays).
+ * Returns 0, or -1 on a bad argument.
+ */
+int orc_forward(int n_widths, const int* widths, int G, int k, int m, double lo, double hi,
+                const double* W, const double* x, long N, unsigned mask, double* jets)
+{
+    orc_net net = {n_widths, widths, G, k, m, lo, hi};
+    int D = widths[0], L = n_widths - 1;
+    if (widths[L] != 1 || !(mask & 1u)) return -1;
+    int rows[16];
+    int J = mask_rows(mask, D, rows);
+    int n = G + k;
+    double* s = malloc(sizeof(double) * n);
+    double* e = malloc(sizeof(double) * n);
+    orc_support(G, k, lo, hi, s, e);
+    point_tape t;
+    if (tape_alloc(&t, &net, D)) return -1;
+    double xp[8];
+    int w = t.stride;
+    for (long p = 0; p < N; ++p) {
+        for (int d = 0; d < D; ++d) xp[d] = x[(long)d * N + p];
+        point_forward(&net, W, D, s, e, xp, &t);
+        const double* u = t.z + (long)L * w;
+        const double* du = t.dz + (long)L * w * D;
+        const double* d2u = t.d2z + (long)L * w * D;
+        for (int r = 0; r < J; ++r) {
+            int b = rows[r];
+            double v = (b == 0) ? u[0] : (b <= D) ? du[b - 1] : d2u[b - 1 - D];
+            jets[(long)r * N + p] = v;
+        }
+    }
+    tape_free(&t);
+    free(s); free(e);
+    return 0;
+}
+
+/*
+ * Reverse mode of point_forward.  g*, gd*, gd2* hold dL/d(output jets) of the
+ * layer on entry and are overwritten with dL/d(input jets).  dW accumulates.
+ */
+static void layer_backward(const orc_net* net, int l, const double* Wl, double* dWl, int D,
+                           const double* s, const double* e, const double* z,
+                           const double* dz, const double* d2z, const double* gy,
+                           const double* gdy, const double* gd2y, double* gz, double* gdz,
+                           double* gd2z)
+{
+    int I = net->widths[l], O = net->widths[l + 1], n = orc_nbasis(net);
+    for (int j = 0; j < I; ++j) {
+        gz[j] = 0.0;
+        for (int d = 0; d < D; ++d) gdz[j * D + d] = gd2z[j * D + d] = 0.0;
+    }
+    for (int j = 0; j < I; ++j) {
+        for (int i = 0; i < n; ++i) {
+            double b[4];
+            orc_hr_basis(net->m, s[i], e[i], z[j], b);
+            for (int o = 0; o < O; ++o) {
+                long wi = ((long)o * I + j) * n + i;
+                double w = Wl[wi];
+                double gW = gy[o] * b[0];
+                double acc_z = gy[o] * b[1];
+                for (int d = 0; d < D; ++d) {
+                    double zd = dz[j * D + d], zdd = d2z[j * D + d];
+                    double g1 = gdy[o * D + d], g2 = gd2y[o * D + d];
+                    gW += g1 * b[1] * zd + g2 * (b[2] * zd * zd + b[1] * zdd);
+                    acc_z += g1 * b[2] * zd + g2 * (b[3] * zd * zd + b[2] * zdd);
+                    gdz[j * D + d] += w * (g1 * b[1] + g2 * 2.0 * b[2] * zd);
+                    gd2z[j * D + d] += w * g2 * b[1];
+                }
+                dWl[wi] += gW;
+                gz[j] += w * acc_z;
+            }
+        }
+    }
+}
+
+/*
+ * dW (+)= d/dW sum_p sum_r dL_djets[r][p] * jets[r][p].
+ * accumulate = 0 overwrites dW, 1 adds to it.
+ */
+int orc_backward(int n_widths, const int* widths, int G, int k, int m, double lo, double hi,
+                 const double* W, const double* x, long N, unsigned mask, const double* dL_djets,
+                 double* dW, int accumulate)
+{
+    orc_net net = {n_widths, widths, G, k, m, lo, hi};
+    int D = widths[0], L = n_widths - 1;
+    if (widths[L] != 1 || !(mask & 1u)) return -1;
+    int rows[16];
+    int J = mask_rows(mask, D, rows);
+    int n = G + k;
+    long P = orc_param_count(n_widths, widths, G, k);
+    if (!accumulate) memset(dW, 0, sizeof(double) * P);
+    double* s = malloc(sizeof(double) * n);
+    double* e = malloc(sizeof(double) * n);
+    orc_support(G, k, lo, hi, s, e);
+    point_tape t;
+    if (tape_alloc(&t, &net, D)) return -1;
+    int w = t.stride;
+    double *g = calloc(w, sizeof(double)), *gd = calloc((size_t)w * D, sizeof(double)),
+           *gd2 = calloc((size_t)w * D, sizeof(double));
+    double *h = calloc(w, sizeof(double)), *hd = calloc((size_t)w * D, sizeof(double)),
+           *hd2 = calloc((size_t)w * D, sizeof(double));
+    double xp[8];
+    for (long p = 0; p < N; ++p) {
+        for (int d = 0; d < D; ++d) xp[d] = x[(long)d * N + p];
+        point_forward(&net, W, D, s, e, xp, &t);
+        g[0] = 0.0;
+        for (int d = 0; d < D; ++d) gd[d] = gd2[d] = 0.0;
+        for (int r = 0; r < J; ++r) {
+            int b = rows[r];
+            double v = dL_djets[(long)r * N + p];
+            if (b == 0) g[0] = v;
+            else if (b <= D) gd[b - 1] = v;
+            else gd2[b - 1 - D] = v;
+        }
+        for (int l = L - 1; l >= 0; --l) {
+            long off = layer_offset(&net, l);
+            layer_backward(&net, l, W + off, dW + off, D, s, e, t.z + (long)l * w,
+                           t.dz + (long)l * w * D, t.d2z + (long)l * w * D, g, gd, gd2, h, hd,
+                           hd2);
+            int I = widths[l];
+            memcpy(g, h, sizeof(double) * I);
+            memcpy(gd, hd, sizeof(double) * I * D);
+            memcpy(gd2, hd2, sizeof(double) * I * D);
+        }
+    }
+    free(g); free(gd); free(gd2); free(h); free(hd); free(hd2);
+    tape_free(&t);
+    free(s); free(e);
+    return 0;
+}
+
+/* ------------------------------------------------------------------- loss */
+
+enum { ORC_POISSON = 0, ORC_BURGERS = 1 };
+
+static int row_of(unsigned mask, int bit)
+{
+    if (!(mask & (1u << bit))) return -1;
+    int r = 0;
+    for (int b = 0; b < bit; ++b) if (mask & (1u << b)) ++r;
+    return r;
+}
+
+/*
+ * PDE residual and loss, D = 2.
+ *   Poisson (Eq. 3-4, generalised to u* = sin(a pi x) sin(b pi y)):
+ *       r = u_xx + u_yy + (a^2+b^2) pi^2 sin(a pi x) sin(b pi y)
+ *   Burgers (Eq. 6-8 form, coordinates (x, t)):
+ *       r = u_t + lam u u_x - nu u_xx
+ *   L_pde = mean_int r^2, L_bnd = mean_bnd (u - g)^2 (pooled over all edges /
+ *   initial points), L = alpha L_pde + L_bnd.
+ * loss[0] = L, loss[1] = L_pde, loss[2] = L_bnd.
+ * dL_djets_int has the layout of jets_int; dL_du_bnd[N_bnd].
+ * Returns -1 if the mask lacks a row the residual needs.
+ */
+int orc_residual_loss(int kind, double a, double b, double lam, double nu, double alpha,
+                      const double* x_int, long N_int, unsigned mask, const double* jets_int,
+                      const double* u_bnd, const double* g_bnd, long N_bnd, double* loss,
+                      double* dL_djets_int, double* dL_du_bnd)
+{
+    int D = 2, rows[16];
+    int J = mask_rows(mask, D, rows);
+    double Lp = 0.0, Lb = 0.0;
+    if (dL_djets_int) memset(dL_djets_int, 0, sizeof(double) * J * N_int);
+    if (kind == ORC_POISSON) {
+        int rxx = row_of(mask, 1 + D + 0), ryy = row_of(mask, 1 + D + 1);
+        if (rxx < 0 || ryy < 0) return -1;
+        for (long p = 0; p < N_int; ++p) {
+            double xx = x_int[p], yy = x_int[N_int + p];
+            double f = (a * a + b * b) * ORC_PI * ORC_PI * sin(a * ORC_PI * xx) * sin(b * ORC_PI * yy);
+            double r = jets_int[(long)rxx * N_int + p] + jets_int[(long)ryy * N_int + p] + f;
+            Lp += r * r;
+            if (dL_djets_int) {
+                double g = 2.0 * alpha * r / (double)N_int;
+                dL_djets_int[(long)rxx * N_int + p] = g;
+                dL_djets_int[(long)ryy * N_int + p] = g;
+            }
+        }
+    } else if (kind == ORC_BURGERS) {
+        int ru = row_of(mask, 0), rx = row_of(mask, 1), rt = row_of(mask, 2),
+            rxx = row_of(mask, 1 + D + 0);
+        if (ru < 0 || rx < 0 || rt < 0 || rxx < 0) return -1;
+        for (long p = 0; p < N_int; ++p) {
+            double u = jets_int[(long)ru * N_int + p], ux = jets_int[(long)rx * N_int + p];
+            double ut = jets_int[(long)rt * N_int + p], uxx = jets_int[(long)rxx * N_int + p];
+            double r = ut + lam * u * ux - nu * uxx;
+            Lp += r * r;
+            if (dL_djets_int) {
+                double g = 2.0 * alpha * r / (double)N_int;
+                dL_djets_int[(long)rt * N_int + p] = g;
+                dL_djets_int[(long)ru * N_int + p] = g * lam * ux;
+                dL_djets_int[(long)rx * N_int + p] = g * lam * u;
+                dL_djets_int[(long)rxx * N_int + p] = -g * nu;
+            }
+        }
+    } else {
+        return -1;
+    }
+    for (long p = 0; p < N_bnd; ++p) {
+        double d = u_bnd[p] - g_bnd[p];
+        Lb += d * d;
+        if (dL_du_bnd) dL_du_bnd[p] = 2.0 * d / (double)N_bnd;
+    }
+    Lp = N_int > 0 ? Lp / (double)N_int : 0.0;
+    Lb = N_bnd > 0 ? Lb / (double)N_bnd : 0.0;
+    loss[0] = alpha * Lp + Lb;
+    loss[1] = Lp;
+    loss[2] = Lb;
+    return 0;
+}
+
+/* ------------------------------------------------------------------- adam */
+
+/*
+ * Bias-corrected Adam, step t >= 1:
+ *   mom1 <- b1 mom1 + (1-b1) g,  mom2 <- b2 mom2 + (1-b2) g^2,
+ *   W <- W - lr (mom1/(1-b1^t)) / (sqrt(mom2/(1-b2^t)) + eps)
+ */
+void orc_adam(long P, double* W, const double* g, double* mom1, double* mom2, double lr,
+              double b1, double b2, double eps, int t)
+{
+    double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
+    for (long i = 0; i < P; ++i) {
+        mom1[i] = b1 * mom1[i] + (1.0 - b1) * g[i];
+        mom2[i] = b2 * mom2[i] + (1.0 - b2) * g[i] * g[i];
+        W[i] -= lr * (mom1[i] / c1) / (sqrt(mom2[i] / c2) + eps);
+    }
+}
+
+/* ------------------------------------------------------------- train step */
+
+/*
+ * One full-batch training step: forward jets at the interior and boundary
+ * points, residual/loss, backward, Adam.  W, mom1, mom2 are updated in place;
+ * loss[3] is the loss at the weights before the update; dW (may be NULL)
+ * receives the gradient.
+ */
+int orc_train_step(int n_widths, const int* widths, int G, int k, int m, double lo, double hi,
+                   int kind, double a, double b, double lam, double nu, double alpha,
+                   double* W, double* mom1, double* mom2, const double* x_int, long N_int,
+                   unsigned mask_int, const double* x_bnd, const double* g_bnd, long N_bnd,
+                   double lr, double b1, double b2, double eps, int t, double* loss, double* dW)
+{
+    int D = widths[0], rows[16];
+    int J = mask_rows(mask_int, D, rows);
+    long P = orc_param_count(n_widths, widths, G, k);
+    double* jets = malloc(sizeof(double) * (J * N_int + 1));
+    double* gj = malloc(sizeof(double) * (J * N_int + 1));
+    double* ub = malloc(sizeof(double) * (N_bnd + 1));
+    double* gb = malloc(sizeof(double) * (N_bnd + 1));
+    double* g = dW ? dW : malloc(sizeof(double) * P);
+    int rc = 0;
+    rc |= orc_forward(n_widths, widths, G, k, m, lo, hi, W, x_int, N_int, mask_int, jets);
+    rc |= orc_forward(n_widths, widths, G, k, m, lo, hi, W, x_bnd, N_bnd, 1u, ub);
+    if (!rc)
+        rc |= orc_residual_loss(kind, a, b, lam, nu, alpha, x_int, N_int, mask_int, jets, ub,
+                                g_bnd, N_bnd, loss, gj, gb);
+    if (!rc) {
+        rc |= orc_backward(n_widths, widths, G, k, m, lo, hi, W, x_int, N_int, mask_int, gj, g, 0);
+        rc |= orc_backward(n_widths, widths, G, k, m, lo, hi, W, x_bnd, N_bnd, 1u, gb, g, 1);
+    }
+    if (!rc) orc_adam(P, W, g, mom1, mom2, lr, b1, b2, eps, t);
+    free(jets); free(gj); free(ub); free(gb);
+    if (!dW) free(g);
+    return rc;
+}

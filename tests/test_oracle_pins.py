@@ -1,0 +1,403 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: hand-derived
+closed forms (golden files), a polynomial expansion of Eq. 2 differentiated by
+numpy, the ReLU-KAN basis of Eq. 1 (the m = 2 case), symbolic differentiation
+(sympy) of a small network, central finite differences, manufactured PDE
+solutions with zero residual, and torch.optim.Adam in float64.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_14248_gb300 import inputs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ support
+
+
+def test_support_matches_bspline_supports_g5_k3():
+    """Section 2.1-2.2: n = g + k = 8 supports of B_{5,3} on [-1, 1]."""
+    gold = np.loadtxt(os.path.join(GOLD, "support_g5_k3.txt"))
+    s, e = oracle.support(5, 3, -1.0, 1.0)
+    assert len(s) == 8
+    np.testing.assert_allclose(s, gold[:, 1], atol=1e-15)
+    np.testing.assert_allclose(e, gold[:, 2], atol=1e-15)
+
+
+def test_every_interior_point_lies_in_k_plus_1_supports():
+    s, e = oracle.support(10, 3, -1.0, 1.0)
+    xs = np.random.default_rng(0).uniform(-1, 1, 500)
+    for x in xs:
+        assert np.sum((x > s) & (x < e)) == 4
+
+
+# -------------------------------------------------------------------- basis
+
+
+def test_basis_golden_values_m4():
+    """Section 3, Eq. 2: hand-derived exact values of v_{4,4} and derivatives."""
+    gold = np.loadtxt(os.path.join(GOLD, "hr_basis_m4.txt"))
+    for row in gold:
+        got = oracle.hr_basis(4, -0.6, 1.0, row[0])
+        np.testing.assert_allclose(got, row[1:], rtol=1e-13, atol=1e-12)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 6])
+def test_basis_peak_one_at_midpoint_and_zero_outside(m):
+    """Eq. 2: c_m normalises the height of each basis to 1 at the midpoint."""
+    s, e = -0.3, 0.9
+    assert oracle.hr_basis(m, s, e, 0.3)[0] == pytest.approx(1.0, rel=1e-14)
+    for x in (-1.0, s, e, 2.0):
+        assert oracle.hr_basis(m, s, e, x)[0] == 0.0
+
+
+@pytest.mark.parametrize("m", [2, 3, 4, 6])
+def test_basis_matches_polynomial_expansion(m):
+    """Eq. 2 inside (s, e) is c_m ((e-x)(x-s))^m; numpy expands and differentiates it."""
+    s, e = -1.4, 0.2
+    c = (2.0 / (e - s)) ** (2 * m)
+    p = np.polynomial.Polynomial([-e * s, e + s, -1.0])  # (e-x)(x-s)
+    P = c * p ** m
+    ders = [P, P.deriv(1), P.deriv(2), P.deriv(3)]
+    # the monomial expansion cancels near the knots: compare on each derivative's own scale
+    scale = np.array([np.abs(d(np.linspace(s, e, 401))).max() for d in ders])
+    for x in np.random.default_rng(m).uniform(s + 1e-3, e - 1e-3, 40):
+        got = oracle.hr_basis(m, s, e, x)
+        want = np.array([d(x) for d in ders])
+        np.testing.assert_allclose(got, want, rtol=1e-8, atol=1e-10 * scale.max())
+        assert np.all(np.abs(got - want) <= 1e-10 * scale)
+
+
+def test_m2_equals_relu_kan_square_of_relu():
+    """Eq. 1 (ReLU-KAN): r_i = [ReLU(e-x) ReLU(x-s)]^2 * 16/(e-s)^4 is the m = 2 case."""
+    s, e = -0.6, 1.0
+    for x in np.linspace(-1.0, 1.4, 97):
+        r = (max(e - x, 0.0) * max(x - s, 0.0)) ** 2 * 16.0 / (e - s) ** 4
+        assert oracle.hr_basis(2, s, e, x)[0] == pytest.approx(r, rel=1e-14, abs=1e-300)
+
+
+@pytest.mark.parametrize("m", [2, 3, 4, 5])
+def test_basis_integral_closed_form(m):
+    """int v = (e-s) 2^{2m} (m!)^2 / (2m+1)!  (Beta integral of (1-u^2)^m)."""
+    from scipy.integrate import quad
+    s, e = -0.2, 1.4
+    val, _ = quad(lambda x: oracle.hr_basis(m, s, e, x)[0], s, e, epsabs=1e-14, epsrel=1e-13)
+    want = (e - s) * 2 ** (2 * m) * math.factorial(m) ** 2 / math.factorial(2 * m + 1)
+    assert val == pytest.approx(want, rel=1e-11)
+
+
+def test_basis_symmetry_and_smoothness_at_knots():
+    """v(s+e-x) = v(x); for m = 4 the derivatives up to order 3 vanish at the knots
+    (Section 3: smooth, C^{m-1} at the ends of the support)."""
+    m, s, e = 4, -0.6, 1.0
+    for x in np.random.default_rng(1).uniform(s, e, 30):
+        a = oracle.hr_basis(m, s, e, x)
+        b = oracle.hr_basis(m, s, e, s + e - x)
+        np.testing.assert_allclose(a * np.array([1, -1, 1, -1]), b, rtol=1e-10, atol=1e-10)
+    # the r-th derivative vanishes like delta^{m-r} next to each knot
+    for knot, sign in ((s, 1.0), (e, -1.0)):
+        a = np.abs(oracle.hr_basis(m, s, e, knot + sign * 1e-6))
+        b = np.abs(oracle.hr_basis(m, s, e, knot + sign * 1e-7))
+        np.testing.assert_allclose(a / b, [1e4, 1e3, 1e2, 1e1], rtol=1e-4)
+
+
+def test_m2_second_derivative_jumps_at_support_end():
+    """Section 3: the square-of-ReLU second derivative jumps at the end points; HR (m=4) does not."""
+    s, e = -0.6, 1.0
+    inside = oracle.hr_basis(2, s, e, s + 1e-9)[2]
+    assert inside == pytest.approx(2 * 16.0 / (e - s) ** 2, rel=1e-6)
+    assert abs(oracle.hr_basis(4, s, e, s + 1e-9)[2]) < 1e-12
+
+
+# ------------------------------------------------------------------ network
+
+
+def _sympy_network_at(widths, G, k, m, lo, hi, W, point):
+    """The network of Sections 1-3 as a sympy expression in (x, y), valid near `point`:
+    each basis of Eq. 2 enters as its polynomial piece c_m ((e-z)(x-s))^m where its ReLUs
+    are active at the point, and not at all where it is zero there."""
+    sp = pytest.importorskip("sympy")
+    X = sp.symbols("x0:%d" % widths[0], real=True)
+    h = (hi - lo) / G
+    n = G + k
+    z = list(X)
+    zn = [float(v) for v in point]
+    off = 0
+    for l in range(len(widths) - 1):
+        I, O = widths[l], widths[l + 1]
+        Wl = W[off: off + O * I * n].reshape(O, I, n)
+        off += O * I * n
+        out, outn = [], []
+        for o in range(O):
+            expr, val = 0, 0.0
+            for j in range(I):
+                for i in range(n):
+                    s = lo + (i - k) * h
+                    e = lo + (i + 1) * h
+                    if s < zn[j] < e:
+                        c = (2.0 / (e - s)) ** (2 * m)
+                        expr += float(Wl[o, j, i]) * c * ((e - z[j]) * (z[j] - s)) ** m
+                        val += float(Wl[o, j, i]) * c * ((e - zn[j]) * (zn[j] - s)) ** m
+            out.append(sp.expand(expr) if l == 0 else expr)
+            outn.append(val)
+        z, zn = out, outn
+    return X, z[0]
+
+
+def test_forward_jets_match_symbolic_differentiation():
+    """Brute force on 8 points: jets of a [2,2,1] net vs sympy derivatives of its definition."""
+    sp = pytest.importorskip("sympy")
+    net = dict(widths=[2, 2, 1], G=5, k=3, m=4, lo=-1.0, hi=1.0)
+    P = oracle.param_count(net)
+    W = np.random.default_rng(3).normal(0, 0.5, P)
+    x = np.random.default_rng(4).uniform(-1, 1, (2, 8))
+    jets = oracle.forward(net, W, x, 0x1F)
+    for p in range(8):
+        X, u = _sympy_network_at(net["widths"], 5, 3, 4, -1.0, 1.0, W, x[:, p])
+        exprs = [u, sp.diff(u, X[0]), sp.diff(u, X[1]), sp.diff(u, X[0], 2), sp.diff(u, X[1], 2)]
+        sub = {X[0]: x[0, p], X[1]: x[1, p]}
+        want = np.array([float(e.evalf(subs=sub)) for e in exprs])
+        np.testing.assert_allclose(jets[:, p], want, rtol=1e-9, atol=1e-9)
+
+
+def test_single_layer_net_is_weighted_basis_sum():
+    """A [1,1] net is u(x) = sum_i w_i v_i(x), here with v_i from the polynomial expansion."""
+    net = dict(widths=[1, 1], G=4, k=3, m=4, lo=-1.0, hi=1.0)
+    n = 7
+    w = np.random.default_rng(5).normal(size=n)
+    s, e = -1.0 + (np.arange(n) - 3) * 0.5, -1.0 + (np.arange(n) + 1) * 0.5
+    x = np.random.default_rng(6).uniform(-1, 1, (1, 50))
+    jets = oracle.forward(net, w, x, 0b111)
+    want = np.zeros((3, 50))
+    for i in range(n):
+        c = (2.0 / (e[i] - s[i])) ** 8
+        P = c * np.polynomial.Polynomial([-e[i] * s[i], e[i] + s[i], -1.0]) ** 4
+        inside = (x[0] > s[i]) & (x[0] < e[i])
+        for r in range(3):
+            want[r] += w[i] * np.where(inside, P.deriv(r)(x[0]), 0.0)
+    np.testing.assert_allclose(jets, want, rtol=1e-10, atol=1e-9)
+
+
+@pytest.mark.parametrize("widths,G", [([2, 3, 1], 5), ([2, 4, 3, 1], 7)])
+def test_forward_jets_match_central_differences(widths, G):
+    net = dict(widths=widths, G=G, k=3, m=4, lo=-1.0, hi=1.0)
+    W = np.random.default_rng(7).normal(0, 0.3, oracle.param_count(net))
+    x = np.random.default_rng(8).uniform(-0.9, 0.9, (2, 16))
+    jets = oracle.forward(net, W, x, 0x1F)
+    u = lambda xx: oracle.forward(net, W, xx, 0x1)[0]
+    for d in range(2):
+        h1, h2 = 1e-6, 1e-4
+        e = np.zeros((2, 1)); e[d] = 1.0
+        fd1 = (u(x + h1 * e) - u(x - h1 * e)) / (2 * h1)
+        fd2 = (u(x + h2 * e) - 2 * u(x) + u(x - h2 * e)) / h2 ** 2
+        np.testing.assert_allclose(jets[1 + d], fd1, rtol=1e-6, atol=1e-7)
+        np.testing.assert_allclose(jets[3 + d], fd2, rtol=1e-4, atol=1e-4 * np.abs(fd2).max())
+
+
+def test_mask_selects_rows_in_bit_order():
+    net = dict(widths=[2, 3, 1], G=5, k=3, m=4, lo=-1.0, hi=1.0)
+    W = np.random.default_rng(9).normal(0, 0.3, oracle.param_count(net))
+    x = np.random.default_rng(10).uniform(-1, 1, (2, 5))
+    full = oracle.forward(net, W, x, 0x1F)
+    np.testing.assert_array_equal(oracle.forward(net, W, x, inputs.MASK_BURGERS), full[[0, 1, 2, 3]])
+    np.testing.assert_array_equal(oracle.forward(net, W, x, 0x1 | 0x4 | 0x10), full[[0, 2, 4]])
+
+
+def test_points_outside_extended_grid_are_dead():
+    """Inputs beyond [lo - k h, hi + k h] touch no basis: the first layer outputs 0, so two
+    such points share one output value and every input derivative is exactly zero."""
+    net = dict(widths=[2, 3, 1], G=5, k=3, m=4, lo=-1.0, hi=1.0)
+    W = np.random.default_rng(11).normal(0, 0.3, oracle.param_count(net))
+    x = np.array([[2.3, -2.5, -2.21], [-3.0, 3.0, 2.5]])
+    jets = oracle.forward(net, W, x, 0x1F)
+    assert np.all(jets[1:] == 0.0)
+    assert jets[0, 0] == jets[0, 1] == jets[0, 2]
+    single = oracle.forward(dict(net, widths=[3, 1]), W[48:], np.zeros((3, 1)), 0x1)
+    assert jets[0, 0] == pytest.approx(single[0, 0], rel=1e-15)
+
+
+# --------------------------------------------------------------------- loss
+
+
+def test_poisson_residual_zero_on_manufactured_solution():
+    """Eq. 3-4: the exact jets of u* = sin(a pi x) sin(b pi y) give r = 0."""
+    rng = np.random.default_rng(12)
+    for a, b in [(1, 1), (2, 2), (3, 1)]:
+        x = rng.uniform(-1, 1, (2, 64))
+        su, sv = np.sin(a * np.pi * x[0]), np.sin(b * np.pi * x[1])
+        cu, cv = np.cos(a * np.pi * x[0]), np.cos(b * np.pi * x[1])
+        jets = np.stack([su * sv, a * np.pi * cu * sv, b * np.pi * su * cv,
+                         -(a * np.pi) ** 2 * su * sv, -(b * np.pi) ** 2 * su * sv])
+        prob = dict(kind=oracle.POISSON, a=a, b=b, alpha=0.05)
+        loss, dj, _ = oracle.residual_loss(prob, x, 0x1F, jets, np.zeros(4), np.zeros(4))
+        assert loss[1] < 1e-24
+        assert np.abs(dj).max() < 1e-12
+
+
+def test_burgers_residual_zero_on_cole_hopf_solution():
+    """Eq. 6-8 form: u = 2 nu pi e^{-nu pi^2 t} sin(pi x) / (a0 + e^{-nu pi^2 t} cos(pi x))
+    solves u_t + u u_x = nu u_xx exactly (Cole-Hopf); sympy supplies its jets."""
+    sp = pytest.importorskip("sympy")
+    X, T = sp.symbols("x t", real=True)
+    nu, a0 = 0.05, 2.0
+    E = sp.exp(-nu * sp.pi ** 2 * T)
+    u = 2 * nu * sp.pi * E * sp.sin(sp.pi * X) / (a0 + E * sp.cos(sp.pi * X))
+    fs = [sp.lambdify((X, T), f, "numpy") for f in (u, sp.diff(u, X), sp.diff(u, T), sp.diff(u, X, 2))]
+    x = np.random.default_rng(13).uniform([[-1], [0]], [[1], [1]], (2, 64))
+    jets = np.stack([f(x[0], x[1]) for f in fs])
+    prob = dict(kind=oracle.BURGERS, lam=1.0, nu=nu, alpha=1.0)
+    loss, _, _ = oracle.residual_loss(prob, x, inputs.MASK_BURGERS, jets, np.zeros(1), np.zeros(1))
+    assert loss[1] < 1e-26
+
+
+def test_loss_of_zero_network_is_mean_source_squared():
+    """W = 0 gives u = 0: L = alpha mean(f^2) + mean(g^2)."""
+    w = inputs.WORKLOADS["poisson_2_5_1"]
+    d = inputs.make(w, n_int=200, n_bnd=40)
+    net = w.net
+    W = np.zeros(oracle.param_count(net))
+    x = d["x_int"].astype(np.float64)
+    g = np.random.default_rng(14).normal(size=40)
+    jets = oracle.forward(net, W, x, 0x1F)
+    ub = oracle.forward(net, W, d["x_bnd"], 0x1)[0]
+    alpha = 0.05
+    loss, _, _ = oracle.residual_loss(dict(kind=oracle.POISSON, a=1, b=1, alpha=alpha), x, 0x1F, jets, ub, g)
+    f = 2 * np.pi ** 2 * np.sin(np.pi * x[0]) * np.sin(np.pi * x[1])
+    assert loss[0] == pytest.approx(alpha * np.mean(f ** 2) + np.mean(g ** 2), rel=1e-13)
+
+
+@pytest.mark.parametrize("kind", [oracle.POISSON, oracle.BURGERS])
+def test_loss_gradient_wrt_jets_matches_central_differences(kind):
+    rng = np.random.default_rng(15)
+    mask = 0x1F if kind == oracle.POISSON else inputs.MASK_BURGERS
+    J = oracle.n_rows(mask)
+    x = rng.uniform(-1, 1, (2, 12))
+    jets = rng.normal(size=(J, 12))
+    ub, gb = rng.normal(size=6), rng.normal(size=6)
+    prob = dict(kind=kind, a=2, b=1, lam=0.7, nu=0.3, alpha=0.4)
+    _, dj, du = oracle.residual_loss(prob, x, mask, jets, ub, gb)
+    h = 1e-6
+    for r in range(J):
+        for p in range(0, 12, 5):
+            jp, jm = jets.copy(), jets.copy()
+            jp[r, p] += h; jm[r, p] -= h
+            fd = (oracle.residual_loss(prob, x, mask, jp, ub, gb)[0][0]
+                  - oracle.residual_loss(prob, x, mask, jm, ub, gb)[0][0]) / (2 * h)
+            assert dj[r, p] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+    for p in range(6):
+        up, um = ub.copy(), ub.copy()
+        up[p] += h; um[p] -= h
+        fd = (oracle.residual_loss(prob, x, mask, jets, up, gb)[0][0]
+              - oracle.residual_loss(prob, x, mask, jets, um, gb)[0][0]) / (2 * h)
+        assert du[p] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+# ----------------------------------------------------------------- backward
+
+
+def _total_loss(net, prob, W, x_int, mask, x_bnd, g_bnd):
+    jets = oracle.forward(net, W, x_int, mask)
+    ub = oracle.forward(net, W, x_bnd, 0x1)[0]
+    loss, dj, du = oracle.residual_loss(prob, x_int, mask, jets, ub, g_bnd)
+    return loss[0], dj, du
+
+
+@pytest.mark.parametrize("case", ["poisson", "burgers"])
+def test_weight_gradient_matches_central_differences(case):
+    """Hand-written backward vs central FD (h = 1e-6, FP64) on 64 random weights."""
+    rng = np.random.default_rng(16)
+    if case == "poisson":
+        net = dict(widths=[2, 4, 3, 1], G=5, k=3, m=4, lo=-1.0, hi=1.0)
+        prob = dict(kind=oracle.POISSON, a=1, b=2, alpha=0.5)
+        mask = 0x1F
+        x_int = rng.uniform(-1, 1, (2, 40))
+        x_bnd = np.stack([rng.choice([-1.0, 1.0], 12), rng.uniform(-1, 1, 12)])
+    else:
+        net = dict(widths=[2, 3, 3, 1], G=6, k=3, m=4, lo=-1.0, hi=1.0)
+        prob = dict(kind=oracle.BURGERS, lam=1.0, nu=0.01 / np.pi, alpha=1.0)
+        mask = inputs.MASK_BURGERS
+        x_int = np.stack([rng.uniform(-1, 1, 40), rng.uniform(0, 1, 40)])
+        x_bnd = np.stack([rng.uniform(-1, 1, 12), np.zeros(12)])
+    g_bnd = rng.normal(0, 0.3, x_bnd.shape[1])
+    P = oracle.param_count(net)
+    W = rng.normal(0, 0.4, P)
+    _, dj, du = _total_loss(net, prob, W, x_int, mask, x_bnd, g_bnd)
+    dW = oracle.backward(net, W, x_int, mask, dj)
+    oracle.backward(net, W, x_bnd, 0x1, du[None, :], dW)
+    idx = rng.choice(P, size=min(64, P), replace=False)
+    h = 1e-6
+    for i in idx:
+        Wp, Wm = W.copy(), W.copy()
+        Wp[i] += h; Wm[i] -= h
+        fd = (_total_loss(net, prob, Wp, x_int, mask, x_bnd, g_bnd)[0]
+              - _total_loss(net, prob, Wm, x_int, mask, x_bnd, g_bnd)[0]) / (2 * h)
+        assert dW[i] == pytest.approx(fd, rel=2e-5, abs=2e-8 * max(1.0, np.abs(dW).max()))
+
+
+def test_backward_accumulate_flag():
+    net = dict(widths=[2, 3, 1], G=5, k=3, m=4, lo=-1.0, hi=1.0)
+    rng = np.random.default_rng(17)
+    W = rng.normal(0, 0.3, oracle.param_count(net))
+    x = rng.uniform(-1, 1, (2, 10))
+    g = rng.normal(size=(1, 10))
+    a = oracle.backward(net, W, x, 0x1, g)
+    b = oracle.backward(net, W, x, 0x1, g, a.copy())
+    np.testing.assert_allclose(b, 2 * a, rtol=1e-12, atol=1e-300)
+
+
+# --------------------------------------------------------------------- adam
+
+
+def test_adam_first_step_closed_form():
+    """Step 1: the bias corrections cancel, so w1 = w0 - lr g / (|g| + eps)."""
+    rng = np.random.default_rng(18)
+    W0 = rng.normal(size=50)
+    g = rng.normal(size=50)
+    W, m1, m2 = W0.copy(), np.zeros(50), np.zeros(50)
+    oracle.adam(W, g, m1, m2, 1e-2, 0.9, 0.999, 1e-8, 1)
+    np.testing.assert_allclose(W, W0 - 1e-2 * g / (np.abs(g) + 1e-8), rtol=1e-14)
+
+
+def test_adam_matches_torch_optim_adam_float64():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(19)
+    W0 = rng.normal(size=30)
+    grads = rng.normal(size=(6, 30))
+    p = torch.nn.Parameter(torch.tensor(W0, dtype=torch.float64))
+    opt = torch.optim.Adam([p], lr=3e-3, betas=(0.9, 0.999), eps=1e-8)
+    W, m1, m2 = W0.copy(), np.zeros(30), np.zeros(30)
+    for t in range(6):
+        p.grad = torch.tensor(grads[t], dtype=torch.float64)
+        opt.step()
+        oracle.adam(W, grads[t], m1, m2, 3e-3, 0.9, 0.999, 1e-8, t + 1)
+    np.testing.assert_allclose(W, p.detach().numpy(), rtol=1e-13, atol=1e-15)
+
+
+# --------------------------------------------------------------- train step
+
+
+def test_train_step_equals_composition_and_loss_decreases():
+    w = inputs.WORKLOADS["poisson_2_5_1"]
+    d = inputs.make(w, n_int=256, n_bnd=64)
+    net, prob = w.net, w.problem()
+    W = d["W"].astype(np.float64)
+    m1, m2 = np.zeros_like(W), np.zeros_like(W)
+    loss0, dj, du = _total_loss(net, prob, W, d["x_int"], 0x1F, d["x_bnd"], d["g_bnd"])
+    g = oracle.backward(net, W, d["x_int"], 0x1F, dj)
+    oracle.backward(net, W, d["x_bnd"], 0x1, du[None], g)
+    Wc = W.copy()
+    loss, dW = oracle.train_step(net, prob, W, m1, m2, d["x_int"], 0x1F, d["x_bnd"], d["g_bnd"], 1e-2, 1)
+    assert loss[0] == pytest.approx(loss0, rel=1e-14)
+    np.testing.assert_allclose(dW, g, rtol=1e-13, atol=1e-16)
+    np.testing.assert_allclose(W, Wc - 1e-2 * g / (np.abs(g) + 1e-8), rtol=1e-13)
+    losses = [loss[0]]
+    for t in range(2, 30):
+        losses.append(oracle.train_step(net, prob, W, m1, m2, d["x_int"], 0x1F, d["x_bnd"], d["g_bnd"],
+                                        1e-2, t)[0][0])
+    assert losses[-1] < 0.5 * losses[0]
