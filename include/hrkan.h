@@ -1,0 +1,220 @@
+/*
+ * hrkan.h — C ABI of the GB300 (sm_103a) HRKAN physics-informed training library.
+ *
+ * The library evaluates Higher-order-ReLU KANs (Section 3, Eq. 2 of
+ * "Higher-order-ReLU-KANs (HRKANs) for solving physics-informed neural
+ * networks (PINNs) more accurately, robustly and faster") together with the
+ * input-derivative jets a PDE residual needs, the residual/loss of the Poisson
+ * (Eq. 3-4) and Burgers (Eq. 6-8) problems, a hand-written weight-gradient
+ * backward and the Adam update (Section 4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Pointers named W, dW, x, jets, tape, loss, dL_* are DEVICE pointers owned by
+ *   the caller; the library never frees them.  Structs passed by pointer
+ *   (hrkan_cfg, pinn_problem) are HOST memory, read during the call only.
+ * - A network with widths [w_0, ..., w_L] (w_0 = D = 2 input coordinates,
+ *   w_L = 1 output) has L layers.  Layer l maps I = w_l units to O = w_{l+1}
+ *   units with weights W_l[O][I][n], n = G + k bases per input unit (row-major,
+ *   basis index fastest).  W is the concatenation of W_0 .. W_{L-1}, float32;
+ *   its length P is hrkan_param_count().  Layer output o is
+ *       y_o = sum_j sum_i W_l[o][j][i] v_i(z_j)
+ *   with no bias, no base branch and no normalisation between layers.
+ * - Supports (Sections 2.1-2.2, "the same support as the B-spline basis"):
+ *   h = (grid_hi - grid_lo)/G, s_i = grid_lo + (i-k)h, e_i = grid_lo + (i+1)h,
+ *   i = 0..n-1, the same for every layer.  Inputs outside [s_0, e_{n-1}] touch
+ *   no basis (all contributions are exactly zero).
+ * - Coordinates x are structure-of-arrays float32 [D][N] (x[d*N + p]).
+ * - Jet rows: bit 0 of a jet mask selects u, bit 1+d selects du/dx_d, bit 1+D+d
+ *   selects d2u/dx_d^2 (D = 2: 0x1F = u,u_x,u_y,u_xx,u_yy; 0x0F = u,u_x,u_t,u_xx
+ *   with coordinates (x, t)).  A second-order bit requires the first-order bit
+ *   of the same dimension.  Jet arrays are float32 [J][N], rows in bit order,
+ *   J = popcount(mask).
+ * - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *   default stream).  Argument errors are detected before anything is
+ *   enqueued and return HRKAN_EINVAL (or HRKAN_EUNSUPPORTED for valid but
+ *   unimplemented shapes); a launch failure returns HRKAN_ECUDA.  On any
+ *   non-OK status hrkan_last_error() holds a message.
+ * - A handle is not thread-safe: calls on one handle must not overlap in
+ *   time from several host threads.  Work enqueued on different streams for
+ *   the same handle must not overlap on the GPU (they share its workspace).
+ */
+#ifndef HRKAN_H
+#define HRKAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hrkan_ctx* hrkan_t;   /* opaque, owned by the library */
+typedef void* hrkan_stream_t;        /* a cudaStream_t */
+
+enum hrkan_status {
+    HRKAN_OK = 0,
+    HRKAN_EINVAL = -1,        /* bad argument (null pointer, bad size or mask) */
+    HRKAN_ENOMEM = -2,        /* device or host allocation failed */
+    HRKAN_ECUDA = -3,         /* a CUDA call or kernel launch failed */
+    HRKAN_EUNSUPPORTED = -4,  /* valid request that this build does not implement */
+    HRKAN_ETIMEOUT = -5,      /* a bounded device-side wait gave up */
+    HRKAN_ENONFINITE = -6     /* the loss became NaN or infinite */
+};
+
+enum hrkan_prec { HRKAN_FP32 = 0, HRKAN_BF16 = 1, HRKAN_TF32 = 2 };
+enum hrkan_pde { HRKAN_POISSON = 0, HRKAN_BURGERS = 1 };
+
+#define HRKAN_MAX_WIDTHS 8
+
+typedef struct hrkan_cfg {
+    int n_widths;                    /* L + 1, in [2, HRKAN_MAX_WIDTHS] */
+    int widths[HRKAN_MAX_WIDTHS];    /* widths[0] = 2 (D), widths[n_widths-1] = 1, all <= 64 */
+    int G;                           /* grid intervals on [grid_lo, grid_hi], >= 1 */
+    int k;                           /* support width in cells minus one (B-spline order); 3 */
+    int m;                           /* HR order of Eq. 2; 4 */
+    int prec;                        /* enum hrkan_prec: arithmetic of the jet contraction */
+    double grid_lo, grid_hi;         /* grid_lo < grid_hi */
+    int n_instances;                 /* independent networks sharing the shape (>= 1) */
+    int reserved;
+    size_t hbm_budget_bytes;         /* advisory cap for stored layer jets (tape); 0 = none */
+} hrkan_cfg;
+
+/*
+ * A PINN problem (Section 4).  Residual r per interior point:
+ *   HRKAN_POISSON: r = u_xx + u_yy + (a^2+b^2) pi^2 sin(a pi x) sin(b pi y)
+ *                  (Eq. 3 with a = b = 1: u* = sin(pi x) sin(pi y))
+ *   HRKAN_BURGERS: r = u_t + lam u u_x - nu u_xx, coordinates (x, t)
+ *                  (Eq. 6 has lam = 1; the rescaled Eq. 7 has lam = 1/4, nu/16)
+ * Loss (Eq. 4, Eq. 8): L = alpha mean_int(r^2) + mean_bnd((u - g)^2), the
+ * boundary mean pooled over every boundary and initial-condition point.
+ */
+typedef struct pinn_problem {
+    int kind;       /* enum hrkan_pde */
+    int reserved;
+    double a, b;    /* Poisson source frequencies */
+    double lam, nu; /* Burgers advection and viscosity coefficients */
+    double alpha;   /* weight of the PDE term */
+} pinn_problem;
+
+/* Number of float weights P of one network of this shape (0 on a bad cfg). */
+int64_t hrkan_param_count(const hrkan_cfg* cfg);
+
+/*
+ * Create a handle for networks of shape cfg (the problem statement of
+ * Section 4: widths, grid g, order k, HR order m).  Allocates the device
+ * workspace and the FP64 Adam moments (zeroed) on the current device.
+ * Returns HRKAN_EINVAL for an invalid cfg, HRKAN_EUNSUPPORTED for a valid
+ * shape this build has no kernels for, HRKAN_ENOMEM if allocation fails.
+ */
+int hrkan_init(hrkan_t* out, const hrkan_cfg* cfg);
+
+/* Release the handle and its device memory (synchronises the device). NULL is a no-op. */
+void hrkan_destroy(hrkan_t h);
+
+/* Message of the last non-OK status returned on this host thread ("" if none). */
+const char* hrkan_last_error(void);
+
+/*
+ * Floats of tape that hrkan_forward_jets may fill for N points under mask so
+ * that hrkan_backward can skip recomputing the forward (0: the shape always
+ * recomputes, pass NULL).
+ */
+int64_t hrkan_tape_floats(hrkan_t h, int64_t N, unsigned jet_mask);
+
+/*
+ * Network output jets at N points (Sections 1-3: the KAN layer as a matrix
+ * operation, Eq. 2 bases; jets by the chain rule, Eq. 3 and Eq. 6 need them).
+ *   W     [P] float32, x [2][N], jets [J][N] (written).
+ *   tape  NULL, or hrkan_tape_floats(h, N, jet_mask) floats to keep the layer
+ *         jets for hrkan_backward.
+ * N = 0 is a valid no-op.
+ */
+int hrkan_forward_jets(hrkan_t h, const float* W, const float* x, int64_t N, unsigned jet_mask,
+                       float* jets, float* tape, hrkan_stream_t stream);
+
+/*
+ * Residual and loss (Eq. 3-4 / Eq. 6-8) from precomputed jets.
+ *   x_int [2][N_int], jets_int [J][N_int] under jet_mask (Poisson needs u_xx,
+ *   u_yy; Burgers needs u, u_x, u_t, u_xx), u_bnd / g_bnd [N_bnd] network
+ *   values and targets at the boundary/initial points.
+ *   loss          [3] float64 device: L, mean r^2, mean (u-g)^2 (written).
+ *   dL_djets_int  [J][N_int] (written; NULL to skip), dL_du_bnd [N_bnd]
+ *                 (written; NULL to skip).
+ * The loss is summed per point in float32, per block in float64, and across
+ * blocks in float64 with compensated (Neumaier) summation in a fixed order.
+ */
+int pinn_residual_loss(hrkan_t h, const pinn_problem* prob, const float* x_int, int64_t N_int,
+                       unsigned jet_mask, const float* jets_int, const float* u_bnd,
+                       const float* g_bnd, int64_t N_bnd, double* loss, float* dL_djets_int,
+                       float* dL_du_bnd, hrkan_stream_t stream);
+
+/*
+ * Weight gradient of sum_{r,p} dL_djets[r][p] * jets[r][p] (reverse mode of
+ * hrkan_forward_jets; the training of Section 4 needs it for Adam).
+ *   tape        NULL (recompute the forward) or the tape of a preceding
+ *               hrkan_forward_jets on the same W, x, N, jet_mask.
+ *   dW          [P] float32: overwritten (accumulate = 0) or added to (1).
+ * Cross-block sums run in a fixed order; within a block float32 atomics in
+ * shared memory make the last bits order-dependent.
+ */
+int hrkan_backward(hrkan_t h, const float* W, const float* x, int64_t N, unsigned jet_mask,
+                   const float* tape, const float* dL_djets, float* dW, int accumulate,
+                   hrkan_stream_t stream);
+
+/*
+ * Adam step t >= 1 on W [P] float32 with gradient dW [P] (Section 4 trains
+ * every model with Adam).  The first and second moments live in the handle in
+ * float64 (zeroed by hrkan_init and hrkan_reset_moments):
+ *   m <- b1 m + (1-b1) g;  v <- b2 v + (1-b2) g^2;
+ *   W <- W - lr (m/(1-b1^t)) / (sqrt(v/(1-b2^t)) + eps)
+ */
+int adam_step(hrkan_t h, float* W, const float* dW, double lr, double b1, double b2, double eps,
+              int t, hrkan_stream_t stream);
+
+/* Zero the Adam moments and the device step counter of the handle. */
+int hrkan_reset_moments(hrkan_t h, hrkan_stream_t stream);
+
+/*
+ * One full-batch training step, fused: forward jets at the interior and
+ * boundary points, residual and loss, backward, cross-block reduction and
+ * Adam.  Same arithmetic as hrkan_forward_jets + pinn_residual_loss +
+ * hrkan_backward + adam_step; the interior mask is 0x1F for Poisson and 0x0F
+ * for Burgers.
+ *   W      [P] float32, updated in place.
+ *   t      Adam step >= 1, or 0: take the step from a device-side counter of
+ *          the handle (zeroed by hrkan_init / hrkan_reset_moments) and advance
+ *          it on the device, so that one captured CUDA graph of this call can
+ *          be replayed for successive steps.
+ *   loss   [3] float64 device: the loss at W before the update (written).
+ *   dW     NULL, or [P] float32 receiving the gradient.
+ * No host synchronisation; capturable in a CUDA graph after one warm-up call
+ * (with profiling disabled).
+ */
+int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float* x_int,
+                     int64_t N_int, const float* x_bnd, const float* g_bnd, int64_t N_bnd,
+                     double lr, double b1, double b2, double eps, int t, double* loss, float* dW,
+                     hrkan_stream_t stream);
+
+/*
+ * Kernel timing.  While enabled, every kernel the handle launches is
+ * bracketed by two CUDA events on its stream (do not enable it around stream
+ * capture).  hrkan_profile_read waits for the recorded events, adds their
+ * elapsed times to per-class totals, and returns the total milliseconds and
+ * launch count of one class (optionally resetting that class).
+ */
+enum hrkan_kernel_class {
+    HRKAN_KERNEL_FUSED = 0,     /* fused forward+residual+backward (or backward) kernel */
+    HRKAN_KERNEL_REDUCE = 1,    /* cross-block gradient/loss reduction and Adam */
+    HRKAN_KERNEL_FORWARD = 2,   /* forward jets */
+    HRKAN_KERNEL_RESIDUAL = 3,  /* stand-alone residual */
+    HRKAN_KERNEL_CLASSES = 4
+};
+int hrkan_profile_enable(hrkan_t h, int enable);
+int hrkan_profile_read(hrkan_t h, int kernel_class, double* total_ms, int64_t* launches, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HRKAN_H */

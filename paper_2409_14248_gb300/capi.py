@@ -1,0 +1,204 @@
+"""Thin Python binding of the C ABI in include/hrkan.h (ctypes).
+
+Argument marshalling only: every computation runs in libhrkan.so's CUDA
+kernels.  Functions carry the C names and take torch CUDA tensors (float32
+or float64 as the header states), which must be contiguous; the stream
+defaults to torch's current stream.  Any non-OK status raises HRKANError with
+the library's message.  There is no CPU fallback: if libhrkan.so has not been
+built (``paper_2409_14248_gb300.build.build()``) loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhrkan.so")
+
+HRKAN_OK, HRKAN_EINVAL, HRKAN_ENOMEM, HRKAN_ECUDA, HRKAN_EUNSUPPORTED, HRKAN_ETIMEOUT, HRKAN_ENONFINITE = \
+    0, -1, -2, -3, -4, -5, -6
+HRKAN_FP32, HRKAN_BF16, HRKAN_TF32 = 0, 1, 2
+HRKAN_POISSON, HRKAN_BURGERS = 0, 1
+HRKAN_MAX_WIDTHS = 8
+
+# every symbol include/hrkan.h declares
+EXPORTS = ("hrkan_param_count", "hrkan_init", "hrkan_destroy", "hrkan_last_error", "hrkan_tape_floats",
+           "hrkan_forward_jets", "pinn_residual_loss", "hrkan_backward", "adam_step", "hrkan_reset_moments",
+           "hrkan_train_step", "hrkan_profile_enable", "hrkan_profile_read")
+HRKAN_KERNEL_FUSED, HRKAN_KERNEL_REDUCE, HRKAN_KERNEL_FORWARD, HRKAN_KERNEL_RESIDUAL = 0, 1, 2, 3
+
+
+class HRKANError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"status {code}: {msg}")
+        self.code = code
+
+
+class hrkan_cfg(ctypes.Structure):
+    _fields_ = [("n_widths", ctypes.c_int), ("widths", ctypes.c_int * HRKAN_MAX_WIDTHS), ("G", ctypes.c_int),
+                ("k", ctypes.c_int), ("m", ctypes.c_int), ("prec", ctypes.c_int), ("grid_lo", ctypes.c_double),
+                ("grid_hi", ctypes.c_double), ("n_instances", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("hbm_budget_bytes", ctypes.c_size_t)]
+
+
+class pinn_problem(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("reserved", ctypes.c_int), ("a", ctypes.c_double),
+                ("b", ctypes.c_double), ("lam", ctypes.c_double), ("nu", ctypes.c_double),
+                ("alpha", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp, _i64, _u32, _i32, _d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint, ctypes.c_int, ctypes.c_double
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libhrkan.so (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(path)
+        lib.hrkan_param_count.argtypes = [ctypes.POINTER(hrkan_cfg)]
+        lib.hrkan_param_count.restype = _i64
+        lib.hrkan_init.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(hrkan_cfg)]
+        lib.hrkan_destroy.argtypes = [_vp]
+        lib.hrkan_destroy.restype = None
+        lib.hrkan_last_error.restype = ctypes.c_char_p
+        lib.hrkan_tape_floats.argtypes = [_vp, _i64, _u32]
+        lib.hrkan_tape_floats.restype = _i64
+        lib.hrkan_forward_jets.argtypes = [_vp, _vp, _vp, _i64, _u32, _vp, _vp, _vp]
+        lib.pinn_residual_loss.argtypes = [_vp, ctypes.POINTER(pinn_problem), _vp, _i64, _u32, _vp, _vp, _vp, _i64,
+                                           _vp, _vp, _vp, _vp]
+        lib.hrkan_backward.argtypes = [_vp, _vp, _vp, _i64, _u32, _vp, _vp, _vp, _i32, _vp]
+        lib.adam_step.argtypes = [_vp, _vp, _vp, _d, _d, _d, _d, _i32, _vp]
+        lib.hrkan_reset_moments.argtypes = [_vp, _vp]
+        lib.hrkan_train_step.argtypes = [_vp, ctypes.POINTER(pinn_problem), _vp, _vp, _i64, _vp, _vp, _i64, _d, _d,
+                                         _d, _d, _i32, _vp, _vp, _vp]
+        lib.hrkan_profile_enable.argtypes = [_vp, _i32]
+        lib.hrkan_profile_read.argtypes = [_vp, _i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
+        for name in EXPORTS:
+            if name not in ("hrkan_destroy", "hrkan_last_error", "hrkan_param_count", "hrkan_tape_floats"):
+                getattr(lib, name).restype = _i32
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != HRKAN_OK:
+        raise HRKANError(rc, load_library().hrkan_last_error().decode())
+
+
+def _ptr(t, dtype=None):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_cfg(widths, G, k=3, m=4, lo=-1.0, hi=1.0, prec=HRKAN_FP32, n_instances=1, hbm_budget_bytes=0):
+    c = hrkan_cfg()
+    c.n_widths = len(widths)
+    for i, w in enumerate(widths):
+        c.widths[i] = int(w)
+    c.G, c.k, c.m, c.prec = int(G), int(k), int(m), int(prec)
+    c.grid_lo, c.grid_hi = float(lo), float(hi)
+    c.n_instances, c.hbm_budget_bytes = int(n_instances), int(hbm_budget_bytes)
+    return c
+
+
+def make_problem(kind, a=1.0, b=1.0, lam=1.0, nu=0.0, alpha=1.0):
+    return pinn_problem(int(kind), 0, float(a), float(b), float(lam), float(nu), float(alpha))
+
+
+def hrkan_param_count(cfg):
+    return int(load_library().hrkan_param_count(ctypes.byref(cfg)))
+
+
+def hrkan_init(cfg):
+    h = ctypes.c_void_p()
+    _check(load_library().hrkan_init(ctypes.byref(h), ctypes.byref(cfg)))
+    return h
+
+
+def hrkan_destroy(h):
+    load_library().hrkan_destroy(h)
+
+
+def hrkan_tape_floats(h, N, jet_mask):
+    return int(load_library().hrkan_tape_floats(h, int(N), int(jet_mask)))
+
+
+def hrkan_forward_jets(h, W, x, N, jet_mask, jets, tape=None, stream=None):
+    import torch
+    _check(load_library().hrkan_forward_jets(h, _ptr(W, torch.float32), _ptr(x, torch.float32), int(N),
+                                             int(jet_mask), _ptr(jets, torch.float32), _ptr(tape, torch.float32),
+                                             _stream(stream)))
+
+
+def pinn_residual_loss(h, prob, x_int, N_int, jet_mask, jets_int, u_bnd, g_bnd, N_bnd, loss, dL_djets_int=None,
+                       dL_du_bnd=None, stream=None):
+    import torch
+    f = torch.float32
+    _check(load_library().pinn_residual_loss(h, ctypes.byref(prob), _ptr(x_int, f), int(N_int), int(jet_mask),
+                                             _ptr(jets_int, f), _ptr(u_bnd, f), _ptr(g_bnd, f), int(N_bnd),
+                                             _ptr(loss, torch.float64), _ptr(dL_djets_int, f), _ptr(dL_du_bnd, f),
+                                             _stream(stream)))
+
+
+def hrkan_backward(h, W, x, N, jet_mask, tape, dL_djets, dW, accumulate=False, stream=None):
+    import torch
+    f = torch.float32
+    _check(load_library().hrkan_backward(h, _ptr(W, f), _ptr(x, f), int(N), int(jet_mask), _ptr(tape, f),
+                                         _ptr(dL_djets, f), _ptr(dW, f), int(bool(accumulate)), _stream(stream)))
+
+
+def adam_step(h, W, dW, lr, b1=0.9, b2=0.999, eps=1e-8, t=1, stream=None):
+    import torch
+    _check(load_library().adam_step(h, _ptr(W, torch.float32), _ptr(dW, torch.float32), float(lr), float(b1),
+                                    float(b2), float(eps), int(t), _stream(stream)))
+
+
+def hrkan_reset_moments(h, stream=None):
+    _check(load_library().hrkan_reset_moments(h, _stream(stream)))
+
+
+def hrkan_train_step(h, prob, W, x_int, N_int, x_bnd, g_bnd, N_bnd, lr, b1, b2, eps, t, loss, dW=None,
+                     stream=None):
+    import torch
+    f = torch.float32
+    _check(load_library().hrkan_train_step(h, ctypes.byref(prob), _ptr(W, f), _ptr(x_int, f), int(N_int),
+                                           _ptr(x_bnd, f), _ptr(g_bnd, f), int(N_bnd), float(lr), float(b1),
+                                           float(b2), float(eps), int(t), _ptr(loss, torch.float64),
+                                           _ptr(dW, f), _stream(stream)))
+
+
+def hrkan_profile_enable(h, enable=True):
+    _check(load_library().hrkan_profile_enable(h, int(bool(enable))))
+
+
+def hrkan_profile_read(h, kernel_class, reset=True):
+    """(total milliseconds, launches) of one kernel class since the last reset."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(load_library().hrkan_profile_read(h, int(kernel_class), ctypes.byref(ms), ctypes.byref(n), int(reset)))
+    return ms.value, n.value

@@ -1,0 +1,493 @@
+// C ABI of the HRKAN library (declared in include/hrkan.h): argument
+// validation, the handle (workspace and Adam moments), and dispatch to the
+// kernels.  Nothing here computes on the host beyond launch geometry.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hrkan.h"
+#include "internal.h"
+#include "narrow.cuh"
+
+using namespace hrkan;
+
+struct hrkan_ctx {
+    hrkan_cfg cfg;
+    int L = 0;            // layers
+    int n = 0;            // bases per unit
+    int64_t P = 0;        // weights per network
+    int net_id = -1;      // fused narrow shape id
+    Grid grid{};
+    int device = 0;
+    int nsm = 0;
+    int max_grid = 0;     // rows of partial
+    float* partial = nullptr;        // [max_grid][P]
+    int max_grid_l = 0;   // rows of loss_partial
+    double* loss_partial = nullptr;  // [max_grid_l][2]
+    double* m1 = nullptr;
+    double* m2 = nullptr;
+    int* t_counter = nullptr;        // [2] device Adam step counter (t = 0 mode)
+    // kernel timing
+    bool prof = false;
+    struct Ev { cudaEvent_t a, b; int cls; };
+    std::vector<Ev> pending;
+    std::vector<Ev> pool;
+    double prof_ms[HRKAN_KERNEL_CLASSES] = {};
+    int64_t prof_n[HRKAN_KERNEL_CLASSES] = {};
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(HRKAN_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define HR_CUDA(call, what)                          \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+int64_t count_params(const hrkan_cfg* c) {
+    int64_t P = 0, n = int64_t(c->G) + c->k;
+    for (int l = 0; l + 1 < c->n_widths; ++l) P += int64_t(c->widths[l]) * c->widths[l + 1] * n;
+    return P;
+}
+
+int check_cfg(const hrkan_cfg* c) {
+    if (!c) return fail(HRKAN_EINVAL, "cfg is NULL");
+    if (c->n_widths < 2 || c->n_widths > HRKAN_MAX_WIDTHS)
+        return fail(HRKAN_EINVAL, "n_widths=%d outside [2, %d]", c->n_widths, HRKAN_MAX_WIDTHS);
+    for (int l = 0; l < c->n_widths; ++l)
+        if (c->widths[l] < 1 || c->widths[l] > 64)
+            return fail(HRKAN_EINVAL, "widths[%d]=%d outside [1, 64]", l, c->widths[l]);
+    if (c->widths[0] != 2) return fail(HRKAN_EUNSUPPORTED, "widths[0]=%d: only D = 2 inputs", c->widths[0]);
+    if (c->widths[c->n_widths - 1] != 1)
+        return fail(HRKAN_EINVAL, "last width %d: the network has one output", c->widths[c->n_widths - 1]);
+    if (c->G < 1 || c->G > 4096) return fail(HRKAN_EINVAL, "G=%d outside [1, 4096]", c->G);
+    if (c->k < 0 || c->m < 1) return fail(HRKAN_EINVAL, "k=%d, m=%d", c->k, c->m);
+    if (c->k != 3 || c->m != 4) return fail(HRKAN_EUNSUPPORTED, "k=%d, m=%d: this build has k=3, m=4", c->k, c->m);
+    if (!(c->grid_lo < c->grid_hi) || !std::isfinite(c->grid_lo) || !std::isfinite(c->grid_hi))
+        return fail(HRKAN_EINVAL, "grid [%g, %g]", c->grid_lo, c->grid_hi);
+    if (c->n_instances < 1) return fail(HRKAN_EINVAL, "n_instances=%d", c->n_instances);
+    if (c->prec < HRKAN_FP32 || c->prec > HRKAN_TF32) return fail(HRKAN_EINVAL, "prec=%d", c->prec);
+    return HRKAN_OK;
+}
+
+bool valid_mask(unsigned m) {
+    if (!(m & 1u) || (m & ~0x1Fu)) return false;
+    if ((m & 0x08u) && !(m & 0x02u)) return false;
+    if ((m & 0x10u) && !(m & 0x04u)) return false;
+    return true;
+}
+
+
+int use_device(hrkan_t h) {
+    int cur = -1;
+    HR_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
+    if (cur != h->device) HR_CUDA(cudaSetDevice(h->device), "cudaSetDevice");
+    return HRKAN_OK;
+}
+
+PdeParams make_pde(const pinn_problem* p) {
+    PdeParams q{};
+    q.kind = p->kind;
+    q.a = float(p->a);
+    q.b = float(p->b);
+    q.src = float((p->a * p->a + p->b * p->b) * M_PI * M_PI);
+    q.lam = float(p->lam);
+    q.nu = float(p->nu);
+    q.alpha = float(p->alpha);
+    return q;
+}
+
+int check_problem(const pinn_problem* p) {
+    if (!p) return fail(HRKAN_EINVAL, "problem is NULL");
+    if (p->kind != HRKAN_POISSON && p->kind != HRKAN_BURGERS) return fail(HRKAN_EINVAL, "problem kind %d", p->kind);
+    if (!std::isfinite(p->a) || !std::isfinite(p->b) || !std::isfinite(p->lam) || !std::isfinite(p->nu) ||
+        !std::isfinite(p->alpha))
+        return fail(HRKAN_EINVAL, "non-finite problem coefficient");
+    return HRKAN_OK;
+}
+
+// Bracket one launch with CUDA events when profiling is on.
+struct ProfScope {
+    hrkan_t h;
+    cudaStream_t s;
+    int slot = -1;
+    ProfScope(hrkan_t h_, int cls, cudaStream_t s_) : h(h_), s(s_) {
+        if (!h->prof) return;
+        hrkan_ctx::Ev ev{};
+        if (!h->pool.empty()) {
+            ev = h->pool.back();
+            h->pool.pop_back();
+        } else if (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess) {
+            return;
+        }
+        ev.cls = cls;
+        if (cudaEventRecord(ev.a, s) != cudaSuccess) { h->pool.push_back(ev); return; }
+        h->pending.push_back(ev);
+        slot = int(h->pending.size()) - 1;
+    }
+    ~ProfScope() {
+        if (slot >= 0) cudaEventRecord(h->pending[slot].b, s);
+    }
+};
+
+NarrowParams base_params(hrkan_t h, const float* W) {
+    NarrowParams p{};
+    p.W = W;
+    p.grid = h->grid;
+    p.P = h->P;
+    return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t hrkan_param_count(const hrkan_cfg* cfg) {
+    if (check_cfg(cfg) == HRKAN_EINVAL) return 0;
+    return count_params(cfg);
+}
+
+const char* hrkan_last_error(void) { return g_err.c_str(); }
+
+int hrkan_init(hrkan_t* out, const hrkan_cfg* cfg) {
+    if (!out) return fail(HRKAN_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = check_cfg(cfg);
+    if (rc) return rc;
+    const int L = cfg->n_widths - 1;
+    int net_id = -1;
+    bool uniform_hidden = true;
+    for (int l = 1; l < L; ++l) uniform_hidden &= (cfg->widths[l] == cfg->widths[1]);
+    if (uniform_hidden) net_id = narrow_net_id(L, cfg->widths[1]);
+    if (net_id < 0)
+        return fail(HRKAN_EUNSUPPORTED, "no kernels for this network shape (L=%d, hidden width %d)", L, cfg->widths[1]);
+    if (cfg->prec != HRKAN_FP32) return fail(HRKAN_EUNSUPPORTED, "precision %d has no kernels for this shape", cfg->prec);
+    if (cfg->n_instances != 1) return fail(HRKAN_EUNSUPPORTED, "n_instances > 1 has no kernels for this shape");
+
+    hrkan_ctx* h = new (std::nothrow) hrkan_ctx();
+    if (!h) return fail(HRKAN_ENOMEM, "host allocation");
+    h->cfg = *cfg;
+    h->L = L;
+    h->n = cfg->G + cfg->k;
+    h->P = count_params(cfg);
+    h->net_id = net_id;
+    const double hh = (cfg->grid_hi - cfg->grid_lo) / cfg->G;
+    h->grid.lo = float(cfg->grid_lo);
+    h->grid.inv_h = float(1.0 / hh);
+    h->grid.inv_a = float(2.0 / ((cfg->k + 1) * hh));
+    h->grid.n = h->n;
+
+    cudaError_t e;
+    if ((e = cudaGetDevice(&h->device)) != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDevice"); }
+    if ((e = cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "cudaDeviceGetAttribute");
+    }
+    h->max_grid = h->nsm * 8;
+    h->max_grid_l = h->nsm * 8;
+    size_t bytes_partial = size_t(h->max_grid) * size_t(h->P) * sizeof(float);
+    if ((e = cudaMalloc(&h->partial, bytes_partial)) != cudaSuccess ||
+        (e = cudaMalloc(&h->loss_partial, size_t(h->max_grid_l) * 2 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&h->m1, size_t(h->P) * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&h->m2, size_t(h->P) * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&h->t_counter, 2 * sizeof(int))) != cudaSuccess) {
+        hrkan_destroy(h);
+        return fail(HRKAN_ENOMEM, "cudaMalloc of the workspace: %s", cudaGetErrorString(e));
+    }
+    if ((e = cudaMemset(h->m1, 0, size_t(h->P) * sizeof(double))) != cudaSuccess ||
+        (e = cudaMemset(h->m2, 0, size_t(h->P) * sizeof(double))) != cudaSuccess ||
+        (e = cudaMemset(h->t_counter, 0, 2 * sizeof(int))) != cudaSuccess ||
+        (e = cudaDeviceSynchronize()) != cudaSuccess) {
+        hrkan_destroy(h);
+        return cuda_fail(e, "zeroing the Adam moments");
+    }
+    *out = h;
+    return HRKAN_OK;
+}
+
+void hrkan_destroy(hrkan_t h) {
+    if (!h) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != h->device) cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    cudaFree(h->partial);
+    cudaFree(h->loss_partial);
+    cudaFree(h->m1);
+    cudaFree(h->m2);
+    cudaFree(h->t_counter);
+    for (auto& ev : h->pending) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
+    for (auto& ev : h->pool) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
+    if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
+    delete h;
+}
+
+int64_t hrkan_tape_floats(hrkan_t h, int64_t N, unsigned jet_mask) {
+    (void)h; (void)N; (void)jet_mask;
+    return 0;   // the fused shapes recompute the forward inside the backward
+}
+
+int hrkan_forward_jets(hrkan_t h, const float* W, const float* x, int64_t N, unsigned jet_mask, float* jets,
+                       float* tape, hrkan_stream_t stream) {
+    (void)tape;
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (N < 0) return fail(HRKAN_EINVAL, "N=%lld", (long long)N);
+    if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
+    if (N == 0) return HRKAN_OK;
+    if (!W || !x || !jets) return fail(HRKAN_EINVAL, "NULL device pointer");
+    if (int rc = use_device(h)) return rc;
+    NarrowParams p = base_params(h, W);
+    p.x0 = x;
+    p.n0 = N;
+    p.jets = jets;
+    int grid = 0;
+    cudaError_t e;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_FORWARD, (cudaStream_t)stream);
+        e = narrow_launch(h->net_id, MODE_FWD, jet_mask, p, &grid, 1 << 30, true, (cudaStream_t)stream);
+    }
+    if (e == cudaErrorInvalidValue) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no forward kernel", jet_mask);
+    if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+    return HRKAN_OK;
+}
+
+int pinn_residual_loss(hrkan_t h, const pinn_problem* prob, const float* x_int, int64_t N_int, unsigned jet_mask,
+                       const float* jets_int, const float* u_bnd, const float* g_bnd, int64_t N_bnd, double* loss,
+                       float* dL_djets_int, float* dL_du_bnd, hrkan_stream_t stream) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (int rc = check_problem(prob)) return rc;
+    if (N_int < 0 || N_bnd < 0) return fail(HRKAN_EINVAL, "negative point count");
+    if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
+    if (!mask_has_rows(jet_mask, prob->kind))
+        return fail(HRKAN_EINVAL, "jet mask 0x%x lacks rows the residual needs", jet_mask);
+    if (!residual_mask_supported(jet_mask)) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x", jet_mask);
+    if (!loss) return fail(HRKAN_EINVAL, "loss is NULL");
+    if (N_int > 0 && (!x_int || !jets_int)) return fail(HRKAN_EINVAL, "NULL interior pointer");
+    if (N_bnd > 0 && (!u_bnd || !g_bnd)) return fail(HRKAN_EINVAL, "NULL boundary pointer");
+    if (int rc = use_device(h)) return rc;
+    ResidualParams r{};
+    r.pde = make_pde(prob);
+    r.mask = jet_mask;
+    r.x = x_int;
+    r.jets = jets_int;
+    r.N = N_int;
+    r.dL = dL_djets_int;
+    r.u_bnd = u_bnd;
+    r.g_bnd = g_bnd;
+    r.Nb = N_bnd;
+    r.dLb = dL_du_bnd;
+    r.scale0 = N_int > 0 ? float(2.0 * prob->alpha / double(N_int)) : 0.0f;
+    r.scale1 = N_bnd > 0 ? float(2.0 / double(N_bnd)) : 0.0f;
+    r.loss_partial = h->loss_partial;
+    int64_t most = N_int > N_bnd ? N_int : N_bnd;
+    int64_t grid = (most + 255) / 256;
+    if (grid > h->max_grid_l) grid = h->max_grid_l;
+    if (grid < 1) grid = 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_RESIDUAL, s);
+        HR_CUDA(launch_residual(r, (int)grid, s), "residual launch");
+    }
+    ReduceParams q{};
+    q.P = 0;
+    q.loss_partial = h->loss_partial;
+    q.Gl = (int)grid;
+    q.loss = loss;
+    q.alpha = prob->alpha;
+    q.n0 = N_int;
+    q.n1 = N_bnd;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_REDUCE, s);
+        HR_CUDA(launch_reduce(q, s), "loss reduce launch");
+    }
+    return HRKAN_OK;
+}
+
+int hrkan_backward(hrkan_t h, const float* W, const float* x, int64_t N, unsigned jet_mask, const float* tape,
+                   const float* dL_djets, float* dW, int accumulate, hrkan_stream_t stream) {
+    (void)tape;
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (N < 0) return fail(HRKAN_EINVAL, "N=%lld", (long long)N);
+    if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
+    if (!W || !dW) return fail(HRKAN_EINVAL, "NULL device pointer");
+    if (N > 0 && (!x || !dL_djets)) return fail(HRKAN_EINVAL, "NULL device pointer");
+    if (int rc = use_device(h)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (N == 0) {
+        if (!accumulate) HR_CUDA(cudaMemsetAsync(dW, 0, size_t(h->P) * sizeof(float), s), "cudaMemsetAsync");
+        return HRKAN_OK;
+    }
+    NarrowParams p = base_params(h, W);
+    p.x0 = x;
+    p.n0 = N;
+    p.dL = dL_djets;
+    p.partial = h->partial;
+    int grid = 0;
+    cudaError_t e;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
+        e = narrow_launch(h->net_id, MODE_BWD, jet_mask, p, &grid, h->max_grid, true, s);
+    }
+    if (e == cudaErrorInvalidValue) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no backward kernel", jet_mask);
+    if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+    ReduceParams q{};
+    q.partial = h->partial;
+    q.G = grid;
+    q.P = h->P;
+    q.dW = dW;
+    q.accumulate = accumulate ? 1 : 0;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_REDUCE, s);
+        HR_CUDA(launch_reduce(q, s), "gradient reduce launch");
+    }
+    return HRKAN_OK;
+}
+
+int adam_step(hrkan_t h, float* W, const float* dW, double lr, double b1, double b2, double eps, int t,
+              hrkan_stream_t stream) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (!W || !dW) return fail(HRKAN_EINVAL, "NULL device pointer");
+    if (t < 1) return fail(HRKAN_EINVAL, "Adam step t=%d must be >= 1", t);
+    if (!(b1 >= 0.0 && b1 < 1.0 && b2 >= 0.0 && b2 < 1.0 && eps >= 0.0 && std::isfinite(lr)))
+        return fail(HRKAN_EINVAL, "Adam hyper-parameters lr=%g b1=%g b2=%g eps=%g", lr, b1, b2, eps);
+    if (int rc = use_device(h)) return rc;
+    ReduceParams q{};
+    q.partial = dW;
+    q.G = 1;
+    q.P = h->P;
+    q.do_adam = 1;
+    q.W = W;
+    q.m1 = h->m1;
+    q.m2 = h->m2;
+    q.lr = lr; q.b1 = b1; q.b2 = b2; q.eps = eps;
+    q.c1 = 1.0 - std::pow(b1, t);
+    q.c2 = 1.0 - std::pow(b2, t);
+    {
+        ProfScope ps(h, HRKAN_KERNEL_REDUCE, (cudaStream_t)stream);
+        HR_CUDA(launch_reduce(q, (cudaStream_t)stream), "Adam launch");
+    }
+    return HRKAN_OK;
+}
+
+int hrkan_reset_moments(hrkan_t h, hrkan_stream_t stream) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (int rc = use_device(h)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    HR_CUDA(cudaMemsetAsync(h->m1, 0, size_t(h->P) * sizeof(double), s), "cudaMemsetAsync");
+    HR_CUDA(cudaMemsetAsync(h->m2, 0, size_t(h->P) * sizeof(double), s), "cudaMemsetAsync");
+    HR_CUDA(cudaMemsetAsync(h->t_counter, 0, 2 * sizeof(int), s), "cudaMemsetAsync");
+    return HRKAN_OK;
+}
+
+int hrkan_profile_enable(hrkan_t h, int enable) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    h->prof = enable != 0;
+    return HRKAN_OK;
+}
+
+int hrkan_profile_read(hrkan_t h, int kernel_class, double* total_ms, int64_t* launches, int reset) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (kernel_class < 0 || kernel_class >= HRKAN_KERNEL_CLASSES)
+        return fail(HRKAN_EINVAL, "kernel class %d", kernel_class);
+    if (int rc = use_device(h)) return rc;
+    for (auto& ev : h->pending) {
+        float ms = 0.0f;
+        HR_CUDA(cudaEventSynchronize(ev.b), "cudaEventSynchronize");
+        HR_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b), "cudaEventElapsedTime");
+        h->prof_ms[ev.cls] += ms;
+        h->prof_n[ev.cls] += 1;
+        h->pool.push_back(ev);
+    }
+    h->pending.clear();
+    if (total_ms) *total_ms = h->prof_ms[kernel_class];
+    if (launches) *launches = h->prof_n[kernel_class];
+    if (reset) {
+        h->prof_ms[kernel_class] = 0.0;
+        h->prof_n[kernel_class] = 0;
+    }
+    return HRKAN_OK;
+}
+
+int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float* x_int, int64_t N_int,
+                     const float* x_bnd, const float* g_bnd, int64_t N_bnd, double lr, double b1, double b2,
+                     double eps, int t, double* loss, float* dW, hrkan_stream_t stream) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (int rc = check_problem(prob)) return rc;
+    if (N_int < 0 || N_bnd < 0) return fail(HRKAN_EINVAL, "negative point count");
+    if (N_int + N_bnd == 0) return fail(HRKAN_EINVAL, "no collocation points");
+    if (!W || !loss) return fail(HRKAN_EINVAL, "NULL device pointer");
+    if (N_int > 0 && !x_int) return fail(HRKAN_EINVAL, "x_int is NULL");
+    if (N_bnd > 0 && (!x_bnd || !g_bnd)) return fail(HRKAN_EINVAL, "boundary pointer is NULL");
+    if (t < 0) return fail(HRKAN_EINVAL, "Adam step t=%d must be >= 0", t);
+    if (!(b1 >= 0.0 && b1 < 1.0 && b2 >= 0.0 && b2 < 1.0 && eps >= 0.0 && std::isfinite(lr)))
+        return fail(HRKAN_EINVAL, "Adam hyper-parameters lr=%g b1=%g b2=%g eps=%g", lr, b1, b2, eps);
+    if (int rc = use_device(h)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned mask = prob->kind == HRKAN_POISSON ? 0x1Fu : 0x0Fu;
+    NarrowParams p = base_params(h, W);
+    p.x0 = x_int;
+    p.n0 = N_int;
+    p.x1 = x_bnd;
+    p.g1 = g_bnd;
+    p.n1 = N_bnd;
+    p.partial = h->partial;
+    p.loss_partial = h->loss_partial;
+    p.pde = make_pde(prob);
+    p.scale0 = N_int > 0 ? float(2.0 * prob->alpha / double(N_int)) : 0.0f;
+    p.scale1 = N_bnd > 0 ? float(2.0 / double(N_bnd)) : 0.0f;
+    if (t == 0) p.t_counter = h->t_counter;
+    int grid = 0;
+    cudaError_t e;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
+        e = narrow_launch(h->net_id, MODE_TRAIN, mask, p, &grid, h->max_grid, true, s);
+    }
+    if (e == cudaErrorInvalidValue) return fail(HRKAN_EUNSUPPORTED, "no fused training kernel");
+    if (e != cudaSuccess) return cuda_fail(e, "train launch");
+    ReduceParams q{};
+    q.partial = h->partial;
+    q.G = grid;
+    q.P = h->P;
+    q.dW = dW;
+    q.do_adam = 1;
+    q.W = W;
+    q.m1 = h->m1;
+    q.m2 = h->m2;
+    q.lr = lr; q.b1 = b1; q.b2 = b2; q.eps = eps;
+    q.c1 = 1.0 - std::pow(b1, t > 0 ? t : 1);
+    q.c2 = 1.0 - std::pow(b2, t > 0 ? t : 1);
+    q.loss_partial = h->loss_partial;
+    q.Gl = grid;
+    q.loss = loss;
+    q.alpha = prob->alpha;
+    q.n0 = N_int;
+    q.n1 = N_bnd;
+    if (t == 0) q.t_counter = h->t_counter;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_REDUCE, s);
+        HR_CUDA(launch_reduce(q, s), "reduce/Adam launch");
+    }
+    return HRKAN_OK;
+}
+
+}  // extern "C"

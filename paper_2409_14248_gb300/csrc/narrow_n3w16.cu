@@ -1,0 +1,3 @@
+// Fused kernels for widths [2, 16, 16, 1] (k = 3, m = 4).
+#include "narrow_inst.cuh"
+HRKAN_NARROW_INSTANCE(narrow_launch_n3w16, 3, 16)

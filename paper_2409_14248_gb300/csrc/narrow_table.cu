@@ -1,0 +1,27 @@
+// Table of the fused narrow-network shapes compiled into the library.
+#include "internal.h"
+
+namespace hrkan {
+
+cudaError_t narrow_launch_n2w5(int, unsigned, const NarrowParams&, int*, int, bool, cudaStream_t);
+cudaError_t narrow_launch_n3w10(int, unsigned, const NarrowParams&, int*, int, bool, cudaStream_t);
+cudaError_t narrow_launch_n3w16(int, unsigned, const NarrowParams&, int*, int, bool, cudaStream_t);
+
+int narrow_net_id(int n_layers, int wh) {
+    if (n_layers == 2 && wh == 5) return 0;
+    if (n_layers == 3 && wh == 10) return 1;
+    if (n_layers == 3 && wh == 16) return 2;
+    return -1;
+}
+
+cudaError_t narrow_launch(int net_id, int mode, unsigned mask, const NarrowParams& p, int* grid, int max_grid,
+                          bool launch, cudaStream_t s) {
+    switch (net_id) {
+        case 0: return narrow_launch_n2w5(mode, mask, p, grid, max_grid, launch, s);
+        case 1: return narrow_launch_n3w10(mode, mask, p, grid, max_grid, launch, s);
+        case 2: return narrow_launch_n3w16(mode, mask, p, grid, max_grid, launch, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace hrkan

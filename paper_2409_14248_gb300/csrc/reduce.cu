@@ -1,0 +1,151 @@
+// Cross-block reductions, the Adam step and the stand-alone residual kernel.
+//
+// reduce_kernel sums per-block weight-gradient partials [G][P] in a fixed
+// order (so the result does not depend on scheduling), optionally writes the
+// gradient and optionally applies Adam with float64 moments; block 0 also
+// finishes the loss (Eq. 4 / Eq. 8) from per-block float64 partials with
+// compensated (Neumaier) summation in a fixed order.
+#include "internal.h"
+
+namespace hrkan {
+
+constexpr int RED_LANES = 32;   // parameters per block
+constexpr int RED_WARPS = 16;   // partial rows split across warps
+
+__device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
+    double t = s + x;
+    if (fabs(s) >= fabs(x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+}
+
+__global__ void __launch_bounds__(RED_LANES * RED_WARPS) reduce_kernel(ReduceParams p) {
+    __shared__ float part[RED_WARPS][RED_LANES];
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int64_t i = int64_t(blockIdx.x) * RED_LANES + lane;
+    if (i < p.P) {
+        float acc = 0.0f;
+        // rows w, w + 16, ...: 4 independent loads in flight per step
+        int g = w;
+        for (; g + 3 * RED_WARPS < p.G; g += 4 * RED_WARPS) {
+            float a0 = p.partial[int64_t(g) * p.P + i];
+            float a1 = p.partial[int64_t(g + RED_WARPS) * p.P + i];
+            float a2 = p.partial[int64_t(g + 2 * RED_WARPS) * p.P + i];
+            float a3 = p.partial[int64_t(g + 3 * RED_WARPS) * p.P + i];
+            acc += a0; acc += a1; acc += a2; acc += a3;
+        }
+        for (; g < p.G; g += RED_WARPS) acc += p.partial[int64_t(g) * p.P + i];
+        part[w][lane] = acc;
+    }
+    __syncthreads();
+    if (w == 0 && i < p.P) {
+        float gsum = 0.0f;
+#pragma unroll
+        for (int t = 0; t < RED_WARPS; ++t) gsum += part[t][lane];
+        if (p.dW) p.dW[i] = p.accumulate ? p.dW[i] + gsum : gsum;
+        if (p.do_adam) {
+            double c1 = p.c1, c2 = p.c2;
+            if (p.t_counter) {
+                const int t = p.t_counter[1];
+                c1 = 1.0 - pow(p.b1, double(t));
+                c2 = 1.0 - pow(p.b2, double(t));
+            }
+            double gd = gsum;
+            double m1 = p.b1 * p.m1[i] + (1.0 - p.b1) * gd;
+            double m2 = p.b2 * p.m2[i] + (1.0 - p.b2) * gd * gd;
+            p.m1[i] = m1;
+            p.m2[i] = m2;
+            double step = p.lr * (m1 / c1) / (sqrt(m2 / c2) + p.eps);
+            p.W[i] = float(double(p.W[i]) - step);
+        }
+    }
+    // commit the step counter; this kernel reads only t_counter[1]
+    if (p.t_counter && blockIdx.x == 0 && w == 0 && lane == 0) p.t_counter[0] = p.t_counter[1];
+    if (blockIdx.x == 0 && w == 1 && p.loss_partial) {
+        // lane l sums rows l, l+32, ... ; lane 0 then folds the 32 lane sums in order
+        double s0 = 0.0, c0 = 0.0, s1 = 0.0, c1 = 0.0;
+        for (int g = lane; g < p.Gl; g += 32) {
+            neumaier_add(s0, c0, p.loss_partial[2 * g]);
+            neumaier_add(s1, c1, p.loss_partial[2 * g + 1]);
+        }
+        __shared__ double fold[4][32];
+        fold[0][lane] = s0; fold[1][lane] = c0; fold[2][lane] = s1; fold[3][lane] = c1;
+        __syncwarp();
+        if (lane == 0) {
+            double t0 = 0.0, e0 = 0.0, t1 = 0.0, e1 = 0.0;
+            for (int l = 0; l < 32; ++l) {
+                neumaier_add(t0, e0, fold[0][l]);
+                e0 += fold[1][l];
+                neumaier_add(t1, e1, fold[2][l]);
+                e1 += fold[3][l];
+            }
+            double lp = p.n0 > 0 ? (t0 + e0) / double(p.n0) : 0.0;
+            double lb = p.n1 > 0 ? (t1 + e1) / double(p.n1) : 0.0;
+            p.loss[0] = p.alpha * lp + lb;
+            p.loss[1] = lp;
+            p.loss[2] = lb;
+        }
+    }
+}
+
+cudaError_t launch_reduce(const ReduceParams& p, cudaStream_t s) {
+    int64_t blocks = (p.P + RED_LANES - 1) / RED_LANES;
+    if (blocks < 1) blocks = 1;
+    reduce_kernel<<<dim3((unsigned)blocks), dim3(RED_LANES, RED_WARPS), 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- residual
+
+constexpr int RES_BLOCK = 256;
+
+template <unsigned MASK>
+__global__ void __launch_bounds__(RES_BLOCK) residual_kernel(ResidualParams p) {
+    using JT = Jet<MASK>;
+    double l0 = 0.0, l1 = 0.0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t pt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; pt < p.N; pt += stride) {
+        float u[JT::J], gu[JT::J];
+#pragma unroll
+        for (int r = 0; r < JT::J; ++r) u[r] = p.jets[r * p.N + pt];
+        float r = pde_residual<MASK>(p.pde, p.x[pt], p.x[p.N + pt], u);
+        l0 += double(r) * double(r);
+        if (p.dL) {
+            pde_residual_grad<MASK>(p.pde, r, u, p.scale0, gu);
+#pragma unroll
+            for (int q = 0; q < JT::J; ++q) p.dL[q * p.N + pt] = gu[q];
+        }
+    }
+    for (int64_t pt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; pt < p.Nb; pt += stride) {
+        float d = p.u_bnd[pt] - p.g_bnd[pt];
+        l1 += double(d) * double(d);
+        if (p.dLb) p.dLb[pt] = p.scale1 * d;
+    }
+    __shared__ double red[2][RES_BLOCK / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        l0 += __shfl_down_sync(0xffffffffu, l0, o);
+        l1 += __shfl_down_sync(0xffffffffu, l1, o);
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = l0; red[1][threadIdx.x >> 5] = l1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int t = 0; t < RES_BLOCK / 32; ++t) { a += red[0][t]; b += red[1][t]; }
+        p.loss_partial[2 * blockIdx.x] = a;
+        p.loss_partial[2 * blockIdx.x + 1] = b;
+    }
+}
+
+bool residual_mask_supported(unsigned mask) { return mask == 0x0Fu || mask == 0x1Fu; }
+
+cudaError_t launch_residual(const ResidualParams& p, int grid, cudaStream_t s) {
+    switch (p.mask) {
+        case 0x0Fu: residual_kernel<0x0Fu><<<grid, RES_BLOCK, 0, s>>>(p); break;
+        case 0x1Fu: residual_kernel<0x1Fu><<<grid, RES_BLOCK, 0, s>>>(p); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace hrkan

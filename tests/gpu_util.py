@@ -1,0 +1,56 @@
+"""Shared helpers of the GPU parity tests (not collected by pytest)."""
+import numpy as np
+
+import oracle
+from paper_2409_14248_gb300 import capi, inputs
+
+
+def relerr(got, want):
+    """Normwise relative error ||got - want||_2 / ||want||_2 (absolute if want is 0)."""
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    d = np.linalg.norm(got - want)
+    n = np.linalg.norm(want)
+    return d / n if n > 0 else d
+
+
+# FP32 path tolerances: 1e-5 on u, 1e-4 on derivative rows, the loss gradient
+# and the weight gradient (normwise, per jet row / per layer).
+TOL_U = 1e-5
+TOL_D = 1e-4
+
+
+def row_tolerances(mask):
+    return [TOL_U] + [TOL_D] * (oracle.n_rows(mask) - 1)
+
+
+def cfg_of(w, prec=capi.HRKAN_FP32):
+    return capi.make_cfg(w.widths, w.G, w.k, w.m, w.lo, w.hi, prec=prec)
+
+
+def layer_slices(widths, G, k=3):
+    n = G + k
+    out, off = [], 0
+    for l in range(len(widths) - 1):
+        sz = widths[l] * widths[l + 1] * n
+        out.append(slice(off, off + sz))
+        off += sz
+    return out
+
+
+def problem_of(w, a=None, b=None):
+    p = w.problem(a, b)
+    return capi.make_problem(p["kind"], p["a"], p["b"], p["lam"], p["nu"], p["alpha"])
+
+
+def oracle_step(w, W, x_int, x_bnd, g_bnd, lr, t=1, m1=None, m2=None, a=None, b=None):
+    """Oracle train step on float64 copies; returns (loss, dW, W_new, m1, m2)."""
+    Wd = np.asarray(W, dtype=np.float64).copy()
+    m1 = np.zeros_like(Wd) if m1 is None else m1
+    m2 = np.zeros_like(Wd) if m2 is None else m2
+    loss, dW = oracle.train_step(w.net, w.problem(a, b), Wd, m1, m2, x_int, w.mask_int, x_bnd, g_bnd, lr, t)
+    return loss, dW, Wd, m1, m2
+
+
+def random_weights(w, seed, sigma=0.5):
+    return (sigma * np.random.default_rng(seed).standard_normal(w.n_params())).astype(np.float32)
