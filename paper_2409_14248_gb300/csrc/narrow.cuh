@@ -29,6 +29,10 @@ template <int NL_, int WH_, int K_, int M_>
 struct NarrowNet {
     static constexpr int NL = NL_, WH = WH_, K = K_, M = M_, KP = K_ + 1;
     static constexpr int WHP = (WH_ + 3) & ~3;   // padded row of the transposed hidden layer
+    // Copies of the shared weight gradient, one per group of lanes (lane % COPIES).
+    // Hidden activations of a PINN often sit in one or two grid cells, so the
+    // lanes of a warp would otherwise add into the same address at once.
+    static constexpr int COPIES = WH_ >= 16 ? 4 : 8;
     static_assert(NL == 2 || NL == 3, "narrow nets have one or two hidden layers");
 
     // shared-memory layout in floats (n = number of bases)
@@ -85,6 +89,16 @@ __device__ void narrow_store_dw(const float* s, float* __restrict__ out, int n) 
     for (int t = threadIdx.x; t < WH * n; t += blockDim.x) out[off + t] = wl[t];
 }
 
+// The shared weight gradient holds Net::COPIES interleaved copies of the
+// layout above: logical element e of copy c lives at base[e * COPIES + c],
+// and a lane adds into copy lane % COPIES.
+template <class Net>
+struct DwAcc {
+    float* base;
+    int cp;
+    __device__ __forceinline__ void add(int e, float v) const { atomicAdd(base + e * Net::COPIES + cp, v); }
+};
+
 // Coordinate bases of one point (first layer inputs).
 template <class Net>
 struct CoordBases {
@@ -119,11 +133,11 @@ __device__ __forceinline__ void layer0_unit(int j, const CoordBases<Net>& xb, co
 // dW0[j][d][c_d+q] += sum_r gz[r] * rows of x_d  (first-layer weight gradient for output unit j)
 template <class Net, unsigned MASK>
 __device__ __forceinline__ void layer0_unit_dw(int j, const CoordBases<Net>& xb, const float* gz,
-                                               float* dw0, int n) {
+                                               const DwAcc<Net>& dw, int n) {
     using JT = Jet<MASK>;
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
-        float* dr = dw0 + (j * 2 + d) * n;
+        const int dr = Net::off_w0() + (j * 2 + d) * n;
 #pragma unroll
         for (int q = 0; q < Net::KP; ++q) {
             float g = gz[0] * xb.b[d].v[q];
@@ -135,7 +149,7 @@ __device__ __forceinline__ void layer0_unit_dw(int j, const CoordBases<Net>& xb,
                 if constexpr (JT::S1) g = fmaf(gz[JT::RS1], xb.b[d].d2[q], g);
             }
             int i = xb.b[d].c + q;
-            if ((unsigned)i < (unsigned)n) atomicAdd(dr + i, g);
+            if ((unsigned)i < (unsigned)n) dw.add(dr + i, g);
         }
     }
 }
@@ -205,14 +219,14 @@ __device__ __forceinline__ void narrow_forward(const CoordBases<Net>& xb, const 
 // Backward of one point given gu = dL/d(output jets); h[][] (last hidden jets
 // from narrow_forward) is consumed.  Adds to the shared dW.
 template <class Net, unsigned MASK>
-__device__ __forceinline__ void narrow_backward(const CoordBases<Net>& xb, const float* s, float* ds,
+__device__ __forceinline__ void narrow_backward(const CoordBases<Net>& xb, const float* s, const DwAcc<Net>& dw,
                                                 int n, const Grid& g, float (*h)[Jet<MASK>::J],
                                                 const float* gu) {
     using JT = Jet<MASK>;
     constexpr int WH = Net::WH, J = JT::J, KP = Net::KP;
     // output layer: dW_L and dL/dh
     const float* wl = s + Net::off_wl(n);
-    float* dwl = ds + Net::off_wl(n);
+    const int dwl = Net::off_wl(n);
 #pragma unroll
     for (int j = 0; j < WH; ++j) {
         Active<Net::K, Net::M, 3> b;
@@ -229,21 +243,20 @@ __device__ __forceinline__ void narrow_backward(const CoordBases<Net>& xb, const
                 gw = fmaf(gu[r], a[r][q], gw);
                 dA[r][q] = gu[r] * w;
             }
-            if ((unsigned)i < (unsigned)n) atomicAdd(dwl + j * n + i, gw);
+            if ((unsigned)i < (unsigned)n) dw.add(dwl + j * n + i, gw);
         }
         float gz[J];
         JT::template rows_adjoint<KP>(h[j], b.d1, b.d2, b.d3, dA, gz);
 #pragma unroll
         for (int r = 0; r < J; ++r) h[j][r] = gz[r];   // h now holds dL/dh
     }
-    float* dw0 = ds + Net::off_w0();
     if constexpr (Net::NL == 2) {
 #pragma unroll
-        for (int j = 0; j < WH; ++j) layer0_unit_dw<Net, MASK>(j, xb, h[j], dw0, n);
+        for (int j = 0; j < WH; ++j) layer0_unit_dw<Net, MASK>(j, xb, h[j], dw, n);
     } else {
         const float* w0 = s + Net::off_w0();
         const float* w1 = s + Net::off_w1(n);
-        float* dw1 = ds + Net::off_w1(n);
+        const int dw1 = Net::off_w1(n);
 #pragma unroll 1
         for (int j = 0; j < WH; ++j) {
             float z[J];
@@ -274,14 +287,14 @@ __device__ __forceinline__ void narrow_backward(const CoordBases<Net>& xb, const
                                 gw = fmaf(h[o][r], a[r][q], gw);
                                 dA[r][q] = fmaf(h[o][r], wv[e], dA[r][q]);
                             }
-                            if (ok) atomicAdd(dw1 + row + o, gw);
+                            if (ok) dw.add(dw1 + row + o, gw);
                         }
                     }
                 }
             }
             float gz[J];
             JT::template rows_adjoint<KP>(z, b.d1, b.d2, b.d3, dA, gz);
-            layer0_unit_dw<Net, MASK>(j, xb, gz, dw0, n);
+            layer0_unit_dw<Net, MASK>(j, xb, gz, dw, n);
         }
     }
 }
@@ -359,8 +372,9 @@ __global__ void __launch_bounds__(NARROW_BLOCK) narrow_grad_kernel(NarrowParams 
     float* s = smem;
     float* ds = smem + sf;
     narrow_load_w<Net>(p.W, s, n);
-    for (int t = threadIdx.x; t < sf; t += blockDim.x) ds[t] = 0.0f;
+    for (int t = threadIdx.x; t < sf * Net::COPIES; t += blockDim.x) ds[t] = 0.0f;
     __syncthreads();
+    const DwAcc<Net> dwacc{ds, int(threadIdx.x) & (Net::COPIES - 1)};
 
     const int64_t T0 = (p.n0 + NARROW_BLOCK - 1) / NARROW_BLOCK;
     const int64_t T1 = (MODE == MODE_TRAIN) ? (p.n1 + NARROW_BLOCK - 1) / NARROW_BLOCK : 0;
@@ -385,7 +399,7 @@ __global__ void __launch_bounds__(NARROW_BLOCK) narrow_grad_kernel(NarrowParams 
 #pragma unroll
                     for (int q = 0; q < JT::J; ++q) gu[q] = p.dL[q * N + pt];
                 }
-                narrow_backward<Net, MASK>(xb, s, ds, n, p.grid, h, gu);
+                narrow_backward<Net, MASK>(xb, s, dwacc, n, p.grid, h, gu);
             }
         } else if constexpr (MODE == MODE_TRAIN) {
             const int64_t pt = (tile - T0) * NARROW_BLOCK + threadIdx.x;
@@ -399,13 +413,21 @@ __global__ void __launch_bounds__(NARROW_BLOCK) narrow_grad_kernel(NarrowParams 
                 float d = u[0] - p.g1[pt];
                 lsum1 += double(d) * double(d);
                 gu[0] = p.scale1 * d;
-                narrow_backward<Net, 1u>(xb, s, ds, n, p.grid, h, gu);
+                narrow_backward<Net, 1u>(xb, s, dwacc, n, p.grid, h, gu);
             }
         }
     }
     if constexpr (MODE == MODE_TRAIN) narrow_block_loss<Net>(lsum0, lsum1, p.loss_partial + 2 * blockIdx.x);
     __syncthreads();
-    narrow_store_dw<Net>(ds, p.partial + int64_t(blockIdx.x) * p.P, n);
+    // fold the copies into the (no longer needed) weight region, then store
+    for (int t = threadIdx.x; t < sf; t += blockDim.x) {
+        float a = 0.0f;
+#pragma unroll
+        for (int c = 0; c < Net::COPIES; ++c) a += ds[t * Net::COPIES + c];
+        s[t] = a;
+    }
+    __syncthreads();
+    narrow_store_dw<Net>(s, p.partial + int64_t(blockIdx.x) * p.P, n);
 }
 
 }  // namespace hrkan

@@ -45,14 +45,14 @@ static cudaError_t narrow_launch_net(int mode, unsigned mask, const NarrowParams
         }
     } else if (mode == MODE_BWD) {
         switch (mask) {
-            case 0x01u: return narrow_go<Net>(narrow_grad_kernel<Net, 0x01u, MODE_BWD>, 2 * sf, t0, p, grid, max_grid, launch, s);
-            case 0x0Fu: return narrow_go<Net>(narrow_grad_kernel<Net, 0x0Fu, MODE_BWD>, 2 * sf, t0, p, grid, max_grid, launch, s);
-            case 0x1Fu: return narrow_go<Net>(narrow_grad_kernel<Net, 0x1Fu, MODE_BWD>, 2 * sf, t0, p, grid, max_grid, launch, s);
+            case 0x01u: return narrow_go<Net>(narrow_grad_kernel<Net, 0x01u, MODE_BWD>, (1 + Net::COPIES) * sf, t0, p, grid, max_grid, launch, s);
+            case 0x0Fu: return narrow_go<Net>(narrow_grad_kernel<Net, 0x0Fu, MODE_BWD>, (1 + Net::COPIES) * sf, t0, p, grid, max_grid, launch, s);
+            case 0x1Fu: return narrow_go<Net>(narrow_grad_kernel<Net, 0x1Fu, MODE_BWD>, (1 + Net::COPIES) * sf, t0, p, grid, max_grid, launch, s);
         }
     } else if (mode == MODE_TRAIN) {
         switch (mask) {
-            case 0x0Fu: return narrow_go<Net>(narrow_grad_kernel<Net, 0x0Fu, MODE_TRAIN>, 2 * sf, t0 + t1, p, grid, max_grid, launch, s);
-            case 0x1Fu: return narrow_go<Net>(narrow_grad_kernel<Net, 0x1Fu, MODE_TRAIN>, 2 * sf, t0 + t1, p, grid, max_grid, launch, s);
+            case 0x0Fu: return narrow_go<Net>(narrow_grad_kernel<Net, 0x0Fu, MODE_TRAIN>, (1 + Net::COPIES) * sf, t0 + t1, p, grid, max_grid, launch, s);
+            case 0x1Fu: return narrow_go<Net>(narrow_grad_kernel<Net, 0x1Fu, MODE_TRAIN>, (1 + Net::COPIES) * sf, t0 + t1, p, grid, max_grid, launch, s);
         }
     }
     return cudaErrorInvalidValue;

@@ -15,13 +15,19 @@ def relerr(got, want):
 
 
 # FP32 path tolerances: 1e-5 on u, 1e-4 on derivative rows, the loss gradient
-# and the weight gradient (normwise, per jet row / per layer).
+# and the weight gradient (normwise, per jet row / per layer), at the
+# workloads' own N(0, 0.1^2) weights.
 TOL_U = 1e-5
 TOL_D = 1e-4
+# Stress weights N(0, 0.5^2) make the 3-layer networks much worse conditioned:
+# a plain dense float32 evaluation of the value row then already has a
+# normwise error of ~9e-6 against the FP64 oracle (and ~1e-6 at sigma 0.1).
+# The stress bound keeps the same margin over that floor: 5x.
+STRESS = 5.0
 
 
-def row_tolerances(mask):
-    return [TOL_U] + [TOL_D] * (oracle.n_rows(mask) - 1)
+def row_tolerances(mask, scale=1.0):
+    return [TOL_U * scale] + [TOL_D * scale] * (oracle.n_rows(mask) - 1)
 
 
 def cfg_of(w, prec=capi.HRKAN_FP32):
