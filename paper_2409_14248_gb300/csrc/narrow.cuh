@@ -257,8 +257,12 @@ __device__ __forceinline__ void narrow_backward(const CoordBases<Net>& xb, const
         const float* w0 = s + Net::off_w0();
         const float* w1 = s + Net::off_w1(n);
         const int dw1 = Net::off_w1(n);
+        // Lanes that share a gradient copy (lane, lane+COPIES, ...) start at
+        // different units, so at any instant they add into different rows.
+        const int rot = ((int(threadIdx.x) & 31) / Net::COPIES) * WH / (32 / Net::COPIES);
 #pragma unroll 1
-        for (int j = 0; j < WH; ++j) {
+        for (int jj = 0; jj < WH; ++jj) {
+            const int j = (jj + rot < WH) ? jj + rot : jj + rot - WH;
             float z[J];
             layer0_unit<Net, MASK>(j, xb, w0, n, z);
             Active<Net::K, Net::M, 3> b;

@@ -19,10 +19,29 @@ __device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
     s = t;
 }
 
+// Sum of two compensated (Neumaier) partial sums (s, c): exact-sum error of
+// s1 + s2 goes into the compensation term.
+__device__ __forceinline__ void neumaier_merge(double& s, double& c, double s2, double c2) {
+    neumaier_add(s, c, s2);
+    c += c2;
+}
+
 __global__ void __launch_bounds__(RED_LANES * RED_WARPS) reduce_kernel(ReduceParams p) {
     __shared__ float part[RED_WARPS][RED_LANES];
+    __shared__ float corr[2];
     const int lane = threadIdx.x, w = threadIdx.y;
     const int64_t i = int64_t(blockIdx.x) * RED_LANES + lane;
+    if (p.do_adam && w == 0 && lane == 0) {
+        // bias corrections 1 - b^t (float64 pow once per block)
+        double c1 = p.c1, c2 = p.c2;
+        if (p.t_counter) {
+            const int t = p.t_counter[1];
+            c1 = 1.0 - pow(p.b1, double(t));
+            c2 = 1.0 - pow(p.b2, double(t));
+        }
+        corr[0] = float(1.0 / c1);
+        corr[1] = float(1.0 / sqrt(c2));
+    }
     if (i < p.P) {
         float acc = 0.0f;
         // rows w, w + 16, ...: 4 independent loads in flight per step
@@ -44,43 +63,40 @@ __global__ void __launch_bounds__(RED_LANES * RED_WARPS) reduce_kernel(ReducePar
         for (int t = 0; t < RED_WARPS; ++t) gsum += part[t][lane];
         if (p.dW) p.dW[i] = p.accumulate ? p.dW[i] + gsum : gsum;
         if (p.do_adam) {
-            double c1 = p.c1, c2 = p.c2;
-            if (p.t_counter) {
-                const int t = p.t_counter[1];
-                c1 = 1.0 - pow(p.b1, double(t));
-                c2 = 1.0 - pow(p.b2, double(t));
-            }
-            double gd = gsum;
-            double m1 = p.b1 * p.m1[i] + (1.0 - p.b1) * gd;
-            double m2 = p.b2 * p.m2[i] + (1.0 - p.b2) * gd * gd;
+            // float64 moments (fused multiply-adds only); the step itself in float32:
+            // W <- W - lr * (m/(1-b1^t)) / (sqrt(v/(1-b2^t)) + eps)
+            const double gd = gsum;
+            const double m1 = fma(p.b1, p.m1[i], (1.0 - p.b1) * gd);
+            const double m2 = fma(p.b2, p.m2[i], (1.0 - p.b2) * gd * gd);
             p.m1[i] = m1;
             p.m2[i] = m2;
-            double step = p.lr * (m1 / c1) / (sqrt(m2 / c2) + p.eps);
-            p.W[i] = float(double(p.W[i]) - step);
+            const float mh = float(m1) * corr[0];
+            const float vh = sqrtf(float(m2)) * corr[1];
+            p.W[i] = p.W[i] - float(p.lr) * mh / (vh + float(p.eps));
         }
     }
     // commit the step counter; this kernel reads only t_counter[1]
     if (p.t_counter && blockIdx.x == 0 && w == 0 && lane == 0) p.t_counter[0] = p.t_counter[1];
     if (blockIdx.x == 0 && w == 1 && p.loss_partial) {
-        // lane l sums rows l, l+32, ... ; lane 0 then folds the 32 lane sums in order
+        // lane l sums rows l, l+32, ...; the 32 compensated sums are then merged
+        // pairwise by shuffles in a fixed tree order
         double s0 = 0.0, c0 = 0.0, s1 = 0.0, c1 = 0.0;
         for (int g = lane; g < p.Gl; g += 32) {
             neumaier_add(s0, c0, p.loss_partial[2 * g]);
             neumaier_add(s1, c1, p.loss_partial[2 * g + 1]);
         }
-        __shared__ double fold[4][32];
-        fold[0][lane] = s0; fold[1][lane] = c0; fold[2][lane] = s1; fold[3][lane] = c1;
-        __syncwarp();
-        if (lane == 0) {
-            double t0 = 0.0, e0 = 0.0, t1 = 0.0, e1 = 0.0;
-            for (int l = 0; l < 32; ++l) {
-                neumaier_add(t0, e0, fold[0][l]);
-                e0 += fold[1][l];
-                neumaier_add(t1, e1, fold[2][l]);
-                e1 += fold[3][l];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double a = __shfl_down_sync(0xffffffffu, s0, o), b = __shfl_down_sync(0xffffffffu, c0, o);
+            double e = __shfl_down_sync(0xffffffffu, s1, o), f = __shfl_down_sync(0xffffffffu, c1, o);
+            if (lane < o) {
+                neumaier_merge(s0, c0, a, b);
+                neumaier_merge(s1, c1, e, f);
             }
-            double lp = p.n0 > 0 ? (t0 + e0) / double(p.n0) : 0.0;
-            double lb = p.n1 > 0 ? (t1 + e1) / double(p.n1) : 0.0;
+        }
+        if (lane == 0) {
+            double lp = p.n0 > 0 ? (s0 + c0) / double(p.n0) : 0.0;
+            double lb = p.n1 > 0 ? (s1 + c1) / double(p.n1) : 0.0;
             p.loss[0] = p.alpha * lp + lb;
             p.loss[1] = lp;
             p.loss[2] = lb;

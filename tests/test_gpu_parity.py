@@ -102,7 +102,9 @@ def test_forward_dead_inputs_and_empty(handles):
     got = jets.cpu().numpy()
     for r, tol in enumerate(row_tolerances(0x1F, STRESS)):
         assert relerr(got[r], want[r]) < tol
-    assert np.all(got[1:, [0, 1, 3]] == 0.0)   # both coordinates dead: no input derivative at all
+    assert np.all(got[1:, [1, 3]] == 0.0)      # both coordinates dead: no input derivative at all
+    assert np.all(got[[1, 3], 0] == 0.0)       # x dead: no x-derivatives
+    assert np.all(got[[2, 4], 2] == 0.0)       # y dead: no y-derivatives
     capi.hrkan_forward_jets(h, _t(W), _t(x), 0, 0x1F, jets)
     torch.cuda.synchronize()
 
