@@ -61,25 +61,17 @@ struct Active {
             for (int e = 0; e < M - 3; ++e) Qm3 *= Q;
             float Qm2 = (M >= 3) ? Qm3 * Q : 1.0f;
             float Qm1 = Qm2 * Q;
-            const float a1 = g.inv_a;
-            const float u2 = u * u;
-            v[q] = Qm1 * Q;
-            d1[q] = (-2.0f * M) * u * Qm1 * a1;
-            d2[q] = ((-2.0f * M) * Qm1 + (4.0f * M * (M - 1)) * u2 * Qm2) * (a1 * a1);
+            float Qm = Qm1 * Q;
+            bool ok = (unsigned)(c + q) < (unsigned)g.n;
+            float a1 = g.inv_a;
+            v[q] = ok ? Qm : 0.0f;
+            d1[q] = ok ? (-2.0f * M) * u * Qm1 * a1 : 0.0f;
+            float u2 = u * u;
+            d2[q] = ok ? ((-2.0f * M) * Qm1 + (4.0f * M * (M - 1)) * u2 * Qm2) * (a1 * a1) : 0.0f;
             if constexpr (NDER >= 3) {
                 float t3 = (12.0f * M * (M - 1)) * u * Qm2;
                 if constexpr (M >= 3) t3 -= (8.0f * M * (M - 1) * (M - 2)) * u2 * u * Qm3;
-                d3[q] = t3 * (a1 * a1 * a1);
-            }
-        }
-        // near the ends of the extended grid some of c..c+K do not exist
-        if ((unsigned)c > (unsigned)(g.n - 1 - K)) {
-#pragma unroll
-            for (int q = 0; q < K + 1; ++q) {
-                if ((unsigned)(c + q) >= (unsigned)g.n) {
-                    v[q] = d1[q] = d2[q] = 0.0f;
-                    if constexpr (NDER >= 3) d3[q] = 0.0f;
-                }
+                d3[q] = ok ? t3 * (a1 * a1 * a1) : 0.0f;
             }
         }
     }
