@@ -197,6 +197,29 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
                      hrkan_stream_t stream);
 
 /*
+ * hrkan_backward without any allocation (the paper has no counterpart; this is
+ * for callers that cannot call cudaMalloc, e.g. code running under another
+ * framework's memory pool or with all device memory reserved up front, which
+ * therefore cannot create a handle).  Same arguments and result as
+ * hrkan_backward, but the network shape comes from cfg and no handle, tape or
+ * workspace is used: the per-block gradient partials live in a file-scope
+ * static device array of 1 Mi floats (4 MiB), which every GPU that loads the
+ * library holds until the process exits.
+ *   - Networks with more than 1 Mi weights are rejected with HRKAN_EINVAL;
+ *     only the fused narrow shapes are supported (else HRKAN_EUNSUPPORTED).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array and leaves its partials there; each
+ *     call overwrites the rows it reads, so nothing needs clearing, but calls
+ *     whose work overlaps on the GPU (other streams, other threads) race.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ */
+int hrkan_backward_noalloc(const hrkan_cfg* cfg, const float* W, const float* x, int64_t N,
+                           unsigned jet_mask, const float* dL_djets, float* dW, int accumulate,
+                           hrkan_stream_t stream);
+
+/*
  * Kernel timing.  While enabled, every kernel the handle launches is
  * bracketed by two CUDA events on its stream (do not enable it around stream
  * capture).  hrkan_profile_read waits for the recorded events, adds their

@@ -25,7 +25,7 @@ HRKAN_MAX_WIDTHS = 8
 # every symbol include/hrkan.h declares
 EXPORTS = ("hrkan_param_count", "hrkan_init", "hrkan_destroy", "hrkan_last_error", "hrkan_tape_floats",
            "hrkan_forward_jets", "pinn_residual_loss", "hrkan_backward", "adam_step", "hrkan_reset_moments",
-           "hrkan_train_step", "hrkan_profile_enable", "hrkan_profile_read")
+           "hrkan_train_step", "hrkan_profile_enable", "hrkan_profile_read", "hrkan_backward_noalloc")
 HRKAN_KERNEL_FUSED, HRKAN_KERNEL_REDUCE, HRKAN_KERNEL_FORWARD, HRKAN_KERNEL_RESIDUAL = 0, 1, 2, 3
 
 
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH):
         lib.hrkan_reset_moments.argtypes = [_vp, _vp]
         lib.hrkan_train_step.argtypes = [_vp, ctypes.POINTER(pinn_problem), _vp, _vp, _i64, _vp, _vp, _i64, _d, _d,
                                          _d, _d, _i32, _vp, _vp, _vp]
+        lib.hrkan_backward_noalloc.argtypes = [ctypes.POINTER(hrkan_cfg), _vp, _vp, _i64, _u32, _vp, _vp, _i32, _vp]
         lib.hrkan_profile_enable.argtypes = [_vp, _i32]
         lib.hrkan_profile_read.argtypes = [_vp, _i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
         for name in EXPORTS:
@@ -202,3 +203,12 @@ def hrkan_profile_read(h, kernel_class, reset=True):
     ms, n = ctypes.c_double(), ctypes.c_int64()
     _check(load_library().hrkan_profile_read(h, int(kernel_class), ctypes.byref(ms), ctypes.byref(n), int(reset)))
     return ms.value, n.value
+
+
+def hrkan_backward_noalloc(cfg, W, x, N, jet_mask, dL_djets, dW, accumulate=False, stream=None):
+    """hrkan_backward for callers that cannot allocate: no handle, static device scratch."""
+    import torch
+    f = torch.float32
+    _check(load_library().hrkan_backward_noalloc(ctypes.byref(cfg), _ptr(W, f), _ptr(x, f), int(N), int(jet_mask),
+                                                 _ptr(dL_djets, f), _ptr(dW, f), int(bool(accumulate)),
+                                                 _stream(stream)))

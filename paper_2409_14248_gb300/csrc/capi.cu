@@ -160,6 +160,14 @@ NarrowParams base_params(hrkan_t h, const float* W) {
 
 }  // namespace
 
+namespace hrkan {
+// Records the message hrkan_last_error() returns (for entry points in other files).
+int set_last_error(int code, const char* msg) {
+    g_err = msg;
+    return code;
+}
+}  // namespace hrkan
+
 extern "C" {
 
 int64_t hrkan_param_count(const hrkan_cfg* cfg) {

@@ -60,4 +60,7 @@ struct ResidualParams {
 cudaError_t launch_residual(const ResidualParams& p, int grid, cudaStream_t s);
 bool residual_mask_supported(unsigned mask);
 
+// Sets the thread's last-error message and returns code.
+int set_last_error(int code, const char* msg);
+
 }  // namespace hrkan
