@@ -197,6 +197,35 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
                      hrkan_stream_t stream);
 
 /*
+ * Many independent networks of the handle's shape trained together: one
+ * persistent launch over all instances plus one per-instance reduction/Adam
+ * launch (the multi-instance workload of the training experiments of
+ * Section 4, run as a batch).  cfg.n_instances = I networks; W is [I][P];
+ * instance i owns interior points [off_int[i], off_int[i+1]) of x_int [2][N]
+ * and boundary points [off_bnd[i], off_bnd[i+1]) of x_bnd / g_bnd.
+ *   probs      host [I]: kind, lam, nu and alpha must agree; a, b may differ.
+ *   off_int, off_bnd  host [I+1], non-decreasing, starting at 0.
+ *   t          Adam step >= 1, or 0 for the device step counter (as in
+ *              hrkan_train_step); the moments of instance i are its own.
+ *   loss       device [I][3] float64 (L, mean r^2, mean (u-g)^2 per instance).
+ * The work list (items of hrkan_set_batch_items points each) is rebuilt and
+ * uploaded only when the offsets or problems change (that call synchronises
+ * the stream); calls with unchanged arguments only enqueue the two kernels, so
+ * they can be captured in a CUDA graph after one warm-up call.
+ */
+int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, const float* x_int,
+                             const int64_t* off_int, const float* x_bnd, const float* g_bnd,
+                             const int64_t* off_bnd, double lr, double b1, double b2, double eps, int t,
+                             double* loss, hrkan_stream_t stream);
+
+/* Output jets of every instance at its points (x [2][N], offsets host [I+1], jets [J][N]). */
+int hrkan_forward_jets_batched(hrkan_t h, const float* W, const float* x, const int64_t* offsets,
+                               unsigned jet_mask, float* jets, hrkan_stream_t stream);
+
+/* Points per work item of the multi-instance calls (default 1024); a tuning knob. */
+int hrkan_set_batch_items(hrkan_t h, int points_per_item);
+
+/*
  * hrkan_backward without any allocation (the paper has no counterpart; this is
  * for callers that cannot call cudaMalloc, e.g. code running under another
  * framework's memory pool or with all device memory reserved up front, which

@@ -25,7 +25,8 @@ HRKAN_MAX_WIDTHS = 8
 # every symbol include/hrkan.h declares
 EXPORTS = ("hrkan_param_count", "hrkan_init", "hrkan_destroy", "hrkan_last_error", "hrkan_tape_floats",
            "hrkan_forward_jets", "pinn_residual_loss", "hrkan_backward", "adam_step", "hrkan_reset_moments",
-           "hrkan_train_step", "hrkan_profile_enable", "hrkan_profile_read", "hrkan_backward_noalloc")
+           "hrkan_train_step", "hrkan_profile_enable", "hrkan_profile_read", "hrkan_backward_noalloc",
+           "hrkan_train_step_batched", "hrkan_forward_jets_batched", "hrkan_set_batch_items")
 HRKAN_KERNEL_FUSED, HRKAN_KERNEL_REDUCE, HRKAN_KERNEL_FORWARD, HRKAN_KERNEL_RESIDUAL = 0, 1, 2, 3
 
 
@@ -80,6 +81,11 @@ def load_library(path: str = LIB_PATH):
         lib.hrkan_train_step.argtypes = [_vp, ctypes.POINTER(pinn_problem), _vp, _vp, _i64, _vp, _vp, _i64, _d, _d,
                                          _d, _d, _i32, _vp, _vp, _vp]
         lib.hrkan_backward_noalloc.argtypes = [ctypes.POINTER(hrkan_cfg), _vp, _vp, _i64, _u32, _vp, _vp, _i32, _vp]
+        _i64p = ctypes.POINTER(_i64)
+        lib.hrkan_train_step_batched.argtypes = [_vp, ctypes.POINTER(pinn_problem), _vp, _vp, _i64p, _vp, _vp, _i64p,
+                                                 _d, _d, _d, _d, _i32, _vp, _vp]
+        lib.hrkan_forward_jets_batched.argtypes = [_vp, _vp, _vp, _i64p, _u32, _vp, _vp]
+        lib.hrkan_set_batch_items.argtypes = [_vp, _i32]
         lib.hrkan_profile_enable.argtypes = [_vp, _i32]
         lib.hrkan_profile_read.argtypes = [_vp, _i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
         for name in EXPORTS:
@@ -212,3 +218,34 @@ def hrkan_backward_noalloc(cfg, W, x, N, jet_mask, dL_djets, dW, accumulate=Fals
     _check(load_library().hrkan_backward_noalloc(ctypes.byref(cfg), _ptr(W, f), _ptr(x, f), int(N), int(jet_mask),
                                                  _ptr(dL_djets, f), _ptr(dW, f), int(bool(accumulate)),
                                                  _stream(stream)))
+
+
+def _i64_array(a):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def hrkan_train_step_batched(h, probs, W, x_int, off_int, x_bnd, g_bnd, off_bnd, lr, b1, b2, eps, t, loss,
+                             stream=None):
+    """probs: sequence of pinn_problem (one per instance); offsets: host int arrays [I+1]."""
+    import torch
+    f = torch.float32
+    arr = (pinn_problem * len(probs))(*probs)
+    oi, oip = _i64_array(off_int)
+    ob, obp = _i64_array(off_bnd)
+    _check(load_library().hrkan_train_step_batched(h, arr, _ptr(W, f), _ptr(x_int, f), oip, _ptr(x_bnd, f),
+                                                   _ptr(g_bnd, f), obp, float(lr), float(b1), float(b2), float(eps),
+                                                   int(t), _ptr(loss, torch.float64), _stream(stream)))
+
+
+def hrkan_forward_jets_batched(h, W, x, offsets, jet_mask, jets, stream=None):
+    import torch
+    f = torch.float32
+    o, op = _i64_array(offsets)
+    _check(load_library().hrkan_forward_jets_batched(h, _ptr(W, f), _ptr(x, f), op, int(jet_mask), _ptr(jets, f),
+                                                     _stream(stream)))
+
+
+def hrkan_set_batch_items(h, points_per_item):
+    _check(load_library().hrkan_set_batch_items(h, int(points_per_item)))

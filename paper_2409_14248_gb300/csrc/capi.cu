@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/hrkan.h"
@@ -30,6 +31,21 @@ struct hrkan_ctx {
     double* m1 = nullptr;
     double* m2 = nullptr;
     int* t_counter = nullptr;        // [2] device Adam step counter (t = 0 mode)
+    // multi-instance work lists (rebuilt only when the offsets or problems change)
+    struct Batch {
+        std::vector<int64_t> off0, off1;
+        std::vector<double> ab;
+        int items_points = 0;
+        int n_items = 0, cap_items = 0, n_inst = 0;
+        BatchItem* items = nullptr;
+        BatchInst* inst = nullptr;
+        int* item_off = nullptr;
+        float* counts = nullptr;
+        float* partial = nullptr;
+        size_t partial_cap = 0;     // floats
+        double* loss_partial = nullptr;
+    } train_batch, fwd_batch;
+    int batch_items_points = 1024;  // points per work item
     // kernel timing
     bool prof = false;
     struct Ev { cudaEvent_t a, b; int cls; };
@@ -160,6 +176,97 @@ NarrowParams base_params(hrkan_t h, const float* W) {
 
 }  // namespace
 
+namespace {
+
+// Validates the offsets and (re)builds the work list of a multi-instance call.
+// Host-to-device copies happen only when the offsets, problems or item size
+// changed since the previous call, so a repeated call enqueues kernels only.
+int build_batch(hrkan_t h, hrkan_ctx::Batch& b, int n_inst, const pinn_problem* probs, const int64_t* off0,
+                const int64_t* off1, bool train, cudaStream_t stream) {
+    const int ip = h->batch_items_points;
+    for (int i = 0; i < n_inst; ++i) {
+        if (off0[i + 1] < off0[i]) return fail(HRKAN_EINVAL, "interior offsets decrease at instance %d", i);
+        if (train && off1[i + 1] < off1[i]) return fail(HRKAN_EINVAL, "boundary offsets decrease at instance %d", i);
+    }
+    if (off0[0] != 0 || (train && off1[0] != 0)) return fail(HRKAN_EINVAL, "offsets must start at 0");
+    std::vector<double> ab;
+    if (probs)
+        for (int i = 0; i < n_inst; ++i) {
+            ab.push_back(probs[i].a);
+            ab.push_back(probs[i].b);
+            ab.push_back(probs[i].alpha);
+        }
+    std::vector<int64_t> o0(off0, off0 + n_inst + 1), o1;
+    if (train) o1.assign(off1, off1 + n_inst + 1);
+    if (b.n_inst == n_inst && b.items_points == ip && b.off0 == o0 && b.off1 == o1 && b.ab == ab) return HRKAN_OK;
+
+    // earlier launches on this stream may still read the old list
+    if (b.n_items > 0) {
+        cudaError_t se = cudaStreamSynchronize(stream);
+        if (se != cudaSuccess) return cuda_fail(se, "cudaStreamSynchronize before rebuilding the work list");
+    }
+    std::vector<BatchItem> items;
+    std::vector<BatchInst> inst(n_inst);
+    std::vector<int> item_off(n_inst + 1, 0);
+    std::vector<float> counts(2 * n_inst, 0.0f);
+    for (int i = 0; i < n_inst; ++i) {
+        item_off[i] = int(items.size());
+        for (int64_t a = off0[i]; a < off0[i + 1]; a += ip) items.push_back({i, 0, a, std::min<int64_t>(a + ip, off0[i + 1])});
+        if (train)
+            for (int64_t a = off1[i]; a < off1[i + 1]; a += ip)
+                items.push_back({i, 1, a, std::min<int64_t>(a + ip, off1[i + 1])});
+        const double ni = double(off0[i + 1] - off0[i]), nb = train ? double(off1[i + 1] - off1[i]) : 0.0;
+        counts[2 * i] = float(ni);
+        counts[2 * i + 1] = float(nb);
+        if (probs) {
+            const double a = probs[i].a, bb = probs[i].b;
+            inst[i] = {float(a), float(bb), float((a * a + bb * bb) * M_PI * M_PI),
+                       ni > 0 ? float(2.0 * probs[i].alpha / ni) : 0.0f, nb > 0 ? float(2.0 / nb) : 0.0f};
+        }
+    }
+    item_off[n_inst] = int(items.size());
+    const int n_items = int(items.size());
+    cudaError_t e;
+    if (n_items > b.cap_items || n_inst > b.n_inst || !b.inst) {
+        cudaFree(b.items); cudaFree(b.loss_partial); cudaFree(b.inst); cudaFree(b.item_off); cudaFree(b.counts);
+        b.items = nullptr; b.loss_partial = nullptr; b.inst = nullptr; b.item_off = nullptr; b.counts = nullptr;
+        const int cap = std::max(n_items, 1);
+        if ((e = cudaMalloc(&b.items, sizeof(BatchItem) * cap)) != cudaSuccess ||
+            (e = cudaMalloc(&b.loss_partial, sizeof(double) * 2 * cap)) != cudaSuccess ||
+            (e = cudaMalloc(&b.inst, sizeof(BatchInst) * std::max(n_inst, 1))) != cudaSuccess ||
+            (e = cudaMalloc(&b.item_off, sizeof(int) * (n_inst + 1))) != cudaSuccess ||
+            (e = cudaMalloc(&b.counts, sizeof(float) * 2 * std::max(n_inst, 1))) != cudaSuccess) {
+            b.cap_items = 0;
+            b.n_inst = 0;
+            return fail(HRKAN_ENOMEM, "cudaMalloc of the work list: %s", cudaGetErrorString(e));
+        }
+        b.cap_items = cap;
+    }
+    if (train && size_t(n_items) * size_t(h->P) > b.partial_cap) {
+        cudaFree(b.partial);
+        b.partial = nullptr;
+        b.partial_cap = 0;
+        if ((e = cudaMalloc(&b.partial, sizeof(float) * size_t(n_items) * size_t(h->P))) != cudaSuccess)
+            return fail(HRKAN_ENOMEM, "cudaMalloc of the gradient partials: %s", cudaGetErrorString(e));
+        b.partial_cap = size_t(n_items) * size_t(h->P);
+    }
+    if (n_items && (e = cudaMemcpy(b.items, items.data(), sizeof(BatchItem) * n_items, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "work list upload");
+    if ((e = cudaMemcpy(b.inst, inst.data(), sizeof(BatchInst) * n_inst, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b.item_off, item_off.data(), sizeof(int) * (n_inst + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b.counts, counts.data(), sizeof(float) * 2 * n_inst, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "work list upload");
+    b.n_items = n_items;
+    b.n_inst = n_inst;
+    b.items_points = ip;
+    b.off0 = std::move(o0);
+    b.off1 = std::move(o1);
+    b.ab = std::move(ab);
+    return HRKAN_OK;
+}
+
+}  // namespace
+
 namespace hrkan {
 // Records the message hrkan_last_error() returns (for entry points in other files).
 int set_last_error(int code, const char* msg) {
@@ -190,7 +297,6 @@ int hrkan_init(hrkan_t* out, const hrkan_cfg* cfg) {
     if (net_id < 0)
         return fail(HRKAN_EUNSUPPORTED, "no kernels for this network shape (L=%d, hidden width %d)", L, cfg->widths[1]);
     if (cfg->prec != HRKAN_FP32) return fail(HRKAN_EUNSUPPORTED, "precision %d has no kernels for this shape", cfg->prec);
-    if (cfg->n_instances != 1) return fail(HRKAN_EUNSUPPORTED, "n_instances > 1 has no kernels for this shape");
 
     hrkan_ctx* h = new (std::nothrow) hrkan_ctx();
     if (!h) return fail(HRKAN_ENOMEM, "host allocation");
@@ -216,14 +322,14 @@ int hrkan_init(hrkan_t* out, const hrkan_cfg* cfg) {
     size_t bytes_partial = size_t(h->max_grid) * size_t(h->P) * sizeof(float);
     if ((e = cudaMalloc(&h->partial, bytes_partial)) != cudaSuccess ||
         (e = cudaMalloc(&h->loss_partial, size_t(h->max_grid_l) * 2 * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&h->m1, size_t(h->P) * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&h->m2, size_t(h->P) * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&h->m1, size_t(h->P) * cfg->n_instances * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&h->m2, size_t(h->P) * cfg->n_instances * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&h->t_counter, 2 * sizeof(int))) != cudaSuccess) {
         hrkan_destroy(h);
         return fail(HRKAN_ENOMEM, "cudaMalloc of the workspace: %s", cudaGetErrorString(e));
     }
-    if ((e = cudaMemset(h->m1, 0, size_t(h->P) * sizeof(double))) != cudaSuccess ||
-        (e = cudaMemset(h->m2, 0, size_t(h->P) * sizeof(double))) != cudaSuccess ||
+    if ((e = cudaMemset(h->m1, 0, size_t(h->P) * cfg->n_instances * sizeof(double))) != cudaSuccess ||
+        (e = cudaMemset(h->m2, 0, size_t(h->P) * cfg->n_instances * sizeof(double))) != cudaSuccess ||
         (e = cudaMemset(h->t_counter, 0, 2 * sizeof(int))) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess) {
         hrkan_destroy(h);
@@ -244,6 +350,10 @@ void hrkan_destroy(hrkan_t h) {
     cudaFree(h->m1);
     cudaFree(h->m2);
     cudaFree(h->t_counter);
+    for (auto* b : {&h->train_batch, &h->fwd_batch}) {
+        cudaFree(b->items); cudaFree(b->inst); cudaFree(b->item_off); cudaFree(b->counts);
+        cudaFree(b->partial); cudaFree(b->loss_partial);
+    }
     for (auto& ev : h->pending) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
     for (auto& ev : h->pool) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
     if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
@@ -401,8 +511,9 @@ int hrkan_reset_moments(hrkan_t h, hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
     if (int rc = use_device(h)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    HR_CUDA(cudaMemsetAsync(h->m1, 0, size_t(h->P) * sizeof(double), s), "cudaMemsetAsync");
-    HR_CUDA(cudaMemsetAsync(h->m2, 0, size_t(h->P) * sizeof(double), s), "cudaMemsetAsync");
+    const size_t mb = size_t(h->P) * h->cfg.n_instances * sizeof(double);
+    HR_CUDA(cudaMemsetAsync(h->m1, 0, mb, s), "cudaMemsetAsync");
+    HR_CUDA(cudaMemsetAsync(h->m2, 0, mb, s), "cudaMemsetAsync");
     HR_CUDA(cudaMemsetAsync(h->t_counter, 0, 2 * sizeof(int), s), "cudaMemsetAsync");
     return HRKAN_OK;
 }
@@ -495,6 +606,118 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
         ProfScope ps(h, HRKAN_KERNEL_REDUCE, s);
         HR_CUDA(launch_reduce(q, s), "reduce/Adam launch");
     }
+    return HRKAN_OK;
+}
+
+int hrkan_set_batch_items(hrkan_t h, int points_per_item) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (points_per_item < 1) return fail(HRKAN_EINVAL, "points_per_item=%d", points_per_item);
+    h->batch_items_points = points_per_item;
+    return HRKAN_OK;
+}
+
+int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, const float* x_int,
+                             const int64_t* off_int, const float* x_bnd, const float* g_bnd, const int64_t* off_bnd,
+                             double lr, double b1, double b2, double eps, int t, double* loss,
+                             hrkan_stream_t stream) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    const int n_inst = h->cfg.n_instances;
+    if (!probs || !off_int || !off_bnd) return fail(HRKAN_EINVAL, "NULL host array");
+    for (int i = 0; i < n_inst; ++i) {
+        if (int rc = check_problem(&probs[i])) return rc;
+        if (probs[i].kind != probs[0].kind || probs[i].lam != probs[0].lam || probs[i].nu != probs[0].nu ||
+            probs[i].alpha != probs[0].alpha)
+            return fail(HRKAN_EINVAL, "instance %d: kind, lam, nu and alpha must agree across instances", i);
+    }
+    if (!W || !loss) return fail(HRKAN_EINVAL, "NULL device pointer");
+    if (t < 0) return fail(HRKAN_EINVAL, "Adam step t=%d must be >= 0", t);
+    if (!(b1 >= 0.0 && b1 < 1.0 && b2 >= 0.0 && b2 < 1.0 && eps >= 0.0 && std::isfinite(lr)))
+        return fail(HRKAN_EINVAL, "Adam hyper-parameters lr=%g b1=%g b2=%g eps=%g", lr, b1, b2, eps);
+    const int64_t n0 = off_int[n_inst], n1 = off_bnd[n_inst];
+    if ((n0 > 0 && !x_int) || (n1 > 0 && (!x_bnd || !g_bnd))) return fail(HRKAN_EINVAL, "NULL point array");
+    if (int rc = use_device(h)) return rc;
+    auto& b = h->train_batch;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (int rc = build_batch(h, b, n_inst, probs, off_int, off_bnd, true, s)) return rc;
+    const unsigned mask = probs[0].kind == HRKAN_POISSON ? 0x1Fu : 0x0Fu;
+    BatchParams p{};
+    p.W = W;
+    p.P = h->P;
+    p.x0 = x_int;
+    p.n0 = n0;
+    p.x1 = x_bnd;
+    p.g1 = g_bnd;
+    p.n1 = n1;
+    p.items = b.items;
+    p.n_items = b.n_items;
+    p.inst = b.inst;
+    p.pde = make_pde(&probs[0]);
+    p.partial = b.partial;
+    p.loss_partial = b.loss_partial;
+    p.grid = h->grid;
+    p.t_counter = t == 0 ? h->t_counter : nullptr;
+    if (b.n_items > 0) {
+        int grid = 0;
+        cudaError_t e;
+        {
+            ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
+            e = narrow_batch_launch(h->net_id, MODE_TRAIN, mask, p, &grid, 1 << 30, true, s);
+        }
+        if (e == cudaErrorInvalidValue) return fail(HRKAN_EUNSUPPORTED, "no multi-instance training kernel");
+        if (e != cudaSuccess) return cuda_fail(e, "multi-instance train launch");
+    }
+    BatchReduceParams q{};
+    q.partial = b.partial;
+    q.item_off = b.item_off;
+    q.n_inst = n_inst;
+    q.P = h->P;
+    q.W = W;
+    q.m1 = h->m1;
+    q.m2 = h->m2;
+    q.lr = lr; q.b1 = b1; q.b2 = b2; q.eps = eps;
+    q.c1 = 1.0 - std::pow(b1, t > 0 ? t : 1);
+    q.c2 = 1.0 - std::pow(b2, t > 0 ? t : 1);
+    q.t_counter = t == 0 ? h->t_counter : nullptr;
+    q.loss_partial = b.loss_partial;
+    q.counts = b.counts;
+    q.loss = loss;
+    q.alpha = probs[0].alpha;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_REDUCE, s);
+        HR_CUDA(launch_batch_reduce(q, s), "multi-instance reduce launch");
+    }
+    return HRKAN_OK;
+}
+
+int hrkan_forward_jets_batched(hrkan_t h, const float* W, const float* x, const int64_t* offsets, unsigned jet_mask,
+                               float* jets, hrkan_stream_t stream) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (!offsets) return fail(HRKAN_EINVAL, "offsets is NULL");
+    if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
+    const int n_inst = h->cfg.n_instances;
+    const int64_t N = offsets[n_inst];
+    if (N > 0 && (!W || !x || !jets)) return fail(HRKAN_EINVAL, "NULL device pointer");
+    if (int rc = use_device(h)) return rc;
+    auto& b = h->fwd_batch;
+    if (int rc = build_batch(h, b, n_inst, nullptr, offsets, nullptr, false, (cudaStream_t)stream)) return rc;
+    if (b.n_items == 0) return HRKAN_OK;
+    BatchParams p{};
+    p.W = W;
+    p.P = h->P;
+    p.x0 = x;
+    p.n0 = N;
+    p.jets = jets;
+    p.items = b.items;
+    p.n_items = b.n_items;
+    p.grid = h->grid;
+    int grid = 0;
+    cudaError_t e;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_FORWARD, (cudaStream_t)stream);
+        e = narrow_batch_launch(h->net_id, MODE_FWD, jet_mask, p, &grid, 1 << 30, true, (cudaStream_t)stream);
+    }
+    if (e == cudaErrorInvalidValue) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no forward kernel", jet_mask);
+    if (e != cudaSuccess) return cuda_fail(e, "multi-instance forward launch");
     return HRKAN_OK;
 }
 

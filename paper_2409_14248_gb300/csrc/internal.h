@@ -9,6 +9,7 @@
 namespace hrkan {
 
 struct NarrowParams;
+struct BatchParams;
 
 // ---- fused narrow-network kernels (narrow_*.cu) --------------------------------
 // Shapes with a fused kernel: widths [2, WH, 1] or [2, WH, WH, 1], k = 3, m = 4.
@@ -20,6 +21,11 @@ int narrow_net_id(int n_layers, int wh);
 // `launch` is false.  Returns cudaErrorInvalidValue for a mask with no kernel.
 cudaError_t narrow_launch(int net_id, int mode, unsigned mask, const NarrowParams& p, int* grid,
                           int max_grid, bool launch, cudaStream_t s);
+
+// Same for the multi-instance kernels (MODE_FWD / MODE_TRAIN) over a work list;
+// *grid is capped at max_grid and at the number of items.
+cudaError_t narrow_batch_launch(int net_id, int mode, unsigned mask, const BatchParams& p, int* grid, int max_grid,
+                                bool launch, cudaStream_t s);
 
 // ---- reductions, Adam, residual (reduce.cu) -------------------------------------
 struct ReduceParams {
@@ -41,6 +47,25 @@ struct ReduceParams {
     int64_t n0, n1;
 };
 cudaError_t launch_reduce(const ReduceParams& p, cudaStream_t s);
+
+// Per-instance reduction + Adam for the multi-instance step: instance i owns
+// partial rows [item_off[i], item_off[i+1]) of [n_items][P].
+struct BatchReduceParams {
+    const float* partial;
+    const int* item_off;       // [n_inst + 1] device
+    int n_inst;
+    int64_t P;
+    float* W;                  // [n_inst][P]
+    double* m1;
+    double* m2;
+    double lr, b1, b2, eps, c1, c2;
+    int* t_counter;
+    const double* loss_partial;  // [n_items][2]
+    const float* counts;         // [n_inst][2] interior / boundary point counts
+    double* loss;                // [n_inst][3]
+    double alpha;
+};
+cudaError_t launch_batch_reduce(const BatchReduceParams& p, cudaStream_t s);
 
 struct ResidualParams {
     PdeParams pde;

@@ -32,7 +32,7 @@ struct NarrowNet {
     // Copies of the shared weight gradient, one per group of lanes (lane % COPIES).
     // Hidden activations of a PINN often sit in one or two grid cells, so the
     // lanes of a warp would otherwise add into the same address at once.
-    static constexpr int COPIES = WH_ >= 16 ? 4 : 8;
+    static constexpr int COPIES = 4;
     static_assert(NL == 2 || NL == 3, "narrow nets have one or two hidden layers");
 
     // shared-memory layout in floats (n = number of bases)
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(NARROW_BLOCK) narrow_fwd_kernel(NarrowParams p
 // MODE_BWD: one point set, gu read from dL.  MODE_TRAIN: interior (MASK)
 // then boundary (value only) tiles, gu from the residual.
 template <class Net, unsigned MASK, int MODE>
-__global__ void __launch_bounds__(NARROW_BLOCK) narrow_grad_kernel(NarrowParams p) {
+__global__ void __launch_bounds__(NARROW_BLOCK, 4) narrow_grad_kernel(NarrowParams p) {
     extern __shared__ __align__(16) float smem[];
     if (MODE == MODE_TRAIN && p.t_counter && blockIdx.x == 0 && threadIdx.x == 0)
         p.t_counter[1] = p.t_counter[0] + 1;
@@ -432,6 +432,139 @@ __global__ void __launch_bounds__(NARROW_BLOCK) narrow_grad_kernel(NarrowParams 
     }
     __syncthreads();
     narrow_store_dw<Net>(s, p.partial + int64_t(blockIdx.x) * p.P, n);
+}
+
+}  // namespace hrkan
+
+// ---------------------------------------------------------------------------
+// Many independent networks of one narrow shape in one persistent launch.
+//
+// The host cuts every instance's interior and boundary points into items of a
+// few tiles; block b walks items b, b + grid, ...  Per item the block loads
+// that instance's weights into shared memory, accumulates the item's weight
+// gradient in the shared copies, and writes one partial row (and one loss
+// partial) per item.  A second kernel sums each instance's rows in a fixed
+// order and applies Adam per instance.
+namespace hrkan {
+
+struct BatchItem {
+    int inst;          // instance
+    int set;           // 0 = interior (residual), 1 = boundary / initial (value)
+    int64_t begin;     // point range [begin, end) in the concatenated set
+    int64_t end;
+};
+
+struct BatchInst {
+    float a, b, src;   // Poisson frequencies and (a^2+b^2) pi^2
+    float scale0;      // 2 alpha / N_int of the instance
+    float scale1;      // 2 / N_bnd of the instance
+};
+
+struct BatchParams {
+    const float* W;            // [inst][P]
+    int64_t P;
+    const float* x0;           // interior [2][n0]
+    int64_t n0;
+    const float* x1;           // boundary [2][n1]
+    const float* g1;
+    int64_t n1;
+    float* jets;               // forward only: [J][n0]
+    const BatchItem* items;
+    int n_items;
+    const BatchInst* inst;
+    PdeParams pde;             // kind, lam, nu, alpha (shared by the instances)
+    float* partial;            // [n_items][P]
+    double* loss_partial;      // [n_items][2]
+    Grid grid;
+    int* t_counter;
+};
+
+template <class Net, unsigned MASK>
+__global__ void __launch_bounds__(NARROW_BLOCK, 4) narrow_batch_kernel(BatchParams p) {
+    extern __shared__ __align__(16) float smem[];
+    if (p.t_counter && blockIdx.x == 0 && threadIdx.x == 0) p.t_counter[1] = p.t_counter[0] + 1;
+    const int n = p.grid.n;
+    const int sf = Net::smem_floats(n);
+    float* s = smem;
+    float* ds = smem + sf;
+    const DwAcc<Net> dwacc{ds, int(threadIdx.x) & (Net::COPIES - 1)};
+    for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
+        const BatchItem item = p.items[it];
+        const BatchInst bi = p.inst[item.inst];
+        narrow_load_w<Net>(p.W + int64_t(item.inst) * p.P, s, n);
+        for (int t = threadIdx.x; t < sf * Net::COPIES; t += blockDim.x) ds[t] = 0.0f;
+        __syncthreads();
+        PdeParams pde = p.pde;
+        pde.a = bi.a;
+        pde.b = bi.b;
+        pde.src = bi.src;
+        double lsum = 0.0;
+        for (int64_t base = item.begin; base < item.end; base += NARROW_BLOCK) {
+            const int64_t pt = base + threadIdx.x;
+            if (pt >= item.end) continue;
+            if (item.set == 0) {
+                using JT = Jet<MASK>;
+                const int64_t N = p.n0;
+                const float x0 = p.x0[pt], x1 = p.x0[N + pt];
+                CoordBases<Net> xb;
+                xb.b[0].eval(x0, p.grid);
+                xb.b[1].eval(x1, p.grid);
+                float h[Net::WH][JT::J], u[JT::J], gu[JT::J];
+                narrow_forward<Net, MASK>(xb, s, n, p.grid, h, u);
+                const float r = pde_residual<MASK>(pde, x0, x1, u);
+                lsum += double(r) * double(r);
+                pde_residual_grad<MASK>(pde, r, u, bi.scale0, gu);
+                narrow_backward<Net, MASK>(xb, s, dwacc, n, p.grid, h, gu);
+            } else {
+                const int64_t N = p.n1;
+                CoordBases<Net> xb;
+                xb.b[0].eval(p.x1[pt], p.grid);
+                xb.b[1].eval(p.x1[N + pt], p.grid);
+                float h[Net::WH][1], u[1], gu[1];
+                narrow_forward<Net, 1u>(xb, s, n, p.grid, h, u);
+                const float d = u[0] - p.g1[pt];
+                lsum += double(d) * double(d);
+                gu[0] = bi.scale1 * d;
+                narrow_backward<Net, 1u>(xb, s, dwacc, n, p.grid, h, gu);
+            }
+        }
+        narrow_block_loss<Net>(item.set == 0 ? lsum : 0.0, item.set == 0 ? 0.0 : lsum,
+                               p.loss_partial + 2 * int64_t(it));
+        __syncthreads();
+        for (int t = threadIdx.x; t < sf; t += blockDim.x) {
+            float a = 0.0f;
+#pragma unroll
+            for (int c = 0; c < Net::COPIES; ++c) a += ds[t * Net::COPIES + c];
+            s[t] = a;
+        }
+        __syncthreads();
+        narrow_store_dw<Net>(s, p.partial + int64_t(it) * p.P, n);
+        __syncthreads();
+    }
+}
+
+// Forward jets of many instances: items carry the instance of each point range.
+template <class Net, unsigned MASK>
+__global__ void __launch_bounds__(NARROW_BLOCK) narrow_batch_fwd_kernel(BatchParams p) {
+    using JT = Jet<MASK>;
+    extern __shared__ __align__(16) float smem[];
+    const int n = p.grid.n;
+    for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
+        const BatchItem item = p.items[it];
+        narrow_load_w<Net>(p.W + int64_t(item.inst) * p.P, smem, n);
+        __syncthreads();
+        const int64_t N = p.n0;
+        for (int64_t pt = item.begin + threadIdx.x; pt < item.end; pt += NARROW_BLOCK) {
+            CoordBases<Net> xb;
+            xb.b[0].eval(p.x0[pt], p.grid);
+            xb.b[1].eval(p.x0[N + pt], p.grid);
+            float h[Net::WH][JT::J], u[JT::J];
+            narrow_forward<Net, MASK>(xb, smem, n, p.grid, h, u);
+#pragma unroll
+            for (int r = 0; r < JT::J; ++r) p.jets[r * N + pt] = u[r];
+        }
+        __syncthreads();
+    }
 }
 
 }  // namespace hrkan

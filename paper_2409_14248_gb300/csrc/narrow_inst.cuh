@@ -6,14 +6,26 @@
 
 namespace hrkan {
 
+// Opt a kernel into the device's full dynamic shared memory once per process
+// (per kernel), so later launches, including ones under stream capture, make
+// no attribute calls.
+template <class KernelT>
+static cudaError_t allow_big_smem(KernelT kern) {
+    static cudaError_t once = [&]() {
+        int dev = 0, optin = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        return e;
+    }();
+    return once;
+}
+
 template <class Net, class KernelT>
 static cudaError_t narrow_go(KernelT kern, size_t smem, int64_t tiles, const NarrowParams& p, int* grid,
                              int max_grid, bool launch, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    if (smem > 48 * 1024 && (e = allow_big_smem(kern)) != cudaSuccess) return e;
     if (*grid <= 0) {
         int dev = 0, nsm = 0, occ = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -58,6 +70,44 @@ static cudaError_t narrow_launch_net(int mode, unsigned mask, const NarrowParams
     return cudaErrorInvalidValue;
 }
 
+template <class Net>
+static cudaError_t narrow_batch_launch_net(int mode, unsigned mask, const BatchParams& p, int* grid, int max_grid,
+                                           bool launch, cudaStream_t s) {
+    const size_t sf = size_t(Net::smem_floats(p.grid.n)) * sizeof(float);
+    const int64_t items = p.n_items;
+    auto go = [&](auto kern, size_t smem) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        if (smem > 48 * 1024 && (e = allow_big_smem(kern)) != cudaSuccess) return e;
+        if (*grid <= 0) {
+            int dev = 0, nsm = 0, occ = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NARROW_BLOCK, smem)) != cudaSuccess)
+                return e;
+            int64_t g = int64_t(nsm) * (occ > 0 ? occ : 1);
+            if (g > max_grid) g = max_grid;
+            if (g > items) g = items;
+            *grid = (int)(g > 0 ? g : 1);
+        }
+        if (!launch) return cudaSuccess;
+        kern<<<*grid, NARROW_BLOCK, smem, s>>>(p);
+        return cudaGetLastError();
+    };
+    if (mode == MODE_FWD) {
+        switch (mask) {
+            case 0x01u: return go(narrow_batch_fwd_kernel<Net, 0x01u>, sf);
+            case 0x0Fu: return go(narrow_batch_fwd_kernel<Net, 0x0Fu>, sf);
+            case 0x1Fu: return go(narrow_batch_fwd_kernel<Net, 0x1Fu>, sf);
+        }
+    } else if (mode == MODE_TRAIN) {
+        switch (mask) {
+            case 0x0Fu: return go(narrow_batch_kernel<Net, 0x0Fu>, (1 + Net::COPIES) * sf);
+            case 0x1Fu: return go(narrow_batch_kernel<Net, 0x1Fu>, (1 + Net::COPIES) * sf);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace hrkan
 
 #define HRKAN_NARROW_INSTANCE(FN, NL, WH)                                                               \
@@ -65,5 +115,9 @@ static cudaError_t narrow_launch_net(int mode, unsigned mask, const NarrowParams
     cudaError_t FN(int mode, unsigned mask, const NarrowParams& p, int* grid, int max_grid, bool launch, \
                    cudaStream_t s) {                                                                    \
         return narrow_launch_net<NarrowNet<NL, WH, 3, 4>>(mode, mask, p, grid, max_grid, launch, s);   \
+    }                                                                                                   \
+    cudaError_t FN##_batch(int mode, unsigned mask, const BatchParams& p, int* grid, int max_grid,       \
+                           bool launch, cudaStream_t s) {                                               \
+        return narrow_batch_launch_net<NarrowNet<NL, WH, 3, 4>>(mode, mask, p, grid, max_grid, launch, s); \
     }                                                                                                   \
     }

@@ -165,3 +165,82 @@ cudaError_t launch_residual(const ResidualParams& p, int grid, cudaStream_t s) {
 }
 
 }  // namespace hrkan
+
+// ------------------------------------------------------- many instances
+
+namespace hrkan {
+
+// grid (ceil(P / 32), n_inst): block (x, i) sums instance i's partial rows for
+// 32 weights in a fixed order, applies Adam, and block (0, i) finishes the
+// instance's loss.
+__global__ void __launch_bounds__(RED_LANES * RED_WARPS) batch_reduce_kernel(BatchReduceParams p) {
+    __shared__ float part[RED_WARPS][RED_LANES];
+    __shared__ float corr[2];
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int inst = blockIdx.y;
+    const int64_t k = int64_t(blockIdx.x) * RED_LANES + lane;
+    const int r0 = p.item_off[inst], r1 = p.item_off[inst + 1];
+    if (w == 0 && lane == 0) {
+        double c1 = p.c1, c2 = p.c2;
+        if (p.t_counter) {
+            const int t = p.t_counter[1];
+            c1 = 1.0 - pow(p.b1, double(t));
+            c2 = 1.0 - pow(p.b2, double(t));
+        }
+        corr[0] = float(1.0 / c1);
+        corr[1] = float(1.0 / sqrt(c2));
+    }
+    if (k < p.P) {
+        float acc = 0.0f;
+        for (int g = r0 + w; g < r1; g += RED_WARPS) acc += p.partial[int64_t(g) * p.P + k];
+        part[w][lane] = acc;
+    }
+    __syncthreads();
+    if (w == 0 && k < p.P) {
+        float gsum = 0.0f;
+#pragma unroll
+        for (int t = 0; t < RED_WARPS; ++t) gsum += part[t][lane];
+        const int64_t i = int64_t(inst) * p.P + k;
+        const double gd = gsum;
+        const double m1 = fma(p.b1, p.m1[i], (1.0 - p.b1) * gd);
+        const double m2 = fma(p.b2, p.m2[i], (1.0 - p.b2) * gd * gd);
+        p.m1[i] = m1;
+        p.m2[i] = m2;
+        const float mh = float(m1) * corr[0];
+        const float vh = sqrtf(float(m2)) * corr[1];
+        p.W[i] = p.W[i] - float(p.lr) * mh / (vh + float(p.eps));
+    }
+    if (p.t_counter && blockIdx.x == 0 && inst == 0 && w == 0 && lane == 0) p.t_counter[0] = p.t_counter[1];
+    if (blockIdx.x == 0 && w == 1) {
+        double s0 = 0.0, c0 = 0.0, s1 = 0.0, c1 = 0.0;
+        for (int g = r0 + lane; g < r1; g += 32) {
+            neumaier_add(s0, c0, p.loss_partial[2 * int64_t(g)]);
+            neumaier_add(s1, c1, p.loss_partial[2 * int64_t(g) + 1]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double a = __shfl_down_sync(0xffffffffu, s0, o), b = __shfl_down_sync(0xffffffffu, c0, o);
+            double e = __shfl_down_sync(0xffffffffu, s1, o), f = __shfl_down_sync(0xffffffffu, c1, o);
+            if (lane < o) {
+                neumaier_merge(s0, c0, a, b);
+                neumaier_merge(s1, c1, e, f);
+            }
+        }
+        if (lane == 0) {
+            const double n0 = p.counts[2 * inst], n1 = p.counts[2 * inst + 1];
+            const double lp = n0 > 0 ? (s0 + c0) / n0 : 0.0;
+            const double lb = n1 > 0 ? (s1 + c1) / n1 : 0.0;
+            p.loss[3 * inst] = p.alpha * lp + lb;
+            p.loss[3 * inst + 1] = lp;
+            p.loss[3 * inst + 2] = lb;
+        }
+    }
+}
+
+cudaError_t launch_batch_reduce(const BatchReduceParams& p, cudaStream_t s) {
+    int64_t bx = (p.P + RED_LANES - 1) / RED_LANES;
+    batch_reduce_kernel<<<dim3((unsigned)bx, (unsigned)p.n_inst), dim3(RED_LANES, RED_WARPS), 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace hrkan

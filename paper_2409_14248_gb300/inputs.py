@@ -172,8 +172,11 @@ def make(w: Workload | str, n_int=None, n_bnd=None, n_ic=None, n_bc=None):
     return dict(x_int=f32(x_int), x_bnd=f32(x_bnd), g_bnd=f32(g_bnd), W=W)
 
 
-def make_batched(w: Workload | str, instances=None, count_lo=None, count_hi=None):
+def make_batched(w: Workload | str, instances=None, count_lo=None, count_hi=None, counts=None, bnd_counts=None):
     """Ragged multi-instance Poisson workload.
+
+    counts / bnd_counts: explicit per-instance interior / boundary counts
+    (else interior counts are drawn uniformly and boundary = interior // 8).
 
     Returns dict with per-instance (a, b) [inst, 2] float64, interior and
     boundary offsets (int32, [inst+1]), concatenated x_int [2, sum N_int],
@@ -185,11 +188,15 @@ def make_batched(w: Workload | str, instances=None, count_lo=None, count_hi=None
     lo_c = w.extra.get("count_lo", 2048) if count_lo is None else count_lo
     hi_c = w.extra.get("count_hi", 32768) if count_hi is None else count_hi
     rng = np.random.default_rng(w.seed)
+    if counts is not None:
+        inst = len(counts)
     ab = rng.integers(1, 5, size=(inst, 2)).astype(np.float64)
-    counts = rng.integers(lo_c, hi_c + 1, size=inst)
+    drawn = rng.integers(lo_c, hi_c + 1, size=inst)
+    counts = drawn if counts is None else np.asarray(counts)
+    bnd_counts = [int(c) // 8 for c in counts] if bnd_counts is None else list(bnd_counts)
     xi, xb, gb = [], [], []
-    for c in counts:
-        a_, b_, g_ = _poisson_points(rng, int(c), int(c) // 8, w.lo, w.hi)
+    for c, cb in zip(counts, bnd_counts):
+        a_, b_, g_ = _poisson_points(rng, int(c), int(cb), w.lo, w.hi)
         xi.append(a_); xb.append(b_); gb.append(g_)
     off_i = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
     off_b = np.concatenate([[0], np.cumsum([x.shape[1] for x in xb])]).astype(np.int32)
