@@ -1,6 +1,9 @@
 // Instantiates the fused narrow-network kernels of one shape and a launcher.
 #pragma once
 
+#include <mutex>
+#include <unordered_set>
+
 #include "internal.h"
 #include "narrow.cuh"
 
@@ -11,14 +14,16 @@ namespace hrkan {
 // no attribute calls.
 template <class KernelT>
 static cudaError_t allow_big_smem(KernelT kern) {
-    static cudaError_t once = [&]() {
-        int dev = 0, optin = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-        return e;
-    }();
-    return once;
+    static std::mutex mu;
+    static std::unordered_set<const void*> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(reinterpret_cast<const void*>(kern))) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) done.insert(reinterpret_cast<const void*>(kern));
+    return e;
 }
 
 template <class Net, class KernelT>
