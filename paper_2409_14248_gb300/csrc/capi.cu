@@ -384,7 +384,7 @@ int hrkan_forward_jets(hrkan_t h, const float* W, const float* x, int64_t N, uns
         ProfScope ps(h, HRKAN_KERNEL_FORWARD, (cudaStream_t)stream);
         e = narrow_launch(h->net_id, MODE_FWD, jet_mask, p, &grid, 1 << 30, true, (cudaStream_t)stream);
     }
-    if (e == cudaErrorInvalidValue) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no forward kernel", jet_mask);
+    if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no forward kernel", jet_mask);
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     return HRKAN_OK;
 }
@@ -466,7 +466,7 @@ int hrkan_backward(hrkan_t h, const float* W, const float* x, int64_t N, unsigne
         ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
         e = narrow_launch(h->net_id, MODE_BWD, jet_mask, p, &grid, h->max_grid, true, s);
     }
-    if (e == cudaErrorInvalidValue) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no backward kernel", jet_mask);
+    if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no backward kernel", jet_mask);
     if (e != cudaSuccess) return cuda_fail(e, "backward launch");
     ReduceParams q{};
     q.partial = h->partial;
@@ -581,7 +581,7 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
         ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
         e = narrow_launch(h->net_id, MODE_TRAIN, mask, p, &grid, h->max_grid, true, s);
     }
-    if (e == cudaErrorInvalidValue) return fail(HRKAN_EUNSUPPORTED, "no fused training kernel");
+    if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "no fused training kernel");
     if (e != cudaSuccess) return cuda_fail(e, "train launch");
     ReduceParams q{};
     q.partial = h->partial;
@@ -663,7 +663,7 @@ int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, con
             ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
             e = narrow_batch_launch(h->net_id, MODE_TRAIN, mask, p, &grid, 1 << 30, true, s);
         }
-        if (e == cudaErrorInvalidValue) return fail(HRKAN_EUNSUPPORTED, "no multi-instance training kernel");
+        if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "no multi-instance training kernel");
         if (e != cudaSuccess) return cuda_fail(e, "multi-instance train launch");
     }
     BatchReduceParams q{};
@@ -716,7 +716,7 @@ int hrkan_forward_jets_batched(hrkan_t h, const float* W, const float* x, const 
         ProfScope ps(h, HRKAN_KERNEL_FORWARD, (cudaStream_t)stream);
         e = narrow_batch_launch(h->net_id, MODE_FWD, jet_mask, p, &grid, 1 << 30, true, (cudaStream_t)stream);
     }
-    if (e == cudaErrorInvalidValue) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no forward kernel", jet_mask);
+    if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no forward kernel", jet_mask);
     if (e != cudaSuccess) return cuda_fail(e, "multi-instance forward launch");
     return HRKAN_OK;
 }

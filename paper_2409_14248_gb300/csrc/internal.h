@@ -18,7 +18,7 @@ int narrow_net_id(int n_layers, int wh);
 // Launch mode (MODE_FWD / MODE_BWD / MODE_TRAIN) for mask on `*grid` blocks.
 // If *grid <= 0 it is replaced by the persistent grid (SMs x resident blocks,
 // capped at max_grid and at the number of tiles) and nothing is launched when
-// `launch` is false.  Returns cudaErrorInvalidValue for a mask with no kernel.
+// `launch` is false.  Returns cudaErrorNotSupported for a mask with no kernel.
 cudaError_t narrow_launch(int net_id, int mode, unsigned mask, const NarrowParams& p, int* grid,
                           int max_grid, bool launch, cudaStream_t s);
 

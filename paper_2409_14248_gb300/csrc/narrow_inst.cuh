@@ -2,27 +2,26 @@
 #pragma once
 
 #include <mutex>
-#include <unordered_set>
+#include <unordered_map>
 
 #include "internal.h"
 #include "narrow.cuh"
 
 namespace hrkan {
 
-// Opt a kernel into the device's full dynamic shared memory once per process
-// (per kernel), so later launches, including ones under stream capture, make
-// no attribute calls.
+// Raise a kernel's dynamic shared-memory limit to what a launch needs; the
+// limit only grows, so repeated launches (including ones under stream
+// capture) make no attribute calls.
 template <class KernelT>
-static cudaError_t allow_big_smem(KernelT kern) {
+static cudaError_t allow_big_smem(KernelT kern, size_t bytes) {
     static std::mutex mu;
-    static std::unordered_set<const void*> done;
+    static std::unordered_map<const void*, size_t> set_to;
     std::lock_guard<std::mutex> lk(mu);
-    if (done.count(reinterpret_cast<const void*>(kern))) return cudaSuccess;
-    int dev = 0, optin = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e == cudaSuccess) done.insert(reinterpret_cast<const void*>(kern));
+    size_t& cur = set_to[reinterpret_cast<const void*>(kern)];
+    if (bytes <= cur) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e == cudaSuccess) cur = bytes;
+    else cudaGetLastError();
     return e;
 }
 
@@ -30,7 +29,7 @@ template <class Net, class KernelT>
 static cudaError_t narrow_go(KernelT kern, size_t smem, int64_t tiles, const NarrowParams& p, int* grid,
                              int max_grid, bool launch, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
-    if (smem > 48 * 1024 && (e = allow_big_smem(kern)) != cudaSuccess) return e;
+    if (smem > 48 * 1024 && (e = allow_big_smem(kern, smem)) != cudaSuccess) return e;
     if (*grid <= 0) {
         int dev = 0, nsm = 0, occ = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -72,7 +71,7 @@ static cudaError_t narrow_launch_net(int mode, unsigned mask, const NarrowParams
             case 0x1Fu: return narrow_go<Net>(narrow_grad_kernel<Net, 0x1Fu, MODE_TRAIN>, (1 + Net::COPIES) * sf, t0 + t1, p, grid, max_grid, launch, s);
         }
     }
-    return cudaErrorInvalidValue;
+    return cudaErrorNotSupported;
 }
 
 template <class Net>
@@ -82,7 +81,7 @@ static cudaError_t narrow_batch_launch_net(int mode, unsigned mask, const BatchP
     const int64_t items = p.n_items;
     auto go = [&](auto kern, size_t smem) -> cudaError_t {
         cudaError_t e = cudaSuccess;
-        if (smem > 48 * 1024 && (e = allow_big_smem(kern)) != cudaSuccess) return e;
+        if (smem > 48 * 1024 && (e = allow_big_smem(kern, smem)) != cudaSuccess) return e;
         if (*grid <= 0) {
             int dev = 0, nsm = 0, occ = 0;
             if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -110,7 +109,7 @@ static cudaError_t narrow_batch_launch_net(int mode, unsigned mask, const BatchP
             case 0x1Fu: return go(narrow_batch_kernel<Net, 0x1Fu>, (1 + Net::COPIES) * sf);
         }
     }
-    return cudaErrorInvalidValue;
+    return cudaErrorNotSupported;
 }
 
 }  // namespace hrkan

@@ -25,7 +25,7 @@ cudaError_t narrow_launch(int net_id, int mode, unsigned mask, const NarrowParam
         case 1: return narrow_launch_n3w10(mode, mask, p, grid, max_grid, launch, s);
         case 2: return narrow_launch_n3w16(mode, mask, p, grid, max_grid, launch, s);
     }
-    return cudaErrorInvalidValue;
+    return cudaErrorNotSupported;
 }
 
 cudaError_t narrow_batch_launch(int net_id, int mode, unsigned mask, const BatchParams& p, int* grid, int max_grid,
@@ -35,7 +35,7 @@ cudaError_t narrow_batch_launch(int net_id, int mode, unsigned mask, const Batch
         case 1: return narrow_launch_n3w10_batch(mode, mask, p, grid, max_grid, launch, s);
         case 2: return narrow_launch_n3w16_batch(mode, mask, p, grid, max_grid, launch, s);
     }
-    return cudaErrorInvalidValue;
+    return cudaErrorNotSupported;
 }
 
 }  // namespace hrkan

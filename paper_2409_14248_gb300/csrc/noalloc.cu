@@ -104,7 +104,7 @@ extern "C" int hrkan_backward_noalloc(const hrkan_cfg* cfg, const float* W, cons
     const int max_rows = int(kScratchFloats / P);
     int grid = 0;
     cudaError_t e = narrow_launch(net_id, MODE_BWD, jet_mask, p, &grid, max_rows, true, s);
-    if (e == cudaErrorInvalidValue)
+    if (e == cudaErrorNotSupported)
         return set_last_error(HRKAN_EUNSUPPORTED, "hrkan_backward_noalloc: jet mask has no backward kernel");
     if (e != cudaSuccess) {
         snprintf(buf, sizeof buf, "hrkan_backward_noalloc: launch failed: %s", cudaGetErrorString(e));
