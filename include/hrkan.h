@@ -66,6 +66,8 @@ enum hrkan_prec { HRKAN_FP32 = 0, HRKAN_BF16 = 1, HRKAN_TF32 = 2 };
 enum hrkan_pde { HRKAN_POISSON = 0, HRKAN_BURGERS = 1 };
 
 #define HRKAN_MAX_WIDTHS 8
+/* Use the layer-wise kernels even where a fused whole-network kernel exists. */
+#define HRKAN_FLAG_LAYERWISE 1
 
 typedef struct hrkan_cfg {
     int n_widths;                    /* L + 1, in [2, HRKAN_MAX_WIDTHS] */
@@ -76,8 +78,10 @@ typedef struct hrkan_cfg {
     int prec;                        /* enum hrkan_prec: arithmetic of the jet contraction */
     double grid_lo, grid_hi;         /* grid_lo < grid_hi */
     int n_instances;                 /* independent networks sharing the shape (>= 1) */
-    int reserved;
-    size_t hbm_budget_bytes;         /* advisory cap for stored layer jets (tape); 0 = none */
+    int flags;                       /* HRKAN_FLAG_*; 0 = defaults */
+    size_t hbm_budget_bytes;         /* layer-wise path: the training step keeps every layer's input
+                                        jets (the tape) while they fit in this many bytes, else it
+                                        recomputes them in the backward; 0 = no cap */
 } hrkan_cfg;
 
 /*
@@ -117,8 +121,9 @@ const char* hrkan_last_error(void);
 
 /*
  * Floats of tape that hrkan_forward_jets may fill for N points under mask so
- * that hrkan_backward can skip recomputing the forward (0: the shape always
- * recomputes, pass NULL).
+ * that hrkan_backward can skip recomputing the forward: the input jets of
+ * every layer but the first, [J][w_l][N] per layer.  0: the handle uses a
+ * fused kernel, which recomputes inside the backward (pass NULL).
  */
 int64_t hrkan_tape_floats(hrkan_t h, int64_t N, unsigned jet_mask);
 

@@ -39,7 +39,7 @@ class HRKANError(RuntimeError):
 class hrkan_cfg(ctypes.Structure):
     _fields_ = [("n_widths", ctypes.c_int), ("widths", ctypes.c_int * HRKAN_MAX_WIDTHS), ("G", ctypes.c_int),
                 ("k", ctypes.c_int), ("m", ctypes.c_int), ("prec", ctypes.c_int), ("grid_lo", ctypes.c_double),
-                ("grid_hi", ctypes.c_double), ("n_instances", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("grid_hi", ctypes.c_double), ("n_instances", ctypes.c_int), ("flags", ctypes.c_int),
                 ("hbm_budget_bytes", ctypes.c_size_t)]
 
 
@@ -123,14 +123,17 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def make_cfg(widths, G, k=3, m=4, lo=-1.0, hi=1.0, prec=HRKAN_FP32, n_instances=1, hbm_budget_bytes=0):
+HRKAN_FLAG_LAYERWISE = 1
+
+
+def make_cfg(widths, G, k=3, m=4, lo=-1.0, hi=1.0, prec=HRKAN_FP32, n_instances=1, hbm_budget_bytes=0, flags=0):
     c = hrkan_cfg()
     c.n_widths = len(widths)
     for i, w in enumerate(widths):
         c.widths[i] = int(w)
     c.G, c.k, c.m, c.prec = int(G), int(k), int(m), int(prec)
     c.grid_lo, c.grid_hi = float(lo), float(hi)
-    c.n_instances, c.hbm_budget_bytes = int(n_instances), int(hbm_budget_bytes)
+    c.n_instances, c.hbm_budget_bytes, c.flags = int(n_instances), int(hbm_budget_bytes), int(flags)
     return c
 
 

@@ -12,6 +12,7 @@
 #include "../../include/hrkan.h"
 #include "internal.h"
 #include "narrow.cuh"
+#include "wide.cuh"
 
 using namespace hrkan;
 
@@ -46,6 +47,10 @@ struct hrkan_ctx {
         double* loss_partial = nullptr;
     } train_batch, fwd_batch;
     int batch_items_points = 1024;  // points per work item
+    // layer-wise path (shapes without a fused kernel)
+    std::vector<int64_t> layer_off;  // first weight of each layer
+    int wide_gp = 0;                 // point groups of the weight-gradient kernels
+    std::vector<std::pair<float*, size_t>> ws;   // growing scratch slots (floats)
     // kernel timing
     bool prof = false;
     struct Ev { cudaEvent_t a, b; int cls; };
@@ -267,6 +272,224 @@ int build_batch(hrkan_t h, hrkan_ctx::Batch& b, int n_inst, const pinn_problem* 
 
 }  // namespace
 
+namespace {
+
+// Scratch slot `slot` with at least `floats` floats (grows; never shrinks).
+float* ws_get(hrkan_t h, int slot, size_t floats, int* rc) {
+    if (int(h->ws.size()) <= slot) h->ws.resize(slot + 1, {nullptr, 0});
+    auto& w = h->ws[slot];
+    if (w.second < floats) {
+        cudaFree(w.first);
+        w.first = nullptr;
+        w.second = 0;
+        cudaError_t e = cudaMalloc(&w.first, std::max<size_t>(floats, 1) * sizeof(float));
+        if (e != cudaSuccess) {
+            *rc = fail(HRKAN_ENOMEM, "cudaMalloc of %zu floats of scratch: %s", floats, cudaGetErrorString(e));
+            return nullptr;
+        }
+        w.second = floats;
+    }
+    return w.first;
+}
+
+int jets_of(unsigned mask) { return __builtin_popcount(mask & 0x1Fu); }
+
+int max_hidden(hrkan_t h) {
+    int m = 1;
+    for (int l = 1; l < h->L; ++l) m = std::max(m, h->cfg.widths[l]);
+    return m;
+}
+
+// Offset (floats) of layer l's input jets (l >= 1) inside a tape for N points.
+int64_t tape_offset(hrkan_t h, int l, int64_t N, int J) {
+    int64_t off = 0;
+    for (int t = 1; t < l; ++t) off += int64_t(J) * h->cfg.widths[t] * N;
+    return off;
+}
+
+int64_t tape_total(hrkan_t h, int64_t N, int J) { return tape_offset(h, h->L, N, J); }
+
+WideLayer wide_layer(hrkan_t h, const float* W, int l, int64_t N) {
+    WideLayer p{};
+    p.W = W + h->layer_off[l];
+    p.I = h->cfg.widths[l];
+    p.O = h->cfg.widths[l + 1];
+    p.N = N;
+    p.g = h->grid;
+    return p;
+}
+
+// Forward of one point set through every layer.  Layer inputs go to `tape`
+// when given (layer l at tape_offset(l)), else to two ping-pong scratch slots
+// (zslot, zslot + 1).  The output jets go to `out` [J][N].
+int wide_forward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsigned mask, float* out, float* tape,
+                     int zslot, cudaStream_t s) {
+    if (N == 0) return HRKAN_OK;
+    const int J = jets_of(mask), L = h->L;
+    int rc = HRKAN_OK;
+    const float* in = x;
+    for (int l = 0; l < L; ++l) {
+        WideLayer p = wide_layer(h, W, l, N);
+        p.z = in;
+        float* y;
+        if (l == L - 1) y = out;
+        else if (tape) y = tape + tape_offset(h, l + 1, N, J);
+        else if (!(y = ws_get(h, zslot + (l % 2), size_t(J) * p.O * N, &rc))) return rc;
+        p.y = y;
+        cudaError_t e = wide_forward_layer(p, mask, l == 0, s);
+        if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no layer kernel", mask);
+        if (e != cudaSuccess) return cuda_fail(e, "layer forward launch");
+        in = y;
+    }
+    return HRKAN_OK;
+}
+
+// Backward of one point set: weight-gradient partial rows [row0, row0 + GP)
+// of h->partial and, for every layer but the first, the input adjoint.  Layer
+// inputs come from `tape`, or are recomputed from x when tape is null.
+int wide_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsigned mask, const float* tape,
+                      const float* gy_out, int row0, cudaStream_t s) {
+    const int J = jets_of(mask), L = h->L;
+    int rc = HRKAN_OK;
+    const float* gy = gy_out;
+    for (int l = L - 1; l >= 0; --l) {
+        const float* zl = x;
+        if (l > 0) {
+            if (tape) {
+                zl = tape + tape_offset(h, l, N, J);
+            } else {
+                // recompute layer l's input jets from the coordinates
+                const float* in = x;
+                for (int t = 0; t < l; ++t) {
+                    WideLayer p = wide_layer(h, W, t, N);
+                    p.z = in;
+                    float* y = ws_get(h, 0 + (t % 2), size_t(J) * p.O * N, &rc);
+                    if (!y) return rc;
+                    p.y = y;
+                    if (N > 0) {
+                        cudaError_t e = wide_forward_layer(p, mask, t == 0, s);
+                        if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x", mask);
+                        if (e != cudaSuccess) return cuda_fail(e, "layer recompute launch");
+                    }
+                    in = y;
+                }
+                zl = in;
+            }
+        }
+        WideDw d{};
+        d.z = zl;
+        d.gy = gy;
+        d.I = h->cfg.widths[l];
+        d.O = h->cfg.widths[l + 1];
+        d.N = N;
+        d.partial = h->partial;
+        d.P = h->P;
+        d.col0 = h->layer_off[l];
+        d.row0 = row0;
+        d.GP = h->wide_gp;
+        d.g = h->grid;
+        cudaError_t e;
+        {
+            ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
+            e = wide_dw_layer(d, mask, l == 0, s);
+        }
+        if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no layer kernel", mask);
+        if (e != cudaSuccess) return cuda_fail(e, "weight-gradient launch");
+        if (l > 0) {
+            WideLayer a = wide_layer(h, W, l, N);
+            a.z = zl;
+            a.gy = gy;
+            float* gz = ws_get(h, 2 + (l % 2), size_t(J) * a.I * N, &rc);
+            if (!gz) return rc;
+            a.gz = gz;
+            e = wide_adjoint_layer(a, mask, s);
+            if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+            gy = gz;
+        }
+    }
+    return HRKAN_OK;
+}
+
+// Training step of the layer-wise path: forward (interior and boundary),
+// residual, backward of both sets into disjoint partial rows, then the same
+// fixed-order reduction + Adam as the fused path.
+int wide_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float* x_int, int64_t N_int,
+                    const float* x_bnd, const float* g_bnd, int64_t N_bnd, double lr, double b1, double b2,
+                    double eps, int t, double* loss, float* dW, cudaStream_t s) {
+    const unsigned mask = prob->kind == HRKAN_POISSON ? 0x1Fu : 0x0Fu;
+    const int J = jets_of(mask);
+    int rc = HRKAN_OK;
+    float* jets = ws_get(h, 4, size_t(J) * std::max<int64_t>(N_int, 1), &rc);
+    float* dli = jets ? ws_get(h, 5, size_t(J) * std::max<int64_t>(N_int, 1), &rc) : nullptr;
+    float* ub = dli ? ws_get(h, 6, size_t(std::max<int64_t>(N_bnd, 1)), &rc) : nullptr;
+    float* dlb = ub ? ws_get(h, 7, size_t(std::max<int64_t>(N_bnd, 1)), &rc) : nullptr;
+    if (!dlb) return rc;
+    // keep the interior tape while it fits the budget, else recompute in the backward
+    const int64_t tape_i = tape_total(h, N_int, J), tape_b = tape_total(h, N_bnd, 1);
+    const size_t budget = h->cfg.hbm_budget_bytes;
+    const bool store = budget == 0 || size_t(tape_i + tape_b) * sizeof(float) <= budget;
+    float* ti = nullptr;
+    float* tb = nullptr;
+    if (store) {
+        if (tape_i > 0 && !(ti = ws_get(h, 8, size_t(tape_i), &rc))) return rc;
+        if (tape_b > 0 && !(tb = ws_get(h, 9, size_t(tape_b), &rc))) return rc;
+    }
+    {
+        ProfScope ps(h, HRKAN_KERNEL_FORWARD, s);
+        if ((rc = wide_forward_set(h, W, x_int, N_int, mask, jets, ti, 0, s))) return rc;
+        if ((rc = wide_forward_set(h, W, x_bnd, N_bnd, 0x1u, ub, tb, 0, s))) return rc;
+    }
+    ResidualParams r{};
+    r.pde = make_pde(prob);
+    r.mask = mask;
+    r.x = x_int;
+    r.jets = jets;
+    r.N = N_int;
+    r.dL = dli;
+    r.u_bnd = ub;
+    r.g_bnd = g_bnd;
+    r.Nb = N_bnd;
+    r.dLb = dlb;
+    r.scale0 = N_int > 0 ? float(2.0 * prob->alpha / double(N_int)) : 0.0f;
+    r.scale1 = N_bnd > 0 ? float(2.0 / double(N_bnd)) : 0.0f;
+    r.loss_partial = h->loss_partial;
+    r.t_counter = t == 0 ? h->t_counter : nullptr;
+    int64_t rg = (std::max(N_int, N_bnd) + 255) / 256;
+    rg = std::min<int64_t>(std::max<int64_t>(rg, 1), h->max_grid_l);
+    {
+        ProfScope ps(h, HRKAN_KERNEL_RESIDUAL, s);
+        HR_CUDA(launch_residual(r, int(rg), s), "residual launch");
+    }
+    if ((rc = wide_backward_set(h, W, x_int, N_int, mask, ti, dli, 0, s))) return rc;
+    if ((rc = wide_backward_set(h, W, x_bnd, N_bnd, 0x1u, tb, dlb, h->wide_gp, s))) return rc;
+    ReduceParams q{};
+    q.partial = h->partial;
+    q.G = 2 * h->wide_gp;
+    q.P = h->P;
+    q.dW = dW;
+    q.do_adam = 1;
+    q.W = W;
+    q.m1 = h->m1;
+    q.m2 = h->m2;
+    q.lr = lr; q.b1 = b1; q.b2 = b2; q.eps = eps;
+    q.c1 = 1.0 - std::pow(b1, t > 0 ? t : 1);
+    q.c2 = 1.0 - std::pow(b2, t > 0 ? t : 1);
+    q.t_counter = t == 0 ? h->t_counter : nullptr;
+    q.loss_partial = h->loss_partial;
+    q.Gl = int(rg);
+    q.loss = loss;
+    q.alpha = prob->alpha;
+    q.n0 = N_int;
+    q.n1 = N_bnd;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_REDUCE, s);
+        HR_CUDA(launch_reduce(q, s), "reduce/Adam launch");
+    }
+    return HRKAN_OK;
+}
+
+}  // namespace
+
 namespace hrkan {
 // Records the message hrkan_last_error() returns (for entry points in other files).
 int set_last_error(int code, const char* msg) {
@@ -294,8 +517,9 @@ int hrkan_init(hrkan_t* out, const hrkan_cfg* cfg) {
     bool uniform_hidden = true;
     for (int l = 1; l < L; ++l) uniform_hidden &= (cfg->widths[l] == cfg->widths[1]);
     if (uniform_hidden) net_id = narrow_net_id(L, cfg->widths[1]);
-    if (net_id < 0)
-        return fail(HRKAN_EUNSUPPORTED, "no kernels for this network shape (L=%d, hidden width %d)", L, cfg->widths[1]);
+    if (cfg->flags & HRKAN_FLAG_LAYERWISE) net_id = -1;
+    if (net_id < 0 && cfg->n_instances != 1)
+        return fail(HRKAN_EUNSUPPORTED, "several instances need a fused shape ([2,W,1] or [2,W,W,1], W in 5,10,16)");
     if (cfg->prec != HRKAN_FP32) return fail(HRKAN_EUNSUPPORTED, "precision %d has no kernels for this shape", cfg->prec);
 
     hrkan_ctx* h = new (std::nothrow) hrkan_ctx();
@@ -317,7 +541,11 @@ int hrkan_init(hrkan_t* out, const hrkan_cfg* cfg) {
         delete h;
         return cuda_fail(e, "cudaDeviceGetAttribute");
     }
-    h->max_grid = h->nsm * 8;
+    h->layer_off.assign(L + 1, 0);
+    for (int l = 0; l < L; ++l)
+        h->layer_off[l + 1] = h->layer_off[l] + int64_t(cfg->widths[l]) * cfg->widths[l + 1] * h->n;
+    h->wide_gp = std::max(1, h->nsm * 2 / 8);
+    h->max_grid = net_id >= 0 ? h->nsm * 8 : 2 * h->wide_gp;
     h->max_grid_l = h->nsm * 8;
     size_t bytes_partial = size_t(h->max_grid) * size_t(h->P) * sizeof(float);
     if ((e = cudaMalloc(&h->partial, bytes_partial)) != cudaSuccess ||
@@ -354,6 +582,7 @@ void hrkan_destroy(hrkan_t h) {
         cudaFree(b->items); cudaFree(b->inst); cudaFree(b->item_off); cudaFree(b->counts);
         cudaFree(b->partial); cudaFree(b->loss_partial);
     }
+    for (auto& w : h->ws) cudaFree(w.first);
     for (auto& ev : h->pending) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
     for (auto& ev : h->pool) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
     if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
@@ -361,8 +590,8 @@ void hrkan_destroy(hrkan_t h) {
 }
 
 int64_t hrkan_tape_floats(hrkan_t h, int64_t N, unsigned jet_mask) {
-    (void)h; (void)N; (void)jet_mask;
-    return 0;   // the fused shapes recompute the forward inside the backward
+    if (!h || N <= 0 || !valid_mask(jet_mask) || h->net_id >= 0) return 0;   // fused shapes recompute
+    return tape_total(h, N, jets_of(jet_mask));
 }
 
 int hrkan_forward_jets(hrkan_t h, const float* W, const float* x, int64_t N, unsigned jet_mask, float* jets,
@@ -374,6 +603,10 @@ int hrkan_forward_jets(hrkan_t h, const float* W, const float* x, int64_t N, uns
     if (N == 0) return HRKAN_OK;
     if (!W || !x || !jets) return fail(HRKAN_EINVAL, "NULL device pointer");
     if (int rc = use_device(h)) return rc;
+    if (h->net_id < 0) {
+        ProfScope ps(h, HRKAN_KERNEL_FORWARD, (cudaStream_t)stream);
+        return wide_forward_set(h, W, x, N, jet_mask, jets, tape, 0, (cudaStream_t)stream);
+    }
     NarrowParams p = base_params(h, W);
     p.x0 = x;
     p.n0 = N;
@@ -455,14 +688,17 @@ int hrkan_backward(hrkan_t h, const float* W, const float* x, int64_t N, unsigne
         if (!accumulate) HR_CUDA(cudaMemsetAsync(dW, 0, size_t(h->P) * sizeof(float), s), "cudaMemsetAsync");
         return HRKAN_OK;
     }
-    NarrowParams p = base_params(h, W);
-    p.x0 = x;
-    p.n0 = N;
-    p.dL = dL_djets;
-    p.partial = h->partial;
     int grid = 0;
-    cudaError_t e;
-    {
+    cudaError_t e = cudaSuccess;
+    if (h->net_id < 0) {
+        if (int rc = wide_backward_set(h, W, x, N, jet_mask, tape, dL_djets, 0, s)) return rc;
+        grid = h->wide_gp;
+    } else {
+        NarrowParams p = base_params(h, W);
+        p.x0 = x;
+        p.n0 = N;
+        p.dL = dL_djets;
+        p.partial = h->partial;
         ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
         e = narrow_launch(h->net_id, MODE_BWD, jet_mask, p, &grid, h->max_grid, true, s);
     }
@@ -563,6 +799,8 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
     if (int rc = use_device(h)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned mask = prob->kind == HRKAN_POISSON ? 0x1Fu : 0x0Fu;
+    if (h->net_id < 0) return wide_train_step(h, prob, W, x_int, N_int, x_bnd, g_bnd, N_bnd, lr, b1, b2, eps, t, loss,
+                                              dW, s);
     NarrowParams p = base_params(h, W);
     p.x0 = x_int;
     p.n0 = N_int;

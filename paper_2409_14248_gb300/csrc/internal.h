@@ -80,6 +80,7 @@ struct ResidualParams {
     float* dLb;            // [Nb] or null
     float scale0, scale1;
     double* loss_partial;  // [grid][2]
+    int* t_counter;        // optional device step counter: t_counter[1] = t_counter[0] + 1
 };
 // Enqueue the residual kernel on `grid` blocks (grid must be <= the rows of loss_partial).
 cudaError_t launch_residual(const ResidualParams& p, int grid, cudaStream_t s);

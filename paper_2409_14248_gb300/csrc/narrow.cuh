@@ -33,6 +33,8 @@ struct NarrowNet {
     // Hidden activations of a PINN often sit in one or two grid cells, so the
     // lanes of a warp would otherwise add into the same address at once.
     static constexpr int COPIES = 4;
+    // resident blocks per SM the register budget is sized for
+    static constexpr int MINB = WH_ >= 16 ? 3 : 4;
     static_assert(NL == 2 || NL == 3, "narrow nets have one or two hidden layers");
 
     // shared-memory layout in floats (n = number of bases)
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(NARROW_BLOCK) narrow_fwd_kernel(NarrowParams p
 // MODE_BWD: one point set, gu read from dL.  MODE_TRAIN: interior (MASK)
 // then boundary (value only) tiles, gu from the residual.
 template <class Net, unsigned MASK, int MODE>
-__global__ void __launch_bounds__(NARROW_BLOCK, 4) narrow_grad_kernel(NarrowParams p) {
+__global__ void __launch_bounds__(NARROW_BLOCK, Net::MINB) narrow_grad_kernel(NarrowParams p) {
     extern __shared__ __align__(16) float smem[];
     if (MODE == MODE_TRAIN && p.t_counter && blockIdx.x == 0 && threadIdx.x == 0)
         p.t_counter[1] = p.t_counter[0] + 1;
@@ -480,7 +482,7 @@ struct BatchParams {
 };
 
 template <class Net, unsigned MASK>
-__global__ void __launch_bounds__(NARROW_BLOCK, 4) narrow_batch_kernel(BatchParams p) {
+__global__ void __launch_bounds__(NARROW_BLOCK, Net::MINB) narrow_batch_kernel(BatchParams p) {
     extern __shared__ __align__(16) float smem[];
     if (p.t_counter && blockIdx.x == 0 && threadIdx.x == 0) p.t_counter[1] = p.t_counter[0] + 1;
     const int n = p.grid.n;

@@ -1,0 +1,42 @@
+// Launch interface of the layer-wise kernels for wide networks (wide.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hr_device.cuh"
+
+namespace hrkan {
+
+// One layer: I inputs, O outputs, weights W [O][I][n].
+struct WideLayer {
+    const float* W;
+    int I, O;
+    const float* z;    // input jets [J][I][N] (first layer: coordinates [2][N])
+    float* y;          // forward: output jets [J][O][N]
+    const float* gy;   // adjoint: dL/d(output jets) [J][O][N]
+    float* gz;         // adjoint: dL/d(input jets) [J][I][N]
+    int64_t N;
+    Grid g;
+};
+
+// Weight gradient of one layer into partial rows [row0, row0 + GP) of a
+// [rows][P] buffer, columns [col0, col0 + O*I*n).
+struct WideDw {
+    const float* z;    // input jets [J][I][N] (first layer: coordinates)
+    const float* gy;   // [J][O][N]
+    int I, O;
+    int64_t N;
+    float* partial;
+    int64_t P;
+    int64_t col0;
+    int row0;
+    int GP;            // point groups = partial rows written
+    Grid g;
+};
+
+cudaError_t wide_forward_layer(const WideLayer& p, unsigned mask, bool first, cudaStream_t s);
+cudaError_t wide_adjoint_layer(const WideLayer& p, unsigned mask, cudaStream_t s);
+cudaError_t wide_dw_layer(const WideDw& p, unsigned mask, bool first, cudaStream_t s);
+
+}  // namespace hrkan
