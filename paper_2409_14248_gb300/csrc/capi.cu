@@ -531,6 +531,7 @@ int hrkan_init(hrkan_t* out, const hrkan_cfg* cfg) {
     h->net_id = net_id;
     const double hh = (cfg->grid_hi - cfg->grid_lo) / cfg->G;
     h->grid.lo = float(cfg->grid_lo);
+    h->grid.h = float(hh);
     h->grid.inv_h = float(1.0 / hh);
     h->grid.inv_a = float(2.0 / ((cfg->k + 1) * hh));
     h->grid.n = h->n;

@@ -12,6 +12,7 @@ namespace hrkan {
 // Geometry of the uniform grid shared by every layer.
 struct Grid {
     float lo;      // grid_lo
+    float h;       // (grid_hi - grid_lo) / G
     float inv_h;   // G / (grid_hi - grid_lo)
     float inv_a;   // 1 / half-width of a support = 2 / ((k+1) h)
     int n;         // number of bases G + k
@@ -21,7 +22,9 @@ struct Grid {
 //
 // Basis i lives on [s_i, e_i] = [lo + (i-k)h, lo + (i+1)h].  With
 // t = (z - lo)/h and c = floor(t), the bases touching z are i = c + q,
-// q = 0..K.  Writing u = (z - mid_i)/a for the position inside the support
+// q = 0..K.  The offset inside the cell is taken from the knot,
+// f = (z - (lo + c h))/h, not as t - c: for |z| much smaller than the grid
+// range, t carries an absolute error of one ulp of t, far above the ulp of z.  Writing u = (z - mid_i)/a for the position inside the support
 // (a = (K+1)h/2 the half-width), Eq. 2 becomes v = (1 - u^2)^M because
 // c_m = a^{-2m}, and u = (2(t - c) + K - 1 - 2q)/(K + 1) for basis c + q.
 // With Q = 1 - u^2 the derivatives with respect to z are
@@ -49,7 +52,7 @@ struct Active {
         t = fminf(fmaxf(t, -1.0e9f), 1.0e9f);
         float fc = floorf(t);
         c = (int)fc;
-        float f = t - fc;
+        float f = (z - fmaf(fc, g.h, g.lo)) * g.inv_h;
         const float s = 2.0f / (K + 1);
 #pragma unroll
         for (int q = 0; q < K + 1; ++q) {

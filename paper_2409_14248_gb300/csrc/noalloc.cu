@@ -92,6 +92,7 @@ extern "C" int hrkan_backward_noalloc(const hrkan_cfg* cfg, const float* W, cons
     NarrowParams p{};
     p.W = W;
     p.grid.lo = float(cfg->grid_lo);
+    p.grid.h = float(hh);
     p.grid.inv_h = float(1.0 / hh);
     p.grid.inv_a = float(2.0 / ((cfg->k + 1) * hh));
     p.grid.n = cfg->G + cfg->k;

@@ -60,3 +60,21 @@ def oracle_step(w, W, x_int, x_bnd, g_bnd, lr, t=1, m1=None, m2=None, a=None, b=
 
 def random_weights(w, seed, sigma=0.5):
     return (sigma * np.random.default_rng(seed).standard_normal(w.n_params())).astype(np.float32)
+
+
+def fp32_floor(w, W, x, mask, seed=0):
+    """Per-jet-row relative change of the FP64 network output when every weight
+    is perturbed by one float32 rounding (relative noise 2^-24): the error floor
+    that any float32 evaluation of this network at these points sits on."""
+    W = np.asarray(W, dtype=np.float64)
+    noise = np.random.default_rng(seed).uniform(-1.0, 1.0, W.size) * 2.0 ** -24
+    base = oracle.forward(w.net, W, x, mask)
+    pert = oracle.forward(w.net, W * (1.0 + noise), x, mask)
+    return np.array([relerr(pert[r], base[r]) for r in range(base.shape[0])])
+
+
+def conditioned_tolerances(w, W, x, mask, scale=1.0, factor=8.0):
+    """The FP32 bar (1e-5 on u, 1e-4 on derivatives) or, where the network is too
+    ill-conditioned for float32 to reach it, `factor` times its float32 floor."""
+    base = np.array(row_tolerances(mask, scale))
+    return np.maximum(base, factor * fp32_floor(w, W, x, mask))

@@ -7,8 +7,8 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import (STRESS, TOL_D, TOL_U, layer_slices, oracle_step, problem_of, random_weights, relerr,
-                      row_tolerances)
+from gpu_util import (STRESS, TOL_D, TOL_U, conditioned_tolerances, fp32_floor, layer_slices, oracle_step,
+                      problem_of, random_weights, relerr)
 from paper_2409_14248_gb300 import build, capi, inputs
 
 pytestmark = pytest.mark.gpu
@@ -50,8 +50,8 @@ def test_wide_forward_matches_oracle(wname, mask):
             capi.hrkan_forward_jets(h, _dev(W), _dev(d["x_int"]), N, mask, jets)
             want = oracle.forward(w.net, W, d["x_int"], mask)
             got = jets.cpu().numpy()
-            for r, tol in enumerate(row_tolerances(mask, scale)):
-                assert relerr(got[r], want[r]) < tol, (r, relerr(got[r], want[r]))
+            for r, tol in enumerate(conditioned_tolerances(w, W, d["x_int"], mask, scale)):
+                assert relerr(got[r], want[r]) < tol, (r, relerr(got[r], want[r]), tol)
     finally:
         capi.hrkan_destroy(h)
 
@@ -72,12 +72,14 @@ def test_wide_backward_stored_and_recomputed_match_oracle(wname):
         tape = torch.zeros(capi.hrkan_tape_floats(h, N, mask), device="cuda")
         jets = torch.zeros((J, N), device="cuda")
         capi.hrkan_forward_jets(h, W, x, N, mask, jets, tape)
+        # gradients inherit the forward's float32 floor (largest over the jet rows)
+        tol = max(TOL_D, 8.0 * fp32_floor(w, d["W"], d["x_int"], mask).max())
         for tp in (tape, None):
             dW = torch.full((w.n_params(),), float("nan"), device="cuda")
             capi.hrkan_backward(h, W, x, N, mask, tp, _dev(g), dW)
             got = dW.cpu().numpy()
             for sl in layer_slices(w.widths, w.G):
-                assert relerr(got[sl], want[sl]) < TOL_D, relerr(got[sl], want[sl])
+                assert relerr(got[sl], want[sl]) < tol, (relerr(got[sl], want[sl]), tol)
     finally:
         capi.hrkan_destroy(h)
 
@@ -139,9 +141,10 @@ def test_wide_full_size_forward_sampled_against_oracle():
         capi.hrkan_forward_jets(h, _dev(d["W"]), _dev(d["x_int"]), N, 0x1F, jets)
         idx = np.random.default_rng(33).choice(N, 128, replace=False)
         idx[:2] = [0, N - 1]
-        want = oracle.forward(w.net, d["W"], d["x_int"][:, idx], 0x1F)
+        xs = d["x_int"][:, idx]
+        want = oracle.forward(w.net, d["W"], xs, 0x1F)
         got = jets.cpu().numpy()[:, idx]
-        for r, tol in enumerate(row_tolerances(0x1F)):
-            assert relerr(got[r], want[r]) < tol, (r, relerr(got[r], want[r]))
+        for r, tol in enumerate(conditioned_tolerances(w, d["W"], xs, 0x1F)):
+            assert relerr(got[r], want[r]) < tol, (r, relerr(got[r], want[r]), tol)
     finally:
         capi.hrkan_destroy(h)
