@@ -213,6 +213,7 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
  *   t          Adam step >= 1, or 0 for the device step counter (as in
  *              hrkan_train_step); the moments of instance i are its own.
  *   loss       device [I][3] float64 (L, mean r^2, mean (u-g)^2 per instance).
+ *   dW         NULL, or device [I][P] float32 receiving each instance's gradient.
  * The work list (items of hrkan_set_batch_items points each) is rebuilt and
  * uploaded only when the offsets or problems change (that call synchronises
  * the stream); calls with unchanged arguments only enqueue the two kernels, so
@@ -221,7 +222,7 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
 int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, const float* x_int,
                              const int64_t* off_int, const float* x_bnd, const float* g_bnd,
                              const int64_t* off_bnd, double lr, double b1, double b2, double eps, int t,
-                             double* loss, hrkan_stream_t stream);
+                             double* loss, float* dW, hrkan_stream_t stream);
 
 /* Output jets of every instance at its points (x [2][N], offsets host [I+1], jets [J][N]). */
 int hrkan_forward_jets_batched(hrkan_t h, const float* W, const float* x, const int64_t* offsets,

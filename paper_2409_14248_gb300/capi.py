@@ -83,7 +83,7 @@ def load_library(path: str = LIB_PATH):
         lib.hrkan_backward_noalloc.argtypes = [ctypes.POINTER(hrkan_cfg), _vp, _vp, _i64, _u32, _vp, _vp, _i32, _vp]
         _i64p = ctypes.POINTER(_i64)
         lib.hrkan_train_step_batched.argtypes = [_vp, ctypes.POINTER(pinn_problem), _vp, _vp, _i64p, _vp, _vp, _i64p,
-                                                 _d, _d, _d, _d, _i32, _vp, _vp]
+                                                 _d, _d, _d, _d, _i32, _vp, _vp, _vp]
         lib.hrkan_forward_jets_batched.argtypes = [_vp, _vp, _vp, _i64p, _u32, _vp, _vp]
         lib.hrkan_set_batch_items.argtypes = [_vp, _i32]
         lib.hrkan_profile_enable.argtypes = [_vp, _i32]
@@ -230,7 +230,7 @@ def _i64_array(a):
 
 
 def hrkan_train_step_batched(h, probs, W, x_int, off_int, x_bnd, g_bnd, off_bnd, lr, b1, b2, eps, t, loss,
-                             stream=None):
+                             dW=None, stream=None):
     """probs: sequence of pinn_problem (one per instance); offsets: host int arrays [I+1]."""
     import torch
     f = torch.float32
@@ -239,7 +239,7 @@ def hrkan_train_step_batched(h, probs, W, x_int, off_int, x_bnd, g_bnd, off_bnd,
     ob, obp = _i64_array(off_bnd)
     _check(load_library().hrkan_train_step_batched(h, arr, _ptr(W, f), _ptr(x_int, f), oip, _ptr(x_bnd, f),
                                                    _ptr(g_bnd, f), obp, float(lr), float(b1), float(b2), float(eps),
-                                                   int(t), _ptr(loss, torch.float64), _stream(stream)))
+                                                   int(t), _ptr(loss, torch.float64), _ptr(dW, f), _stream(stream)))
 
 
 def hrkan_forward_jets_batched(h, W, x, offsets, jet_mask, jets, stream=None):

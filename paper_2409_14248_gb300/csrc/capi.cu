@@ -857,7 +857,7 @@ int hrkan_set_batch_items(hrkan_t h, int points_per_item) {
 
 int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, const float* x_int,
                              const int64_t* off_int, const float* x_bnd, const float* g_bnd, const int64_t* off_bnd,
-                             double lr, double b1, double b2, double eps, int t, double* loss,
+                             double lr, double b1, double b2, double eps, int t, double* loss, float* dW,
                              hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
     const int n_inst = h->cfg.n_instances;
@@ -920,6 +920,7 @@ int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, con
     q.loss_partial = b.loss_partial;
     q.counts = b.counts;
     q.loss = loss;
+    q.dW = dW;
     q.alpha = probs[0].alpha;
     {
         ProfScope ps(h, HRKAN_KERNEL_REDUCE, s);

@@ -63,6 +63,7 @@ struct BatchReduceParams {
     const double* loss_partial;  // [n_items][2]
     const float* counts;         // [n_inst][2] interior / boundary point counts
     double* loss;                // [n_inst][3]
+    float* dW;                   // optional [n_inst][P]
     double alpha;
 };
 cudaError_t launch_batch_reduce(const BatchReduceParams& p, cudaStream_t s);

@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(RED_LANES * RED_WARPS) batch_reduce_kernel(Bat
 #pragma unroll
         for (int t = 0; t < RED_WARPS; ++t) gsum += part[t][lane];
         const int64_t i = int64_t(inst) * p.P + k;
+        if (p.dW) p.dW[i] = gsum;
         const double gd = gsum;
         const double m1 = fma(p.b1, p.m1[i], (1.0 - p.b1) * gd);
         const double m2 = fma(p.b2, p.m2[i], (1.0 - p.b2) * gd * gd);
