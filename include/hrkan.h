@@ -146,8 +146,9 @@ int hrkan_forward_jets(hrkan_t h, const float* W, const float* x, int64_t N, uns
  *   loss          [3] float64 device: L, mean r^2, mean (u-g)^2 (written).
  *   dL_djets_int  [J][N_int] (written; NULL to skip), dL_du_bnd [N_bnd]
  *                 (written; NULL to skip).
- * The loss is summed per point in float32, per block in float64, and across
- * blocks in float64 with compensated (Neumaier) summation in a fixed order.
+ * The loss is squared per point in float32, summed per block in float64, and
+ * across blocks by a fixed-order pairwise float64 tree (all terms are
+ * non-negative, so the relative error stays near log2(blocks) * 2^-53).
  */
 int pinn_residual_loss(hrkan_t h, const pinn_problem* prob, const float* x_int, int64_t N_int,
                        unsigned jet_mask, const float* jets_int, const float* u_bnd,

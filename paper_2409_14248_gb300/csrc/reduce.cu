@@ -3,8 +3,8 @@
 // reduce_kernel sums per-block weight-gradient partials [G][P] in a fixed
 // order (so the result does not depend on scheduling), optionally writes the
 // gradient and optionally applies Adam with float64 moments; block 0 also
-// finishes the loss (Eq. 4 / Eq. 8) from per-block float64 partials with
-// compensated (Neumaier) summation in a fixed order.
+// finishes the loss (Eq. 4 / Eq. 8) from per-block float64 partials with a
+// fixed-order pairwise float64 tree.
 #include "internal.h"
 
 namespace hrkan {
@@ -12,18 +12,39 @@ namespace hrkan {
 constexpr int RED_LANES = 32;   // parameters per block
 constexpr int RED_WARPS = 16;   // partial rows split across warps
 
-__device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
-    double t = s + x;
-    if (fabs(s) >= fabs(x)) c += (s - t) + x;
-    else c += (x - t) + s;
-    s = t;
-}
 
-// Sum of two compensated (Neumaier) partial sums (s, c): exact-sum error of
-// s1 + s2 goes into the compensation term.
-__device__ __forceinline__ void neumaier_merge(double& s, double& c, double s2, double c2) {
-    neumaier_add(s, c, s2);
-    c += c2;
+// Fixed-order pairwise float64 fold of rows [r0, r1) of the loss partials
+// [row][2] by all threads of the block (blockDim = 32 x RED_WARPS).  The
+// partials are sums of squares, all non-negative, so the pairwise tree (depth
+// ~log2 of the row count) bounds the relative error by ~depth * 2^-53 without a
+// compensation term, and keeps the float64 dependency chain short (float64
+// latency dominates this step on GB300).  Thread (0,0) receives the totals.
+__device__ __forceinline__ void fold_loss_rows(const double* lp, int r0, int r1, double& t0, double& t1) {
+    __shared__ double sh[2][RED_WARPS];
+    const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane, nt = 32 * RED_WARPS;
+    double a = 0.0, b = 0.0;
+    for (int g = r0 + tid; g < r1; g += nt) {
+        a += lp[2 * int64_t(g)];
+        b += lp[2 * int64_t(g) + 1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) { sh[0][w] = a; sh[1][w] = b; }
+    __syncthreads();
+    if (w == 0) {
+        a = lane < RED_WARPS ? sh[0][lane] : 0.0;
+        b = lane < RED_WARPS ? sh[1][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+    }
+    t0 = a;
+    t1 = b;
 }
 
 __global__ void __launch_bounds__(RED_LANES * RED_WARPS) reduce_kernel(ReduceParams p) {
@@ -77,26 +98,12 @@ __global__ void __launch_bounds__(RED_LANES * RED_WARPS) reduce_kernel(ReducePar
     }
     // commit the step counter; this kernel reads only t_counter[1]
     if (p.t_counter && blockIdx.x == 0 && w == 0 && lane == 0) p.t_counter[0] = p.t_counter[1];
-    if (blockIdx.x == 0 && w == 1 && p.loss_partial) {
-        // lane l sums rows l, l+32, ...; the 32 compensated sums are then merged
-        // pairwise by shuffles in a fixed tree order
-        double s0 = 0.0, c0 = 0.0, s1 = 0.0, c1 = 0.0;
-        for (int g = lane; g < p.Gl; g += 32) {
-            neumaier_add(s0, c0, p.loss_partial[2 * g]);
-            neumaier_add(s1, c1, p.loss_partial[2 * g + 1]);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            double a = __shfl_down_sync(0xffffffffu, s0, o), b = __shfl_down_sync(0xffffffffu, c0, o);
-            double e = __shfl_down_sync(0xffffffffu, s1, o), f = __shfl_down_sync(0xffffffffu, c1, o);
-            if (lane < o) {
-                neumaier_merge(s0, c0, a, b);
-                neumaier_merge(s1, c1, e, f);
-            }
-        }
-        if (lane == 0) {
-            double lp = p.n0 > 0 ? (s0 + c0) / double(p.n0) : 0.0;
-            double lb = p.n1 > 0 ? (s1 + c1) / double(p.n1) : 0.0;
+    if (blockIdx.x == 0 && p.loss_partial) {   // block-uniform: the fold synchronises the block
+        double s0, s1;
+        fold_loss_rows(p.loss_partial, 0, p.Gl, s0, s1);
+        if (w == 0 && lane == 0) {
+            const double lp = p.n0 > 0 ? s0 / double(p.n0) : 0.0;
+            const double lb = p.n1 > 0 ? s1 / double(p.n1) : 0.0;
             p.loss[0] = p.alpha * lp + lb;
             p.loss[1] = lp;
             p.loss[2] = lb;
@@ -213,25 +220,13 @@ __global__ void __launch_bounds__(RED_LANES * RED_WARPS) batch_reduce_kernel(Bat
         p.W[i] = p.W[i] - float(p.lr) * mh / (vh + float(p.eps));
     }
     if (p.t_counter && blockIdx.x == 0 && inst == 0 && w == 0 && lane == 0) p.t_counter[0] = p.t_counter[1];
-    if (blockIdx.x == 0 && w == 1) {
-        double s0 = 0.0, c0 = 0.0, s1 = 0.0, c1 = 0.0;
-        for (int g = r0 + lane; g < r1; g += 32) {
-            neumaier_add(s0, c0, p.loss_partial[2 * int64_t(g)]);
-            neumaier_add(s1, c1, p.loss_partial[2 * int64_t(g) + 1]);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            double a = __shfl_down_sync(0xffffffffu, s0, o), b = __shfl_down_sync(0xffffffffu, c0, o);
-            double e = __shfl_down_sync(0xffffffffu, s1, o), f = __shfl_down_sync(0xffffffffu, c1, o);
-            if (lane < o) {
-                neumaier_merge(s0, c0, a, b);
-                neumaier_merge(s1, c1, e, f);
-            }
-        }
-        if (lane == 0) {
+    if (blockIdx.x == 0) {   // block-uniform
+        double s0, s1;
+        fold_loss_rows(p.loss_partial, r0, r1, s0, s1);
+        if (w == 0 && lane == 0) {
             const double n0 = p.counts[2 * inst], n1 = p.counts[2 * inst + 1];
-            const double lp = n0 > 0 ? (s0 + c0) / n0 : 0.0;
-            const double lb = n1 > 0 ? (s1 + c1) / n1 : 0.0;
+            const double lp = n0 > 0 ? s0 / n0 : 0.0;
+            const double lb = n1 > 0 ? s1 / n1 : 0.0;
             p.loss[3 * inst] = p.alpha * lp + lb;
             p.loss[3 * inst + 1] = lp;
             p.loss[3 * inst + 2] = lb;
