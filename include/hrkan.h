@@ -75,7 +75,12 @@ typedef struct hrkan_cfg {
     int G;                           /* grid intervals on [grid_lo, grid_hi], >= 1 */
     int k;                           /* support width in cells minus one (B-spline order); 3 */
     int m;                           /* HR order of Eq. 2; 4 */
-    int prec;                        /* enum hrkan_prec: arithmetic of the jet contraction */
+    int prec;                        /* enum hrkan_prec: arithmetic of the jet contraction.  BF16 /
+                                        TF32: hidden layers with 16 <= O <= 64 (O % 16 == 0) contract
+                                        on tcgen05 tensor cores (FP32 accumulation in TMEM); the first
+                                        and last layers and the backward stay FP32.  Needs the
+                                        layer-wise path (a shape without a fused kernel, or
+                                        HRKAN_FLAG_LAYERWISE) */
     double grid_lo, grid_hi;         /* grid_lo < grid_hi */
     int n_instances;                 /* independent networks sharing the shape (>= 1) */
     int flags;                       /* HRKAN_FLAG_*; 0 = defaults */
@@ -177,6 +182,14 @@ int hrkan_backward(hrkan_t h, const float* W, const float* x, int64_t N, unsigne
  */
 int adam_step(hrkan_t h, float* W, const float* dW, double lr, double b1, double b2, double eps,
               int t, hrkan_stream_t stream);
+
+/*
+ * Synchronise the device and report device-side failures recorded since the
+ * last call: HRKAN_ETIMEOUT if a bounded wait inside a tensor-core kernel gave
+ * up (the kernel then skipped its output, freed its tensor memory and
+ * returned).  Clears the record.
+ */
+int hrkan_sync_status(hrkan_t h);
 
 /* Zero the Adam moments and the device step counter of the handle. */
 int hrkan_reset_moments(hrkan_t h, hrkan_stream_t stream);

@@ -26,7 +26,7 @@ HRKAN_MAX_WIDTHS = 8
 EXPORTS = ("hrkan_param_count", "hrkan_init", "hrkan_destroy", "hrkan_last_error", "hrkan_tape_floats",
            "hrkan_forward_jets", "pinn_residual_loss", "hrkan_backward", "adam_step", "hrkan_reset_moments",
            "hrkan_train_step", "hrkan_profile_enable", "hrkan_profile_read", "hrkan_backward_noalloc",
-           "hrkan_train_step_batched", "hrkan_forward_jets_batched", "hrkan_set_batch_items")
+           "hrkan_train_step_batched", "hrkan_forward_jets_batched", "hrkan_set_batch_items", "hrkan_sync_status")
 HRKAN_KERNEL_FUSED, HRKAN_KERNEL_REDUCE, HRKAN_KERNEL_FORWARD, HRKAN_KERNEL_RESIDUAL = 0, 1, 2, 3
 
 
@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH):
                                                  _d, _d, _d, _d, _i32, _vp, _vp, _vp]
         lib.hrkan_forward_jets_batched.argtypes = [_vp, _vp, _vp, _i64p, _u32, _vp, _vp]
         lib.hrkan_set_batch_items.argtypes = [_vp, _i32]
+        lib.hrkan_sync_status.argtypes = [_vp]
         lib.hrkan_profile_enable.argtypes = [_vp, _i32]
         lib.hrkan_profile_read.argtypes = [_vp, _i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
         for name in EXPORTS:
@@ -252,3 +253,8 @@ def hrkan_forward_jets_batched(h, W, x, offsets, jet_mask, jets, stream=None):
 
 def hrkan_set_batch_items(h, points_per_item):
     _check(load_library().hrkan_set_batch_items(h, int(points_per_item)))
+
+
+def hrkan_sync_status(h):
+    """Synchronise; raise HRKANError(HRKAN_ETIMEOUT) if a bounded device wait gave up."""
+    _check(load_library().hrkan_sync_status(h))

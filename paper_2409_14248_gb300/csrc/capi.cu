@@ -13,6 +13,7 @@
 #include "internal.h"
 #include "narrow.cuh"
 #include "wide.cuh"
+#include "tc.cuh"
 
 using namespace hrkan;
 
@@ -32,6 +33,7 @@ struct hrkan_ctx {
     double* m1 = nullptr;
     double* m2 = nullptr;
     int* t_counter = nullptr;        // [2] device Adam step counter (t = 0 mode)
+    int* status = nullptr;           // device error word written by bounded waits
     // multi-instance work lists (rebuilt only when the offsets or problems change)
     struct Batch {
         std::vector<int64_t> off0, off1;
@@ -319,6 +321,29 @@ WideLayer wide_layer(hrkan_t h, const float* W, int l, int64_t N) {
     return p;
 }
 
+// One layer's forward: the tensor-core kernel for hidden layers when the
+// handle's precision is BF16/TF32 and the shape fits it, else FP32 SIMT.
+int forward_layer(hrkan_t h, const float* W, int l, const float* in, float* out, int64_t N, unsigned mask,
+                  cudaStream_t s) {
+    WideLayer p = wide_layer(h, W, l, N);
+    p.z = in;
+    p.y = out;
+    if (N == 0) return HRKAN_OK;
+    if (l > 0 && tc_layer_supported(h->cfg.prec, p.I, p.O, h->n, mask)) {
+        int rc = HRKAN_OK;
+        const int64_t welems = tc_w_elems(p.O, p.I, h->n, h->cfg.prec);
+        float* wp = ws_get(h, 10, size_t(welems), &rc);   // 4-byte slots cover both element sizes
+        if (!wp) return rc;
+        cudaError_t e = tc_forward_layer(p.W, wp, in, out, p.I, p.O, N, h->grid, h->cfg.prec, mask, h->status, s);
+        if (e != cudaSuccess) return cuda_fail(e, "tensor-core layer launch");
+        return HRKAN_OK;
+    }
+    cudaError_t e = wide_forward_layer(p, mask, l == 0, s);
+    if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no layer kernel", mask);
+    if (e != cudaSuccess) return cuda_fail(e, "layer forward launch");
+    return HRKAN_OK;
+}
+
 // Forward of one point set through every layer.  Layer inputs go to `tape`
 // when given (layer l at tape_offset(l)), else to two ping-pong scratch slots
 // (zslot, zslot + 1).  The output jets go to `out` [J][N].
@@ -329,16 +354,12 @@ int wide_forward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsig
     int rc = HRKAN_OK;
     const float* in = x;
     for (int l = 0; l < L; ++l) {
-        WideLayer p = wide_layer(h, W, l, N);
-        p.z = in;
+        const int O = h->cfg.widths[l + 1];
         float* y;
         if (l == L - 1) y = out;
         else if (tape) y = tape + tape_offset(h, l + 1, N, J);
-        else if (!(y = ws_get(h, zslot + (l % 2), size_t(J) * p.O * N, &rc))) return rc;
-        p.y = y;
-        cudaError_t e = wide_forward_layer(p, mask, l == 0, s);
-        if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no layer kernel", mask);
-        if (e != cudaSuccess) return cuda_fail(e, "layer forward launch");
+        else if (!(y = ws_get(h, zslot + (l % 2), size_t(J) * O * N, &rc))) return rc;
+        if ((rc = forward_layer(h, W, l, in, y, N, mask, s))) return rc;
         in = y;
     }
     return HRKAN_OK;
@@ -361,16 +382,9 @@ int wide_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsi
                 // recompute layer l's input jets from the coordinates
                 const float* in = x;
                 for (int t = 0; t < l; ++t) {
-                    WideLayer p = wide_layer(h, W, t, N);
-                    p.z = in;
-                    float* y = ws_get(h, 0 + (t % 2), size_t(J) * p.O * N, &rc);
+                    float* y = ws_get(h, 0 + (t % 2), size_t(J) * h->cfg.widths[t + 1] * N, &rc);
                     if (!y) return rc;
-                    p.y = y;
-                    if (N > 0) {
-                        cudaError_t e = wide_forward_layer(p, mask, t == 0, s);
-                        if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x", mask);
-                        if (e != cudaSuccess) return cuda_fail(e, "layer recompute launch");
-                    }
+                    if ((rc = forward_layer(h, W, t, in, y, N, mask, s))) return rc;
                     in = y;
                 }
                 zl = in;
@@ -520,7 +534,9 @@ int hrkan_init(hrkan_t* out, const hrkan_cfg* cfg) {
     if (cfg->flags & HRKAN_FLAG_LAYERWISE) net_id = -1;
     if (net_id < 0 && cfg->n_instances != 1)
         return fail(HRKAN_EUNSUPPORTED, "several instances need a fused shape ([2,W,1] or [2,W,W,1], W in 5,10,16)");
-    if (cfg->prec != HRKAN_FP32) return fail(HRKAN_EUNSUPPORTED, "precision %d has no kernels for this shape", cfg->prec);
+    if (cfg->prec != HRKAN_FP32 && net_id >= 0)
+        return fail(HRKAN_EUNSUPPORTED, "precision %d: the fused narrow kernels are FP32 only (set HRKAN_FLAG_LAYERWISE)",
+                    cfg->prec);
 
     hrkan_ctx* h = new (std::nothrow) hrkan_ctx();
     if (!h) return fail(HRKAN_ENOMEM, "host allocation");
@@ -553,13 +569,15 @@ int hrkan_init(hrkan_t* out, const hrkan_cfg* cfg) {
         (e = cudaMalloc(&h->loss_partial, size_t(h->max_grid_l) * 2 * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&h->m1, size_t(h->P) * cfg->n_instances * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&h->m2, size_t(h->P) * cfg->n_instances * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&h->t_counter, 2 * sizeof(int))) != cudaSuccess) {
+        (e = cudaMalloc(&h->t_counter, 2 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&h->status, sizeof(int))) != cudaSuccess) {
         hrkan_destroy(h);
         return fail(HRKAN_ENOMEM, "cudaMalloc of the workspace: %s", cudaGetErrorString(e));
     }
     if ((e = cudaMemset(h->m1, 0, size_t(h->P) * cfg->n_instances * sizeof(double))) != cudaSuccess ||
         (e = cudaMemset(h->m2, 0, size_t(h->P) * cfg->n_instances * sizeof(double))) != cudaSuccess ||
         (e = cudaMemset(h->t_counter, 0, 2 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(h->status, 0, sizeof(int))) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess) {
         hrkan_destroy(h);
         return cuda_fail(e, "zeroing the Adam moments");
@@ -579,6 +597,7 @@ void hrkan_destroy(hrkan_t h) {
     cudaFree(h->m1);
     cudaFree(h->m2);
     cudaFree(h->t_counter);
+    cudaFree(h->status);
     for (auto* b : {&h->train_batch, &h->fwd_batch}) {
         cudaFree(b->items); cudaFree(b->inst); cudaFree(b->item_off); cudaFree(b->counts);
         cudaFree(b->partial); cudaFree(b->loss_partial);
@@ -958,6 +977,19 @@ int hrkan_forward_jets_batched(hrkan_t h, const float* W, const float* x, const 
     }
     if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no forward kernel", jet_mask);
     if (e != cudaSuccess) return cuda_fail(e, "multi-instance forward launch");
+    return HRKAN_OK;
+}
+
+int hrkan_sync_status(hrkan_t h) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (int rc = use_device(h)) return rc;
+    HR_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    int st = 0;
+    HR_CUDA(cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+    if (st != 0) {
+        HR_CUDA(cudaMemset(h->status, 0, sizeof(int)), "status reset");
+        return fail(st, "a device-side wait gave up (status %d)", st);
+    }
     return HRKAN_OK;
 }
 

@@ -1,0 +1,31 @@
+// Tensor-core forward of one hidden layer (tc_jets.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/hrkan.h"
+#include "hr_device.cuh"
+
+namespace hrkan {
+
+struct TcLayer {
+    const float* z;   // input jets [J][I][N]
+    float* y;         // output jets [J][O][N]
+    int I, O;
+    int64_t N;
+    int ksteps;       // K steps of 128 bytes per row
+    Grid g;
+    int* status;      // device error word (HRKAN_ETIMEOUT on a timed-out wait)
+};
+
+// Layers the tensor-core kernel handles: 16 <= O <= 64, O % 16 == 0, J*O <= 320.
+bool tc_layer_supported(int prec, int I, int O, int n, unsigned mask);
+// Elements of the converted weight buffer of one layer.
+int64_t tc_w_elems(int O, int I, int n, int prec);
+// Converts W (float32 [O][I][n]) into w_prep (tc_w_elems elements of 2 or 4
+// bytes) and runs the tensor-core contraction: y = jets of the layer output.
+cudaError_t tc_forward_layer(const float* W, void* w_prep, const float* z, float* y, int I, int O, int64_t N,
+                             const Grid& g, int prec, unsigned mask, int* status, cudaStream_t s);
+
+}  // namespace hrkan
