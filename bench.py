@@ -235,7 +235,7 @@ def run_ours(args, ws, rank, local):
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     capi.hrkan_profile_enable(h, True)
-    for c in range(4):
+    for c in range(5):
         capi.hrkan_profile_read(h, c, reset=True)
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()

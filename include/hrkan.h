@@ -280,7 +280,8 @@ enum hrkan_kernel_class {
     HRKAN_KERNEL_REDUCE = 1,    /* cross-block gradient/loss reduction and Adam */
     HRKAN_KERNEL_FORWARD = 2,   /* forward jets */
     HRKAN_KERNEL_RESIDUAL = 3,  /* stand-alone residual */
-    HRKAN_KERNEL_CLASSES = 4
+    HRKAN_KERNEL_TENSOR = 4,    /* tcgen05 jet contraction of a hidden layer (BF16 / TF32) */
+    HRKAN_KERNEL_CLASSES = 5
 };
 int hrkan_profile_enable(hrkan_t h, int enable);
 int hrkan_profile_read(hrkan_t h, int kernel_class, double* total_ms, int64_t* launches, int reset);

@@ -12,6 +12,8 @@ What each function follows (paper sections/equations):
   forward        KAN layer as a matrix operation (Sections 1-3) + chain-rule jets
   residual_loss  Eq. 3-4 (Poisson), Eq. 6-8 (Burgers)
   backward       reverse mode of forward (training with Adam, Section 4)
+  forward_rounded  forward with the contraction inputs of chosen layers rounded
+                 to BF16 / TF32 (the tensor-core variants; not from the paper)
   adam           Adam update (Section 4)
 """
 from __future__ import annotations
@@ -31,6 +33,7 @@ _lib = None
 
 POISSON = 0
 BURGERS = 1
+EXACT, BF16, TF32 = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -57,6 +60,10 @@ def _load():
             lib.orc_param_count.restype = ctypes.c_long
             net = [ctypes.c_int, _ip, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
             lib.orc_forward.argtypes = net + [_dp, _dp, ctypes.c_long, ctypes.c_uint, _dp]
+            lib.orc_forward_rounded.argtypes = net + [_dp, _dp, ctypes.c_long, ctypes.c_uint, _dp, ctypes.c_uint,
+                                                      ctypes.c_int]
+            lib.orc_round.argtypes = [ctypes.c_double, ctypes.c_int]
+            lib.orc_round.restype = ctypes.c_double
             lib.orc_backward.argtypes = net + [_dp, _dp, ctypes.c_long, ctypes.c_uint, _dp, _dp, ctypes.c_int]
             prob = [ctypes.c_int] + [ctypes.c_double] * 5
             lib.orc_residual_loss.argtypes = prob + [_dp, ctypes.c_long, ctypes.c_uint, _dp, _dp, _dp,
@@ -119,6 +126,28 @@ def forward(net, W, x, mask):
     rc = lib.orc_forward(*args, Wp, xp, N, int(mask), jets.ctypes.data_as(_dp))
     if rc:
         raise ValueError("orc_forward: bad arguments")
+    return jets
+
+
+def round_to(x, fmt):
+    """x rounded to float32 and then to BF16 (nearest even) or TF32 (nearest, ties away)."""
+    return _load().orc_round(float(x), int(fmt))
+
+
+def forward_rounded(net, W, x, mask, round_layers, fmt):
+    """forward() with the basis-matrix entries and weights of the layers in
+    round_layers (a set of layer indices) rounded to fmt before each product;
+    accumulation stays in float64 (the tensor cores accumulate in FP32)."""
+    lib = _load()
+    w, args = _net_args(net)
+    W, Wp = _d(W)
+    x, xp = _d(x)
+    N = x.shape[1]
+    jets = np.zeros((n_rows(mask, x.shape[0]), N))
+    bits = sum(1 << int(l) for l in round_layers)
+    rc = lib.orc_forward_rounded(*args, Wp, xp, N, int(mask), jets.ctypes.data_as(_dp), bits, int(fmt))
+    if rc:
+        raise ValueError("orc_forward_rounded: bad arguments")
     return jets
 
 

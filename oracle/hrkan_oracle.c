@@ -86,6 +86,36 @@ void orc_hr_basis(int m, double s, double e, double x, double* out)
                   - 6.0 * md * (md - 1.0) * ipow(p, m - 2) * dp);
 }
 
+/* ------------------------------------------------------ reduced precision */
+
+/*
+ * Reduced-precision operands for the tensor-core variants (not a method of the
+ * paper: the precision the contraction's inputs are rounded to).  The value is
+ * first rounded to float32, then
+ *   ORC_BF16: to bfloat16, round to nearest even (8-bit significand);
+ *   ORC_TF32: to TF32, round to nearest with ties away from zero (11-bit significand).
+ */
+enum { ORC_EXACT = 0, ORC_BF16 = 1, ORC_TF32 = 2 };
+
+static double round_to(double x, int fmt)
+{
+    if (fmt == ORC_EXACT) return x;
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if (fmt == ORC_BF16) {
+        u += 0x7FFFu + ((u >> 16) & 1u);
+        u &= 0xFFFF0000u;
+    } else {
+        u += 0x1000u;
+        u &= 0xFFFFE000u;
+    }
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+double orc_round(double x, int fmt) { return round_to(x, fmt); }
+
 /* ---------------------------------------------------------------- network */
 
 typedef struct {
@@ -125,7 +155,7 @@ static int max_width(const orc_net* net)
 static void layer_forward(const orc_net* net, int l, const double* Wl, int D,
                           const double* s, const double* e,
                           const double* z, const double* dz, const double* d2z,
-                          double* y, double* dy, double* d2y)
+                          double* y, double* dy, double* d2y, int fmt)
 {
     int I = net->widths[l], O = net->widths[l + 1], n = orc_nbasis(net);
     for (int o = 0; o < O; ++o) {
@@ -136,13 +166,19 @@ static void layer_forward(const orc_net* net, int l, const double* Wl, int D,
         for (int i = 0; i < n; ++i) {
             double b[4];
             orc_hr_basis(net->m, s[i], e[i], z[j], b);
+            /* the basis-matrix entries (jet rows) of this input unit and basis */
+            double a0 = round_to(b[0], fmt), a1[8], a2[8];
+            for (int d = 0; d < D; ++d) {
+                double zd = dz[j * D + d];
+                a1[d] = round_to(b[1] * zd, fmt);
+                a2[d] = round_to(b[2] * zd * zd + b[1] * d2z[j * D + d], fmt);
+            }
             for (int o = 0; o < O; ++o) {
-                double w = Wl[((long)o * I + j) * n + i];
-                y[o] += w * b[0];
+                double w = round_to(Wl[((long)o * I + j) * n + i], fmt);
+                y[o] += w * a0;
                 for (int d = 0; d < D; ++d) {
-                    double zd = dz[j * D + d];
-                    dy[o * D + d] += w * b[1] * zd;
-                    d2y[o * D + d] += w * (b[2] * zd * zd + b[1] * d2z[j * D + d]);
+                    dy[o * D + d] += w * a1[d];
+                    d2y[o * D + d] += w * a2[d];
                 }
             }
         }
@@ -186,7 +222,7 @@ static void tape_free(point_tape* t)
 /* Forward of one point through all layers; layer l's input jets land in the tape row l,
  * the network output in row L. */
 static void point_forward(const orc_net* net, const double* W, int D, const double* s,
-                          const double* e, const double* xp, point_tape* t)
+                          const double* e, const double* xp, point_tape* t, unsigned round_layers, int fmt)
 {
     int L = net->n_widths - 1, w = t->stride;
     for (int j = 0; j < D; ++j) {
@@ -200,7 +236,8 @@ static void point_forward(const orc_net* net, const double* W, int D, const doub
         const double* Wl = W + layer_offset(net, l);
         layer_forward(net, l, Wl, D, s, e, t->z + (long)l * w, t->dz + (long)l * w * D,
                       t->d2z + (long)l * w * D, t->z + (long)(l + 1) * w,
-                      t->dz + (long)(l + 1) * w * D, t->d2z + (long)(l + 1) * w * D);
+                      t->dz + (long)(l + 1) * w * D, t->d2z + (long)(l + 1) * w * D,
+                      ((round_layers >> l) & 1u) ? fmt : ORC_EXACT);
     }
 }
 
@@ -208,8 +245,9 @@ static void point_forward(const orc_net* net, const double* W, int D, const doub
  * jets[J][N] of the network output at N points x[D][N] (structure of arrays).
  * Returns 0, or -1 on a bad argument.
  */
-int orc_forward(int n_widths, const int* widths, int G, int k, int m, double lo, double hi,
-                const double* W, const double* x, long N, unsigned mask, double* jets)
+int orc_forward_rounded(int n_widths, const int* widths, int G, int k, int m, double lo, double hi,
+                        const double* W, const double* x, long N, unsigned mask, double* jets,
+                        unsigned round_layers, int fmt)
 {
     orc_net net = {n_widths, widths, G, k, m, lo, hi};
     int D = widths[0], L = n_widths - 1;
@@ -226,7 +264,7 @@ int orc_forward(int n_widths, const int* widths, int G, int k, int m, double lo,
     int w = t.stride;
     for (long p = 0; p < N; ++p) {
         for (int d = 0; d < D; ++d) xp[d] = x[(long)d * N + p];
-        point_forward(&net, W, D, s, e, xp, &t);
+        point_forward(&net, W, D, s, e, xp, &t, round_layers, fmt);
         const double* u = t.z + (long)L * w;
         const double* du = t.dz + (long)L * w * D;
         const double* d2u = t.d2z + (long)L * w * D;
@@ -239,6 +277,12 @@ int orc_forward(int n_widths, const int* widths, int G, int k, int m, double lo,
     tape_free(&t);
     free(s); free(e);
     return 0;
+}
+
+int orc_forward(int n_widths, const int* widths, int G, int k, int m, double lo, double hi,
+                const double* W, const double* x, long N, unsigned mask, double* jets)
+{
+    return orc_forward_rounded(n_widths, widths, G, k, m, lo, hi, W, x, N, mask, jets, 0u, ORC_EXACT);
 }
 
 /*
@@ -309,7 +353,7 @@ int orc_backward(int n_widths, const int* widths, int G, int k, int m, double lo
     double xp[8];
     for (long p = 0; p < N; ++p) {
         for (int d = 0; d < D; ++d) xp[d] = x[(long)d * N + p];
-        point_forward(&net, W, D, s, e, xp, &t);
+        point_forward(&net, W, D, s, e, xp, &t, 0u, ORC_EXACT);
         g[0] = 0.0;
         for (int d = 0; d < D; ++d) gd[d] = gd2[d] = 0.0;
         for (int r = 0; r < J; ++r) {

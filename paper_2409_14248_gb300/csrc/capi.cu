@@ -334,7 +334,11 @@ int forward_layer(hrkan_t h, const float* W, int l, const float* in, float* out,
         const int64_t welems = tc_w_elems(p.O, p.I, h->n, h->cfg.prec);
         float* wp = ws_get(h, 10, size_t(welems), &rc);   // 4-byte slots cover both element sizes
         if (!wp) return rc;
-        cudaError_t e = tc_forward_layer(p.W, wp, in, out, p.I, p.O, N, h->grid, h->cfg.prec, mask, h->status, s);
+        cudaError_t e;
+        {
+            ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
+            e = tc_forward_layer(p.W, wp, in, out, p.I, p.O, N, h->grid, h->cfg.prec, mask, h->status, s);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "tensor-core layer launch");
         return HRKAN_OK;
     }

@@ -1,21 +1,32 @@
-"""Tensor-core (tcgen05) forward of the hidden layers in BF16 / TF32 vs the
-FP64 oracle, error reported per jet order (value, first, second derivatives).
+"""Tensor-core (tcgen05) forward of the hidden layers in BF16 / TF32.
 
-Bar for BF16 jets: 2e-2 relative (normwise per jet row).  TF32 keeps 10
-mantissa bits instead of BF16's 7, so its bar is 8x tighter (2.5e-3).
+Two questions, kept apart:
+
+1. Does the kernel compute the BF16 / TF32 contraction correctly?  It is
+   compared with the oracle's forward in which the basis-matrix entries and
+   weights of the same layers are rounded to BF16 (nearest even) or TF32
+   (nearest, ties away) and everything else is exact: the kernel must sit far
+   closer to that than the rounding moves the result (a wrong operand layout
+   or K order gives an O(1) difference).
+2. How accurate is the precision itself?  The error against the exact FP64
+   oracle per jet order (value, first, second derivatives).  The 2e-2 bar for
+   BF16 jets holds on the [2,32,32,1] network; the [2,64,64,64,1] G=32
+   network at its initial weights amplifies input rounding ~600x (measured in
+   FP32), so there BF16 gives ~0.4 and TF32 ~5e-2: reported, not asserted.
 """
 import numpy as np
 import pytest
 
 import oracle
-from gpu_util import relerr
+from gpu_util import conditioned_tolerances, relerr
 from paper_2409_14248_gb300 import build, capi, inputs
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-TOL = {capi.HRKAN_BF16: 2e-2, capi.HRKAN_TF32: 2.5e-3}
+BAR = {capi.HRKAN_BF16: 2e-2, capi.HRKAN_TF32: 2.5e-3}
+FMT = {capi.HRKAN_BF16: oracle.BF16, capi.HRKAN_TF32: oracle.TF32}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -40,25 +51,59 @@ def _forward(w, prec, W, x, mask, flags=0):
         capi.hrkan_destroy(h)
 
 
+def _check(w, prec, d, mask):
+    """Returns the per-jet-order error vs exact FP64, after checking the kernel
+    against the rounding-aware oracle."""
+    x = d["x_int"]
+    got = _forward(w, prec, d["W"], x, mask)
+    assert np.all(np.isfinite(got))
+    exact = oracle.forward(w.net, d["W"], x, mask)
+    hidden = set(range(1, len(w.widths) - 2))     # the layers the tensor cores take
+    rounded = oracle.forward_rounded(w.net, d["W"], x, mask, hidden, FMT[prec])
+    floor = conditioned_tolerances(w, d["W"], x, mask)   # the FP32 part of the path
+    errs = []
+    for r in range(exact.shape[0]):
+        e_fmt = relerr(rounded[r], exact[r])
+        e_impl = relerr(got[r], rounded[r])
+        assert e_impl < 0.05 * e_fmt + floor[r], (r, e_impl, e_fmt)
+        errs.append(relerr(got[r], exact[r]))
+    print(f"\nper-jet-order relative error, prec {prec}, mask {mask:#x}: {np.array(errs)}")
+    return errs
+
+
 @pytest.mark.parametrize("prec", [capi.HRKAN_BF16, capi.HRKAN_TF32])
 @pytest.mark.parametrize("mask", [0x01, 0x1F])
-def test_tc_forward_per_jet_order_error(prec, mask):
+def test_tc_forward_poisson_64x3(prec, mask):
     w = inputs.WORKLOADS["poisson_2_64x3_1"]
-    d = inputs.make(w, n_int=300, n_bnd=40)
-    got = _forward(w, prec, d["W"], d["x_int"], mask)
-    want = oracle.forward(w.net, d["W"], d["x_int"], mask)
-    errs = [relerr(got[r], want[r]) for r in range(want.shape[0])]
-    print("per-jet-order relative error", prec, mask, errs)
-    assert np.all(np.isfinite(got))
-    assert max(errs) < TOL[prec], errs
+    _check(w, prec, inputs.make(w, n_int=300, n_bnd=40), mask)
 
 
 @pytest.mark.parametrize("prec", [capi.HRKAN_BF16, capi.HRKAN_TF32])
-def test_tc_forward_burgers_32_and_ragged_tile(prec):
-    """[2,32,32,1], G=20 (n = 23, several units per K step), 389 points (ragged last tile)."""
+def test_tc_forward_burgers_32_meets_the_jet_bar(prec):
+    """[2,32,32,1], G=20 (n = 23: up to four units per K step), 389 points (ragged last tile)."""
     w = inputs.WORKLOADS["burgers_2_32_32_1"]
-    d = inputs.make(w, n_int=389, n_ic=8, n_bc=8)
-    got = _forward(w, prec, d["W"], d["x_int"], 0x0F)
-    want = oracle.forward(w.net, d["W"], d["x_int"], 0x0F)
-    errs = [relerr(got[r], want[r]) for r in range(4)]
-    assert max(errs) < TOL[prec], errs
+    errs = _check(w, prec, inputs.make(w, n_int=389, n_ic=8, n_bc=8), 0x0F)
+    assert max(errs) < BAR[prec], errs
+
+
+def test_tc_full_size_forward_sampled():
+    """[2,64,64,64,1] at its full 262144 interior points in BF16; 96 sampled points vs the rounding-aware oracle."""
+    w = inputs.WORKLOADS["poisson_2_64x3_1"]
+    d = inputs.make(w)
+    N = d["x_int"].shape[1]
+    h = capi.hrkan_init(capi.make_cfg(w.widths, w.G, prec=capi.HRKAN_BF16))
+    try:
+        jets = torch.zeros((5, N), device="cuda")
+        capi.hrkan_forward_jets(h, _dev(d["W"]), _dev(d["x_int"]), N, 0x1F, jets)
+        capi.hrkan_sync_status(h)
+        idx = np.random.default_rng(51).choice(N, 96, replace=False)
+        idx[:2] = [0, N - 1]
+        xs = d["x_int"][:, idx]
+        got = jets.cpu().numpy()[:, idx]
+        exact = oracle.forward(w.net, d["W"], xs, 0x1F)
+        rounded = oracle.forward_rounded(w.net, d["W"], xs, 0x1F, {1, 2}, oracle.BF16)
+        floor = conditioned_tolerances(w, d["W"], xs, 0x1F)
+        for r in range(5):
+            assert relerr(got[r], rounded[r]) < 0.05 * relerr(rounded[r], exact[r]) + floor[r], r
+    finally:
+        capi.hrkan_destroy(h)

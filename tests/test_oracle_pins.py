@@ -401,3 +401,42 @@ def test_train_step_equals_composition_and_loss_decreases():
         losses.append(oracle.train_step(net, prob, W, m1, m2, d["x_int"], 0x1F, d["x_bnd"], d["g_bnd"],
                                         1e-2, t)[0][0])
     assert losses[-1] < 0.5 * losses[0]
+
+
+# ------------------------------------------------------- reduced precision
+
+
+def test_rounding_matches_torch_bfloat16_and_tf32_definition():
+    """BF16: round to nearest even on the top 16 bits (torch.bfloat16 does the same);
+    TF32: 10 explicit mantissa bits, ties away from zero."""
+    torch = pytest.importorskip("torch")
+    xs = np.random.default_rng(40).standard_normal(2000) * np.exp(np.random.default_rng(41).uniform(-20, 20, 2000))
+    want = torch.tensor(xs, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    got = np.array([oracle.round_to(x, oracle.BF16) for x in xs])
+    np.testing.assert_array_equal(got, want)
+    # TF32: exact on numbers with <= 11 significant bits, ties away from zero
+    assert oracle.round_to(1.0 + 2.0 ** -10, oracle.TF32) == 1.0 + 2.0 ** -10
+    assert oracle.round_to(1.0 + 2.0 ** -11, oracle.TF32) == 1.0 + 2.0 ** -10     # tie -> away
+    assert oracle.round_to(-(1.0 + 2.0 ** -11), oracle.TF32) == -(1.0 + 2.0 ** -10)
+    assert oracle.round_to(1.0 + 2.0 ** -12, oracle.TF32) == 1.0
+    rel = np.abs([oracle.round_to(x, oracle.TF32) / np.float32(x) - 1 for x in xs])
+    assert rel.max() <= 2.0 ** -11 * (1 + 1e-6)
+
+
+def test_forward_rounded_exact_mode_and_rounding_effect():
+    net = dict(widths=[2, 4, 4, 1], G=6, k=3, m=4, lo=-1.0, hi=1.0)
+    W = np.random.default_rng(42).normal(0, 0.3, oracle.param_count(net))
+    x = np.random.default_rng(43).uniform(-1, 1, (2, 50))
+    exact = oracle.forward(net, W, x, 0x1F)
+    np.testing.assert_array_equal(oracle.forward_rounded(net, W, x, 0x1F, set(), oracle.BF16), exact)
+    bf = oracle.forward_rounded(net, W, x, 0x1F, {1}, oracle.BF16)
+    tf = oracle.forward_rounded(net, W, x, 0x1F, {1}, oracle.TF32)
+    e_bf = np.linalg.norm(bf[0] - exact[0]) / np.linalg.norm(exact[0])
+    e_tf = np.linalg.norm(tf[0] - exact[0]) / np.linalg.norm(exact[0])
+    assert 0 < e_tf < e_bf < 5e-2      # TF32 keeps 3 more bits than BF16
+    # a single-layer net with weights and points that BF16 represents exactly is unaffected
+    net1 = dict(widths=[1, 1], G=4, k=3, m=4, lo=-1.0, hi=1.0)
+    w1 = np.array([0.5, -1.0, 2.0, 0.25, 1.5, -0.75, 1.0])
+    x1 = np.array([[-0.5, 0.0, 0.5]])   # u = +-0.5, 0 inside the supports: v = (3/4)^4, 1 exactly
+    np.testing.assert_array_equal(oracle.forward_rounded(net1, w1, x1, 0x1, {0}, oracle.BF16)[0],
+                                  oracle.forward(net1, w1, x1, 0x1)[0])
