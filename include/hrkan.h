@@ -144,6 +144,17 @@ int hrkan_forward_jets(hrkan_t h, const float* W, const float* x, int64_t N, uns
                        float* jets, float* tape, hrkan_stream_t stream);
 
 /*
+ * One layer of the network applied to given input jets (the KAN layer of
+ * Sections 1-3 with its jets): layer index l, W = that layer's weights
+ * [O][I][n] (a pointer into the network's W), z = input jets [J][I][N] (for
+ * l = 0: the coordinates [2][N]), y = output jets [J][O][N] (written).  Runs
+ * the same kernel the network forward would use for that layer under the
+ * handle's precision (tensor cores for BF16/TF32 hidden layers).
+ */
+int hrkan_layer_jets(hrkan_t h, int layer, const float* W, const float* z, int64_t N, unsigned jet_mask,
+                     float* y, hrkan_stream_t stream);
+
+/*
  * Residual and loss (Eq. 3-4 / Eq. 6-8) from precomputed jets.
  *   x_int [2][N_int], jets_int [J][N_int] under jet_mask (Poisson needs u_xx,
  *   u_yy; Burgers needs u, u_x, u_t, u_xx), u_bnd / g_bnd [N_bnd] network

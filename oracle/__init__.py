@@ -62,6 +62,9 @@ def _load():
             lib.orc_forward.argtypes = net + [_dp, _dp, ctypes.c_long, ctypes.c_uint, _dp]
             lib.orc_forward_rounded.argtypes = net + [_dp, _dp, ctypes.c_long, ctypes.c_uint, _dp, ctypes.c_uint,
                                                       ctypes.c_int]
+            lib.orc_layer_forward.argtypes = [ctypes.c_int] * 5 + [ctypes.c_double] * 2 + [_dp, _dp, ctypes.c_long,
+                                                                                        ctypes.c_uint, _dp,
+                                                                                        ctypes.c_int]
             lib.orc_round.argtypes = [ctypes.c_double, ctypes.c_int]
             lib.orc_round.restype = ctypes.c_double
             lib.orc_backward.argtypes = net + [_dp, _dp, ctypes.c_long, ctypes.c_uint, _dp, _dp, ctypes.c_int]
@@ -149,6 +152,20 @@ def forward_rounded(net, W, x, mask, round_layers, fmt):
     if rc:
         raise ValueError("orc_forward_rounded: bad arguments")
     return jets
+
+
+def layer_forward(I, O, G, k, m, lo, hi, Wl, zin, mask, fmt=EXACT):
+    """One KAN layer on given input jets zin[J, I, N] (rows of mask) -> [J, O, N]."""
+    lib = _load()
+    Wl, Wp = _d(Wl)
+    z, zp = _d(zin)
+    J, _, N = z.shape
+    out = np.zeros((J, O, N))
+    rc = lib.orc_layer_forward(int(I), int(O), int(G), int(k), int(m), float(lo), float(hi), Wp, zp, N, int(mask),
+                               out.ctypes.data_as(_dp), int(fmt))
+    if rc:
+        raise ValueError("orc_layer_forward: bad arguments")
+    return out
 
 
 def backward(net, W, x, mask, dL_djets, dW=None):

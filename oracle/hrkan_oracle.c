@@ -286,6 +286,56 @@ int orc_forward(int n_widths, const int* widths, int G, int k, int m, double lo,
 }
 
 /*
+ * One layer (Sections 1-3) applied to given input jets, D = 2:
+ *   zin[r][j][p] for the jet rows r of mask (value, first, second derivatives
+ *   in bit order), units j < I, points p < N; rows not in mask are zero.
+ *   yout[r][o][p], the same rows for the O outputs.
+ * Basis-matrix entries and weights rounded to fmt (ORC_EXACT: none).
+ */
+int orc_layer_forward(int I, int O, int G, int k, int m, double lo, double hi, const double* Wl,
+                      const double* zin, long N, unsigned mask, double* yout, int fmt)
+{
+    const int D = 2;
+    int widths[2] = {I, O};
+    orc_net net = {2, widths, G, k, m, lo, hi};
+    int rows[16];
+    int J = mask_rows(mask, D, rows);
+    if (!(mask & 1u)) return -1;
+    int n = G + k;
+    double* s = malloc(sizeof(double) * n);
+    double* e = malloc(sizeof(double) * n);
+    double* z = malloc(sizeof(double) * I);
+    double* dz = calloc((size_t)I * D, sizeof(double));
+    double* d2z = calloc((size_t)I * D, sizeof(double));
+    double* y = malloc(sizeof(double) * O);
+    double* dy = malloc(sizeof(double) * O * D);
+    double* d2y = malloc(sizeof(double) * O * D);
+    orc_support(G, k, lo, hi, s, e);
+    for (long p = 0; p < N; ++p) {
+        for (int j = 0; j < I; ++j) {
+            z[j] = 0.0;
+            for (int d = 0; d < D; ++d) dz[j * D + d] = d2z[j * D + d] = 0.0;
+            for (int r = 0; r < J; ++r) {
+                double v = zin[((long)r * I + j) * N + p];
+                int b = rows[r];
+                if (b == 0) z[j] = v;
+                else if (b <= D) dz[j * D + b - 1] = v;
+                else d2z[j * D + b - 1 - D] = v;
+            }
+        }
+        layer_forward(&net, 0, Wl, D, s, e, z, dz, d2z, y, dy, d2y, fmt);
+        for (int o = 0; o < O; ++o)
+            for (int r = 0; r < J; ++r) {
+                int b = rows[r];
+                double v = (b == 0) ? y[o] : (b <= D) ? dy[o * D + b - 1] : d2y[o * D + b - 1 - D];
+                yout[((long)r * O + o) * N + p] = v;
+            }
+    }
+    free(s); free(e); free(z); free(dz); free(d2z); free(y); free(dy); free(d2y);
+    return 0;
+}
+
+/*
  * Reverse mode of point_forward.  g*, gd*, gd2* hold dL/d(output jets) of the
  * layer on entry and are overwritten with dL/d(input jets).  dW accumulates.
  */

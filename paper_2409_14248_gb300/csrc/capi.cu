@@ -997,4 +997,17 @@ int hrkan_sync_status(hrkan_t h) {
     return HRKAN_OK;
 }
 
+int hrkan_layer_jets(hrkan_t h, int layer, const float* W, const float* z, int64_t N, unsigned jet_mask, float* y,
+                     hrkan_stream_t stream) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (layer < 0 || layer >= h->L) return fail(HRKAN_EINVAL, "layer %d outside [0, %d)", layer, h->L);
+    if (N < 0) return fail(HRKAN_EINVAL, "N=%lld", (long long)N);
+    if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
+    if (N == 0) return HRKAN_OK;
+    if (!W || !z || !y) return fail(HRKAN_EINVAL, "NULL device pointer");
+    if (int rc = use_device(h)) return rc;
+    // forward_layer takes the whole network's weights and offsets into them
+    return forward_layer(h, W - h->layer_off[layer], layer, z, y, N, jet_mask, (cudaStream_t)stream);
+}
+
 }  // extern "C"

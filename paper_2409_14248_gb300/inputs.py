@@ -204,3 +204,18 @@ def make_batched(w: Workload | str, instances=None, count_lo=None, count_hi=None
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
     return dict(ab=ab, off_int=off_i, off_bnd=off_b, x_int=f32(np.concatenate(xi, axis=1)),
                 x_bnd=f32(np.concatenate(xb, axis=1)), g_bnd=f32(np.concatenate(gb)), W=W)
+
+
+def layer_jets(I, N, mask, seed, lo=-1.0, hi=1.0):
+    """Random input jets [J][I][N] for testing one layer: values uniform on
+    [lo, hi] (the grid range), first derivatives N(0, 1), second N(0, 3^2)."""
+    rng = np.random.default_rng([seed, 0x1A7E])
+    J = bin(mask & 0x1F).count("1")
+    z = np.empty((J, I, N))
+    z[0] = rng.uniform(lo, hi, (I, N))
+    r = 1
+    for bit in range(1, 5):
+        if mask & (1 << bit):
+            z[r] = rng.standard_normal((I, N)) * (1.0 if bit <= 2 else 3.0)
+            r += 1
+    return np.ascontiguousarray(z, dtype=np.float32)

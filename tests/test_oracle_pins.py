@@ -440,3 +440,21 @@ def test_forward_rounded_exact_mode_and_rounding_effect():
     x1 = np.array([[-0.5, 0.0, 0.5]])   # u = +-0.5, 0 inside the supports: v = (3/4)^4, 1 exactly
     np.testing.assert_array_equal(oracle.forward_rounded(net1, w1, x1, 0x1, {0}, oracle.BF16)[0],
                                   oracle.forward(net1, w1, x1, 0x1)[0])
+
+
+def test_layer_forward_composes_to_the_network_forward():
+    """Applying layer_forward layer by layer (from coordinate jets) equals forward."""
+    net = dict(widths=[2, 4, 3, 1], G=6, k=3, m=4, lo=-1.0, hi=1.0)
+    n = 9
+    W = np.random.default_rng(44).normal(0, 0.4, oracle.param_count(net))
+    x = np.random.default_rng(45).uniform(-1, 1, (2, 20))
+    z = np.zeros((5, 2, 20))
+    z[0] = x
+    z[1, 0] = 1.0     # dx/dx
+    z[2, 1] = 1.0     # dy/dy
+    off = 0
+    for l in range(3):
+        I, O = net["widths"][l], net["widths"][l + 1]
+        z = oracle.layer_forward(I, O, 6, 3, 4, -1.0, 1.0, W[off: off + O * I * n], z, 0x1F)
+        off += O * I * n
+    np.testing.assert_allclose(z[:, 0, :], oracle.forward(net, W, x, 0x1F), rtol=1e-12, atol=1e-12)
