@@ -6,10 +6,11 @@
 //
 // One CTA owns 128 points (the MMA's M) and all O outputs (N = O).  Per K
 // step of 128 bytes of a row (64 BF16 or 32 TF32 elements):
-//   * thread t (= TMEM lane t = point t of the tile) evaluates the active HR
-//     bases of the units the step covers, forms the J jet rows, places their
-//     4 non-zeros per unit into 32 registers (the rest of the row is zero) and
-//     stores them into its TMEM lane with tcgen05.st (A operand in TMEM);
+//   * two threads per point (TMEM lane = point of the tile) evaluate the
+//     active HR bases of the units the step covers, form the J jet rows (each
+//     thread half of them), place their 4 non-zeros per unit into 32 registers
+//     (the rest of the row is zero) and store them into the point's TMEM lane
+//     with tcgen05.st (A operand in TMEM);
 //   * one thread issues J x 4 tcgen05.mma (A from TMEM, B = W tile from
 //     shared memory, FP32 accumulators in TMEM, one per jet row) and commits
 //     them to an mbarrier;
@@ -31,7 +32,7 @@
 namespace hrkan {
 namespace {
 
-constexpr int TC_M = 128;           // points per tile = threads per CTA
+constexpr int TC_M = 128;           // points per tile (the MMA M); the CTA has 2 threads per point
 constexpr int TMEM_COLS = 512;
 constexpr uint32_t A_COL0 = 320;    // A region after the accumulators (J * O <= 320 columns)
 constexpr long long WAIT_CYCLES = 2000000000LL;   // ~1 s at 2 GHz
@@ -163,19 +164,98 @@ struct Elem<HRKAN_TF32> {
     }
 };
 
-template <unsigned MASK, int PREC>
-__global__ void __launch_bounds__(TC_M, 1) tc_fwd_kernel(TcLayer p, const __grid_constant__ CUtensorMap tmap) {
+// Stores the jet rows [R0, R1) of this thread's point for one K step into its
+// TMEM lane.  The U units the step touches are the same for every point of
+// the tile (they depend only on the step), so U is a compile-time constant of
+// the call; only each unit's active window (cell) varies per point.
+template <unsigned MASK, int PREC, int R0, int R1, int U>
+__device__ __forceinline__ void build_rows(const TcLayer& p, int I, int n, int64_t N, int64_t ptc, int k0, int jf,
+                                           uint32_t a_taddr) {
     using JT = Jet<MASK>;
     using E = Elem<PREC>;
     constexpr int J = JT::J;
-    constexpr int MAXU = 4;   // units one K step can touch (n >= 17 for BF16)
+    constexpr int NR = R1 - R0;
+    constexpr int NS = E::PER_WORD == 2 ? 3 : 4;   // words the 4 values of a unit can span
+    if constexpr (NR > 0) {
+        int w0[U];
+        uint32_t x[U][NR][NS];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = jf + u;
+            float z[J];
+#pragma unroll
+            for (int r = 0; r < J; ++r) z[r] = p.z[(int64_t(r) * I + j) * N + ptc];
+            Active<3, 4, 2> b;
+            b.eval(z[0], p.g);
+            float a[J][4];
+            JT::template rows<4>(z, b.v, b.d1, b.d2, a);
+            const int P = j * n + b.c - k0;   // element offset of the first active basis in this step
+            if constexpr (E::PER_WORD == 2) {
+                // 4 BF16 values at elements P..P+3 span words P>>1 .. (P+3)>>1
+                const bool odd = (P & 1) != 0;
+                w0[u] = (P - (odd ? 1 : 0)) / 2;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const uint32_t e0 = E::bits(a[R0 + r][0]), e1 = E::bits(a[R0 + r][1]);
+                    const uint32_t e2 = E::bits(a[R0 + r][2]), e3 = E::bits(a[R0 + r][3]);
+                    x[u][r][0] = odd ? (e0 << 16) : (e0 | (e1 << 16));
+                    x[u][r][1] = odd ? (e1 | (e2 << 16)) : (e2 | (e3 << 16));
+                    x[u][r][2] = odd ? e3 : 0u;
+                }
+            } else {
+                w0[u] = P;
+#pragma unroll
+                for (int r = 0; r < NR; ++r)
+#pragma unroll
+                    for (int k = 0; k < NS; ++k) x[u][r][k] = E::bits(a[R0 + r][k]);
+            }
+            // a basis index outside [0, n) has value 0 already (Active masks it)
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            uint32_t v[32];
+#pragma unroll
+            for (int w = 0; w < 32; ++w) {
+                uint32_t acc = 0u;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int d = w - w0[u];
+#pragma unroll
+                    for (int k = 0; k < NS; ++k) acc |= (d == k) ? x[u][r][k] : 0u;
+                }
+                v[w] = acc;
+            }
+            tmem_st32(a_taddr + uint32_t((R0 + r) * 32), v);
+        }
+    }
+}
+
+template <unsigned MASK, int PREC, int R0, int R1>
+__device__ __forceinline__ void build_rows_u(int U, const TcLayer& p, int I, int n, int64_t N, int64_t ptc, int k0,
+                                             int jf, uint32_t a_taddr) {
+    switch (U) {
+        case 1: build_rows<MASK, PREC, R0, R1, 1>(p, I, n, N, ptc, k0, jf, a_taddr); break;
+        case 2: build_rows<MASK, PREC, R0, R1, 2>(p, I, n, N, ptc, k0, jf, a_taddr); break;
+        case 3: build_rows<MASK, PREC, R0, R1, 3>(p, I, n, N, ptc, k0, jf, a_taddr); break;
+        default: build_rows<MASK, PREC, R0, R1, 4>(p, I, n, N, ptc, k0, jf, a_taddr); break;
+    }
+}
+
+template <unsigned MASK, int PREC>
+__global__ void __launch_bounds__(2 * TC_M, 1) tc_fwd_kernel(TcLayer p, const __grid_constant__ CUtensorMap tmap) {
+    using JT = Jet<MASK>;
+    using E = Elem<PREC>;
+    constexpr int J = JT::J;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ __align__(8) uint64_t bar_tma[2];
     __shared__ __align__(8) uint64_t bar_mma;
     __shared__ uint32_t tmem_base_sh;
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    // 256 threads: thread t works on point (t mod 128) of the tile, i.e. TMEM lane
+    // t mod 128; threads 0..127 build jet rows [0, JA), threads 128..255 rows [JA, J).
+    constexpr int JA = (J + 1) / 2;
+    const int tid = threadIdx.x, warp = tid >> 5, row = tid & (TC_M - 1), half = tid >> 7;
     const int O = p.O, I = p.I, n = p.g.n;
     const uint32_t b_bytes = uint32_t(O) * 128u;
     uint8_t* bbuf[2] = {smem, smem + b_bytes};
@@ -196,11 +276,11 @@ __global__ void __launch_bounds__(TC_M, 1) tc_fwd_kernel(TcLayer p, const __grid
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = tmem_base_sh;
-    const uint32_t lane_base = uint32_t(warp * 32) << 16;
+    const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
     const uint32_t idesc = idesc_of(E::FMT, O);
 
     const int64_t N = p.N;
-    const int64_t pt = int64_t(blockIdx.x) * TC_M + tid;
+    const int64_t pt = int64_t(blockIdx.x) * TC_M + row;
     const bool valid = pt < N;
     const int64_t ptc = valid ? pt : N - 1;   // idle lanes compute on a real point, results dropped
 
@@ -221,65 +301,14 @@ __global__ void __launch_bounds__(TC_M, 1) tc_fwd_kernel(TcLayer p, const __grid
             tma_pending[buf ^ 1] = true;
         }
         // ---- A rows of this step into TMEM
-        constexpr int NS = E::PER_WORD == 2 ? 3 : 4;   // words the 4 values of a unit can span
-        const int k0 = s * E::PER_STEP;
-        const int jf = k0 / n;
-        int w0[MAXU];
-        uint32_t x[MAXU][J][NS];
-#pragma unroll
-        for (int u = 0; u < MAXU; ++u) {
-            const int j = jf + u;
-            w0[u] = -100;   // no words
-#pragma unroll
-            for (int r = 0; r < J; ++r)
-#pragma unroll
-                for (int k = 0; k < NS; ++k) x[u][r][k] = 0u;
-            if (j < I && j * n < k0 + E::PER_STEP) {
-                float z[J];
-#pragma unroll
-                for (int r = 0; r < J; ++r) z[r] = p.z[(int64_t(r) * I + j) * N + ptc];
-                Active<3, 4, 2> b;
-                b.eval(z[0], p.g);
-                float a[J][4];
-                JT::template rows<4>(z, b.v, b.d1, b.d2, a);
-                const int P = j * n + b.c - k0;   // element offset of the first active basis
-                if constexpr (E::PER_WORD == 2) {
-                    // 4 BF16 values at elements P..P+3 span words P>>1 .. (P+3)>>1
-                    const bool odd = (P & 1) != 0;
-                    w0[u] = (P - (odd ? 1 : 0)) / 2;
-#pragma unroll
-                    for (int r = 0; r < J; ++r) {
-                        const uint32_t e0 = E::bits(a[r][0]), e1 = E::bits(a[r][1]);
-                        const uint32_t e2 = E::bits(a[r][2]), e3 = E::bits(a[r][3]);
-                        x[u][r][0] = odd ? (e0 << 16) : (e0 | (e1 << 16));
-                        x[u][r][1] = odd ? (e1 | (e2 << 16)) : (e2 | (e3 << 16));
-                        x[u][r][2] = odd ? e3 : 0u;
-                    }
-                } else {
-                    w0[u] = P;
-#pragma unroll
-                    for (int r = 0; r < J; ++r)
-#pragma unroll
-                        for (int k = 0; k < NS; ++k) x[u][r][k] = E::bits(a[r][k]);
-                }
-                // a basis index outside [0, n) has value 0 already (Active masks it)
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < J; ++r) {
-            uint32_t v[32];
-#pragma unroll
-            for (int w = 0; w < 32; ++w) {
-                uint32_t acc = 0u;
-#pragma unroll
-                for (int u = 0; u < MAXU; ++u) {
-                    const int d = w - w0[u];
-#pragma unroll
-                    for (int k = 0; k < NS; ++k) acc |= (d == k) ? x[u][r][k] : 0u;
-                }
-                v[w] = acc;
-            }
-            tmem_st32(tbase + lane_base + A_COL0 + uint32_t(r * 32), v);
+        {
+            const int k0 = s * E::PER_STEP;
+            const int jf = k0 / n;
+            const int jl = min(I - 1, (k0 + E::PER_STEP - 1) / n);
+            const int U = jl - jf + 1;   // same for every point of the tile
+            const uint32_t a_taddr = tbase + lane_base + A_COL0;
+            if (half == 0) build_rows_u<MASK, PREC, 0, JA>(U, p, I, n, N, ptc, k0, jf, a_taddr);
+            else build_rows_u<MASK, PREC, JA, J>(U, p, I, n, N, ptc, k0, jf, a_taddr);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
@@ -313,9 +342,9 @@ __global__ void __launch_bounds__(TC_M, 1) tc_fwd_kernel(TcLayer p, const __grid
         if (__syncthreads_or(!ok)) { failed = 1; break; }
     }
     if (!failed) {
-        // ---- epilogue: accumulators -> output jets [J][O][N]
-#pragma unroll
-        for (int r = 0; r < J; ++r) {
+        // ---- epilogue: accumulators -> output jets [J][O][N] (each half its own rows)
+        const int r0 = half == 0 ? 0 : JA, r1 = half == 0 ? JA : J;
+        for (int r = r0; r < r1; ++r) {
             for (int c = 0; c < O; c += 16) {
                 uint32_t v[16];
                 tmem_ld16(tbase + lane_base + uint32_t(r * O + c), v);
@@ -392,7 +421,7 @@ cudaError_t launch_mask(const TcLayer& p, const CUtensorMap& map, cudaStream_t s
         }
     }
     const unsigned grid = unsigned((p.N + TC_M - 1) / TC_M);
-    kern<<<grid, TC_M, want, s>>>(p, map);
+    kern<<<grid, 2 * TC_M, want, s>>>(p, map);
     return cudaGetLastError();
 }
 
