@@ -1,0 +1,54 @@
+"""Training outcome: the relative L2 error of the trained solution against the
+manufactured Poisson solution sin(a pi x) sin(b pi y) on a 100 x 100 test grid
+(the paper's Poisson test set size), FP32 vs the BF16 tensor-core forward.
+The BF16 run must end within 1.2x of the FP32 run's error."""
+import numpy as np
+import pytest
+
+from paper_2409_14248_gb300 import build, capi, inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    capi.load_library()
+
+
+def _train_and_eval(prec, steps=300):
+    w = inputs.WORKLOADS["poisson_2_64x3_1"]
+    widths, G = [2, 32, 32, 1], 10          # a net the BF16 contraction evaluates to < 2e-2
+    n = G + 3
+    P = sum(widths[l] * widths[l + 1] * n for l in range(3))
+    d = inputs.make(w, n_int=8192, n_bnd=1024)
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    W = dev(inputs.init_weights(P, 7))
+    h = capi.hrkan_init(capi.make_cfg(widths, G, prec=prec, flags=capi.HRKAN_FLAG_LAYERWISE))
+    try:
+        prob = capi.make_problem(capi.HRKAN_POISSON, 2.0, 2.0)
+        xi, xb, gb = dev(d["x_int"]), dev(d["x_bnd"]), dev(d["g_bnd"])
+        loss = torch.zeros(3, dtype=torch.float64, device="cuda")
+        for t in range(1, steps + 1):
+            capi.hrkan_train_step(h, prob, W, xi, xi.shape[1], xb, gb, xb.shape[1], 1e-2, 0.9, 0.999, 1e-8, t, loss)
+        capi.hrkan_sync_status(h)
+        g = np.linspace(-1, 1, 100)
+        X, Y = np.meshgrid(g, g, indexing="ij")
+        xt = np.stack([X.ravel(), Y.ravel()]).astype(np.float32)
+        u = torch.zeros((1, xt.shape[1]), device="cuda")
+        capi.hrkan_forward_jets(h, W, dev(xt), xt.shape[1], 0x1, u)
+        u = u.cpu().numpy()[0].astype(np.float64)
+    finally:
+        capi.hrkan_destroy(h)
+    truth = np.sin(2 * np.pi * xt[0]) * np.sin(2 * np.pi * xt[1])
+    return np.linalg.norm(u - truth) / np.linalg.norm(truth), loss.cpu().numpy()[0]
+
+
+def test_bf16_training_reaches_the_fp32_error():
+    e32, l32 = _train_and_eval(capi.HRKAN_FP32)
+    e16, l16 = _train_and_eval(capi.HRKAN_BF16)
+    print(f"\nrel-L2 FP32 {e32:.4e} (loss {l32:.3e}); BF16 {e16:.4e} (loss {l16:.3e})")
+    assert e32 < 0.5                        # the FP32 run learned something
+    assert e16 <= 1.2 * e32
