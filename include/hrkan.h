@@ -77,10 +77,12 @@ typedef struct hrkan_cfg {
     int m;                           /* HR order of Eq. 2; 4 */
     int prec;                        /* enum hrkan_prec: arithmetic of the jet contraction.  BF16 /
                                         TF32: hidden layers with 16 <= O <= 64 (O % 16 == 0) contract
-                                        on tcgen05 tensor cores (FP32 accumulation in TMEM); the first
-                                        and last layers and the backward stay FP32.  Needs the
-                                        layer-wise path (a shape without a fused kernel, or
-                                        HRKAN_FLAG_LAYERWISE) */
+                                        on tcgen05 tensor cores (FP32 accumulation in TMEM) when
+                                        G + k >= 13 (BF16) or >= 7 (TF32); the first and last layers,
+                                        other hidden layers and the backward stay FP32
+                                        (hrkan_profile_read(HRKAN_KERNEL_TENSOR) counts the tensor
+                                        launches).  Needs the layer-wise path (a shape without a
+                                        fused kernel, or HRKAN_FLAG_LAYERWISE) */
     double grid_lo, grid_hi;         /* grid_lo < grid_hi */
     int n_instances;                 /* independent networks sharing the shape (>= 1) */
     int flags;                       /* HRKAN_FLAG_*; 0 = defaults */

@@ -237,7 +237,9 @@ __device__ __forceinline__ void build_rows_u(int U, const TcLayer& p, int I, int
         case 1: build_rows<MASK, PREC, R0, R1, 1>(p, I, n, N, ptc, k0, jf, a_taddr); break;
         case 2: build_rows<MASK, PREC, R0, R1, 2>(p, I, n, N, ptc, k0, jf, a_taddr); break;
         case 3: build_rows<MASK, PREC, R0, R1, 3>(p, I, n, N, ptc, k0, jf, a_taddr); break;
-        default: build_rows<MASK, PREC, R0, R1, 4>(p, I, n, N, ptc, k0, jf, a_taddr); break;
+        case 4: build_rows<MASK, PREC, R0, R1, 4>(p, I, n, N, ptc, k0, jf, a_taddr); break;
+        case 5: build_rows<MASK, PREC, R0, R1, 5>(p, I, n, N, ptc, k0, jf, a_taddr); break;
+        default: build_rows<MASK, PREC, R0, R1, 6>(p, I, n, N, ptc, k0, jf, a_taddr); break;
     }
 }
 
@@ -442,8 +444,8 @@ bool tc_layer_supported(int prec, int I, int O, int n, unsigned mask) {
     if (prec != HRKAN_BF16 && prec != HRKAN_TF32) return false;
     if (O < 16 || O > 64 || O % 16 != 0 || J * O > int(A_COL0)) return false;
     const int per_step = prec == HRKAN_BF16 ? 64 : 32;
-    // a K step of per_step elements touches at most ceil((per_step-1)/n) + 1 units; the kernel holds 4
-    if ((per_step - 1 + n - 1) / n + 1 > 4) return false;
+    // a K step of per_step elements touches at most ceil((per_step-1)/n) + 1 units; the kernel holds 6
+    if ((per_step - 1 + n - 1) / n + 1 > 6) return false;
     return I >= 1 && (mask == 0x01u || mask == 0x0Fu || mask == 0x1Fu);
 }
 
