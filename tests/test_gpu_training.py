@@ -1,7 +1,8 @@
 """Training outcome: the relative L2 error of the trained solution against the
 manufactured Poisson solution sin(pi x) sin(pi y) on a 100 x 100 test grid
 (the paper's Poisson test set size), FP32 vs the BF16 tensor-core forward, on a
-[2,32,32,1] G=20 network trained for 600 full-batch Adam steps on 8192 + 1024 points.
+[2,16,16,1] G=13 network trained for 2000 full-batch Adam steps (lr 3e-3) on
+8192 + 1024 points from N(0, 0.01^2) initial weights.
 The BF16 run must end within 1.2x of the FP32 run's error."""
 import numpy as np
 import pytest
@@ -19,14 +20,16 @@ def _lib():
     capi.load_library()
 
 
-def _train_and_eval(prec, steps=600):
+def _train_and_eval(prec, steps=2000):
     w = inputs.WORKLOADS["poisson_2_64x3_1"]
-    widths, G = [2, 32, 32, 1], 20          # a net the BF16 contraction evaluates to ~2e-2
+    widths, G = [2, 16, 16, 1], 13          # hidden 16 -> 16 layer on the tensor cores (n = 16)
     n = G + 3
     P = sum(widths[l] * widths[l + 1] * n for l in range(3))
     d = inputs.make(w, n_int=8192, n_bnd=1024)
     dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
-    W = dev(inputs.init_weights(P, 7))
+    # N(0, 0.01^2): with N(0, 0.1^2) the second-derivative jets of this finer, deeper net
+    # start ~1e4 (loss ~1e7) and neither precision trains in a few thousand steps
+    W = dev(inputs.init_weights(P, 7, sigma=0.01))
     h = capi.hrkan_init(capi.make_cfg(widths, G, prec=prec, flags=capi.HRKAN_FLAG_LAYERWISE))
     try:
         prob = capi.make_problem(capi.HRKAN_POISSON, 1.0, 1.0)
@@ -34,7 +37,7 @@ def _train_and_eval(prec, steps=600):
         xi, xb, gb = dev(d["x_int"]), dev(d["x_bnd"]), dev(d["g_bnd"])
         loss = torch.zeros(3, dtype=torch.float64, device="cuda")
         for t in range(1, steps + 1):
-            capi.hrkan_train_step(h, prob, W, xi, xi.shape[1], xb, gb, xb.shape[1], 1e-2, 0.9, 0.999, 1e-8, t, loss)
+            capi.hrkan_train_step(h, prob, W, xi, xi.shape[1], xb, gb, xb.shape[1], 3e-3, 0.9, 0.999, 1e-8, t, loss)
         capi.hrkan_sync_status(h)
         tensor_launches = capi.hrkan_profile_read(h, capi.HRKAN_KERNEL_TENSOR)[1]
         assert (tensor_launches > 0) == (prec != capi.HRKAN_FP32)
@@ -55,5 +58,5 @@ def test_bf16_training_reaches_the_fp32_error():
     e32, l32 = _train_and_eval(capi.HRKAN_FP32)
     e16, l16 = _train_and_eval(capi.HRKAN_BF16)
     print(f"\nrel-L2 FP32 {e32:.4e} (loss {l32:.3e}); BF16 {e16:.4e} (loss {l16:.3e})")
-    assert e32 < 0.5                        # the FP32 run learned something
+    assert e32 < 0.3                        # the FP32 run learned the solution
     assert e16 <= 1.2 * e32
