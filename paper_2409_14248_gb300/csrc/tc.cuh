@@ -1,4 +1,4 @@
-// Tensor-core forward of one hidden layer (tc_jets.cu).
+// Tensor-core forward of one hidden layer (tc_kernel.cuh, tc_jets.cu, tc_np*.cu).
 #pragma once
 
 #include <cstdint>
@@ -14,17 +14,22 @@ struct TcLayer {
     float* y;         // output jets [J][O][N]
     int I, O;
     int64_t N;
-    int ksteps;       // K steps of 128 bytes per row
+    int ks;           // K slots (one MMA each) over the padded units
+    int nbox;         // W tiles of 128 bytes per row (4 slots each)
+    int ring;         // A ring slots in TMEM
+    int ntiles;       // tiles of 128 points
     Grid g;
     int* status;      // device error word (HRKAN_ETIMEOUT on a timed-out wait)
 };
 
-// Layers the tensor-core kernel handles: 16 <= O <= 64, O % 16 == 0, J*O <= 320.
+// Layers the tensor-core kernel handles: 16 <= O <= 64, O % 16 == 0,
+// J * O <= 320, n <= 64, masks 0x01 / 0x0F / 0x1F.
 bool tc_layer_supported(int prec, int I, int O, int n, unsigned mask);
 // Elements of the converted weight buffer of one layer.
 int64_t tc_w_elems(int O, int I, int n, int prec);
 // Converts W (float32 [O][I][n]) into w_prep (tc_w_elems elements of 2 or 4
-// bytes) and runs the tensor-core contraction: y = jets of the layer output.
+// bytes, units padded) and runs the tensor-core contraction: y = jets of the
+// layer output.
 cudaError_t tc_forward_layer(const float* W, void* w_prep, const float* z, float* y, int I, int O, int64_t N,
                              const Grid& g, int prec, unsigned mask, int* status, cudaStream_t s);
 

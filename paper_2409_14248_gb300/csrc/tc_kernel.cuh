@@ -1,0 +1,483 @@
+// Tensor-core (tcgen05 / TMEM / TMA) contraction of the stacked jet rows with
+// the layer weights, for the hidden layers of wide networks (Sections 1-3:
+// the KAN layer as a matrix operation; Eq. 2 bases).
+//
+//   Y_r[p, o] = sum_k A_r[p, k] W[o, k],   r = 0..J-1 jet rows
+//
+// K runs over the layer's input units, each padded to NP elements: k = j*NP + i
+// (basis i of unit j; W and A are zero for i >= n).  Per point and unit only the
+// k+1 = 4 bases c..c+3 are non-zero, so A is built on the fly, never stored.
+//
+// One persistent CTA per SM walks tiles of 128 points (the MMA's M); every jet
+// row has an FP32 accumulator of 128 x O in TMEM (N = O).  Warp roles:
+//   warps 0-3  producers: thread = point = TMEM lane.  For each slot of 16 BF16
+//              (8 TF32) K elements they write the point's A words of every jet
+//              row into a ring of slots in TMEM (tcgen05.st), then run the
+//              tile's epilogue (tcgen05.ld -> y);
+//   warp 4     one thread issues, per slot, J tcgen05.mma (A from TMEM, B = W
+//              from shared memory) and commits them to the slot's "empty" barrier;
+//   warp 5     one thread streams W tiles of 128 bytes per row into a ring of
+//              shared-memory buffers with TMA (128-byte swizzle, K-major).
+// The placement of the 4 non-zeros is the cost that matters: with NP fixed at
+// compile time, the unit and word offset of every word of a slot are constants
+// of an unrolled period of slots, so a word of one jet row costs a short select
+// among the unit's 3 (BF16) or 4 (TF32) packed window words.
+//
+// Every mbarrier wait is bounded (~1 s) and also gives up when another role has
+// given up: the CTA then records HRKAN_ETIMEOUT in a device status word, waits
+// (bounded) for its own copies and MMAs, frees its TMEM and returns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "tc.cuh"
+
+namespace hrkan {
+namespace tck {
+
+constexpr int TILE_M = 128;
+constexpr int TMEM_COLS = 512;
+constexpr int NB = 8;            // W tiles (4 slots each) in flight
+constexpr int RS_MAX = 8;        // A ring slots
+constexpr int THREADS = 192;     // 4 producer warps, the MMA warp, the TMA warp
+constexpr long long WAIT_CYCLES = 2000000000LL;   // ~1 s at 2 GHz
+constexpr int ERR_TIMEOUT = -5;                   // HRKAN_ETIMEOUT
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for the phase of the given parity.  Gives up (false) after WAIT_CYCLES,
+// raising *abort, or as soon as *abort is raised by another thread.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    if (mbar_test(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > WAIT_CYCLES) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+// Bounded wait that ignores *abort (draining own work on the way out).
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity))
+        if (clock64() - t0 > WAIT_CYCLES) return;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= uint64_t((saddr & 0x3FFFF) >> 4);      // start address
+    d |= uint64_t(1) << 16;                     // leading byte offset (unused for swizzled K-major)
+    d |= uint64_t(1024 >> 4) << 32;             // stride byte offset: next 8-row group
+    d |= uint64_t(1) << 46;                     // descriptor version
+    d |= uint64_t(2) << 61;                     // layout: 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulate, A/B format fmt (1 = BF16 under
+// kind::f16, 2 = TF32 under kind::tf32), both K-major, M = 128, N.
+__host__ __device__ constexpr uint32_t idesc_of(int fmt, int N) {
+    return (1u << 4) | (uint32_t(fmt) << 7) | (uint32_t(fmt) << 10) | (uint32_t(N >> 3) << 17) |
+           (uint32_t(TILE_M >> 4) << 24);
+}
+
+template <int PREC>
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    if constexpr (PREC == HRKAN_TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+// Element type of the contraction.
+template <int PREC>
+struct Elem;
+template <>
+struct Elem<HRKAN_BF16> {
+    static constexpr int PER_WORD = 2;   // elements per 32-bit word (TMEM column)
+    static constexpr int SLOT = 16;      // K elements per MMA (one slot)
+    static constexpr int BOX = 64;       // K elements per 128-byte W row tile
+    static constexpr int NWIN = 3;       // words a unit's 4 values can span
+    static constexpr int FMT = 1;
+};
+template <>
+struct Elem<HRKAN_TF32> {
+    static constexpr int PER_WORD = 1, SLOT = 8, BOX = 32, NWIN = 4, FMT = 2;
+};
+
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+    __nv_bfloat162 t = __floats2bfloat162_rn(lo, hi);   // round to nearest even; lo in bits 0..15
+    return *reinterpret_cast<uint32_t*>(&t);
+}
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+
+// Compile-time shape of the slot stream for units padded to NP elements.
+template <int PREC, int NP>
+struct Period {
+    using E = Elem<PREC>;
+    static constexpr int NW = NP / E::PER_WORD;                    // words per unit
+    static constexpr int SW = E::SLOT / E::PER_WORD;               // words per slot (8)
+    static constexpr int WORDS = NW / gcd_c(NW, SW) * SW;          // lcm(NW, SW)
+    static constexpr int PS = WORDS / SW;                          // slots per period
+    static constexpr int PU = WORDS / NW;                          // units per period
+    static_assert(NP % E::PER_WORD == 0, "a unit starts on a word boundary");
+    static_assert(SW == 8, "one slot is 8 TMEM columns");
+};
+
+// The non-zero words of one unit in every jet row: the word offset h of the
+// first one (relative to the unit's first word) and the packed words.
+template <int J, int NWIN>
+struct UnitWin {
+    int h;
+    uint32_t y[J][NWIN];
+};
+
+// Active bases (Eq. 2) of the unit value z[0], the jet rows of its 4 non-zero
+// columns, rounded to the MMA type and packed into the window words.
+template <unsigned MASK, int PREC>
+__device__ __forceinline__ void unit_window(const float* z, const Grid& g, bool live,
+                                            UnitWin<Jet<MASK>::J, Elem<PREC>::NWIN>& w) {
+    using JT = Jet<MASK>;
+    constexpr int J = JT::J;
+    Active<3, 4, 2> b;
+    b.eval(z[0], g);
+    float a[J][4];
+    JT::template rows<4>(z, b.v, b.d1, b.d2, a);
+    if constexpr (PREC == HRKAN_BF16) {
+        // values of bases c..c+3 sit at elements c..c+3 of the unit: words
+        // h = c >> 1 .. h + 2 (the third only when c is odd)
+        const bool odd = (b.c & 1) != 0;
+        w.h = b.c >> 1;   // arithmetic shift: floor(c / 2) also for c < 0
+#pragma unroll
+        for (int r = 0; r < J; ++r) {
+            const uint32_t lo = bf16x2_bits(a[r][0], a[r][1]), hi = bf16x2_bits(a[r][2], a[r][3]);
+            w.y[r][0] = odd ? (lo << 16) : lo;
+            w.y[r][1] = odd ? __byte_perm(lo, hi, 0x5432) : hi;
+            w.y[r][2] = odd ? (hi >> 16) : 0u;
+        }
+    } else {
+        w.h = b.c;
+#pragma unroll
+        for (int r = 0; r < J; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w.y[r][q] = tf32_bits(a[r][q]);
+    }
+    // bases outside [0, n) are zero already; a unit past the layer's inputs places nothing
+    if (!live) w.h = -(1 << 24);
+}
+
+template <unsigned MASK, int PREC, int NP>
+__global__ void __launch_bounds__(THREADS, 1) tc_fwd_kernel(TcLayer p, const __grid_constant__ CUtensorMap tmap) {
+    using JT = Jet<MASK>;
+    using E = Elem<PREC>;
+    using PD = Period<PREC, NP>;
+    constexpr int J = JT::J, NWIN = E::NWIN, PU = PD::PU, PS = PD::PS, NW = PD::NW;
+    using Win = UnitWin<J, NWIN>;
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t bar_full[RS_MAX], bar_empty[RS_MAX], bar_wfull[NB], bar_wempty[NB];
+    __shared__ __align__(8) uint64_t bar_accfull, bar_accempty, bar_drain;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int O = p.O, I = p.I, RS = p.ring, KS = p.ks;
+    const uint32_t b_bytes = uint32_t(O) * 128u;
+    const uint32_t A0 = uint32_t(J * O);            // first A column; accumulators at r * O
+    const uint32_t RW = uint32_t(RS * 8);           // ring words per jet row
+    volatile int* abort = &abort_sh;
+
+    if (tid == 0) {
+        for (int s = 0; s < RS_MAX; ++s) {
+            mbar_init(&bar_full[s], 4);    // one arrive per producer warp
+            mbar_init(&bar_empty[s], 1);   // tcgen05.commit
+        }
+        for (int b = 0; b < NB; ++b) {
+            mbar_init(&bar_wfull[b], 1);
+            mbar_init(&bar_wempty[b], 1);
+        }
+        mbar_init(&bar_accfull, 1);
+        mbar_init(&bar_accempty, 4);
+        mbar_init(&bar_drain, 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tmem_base_sh;
+    const int64_t N = p.N;
+    const int ntiles = p.ntiles;
+
+    if (warp < 4) {
+        // ------------------------------------------------------------ producers
+        const uint32_t lane_base = uint32_t(warp * 32) << 16;
+        const int row = warp * 32 + lane;
+        int slot = 0;
+        uint32_t ph = 0;            // parity of the current pass over the ring
+        int pend_slot = -1;         // slot whose stores still have to be published
+        const int nper = (KS + PS - 1) / PS;
+        int it = 0;
+        // z of the first period of this CTA's first tile; later ones are loaded one period ahead
+        float zn[PU][J];
+        {
+            const int64_t pt0 = int64_t(blockIdx.x) * TILE_M + row;
+            const float* zp0 = p.z + (pt0 < N ? pt0 : N - 1);
+#pragma unroll
+            for (int u = 0; u < PU; ++u)
+#pragma unroll
+                for (int r = 0; r < J; ++r) zn[u][r] = u < I ? zp0[(int64_t(r) * I + u) * N] : 0.0f;
+        }
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int64_t pt = int64_t(tile) * TILE_M + row;
+            const bool valid = pt < N;
+            const int64_t ptc = valid ? pt : N - 1;   // idle lanes compute on a real point, results dropped
+            const float* zp = p.z + ptc;
+            const int64_t ptn = pt + int64_t(gridDim.x) * TILE_M;   // same lane of the next tile
+            const float* zpn = p.z + (ptn < N ? ptn : N - 1);
+            for (int per = 0; per < nper; ++per) {
+                float zc[PU][J];
+#pragma unroll
+                for (int u = 0; u < PU; ++u)
+#pragma unroll
+                    for (int r = 0; r < J; ++r) zc[u][r] = zn[u][r];
+                if (per + 1 < nper) {
+#pragma unroll
+                    for (int u = 0; u < PU; ++u) {
+                        const int j = (per + 1) * PU + u;
+#pragma unroll
+                        for (int r = 0; r < J; ++r) zn[u][r] = j < I ? zp[(int64_t(r) * I + j) * N] : 0.0f;
+                    }
+                } else if (tile + int(gridDim.x) < ntiles) {
+#pragma unroll
+                    for (int u = 0; u < PU; ++u)
+#pragma unroll
+                        for (int r = 0; r < J; ++r) zn[u][r] = u < I ? zpn[(int64_t(r) * I + u) * N] : 0.0f;
+                }
+                Win uw[PU];
+#pragma unroll
+                for (int S = 0; S < PS; ++S) {
+                    // units whose first word falls in this slot are evaluated here
+#pragma unroll
+                    for (int u = 0; u < PU; ++u)
+                        if ((u * NW) / 8 == S) unit_window<MASK, PREC>(zc[u], p.g, per * PU + u < I, uw[u]);
+                    const int t = per * PS + S;
+                    if (t < KS) {
+                        uint32_t v[J][8];
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) {
+                            const int gw = S * 8 + w, u = gw / NW, lw = gw % NW;
+#pragma unroll
+                            for (int r = 0; r < J; ++r) {
+                                uint32_t x = 0u;
+#pragma unroll
+                                for (int d = NWIN - 1; d >= 0; --d) x = (uw[u].h == lw - d) ? uw[u].y[r][d] : x;
+                                v[r][w] = x;
+                            }
+                        }
+                        if (pend_slot >= 0) {   // publish the previous slot (its stores had time to land)
+                            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&bar_full[pend_slot]);
+                        }
+                        if (!__all_sync(0xffffffffu, mbar_wait(&bar_empty[slot], ph ^ 1u, abort))) goto done;
+                        tc_fence_after();
+#pragma unroll
+                        for (int r = 0; r < J; ++r)
+                            tmem_st8(tbase + lane_base + A0 + uint32_t(r) * RW + uint32_t(slot * 8), v[r]);
+                        pend_slot = slot;
+                        if (++slot == RS) { slot = 0; ph ^= 1u; }
+                    }
+                }
+            }
+            if (pend_slot >= 0) {
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar_full[pend_slot]);
+                pend_slot = -1;
+            }
+            // ---- epilogue: accumulators -> y [J][O][N]
+            if (!__all_sync(0xffffffffu, mbar_wait(&bar_accfull, uint32_t(it & 1), abort))) goto done;
+            tc_fence_after();
+#pragma unroll 1
+            for (int r = 0; r < J; ++r) {
+#pragma unroll 1
+                for (int c = 0; c < O; c += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(tbase + lane_base + uint32_t(r * O + c), v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (valid) {
+                        float* yp = p.y + (int64_t(r) * O + c) * N + pt;
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) yp[int64_t(e) * N] = __uint_as_float(v[e]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_accempty);
+        }
+    } else if (warp == 4) {
+        // ------------------------------------------------------------ MMA issue
+        if (lane == 0) {
+            const uint32_t idesc = idesc_of(E::FMT, O);
+            int slot = 0, wb = 0;
+            uint32_t ph = 0, wph = 0;
+            bool issued = false;
+            int it = 0;
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+                if (!mbar_wait(&bar_accempty, uint32_t(it & 1) ^ 1u, abort)) break;
+                tc_fence_after();
+                uint64_t bd = 0;
+                for (int t = 0; t < KS; ++t) {
+                    if ((t & 3) == 0) {
+                        if (!mbar_wait(&bar_wfull[wb], wph, abort)) goto mma_out;
+                        bd = sdesc_sw128(smem_u32(smem + size_t(wb) * b_bytes));
+                    }
+                    if (!mbar_wait(&bar_full[slot], ph, abort)) goto mma_out;
+                    tc_fence_after();
+#pragma unroll
+                    for (int r = 0; r < J; ++r)
+                        mma_ts<PREC>(tbase + uint32_t(r * O), tbase + A0 + uint32_t(r) * RW + uint32_t(slot * 8),
+                                     bd + uint64_t((t & 3) * 2),   // +32 bytes per slot (descriptor counts 16 B)
+                                     idesc, t > 0 ? 1u : 0u);
+                    issued = true;
+                    mma_commit(&bar_empty[slot]);
+                    if (++slot == RS) { slot = 0; ph ^= 1u; }
+                    if ((t & 3) == 3 || t == KS - 1) {
+                        mma_commit(&bar_wempty[wb]);
+                        if (++wb == NB) { wb = 0; wph ^= 1u; }
+                    }
+                }
+                mma_commit(&bar_accfull);
+            }
+        mma_out:
+            if (*abort && issued) {   // wait (bounded) for this thread's MMAs before TMEM is freed
+                mma_commit(&bar_drain);
+                mbar_drain(&bar_drain, 0u);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ W tiles by TMA
+        if (lane == 0) {
+            const int nbox = p.nbox;
+            int wb = 0;
+            uint32_t wph = 0;
+            uint32_t used = 0u, last_par = 0u;   // bit b: buffer b has had a load / parity of its last one
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+                for (int bx = 0; bx < nbox; ++bx) {
+                    if (!mbar_wait(&bar_wempty[wb], wph ^ 1u, abort)) goto tma_out;
+                    mbar_expect_tx(&bar_wfull[wb], b_bytes);
+                    tma_load_2d(smem + size_t(wb) * b_bytes, &tmap, &bar_wfull[wb], bx * E::BOX, 0);
+                    used |= 1u << wb;
+                    last_par = (last_par & ~(1u << wb)) | (wph << wb);
+                    if (++wb == NB) { wb = 0; wph ^= 1u; }
+                }
+            }
+        tma_out:
+            if (*abort)
+                for (int b = 0; b < NB; ++b)
+                    if ((used >> b) & 1u) mbar_drain(&bar_wfull[b], (last_par >> b) & 1u);
+        }
+    }
+done:
+    __syncwarp();
+    if (warp < 4) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && *abort) atomicExch(p.status, ERR_TIMEOUT);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS) : "memory");
+}
+
+// Host side: launch one instantiation (tc_np*.cu).
+template <unsigned MASK, int PREC, int NP>
+cudaError_t launch_one(const TcLayer& p, const CUtensorMap& map, cudaStream_t s);
+
+}  // namespace tck
+}  // namespace hrkan
