@@ -10,13 +10,14 @@
 //
 // One persistent CTA per SM walks tiles of 128 points (the MMA's M); every jet
 // row has an FP32 accumulator of 128 x O in TMEM (N = O).  Warp roles:
-//   warps 0-3  producers: thread = point = TMEM lane.  For each slot of 16 BF16
-//              (8 TF32) K elements they write the point's A words of every jet
-//              row into a ring of slots in TMEM (tcgen05.st), then run the
-//              tile's epilogue (tcgen05.ld -> y);
-//   warp 4     one thread issues, per slot, J tcgen05.mma (A from TMEM, B = W
+//   warps 0-3  producers: thread = point = TMEM lane (with PARTS > 1, warps
+//              w, w+4, ... share the lanes of quarter w and split the units).  For
+//              each slot of 16 BF16 (8 TF32) K elements they write the point's A
+//              words of every jet row into a ring of slots in TMEM
+//              (tcgen05.st), then run the tile's epilogue (tcgen05.ld -> y);
+//   next warp  one thread issues, per slot, J tcgen05.mma (A from TMEM, B = W
 //              from shared memory) and commits them to the slot's "empty" barrier;
-//   warp 5     one thread streams W tiles of 128 bytes per row into a ring of
+//   last warp  one thread streams W tiles of 128 bytes per row into a ring of
 //              shared-memory buffers with TMA (128-byte swizzle, K-major).
 // The placement of the 4 non-zeros is the cost that matters: with NP fixed at
 // compile time, the unit and word offset of every word of a slot are constants
@@ -42,7 +43,9 @@ constexpr int TILE_M = 128;
 constexpr int TMEM_COLS = 512;
 constexpr int NB = 8;            // W tiles (4 slots each) in flight
 constexpr int RS_MAX = 8;        // A ring slots
-constexpr int THREADS = 192;     // 4 producer warps, the MMA warp, the TMA warp
+constexpr int PARTS = 1;                  // producer warps per TMEM lane quarter
+constexpr int PRODUCER_WARPS = 4 * PARTS;
+constexpr int THREADS = 32 * PRODUCER_WARPS + 64;   // producer warps, the MMA warp, the TMA warp
 constexpr long long WAIT_CYCLES = 2000000000LL;   // ~1 s at 2 GHz
 constexpr int ERR_TIMEOUT = -5;                   // HRKAN_ETIMEOUT
 
@@ -242,45 +245,240 @@ __device__ __forceinline__ void unit_window(const float* z, const Grid& g, bool 
     if (!live) w.h = -(1 << 24);
 }
 
+// Work split between the PARTS producer warps of a TMEM lane quarter: warp
+// part q takes the units u of a period with u % PARTS == q (the period is
+// repeated until it holds a multiple of PARTS units), evaluates only those and
+// stores only their words of each slot.
+template <int PREC, int NP, int PARTS>
+struct Split {
+    using PD = Period<PREC, NP>;
+    static constexpr int MUL = PARTS / gcd_c(PD::PU, PARTS);
+    static constexpr int PU = PD::PU * MUL;
+    static constexpr int PS = PD::PS * MUL;
+    static constexpr int NW = PD::NW;
+};
+
+__device__ __forceinline__ void mbar_arrive_if(uint64_t* bar, bool pred) {
+    asm volatile("{\n\t.reg .pred P;\n\tsetp.ne.b32 P, %1, 0;\n\t@P mbarrier.arrive.shared::cta.b64 _, [%0];\n\t}" ::"r"(
+                     smem_u32(bar)),
+                 "r"(int(pred))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, uint32_t a, uint32_t b) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(a), "r"(b) : "memory");
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(a), "r"(b), "r"(c),
+                 "r"(d)
+                 : "memory");
+}
+
+// Shared state of one CTA.
+struct TcShared {
+    uint64_t full[RS_MAX], empty[RS_MAX], wfull[NB], wempty[NB];
+    uint64_t accfull, accempty, drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+// One producer warp (part PART of its lane quarter): A words of its units for
+// every slot of every tile of this CTA, then its rows of each tile's epilogue.
+template <unsigned MASK, int PREC, int NP, int PART>
+__device__ __forceinline__ void produce(const TcLayer& p, TcShared& sh, uint32_t tbase, int quarter, int lane) {
+    using JT = Jet<MASK>;
+    using E = Elem<PREC>;
+    using SP = Split<PREC, NP, PARTS>;
+    constexpr int J = JT::J, NWIN = E::NWIN, PU = SP::PU, PS = SP::PS, NW = SP::NW;
+    constexpr int HU = PU / PARTS;   // units of this warp per period: u = PARTS * i + PART
+    using Win = UnitWin<J, NWIN>;
+    volatile int* abort = &sh.abort;
+    const int O = p.O, I = p.I, RS = p.ring, KS = p.ks;
+    const int64_t N = p.N;
+    const int ntiles = p.ntiles;
+    const uint32_t A0 = uint32_t(J * O), RW = uint32_t(RS * 8);
+    const uint32_t lane_base = uint32_t(quarter * 32) << 16;
+    const int row = quarter * 32 + lane;
+    int slot = 0;
+    uint32_t ph = 0;        // parity of the current pass over the ring
+    int pend_slot = -1;     // slot whose stores still have to be published
+    const int nper = (KS + PS - 1) / PS;
+
+    // z of this warp's units of the first period of the CTA's first tile; later
+    // periods are loaded one period ahead
+    float zn[HU][J];
+    {
+        const int64_t pt0 = int64_t(blockIdx.x) * TILE_M + row;
+        const float* zp0 = p.z + (pt0 < N ? pt0 : N - 1);
+#pragma unroll
+        for (int i = 0; i < HU; ++i) {
+            const int j = PARTS * i + PART;
+#pragma unroll
+            for (int r = 0; r < J; ++r) zn[i][r] = j < I ? zp0[(int64_t(r) * I + j) * N] : 0.0f;
+        }
+    }
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int64_t pt = int64_t(tile) * TILE_M + row;
+        const bool valid = pt < N;
+        const float* zp = p.z + (valid ? pt : N - 1);   // idle lanes compute on a real point, results dropped
+        const int64_t ptn = pt + int64_t(gridDim.x) * TILE_M;   // same lane of the next tile
+        const float* zpn = p.z + (ptn < N ? ptn : N - 1);
+        for (int per = 0; per < nper; ++per) {
+            float zc[HU][J];
+#pragma unroll
+            for (int i = 0; i < HU; ++i)
+#pragma unroll
+                for (int r = 0; r < J; ++r) zc[i][r] = zn[i][r];
+            if (per + 1 < nper) {
+#pragma unroll
+                for (int i = 0; i < HU; ++i) {
+                    const int j = (per + 1) * PU + PARTS * i + PART;
+#pragma unroll
+                    for (int r = 0; r < J; ++r) zn[i][r] = j < I ? zp[(int64_t(r) * I + j) * N] : 0.0f;
+                }
+            } else if (tile + int(gridDim.x) < ntiles) {
+#pragma unroll
+                for (int i = 0; i < HU; ++i) {
+                    const int j = PARTS * i + PART;
+#pragma unroll
+                    for (int r = 0; r < J; ++r) zn[i][r] = j < I ? zpn[(int64_t(r) * I + j) * N] : 0.0f;
+                }
+            }
+            Win uw[HU];
+#pragma unroll
+            for (int S = 0; S < PS; ++S) {
+                // this warp's units whose first word falls in this slot are evaluated here
+#pragma unroll
+                for (int i = 0; i < HU; ++i)
+                    if (((PARTS * i + PART) * NW) / 8 == S)
+                        unit_window<MASK, PREC>(zc[i], p.g, per * PU + PARTS * i + PART < I, uw[i]);
+                const int t = per * PS + S;
+                if (t < KS) {
+                    // own(w): word w of this slot belongs to a unit of this warp (a constant)
+                    uint32_t v[J][8];
+#pragma unroll
+                    for (int w = 0; w < 8; ++w) {
+                        const int gw = S * 8 + w, u = gw / NW, lw = gw % NW;
+                        if (u % PARTS == PART) {
+                            const int i = u / PARTS;
+#pragma unroll
+                            for (int r = 0; r < J; ++r) {
+                                // word = y[d] for d = lw - h in [0, NWIN), else 0
+                                uint32_t x = 0u;
+#pragma unroll
+                                for (int d = NWIN - 1; d >= 0; --d) x = (uw[i].h == lw - d) ? uw[i].y[r][d] : x;
+                                v[r][w] = x;
+                            }
+                        }
+                    }
+                    if (pend_slot >= 0) {   // publish the previous slot (its stores had time to land)
+                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                        tc_fence_before();
+                        __syncwarp();
+                        mbar_arrive_if(&sh.full[pend_slot], lane == 0);
+                    }
+                    if (!__all_sync(0xffffffffu, mbar_wait(&sh.empty[slot], ph ^ 1u, abort))) return;
+                    tc_fence_after();
+                    const uint32_t col = tbase + lane_base + A0 + uint32_t(slot * 8);
+#define OWN(w) ((((S * 8 + (w)) / NW) % PARTS) == PART)
+                    const bool all8 = OWN(0) && OWN(2) && OWN(4) && OWN(6);
+#pragma unroll
+                    for (int r = 0; r < J; ++r) {
+                        const uint32_t c = col + uint32_t(r) * RW;
+                        if (all8) {
+                            tmem_st8(c, v[r]);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 8; q += 4) {
+                                if (OWN(q) && OWN(q + 2)) {
+                                    tmem_st4(c + q, v[r][q], v[r][q + 1], v[r][q + 2], v[r][q + 3]);
+                                } else {
+                                    if (OWN(q)) tmem_st2(c + q, v[r][q], v[r][q + 1]);
+                                    if (OWN(q + 2)) tmem_st2(c + q + 2, v[r][q + 2], v[r][q + 3]);
+                                }
+                            }
+                        }
+                    }
+#undef OWN
+                    pend_slot = slot;
+                    if (++slot == RS) { slot = 0; ph ^= 1u; }
+                }
+            }
+        }
+        if (pend_slot >= 0) {
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            __syncwarp();
+            mbar_arrive_if(&sh.full[pend_slot], lane == 0);
+            pend_slot = -1;
+        }
+        // ---- epilogue: this warp's jet rows of the accumulators -> y [J][O][N]
+        if (!__all_sync(0xffffffffu, mbar_wait(&sh.accfull, uint32_t(it & 1), abort))) return;
+        tc_fence_after();
+#pragma unroll 1
+        for (int r = PART; r < J; r += PARTS) {
+#pragma unroll 1
+            for (int c = 0; c < O; c += 16) {
+                uint32_t v[16];
+                tmem_ld16(tbase + lane_base + uint32_t(r * O + c), v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (valid) {
+                    float* yp = p.y + (int64_t(r) * O + c) * N + pt;
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) yp[int64_t(e) * N] = __uint_as_float(v[e]);
+                }
+            }
+        }
+        tc_fence_before();
+        __syncwarp();
+        mbar_arrive_if(&sh.accempty, lane == 0);
+    }
+}
+
+// Runs produce<..., part> for a warp-uniform runtime part.
+template <unsigned MASK, int PREC, int NP, int Q>
+__device__ __forceinline__ void produce_part(int part, const TcLayer& p, TcShared& sh, uint32_t tbase, int quarter,
+                                             int lane) {
+    if constexpr (Q < PARTS) {
+        if (part == Q) produce<MASK, PREC, NP, Q>(p, sh, tbase, quarter, lane);
+        else produce_part<MASK, PREC, NP, Q + 1>(part, p, sh, tbase, quarter, lane);
+    }
+}
+
 template <unsigned MASK, int PREC, int NP>
 __global__ void __launch_bounds__(THREADS, 1) tc_fwd_kernel(TcLayer p, const __grid_constant__ CUtensorMap tmap) {
     using JT = Jet<MASK>;
     using E = Elem<PREC>;
-    using PD = Period<PREC, NP>;
-    constexpr int J = JT::J, NWIN = E::NWIN, PU = PD::PU, PS = PD::PS, NW = PD::NW;
-    using Win = UnitWin<J, NWIN>;
+    constexpr int J = JT::J;
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t bar_full[RS_MAX], bar_empty[RS_MAX], bar_wfull[NB], bar_wempty[NB];
-    __shared__ __align__(8) uint64_t bar_accfull, bar_accempty, bar_drain;
-    __shared__ uint32_t tmem_base_sh;
-    __shared__ int abort_sh;
+    __shared__ TcShared sh;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int O = p.O, I = p.I, RS = p.ring, KS = p.ks;
+    const int O = p.O, RS = p.ring, KS = p.ks;
     const uint32_t b_bytes = uint32_t(O) * 128u;
     const uint32_t A0 = uint32_t(J * O);            // first A column; accumulators at r * O
     const uint32_t RW = uint32_t(RS * 8);           // ring words per jet row
-    volatile int* abort = &abort_sh;
+    volatile int* abort = &sh.abort;
 
     if (tid == 0) {
         for (int s = 0; s < RS_MAX; ++s) {
-            mbar_init(&bar_full[s], 4);    // one arrive per producer warp
-            mbar_init(&bar_empty[s], 1);   // tcgen05.commit
+            mbar_init(&sh.full[s], PRODUCER_WARPS);   // one arrive per producer warp
+            mbar_init(&sh.empty[s], 1);               // tcgen05.commit
         }
         for (int b = 0; b < NB; ++b) {
-            mbar_init(&bar_wfull[b], 1);
-            mbar_init(&bar_wempty[b], 1);
+            mbar_init(&sh.wfull[b], 1);
+            mbar_init(&sh.wempty[b], 1);
         }
-        mbar_init(&bar_accfull, 1);
-        mbar_init(&bar_accempty, 4);
-        mbar_init(&bar_drain, 1);
-        abort_sh = 0;
+        mbar_init(&sh.accfull, 1);
+        mbar_init(&sh.accempty, PRODUCER_WARPS);
+        mbar_init(&sh.drain, 1);
+        sh.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
                      "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -288,121 +486,12 @@ __global__ void __launch_bounds__(THREADS, 1) tc_fwd_kernel(TcLayer p, const __g
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tbase = tmem_base_sh;
-    const int64_t N = p.N;
+    const uint32_t tbase = sh.tmem_base;
     const int ntiles = p.ntiles;
 
-    if (warp < 4) {
-        // ------------------------------------------------------------ producers
-        const uint32_t lane_base = uint32_t(warp * 32) << 16;
-        const int row = warp * 32 + lane;
-        int slot = 0;
-        uint32_t ph = 0;            // parity of the current pass over the ring
-        int pend_slot = -1;         // slot whose stores still have to be published
-        const int nper = (KS + PS - 1) / PS;
-        int it = 0;
-        // z of the first period of this CTA's first tile; later ones are loaded one period ahead
-        float zn[PU][J];
-        {
-            const int64_t pt0 = int64_t(blockIdx.x) * TILE_M + row;
-            const float* zp0 = p.z + (pt0 < N ? pt0 : N - 1);
-#pragma unroll
-            for (int u = 0; u < PU; ++u)
-#pragma unroll
-                for (int r = 0; r < J; ++r) zn[u][r] = u < I ? zp0[(int64_t(r) * I + u) * N] : 0.0f;
-        }
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-            const int64_t pt = int64_t(tile) * TILE_M + row;
-            const bool valid = pt < N;
-            const int64_t ptc = valid ? pt : N - 1;   // idle lanes compute on a real point, results dropped
-            const float* zp = p.z + ptc;
-            const int64_t ptn = pt + int64_t(gridDim.x) * TILE_M;   // same lane of the next tile
-            const float* zpn = p.z + (ptn < N ? ptn : N - 1);
-            for (int per = 0; per < nper; ++per) {
-                float zc[PU][J];
-#pragma unroll
-                for (int u = 0; u < PU; ++u)
-#pragma unroll
-                    for (int r = 0; r < J; ++r) zc[u][r] = zn[u][r];
-                if (per + 1 < nper) {
-#pragma unroll
-                    for (int u = 0; u < PU; ++u) {
-                        const int j = (per + 1) * PU + u;
-#pragma unroll
-                        for (int r = 0; r < J; ++r) zn[u][r] = j < I ? zp[(int64_t(r) * I + j) * N] : 0.0f;
-                    }
-                } else if (tile + int(gridDim.x) < ntiles) {
-#pragma unroll
-                    for (int u = 0; u < PU; ++u)
-#pragma unroll
-                        for (int r = 0; r < J; ++r) zn[u][r] = u < I ? zpn[(int64_t(r) * I + u) * N] : 0.0f;
-                }
-                Win uw[PU];
-#pragma unroll
-                for (int S = 0; S < PS; ++S) {
-                    // units whose first word falls in this slot are evaluated here
-#pragma unroll
-                    for (int u = 0; u < PU; ++u)
-                        if ((u * NW) / 8 == S) unit_window<MASK, PREC>(zc[u], p.g, per * PU + u < I, uw[u]);
-                    const int t = per * PS + S;
-                    if (t < KS) {
-                        uint32_t v[J][8];
-#pragma unroll
-                        for (int w = 0; w < 8; ++w) {
-                            const int gw = S * 8 + w, u = gw / NW, lw = gw % NW;
-#pragma unroll
-                            for (int r = 0; r < J; ++r) {
-                                uint32_t x = 0u;
-#pragma unroll
-                                for (int d = NWIN - 1; d >= 0; --d) x = (uw[u].h == lw - d) ? uw[u].y[r][d] : x;
-                                v[r][w] = x;
-                            }
-                        }
-                        if (pend_slot >= 0) {   // publish the previous slot (its stores had time to land)
-                            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                            tc_fence_before();
-                            __syncwarp();
-                            if (lane == 0) mbar_arrive(&bar_full[pend_slot]);
-                        }
-                        if (!__all_sync(0xffffffffu, mbar_wait(&bar_empty[slot], ph ^ 1u, abort))) goto done;
-                        tc_fence_after();
-#pragma unroll
-                        for (int r = 0; r < J; ++r)
-                            tmem_st8(tbase + lane_base + A0 + uint32_t(r) * RW + uint32_t(slot * 8), v[r]);
-                        pend_slot = slot;
-                        if (++slot == RS) { slot = 0; ph ^= 1u; }
-                    }
-                }
-            }
-            if (pend_slot >= 0) {
-                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&bar_full[pend_slot]);
-                pend_slot = -1;
-            }
-            // ---- epilogue: accumulators -> y [J][O][N]
-            if (!__all_sync(0xffffffffu, mbar_wait(&bar_accfull, uint32_t(it & 1), abort))) goto done;
-            tc_fence_after();
-#pragma unroll 1
-            for (int r = 0; r < J; ++r) {
-#pragma unroll 1
-                for (int c = 0; c < O; c += 16) {
-                    uint32_t v[16];
-                    tmem_ld16(tbase + lane_base + uint32_t(r * O + c), v);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (valid) {
-                        float* yp = p.y + (int64_t(r) * O + c) * N + pt;
-#pragma unroll
-                        for (int e = 0; e < 16; ++e) yp[int64_t(e) * N] = __uint_as_float(v[e]);
-                    }
-                }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar_accempty);
-        }
-    } else if (warp == 4) {
+    if (warp < PRODUCER_WARPS) {
+        produce_part<MASK, PREC, NP, 0>(warp >> 2, p, sh, tbase, warp & 3, lane);
+    } else if (warp == PRODUCER_WARPS) {
         // ------------------------------------------------------------ MMA issue
         if (lane == 0) {
             const uint32_t idesc = idesc_of(E::FMT, O);
@@ -411,15 +500,15 @@ __global__ void __launch_bounds__(THREADS, 1) tc_fwd_kernel(TcLayer p, const __g
             bool issued = false;
             int it = 0;
             for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-                if (!mbar_wait(&bar_accempty, uint32_t(it & 1) ^ 1u, abort)) break;
+                if (!mbar_wait(&sh.accempty, uint32_t(it & 1) ^ 1u, abort)) break;
                 tc_fence_after();
                 uint64_t bd = 0;
                 for (int t = 0; t < KS; ++t) {
                     if ((t & 3) == 0) {
-                        if (!mbar_wait(&bar_wfull[wb], wph, abort)) goto mma_out;
+                        if (!mbar_wait(&sh.wfull[wb], wph, abort)) goto mma_out;
                         bd = sdesc_sw128(smem_u32(smem + size_t(wb) * b_bytes));
                     }
-                    if (!mbar_wait(&bar_full[slot], ph, abort)) goto mma_out;
+                    if (!mbar_wait(&sh.full[slot], ph, abort)) goto mma_out;
                     tc_fence_after();
 #pragma unroll
                     for (int r = 0; r < J; ++r)
@@ -427,19 +516,19 @@ __global__ void __launch_bounds__(THREADS, 1) tc_fwd_kernel(TcLayer p, const __g
                                      bd + uint64_t((t & 3) * 2),   // +32 bytes per slot (descriptor counts 16 B)
                                      idesc, t > 0 ? 1u : 0u);
                     issued = true;
-                    mma_commit(&bar_empty[slot]);
+                    mma_commit(&sh.empty[slot]);
                     if (++slot == RS) { slot = 0; ph ^= 1u; }
                     if ((t & 3) == 3 || t == KS - 1) {
-                        mma_commit(&bar_wempty[wb]);
+                        mma_commit(&sh.wempty[wb]);
                         if (++wb == NB) { wb = 0; wph ^= 1u; }
                     }
                 }
-                mma_commit(&bar_accfull);
+                mma_commit(&sh.accfull);
             }
         mma_out:
             if (*abort && issued) {   // wait (bounded) for this thread's MMAs before TMEM is freed
-                mma_commit(&bar_drain);
-                mbar_drain(&bar_drain, 0u);
+                mma_commit(&sh.drain);
+                mbar_drain(&sh.drain, 0u);
             }
         }
     } else {
@@ -451,9 +540,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_fwd_kernel(TcLayer p, const __g
             uint32_t used = 0u, last_par = 0u;   // bit b: buffer b has had a load / parity of its last one
             for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
                 for (int bx = 0; bx < nbox; ++bx) {
-                    if (!mbar_wait(&bar_wempty[wb], wph ^ 1u, abort)) goto tma_out;
-                    mbar_expect_tx(&bar_wfull[wb], b_bytes);
-                    tma_load_2d(smem + size_t(wb) * b_bytes, &tmap, &bar_wfull[wb], bx * E::BOX, 0);
+                    if (!mbar_wait(&sh.wempty[wb], wph ^ 1u, abort)) goto tma_out;
+                    mbar_expect_tx(&sh.wfull[wb], b_bytes);
+                    tma_load_2d(smem + size_t(wb) * b_bytes, &tmap, &sh.wfull[wb], bx * E::BOX, 0);
                     used |= 1u << wb;
                     last_par = (last_par & ~(1u << wb)) | (wph << wb);
                     if (++wb == NB) { wb = 0; wph ^= 1u; }
@@ -462,12 +551,11 @@ __global__ void __launch_bounds__(THREADS, 1) tc_fwd_kernel(TcLayer p, const __g
         tma_out:
             if (*abort)
                 for (int b = 0; b < NB; ++b)
-                    if ((used >> b) & 1u) mbar_drain(&bar_wfull[b], (last_par >> b) & 1u);
+                    if ((used >> b) & 1u) mbar_drain(&sh.wfull[b], (last_par >> b) & 1u);
         }
     }
-done:
     __syncwarp();
-    if (warp < 4) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    if (warp < PRODUCER_WARPS) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     if (tid == 0 && *abort) atomicExch(p.status, ERR_TIMEOUT);
