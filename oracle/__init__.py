@@ -65,6 +65,8 @@ def _load():
             lib.orc_layer_forward.argtypes = [ctypes.c_int] * 5 + [ctypes.c_double] * 2 + [_dp, _dp, ctypes.c_long,
                                                                                         ctypes.c_uint, _dp,
                                                                                         ctypes.c_int]
+            lib.orc_layer_dw.argtypes = [ctypes.c_int] * 5 + [ctypes.c_double] * 2 + [_dp, _dp, ctypes.c_long,
+                                                                                   ctypes.c_uint, _dp, ctypes.c_int]
             lib.orc_round.argtypes = [ctypes.c_double, ctypes.c_int]
             lib.orc_round.restype = ctypes.c_double
             lib.orc_backward.argtypes = net + [_dp, _dp, ctypes.c_long, ctypes.c_uint, _dp, _dp, ctypes.c_int]
@@ -165,6 +167,21 @@ def layer_forward(I, O, G, k, m, lo, hi, Wl, zin, mask, fmt=EXACT):
                                out.ctypes.data_as(_dp), int(fmt))
     if rc:
         raise ValueError("orc_layer_forward: bad arguments")
+    return out
+
+
+def layer_dw(I, O, G, k, m, lo, hi, zin, gy, mask, fmt=EXACT):
+    """Weight gradient [O*I*n] of one KAN layer for input jets zin[J, I, N] and
+    output-jet gradients gy[J, O, N]; fmt rounds the basis-matrix entries and gy."""
+    lib = _load()
+    z, zp = _d(zin)
+    g, gp = _d(gy)
+    J, _, N = z.shape
+    out = np.zeros(O * I * (G + k))
+    rc = lib.orc_layer_dw(int(I), int(O), int(G), int(k), int(m), float(lo), float(hi), zp, gp, N, int(mask),
+                          out.ctypes.data_as(_dp), int(fmt))
+    if rc:
+        raise ValueError("orc_layer_dw: bad arguments")
     return out
 
 

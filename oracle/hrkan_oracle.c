@@ -336,6 +336,62 @@ int orc_layer_forward(int I, int O, int G, int k, int m, double lo, double hi, c
 }
 
 /*
+ * Weight gradient of one layer for given output-jet gradients (the
+ * contraction of Sections 2-3 differentiated w.r.t. W):
+ *   dW[o][j][i] = sum_p sum_r gy[r][o][p] * A_r[p][j][i]
+ * with the basis-matrix entries A_r of layer_forward (value, first and second
+ * derivative rows of input unit j and basis i).  fmt rounds the A entries and
+ * gy to BF16/TF32 before the FP64 products and sums (the reduced-precision
+ * contraction's inputs); ORC_EXACT rounds nothing.  zin [J][I][N], gy [J][O][N],
+ * dW [O][I][n] overwritten.
+ */
+int orc_layer_dw(int I, int O, int G, int k, int m, double lo, double hi, const double* zin,
+                 const double* gy, long N, unsigned mask, double* dW, int fmt)
+{
+    const int D = 2;
+    int rows[16];
+    int J = mask_rows(mask, D, rows);
+    if (!(mask & 1u)) return -1;
+    int n = G + k;
+    double* s = malloc(sizeof(double) * n);
+    double* e = malloc(sizeof(double) * n);
+    orc_support(G, k, lo, hi, s, e);
+    memset(dW, 0, sizeof(double) * (size_t)O * I * n);
+    double a[16];
+    for (long p = 0; p < N; ++p) {
+        for (int j = 0; j < I; ++j) {
+            double z = 0.0, dz[2] = {0.0, 0.0}, d2z[2] = {0.0, 0.0};
+            for (int r = 0; r < J; ++r) {
+                double v = zin[((long)r * I + j) * N + p];
+                int b = rows[r];
+                if (b == 0) z = v;
+                else if (b <= D) dz[b - 1] = v;
+                else d2z[b - 1 - D] = v;
+            }
+            for (int i = 0; i < n; ++i) {
+                double b[4];
+                orc_hr_basis(m, s[i], e[i], z, b);
+                for (int r = 0; r < J; ++r) {
+                    int bit = rows[r];
+                    double v;
+                    if (bit == 0) v = b[0];
+                    else if (bit <= D) v = b[1] * dz[bit - 1];
+                    else v = b[2] * dz[bit - 1 - D] * dz[bit - 1 - D] + b[1] * d2z[bit - 1 - D];
+                    a[r] = round_to(v, fmt);
+                }
+                for (int o = 0; o < O; ++o) {
+                    double acc = 0.0;
+                    for (int r = 0; r < J; ++r) acc += round_to(gy[((long)r * O + o) * N + p], fmt) * a[r];
+                    dW[((long)o * I + j) * n + i] += acc;
+                }
+            }
+        }
+    }
+    free(s); free(e);
+    return 0;
+}
+
+/*
  * Reverse mode of point_forward.  g*, gd*, gd2* hold dL/d(output jets) of the
  * layer on entry and are overwritten with dL/d(input jets).  dW accumulates.
  */

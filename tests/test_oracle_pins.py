@@ -458,3 +458,64 @@ def test_layer_forward_composes_to_the_network_forward():
         z = oracle.layer_forward(I, O, 6, 3, 4, -1.0, 1.0, W[off: off + O * I * n], z, 0x1F)
         off += O * I * n
     np.testing.assert_allclose(z[:, 0, :], oracle.forward(net, W, x, 0x1F), rtol=1e-12, atol=1e-12)
+
+
+def test_layer_dw_matches_central_differences():
+    """layer_dw is the gradient of sum(gy * layer_forward) w.r.t. the layer weights: the
+    layer output is linear in W, so central differences are exact up to rounding."""
+    I, O, G, N = 3, 4, 5, 7
+    n = G + 3
+    rng = np.random.default_rng(70)
+    z = rng.normal(0, 0.5, (5, I, N))
+    gy = rng.normal(0, 1, (5, O, N))
+    W = rng.normal(0, 0.3, O * I * n)
+    dw = oracle.layer_dw(I, O, G, 3, 4, -1.0, 1.0, z, gy, 0x1F)
+
+    def f(Wv):
+        return float((gy * oracle.layer_forward(I, O, G, 3, 4, -1.0, 1.0, Wv, z, 0x1F)).sum())
+
+    h = 1e-3
+    for i in rng.choice(W.size, 24, replace=False):
+        e = np.zeros_like(W)
+        e[i] = h
+        assert abs((f(W + e) - f(W - e)) / (2 * h) - dw[i]) <= 1e-9 * (1 + abs(dw[i]))
+
+
+def test_layer_dw_of_last_layer_equals_network_backward():
+    """For [2, I, 1], the network backward's last-layer block equals layer_dw of the hidden
+    jets (layer_forward of the coordinate jets) with gy = dL/d(output jets)."""
+    net = dict(widths=[2, 5, 1], G=6, k=3, m=4, lo=-1.0, hi=1.0)
+    n = 9
+    W = np.random.default_rng(71).normal(0, 0.4, oracle.param_count(net))
+    x = np.random.default_rng(72).uniform(-1, 1, (2, 30))
+    g = np.random.default_rng(73).normal(0, 1, (5, 30))
+    full = oracle.backward(net, W, x, 0x1F, g)
+    z = np.zeros((5, 2, 30))
+    z[0] = x
+    z[1, 0] = 1.0
+    z[2, 1] = 1.0
+    hid = oracle.layer_forward(2, 5, 6, 3, 4, -1.0, 1.0, W[: 5 * 2 * n], z, 0x1F)
+    last = oracle.layer_dw(5, 1, 6, 3, 4, -1.0, 1.0, hid, g[:, None, :], 0x1F)
+    np.testing.assert_allclose(last, full[5 * 2 * n:], rtol=1e-12, atol=1e-12)
+
+
+def test_layer_dw_rounding_is_a_no_op_on_representable_inputs():
+    """Knot inputs (cell offset 0, h = 1/8, jets +-1/2 and 0/+-2/+-4) give basis-matrix entries
+    with at most 8 significant bits and gy multiples of 1/8 below 16: rounding to BF16/TF32
+    changes nothing, and a value off the format's grid does change."""
+    I, O, G, lo, hi = 4, 3, 16, -1.0, 1.0
+    h = (hi - lo) / G
+    rng = np.random.default_rng(74)
+    N = 50
+    z = np.zeros((5, I, N))
+    z[0] = lo + rng.integers(-4, G + 4, (I, N)) * h
+    z[1:3] = rng.choice([-0.5, 0.5], (2, I, N))
+    z[3:5] = rng.choice([0.0, -2.0, 2.0, -4.0, 4.0], (2, I, N))
+    gy = rng.integers(-127, 128, (5, O, N)) / 8.0
+    exact = oracle.layer_dw(I, O, G, 3, 4, lo, hi, z, gy, 0x1F)
+    for fmt in (oracle.BF16, oracle.TF32):
+        np.testing.assert_array_equal(oracle.layer_dw(I, O, G, 3, 4, lo, hi, z, gy, 0x1F, fmt), exact)
+    gy2 = gy.copy()
+    gy2[0, 0, 0] = 1.0 + 2.0 ** -12
+    assert not np.array_equal(oracle.layer_dw(I, O, G, 3, 4, lo, hi, z, gy2, 0x1F, oracle.BF16),
+                              oracle.layer_dw(I, O, G, 3, 4, lo, hi, z, gy2, 0x1F))
