@@ -157,6 +157,18 @@ int hrkan_layer_jets(hrkan_t h, int layer, const float* W, const float* z, int64
                      float* y, hrkan_stream_t stream);
 
 /*
+ * Weight gradient of one layer (reverse mode of hrkan_layer_jets w.r.t. that
+ * layer's weights): dW[o][j][i] = sum_p sum_r gy[r][o][p] * A_r[p][j][i] with
+ * the basis-matrix entries A_r of the layer (Sections 2-3), z = input jets
+ * [J][I][N] (l = 0: the coordinates [2][N]), gy = dL/d(output jets) [J][O][N],
+ * dW = [O][I][n] float32 (written).  Runs the kernel the network backward uses
+ * for that layer (tensor cores for BF16 hidden layers), then a fixed-order sum
+ * of its partial rows.  N = 0 writes zeros.
+ */
+int hrkan_layer_dw(hrkan_t h, int layer, const float* z, const float* gy, int64_t N, unsigned jet_mask,
+                   float* dW, hrkan_stream_t stream);
+
+/*
  * Residual and loss (Eq. 3-4 / Eq. 6-8) from precomputed jets.
  *   x_int [2][N_int], jets_int [J][N_int] under jet_mask (Poisson needs u_xx,
  *   u_yy; Burgers needs u, u_x, u_t, u_xx), u_bnd / g_bnd [N_bnd] network

@@ -369,6 +369,26 @@ int wide_forward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsig
     return HRKAN_OK;
 }
 
+// Weight gradient of layer l into partial rows [d.row0, d.row0 + d.GP): the
+// tensor-core kernel for BF16 hidden layers it supports, else FP32 SIMT.
+int layer_dw(hrkan_t h, const WideDw& d, int l, unsigned mask, cudaStream_t s) {
+    cudaError_t e;
+    if (l > 0 && tc_dw_supported(h->cfg.prec, d.I, d.O, h->n, mask)) {
+        int rc = HRKAN_OK;
+        const int64_t el = tc_dw_gy_elems(jets_of(mask), d.O, d.N);
+        float* gbf = ws_get(h, 11, size_t((el + 1) / 2), &rc);   // 2-byte elements in 4-byte slots
+        if (!gbf) return rc;
+        ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
+        e = tc_dw_layer(d.z, d.gy, gbf, d.I, d.O, d.N, d.g, mask, d.partial, d.P, d.col0, d.row0, d.GP, h->status, s);
+    } else {
+        ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
+        e = wide_dw_layer(d, mask, l == 0, s);
+    }
+    if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no layer kernel", mask);
+    if (e != cudaSuccess) return cuda_fail(e, "weight-gradient launch");
+    return HRKAN_OK;
+}
+
 // Backward of one point set: weight-gradient partial rows [row0, row0 + GP)
 // of h->partial and, for every layer but the first, the input adjoint.  Layer
 // inputs come from `tape`, or are recomputed from x when tape is null.
@@ -406,13 +426,8 @@ int wide_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsi
         d.row0 = row0;
         d.GP = h->wide_gp;
         d.g = h->grid;
+        if ((rc = layer_dw(h, d, l, mask, s))) return rc;
         cudaError_t e;
-        {
-            ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
-            e = wide_dw_layer(d, mask, l == 0, s);
-        }
-        if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no layer kernel", mask);
-        if (e != cudaSuccess) return cuda_fail(e, "weight-gradient launch");
         if (l > 0) {
             WideLayer a = wide_layer(h, W, l, N);
             a.z = zl;
@@ -1008,6 +1023,38 @@ int hrkan_layer_jets(hrkan_t h, int layer, const float* W, const float* z, int64
     if (int rc = use_device(h)) return rc;
     // forward_layer takes the whole network's weights and offsets into them
     return forward_layer(h, W - h->layer_off[layer], layer, z, y, N, jet_mask, (cudaStream_t)stream);
+}
+
+int hrkan_layer_dw(hrkan_t h, int layer, const float* z, const float* gy, int64_t N, unsigned jet_mask, float* dW,
+                   hrkan_stream_t stream) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (layer < 0 || layer >= h->L) return fail(HRKAN_EINVAL, "layer %d outside [0, %d)", layer, h->L);
+    if (N < 0) return fail(HRKAN_EINVAL, "N=%lld", (long long)N);
+    if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
+    if (!z || !gy || !dW) return fail(HRKAN_EINVAL, "NULL device pointer");
+    if (int rc = use_device(h)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int I = h->cfg.widths[layer], O = h->cfg.widths[layer + 1];
+    const int64_t cols = int64_t(O) * I * h->n;
+    if (N == 0) {
+        cudaError_t e = cudaMemsetAsync(dW, 0, sizeof(float) * size_t(cols), s);
+        return e == cudaSuccess ? HRKAN_OK : cuda_fail(e, "memset");
+    }
+    WideDw d{};
+    d.z = z;
+    d.gy = gy;
+    d.I = I;
+    d.O = O;
+    d.N = N;
+    d.partial = h->partial;
+    d.P = h->P;
+    d.col0 = h->layer_off[layer];
+    d.row0 = 0;
+    d.GP = h->wide_gp;
+    d.g = h->grid;
+    if (int rc = layer_dw(h, d, layer, jet_mask, s)) return rc;
+    cudaError_t e = sum_rows(h->partial + d.col0, h->wide_gp, h->P, cols, dW, s);
+    return e == cudaSuccess ? HRKAN_OK : cuda_fail(e, "row sum launch");
 }
 
 }  // extern "C"

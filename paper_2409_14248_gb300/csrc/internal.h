@@ -87,6 +87,9 @@ struct ResidualParams {
 cudaError_t launch_residual(const ResidualParams& p, int grid, cudaStream_t s);
 bool residual_mask_supported(unsigned mask);
 
+// out[c] = fixed-order sum of rows [0, rows) of src (row stride `stride`), c < cols.
+cudaError_t sum_rows(const float* src, int rows, int64_t stride, int64_t cols, float* out, cudaStream_t s);
+
 // Sets the thread's last-error message and returns code.
 int set_last_error(int code, const char* msg);
 

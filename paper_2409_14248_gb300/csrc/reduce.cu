@@ -5,6 +5,8 @@
 // gradient and optionally applies Adam with float64 moments; block 0 also
 // finishes the loss (Eq. 4 / Eq. 8) from per-block float64 partials with a
 // fixed-order pairwise float64 tree.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace hrkan {
@@ -240,4 +242,25 @@ cudaError_t launch_batch_reduce(const BatchReduceParams& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+}  // namespace hrkan
+
+namespace hrkan {
+namespace {
+// out[c] = sum over rows r (in order) of src[r * stride + c].
+__global__ void sum_rows_kernel(const float* __restrict__ src, int rows, int64_t stride, int64_t cols,
+                                float* __restrict__ out) {
+    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < cols; c += int64_t(gridDim.x) * blockDim.x) {
+        float a = 0.0f;
+        for (int r = 0; r < rows; ++r) a += src[int64_t(r) * stride + c];
+        out[c] = a;
+    }
+}
+}  // namespace
+
+cudaError_t sum_rows(const float* src, int rows, int64_t stride, int64_t cols, float* out, cudaStream_t s) {
+    if (cols <= 0) return cudaSuccess;
+    const int grid = int(std::min<int64_t>((cols + 255) / 256, 4096));
+    sum_rows_kernel<<<grid, 256, 0, s>>>(src, rows, stride, cols, out);
+    return cudaGetLastError();
+}
 }  // namespace hrkan

@@ -33,4 +33,16 @@ int64_t tc_w_elems(int O, int I, int n, int prec);
 cudaError_t tc_forward_layer(const float* W, void* w_prep, const float* z, float* y, int I, int O, int64_t N,
                              const Grid& g, int prec, unsigned mask, int* status, cudaStream_t s);
 
+// Tensor-core weight gradient of one hidden layer (tc_dw.cu): BF16 inputs,
+// FP32 accumulation, 16 <= O <= 64 with O % 16 == 0, n <= 64.
+bool tc_dw_supported(int prec, int I, int O, int n, unsigned mask);
+// BF16 elements of the gy copy the kernel needs (J * O * N rounded up to 64 points).
+int64_t tc_dw_gy_elems(int J, int O, int64_t N);
+// dW of the layer (columns [col0, col0 + O*I*n) of rows [row0, row0 + nchunk)
+// of partial [rows][P]) from input jets z [J][I][N] and output-jet gradients
+// gy [J][O][N]; gy_bf is scratch of tc_dw_gy_elems 2-byte elements.
+cudaError_t tc_dw_layer(const float* z, const float* gy, void* gy_bf, int I, int O, int64_t N, const Grid& g,
+                        unsigned mask, float* partial, int64_t P, int64_t col0, int row0, int nchunk, int* status,
+                        cudaStream_t s);
+
 }  // namespace hrkan

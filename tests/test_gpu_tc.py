@@ -227,3 +227,75 @@ def test_tc_full_size_forward_sampled():
         assert relerr(got[0], rounded[0]) < 0.05 * relerr(rounded[0], exact[0]) + floor[0]
     finally:
         capi.hrkan_destroy(h)
+
+
+# ------------------------------------------------------------------ weight gradient (BF16)
+
+def _layer_dw(prec, I, O, G, z, gy, mask, N, lo=-1.0, hi=1.0):
+    cfg = capi.make_cfg([2, I, O, 1], G, lo=lo, hi=hi, prec=prec, flags=capi.HRKAN_FLAG_LAYERWISE)
+    h = capi.hrkan_init(cfg)
+    try:
+        dW = torch.full((O * I * (G + 3),), float("nan"), device="cuda")
+        capi.hrkan_profile_enable(h, True)
+        capi.hrkan_layer_dw(h, 1, _dev(z), _dev(gy), N, mask, dW)
+        capi.hrkan_sync_status(h)
+        tensor_launches = capi.hrkan_profile_read(h, capi.HRKAN_KERNEL_TENSOR)[1]
+        return dW.cpu().numpy(), tensor_launches
+    finally:
+        capi.hrkan_destroy(h)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("mask", [0x01, 0x0F, 0x1F])
+def test_tc_layer_dw_matches_rounding_aware_oracle(shape, mask):
+    """BF16 tensor-core weight gradient of one hidden layer on seeded random jets: equal to the
+    oracle gradient with BF16-rounded basis-matrix entries and gy up to float32 accumulation
+    (FLIP covers entries whose float32 and float64 versions round differently), far from the
+    unrounded one."""
+    I, O, G = shape
+    N = 389
+    J = oracle.n_rows(mask)
+    z = inputs.layer_jets(I, N, mask, seed=I * 17 + O)
+    gy = np.random.default_rng(G).normal(0, 1, (J, O, N)).astype(np.float32)
+    got, launches = _layer_dw(capi.HRKAN_BF16, I, O, G, z, gy, mask, N)
+    assert launches == 1
+    rounded = oracle.layer_dw(I, O, G, 3, 4, -1.0, 1.0, z, gy, mask, oracle.BF16)
+    exact = oracle.layer_dw(I, O, G, 3, 4, -1.0, 1.0, z, gy, mask)
+    e_impl, e_fmt = relerr(got, rounded), relerr(rounded, exact)
+    assert e_impl < 2e-5 + FLIP * e_fmt, (e_impl, e_fmt)
+    assert e_fmt > 4 * e_impl
+
+
+@pytest.mark.parametrize("shape", KNOT_SHAPES)
+def test_tc_layer_dw_exact_on_knots(shape):
+    """Knot inputs and gy multiples of 1/8 below 16 (exact in BF16): the tensor-core gradient
+    equals the exact oracle up to float32 accumulation; N spans several 64-point groups in some
+    chunks and none in others."""
+    I, O, G, lo, hi = shape
+    n = G + 3
+    h = (hi - lo) / G
+    N = 64 * 40 + 333   # 46 groups of 64 over 38 point chunks: some chunks take two (ring wrap), none empty
+    rng = np.random.default_rng(I * 7 + G)
+    z = np.zeros((5, I, N), np.float32)
+    z[0] = lo + rng.integers(-5, G + 5, (I, N)) * h
+    z[1:3] = rng.choice([-0.5, 0.5], (2, I, N))
+    z[3:5] = rng.choice([0.0, -2.0, 2.0, -4.0, 4.0], (2, I, N))
+    gy = (rng.integers(-127, 128, (5, O, N)) / 8.0).astype(np.float32)
+    got, launches = _layer_dw(capi.HRKAN_BF16, I, O, G, z, gy, 0x1F, N, lo, hi)
+    assert launches == 1
+    exact = oracle.layer_dw(I, O, G, 3, 4, lo, hi, z, gy, 0x1F)
+    assert np.array_equal(oracle.layer_dw(I, O, G, 3, 4, lo, hi, z, gy, 0x1F, oracle.BF16), exact)
+    assert relerr(got, exact) < 1e-6
+    assert np.abs(got - exact).max() <= 1e-5 * np.abs(exact).max()
+
+
+@pytest.mark.parametrize("mask", [0x01, 0x1F])
+def test_fp32_layer_dw_matches_oracle(mask):
+    """The same entry point on an FP32 handle runs the SIMT weight-gradient kernel."""
+    I, O, G, N = 32, 32, 20, 389
+    J = oracle.n_rows(mask)
+    z = inputs.layer_jets(I, N, mask, seed=5)
+    gy = np.random.default_rng(6).normal(0, 1, (J, O, N)).astype(np.float32)
+    got, launches = _layer_dw(capi.HRKAN_FP32, I, O, G, z, gy, mask, N)
+    assert launches == 0
+    assert relerr(got, oracle.layer_dw(I, O, G, 3, 4, -1.0, 1.0, z, gy, mask)) < 1e-5
