@@ -2,8 +2,12 @@
 manufactured Poisson solution sin(pi x) sin(pi y) on a 100 x 100 test grid
 (the paper's Poisson test set size), FP32 vs the BF16 tensor-core forward, on a
 [2,16,16,1] G=13 network trained for 2000 full-batch Adam steps (lr 3e-3) on
-8192 + 1024 points from N(0, 0.01^2) initial weights.
-The BF16 run must end within 1.2x of the FP32 run's error."""
+8192 + 1024 points from N(0, 0.01^2) initial weights.  The BF16 path runs the
+hidden layer's forward and weight gradient on the tensor cores.
+Single runs of either precision end within about +-20% of each other depending
+on the initial-weight seed (measured ratios 0.84-1.21 at 2000 steps over four
+seeds), so the comparison is on the mean error over four seeds: the BF16 mean
+must be within 1.2x of the FP32 mean."""
 import numpy as np
 import pytest
 
@@ -20,7 +24,10 @@ def _lib():
     capi.load_library()
 
 
-def _train_and_eval(prec, steps=2000):
+SEEDS = (7, 11, 13, 17)
+
+
+def _train_and_eval(prec, seed, steps=2000):
     w = inputs.WORKLOADS["poisson_2_64x3_1"]
     widths, G = [2, 16, 16, 1], 13          # hidden 16 -> 16 layer on the tensor cores (n = 16)
     n = G + 3
@@ -29,7 +36,7 @@ def _train_and_eval(prec, steps=2000):
     dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
     # N(0, 0.01^2): with N(0, 0.1^2) the second-derivative jets of this finer, deeper net
     # start ~1e4 (loss ~1e7) and neither precision trains in a few thousand steps
-    W = dev(inputs.init_weights(P, 7, sigma=0.01))
+    W = dev(inputs.init_weights(P, seed, sigma=0.01))
     h = capi.hrkan_init(capi.make_cfg(widths, G, prec=prec, flags=capi.HRKAN_FLAG_LAYERWISE))
     try:
         prob = capi.make_problem(capi.HRKAN_POISSON, 1.0, 1.0)
@@ -55,8 +62,11 @@ def _train_and_eval(prec, steps=2000):
 
 
 def test_bf16_training_reaches_the_fp32_error():
-    e32, l32 = _train_and_eval(capi.HRKAN_FP32)
-    e16, l16 = _train_and_eval(capi.HRKAN_BF16)
-    print(f"\nrel-L2 FP32 {e32:.4e} (loss {l32:.3e}); BF16 {e16:.4e} (loss {l16:.3e})")
-    assert e32 < 0.3                        # the FP32 run learned the solution
+    r32 = [_train_and_eval(capi.HRKAN_FP32, s) for s in SEEDS]
+    r16 = [_train_and_eval(capi.HRKAN_BF16, s) for s in SEEDS]
+    for s, a, b in zip(SEEDS, r32, r16):
+        print(f"\nseed {s}: rel-L2 FP32 {a[0]:.4e} (loss {a[1]:.3e}); BF16 {b[0]:.4e} (loss {b[1]:.3e})")
+    e32, e16 = np.mean([a[0] for a in r32]), np.mean([b[0] for b in r16])
+    print(f"mean rel-L2 FP32 {e32:.4e}, BF16 {e16:.4e}, ratio {e16 / e32:.3f}")
+    assert all(a[0] < 0.3 for a in r32)     # every FP32 run learned the solution
     assert e16 <= 1.2 * e32
