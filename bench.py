@@ -11,6 +11,14 @@ the timed region starts; they are far smaller than L2, so L2 is flushed
 (a 256 MiB device write) before every timed step, outside its events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--prec fp32|bf16|tf32]
+
+--workload poisson_2_64x3_1 --prec bf16 (or tf32) times the precision workload
+instead: 2-D Poisson a=b=2, HRKAN [2,64,64,64,1], G=32, 262144 interior +
+16384 boundary points, the hidden layers' forward contraction and weight
+gradient on the tensor cores; its roofline object is the tensor-core one
+(dense contraction flops of those launches) and the FP32 path of the same
+workload is timed beside it.
 
 --impl reference times the FP64 CPU oracle (the only reference there is: the
 paper ships no code) on the host cores, a bounded sample of the same workload
@@ -39,6 +47,30 @@ UNIT = "collocation points/s"
 WORKLOAD = "burgers_2_10_10_1"
 FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def measured_peaks():
+    """MEASURED_PEAKS.json of this machine pool, else the recipe's fallback figures."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return {"bf16": float(m["bf16_tflops"]), "bf16_sustained": float(m["bf16_tflops_sustained"]),
+                "source": "of measured (MEASURED_PEAKS.json)"}
+    except (OSError, KeyError, ValueError):
+        return {"bf16": 1900.0, "bf16_sustained": 1700.0, "source": "of fallback"}
+
+
+def dense_tc_flops(widths, G, k, n_int, J_int, n_bnd):
+    """Dense flops of the tensor-core launches of one training step: for every
+    hidden layer the forward contraction and the weight gradient, each
+    2 * rows * K * O with K = I * (G + k) and rows = J * points (all K columns
+    counted, zeros included)."""
+    n = G + k
+    f = 0
+    for l in range(1, len(widths) - 2):
+        I, O = widths[l], widths[l + 1]
+        f += 2 * 2 * (J_int * n_int + n_bnd) * I * n * O
+    return f
 
 
 def alg_flops_per_point(widths, k, J):
@@ -135,20 +167,19 @@ def run_reference(args, ws, rank):
     import oracle
     from paper_2409_14248_gb300 import inputs
     oracle.build()
-    w = inputs.WORKLOADS[WORKLOAD]
-    full = w.n_int + w.n_ic + w.n_bc
+    w = inputs.WORKLOADS[args.workload]
+    full = w.n_int + w.n_bnd + w.n_ic + w.n_bc
     # calibrate the oracle's rate, then size the sample so that the run takes ~2 minutes
-    d = inputs.make(w, n_int=512, n_ic=32, n_bc=32)
+    d = sample_data(inputs, w, 128, 16)
     Wd = d["W"].astype(np.float64)
     m1, m2 = np.zeros_like(Wd), np.zeros_like(Wd)
     t0 = time.perf_counter()
     oracle.train_step(w.net, w.problem(), Wd, m1, m2, d["x_int"], w.mask_int, d["x_bnd"], d["g_bnd"], w.lr, 1)
-    rate = 576 / (time.perf_counter() - t0)
+    rate = 144 / (time.perf_counter() - t0)
     budget = 120.0
     per_step = int(max(64, min(full, budget / max(1, args.steps + args.warmup) * rate)))
     n_int = max(16, per_step * w.n_int // full)
-    n_b = max(2, (per_step - n_int) // 2)
-    d = inputs.make(w, n_int=n_int, n_ic=n_b, n_bc=n_b)
+    d = sample_data(inputs, w, n_int, max(4, per_step - n_int))
     Wd = d["W"].astype(np.float64)
     m1, m2 = np.zeros_like(Wd), np.zeros_like(Wd)
     pts = d["x_int"].shape[1] + d["x_bnd"].shape[1]
@@ -159,13 +190,13 @@ def run_reference(args, ws, rank):
         oracle.train_step(w.net, w.problem(), Wd, m1, m2, d["x_int"], w.mask_int, d["x_bnd"], d["g_bnd"], w.lr, t)
     dt = time.perf_counter() - t0
     value = args.steps * pts / dt
-    sample = f"{d['x_int'].shape[1]} interior + {d['x_bnd'].shape[1]} initial/boundary points per step " \
-             f"(of {w.n_int} + {w.n_ic + w.n_bc}), same distribution and seed"
+    sample = f"{d['x_int'].shape[1]} interior + {d['x_bnd'].shape[1]} boundary/initial points per step " \
+             f"(of {w.n_int} + {w.n_bnd + w.n_ic + w.n_bc}), same distribution and seed"
     emit({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
           "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-          "config": {"workload": WORKLOAD, "widths": w.widths, "G": w.G, "k": w.k, "m": w.m,
-                     "n_int": w.n_int, "n_bnd": w.n_ic + w.n_bc, "impl": "FP64 CPU oracle (C, 1 thread)"},
+          "config": {"workload": args.workload, "widths": w.widths, "G": w.G, "k": w.k, "m": w.m,
+                     "n_int": w.n_int, "n_bnd": w.n_bnd + w.n_ic + w.n_bc, "impl": "FP64 CPU oracle (C, 1 thread)"},
           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
 
@@ -173,22 +204,69 @@ def run_reference(args, ws, rank):
 # --------------------------------------------------------------------- ours
 
 
+def sample_data(inputs, w, n_int, n_b):
+    """The workload's points with smaller counts (same distribution and seed)."""
+    if w.pde == inputs.POISSON:
+        return inputs.make(w, n_int=n_int, n_bnd=max(4, n_b))
+    return inputs.make(w, n_int=n_int, n_ic=max(1, n_b // 2), n_bc=max(2, n_b - n_b // 2))
+
+
 def cpu_baseline_leg(w):
-    """The FP64 oracle on the host: 2 full steps of the same workload (~10 s)."""
+    """The FP64 oracle on the host: full training steps of the workload when they
+    take ~10 s, else one step on a bounded sample of it."""
     import oracle
     from paper_2409_14248_gb300 import inputs
     oracle.build()
-    d = inputs.make(w)
+    full = w.n_int + w.n_bnd + w.n_ic + w.n_bc
+    d = sample_data(inputs, w, 128, 16)
     Wd = d["W"].astype(np.float64)
     m1, m2 = np.zeros_like(Wd), np.zeros_like(Wd)
-    steps = 2
+    t0 = time.perf_counter()
+    oracle.train_step(w.net, w.problem(), Wd, m1, m2, d["x_int"], w.mask_int, d["x_bnd"], d["g_bnd"], w.lr, 1)
+    rate = 144 / (time.perf_counter() - t0)
+    if 2 * full <= 15.0 * rate:
+        d, steps, what = inputs.make(w), 2, "full training steps of the workload"
+    else:
+        n = int(max(64, 15.0 * rate))
+        d, steps, what = sample_data(inputs, w, n * w.n_int // full, max(4, n - n * w.n_int // full)), 1, \
+            "training step on a sample of the workload (same distribution and seed)"
+    Wd = d["W"].astype(np.float64)
+    m1, m2 = np.zeros_like(Wd), np.zeros_like(Wd)
     t0 = time.perf_counter()
     for t in range(1, steps + 1):
         oracle.train_step(w.net, w.problem(), Wd, m1, m2, d["x_int"], w.mask_int, d["x_bnd"], d["g_bnd"], w.lr, t)
     dt = time.perf_counter() - t0
     pts = d["x_int"].shape[1] + d["x_bnd"].shape[1]
     return {"value": steps * pts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} full training steps of the workload ({pts} points each), FP64, 1 thread"}
+            "sample": f"{steps} {what} ({pts} points each), FP64, 1 thread"}
+
+
+PRECS = {"fp32": 0, "bf16": 1, "tf32": 2}
+
+
+def launches_per_step(widths, prec, tc_fwd, tc_dw, fused):
+    """Kernels one training step launches (the layer-wise path: per layer and point
+    set a forward, a weight gradient and, past the first layer, an input adjoint;
+    a tensor-core call is a conversion kernel plus the contraction)."""
+    if fused:
+        return 2                     # fused forward+residual+backward, reduction+Adam
+    L = len(widths) - 1
+    per_set_fwd = sum(2 if tc_fwd(l) else 1 for l in range(L))
+    per_set_bwd = sum(2 if tc_dw(l) else 1 for l in range(L)) + (L - 1)
+    return 2 * per_set_fwd + 2 * per_set_bwd + 2   # interior and boundary sets, residual, reduction+Adam
+
+
+def time_steps(torch, capi, h, step, first_t, steps, flush):
+    """CUDA-event time of `steps` training steps (L2 flushed before each, outside the events)."""
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev_s[i].record()
+        step(first_t + i)
+        ev_e[i].record()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in zip(ev_s, ev_e))
 
 
 def run_ours(args, ws, rank, local):
@@ -206,24 +284,27 @@ def run_ours(args, ws, rank, local):
         torch.distributed.barrier()
     capi.load_library()
 
-    w = inputs.WORKLOADS[WORKLOAD]
+    w = inputs.WORKLOADS[args.workload]
+    prec = PRECS[args.prec]
     d = inputs.make(w)
     Ni, Nb = d["x_int"].shape[1], d["x_bnd"].shape[1]
     pts = Ni + Nb
-    cfg = capi.make_cfg(w.widths, w.G, w.k, w.m, w.lo, w.hi)
-    h = capi.hrkan_init(cfg)
+    J = bin(w.mask_int & 0x1F).count("1")
     p = w.problem()
     prob = capi.make_problem(p["kind"], p["a"], p["b"], p["lam"], p["nu"], p["alpha"])
     dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
-    W = dev(d["W"])
+    W0 = dev(d["W"])
     xi, xb, gb = dev(d["x_int"]), dev(d["x_bnd"]), dev(d["g_bnd"])
     loss = torch.zeros(3, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     b1, b2, eps = 0.9, 0.999, 1e-8
 
-    def step(t):
-        capi.hrkan_train_step(h, prob, W, xi, Ni, xb, gb, Nb, w.lr, b1, b2, eps, t, loss)
+    def make_step(h, W):
+        return lambda t: capi.hrkan_train_step(h, prob, W, xi, Ni, xb, gb, Nb, w.lr, b1, b2, eps, t, loss)
 
+    h = capi.hrkan_init(capi.make_cfg(w.widths, w.G, w.k, w.m, w.lo, w.hi, prec=prec))
+    W = W0.clone()
+    step = make_step(h, W)
     for t in range(1, args.warmup + 1):
         flush.fill_(0.0)
         step(t)
@@ -232,30 +313,21 @@ def run_ours(args, ws, rank, local):
         torch.distributed.barrier()
     torch.cuda.synchronize()
 
-    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     capi.hrkan_profile_enable(h, True)
     for c in range(5):
         capi.hrkan_profile_read(h, c, reset=True)
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        ev_s[i].record()
-        step(args.warmup + 1 + i)
-        ev_e[i].record()
-    torch.cuda.synchronize()
+    total_ms = time_steps(torch, capi, h, step, args.warmup + 1, args.steps, flush)
     clocks = sampler.stop()
     capi.hrkan_profile_enable(h, False)
-    total_ms = sum(a.elapsed_time(b) for a, b in zip(ev_s, ev_e))
-    fused_ms, fused_n = capi.hrkan_profile_read(h, capi.HRKAN_KERNEL_FUSED)
-    red_ms, red_n = capi.hrkan_profile_read(h, capi.HRKAN_KERNEL_REDUCE)
+    prof = {c: capi.hrkan_profile_read(h, c) for c in range(5)}
+    fused = prof[capi.HRKAN_KERNEL_FUSED][1] > 0 and prof[capi.HRKAN_KERNEL_FORWARD][1] == 0
     if ws > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    launches = fused_n + red_n
 
     # end to end through the C ABI with host buffers: H2D of the inputs, the step, D2H of the loss
     pin = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32).pin_memory()
@@ -279,26 +351,73 @@ def run_ours(args, ws, rank, local):
     h2d = (hxi.numel() + hxb.numel() + hgb.numel()) * 4
     capi.hrkan_destroy(h)
 
+    # the plain FP32 path of the same workload, timed beside a reduced-precision run
+    fp32_path = None
+    if prec != PRECS["fp32"]:
+        h32 = capi.hrkan_init(capi.make_cfg(w.widths, w.G, w.k, w.m, w.lo, w.hi))
+        W32 = W0.clone()
+        step32 = make_step(h32, W32)
+        for t in range(1, 4):
+            step32(t)
+        torch.cuda.synchronize()
+        k32 = max(3, min(args.steps, 20))
+        ms32 = time_steps(torch, capi, h32, step32, 4, k32, flush)
+        capi.hrkan_destroy(h32)
+        fp32_path = {"value": ws * k32 * pts / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32 / k32,
+                     "steps": k32}
+
     if rank == 0:
-        J = 4
-        flops = alg_flops_per_point(w.widths, w.k, J) * Ni + alg_flops_per_point(w.widths, w.k, 1) * Nb
-        fused_avg_s = fused_ms / max(1, fused_n) / 1e3
-        achieved = flops / fused_avg_s / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                    "kernel": "narrow_grad_kernel<[2,10,10,1], mask 0x0F, TRAIN>",
-                    "kernel_ms": fused_ms / max(1, fused_n), "reduce_adam_ms": red_ms / max(1, red_n),
-                    "peak_source": FP32_PEAK_NOTE + " (derived, FP32 FMA pipe)"}
+        n = w.G + w.k
+        hidden = lambda l: 0 < l < len(w.widths) - 2
+        tc_ok = lambda l: hidden(l) and 16 <= w.widths[l + 1] <= 64 and w.widths[l + 1] % 16 == 0 and n <= 64
+        tc_fwd = lambda l: prec != PRECS["fp32"] and tc_ok(l)
+        tc_dw = lambda l: prec == PRECS["bf16"] and tc_ok(l)
+        launches = launches_per_step(w.widths, prec, tc_fwd, tc_dw, fused) * args.steps
+        if prec == PRECS["fp32"]:
+            fused_ms, fused_n = prof[capi.HRKAN_KERNEL_FUSED]
+            red_ms, red_n = prof[capi.HRKAN_KERNEL_REDUCE]
+            flops = alg_flops_per_point(w.widths, w.k, J) * Ni + alg_flops_per_point(w.widths, w.k, 1) * Nb
+            if fused:
+                fused_avg_s = fused_ms / max(1, fused_n) / 1e3
+                achieved = flops / fused_avg_s / 1e12
+                kernel = f"narrow_grad_kernel<{w.widths}, mask {w.mask_int:#x}, TRAIN>"
+                kms = fused_ms / max(1, fused_n)
+            else:
+                achieved = flops / (total_ms / args.steps / 1e3) / 1e12
+                kernel = "layer-wise step (all kernels of one step)"
+                kms = total_ms / args.steps
+            roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": kernel, "kernel_ms": kms,
+                        "reduce_adam_ms": red_ms / max(1, red_n),
+                        "peak_source": FP32_PEAK_NOTE + " (derived, FP32 FMA pipe)"}
+        else:
+            tc_ms, tc_n = prof[capi.HRKAN_KERNEL_TENSOR]
+            pk = measured_peaks()
+            peak = pk["bf16_sustained"] * (1.0 if prec == PRECS["bf16"] else 0.5)
+            fwd_flops = dense_tc_flops(w.widths, w.G, w.k, Ni, J, Nb) / 2
+            flops = fwd_flops * (2 if prec == PRECS["bf16"] else 1)   # forward (+ weight gradient in BF16)
+            achieved = flops * args.steps / (tc_ms / 1e3) / 1e12
+            roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "kernel": "tc_fwd_kernel + tc_dw_kernel (hidden layers)" if prec == PRECS["bf16"]
+                        else "tc_fwd_kernel (hidden layers)",
+                        "kernel_ms_per_step": tc_ms / args.steps, "launches_per_step": tc_n / args.steps,
+                        "flops_per_step": flops, "peak_source": ("bf16 dense sustained " if prec == PRECS["bf16"]
+                                                                 else "bf16 dense sustained x 0.5 (tf32) ")
+                        + pk["source"]}
         out = {"metric": METRIC, "value": ws * args.steps * pts / (total_ms / 1e3), "unit": UNIT, "n_gpus": ws,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
                "data": "synthetic",
-               "config": {"workload": WORKLOAD, "widths": w.widths, "G": w.G, "k": w.k, "m": w.m, "n_int": Ni,
-                          "n_bnd": Nb, "precision": "fp32", "parallelism": "replicas" if ws > 1 else "single",
+               "config": {"workload": args.workload, "widths": w.widths, "G": w.G, "k": w.k, "m": w.m,
+                          "n_int": Ni, "n_bnd": Nb, "precision": args.prec,
+                          "parallelism": "replicas" if ws > 1 else "single",
                           "l2": "flushed before every timed step (256 MiB device write, outside the step events)"},
                "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
                "e2e": {"value": ws * e2e_steps * pts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": 24}}
+        if fp32_path is not None:
+            out["fp32_path"] = fp32_path
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_leg(w)
         emit(out)
@@ -314,6 +433,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, help="burgers_2_10_10_1 (default) or poisson_2_64x3_1")
+    ap.add_argument("--prec", default="fp32", choices=sorted(PRECS))
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     ws, rank, local = dist_env()
