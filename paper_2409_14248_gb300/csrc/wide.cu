@@ -9,6 +9,8 @@
 //   forward      y[r][o] = sum_j sum_q W[o][j][c_j+q] A_r[j][q]
 //   adjoint      dA[j][r][q] = sum_o gy[r][o] W[o][j][c_j+q], then through v'''
 //   weight grad  dW[o][j][c_j+q] += sum_r gy[r][o] A_r[j][q]  (summed over points)
+#include <algorithm>
+
 #include "internal.h"
 #include "narrow.cuh"
 #include "wide.cuh"
@@ -183,6 +185,10 @@ __global__ void __launch_bounds__(WB) wide_dw_kernel(WideDw p) {
     const int jc = blockIdx.x % njc, gp = blockIdx.x / njc;
     const int j0 = jc * JC;
     const int nj = min(JC, I - j0);
+    // outputs [o0, o0 + Ob) of this block (blockIdx.y slices the outputs when the
+    // unit chunks alone give too few blocks, e.g. the 2-input first layer)
+    const int OS = (O + gridDim.y - 1) / gridDim.y;
+    const int o0 = blockIdx.y * OS, Ob = min(OS, O - o0);
     const int sz_dw = (JC * O * NP + 3) & ~3, sz_gy = (PB * J * O + 3) & ~3;
     float* dws = sm;                                  // [JC][O][NP]
     float* gys = dws + sz_dw;                         // [PB][J][O]
@@ -195,10 +201,11 @@ __global__ void __launch_bounds__(WB) wide_dw_kernel(WideDw p) {
         const int64_t base = tile * PB;
         __syncthreads();
         // stage gy: element (pp, r, o) = gy[r][o][base + pp]
-        for (int t = threadIdx.x; t < PB * J * O; t += blockDim.x) {
-            const int pp = t % PB, ro = t / PB;   // ro = r * O + o
+        for (int t = threadIdx.x; t < PB * J * Ob; t += blockDim.x) {
+            const int pp = t % PB, ro = t / PB;   // ro = r * Ob + o
+            const int r = ro / Ob, o = ro % Ob;
             const int64_t pt = base + pp;
-            gys[pp * J * O + ro] = (pt < N) ? p.gy[int64_t(ro) * N + pt] : 0.0f;
+            gys[pp * J * Ob + ro] = (pt < N) ? p.gy[(int64_t(r) * O + o0 + o) * N + pt] : 0.0f;
         }
         // stage basis rows of the chunk's units
         for (int t = threadIdx.x; t < PB * JC; t += blockDim.x) {
@@ -227,18 +234,18 @@ __global__ void __launch_bounds__(WB) wide_dw_kernel(WideDw p) {
         }
         __syncthreads();
         // owners: row (jj, o) of the gradient
-        for (int k = threadIdx.x; k < nj * O; k += blockDim.x) {
-            const int o = k % O, jj = k / O;
-            float* row = dws + (jj * O + o) * NP;
+        for (int k = threadIdx.x; k < nj * Ob; k += blockDim.x) {
+            const int o = k % Ob, jj = k / Ob;
+            float* row = dws + (jj * Ob + o) * NP;
 #pragma unroll 4
             for (int pp = 0; pp < PB; ++pp) {
                 const int c = cs[pp * JC + jj];
                 const float* ar = as + (pp * JC + jj) * J * KPW;
-                const float* gr = gys + pp * J * O + o;
+                const float* gr = gys + pp * J * Ob + o;
                 float gq[KPW] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
                 for (int r = 0; r < J; ++r) {
-                    const float gv = gr[r * O];
+                    const float gv = gr[r * Ob];
                     const float4 a4 = reinterpret_cast<const float4*>(ar)[r];
                     gq[0] = fmaf(gv, a4.x, gq[0]);
                     gq[1] = fmaf(gv, a4.y, gq[1]);
@@ -253,9 +260,9 @@ __global__ void __launch_bounds__(WB) wide_dw_kernel(WideDw p) {
     }
     __syncthreads();
     float* out = p.partial + int64_t(p.row0 + gp) * p.P + p.col0;
-    for (int t = threadIdx.x; t < nj * O * n; t += blockDim.x) {
-        const int i = t % n, rest = t / n, o = rest % O, jj = rest / O;
-        out[(int64_t(o) * I + j0 + jj) * n + i] = dws[(jj * O + o) * NP + i];
+    for (int t = threadIdx.x; t < nj * Ob * n; t += blockDim.x) {
+        const int i = t % n, rest = t / n, o = rest % Ob, jj = rest / Ob;
+        out[(int64_t(o0 + o) * I + j0 + jj) * n + i] = dws[(jj * Ob + o) * NP + i];
     }
 }
 
@@ -310,7 +317,13 @@ static cudaError_t dw_mask(const WideDw& p, bool first, cudaStream_t s) {
         cudaError_t e = smem_optin((const void*)kern, sm);
         if (e != cudaSuccess) return e;
         const int njc = (p.I + jc - 1) / jc;
-        kern<<<unsigned(njc * p.GP), WB, sm, s>>>(p);
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        // slice the outputs until there are about two blocks per SM (at least 8 outputs a slice)
+        const int want = (2 * nsm + njc * p.GP - 1) / (njc * p.GP);
+        const int nos = std::max(1, std::min(want, p.O / 8));
+        kern<<<dim3(unsigned(njc * p.GP), unsigned(nos)), WB, sm, s>>>(p);
         return cudaGetLastError();
     };
     if (first) return go(wide_dw_kernel<MASK, 2, PB, true>, 2, dw_smem<MASK, 2, PB, true>(p.O, p.g.n));
