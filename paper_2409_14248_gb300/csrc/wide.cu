@@ -136,11 +136,26 @@ __global__ void __launch_bounds__(WB) wide_adjoint_kernel(WideLayer p) {
         for (int r = 0; r < J; ++r)
 #pragma unroll
             for (int q = 0; q < KPW; ++q) dA[jj][r][q] = 0.0f;
+    // gy of output o + GPF is loaded while output o is contracted (hides the load latency)
+    constexpr int GPF = 4;
+    float gq[GPF][J];
+#pragma unroll
+    for (int u = 0; u < GPF; ++u)
+#pragma unroll
+        for (int r = 0; r < J; ++r) gq[u][r] = u < O ? p.gy[(int64_t(r) * O + u) * N + pt] : 0.0f;
 #pragma unroll 1
-    for (int o = 0; o < O; ++o) {
+    for (int ob = 0; ob < O; ob += GPF) {
+#pragma unroll
+      for (int u = 0; u < GPF; ++u) {
+        const int o = ob + u;
+        if (o >= O) break;
         float g[J];
 #pragma unroll
-        for (int r = 0; r < J; ++r) g[r] = p.gy[(int64_t(r) * O + o) * N + pt];
+        for (int r = 0; r < J; ++r) g[r] = gq[u][r];
+        if (o + GPF < O) {
+#pragma unroll
+            for (int r = 0; r < J; ++r) gq[u][r] = p.gy[(int64_t(r) * O + o + GPF) * N + pt];
+        }
 #pragma unroll
         for (int jj = 0; jj < IT; ++jj) {
             const float* wr = ws + (jj * O + o) * n;
@@ -153,6 +168,7 @@ __global__ void __launch_bounds__(WB) wide_adjoint_kernel(WideLayer p) {
                 for (int r = 0; r < J; ++r) dA[jj][r][q] = fmaf(g[r], w, dA[jj][r][q]);
             }
         }
+      }
     }
 #pragma unroll
     for (int jj = 0; jj < IT; ++jj) {
@@ -293,7 +309,7 @@ static cudaError_t fwd_mask(const WideLayer& p, bool first, cudaStream_t s) {
 
 template <unsigned MASK>
 static cudaError_t adj_mask(const WideLayer& p, cudaStream_t s) {
-    constexpr int IT = 4;
+    constexpr int IT = 2;   // measured best of 2 / 4 / 8 (registers vs gy reuse)
     const size_t sm = size_t(IT) * p.O * p.g.n * sizeof(float);
     auto kern = wide_adjoint_kernel<MASK, IT>;
     cudaError_t e = smem_optin((const void*)kern, sm);
