@@ -67,6 +67,9 @@ def _load():
                                                                                         ctypes.c_int]
             lib.orc_layer_dw.argtypes = [ctypes.c_int] * 5 + [ctypes.c_double] * 2 + [_dp, _dp, ctypes.c_long,
                                                                                    ctypes.c_uint, _dp, ctypes.c_int]
+            lib.orc_layer_adjoint.argtypes = [ctypes.c_int] * 5 + [ctypes.c_double] * 2 + [_dp, _dp, _dp,
+                                                                                        ctypes.c_long, ctypes.c_uint,
+                                                                                        _dp, ctypes.c_int]
             lib.orc_round.argtypes = [ctypes.c_double, ctypes.c_int]
             lib.orc_round.restype = ctypes.c_double
             lib.orc_backward.argtypes = net + [_dp, _dp, ctypes.c_long, ctypes.c_uint, _dp, _dp, ctypes.c_int]
@@ -182,6 +185,22 @@ def layer_dw(I, O, G, k, m, lo, hi, zin, gy, mask, fmt=EXACT):
                           out.ctypes.data_as(_dp), int(fmt))
     if rc:
         raise ValueError("orc_layer_dw: bad arguments")
+    return out
+
+
+def layer_adjoint(I, O, G, k, m, lo, hi, Wl, zin, gy, mask, fmt=EXACT):
+    """dL/d(input jets) [J, I, N] of one KAN layer for output-jet gradients gy[J, O, N];
+    fmt rounds gy and the weights."""
+    lib = _load()
+    Wl, Wp = _d(Wl)
+    z, zp = _d(zin)
+    g, gp = _d(gy)
+    J, _, N = z.shape
+    out = np.zeros((J, I, N))
+    rc = lib.orc_layer_adjoint(int(I), int(O), int(G), int(k), int(m), float(lo), float(hi), Wp, zp, gp, N,
+                               int(mask), out.ctypes.data_as(_dp), int(fmt))
+    if rc:
+        raise ValueError("orc_layer_adjoint: bad arguments")
     return out
 
 

@@ -392,6 +392,76 @@ int orc_layer_dw(int I, int O, int G, int k, int m, double lo, double hi, const 
 }
 
 /*
+ * Input adjoint of one layer: gz = d/d(input jets) of
+ * sum_p sum_r sum_o gy[r][o][p] * y_r[o][p], the chain rule of Section 3
+ * reversed through the third derivative of Eq. 2.  With
+ * dA_r[j][i] = sum_o gy[r][o] W[o][j][i] and v1, v2, v3 the derivatives:
+ *   value row:        d/dz += dA_0 v1
+ *   d-row (A = v1 z_d):  d/dz += dA_d v2 z_d,                d/dz_d += dA_d v1
+ *   dd-row (A = v2 z_d^2 + v1 z_dd):
+ *                     d/dz += dA_dd (v3 z_d^2 + v2 z_dd),   d/dz_d += dA_dd 2 v2 z_d,
+ *                     d/dz_dd += dA_dd v1
+ * fmt rounds gy and W before the FP64 sum over o (the reduced-precision
+ * contraction's inputs); ORC_EXACT rounds nothing.  zin [J][I][N],
+ * gy [J][O][N], gz [J][I][N] written.
+ */
+int orc_layer_adjoint(int I, int O, int G, int k, int m, double lo, double hi, const double* Wl,
+                      const double* zin, const double* gy, long N, unsigned mask, double* gz, int fmt)
+{
+    const int D = 2;
+    int rows[16];
+    int J = mask_rows(mask, D, rows);
+    if (!(mask & 1u)) return -1;
+    int n = G + k;
+    double* s = malloc(sizeof(double) * n);
+    double* e = malloc(sizeof(double) * n);
+    orc_support(G, k, lo, hi, s, e);
+    for (long p = 0; p < N; ++p) {
+        for (int j = 0; j < I; ++j) {
+            double z = 0.0, dz[2] = {0.0, 0.0}, d2z[2] = {0.0, 0.0};
+            for (int r = 0; r < J; ++r) {
+                double v = zin[((long)r * I + j) * N + p];
+                int b = rows[r];
+                if (b == 0) z = v;
+                else if (b <= D) dz[b - 1] = v;
+                else d2z[b - 1 - D] = v;
+            }
+            double g_z = 0.0, g_d[2] = {0.0, 0.0}, g_dd[2] = {0.0, 0.0};
+            for (int i = 0; i < n; ++i) {
+                double b[4];
+                orc_hr_basis(m, s[i], e[i], z, b);
+                for (int r = 0; r < J; ++r) {
+                    double dA = 0.0;
+                    for (int o = 0; o < O; ++o)
+                        dA += round_to(gy[((long)r * O + o) * N + p], fmt) *
+                              round_to(Wl[((long)o * I + j) * n + i], fmt);
+                    int bit = rows[r];
+                    if (bit == 0) {
+                        g_z += dA * b[1];
+                    } else if (bit <= D) {
+                        int d = bit - 1;
+                        g_z += dA * b[2] * dz[d];
+                        g_d[d] += dA * b[1];
+                    } else {
+                        int d = bit - 1 - D;
+                        g_z += dA * (b[3] * dz[d] * dz[d] + b[2] * d2z[d]);
+                        g_d[d] += dA * 2.0 * b[2] * dz[d];
+                        g_dd[d] += dA * b[1];
+                    }
+                }
+            }
+            for (int r = 0; r < J; ++r) {
+                int bit = rows[r];
+                double v = (bit == 0) ? g_z : (bit <= D) ? g_d[bit - 1] : g_dd[bit - 1 - D];
+                gz[((long)r * I + j) * N + p] = v;
+            }
+        }
+    }
+    free(s); free(e);
+    return 0;
+}
+
+/*
  * Reverse mode of point_forward.  g*, gd*, gd2* hold dL/d(output jets) of the
  * layer on entry and are overwritten with dL/d(input jets).  dW accumulates.
  */

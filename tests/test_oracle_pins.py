@@ -519,3 +519,48 @@ def test_layer_dw_rounding_is_a_no_op_on_representable_inputs():
     gy2[0, 0, 0] = 1.0 + 2.0 ** -12
     assert not np.array_equal(oracle.layer_dw(I, O, G, 3, 4, lo, hi, z, gy2, 0x1F, oracle.BF16),
                               oracle.layer_dw(I, O, G, 3, 4, lo, hi, z, gy2, 0x1F))
+
+
+@pytest.mark.parametrize("mask", [0x01, 0x0F, 0x1F])
+def test_layer_adjoint_matches_central_differences(mask):
+    """layer_adjoint is the gradient of sum(gy * layer_forward(z)) w.r.t. the input jets z."""
+    I, O, G, N = 3, 4, 5, 6
+    n = G + 3
+    J = oracle.n_rows(mask)
+    rng = np.random.default_rng(80 + mask)
+    z = rng.normal(0, 0.5, (J, I, N))
+    gy = rng.normal(0, 1, (J, O, N))
+    W = rng.normal(0, 0.3, O * I * n)
+    gz = oracle.layer_adjoint(I, O, G, 3, 4, -1.0, 1.0, W, z, gy, mask)
+
+    def f(zz):
+        return float((gy * oracle.layer_forward(I, O, G, 3, 4, -1.0, 1.0, W, zz, mask)).sum())
+
+    h = 1e-6
+    for idx in [(r, j, p) for r in range(J) for j in range(I) for p in range(0, N, 2)]:
+        e = np.zeros_like(z)
+        e[idx] = h
+        fd = (f(z + e) - f(z - e)) / (2 * h)
+        assert abs(fd - gz[idx]) <= 1e-6 * (1 + abs(gz[idx])), (idx, fd, gz[idx])
+
+
+def test_layer_adjoint_chains_to_the_network_backward():
+    """For [2, 4, 3, 1]: the network backward's first-layer block equals layer_dw of the
+    coordinate jets with gy = the layer adjoint of the last two layers chained."""
+    net = dict(widths=[2, 4, 3, 1], G=6, k=3, m=4, lo=-1.0, hi=1.0)
+    n = 9
+    W = np.random.default_rng(81).normal(0, 0.4, oracle.param_count(net))
+    x = np.random.default_rng(82).uniform(-1, 1, (2, 25))
+    g = np.random.default_rng(83).normal(0, 1, (5, 25))
+    full = oracle.backward(net, W, x, 0x1F, g)
+    z0 = np.zeros((5, 2, 25))
+    z0[0] = x
+    z0[1, 0] = 1.0
+    z0[2, 1] = 1.0
+    W0, W1, W2 = W[:4 * 2 * n], W[4 * 2 * n: 4 * 2 * n + 3 * 4 * n], W[4 * 2 * n + 3 * 4 * n:]
+    z1 = oracle.layer_forward(2, 4, 6, 3, 4, -1.0, 1.0, W0, z0, 0x1F)
+    z2 = oracle.layer_forward(4, 3, 6, 3, 4, -1.0, 1.0, W1, z1, 0x1F)
+    g2 = oracle.layer_adjoint(3, 1, 6, 3, 4, -1.0, 1.0, W2, z2, g[:, None, :], 0x1F)
+    g1 = oracle.layer_adjoint(4, 3, 6, 3, 4, -1.0, 1.0, W1, z1, g2, 0x1F)
+    first = oracle.layer_dw(2, 4, 6, 3, 4, -1.0, 1.0, z0, g1, 0x1F)
+    np.testing.assert_allclose(first, full[:4 * 2 * n], rtol=1e-11, atol=1e-11)
