@@ -169,6 +169,18 @@ int hrkan_layer_dw(hrkan_t h, int layer, const float* z, const float* gy, int64_
                    float* dW, hrkan_stream_t stream);
 
 /*
+ * Input adjoint of one layer l >= 1 (reverse mode of hrkan_layer_jets w.r.t.
+ * its input jets, through the third basis derivative of Eq. 2):
+ * gz = d/dz of sum_{r,o,p} gy[r][o][p] * y_r[o][p] for W = that layer's
+ * weights [O][I][n] (a pointer into the network's W), z = input jets
+ * [J][I][N], gy [J][O][N], gz [J][I][N] (written).  Runs the kernel the
+ * network backward uses (tensor cores for BF16 hidden layers with masks 0x0F
+ * and 0x1F).
+ */
+int hrkan_layer_adjoint(hrkan_t h, int layer, const float* W, const float* z, const float* gy, int64_t N,
+                        unsigned jet_mask, float* gz, hrkan_stream_t stream);
+
+/*
  * Residual and loss (Eq. 3-4 / Eq. 6-8) from precomputed jets.
  *   x_int [2][N_int], jets_int [J][N_int] under jet_mask (Poisson needs u_xx,
  *   u_yy; Burgers needs u, u_x, u_t, u_xx), u_bnd / g_bnd [N_bnd] network

@@ -27,7 +27,7 @@ EXPORTS = ("hrkan_param_count", "hrkan_init", "hrkan_destroy", "hrkan_last_error
            "hrkan_forward_jets", "pinn_residual_loss", "hrkan_backward", "adam_step", "hrkan_reset_moments",
            "hrkan_train_step", "hrkan_profile_enable", "hrkan_profile_read", "hrkan_backward_noalloc",
            "hrkan_train_step_batched", "hrkan_forward_jets_batched", "hrkan_set_batch_items", "hrkan_sync_status",
-           "hrkan_layer_jets", "hrkan_layer_dw")
+           "hrkan_layer_jets", "hrkan_layer_dw", "hrkan_layer_adjoint")
 HRKAN_KERNEL_FUSED, HRKAN_KERNEL_REDUCE, HRKAN_KERNEL_FORWARD, HRKAN_KERNEL_RESIDUAL, HRKAN_KERNEL_TENSOR = 0, 1, 2, 3, 4
 
 
@@ -90,6 +90,7 @@ def load_library(path: str = LIB_PATH):
         lib.hrkan_sync_status.argtypes = [_vp]
         lib.hrkan_layer_jets.argtypes = [_vp, _i32, _vp, _vp, _i64, _u32, _vp, _vp]
         lib.hrkan_layer_dw.argtypes = [_vp, _i32, _vp, _vp, _i64, _u32, _vp, _vp]
+        lib.hrkan_layer_adjoint.argtypes = [_vp, _i32, _vp, _vp, _vp, _i64, _u32, _vp, _vp]
         lib.hrkan_profile_enable.argtypes = [_vp, _i32]
         lib.hrkan_profile_read.argtypes = [_vp, _i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
         for name in EXPORTS:
@@ -269,6 +270,14 @@ def hrkan_layer_dw(h, layer, z, gy, N, jet_mask, dW, stream=None):
     f = torch.float32
     _check(load_library().hrkan_layer_dw(h, int(layer), _ptr(z, f), _ptr(gy, f), int(N), int(jet_mask), _ptr(dW, f),
                                          _stream(stream)))
+
+
+def hrkan_layer_adjoint(h, layer, W_layer, z, gy, N, jet_mask, gz, stream=None):
+    """Input adjoint gz [J][I][N] of layer >= 1 from z [J][I][N] and gy [J][O][N]."""
+    import torch
+    f = torch.float32
+    _check(load_library().hrkan_layer_adjoint(h, int(layer), _ptr(W_layer, f), _ptr(z, f), _ptr(gy, f), int(N),
+                                              int(jet_mask), _ptr(gz, f), _stream(stream)))
 
 
 def hrkan_layer_jets(h, layer, W_layer, z, N, jet_mask, y, stream=None):

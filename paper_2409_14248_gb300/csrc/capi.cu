@@ -435,7 +435,17 @@ int wide_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsi
             float* gz = ws_get(h, 2 + (l % 2), size_t(J) * a.I * N, &rc);
             if (!gz) return rc;
             a.gz = gz;
-            e = wide_adjoint_layer(a, mask, s);
+            if (tc_adj_supported(h->cfg.prec, a.I, a.O, h->n, mask) &&
+                tc_dw_supported(h->cfg.prec, a.I, a.O, h->n, mask)) {
+                // the weight-gradient call above left the BF16 gy copy in slot 11
+                float* gbf = ws_get(h, 11, size_t((tc_dw_gy_elems(J, a.O, N) + 1) / 2), &rc);
+                float* wbf = gbf ? ws_get(h, 12, size_t((tc_adj_w_elems(a.O, a.I, h->n) + 1) / 2), &rc) : nullptr;
+                if (!wbf) return rc;
+                ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
+                e = tc_adj_layer(a.W, wbf, gbf, zl, gz, a.I, a.O, N, h->grid, mask, h->status, s);
+            } else {
+                e = wide_adjoint_layer(a, mask, s);
+            }
             if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
             gy = gz;
         }
@@ -1055,6 +1065,37 @@ int hrkan_layer_dw(hrkan_t h, int layer, const float* z, const float* gy, int64_
     if (int rc = layer_dw(h, d, layer, jet_mask, s)) return rc;
     cudaError_t e = sum_rows(h->partial + d.col0, h->wide_gp, h->P, cols, dW, s);
     return e == cudaSuccess ? HRKAN_OK : cuda_fail(e, "row sum launch");
+}
+
+int hrkan_layer_adjoint(hrkan_t h, int layer, const float* W, const float* z, const float* gy, int64_t N,
+                        unsigned jet_mask, float* gz, hrkan_stream_t stream) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (layer < 1 || layer >= h->L) return fail(HRKAN_EINVAL, "layer %d outside [1, %d)", layer, h->L);
+    if (N < 0) return fail(HRKAN_EINVAL, "N=%lld", (long long)N);
+    if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
+    if (N == 0) return HRKAN_OK;
+    if (!W || !z || !gy || !gz) return fail(HRKAN_EINVAL, "NULL device pointer");
+    if (int rc = use_device(h)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    WideLayer a = wide_layer(h, W - h->layer_off[layer], layer, N);
+    a.z = z;
+    a.gy = gy;
+    a.gz = gz;
+    const int J = jets_of(jet_mask);
+    cudaError_t e;
+    if (tc_adj_supported(h->cfg.prec, a.I, a.O, h->n, jet_mask)) {
+        int rc = HRKAN_OK;
+        float* gbf = ws_get(h, 11, size_t((tc_dw_gy_elems(J, a.O, N) + 1) / 2), &rc);
+        float* wbf = gbf ? ws_get(h, 12, size_t((tc_adj_w_elems(a.O, a.I, h->n) + 1) / 2), &rc) : nullptr;
+        if (!wbf) return rc;
+        ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
+        e = tc_gy_to_bf16(gy, gbf, J, a.O, N, s);
+        if (e == cudaSuccess) e = tc_adj_layer(a.W, wbf, gbf, z, gz, a.I, a.O, N, h->grid, jet_mask, h->status, s);
+    } else {
+        e = wide_adjoint_layer(a, jet_mask, s);
+    }
+    if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no layer kernel", jet_mask);
+    return e == cudaSuccess ? HRKAN_OK : cuda_fail(e, "adjoint launch");
 }
 
 }  // extern "C"

@@ -36,6 +36,8 @@ cudaError_t tc_forward_layer(const float* W, void* w_prep, const float* z, float
 // Tensor-core weight gradient of one hidden layer (tc_dw.cu): BF16 inputs,
 // FP32 accumulation, 16 <= O <= 64 with O % 16 == 0, n <= 64.
 bool tc_dw_supported(int prec, int I, int O, int n, unsigned mask);
+// gy [J][O][N] float32 -> BF16 [J*O][N rounded up to 64] (zero past N).
+cudaError_t tc_gy_to_bf16(const float* gy, void* gy_bf, int J, int O, int64_t N, cudaStream_t s);
 // BF16 elements of the gy copy the kernel needs (J * O * N rounded up to 64 points).
 int64_t tc_dw_gy_elems(int J, int O, int64_t N);
 // dW of the layer (columns [col0, col0 + O*I*n) of rows [row0, row0 + nchunk)
@@ -44,5 +46,13 @@ int64_t tc_dw_gy_elems(int J, int O, int64_t N);
 cudaError_t tc_dw_layer(const float* z, const float* gy, void* gy_bf, int I, int O, int64_t N, const Grid& g,
                         unsigned mask, float* partial, int64_t P, int64_t col0, int row0, int nchunk, int* status,
                         cudaStream_t s);
+
+// Tensor-core input adjoint of one hidden layer (tc_adj.cu): BF16, masks 0x0F
+// and 0x1F, after tc_dw_layer of the same layer and point set (it reuses that
+// call's BF16 gy copy).  w_bf: tc_adj_w_elems 2-byte scratch elements.
+bool tc_adj_supported(int prec, int I, int O, int n, unsigned mask);
+int64_t tc_adj_w_elems(int O, int I, int n);
+cudaError_t tc_adj_layer(const float* W, void* w_bf, const void* gy_bf, const float* z, float* gz, int I, int O,
+                         int64_t N, const Grid& g, unsigned mask, int* status, cudaStream_t s);
 
 }  // namespace hrkan

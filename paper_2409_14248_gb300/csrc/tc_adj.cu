@@ -1,0 +1,427 @@
+// Tensor-core (tcgen05) input adjoint of one hidden layer in BF16 with FP32
+// accumulation (reverse mode of the layer contraction w.r.t. its input jets,
+// Sections 2-3, through v''' of Eq. 2):
+//
+//   G_r[p, k] = sum_o gy_r[p, o] W[o, k]                    (dense, tensor cores)
+//   dA_r[p, j, q] = G_r[p, j*NP + c_pj + q],  q = 0..3        (the active bases)
+//   gz[p, j] = rows_adjoint(z[p, j], v', v'', v''', dA[p, j]) (FP32, per unit)
+//
+// A CTA owns UK consecutive units (a K-range of N = UK*NP columns, NP the
+// forward's unit padding) and a chunk of 128-point tiles.  Its W tile
+// [N x O] stays in shared memory; gy_r tiles [128 points x O] stream in by TMA.
+// Both operands are MN-major in the 128-byte swizzle (points / k contiguous,
+// o the MMA's K); D_r = 128 x N accumulates in one of two TMEM buffers so the
+// MMAs of jet row r+1 overlap the epilogue of row r.  The epilogue warps
+// (thread = point = TMEM lane) copy their lane's row of D to shared memory,
+// read back the four entries of each unit at its cell, and after the last jet
+// row apply the adjoint of the jet rows.  Every wait is bounded as in the
+// forward kernel.
+#include <cuda.h>
+
+#include <algorithm>
+#include <mutex>
+#include <unordered_map>
+
+#include "internal.h"
+#include "tc.cuh"
+#include "tc_kernel.cuh"
+
+namespace hrkan {
+namespace tcadj {
+
+using tck::mbar_arrive_if;
+using tck::mbar_drain;
+using tck::mbar_expect_tx;
+using tck::mbar_init;
+using tck::mbar_wait;
+using tck::mma_commit;
+using tck::smem_u32;
+using tck::tc_fence_after;
+using tck::tc_fence_before;
+using tck::tmem_ld16;
+
+constexpr int TILE = 128;   // points per tile (the MMA's M)
+constexpr int NSB = 6;      // gy tile ring
+constexpr int THREADS = 192;
+
+struct AdjParams {
+    const float* z;          // layer input jets [J][I][N]
+    float* gz;               // dL/d(input jets) [J][I][N] (written)
+    int I, O, n;
+    int64_t N;
+    int ntiles, nkr, nchunk;
+    uint32_t tmem_cols;
+    Grid g;
+    int* status;
+};
+
+template <int NP>
+struct Shape {
+    static constexpr int UK = (NP * 4 <= 144) ? 4 : (NP * 3 <= 144 ? 3 : 2);   // units per CTA
+    static constexpr int NC = UK * NP;                                         // D columns
+    static constexpr int NBW = (NC + 63) / 64;                                 // W boxes of 64 k
+    static constexpr int PS = NC + 4;                                          // pick-row stride (floats)
+    static_assert(NC % 16 == 0 && NC <= 256, "MMA N");
+};
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= uint64_t((saddr & 0x3FFFF) >> 4);
+    d |= uint64_t((lbo >> 4) & 0x3FFF) << 16;
+    d |= uint64_t((sbo >> 4) & 0x3FFF) << 32;
+    d |= uint64_t(1) << 46;
+    d |= uint64_t(2) << 61;   // 128-byte swizzle
+    return d;
+}
+
+template <unsigned MASK, int NP>
+__global__ void __launch_bounds__(THREADS, 1)
+    tc_adj_kernel(AdjParams p, const __grid_constant__ CUtensorMap gmap, const __grid_constant__ CUtensorMap wmap) {
+    using JT = Jet<MASK>;
+    using SH = Shape<NP>;
+    constexpr int J = JT::J, UK = SH::UK, NC = SH::NC, NBW = SH::NBW, PS = SH::PS;
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t bar_gfull[NSB], bar_gempty[NSB], bar_dfull[2], bar_dempty[2];
+    __shared__ __align__(8) uint64_t bar_wfull, bar_drain;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+    volatile int* abort = &abort_sh;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int O = p.O, I = p.I;
+    const uint32_t box_bytes = uint32_t(O) * 128u;        // one 64-wide box of O rows
+    const uint32_t g_bytes = 2u * box_bytes;              // gy tile: 128 points
+    uint8_t* wtile = smem;                                // NBW boxes
+    uint8_t* gring = smem + size_t(NBW) * box_bytes;      // NSB tiles
+    float* pick = reinterpret_cast<float*>(gring + size_t(NSB) * g_bytes);   // [128][PS]
+    const int kr = blockIdx.x % p.nkr, chunk = blockIdx.x / p.nkr;
+    const int j0 = kr * UK;
+    const int t0 = int(int64_t(chunk) * p.ntiles / p.nchunk), t1 = int(int64_t(chunk + 1) * p.ntiles / p.nchunk);
+    const int nt = t1 - t0;
+
+    if (tid == 0) {
+        for (int b = 0; b < NSB; ++b) {
+            mbar_init(&bar_gfull[b], 1);
+            mbar_init(&bar_gempty[b], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar_dfull[b], 1);
+            mbar_init(&bar_dempty[b], 4);   // the four epilogue warps
+        }
+        mbar_init(&bar_wfull, 1);
+        mbar_init(&bar_drain, 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(p.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tmem_base_sh;
+
+    if (warp < 4) {
+        // ------------------------------------------------------------ epilogue (thread = point)
+        const int row = warp * 32 + lane;
+        const uint32_t lane_base = uint32_t(warp * 32) << 16;
+        float* prow = pick + row * PS;
+        const int64_t N = p.N;
+        int q = 0;
+        for (int ti = 0; ti < nt; ++ti) {
+            const int64_t pt = int64_t(t0 + ti) * TILE + row;
+            const bool valid = pt < N;
+            const int64_t ptc = valid ? pt : N - 1;
+            float z[UK][J];
+            int cell[UK];
+#pragma unroll
+            for (int u = 0; u < UK; ++u) {
+                const int j = min(j0 + u, I - 1);
+#pragma unroll
+                for (int r = 0; r < J; ++r) z[u][r] = p.z[(int64_t(r) * I + j) * N + ptc];
+                Active<3, 4, 2> b;
+                b.eval(z[u][0], p.g);
+                cell[u] = b.c;
+            }
+            float dA[UK][J][4];
+#pragma unroll
+            for (int r = 0; r < J; ++r, ++q) {
+                const int b = q & 1;
+                if (!__all_sync(0xffffffffu, mbar_wait(&bar_dfull[b], uint32_t(q >> 1) & 1u, abort))) goto done;
+                tc_fence_after();
+#pragma unroll
+                for (int c = 0; c < NC; c += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(tbase + lane_base + uint32_t(b * NC + c), v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int e = 0; e < 16; e += 4)
+                        *reinterpret_cast<uint4*>(prow + c + e) = make_uint4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                mbar_arrive_if(&bar_dempty[b], lane == 0);
+#pragma unroll
+                for (int u = 0; u < UK; ++u)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        int i = cell[u] + k;   // bases outside [0, n) get a clamped entry; their v', v'', v''' are 0
+                        i = i < 0 ? 0 : (i > NP - 1 ? NP - 1 : i);
+                        dA[u][r][k] = prow[u * NP + i];
+                    }
+            }
+#pragma unroll
+            for (int u = 0; u < UK; ++u) {
+                if (j0 + u >= I) break;
+                Active<3, 4, 3> b;
+                b.eval(z[u][0], p.g);
+                float g[J];
+                JT::template rows_adjoint<4>(z[u], b.d1, b.d2, b.d3, dA[u], g);
+                if (valid)
+#pragma unroll
+                    for (int r = 0; r < J; ++r) p.gz[(int64_t(r) * I + j0 + u) * N + pt] = g[r];
+            }
+        }
+    } else if (warp == 4) {
+        // ------------------------------------------------------------ MMA issue
+        if (lane == 0 && nt > 0) {
+            // kind::f16, BF16, A (gy, points contiguous) and B (W, k contiguous) MN-major, FP32 D, M = 128, N = NC
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                                   (uint32_t(NC >> 3) << 17) | (uint32_t(TILE >> 4) << 24);
+            bool issued = false;
+            if (mbar_wait(&bar_wfull, 0u, abort)) {
+                tc_fence_after();
+                const uint32_t wbase = smem_u32(wtile);
+                const int total = nt * J;
+                for (int q = 0; q < total; ++q) {
+                    const int gb = q % NSB, db = q & 1;
+                    if (!mbar_wait(&bar_gfull[gb], uint32_t(q / NSB) & 1u, abort)) break;
+                    if (!mbar_wait(&bar_dempty[db], (uint32_t(q >> 1) & 1u) ^ 1u, abort)) break;
+                    tc_fence_after();
+                    const uint32_t gbase = smem_u32(gring + size_t(gb) * g_bytes);
+                    for (int s = 0; s < O / 16; ++s) {
+                        // 16 o per step = two 8-row K groups (1 KB apart) of both operands
+                        const uint64_t ad = sdesc(gbase + uint32_t(s) * 2048u, box_bytes, 1024);
+                        const uint64_t bd = sdesc(wbase + uint32_t(s) * 2048u, box_bytes, 1024);
+                        asm volatile(
+                            "{\n\t.reg .pred pa;\n\tsetp.ne.b32 pa, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n\t}" ::"r"(
+                                tbase + uint32_t(db * NC)),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(s > 0 ? 1u : 0u)
+                            : "memory");
+                    }
+                    issued = true;
+                    mma_commit(&bar_gempty[gb]);
+                    mma_commit(&bar_dfull[db]);
+                }
+            }
+            if (*abort && issued) {
+                mma_commit(&bar_drain);
+                mbar_drain(&bar_drain, 0u);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ W tile once, gy tiles by TMA
+        if (lane == 0 && nt > 0) {
+            mbar_expect_tx(&bar_wfull, uint32_t(NBW) * box_bytes);
+            for (int bx = 0; bx < NBW; ++bx)
+                tck::tma_load_2d(wtile + size_t(bx) * box_bytes, &wmap, &bar_wfull, j0 * NP + 64 * bx, 0);
+            const int total = nt * J;
+            uint32_t used = 0u, last_par = 0u;
+            for (int q = 0; q < total; ++q) {
+                const int b = q % NSB, ti = q / J, r = q % J;
+                const uint32_t ph = uint32_t(q / NSB) & 1u;
+                if (!mbar_wait(&bar_gempty[b], ph ^ 1u, abort)) break;
+                mbar_expect_tx(&bar_gfull[b], g_bytes);
+                uint8_t* dst = gring + size_t(b) * g_bytes;
+                const int x = (t0 + ti) * TILE;
+                tck::tma_load_2d(dst, &gmap, &bar_gfull[b], x, r * O);
+                tck::tma_load_2d(dst + box_bytes, &gmap, &bar_gfull[b], x + 64, r * O);
+                used |= 1u << b;
+                last_par = (last_par & ~(1u << b)) | (ph << b);
+            }
+            if (*abort) {
+                (void)mbar_wait(&bar_wfull, 0u, abort);
+                mbar_drain(&bar_wfull, 0u);
+                for (int b = 0; b < NSB; ++b)
+                    if ((used >> b) & 1u) mbar_drain(&bar_gfull[b], (last_par >> b) & 1u);
+            }
+        }
+    }
+done:
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && *abort) atomicExch(p.status, tck::ERR_TIMEOUT);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(p.tmem_cols)
+                     : "memory");
+}
+
+// W [O][I][n] float32 -> [O][Kt] BF16, element k = j * NP + i (zero for i >= n or j >= I).
+__global__ void w_bf16_kernel(const float* __restrict__ W, uint16_t* __restrict__ out, int O, int I, int n, int NP,
+                              int Kt) {
+    const int64_t total = int64_t(O) * Kt;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+        const int o = int(t / Kt), k = int(t % Kt);
+        const int j = k / NP, i = k % NP;
+        const float w = (j < I && i < n) ? W[(int64_t(o) * I + j) * n + i] : 0.0f;
+        out[t] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
+    }
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+int np_of(int n) {
+    for (int np : {16, 24, 32, 36, 48, 64})
+        if (n <= np) return np;
+    return 0;
+}
+
+template <unsigned MASK, int NP>
+cudaError_t launch(const AdjParams& p, const CUtensorMap& gm, const CUtensorMap& wm, unsigned grid, cudaStream_t s) {
+    using SH = Shape<NP>;
+    const size_t box = size_t(p.O) * 128;
+    const size_t smem = size_t(SH::NBW) * box + size_t(NSB) * 2 * box + size_t(TILE) * SH::PS * 4 + 1024;
+    auto kern = tc_adj_kernel<MASK, NP>;
+    static std::mutex mu;
+    static std::unordered_map<const void*, size_t> set;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        size_t& cur = set[reinterpret_cast<const void*>(kern)];
+        if (cur < smem) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            if (e != cudaSuccess) { cudaGetLastError(); return e; }
+            cur = smem;
+        }
+    }
+    kern<<<grid, THREADS, smem, s>>>(p, gm, wm);
+    return cudaGetLastError();
+}
+
+template <unsigned MASK>
+cudaError_t launch_np(int np, const AdjParams& p, const CUtensorMap& gm, const CUtensorMap& wm, unsigned grid,
+                      cudaStream_t s) {
+    switch (np) {
+        case 16: return launch<MASK, 16>(p, gm, wm, grid, s);
+        case 24: return launch<MASK, 24>(p, gm, wm, grid, s);
+        case 32: return launch<MASK, 32>(p, gm, wm, grid, s);
+        case 36: return launch<MASK, 36>(p, gm, wm, grid, s);
+        case 48: return launch<MASK, 48>(p, gm, wm, grid, s);
+        case 64: return launch<MASK, 64>(p, gm, wm, grid, s);
+    }
+    return cudaErrorNotSupported;
+}
+
+int units_per_cta(int np) {
+    switch (np) {
+        case 16: return Shape<16>::UK;
+        case 24: return Shape<24>::UK;
+        case 32: return Shape<32>::UK;
+        case 36: return Shape<36>::UK;
+        case 48: return Shape<48>::UK;
+        case 64: return Shape<64>::UK;
+    }
+    return 0;
+}
+
+}  // namespace tcadj
+
+bool tc_adj_supported(int prec, int I, int O, int n, unsigned mask) {
+    return tc_dw_supported(prec, I, O, n, mask) && tcadj::np_of(n) != 0 && mask != 0x01u;
+}
+
+int64_t tc_adj_w_elems(int O, int I, int n) {
+    const int np = tcadj::np_of(n);
+    return int64_t(O) * ((int64_t(I) * np + 63) / 64 * 64);
+}
+
+cudaError_t tc_adj_layer(const float* W, void* w_bf, const void* gy_bf, const float* z, float* gz, int I, int O,
+                         int64_t N, const Grid& g, unsigned mask, int* status, cudaStream_t s) {
+    using namespace tcadj;
+    if (N == 0) return cudaSuccess;
+    const int n = g.n, np = np_of(n);
+    const int J = __builtin_popcount(mask & 0x1Fu);
+    const int Kt = int((int64_t(I) * np + 63) / 64 * 64);
+    {
+        const int64_t total = int64_t(O) * Kt;
+        const int pb = int(std::min<int64_t>((total + 255) / 256, 4096));
+        w_bf16_kernel<<<pb, 256, 0, s>>>(W, static_cast<uint16_t*>(w_bf), O, I, n, np, Kt);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const int64_t Npad = (N + 63) / 64 * 64;
+    CUtensorMap gm, wm;
+    {
+        const cuuint64_t dims[2] = {cuuint64_t(Npad), cuuint64_t(int64_t(J) * O)};
+        const cuuint64_t strides[1] = {cuuint64_t(Npad) * 2};
+        const cuuint32_t box[2] = {64, cuuint32_t(O)};
+        const cuuint32_t estr[2] = {1, 1};
+        if (enc(&gm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(gy_bf), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        const cuuint64_t dims[2] = {cuuint64_t(Kt), cuuint64_t(O)};
+        const cuuint64_t strides[1] = {cuuint64_t(Kt) * 2};
+        const cuuint32_t box[2] = {64, cuuint32_t(O)};
+        const cuuint32_t estr[2] = {1, 1};
+        if (enc(&wm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, w_bf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    AdjParams p{};
+    p.z = z;
+    p.gz = gz;
+    p.I = I;
+    p.O = O;
+    p.n = n;
+    p.N = N;
+    p.ntiles = int((N + TILE - 1) / TILE);
+    const int uk = units_per_cta(np);
+    p.nkr = (I + uk - 1) / uk;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // about one CTA per SM over the K-ranges, at least one tile each
+    p.nchunk = std::max(1, std::min(p.ntiles, (nsm + p.nkr - 1) / p.nkr));
+    const int cols = 2 * uk * np;
+    p.tmem_cols = cols <= 32 ? 32u : cols <= 64 ? 64u : cols <= 128 ? 128u : cols <= 256 ? 256u : 512u;
+    p.g = g;
+    p.status = status;
+    const unsigned grid = unsigned(p.nkr) * unsigned(p.nchunk);
+    switch (mask) {
+        case 0x0Fu: return launch_np<0x0Fu>(np, p, gm, wm, grid, s);
+        case 0x1Fu: return launch_np<0x1Fu>(np, p, gm, wm, grid, s);
+    }
+    return cudaErrorNotSupported;
+}
+
+}  // namespace hrkan

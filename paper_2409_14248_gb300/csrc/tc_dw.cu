@@ -367,6 +367,14 @@ cudaError_t launch_nc(int nc, const DwParams& p, const CUtensorMap& map, unsigne
 
 }  // namespace tcdw
 
+cudaError_t tc_gy_to_bf16(const float* gy, void* gy_bf, int J, int O, int64_t N, cudaStream_t s) {
+    const int64_t Npad = (std::max<int64_t>(N, 1) + 63) / 64 * 64;
+    const int64_t rows = int64_t(J) * O, total = rows * Npad;
+    const int pb = int(std::min<int64_t>((total + 255) / 256, 8192));
+    tcdw::gy_bf16_kernel<<<pb, 256, 0, s>>>(gy, static_cast<uint16_t*>(gy_bf), rows, N, Npad);
+    return cudaGetLastError();
+}
+
 bool tc_dw_supported(int prec, int I, int O, int n, unsigned mask) {
     if (prec != HRKAN_BF16) return false;
     if (O < 16 || O > 64 || O % 16 != 0 || n > 64 || n < 1 || I < 1) return false;
@@ -383,13 +391,7 @@ cudaError_t tc_dw_layer(const float* z, const float* gy, void* gy_bf, int I, int
     const int n = g.n, np8 = np8_of(n);
     const int64_t Npad = (std::max<int64_t>(N, 1) + 63) / 64 * 64;
     const int64_t rows = int64_t(J) * O;
-    {
-        const int64_t total = rows * Npad;
-        const int pb = int(std::min<int64_t>((total + 255) / 256, 8192));
-        gy_bf16_kernel<<<pb, 256, 0, s>>>(gy, static_cast<uint16_t*>(gy_bf), rows, N, Npad);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
+    if (cudaError_t e = tc_gy_to_bf16(gy, gy_bf, J, O, N, s)) return e;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;

@@ -299,3 +299,67 @@ def test_fp32_layer_dw_matches_oracle(mask):
     got, launches = _layer_dw(capi.HRKAN_FP32, I, O, G, z, gy, mask, N)
     assert launches == 0
     assert relerr(got, oracle.layer_dw(I, O, G, 3, 4, -1.0, 1.0, z, gy, mask)) < 1e-5
+
+
+# ------------------------------------------------------------------ input adjoint (BF16)
+
+def _layer_adj(prec, I, O, G, Wl, z, gy, mask, N, lo=-1.0, hi=1.0):
+    cfg = capi.make_cfg([2, I, O, 1], G, lo=lo, hi=hi, prec=prec, flags=capi.HRKAN_FLAG_LAYERWISE)
+    h = capi.hrkan_init(cfg)
+    try:
+        J = oracle.n_rows(mask)
+        gz = torch.full((J, I, N), float("nan"), device="cuda")
+        capi.hrkan_profile_enable(h, True)
+        capi.hrkan_layer_adjoint(h, 1, _dev(Wl), _dev(z), _dev(gy), N, mask, gz)
+        capi.hrkan_sync_status(h)
+        tensor_launches = capi.hrkan_profile_read(h, capi.HRKAN_KERNEL_TENSOR)[1]
+        return gz.cpu().numpy(), tensor_launches
+    finally:
+        capi.hrkan_destroy(h)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("mask", [0x0F, 0x1F])
+def test_tc_layer_adjoint_matches_rounding_aware_oracle(shape, mask):
+    """BF16 tensor-core input adjoint of one hidden layer on seeded random jets: per jet row
+    equal to the oracle adjoint with BF16-rounded gy and weights up to float32 arithmetic, far
+    from the unrounded one."""
+    I, O, G = shape
+    n = G + 3
+    N = 389
+    J = oracle.n_rows(mask)
+    z = inputs.layer_jets(I, N, mask, seed=I * 23 + O)
+    gy = np.random.default_rng(G + 1).normal(0, 1, (J, O, N)).astype(np.float32)
+    Wl = (0.3 * np.random.default_rng(O + 2).standard_normal(O * I * n)).astype(np.float32)
+    got, launches = _layer_adj(capi.HRKAN_BF16, I, O, G, Wl, z, gy, mask, N)
+    assert launches == 1
+    rounded = oracle.layer_adjoint(I, O, G, 3, 4, -1.0, 1.0, Wl, z, gy, mask, oracle.BF16)
+    exact = oracle.layer_adjoint(I, O, G, 3, 4, -1.0, 1.0, Wl, z, gy, mask)
+    for r in range(J):
+        e_impl, e_fmt = relerr(got[r], rounded[r]), relerr(rounded[r], exact[r])
+        assert e_impl < 2e-5 + FLIP * e_fmt, (r, e_impl, e_fmt)
+        assert e_fmt > 4 * e_impl, (r, e_impl, e_fmt)
+
+
+@pytest.mark.parametrize("shape", KNOT_SHAPES)
+def test_tc_layer_adjoint_exact_on_knots(shape):
+    """Knot inputs, gy multiples of 1/8 below 16 and weights multiples of 2^-7 (all exact in
+    BF16): the tensor-core adjoint equals the exact oracle up to float32 arithmetic, over
+    several tiles per CTA."""
+    I, O, G, lo, hi = shape
+    n = G + 3
+    h = (hi - lo) / G
+    N = 64 * 40 + 333
+    rng = np.random.default_rng(I * 11 + G)
+    z = np.zeros((5, I, N), np.float32)
+    z[0] = lo + rng.integers(-5, G + 5, (I, N)) * h
+    z[1:3] = rng.choice([-0.5, 0.5], (2, I, N))
+    z[3:5] = rng.choice([0.0, -2.0, 2.0, -4.0, 4.0], (2, I, N))
+    gy = (rng.integers(-127, 128, (5, O, N)) / 8.0).astype(np.float32)
+    Wl = (rng.integers(-127, 128, O * I * n) / 128.0).astype(np.float32)
+    got, launches = _layer_adj(capi.HRKAN_BF16, I, O, G, Wl, z, gy, 0x1F, N, lo, hi)
+    assert launches == 1
+    exact = oracle.layer_adjoint(I, O, G, 3, 4, lo, hi, Wl, z, gy, 0x1F)
+    assert np.array_equal(oracle.layer_adjoint(I, O, G, 3, 4, lo, hi, Wl, z, gy, 0x1F, oracle.BF16), exact)
+    for r in range(5):
+        assert relerr(got[r], exact[r]) < 1e-5, r
