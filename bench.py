@@ -60,16 +60,21 @@ def measured_peaks():
         return {"bf16": 1900.0, "bf16_sustained": 1700.0, "source": "of fallback"}
 
 
-def dense_tc_flops(widths, G, k, n_int, J_int, n_bnd):
-    """Dense flops of the tensor-core launches of one training step: for every
-    hidden layer the forward contraction and the weight gradient, each
+def dense_tc_flops(widths, G, k, n_int, J_int, n_bnd, bf16):
+    """Dense flops of the tensor-core launches of one training step, each
     2 * rows * K * O with K = I * (G + k) and rows = J * points (all K columns
-    counted, zeros included)."""
+    counted, zeros included): for every hidden layer the forward contraction
+    (interior and boundary points) and, in BF16, the weight gradient (both
+    point sets) and the input adjoint G = gy W (interior points; the
+    boundary's single jet row keeps the FP32 adjoint)."""
     n = G + k
     f = 0
     for l in range(1, len(widths) - 2):
         I, O = widths[l], widths[l + 1]
-        f += 2 * 2 * (J_int * n_int + n_bnd) * I * n * O
+        fwd = 2 * (J_int * n_int + n_bnd) * I * n * O
+        f += fwd
+        if bf16:
+            f += fwd + 2 * J_int * n_int * I * n * O
     return f
 
 
@@ -253,7 +258,8 @@ def launches_per_step(widths, prec, tc_fwd, tc_dw, fused):
     L = len(widths) - 1
     per_set_fwd = sum(2 if tc_fwd(l) else 1 for l in range(L))
     per_set_bwd = sum(2 if tc_dw(l) else 1 for l in range(L)) + (L - 1)
-    return 2 * per_set_fwd + 2 * per_set_bwd + 2   # interior and boundary sets, residual, reduction+Adam
+    tc_adj = sum(1 for l in range(1, L) if tc_dw(l))   # interior set: the adjoint kernel reuses the dW's gy copy
+    return 2 * per_set_fwd + 2 * per_set_bwd + tc_adj * 1 + 2   # + w conversion; residual, reduction+Adam
 
 
 def time_steps(torch, capi, h, step, first_t, steps, flush):
@@ -394,12 +400,12 @@ def run_ours(args, ws, rank, local):
             tc_ms, tc_n = prof[capi.HRKAN_KERNEL_TENSOR]
             pk = measured_peaks()
             peak = pk["bf16_sustained"] * (1.0 if prec == PRECS["bf16"] else 0.5)
-            fwd_flops = dense_tc_flops(w.widths, w.G, w.k, Ni, J, Nb) / 2
-            flops = fwd_flops * (2 if prec == PRECS["bf16"] else 1)   # forward (+ weight gradient in BF16)
+            flops = dense_tc_flops(w.widths, w.G, w.k, Ni, J, Nb, prec == PRECS["bf16"])
             achieved = flops * args.steps / (tc_ms / 1e3) / 1e12
             roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak, "traffic": None,
-                        "kernel": "tc_fwd_kernel + tc_dw_kernel (hidden layers)" if prec == PRECS["bf16"]
+                        "kernel": "tc_fwd_kernel + tc_dw_kernel + tc_adj_kernel (hidden layers)"
+                        if prec == PRECS["bf16"]
                         else "tc_fwd_kernel (hidden layers)",
                         "kernel_ms_per_step": tc_ms / args.steps, "launches_per_step": tc_n / args.steps,
                         "flops_per_step": flops, "peak_source": ("bf16 dense sustained " if prec == PRECS["bf16"]
