@@ -14,7 +14,8 @@
 // MMAs of jet row r+1 overlap the epilogue of row r.  The epilogue warps
 // (thread = point = TMEM lane) copy their lane's row of D to shared memory,
 // read back the four entries of each unit at its cell, and after the last jet
-// row apply the adjoint of the jet rows.  Every wait is bounded as in the
+// row apply the adjoint of the jet rows (two warps per lane quarter, each half
+// of the units).  Every wait is bounded as in the
 // forward kernel.
 #include <cuda.h>
 
@@ -38,11 +39,11 @@ using tck::mma_commit;
 using tck::smem_u32;
 using tck::tc_fence_after;
 using tck::tc_fence_before;
-using tck::tmem_ld16;
 
 constexpr int TILE = 128;   // points per tile (the MMA's M)
 constexpr int NSB = 6;      // gy tile ring
-constexpr int THREADS = 192;
+constexpr int EPI_WARPS = 8;   // two per TMEM lane quarter, each half of the CTA's units
+constexpr int THREADS = 32 * EPI_WARPS + 64;
 
 struct AdjParams {
     const float* z;          // layer input jets [J][I][N]
@@ -55,12 +56,20 @@ struct AdjParams {
     int* status;
 };
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+
 template <int NP>
 struct Shape {
-    static constexpr int UK = (NP * 4 <= 144) ? 4 : (NP * 3 <= 144 ? 3 : 2);   // units per CTA
-    static constexpr int NC = UK * NP;                                         // D columns
-    static constexpr int NBW = (NC + 63) / 64;                                 // W boxes of 64 k
-    static constexpr int PS = NC + 4;                                          // pick-row stride (floats)
+    static constexpr int UK = (NP * 4 <= 144) ? 4 : 2;   // units per CTA (even: two epilogue halves)
+    static constexpr int UH = UK / 2;                    // units per epilogue warp
+    static constexpr int NC = UK * NP;                   // D columns
+    static constexpr int NBW = (NC + 63) / 64;           // W boxes of 64 k
+    static constexpr int PS = UH * NP + 4;               // pick-row stride (floats) of one half
     static_assert(NC % 16 == 0 && NC <= 256, "MMA N");
 };
 
@@ -80,6 +89,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     using JT = Jet<MASK>;
     using SH = Shape<NP>;
     constexpr int J = JT::J, UK = SH::UK, NC = SH::NC, NBW = SH::NBW, PS = SH::PS;
+    static_assert(UK % 2 == 0, "two epilogue halves");
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -108,7 +118,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&bar_dfull[b], 1);
-            mbar_init(&bar_dempty[b], 4);   // the four epilogue warps
+            mbar_init(&bar_dempty[b], EPI_WARPS);
         }
         mbar_init(&bar_wfull, 1);
         mbar_init(&bar_drain, 1);
@@ -126,68 +136,84 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc_fence_after();
     const uint32_t tbase = tmem_base_sh;
 
-    if (warp < 4) {
+    if (warp < EPI_WARPS) {
         // ------------------------------------------------------------ epilogue (thread = point)
-        const int row = warp * 32 + lane;
-        const uint32_t lane_base = uint32_t(warp * 32) << 16;
-        float* prow = pick + row * PS;
+        constexpr int UH = SH::UH;
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row = quarter * 32 + lane;
+        const uint32_t lane_base = uint32_t(quarter * 32) << 16;
+        float* prow = pick + (half * TILE + row) * PS;
+        const int ju = j0 + half * UH;                 // this warp's first unit
         const int64_t N = p.N;
+        auto load_z = [&](int ti, float (&zz)[UH][J]) {
+            const int64_t pt = int64_t(t0 + ti) * TILE + row;
+            const float* zp = p.z + (pt < N ? pt : N - 1);
+#pragma unroll
+            for (int u = 0; u < UH; ++u) {
+                const int j = min(ju + u, I - 1);
+#pragma unroll
+                for (int r = 0; r < J; ++r) zz[u][r] = zp[(int64_t(r) * I + j) * N];
+            }
+        };
+        float zn[UH][J];
+        if (nt > 0) load_z(0, zn);
         int q = 0;
         for (int ti = 0; ti < nt; ++ti) {
             const int64_t pt = int64_t(t0 + ti) * TILE + row;
             const bool valid = pt < N;
-            const int64_t ptc = valid ? pt : N - 1;
-            float z[UK][J];
-            int cell[UK];
+            float z[UH][J];
 #pragma unroll
-            for (int u = 0; u < UK; ++u) {
-                const int j = min(j0 + u, I - 1);
+            for (int u = 0; u < UH; ++u)
 #pragma unroll
-                for (int r = 0; r < J; ++r) z[u][r] = p.z[(int64_t(r) * I + j) * N + ptc];
+                for (int r = 0; r < J; ++r) z[u][r] = zn[u][r];
+            if (ti + 1 < nt) load_z(ti + 1, zn);   // next tile's jets, one tile ahead
+            int cell[UH];
+#pragma unroll
+            for (int u = 0; u < UH; ++u) {
                 Active<3, 4, 2> b;
                 b.eval(z[u][0], p.g);
                 cell[u] = b.c;
             }
-            float dA[UK][J][4];
+            float dA[UH][J][4];
 #pragma unroll
             for (int r = 0; r < J; ++r, ++q) {
                 const int b = q & 1;
                 if (!__all_sync(0xffffffffu, mbar_wait(&bar_dfull[b], uint32_t(q >> 1) & 1u, abort))) goto done;
                 tc_fence_after();
+                const uint32_t col0 = uint32_t(b * NC + half * UH * NP);
 #pragma unroll
-                for (int c = 0; c < NC; c += 16) {
-                    uint32_t v[16];
-                    tmem_ld16(tbase + lane_base + uint32_t(b * NC + c), v);
+                for (int c = 0; c < UH * NP; c += 8) {
+                    uint32_t v[8];
+                    tmem_ld8(tbase + lane_base + col0 + uint32_t(c), v);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int e = 0; e < 16; e += 4)
-                        *reinterpret_cast<uint4*>(prow + c + e) = make_uint4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                    *reinterpret_cast<uint4*>(prow + c) = make_uint4(v[0], v[1], v[2], v[3]);
+                    *reinterpret_cast<uint4*>(prow + c + 4) = make_uint4(v[4], v[5], v[6], v[7]);
                 }
                 tc_fence_before();
                 __syncwarp();
                 mbar_arrive_if(&bar_dempty[b], lane == 0);
 #pragma unroll
-                for (int u = 0; u < UK; ++u)
+                for (int u = 0; u < UH; ++u)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        int i = cell[u] + k;   // bases outside [0, n) get a clamped entry; their v', v'', v''' are 0
+                        int i = cell[u] + k;   // bases outside [0, n) get a clamped entry; their derivatives are 0
                         i = i < 0 ? 0 : (i > NP - 1 ? NP - 1 : i);
                         dA[u][r][k] = prow[u * NP + i];
                     }
             }
 #pragma unroll
-            for (int u = 0; u < UK; ++u) {
-                if (j0 + u >= I) break;
+            for (int u = 0; u < UH; ++u) {
+                if (ju + u >= I) break;
                 Active<3, 4, 3> b;
                 b.eval(z[u][0], p.g);
                 float g[J];
                 JT::template rows_adjoint<4>(z[u], b.d1, b.d2, b.d3, dA[u], g);
                 if (valid)
 #pragma unroll
-                    for (int r = 0; r < J; ++r) p.gz[(int64_t(r) * I + j0 + u) * N + pt] = g[r];
+                    for (int r = 0; r < J; ++r) p.gz[(int64_t(r) * I + ju + u) * N + pt] = g[r];
             }
         }
-    } else if (warp == 4) {
+    } else if (warp == EPI_WARPS) {
         // ------------------------------------------------------------ MMA issue
         if (lane == 0 && nt > 0) {
             // kind::f16, BF16, A (gy, points contiguous) and B (W, k contiguous) MN-major, FP32 D, M = 128, N = NC
@@ -305,7 +331,7 @@ template <unsigned MASK, int NP>
 cudaError_t launch(const AdjParams& p, const CUtensorMap& gm, const CUtensorMap& wm, unsigned grid, cudaStream_t s) {
     using SH = Shape<NP>;
     const size_t box = size_t(p.O) * 128;
-    const size_t smem = size_t(SH::NBW) * box + size_t(NSB) * 2 * box + size_t(TILE) * SH::PS * 4 + 1024;
+    const size_t smem = size_t(SH::NBW) * box + size_t(NSB) * 2 * box + size_t(2 * TILE) * SH::PS * 4 + 1024;
     auto kern = tc_adj_kernel<MASK, NP>;
     static std::mutex mu;
     static std::unordered_map<const void*, size_t> set;
@@ -410,8 +436,8 @@ cudaError_t tc_adj_layer(const float* W, void* w_bf, const void* gy_bf, const fl
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    // about one CTA per SM over the K-ranges, at least one tile each
-    p.nchunk = std::max(1, std::min(p.ntiles, (nsm + p.nkr - 1) / p.nkr));
+    // at most one CTA per SM over the K-ranges (a single wave), at least one tile each
+    p.nchunk = std::max(1, std::min(p.ntiles, nsm / p.nkr));
     const int cols = 2 * uk * np;
     p.tmem_cols = cols <= 32 ? 32u : cols <= 64 ? 64u : cols <= 128 ? 128u : cols <= 256 ? 256u : 512u;
     p.g = g;
