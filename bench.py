@@ -65,8 +65,8 @@ def dense_tc_flops(widths, G, k, n_int, J_int, n_bnd, bf16):
     2 * rows * K * O with K = I * (G + k) and rows = J * points (all K columns
     counted, zeros included): for every hidden layer the forward contraction
     (interior and boundary points) and, in BF16, the weight gradient (both
-    point sets) and the input adjoint G = gy W (interior points; the
-    boundary's single jet row keeps the FP32 adjoint)."""
+    point sets; also of the first layer) and the input adjoint G = gy W
+    (interior points; the boundary's single jet row keeps the FP32 adjoint)."""
     n = G + k
     f = 0
     for l in range(1, len(widths) - 2):
@@ -75,6 +75,8 @@ def dense_tc_flops(widths, G, k, n_int, J_int, n_bnd, bf16):
         f += fwd
         if bf16:
             f += fwd + 2 * J_int * n_int * I * n * O
+    if bf16 and 16 <= widths[1] <= 64 and widths[1] % 16 == 0:   # first layer's weight gradient
+        f += 2 * (J_int * n_int + n_bnd) * widths[0] * n * widths[1]
     return f
 
 
@@ -258,7 +260,7 @@ def launches_per_step(widths, prec, tc_fwd, tc_dw, fused):
     L = len(widths) - 1
     per_set_fwd = sum(2 if tc_fwd(l) else 1 for l in range(L))
     per_set_bwd = sum(2 if tc_dw(l) else 1 for l in range(L)) + (L - 1)
-    tc_adj = sum(1 for l in range(1, L) if tc_dw(l))   # interior set: the adjoint kernel reuses the dW's gy copy
+    tc_adj = sum(1 for l in range(1, L) if tc_dw(l) and 0 < l < L - 1)   # interior set (reuses the dW's gy copy)
     return 2 * per_set_fwd + 2 * per_set_bwd + tc_adj * 1 + 2   # + w conversion; residual, reduction+Adam
 
 
@@ -377,7 +379,8 @@ def run_ours(args, ws, rank, local):
         hidden = lambda l: 0 < l < len(w.widths) - 2
         tc_ok = lambda l: hidden(l) and 16 <= w.widths[l + 1] <= 64 and w.widths[l + 1] % 16 == 0 and n <= 64
         tc_fwd = lambda l: prec != PRECS["fp32"] and tc_ok(l)
-        tc_dw = lambda l: prec == PRECS["bf16"] and tc_ok(l)
+        tc_dw = lambda l: prec == PRECS["bf16"] and (tc_ok(l) or (l == 0 and 16 <= w.widths[1] <= 64
+                                                                   and w.widths[1] % 16 == 0 and n <= 64))
         launches = launches_per_step(w.widths, prec, tc_fwd, tc_dw, fused) * args.steps
         if prec == PRECS["fp32"]:
             fused_ms, fused_n = prof[capi.HRKAN_KERNEL_FUSED]

@@ -370,16 +370,18 @@ int wide_forward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsig
 }
 
 // Weight gradient of layer l into partial rows [d.row0, d.row0 + d.GP): the
-// tensor-core kernel for BF16 hidden layers it supports, else FP32 SIMT.
+// tensor-core kernel for the BF16 layers it supports (hidden layers and the
+// first layer), else FP32 SIMT.
 int layer_dw(hrkan_t h, const WideDw& d, int l, unsigned mask, cudaStream_t s) {
     cudaError_t e;
-    if (l > 0 && tc_dw_supported(h->cfg.prec, d.I, d.O, h->n, mask)) {
+    if (tc_dw_supported(h->cfg.prec, d.I, d.O, h->n, mask)) {
         int rc = HRKAN_OK;
         const int64_t el = tc_dw_gy_elems(jets_of(mask), d.O, d.N);
         float* gbf = ws_get(h, 11, size_t((el + 1) / 2), &rc);   // 2-byte elements in 4-byte slots
         if (!gbf) return rc;
         ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
-        e = tc_dw_layer(d.z, d.gy, gbf, d.I, d.O, d.N, d.g, mask, d.partial, d.P, d.col0, d.row0, d.GP, h->status, s);
+        e = tc_dw_layer(d.z, d.gy, gbf, d.I, d.O, d.N, d.g, mask, l == 0, d.partial, d.P, d.col0, d.row0, d.GP,
+                        h->status, s);
     } else {
         ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
         e = wide_dw_layer(d, mask, l == 0, s);

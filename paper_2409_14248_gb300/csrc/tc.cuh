@@ -43,9 +43,10 @@ int64_t tc_dw_gy_elems(int J, int O, int64_t N);
 // dW of the layer (columns [col0, col0 + O*I*n) of rows [row0, row0 + nchunk)
 // of partial [rows][P]) from input jets z [J][I][N] and output-jet gradients
 // gy [J][O][N]; gy_bf is scratch of tc_dw_gy_elems 2-byte elements.
+// first: z is the coordinates [2][N] (layer 0).
 cudaError_t tc_dw_layer(const float* z, const float* gy, void* gy_bf, int I, int O, int64_t N, const Grid& g,
-                        unsigned mask, float* partial, int64_t P, int64_t col0, int row0, int nchunk, int* status,
-                        cudaStream_t s);
+                        unsigned mask, bool first, float* partial, int64_t P, int64_t col0, int row0, int nchunk,
+                        int* status, cudaStream_t s);
 
 // Tensor-core input adjoint of one hidden layer (tc_adj.cu): BF16, masks 0x0F
 // and 0x1F, after tc_dw_layer of the same layer and point set (it reuses that

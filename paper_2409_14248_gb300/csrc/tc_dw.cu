@@ -1,5 +1,6 @@
 // Tensor-core (tcgen05) weight gradient of one hidden layer in BF16 with FP32
-// accumulation (reverse mode of the layer contraction, Sections 2-3):
+// accumulation (reverse mode of the layer contraction, Sections 2-3), hidden
+// layers and (FIRST) the first layer, whose inputs are the coordinates:
 //
 //   dW[o, k] = sum_p sum_r gy_r[p, o] * A_r[p, k],   k = j*NP8 + i (padded units)
 //
@@ -81,7 +82,7 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
-template <unsigned MASK, int NC>
+template <unsigned MASK, int NC, bool FIRST>
 __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __grid_constant__ CUtensorMap gmap) {
     using JT = Jet<MASK>;
     constexpr int J = JT::J;
@@ -146,7 +147,18 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
 #pragma unroll
             for (int u = 0; u < MAXU; ++u)
 #pragma unroll
-                for (int r = 0; r < J; ++r) zz[u][r] = u < nu ? zp[(int64_t(r) * I + jn[u]) * N] : 0.0f;
+                for (int r = 0; r < J; ++r) {
+                    if constexpr (FIRST) {
+                        // first layer: the coordinate x_j, dx_j/dx_d = [j == d], no second derivative
+                        const int j = u < nu ? jn[u] : 0;
+                        if (r == 0) zz[u][r] = zp[int64_t(j) * N];
+                        else if (r == JT::RF0 && JT::F0) zz[u][r] = j == 0 ? 1.0f : 0.0f;
+                        else if (r == JT::RF1 && JT::F1) zz[u][r] = j == 1 ? 1.0f : 0.0f;
+                        else zz[u][r] = 0.0f;
+                    } else {
+                        zz[u][r] = u < nu ? zp[(int64_t(r) * I + jn[u]) * N] : 0.0f;
+                    }
+                }
         };
         float zn[MAXU][J];
         if (ng > 0) load_z(g0, zn);
@@ -332,10 +344,10 @@ EncodeTiledFn encode_fn() {
 
 int np8_of(int n) { return (n + 7) / 8 * 8; }
 
-template <unsigned MASK, int NC>
+template <unsigned MASK, int NC, bool FIRST>
 cudaError_t launch(const DwParams& p, const CUtensorMap& map, unsigned grid, cudaStream_t s) {
     const size_t smem = size_t(NSB) * (A_BYTES + size_t(p.O) * 128) + 1024;
-    auto kern = tc_dw_kernel<MASK, NC>;
+    auto kern = tc_dw_kernel<MASK, NC, FIRST>;
     static std::mutex mu;
     static std::unordered_map<const void*, size_t> set;
     {
@@ -351,16 +363,16 @@ cudaError_t launch(const DwParams& p, const CUtensorMap& map, unsigned grid, cud
     return cudaGetLastError();
 }
 
-template <unsigned MASK>
+template <unsigned MASK, bool FIRST>
 cudaError_t launch_nc(int nc, const DwParams& p, const CUtensorMap& map, unsigned grid, cudaStream_t s) {
     switch (nc) {
-        case 2: return launch<MASK, 2>(p, map, grid, s);
-        case 3: return launch<MASK, 3>(p, map, grid, s);
-        case 4: return launch<MASK, 4>(p, map, grid, s);
-        case 5: return launch<MASK, 5>(p, map, grid, s);
-        case 6: return launch<MASK, 6>(p, map, grid, s);
-        case 7: return launch<MASK, 7>(p, map, grid, s);
-        case 8: return launch<MASK, 8>(p, map, grid, s);
+        case 2: return launch<MASK, 2, FIRST>(p, map, grid, s);
+        case 3: return launch<MASK, 3, FIRST>(p, map, grid, s);
+        case 4: return launch<MASK, 4, FIRST>(p, map, grid, s);
+        case 5: return launch<MASK, 5, FIRST>(p, map, grid, s);
+        case 6: return launch<MASK, 6, FIRST>(p, map, grid, s);
+        case 7: return launch<MASK, 7, FIRST>(p, map, grid, s);
+        case 8: return launch<MASK, 8, FIRST>(p, map, grid, s);
     }
     return cudaErrorNotSupported;
 }
@@ -384,8 +396,8 @@ bool tc_dw_supported(int prec, int I, int O, int n, unsigned mask) {
 int64_t tc_dw_gy_elems(int J, int O, int64_t N) { return int64_t(J) * O * ((N + 63) / 64 * 64); }
 
 cudaError_t tc_dw_layer(const float* z, const float* gy, void* gy_bf, int I, int O, int64_t N, const Grid& g,
-                        unsigned mask, float* partial, int64_t P, int64_t col0, int row0, int nchunk, int* status,
-                        cudaStream_t s) {
+                        unsigned mask, bool first, float* partial, int64_t P, int64_t col0, int row0, int nchunk,
+                        int* status, cudaStream_t s) {
     using namespace tcdw;
     const int J = __builtin_popcount(mask & 0x1Fu);
     const int n = g.n, np8 = np8_of(n);
@@ -422,10 +434,18 @@ cudaError_t tc_dw_layer(const float* z, const float* gy, void* gy_bf, int I, int
     p.status = status;
     const unsigned grid = unsigned(p.nkr) * unsigned(nchunk);
     const int nc = np8 / 8;
-    switch (mask) {
-        case 0x01u: return launch_nc<0x01u>(nc, p, map, grid, s);
-        case 0x0Fu: return launch_nc<0x0Fu>(nc, p, map, grid, s);
-        case 0x1Fu: return launch_nc<0x1Fu>(nc, p, map, grid, s);
+    if (first) {
+        switch (mask) {
+            case 0x01u: return launch_nc<0x01u, true>(nc, p, map, grid, s);
+            case 0x0Fu: return launch_nc<0x0Fu, true>(nc, p, map, grid, s);
+            case 0x1Fu: return launch_nc<0x1Fu, true>(nc, p, map, grid, s);
+        }
+    } else {
+        switch (mask) {
+            case 0x01u: return launch_nc<0x01u, false>(nc, p, map, grid, s);
+            case 0x0Fu: return launch_nc<0x0Fu, false>(nc, p, map, grid, s);
+            case 0x1Fu: return launch_nc<0x1Fu, false>(nc, p, map, grid, s);
+        }
     }
     return cudaErrorNotSupported;
 }

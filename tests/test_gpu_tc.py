@@ -363,3 +363,35 @@ def test_tc_layer_adjoint_exact_on_knots(shape):
     assert np.array_equal(oracle.layer_adjoint(I, O, G, 3, 4, lo, hi, Wl, z, gy, 0x1F, oracle.BF16), exact)
     for r in range(5):
         assert relerr(got[r], exact[r]) < 1e-5, r
+
+
+@pytest.mark.parametrize("mask", [0x01, 0x0F, 0x1F])
+def test_tc_first_layer_dw_matches_rounding_aware_oracle(mask):
+    """The first layer's BF16 weight gradient (inputs = the coordinates, dx_j/dx_d = [j == d])
+    runs on the tensor cores too."""
+    O, G, N = 64, 32, 389
+    J = oracle.n_rows(mask)
+    x = np.random.default_rng(90).uniform(-1, 1, (2, N)).astype(np.float32)
+    gy = np.random.default_rng(91).normal(0, 1, (J, O, N)).astype(np.float32)
+    z0 = np.zeros((J, 2, N))
+    z0[0] = x
+    rows = [b for b in range(5) if mask >> b & 1]
+    for r, b in enumerate(rows):
+        if b in (1, 2):
+            z0[r, b - 1] = 1.0
+    cfg = capi.make_cfg([2, O, O, 1], G, prec=capi.HRKAN_BF16, flags=capi.HRKAN_FLAG_LAYERWISE)
+    h = capi.hrkan_init(cfg)
+    try:
+        dW = torch.full((O * 2 * (G + 3),), float("nan"), device="cuda")
+        capi.hrkan_profile_enable(h, True)
+        capi.hrkan_layer_dw(h, 0, _dev(x), _dev(gy), N, mask, dW)
+        capi.hrkan_sync_status(h)
+        assert capi.hrkan_profile_read(h, capi.HRKAN_KERNEL_TENSOR)[1] == 1
+        got = dW.cpu().numpy()
+    finally:
+        capi.hrkan_destroy(h)
+    rounded = oracle.layer_dw(2, O, G, 3, 4, -1.0, 1.0, z0, gy, mask, oracle.BF16)
+    exact = oracle.layer_dw(2, O, G, 3, 4, -1.0, 1.0, z0, gy, mask)
+    e_impl, e_fmt = relerr(got, rounded), relerr(rounded, exact)
+    assert e_impl < 2e-5 + FLIP * e_fmt, (e_impl, e_fmt)
+    assert e_fmt > 4 * e_impl
