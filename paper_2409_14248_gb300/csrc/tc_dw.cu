@@ -312,13 +312,23 @@ done:
                      : "memory");
 }
 
-// gy [J][O][N] float32 -> [J*O][Npad] BF16, zero for points >= N.
+// gy [J][O][N] float32 -> [J*O][Npad] BF16, zero for points >= N; one thread
+// converts 8 consecutive points of a row and stores them as one 16-byte word.
 __global__ void gy_bf16_kernel(const float* __restrict__ gy, uint16_t* __restrict__ out, int64_t rows, int64_t N,
                                int64_t Npad) {
-    const int64_t total = rows * Npad;
+    const int64_t per_row = Npad / 8, total = rows * per_row;
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t row = t / Npad, c = t % Npad;
-        out[t] = c < N ? __bfloat16_as_ushort(__float2bfloat16_rn(gy[row * N + c])) : uint16_t(0);
+        const int64_t row = t / per_row, c0 = (t % per_row) * 8;
+        const float* src = gy + row * N + c0;
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float a = c0 + 2 * e < N ? src[2 * e] : 0.0f;
+            const float b = c0 + 2 * e + 1 < N ? src[2 * e + 1] : 0.0f;
+            w[e] = uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(a))) |
+                   (uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(b))) << 16);
+        }
+        *reinterpret_cast<uint4*>(out + row * Npad + c0) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
@@ -381,7 +391,7 @@ cudaError_t launch_nc(int nc, const DwParams& p, const CUtensorMap& map, unsigne
 
 cudaError_t tc_gy_to_bf16(const float* gy, void* gy_bf, int J, int O, int64_t N, cudaStream_t s) {
     const int64_t Npad = (std::max<int64_t>(N, 1) + 63) / 64 * 64;
-    const int64_t rows = int64_t(J) * O, total = rows * Npad;
+    const int64_t rows = int64_t(J) * O, total = rows * (Npad / 8);
     const int pb = int(std::min<int64_t>((total + 255) / 256, 8192));
     tcdw::gy_bf16_kernel<<<pb, 256, 0, s>>>(gy, static_cast<uint16_t*>(gy_bf), rows, N, Npad);
     return cudaGetLastError();
