@@ -395,8 +395,11 @@ def run_ours(args, ws, rank, local):
                 achieved = flops / (total_ms / args.steps / 1e3) / 1e12
                 kernel = "layer-wise step (all kernels of one step)"
                 kms = total_ms / args.steps
+            # DRAM bytes of one launch of the fused kernel from one ncu capture of this workload
+            # (its inputs and weights only); unknown for the other shapes
+            traffic = 783616 if fused and args.workload == WORKLOAD else None
             roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": kernel, "kernel_ms": kms,
+                        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": kernel, "kernel_ms": kms,
                         "reduce_adam_ms": red_ms / max(1, red_n),
                         "peak_source": FP32_PEAK_NOTE + " (derived, FP32 FMA pipe)"}
         else:
