@@ -283,6 +283,21 @@ int hrkan_forward_jets_batched(hrkan_t h, const float* W, const float* x, const 
 int hrkan_set_batch_items(hrkan_t h, int points_per_item);
 
 /*
+ * Picks the points per work item of the multi-instance training step by
+ * timing it: for each candidate (NULL: 256, 512, 1024, 2048, 4096) one
+ * untimed call, then `reps` (< 1: 3) calls timed with CUDA events on the
+ * stream, all with lr = 0 so that W keeps its values; the fastest candidate
+ * becomes the handle's item size.  Arguments as hrkan_train_step_batched.
+ * Synchronises the stream; resets the Adam moments and the device step
+ * counter (call it before training).  chosen / ms_per_step (host, may be
+ * NULL) receive the winner and its time per step.
+ */
+int hrkan_autotune_batch(hrkan_t h, const pinn_problem* probs, float* W, const float* x_int,
+                         const int64_t* off_int, const float* x_bnd, const float* g_bnd,
+                         const int64_t* off_bnd, const int* candidates, int n_candidates, int reps,
+                         int* chosen, double* ms_per_step, hrkan_stream_t stream);
+
+/*
  * hrkan_backward without any allocation (the paper has no counterpart; this is
  * for callers that cannot call cudaMalloc, e.g. code running under another
  * framework's memory pool or with all device memory reserved up front, which

@@ -27,7 +27,7 @@ EXPORTS = ("hrkan_param_count", "hrkan_init", "hrkan_destroy", "hrkan_last_error
            "hrkan_forward_jets", "pinn_residual_loss", "hrkan_backward", "adam_step", "hrkan_reset_moments",
            "hrkan_train_step", "hrkan_profile_enable", "hrkan_profile_read", "hrkan_backward_noalloc",
            "hrkan_train_step_batched", "hrkan_forward_jets_batched", "hrkan_set_batch_items", "hrkan_sync_status",
-           "hrkan_layer_jets", "hrkan_layer_dw", "hrkan_layer_adjoint")
+           "hrkan_layer_jets", "hrkan_layer_dw", "hrkan_layer_adjoint", "hrkan_autotune_batch")
 HRKAN_KERNEL_FUSED, HRKAN_KERNEL_REDUCE, HRKAN_KERNEL_FORWARD, HRKAN_KERNEL_RESIDUAL, HRKAN_KERNEL_TENSOR = 0, 1, 2, 3, 4
 
 
@@ -83,6 +83,9 @@ def load_library(path: str = LIB_PATH):
                                          _d, _d, _i32, _vp, _vp, _vp]
         lib.hrkan_backward_noalloc.argtypes = [ctypes.POINTER(hrkan_cfg), _vp, _vp, _i64, _u32, _vp, _vp, _i32, _vp]
         _i64p = ctypes.POINTER(_i64)
+        lib.hrkan_autotune_batch.argtypes = [_vp, ctypes.POINTER(pinn_problem), _vp, _vp, _i64p, _vp, _vp, _i64p,
+                                             ctypes.POINTER(ctypes.c_int), _i32, _i32, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_double), _vp]
         lib.hrkan_train_step_batched.argtypes = [_vp, ctypes.POINTER(pinn_problem), _vp, _vp, _i64p, _vp, _vp, _i64p,
                                                  _d, _d, _d, _d, _i32, _vp, _vp, _vp]
         lib.hrkan_forward_jets_batched.argtypes = [_vp, _vp, _vp, _i64p, _u32, _vp, _vp]
@@ -253,6 +256,23 @@ def hrkan_forward_jets_batched(h, W, x, offsets, jet_mask, jets, stream=None):
     o, op = _i64_array(offsets)
     _check(load_library().hrkan_forward_jets_batched(h, _ptr(W, f), _ptr(x, f), op, int(jet_mask), _ptr(jets, f),
                                                      _stream(stream)))
+
+
+def hrkan_autotune_batch(h, probs, W, x_int, off_int, x_bnd, g_bnd, off_bnd, candidates=None, reps=3,
+                         stream=None):
+    """Times the multi-instance step for each item size (lr = 0: W unchanged), keeps the
+    fastest, resets the Adam moments.  Returns (points per item, ms per step)."""
+    import torch
+    f = torch.float32
+    arr = (pinn_problem * len(probs))(*probs)
+    oi, oip = _i64_array(off_int)
+    ob, obp = _i64_array(off_bnd)
+    cand = None if candidates is None else (ctypes.c_int * len(candidates))(*[int(c) for c in candidates])
+    chosen, ms = ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(load_library().hrkan_autotune_batch(h, arr, _ptr(W, f), _ptr(x_int, f), oip, _ptr(x_bnd, f),
+                                               _ptr(g_bnd, f), obp, cand, 0 if cand is None else len(candidates),
+                                               int(reps), ctypes.byref(chosen), ctypes.byref(ms), _stream(stream)))
+    return chosen.value, ms.value
 
 
 def hrkan_set_batch_items(h, points_per_item):

@@ -979,6 +979,68 @@ int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, con
     return HRKAN_OK;
 }
 
+int hrkan_autotune_batch(hrkan_t h, const pinn_problem* probs, float* W, const float* x_int, const int64_t* off_int,
+                         const float* x_bnd, const float* g_bnd, const int64_t* off_bnd, const int* candidates,
+                         int n_candidates, int reps, int* chosen, double* ms_per_step, hrkan_stream_t stream) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    static const int kDefault[] = {256, 512, 1024, 2048, 4096};
+    if (!candidates) {
+        candidates = kDefault;
+        n_candidates = 5;
+    }
+    if (n_candidates < 1) return fail(HRKAN_EINVAL, "n_candidates=%d", n_candidates);
+    for (int c = 0; c < n_candidates; ++c)
+        if (candidates[c] < 1) return fail(HRKAN_EINVAL, "candidate %d: %d points per item", c, candidates[c]);
+    if (reps < 1) reps = 3;
+    if (int rc = use_device(h)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = HRKAN_OK;
+    float* loss_f = ws_get(h, 13, size_t(2 * 3 * std::max(h->cfg.n_instances, 1)), &rc);
+    if (!loss_f) return rc;
+    double* loss = reinterpret_cast<double*>(loss_f);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+    }
+    const int saved = h->batch_items_points;
+    int best = saved;
+    float best_ms = 0.0f;
+    for (int c = 0; c < n_candidates && rc == HRKAN_OK; ++c) {
+        h->batch_items_points = candidates[c];
+        // lr = 0 leaves W as it is; the first call builds this candidate's work list
+        auto step = [&]() {
+            return hrkan_train_step_batched(h, probs, W, x_int, off_int, x_bnd, g_bnd, off_bnd, 0.0, 0.9, 0.999, 1e-8,
+                                            1, loss, nullptr, stream);
+        };
+        if ((rc = step())) break;
+        cudaEventRecord(a, s);
+        for (int r = 0; r < reps && rc == HRKAN_OK; ++r) rc = step();
+        cudaEventRecord(b, s);
+        if (rc) break;
+        cudaError_t e = cudaEventSynchronize(b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "autotune timing");
+            break;
+        }
+        ms /= float(reps);
+        if (c == 0 || ms < best_ms) {
+            best_ms = ms;
+            best = candidates[c];
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    h->batch_items_points = rc == HRKAN_OK ? best : saved;
+    if (rc) return rc;
+    if ((rc = hrkan_reset_moments(h, stream))) return rc;
+    if (chosen) *chosen = best;
+    if (ms_per_step) *ms_per_step = double(best_ms);
+    return HRKAN_OK;
+}
+
 int hrkan_forward_jets_batched(hrkan_t h, const float* W, const float* x, const int64_t* offsets, unsigned jet_mask,
                                float* jets, hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");

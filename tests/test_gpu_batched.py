@@ -210,3 +210,31 @@ def test_batched_rejects_inconsistent_problems():
                                           _dev(d["g_bnd"]), d["off_bnd"], 1e-2, 0.9, 0.999, 1e-8, 1, loss)
     finally:
         capi.hrkan_destroy(h)
+
+
+def test_autotune_picks_a_candidate_and_leaves_weights_and_moments_fresh():
+    """hrkan_autotune_batch times each item size with lr = 0 (W keeps its values), keeps the
+    fastest and resets the Adam state: the next step equals a fresh handle's step."""
+    d, I, h, probs = _setup()
+    h2 = None
+    try:
+        W = _dev(d["W"])
+        xi, xb, gb = _dev(d["x_int"]), _dev(d["x_bnd"]), _dev(d["g_bnd"])
+        cands = [256, 512, 1024]
+        chosen, ms = capi.hrkan_autotune_batch(h, probs, W, xi, d["off_int"], xb, gb, d["off_bnd"], cands, reps=2)
+        assert chosen in cands and ms > 0.0
+        assert np.array_equal(W.cpu().numpy(), d["W"])
+        loss = torch.zeros((I, 3), dtype=torch.float64, device="cuda")
+        capi.hrkan_train_step_batched(h, probs, W, xi, d["off_int"], xb, gb, d["off_bnd"], W_BATCH.lr, 0.9, 0.999,
+                                      1e-8, 1, loss)
+        _, _, h2, _ = _setup(chosen)
+        W2 = _dev(d["W"])
+        loss2 = torch.zeros((I, 3), dtype=torch.float64, device="cuda")
+        capi.hrkan_train_step_batched(h2, probs, W2, xi, d["off_int"], xb, gb, d["off_bnd"], W_BATCH.lr, 0.9, 0.999,
+                                      1e-8, 1, loss2)
+        assert np.array_equal(W.cpu().numpy(), W2.cpu().numpy())
+        assert np.array_equal(loss.cpu().numpy(), loss2.cpu().numpy())
+    finally:
+        capi.hrkan_destroy(h)
+        if h2 is not None:
+            capi.hrkan_destroy(h2)
