@@ -232,8 +232,10 @@ def test_autotune_picks_a_candidate_and_leaves_weights_and_moments_fresh():
         loss2 = torch.zeros((I, 3), dtype=torch.float64, device="cuda")
         capi.hrkan_train_step_batched(h2, probs, W2, xi, d["off_int"], xb, gb, d["off_bnd"], W_BATCH.lr, 0.9, 0.999,
                                       1e-8, 1, loss2)
-        assert np.array_equal(W.cpu().numpy(), W2.cpu().numpy())
+        # the loss is reduced in a fixed order; the gradient's shared-memory float atomics are not
+        # ordered, so the updated weights agree to rounding (stale moments would differ by O(lr))
         assert np.array_equal(loss.cpu().numpy(), loss2.cpu().numpy())
+        assert relerr(W.cpu().numpy(), W2.cpu().numpy()) < 1e-6
     finally:
         capi.hrkan_destroy(h)
         if h2 is not None:
