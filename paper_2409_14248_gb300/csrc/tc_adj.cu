@@ -3,7 +3,8 @@
 // Sections 2-3, through v''' of Eq. 2):
 //
 //   G_r[p, k] = sum_o gy_r[p, o] W[o, k]                    (dense, tensor cores)
-//   dA_r[p, j, q] = G_r[p, j*NP + c_pj + q],  q = 0..3        (the active bases)
+//   dA_r[p, j, q] = G_r[p, k(j, c_pj + q)],  q = 0..3          (the active bases;
+//                   k(j, i) = j*NP + (i mod 4)*NP/4 + i/4, the forward's layout)
 //   gz[p, j] = rows_adjoint(z[p, j], v', v'', v''', dA[p, j]) (FP32, per unit)
 //
 // A CTA owns UK consecutive units (a K-range of N = UK*NP columns, NP the
@@ -65,12 +66,12 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
 
 template <int NP>
 struct Shape {
-    static constexpr int UK = (NP * 4 <= 144) ? 4 : 2;   // units per CTA (even: two epilogue halves)
+    static constexpr int UK = (NP * 4 <= 160) ? 4 : 2;   // units per CTA (even: two epilogue halves)
     static constexpr int UH = UK / 2;                    // units per epilogue warp
     static constexpr int NC = UK * NP;                   // D columns
     static constexpr int NBW = (NC + 63) / 64;           // W boxes of 64 k
     static constexpr int PS = UH * NP + 4;               // pick-row stride (floats) of one half
-    static_assert(NC % 16 == 0 && NC <= 256, "MMA N");
+    static_assert(NC % 16 == 0 && NC <= 256 && 2 * NC <= 512, "MMA N, two D buffers in TMEM");
 };
 
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -196,9 +197,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                 for (int u = 0; u < UH; ++u)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        int i = cell[u] + k;   // bases outside [0, n) get a clamped entry; their derivatives are 0
-                        i = i < 0 ? 0 : (i > NP - 1 ? NP - 1 : i);
-                        dA[u][r][k] = prow[u * NP + i];
+                        // basis i at element (i mod 4) * NP/4 + i/4 of the unit; bases outside
+                        // [0, n) read a clamped entry (their derivatives are 0)
+                        const int i = cell[u] + k;
+                        int pos = (i & 3) * (NP / 4) + (i >> 2);
+                        pos = pos < 0 ? 0 : (pos > NP - 1 ? NP - 1 : pos);
+                        dA[u][r][k] = prow[u * NP + pos];
                     }
             }
 #pragma unroll
@@ -289,13 +293,14 @@ done:
                      : "memory");
 }
 
-// W [O][I][n] float32 -> [O][Kt] BF16, element k = j * NP + i (zero for i >= n or j >= I).
+// W [O][I][n] float32 -> [O][Kt] BF16, element k = j * NP + pos holding basis
+// i = 4 * (pos mod NP/4) + pos / (NP/4) (zero for i >= n or j >= I).
 __global__ void w_bf16_kernel(const float* __restrict__ W, uint16_t* __restrict__ out, int O, int I, int n, int NP,
                               int Kt) {
     const int64_t total = int64_t(O) * Kt;
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
         const int o = int(t / Kt), k = int(t % Kt);
-        const int j = k / NP, i = k % NP;
+        const int j = k / NP, pos = k % NP, q = NP / 4, i = 4 * (pos % q) + pos / q;
         const float w = (j < I && i < n) ? W[(int64_t(o) * I + j) * n + i] : 0.0f;
         out[t] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
     }
@@ -322,7 +327,7 @@ EncodeTiledFn encode_fn() {
 }
 
 int np_of(int n) {
-    for (int np : {16, 24, 32, 36, 48, 64})
+    for (int np : {16, 24, 32, 40, 48, 64})
         if (n <= np) return np;
     return 0;
 }
@@ -355,7 +360,7 @@ cudaError_t launch_np(int np, const AdjParams& p, const CUtensorMap& gm, const C
         case 16: return launch<MASK, 16>(p, gm, wm, grid, s);
         case 24: return launch<MASK, 24>(p, gm, wm, grid, s);
         case 32: return launch<MASK, 32>(p, gm, wm, grid, s);
-        case 36: return launch<MASK, 36>(p, gm, wm, grid, s);
+        case 40: return launch<MASK, 40>(p, gm, wm, grid, s);
         case 48: return launch<MASK, 48>(p, gm, wm, grid, s);
         case 64: return launch<MASK, 64>(p, gm, wm, grid, s);
     }
@@ -367,7 +372,7 @@ int units_per_cta(int np) {
         case 16: return Shape<16>::UK;
         case 24: return Shape<24>::UK;
         case 32: return Shape<32>::UK;
-        case 36: return Shape<36>::UK;
+        case 40: return Shape<40>::UK;
         case 48: return Shape<48>::UK;
         case 64: return Shape<64>::UK;
     }

@@ -2,7 +2,10 @@
 // accumulation (reverse mode of the layer contraction, Sections 2-3), hidden
 // layers and (FIRST) the first layer, whose inputs are the coordinates:
 //
-//   dW[o, k] = sum_p sum_r gy_r[p, o] * A_r[p, k],   k = j*NP8 + i (padded units)
+//   dW[o, k] = sum_p sum_r gy_r[p, o] * A_r[p, k]
+//
+// with k running over the units padded to NP8 elements, bases stored by residue
+// mod 4 inside a unit (basis i at j*NP8 + (i mod 4)*NP8/4 + i/4, as the forward).
 //
 // i.e. D = A_r^T gy_r summed over jet rows r and points p.  The MMA's M runs
 // over 128 consecutive k (one "K-range" per CTA), N over the O outputs and its
@@ -88,7 +91,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
     constexpr int J = JT::J;
     constexpr int NP8 = 8 * NC;                               // elements per padded unit
     constexpr int MAXU = ((127 / NP8) + 2 + 1) / 2;           // units of one parity overlapping 128 k
-    using Win = tck::UnitWin<J, 3>;
+    using Win = tck::UnitWin<J>;
+    constexpr int QW = NP8 / 8;                               // words per residue quarter of a unit
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -195,11 +199,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
                                 uint32_t v[4];
 #pragma unroll
                                 for (int e = 0; e < 4; ++e) {
-                                    const int lw = 4 * ci + e;
-                                    uint32_t x = 0u;
-#pragma unroll
-                                    for (int d = 2; d >= 0; --d) x = (w.h == lw - d) ? w.y[r][d] : x;
-                                    v[e] = x;
+                                    const int lw = 4 * ci + e, qr = lw / QW, qo = lw % QW;
+                                    v[e] = w.tw[qr] == qo ? w.y[r][qr] : 0u;
                                 }
                                 const int b = (q + r) % NSB;
                                 st_shared_v4(smem_u32(smem + size_t(b) * buf_bytes) + off, v[0], v[1], v[2], v[3]);
@@ -230,7 +231,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
         tc_fence_after();
         {
             const int k = k0 + warp * 32 + lane;
-            const int j = k / NP8, i = k % NP8;
+            // element pos of the unit holds basis 4 * (pos mod NP8/4) + pos / (NP8/4)
+            const int j = k / NP8, pos = k % NP8, i = 4 * (pos % (NP8 / 4)) + pos / (NP8 / 4);
             const bool live = j < I && i < p.n;
             float* out = p.partial + int64_t(p.row0 + chunk) * p.P + p.col0 + int64_t(j) * p.n + i;
             const uint32_t lane_base = uint32_t(warp * 32) << 16;
@@ -352,7 +354,7 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-int np8_of(int n) { return (n + 7) / 8 * 8; }
+int np8_of(int n) { return std::max(16, (n + 7) / 8 * 8); }
 
 template <unsigned MASK, int NC, bool FIRST>
 cudaError_t launch(const DwParams& p, const CUtensorMap& map, unsigned grid, cudaStream_t s) {

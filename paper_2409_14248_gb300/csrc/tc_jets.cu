@@ -15,7 +15,7 @@ namespace hrkan {
 cudaError_t tc_launch_np16(const TcLayer&, const CUtensorMap&, int, unsigned, cudaStream_t);
 cudaError_t tc_launch_np24(const TcLayer&, const CUtensorMap&, int, unsigned, cudaStream_t);
 cudaError_t tc_launch_np32(const TcLayer&, const CUtensorMap&, int, unsigned, cudaStream_t);
-cudaError_t tc_launch_np36(const TcLayer&, const CUtensorMap&, int, unsigned, cudaStream_t);
+cudaError_t tc_launch_np40(const TcLayer&, const CUtensorMap&, int, unsigned, cudaStream_t);
 cudaError_t tc_launch_np48(const TcLayer&, const CUtensorMap&, int, unsigned, cudaStream_t);
 cudaError_t tc_launch_np64(const TcLayer&, const CUtensorMap&, int, unsigned, cudaStream_t);
 
@@ -26,7 +26,7 @@ constexpr int RING_MAX = 8;
 
 // Smallest supported padding of a unit's n bases (0 = none).
 int np_of(int n) {
-    for (int np : {16, 24, 32, 36, 48, 64})
+    for (int np : {16, 24, 32, 40, 48, 64})
         if (n <= np) return np;
     return 0;
 }
@@ -36,14 +36,15 @@ int box_elems(int prec) { return prec == HRKAN_BF16 ? 64 : 32; }
 int ring_slots(int J, int O) { return std::min(RING_MAX, (TMEM_COLS - J * O) / (8 * J)); }
 
 // W [O][I][n] float32 -> [O][Kt] in the MMA's element type (BF16 bits, or
-// TF32-rounded float32): element k = j * NP + i holds W[o][j][i] for i < n and
-// j < I, zero elsewhere.
+// TF32-rounded float32): element k = j * NP + pos holds W[o][j][i], i = 4 *
+// (pos mod NP/4) + pos / (NP/4) (the bases of a unit stored by residue mod 4),
+// for i < n and j < I, zero elsewhere.
 template <int PREC>
 __global__ void tc_prep_w_kernel(const float* __restrict__ W, void* out, int O, int I, int n, int NP, int Kt) {
     const int64_t total = int64_t(O) * Kt;
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
         const int o = int(t / Kt), k = int(t % Kt);
-        const int j = k / NP, i = k % NP;
+        const int j = k / NP, pos = k % NP, q = NP / 4, i = 4 * (pos % q) + pos / q;
         const float w = (j < I && i < n) ? W[(int64_t(o) * I + j) * n + i] : 0.0f;
         if constexpr (PREC == HRKAN_BF16) {
             static_cast<uint16_t*>(out)[t] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
@@ -143,7 +144,7 @@ cudaError_t tc_forward_layer(const float* W, void* w_prep, const float* z, float
         case 16: return tc_launch_np16(p, map, prec, mask, s);
         case 24: return tc_launch_np24(p, map, prec, mask, s);
         case 32: return tc_launch_np32(p, map, prec, mask, s);
-        case 36: return tc_launch_np36(p, map, prec, mask, s);
+        case 40: return tc_launch_np40(p, map, prec, mask, s);
         case 48: return tc_launch_np48(p, map, prec, mask, s);
         case 64: return tc_launch_np64(p, map, prec, mask, s);
     }

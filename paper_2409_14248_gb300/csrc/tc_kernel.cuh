@@ -4,8 +4,8 @@
 //
 //   Y_r[p, o] = sum_k A_r[p, k] W[o, k],   r = 0..J-1 jet rows
 //
-// K runs over the layer's input units, each padded to NP elements: k = j*NP + i
-// (basis i of unit j; W and A are zero for i >= n).  Per point and unit only the
+// K runs over the layer's input units, each padded to NP elements (basis i of
+// unit j at k = j*NP + (i mod 4)*NP/4 + i/4; W and A are zero for i >= n).  Per point and unit only the
 // k+1 = 4 bases c..c+3 are non-zero, so A is built on the fly, never stored.
 //
 // One persistent CTA per SM walks tiles of 128 points (the MMA's M); every jet
@@ -21,8 +21,9 @@
 //              shared-memory buffers with TMA (128-byte swizzle, K-major).
 // The placement of the 4 non-zeros is the cost that matters: with NP fixed at
 // compile time, the unit and word offset of every word of a slot are constants
-// of an unrolled period of slots, so a word of one jet row costs a short select
-// among the unit's 3 (BF16) or 4 (TF32) packed window words.
+// of an unrolled period of slots; the bases of a unit are stored by residue
+// mod 4 (four quarters), so every word holds at most one non-zero and a word of
+// one jet row costs one select.
 //
 // Every mbarrier wait is bounded (~1 s) and also gives up when another role has
 // given up: the CTA then records HRKAN_ETIMEOUT in a device status word, waits
@@ -170,12 +171,11 @@ struct Elem<HRKAN_BF16> {
     static constexpr int PER_WORD = 2;   // elements per 32-bit word (TMEM column)
     static constexpr int SLOT = 16;      // K elements per MMA (one slot)
     static constexpr int BOX = 64;       // K elements per 128-byte W row tile
-    static constexpr int NWIN = 3;       // words a unit's 4 values can span
     static constexpr int FMT = 1;
 };
 template <>
 struct Elem<HRKAN_TF32> {
-    static constexpr int PER_WORD = 1, SLOT = 8, BOX = 32, NWIN = 4, FMT = 2;
+    static constexpr int PER_WORD = 1, SLOT = 8, BOX = 32, FMT = 2;
 };
 
 __device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
@@ -203,46 +203,70 @@ struct Period {
     static_assert(SW == 8, "one slot is 8 TMEM columns");
 };
 
-// The non-zero words of one unit in every jet row: the word offset h of the
-// first one (relative to the unit's first word) and the packed words.
-template <int J, int NWIN>
+// Within a unit's padded segment of NP elements the bases are stored by
+// residue mod 4: basis i sits at element (i mod 4) * NP/4 + floor(i / 4).  The
+// k+1 = 4 active bases c..c+3 have distinct residues, so each quarter of the
+// segment holds exactly one of them and every 32-bit word of the segment at
+// most one non-zero (BF16: in one half of the word).
+template <int PREC, int NP>
+struct Quarter {
+    static constexpr int Q = NP / 4;                            // elements per quarter
+    static constexpr int QW = Q / Elem<PREC>::PER_WORD;        // words per quarter
+    static_assert(NP % 4 == 0 && Q % Elem<PREC>::PER_WORD == 0, "quarters start on word boundaries");
+};
+
+// The non-zero of each quarter of one unit: its word offset inside the quarter
+// (out of range: none) and, per jet row, the word holding it.
+template <int J>
 struct UnitWin {
-    int h;
-    uint32_t y[J][NWIN];
+    int tw[4];
+    uint32_t y[J][4];
 };
 
 // Active bases (Eq. 2) of the unit value z[0], the jet rows of its 4 non-zero
-// columns, rounded to the MMA type and packed into the window words.
+// columns, rounded to the MMA type and assigned to the quarters.  With
+// c = 4a + s, basis c + q lands in quarter r = (s + q) mod 4 at element
+// offset a + [r < s] of that quarter.
 template <unsigned MASK, int PREC>
-__device__ __forceinline__ void unit_window(const float* z, const Grid& g, bool live,
-                                            UnitWin<Jet<MASK>::J, Elem<PREC>::NWIN>& w) {
+__device__ __forceinline__ void unit_window(const float* z, const Grid& g, bool live, UnitWin<Jet<MASK>::J>& w) {
     using JT = Jet<MASK>;
     constexpr int J = JT::J;
     Active<3, 4, 2> b;
     b.eval(z[0], g);
     float a[J][4];
     JT::template rows<4>(z, b.v, b.d1, b.d2, a);
-    if constexpr (PREC == HRKAN_BF16) {
-        // values of bases c..c+3 sit at elements c..c+3 of the unit: words
-        // h = c >> 1 .. h + 2 (the third only when c is odd)
-        const bool odd = (b.c & 1) != 0;
-        w.h = b.c >> 1;   // arithmetic shift: floor(c / 2) also for c < 0
+    const int base = b.c >> 2, s = b.c & 3;   // arithmetic shift: floor also for c < 0
+    uint32_t e[J][4];
 #pragma unroll
-        for (int r = 0; r < J; ++r) {
-            const uint32_t lo = bf16x2_bits(a[r][0], a[r][1]), hi = bf16x2_bits(a[r][2], a[r][3]);
-            w.y[r][0] = odd ? (lo << 16) : lo;
-            w.y[r][1] = odd ? __byte_perm(lo, hi, 0x5432) : hi;
-            w.y[r][2] = odd ? (hi >> 16) : 0u;
+    for (int r = 0; r < J; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            e[r][q] = PREC == HRKAN_BF16 ? uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(a[r][q])))
+                                         : tf32_bits(a[r][q]);
+    // quarter r takes basis q = (r - s) mod 4: rotate the four values by s (two select stages)
+#pragma unroll
+    for (int r = 0; r < J; ++r) {
+        uint32_t t1[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t1[k] = (s & 1) ? e[r][(k + 3) & 3] : e[r][k];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) e[r][k] = (s & 2) ? t1[(k + 2) & 3] : t1[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int t = base + (k < s ? 1 : 0);   // element offset inside quarter k
+        if constexpr (PREC == HRKAN_BF16) {
+            w.tw[k] = live ? (t >> 1) : -(1 << 24);
+            const int sh = (t & 1) * 16;
+#pragma unroll
+            for (int r = 0; r < J; ++r) w.y[r][k] = e[r][k] << sh;
+        } else {
+            w.tw[k] = live ? t : -(1 << 24);
+#pragma unroll
+            for (int r = 0; r < J; ++r) w.y[r][k] = e[r][k];
         }
-    } else {
-        w.h = b.c;
-#pragma unroll
-        for (int r = 0; r < J; ++r)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) w.y[r][q] = tf32_bits(a[r][q]);
     }
     // bases outside [0, n) are zero already; a unit past the layer's inputs places nothing
-    if (!live) w.h = -(1 << 24);
 }
 
 // Work split between the PARTS producer warps of a TMEM lane quarter: warp
@@ -288,9 +312,9 @@ __device__ __forceinline__ void produce(const TcLayer& p, TcShared& sh, uint32_t
     using JT = Jet<MASK>;
     using E = Elem<PREC>;
     using SP = Split<PREC, NP, PARTS>;
-    constexpr int J = JT::J, NWIN = E::NWIN, PU = SP::PU, PS = SP::PS, NW = SP::NW;
+    constexpr int J = JT::J, PU = SP::PU, PS = SP::PS, NW = SP::NW, QW = Quarter<PREC, NP>::QW;
     constexpr int HU = PU / PARTS;   // units of this warp per period: u = PARTS * i + PART
-    using Win = UnitWin<J, NWIN>;
+    using Win = UnitWin<J>;
     volatile int* abort = &sh.abort;
     const int O = p.O, I = p.I, RS = p.ring, KS = p.ks;
     const int64_t N = p.N;
@@ -361,14 +385,12 @@ __device__ __forceinline__ void produce(const TcLayer& p, TcShared& sh, uint32_t
                         const int gw = S * 8 + w, u = gw / NW, lw = gw % NW;
                         if (u % PARTS == PART) {
                             const int i = u / PARTS;
+                            // word lw of the unit: quarter lw / QW, holding that quarter's
+                            // non-zero when its offset is lw % QW
+                            const int qr = lw / QW, qo = lw % QW;
+                            const bool hit = uw[i].tw[qr] == qo;
 #pragma unroll
-                            for (int r = 0; r < J; ++r) {
-                                // word = y[d] for d = lw - h in [0, NWIN), else 0
-                                uint32_t x = 0u;
-#pragma unroll
-                                for (int d = NWIN - 1; d >= 0; --d) x = (uw[i].h == lw - d) ? uw[i].y[r][d] : x;
-                                v[r][w] = x;
-                            }
+                            for (int r = 0; r < J; ++r) v[r][w] = hit ? uw[i].y[r][qr] : 0u;
                         }
                     }
                     if (pend_slot >= 0) {   // publish the previous slot (its stores had time to land)

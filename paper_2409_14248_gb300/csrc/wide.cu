@@ -188,8 +188,9 @@ __global__ void __launch_bounds__(WB) wide_adjoint_kernel(WideLayer p) {
 // units [jc*JC, +JC) and walks point tiles gp, gp + GP, ... : it stages the
 // tile's gy [PB][J][O] and basis rows [PB][JC][J][4] (+ cells) in shared
 // memory, then each thread exclusively owns whole (unit, output) rows of the
-// gradient, so the accumulation needs no atomics and is deterministic.  At the
-// end the block writes its rows into partial row gp (columns of its units).
+// gradient (with fewer rows than threads, a copy of a row and every S-th point),
+// so the accumulation needs no atomics and is deterministic.  At the end the
+// block writes its rows into partial row gp (columns of its units).
 template <unsigned MASK, int JC, int PB, bool FIRST>
 __global__ void __launch_bounds__(WB) wide_dw_kernel(WideDw p) {
     using JT = Jet<MASK>;
@@ -205,12 +206,16 @@ __global__ void __launch_bounds__(WB) wide_dw_kernel(WideDw p) {
     // unit chunks alone give too few blocks, e.g. the 2-input first layer)
     const int OS = (O + gridDim.y - 1) / gridDim.y;
     const int o0 = blockIdx.y * OS, Ob = min(OS, O - o0);
-    const int sz_dw = (JC * O * NP + 3) & ~3, sz_gy = (PB * J * O + 3) & ~3;
-    float* dws = sm;                                  // [JC][O][NP]
+    // R owned rows; with fewer rows than threads, S threads share a row, each
+    // accumulating every S-th point of a tile into its own copy (summed at the end)
+    const int R = nj * Ob, S = max(1, int(blockDim.x) / max(R, 1));
+    const int cap = max(JC * O, WB);                  // rows of gradient storage
+    const int sz_dw = (cap * NP + 3) & ~3, sz_gy = (PB * J * O + 3) & ~3;
+    float* dws = sm;                                  // [S][R][NP]
     float* gys = dws + sz_dw;                         // [PB][J][O]
     float* as = gys + sz_gy;                          // [PB][JC][J][4] (16-byte aligned)
     int* cs = reinterpret_cast<int*>(as + PB * JC * J * KPW);   // [PB][JC]
-    for (int t = threadIdx.x; t < JC * O * NP; t += blockDim.x) dws[t] = 0.0f;
+    for (int t = threadIdx.x; t < S * R * NP; t += blockDim.x) dws[t] = 0.0f;
     const int64_t N = p.N;
     const int64_t tiles = (N + PB - 1) / PB;
     for (int64_t tile = gp; tile < tiles; tile += p.GP) {
@@ -249,12 +254,13 @@ __global__ void __launch_bounds__(WB) wide_dw_kernel(WideDw p) {
             cs[pp * JC + jj] = c;
         }
         __syncthreads();
-        // owners: row (jj, o) of the gradient
-        for (int k = threadIdx.x; k < nj * Ob; k += blockDim.x) {
-            const int o = k % Ob, jj = k / Ob;
-            float* row = dws + (jj * Ob + o) * NP;
+        // owners: row (jj, o) of the gradient, copy `sub`
+        for (int k = threadIdx.x; k < R * S; k += blockDim.x) {
+            const int rk = k % R, sub = k / R;
+            const int o = rk % Ob, jj = rk / Ob;
+            float* row = dws + (sub * R + rk) * NP;
 #pragma unroll 4
-            for (int pp = 0; pp < PB; ++pp) {
+            for (int pp = sub; pp < PB; pp += S) {
                 const int c = cs[pp * JC + jj];
                 const float* ar = as + (pp * JC + jj) * J * KPW;
                 const float* gr = gys + pp * J * Ob + o;
@@ -278,7 +284,9 @@ __global__ void __launch_bounds__(WB) wide_dw_kernel(WideDw p) {
     float* out = p.partial + int64_t(p.row0 + gp) * p.P + p.col0;
     for (int t = threadIdx.x; t < nj * Ob * n; t += blockDim.x) {
         const int i = t % n, rest = t / n, o = rest % Ob, jj = rest / Ob;
-        out[(int64_t(o0 + o) * I + j0 + jj) * n + i] = dws[(jj * Ob + o) * NP + i];
+        float v = 0.0f;
+        for (int sub = 0; sub < S; ++sub) v += dws[(sub * R + jj * Ob + o) * NP + i];   // fixed order
+        out[(int64_t(o0 + o) * I + j0 + jj) * n + i] = v;
     }
 }
 
@@ -321,7 +329,8 @@ static cudaError_t adj_mask(const WideLayer& p, cudaStream_t s) {
 template <unsigned MASK, int JC, int PB, bool FIRST>
 static size_t dw_smem(int O, int n) {
     constexpr int J = Jet<MASK>::J;
-    return sizeof(float) * (((size_t(JC) * O * (n | 1) + 3) & ~size_t(3)) + ((size_t(PB) * J * O + 3) & ~size_t(3)) +
+    return sizeof(float) * (((std::max<size_t>(size_t(JC) * O, WB) * (n | 1) + 3) & ~size_t(3)) +
+                            ((size_t(PB) * J * O + 3) & ~size_t(3)) +
                             size_t(PB) * JC * J * KPW) +
            sizeof(int) * size_t(PB) * JC;
 }

@@ -81,8 +81,8 @@ def _check(w, prec, d, mask, check_impl=True):
     return errs
 
 
-# (I, O, G): units padded to 36, 24, 36, 16, 32 (odd I: a partial last slot), 48 and 64
-# elements (the kernel's unrolled slot periods of 9, 3, 9, 1, 2, 3 and 4 slots in BF16)
+# (I, O, G): units padded to 40, 24, 40, 16, 32 (odd I: a partial last slot), 48 and 64
+# elements (the kernel's unrolled slot periods of 5, 3, 5, 1, 2, 3 and 4 slots in BF16)
 SHAPES = [(64, 64, 32), (32, 32, 20), (64, 16, 32), (48, 48, 13), (13, 32, 29), (7, 16, 45), (5, 64, 61)]
 
 
@@ -122,8 +122,8 @@ def test_tc_single_layer_matches_rounding_aware_oracle(prec, shape, mask):
         assert e_fmt > 4 * e_impl      # the contraction really ran in the reduced precision
 
 
-# (I, O, G, lo, hi): grid spacings h = 1/4, 1/16, 1/8, 1/8, 1/8, 1/16 -> units padded to 16, 36, 32,
-# 48, 64 and 24 elements
+# (I, O, G, lo, hi): grid spacings h = 1/4, 1/16, 1/8, 1/8, 1/8, 1/16 -> units padded to 16, 40, 32,
+# 48, 64 and 40 elements
 KNOT_SHAPES = [(16, 16, 8, -1.0, 1.0), (64, 64, 32, -1.0, 1.0), (13, 32, 24, -1.5, 1.5), (7, 48, 40, -2.5, 2.5),
                (5, 64, 56, -3.5, 3.5), (32, 32, 32, -1.0, 1.0)]
 
