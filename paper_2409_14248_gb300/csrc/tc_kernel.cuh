@@ -223,47 +223,49 @@ struct UnitWin {
     uint32_t y[J][4];
 };
 
-// Active bases (Eq. 2) of the unit value z[0], the jet rows of its 4 non-zero
-// columns, rounded to the MMA type and assigned to the quarters.  With
-// c = 4a + s, basis c + q lands in quarter r = (s + q) mod 4 at element
-// offset a + [r < s] of that quarter.
+// Active bases (Eq. 2) of the unit value z[0], evaluated directly in quarter
+// order, the jet rows of the 4 non-zero columns, rounded to the MMA type.
+// With c = 4a + s the cell and f the offset inside it, quarter k holds basis
+// c + q_k, q_k = (k - s) mod 4, at element offset a + [k < s] of the quarter;
+// its position inside the support is u = (f + 1 - q_k) / 2 (the u-form of Eq. 2
+// for k+1 = 4 active bases: v = (1 - u^2)^4, v' = -8u(1 - u^2)^3 / a_s,
+// v'' = (-8(1 - u^2)^3 + 48u^2(1 - u^2)^2) / a_s^2 with a_s the half-width).
 template <unsigned MASK, int PREC>
 __device__ __forceinline__ void unit_window(const float* z, const Grid& g, bool live, UnitWin<Jet<MASK>::J>& w) {
     using JT = Jet<MASK>;
     constexpr int J = JT::J;
-    Active<3, 4, 2> b;
-    b.eval(z[0], g);
-    float a[J][4];
-    JT::template rows<4>(z, b.v, b.d1, b.d2, a);
-    const int base = b.c >> 2, s = b.c & 3;   // arithmetic shift: floor also for c < 0
-    uint32_t e[J][4];
-#pragma unroll
-    for (int r = 0; r < J; ++r)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            e[r][q] = PREC == HRKAN_BF16 ? uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(a[r][q])))
-                                         : tf32_bits(a[r][q]);
-    // quarter r takes basis q = (r - s) mod 4: rotate the four values by s (two select stages)
-#pragma unroll
-    for (int r = 0; r < J; ++r) {
-        uint32_t t1[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) t1[k] = (s & 1) ? e[r][(k + 3) & 3] : e[r][k];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) e[r][k] = (s & 2) ? t1[(k + 2) & 3] : t1[k];
-    }
+    float t = (z[0] - g.lo) * g.inv_h;
+    t = fminf(fmaxf(t, -1.0e9f), 1.0e9f);   // keep floorf's result in int range
+    const float fc = floorf(t);
+    const int c = int(fc);
+    const float f = (z[0] - fmaf(fc, g.h, g.lo)) * g.inv_h;   // offset from the knot (see Active)
+    const int base = c >> 2, s = c & 3;                        // arithmetic shift: floor also for c < 0
+    float v[4], d1[4], d2[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const int t = base + (k < s ? 1 : 0);   // element offset inside quarter k
-        if constexpr (PREC == HRKAN_BF16) {
-            w.tw[k] = live ? (t >> 1) : -(1 << 24);
-            const int sh = (t & 1) * 16;
+        const int q = (k - s) & 3;
+        const float u = (f + float(1 - q)) * 0.5f;
+        const float Q = fmaxf(1.0f - u * u, 0.0f);
+        const float Q2 = Q * Q, Q3 = Q2 * Q;
+        const bool ok = unsigned(c + q) < unsigned(g.n);
+        v[k] = ok ? Q3 * Q : 0.0f;
+        d1[k] = ok ? -8.0f * u * Q3 * g.inv_a : 0.0f;
+        d2[k] = ok ? (-8.0f * Q3 + 48.0f * u * u * Q2) * (g.inv_a * g.inv_a) : 0.0f;
+        const int tk = base + (k < s ? 1 : 0);
+        if constexpr (PREC == HRKAN_BF16) w.tw[k] = live ? (tk >> 1) : -(1 << 24);
+        else w.tw[k] = live ? tk : -(1 << 24);
+    }
+    float a[J][4];
+    JT::template rows<4>(z, v, d1, d2, a);
 #pragma unroll
-            for (int r = 0; r < J; ++r) w.y[r][k] = e[r][k] << sh;
-        } else {
-            w.tw[k] = live ? t : -(1 << 24);
+    for (int k = 0; k < 4; ++k) {
+        const int tk = base + (k < s ? 1 : 0);
 #pragma unroll
-            for (int r = 0; r < J; ++r) w.y[r][k] = e[r][k];
+        for (int r = 0; r < J; ++r) {
+            if constexpr (PREC == HRKAN_BF16)
+                w.y[r][k] = uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(a[r][k]))) << ((tk & 1) * 16);
+            else
+                w.y[r][k] = tf32_bits(a[r][k]);
         }
     }
     // bases outside [0, n) are zero already; a unit past the layer's inputs places nothing
