@@ -296,12 +296,6 @@ float* ws_get(hrkan_t h, int slot, size_t floats, int* rc) {
 
 int jets_of(unsigned mask) { return __builtin_popcount(mask & 0x1Fu); }
 
-int max_hidden(hrkan_t h) {
-    int m = 1;
-    for (int l = 1; l < h->L; ++l) m = std::max(m, h->cfg.widths[l]);
-    return m;
-}
-
 // Offset (floats) of layer l's input jets (l >= 1) inside a tape for N points.
 int64_t tape_offset(hrkan_t h, int l, int64_t N, int J) {
     int64_t off = 0;
