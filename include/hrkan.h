@@ -74,7 +74,7 @@ typedef struct hrkan_cfg {
     int widths[HRKAN_MAX_WIDTHS];    /* widths[0] = 2 (D), widths[n_widths-1] = 1, all <= 64 */
     int G;                           /* grid intervals on [grid_lo, grid_hi], >= 1 */
     int k;                           /* support width in cells minus one (B-spline order); 3 */
-    int m;                           /* HR order of Eq. 2; 4 */
+    int m;                           /* HR order of Eq. 2: 2..6 (FP32); the fused narrow and tensor-core kernels need 4 */
     int prec;                        /* enum hrkan_prec: arithmetic of the jet contraction.  BF16 /
                                         TF32: hidden layers with 16 <= O <= 64 (O % 16 == 0) contract
                                         on tcgen05 tensor cores (FP32 accumulation in TMEM) when

@@ -105,7 +105,8 @@ int check_cfg(const hrkan_cfg* c) {
         return fail(HRKAN_EINVAL, "last width %d: the network has one output", c->widths[c->n_widths - 1]);
     if (c->G < 1 || c->G > 4096) return fail(HRKAN_EINVAL, "G=%d outside [1, 4096]", c->G);
     if (c->k < 0 || c->m < 1) return fail(HRKAN_EINVAL, "k=%d, m=%d", c->k, c->m);
-    if (c->k != 3 || c->m != 4) return fail(HRKAN_EUNSUPPORTED, "k=%d, m=%d: this build has k=3, m=4", c->k, c->m);
+    if (c->k != 3 || c->m < 2 || c->m > 6)
+        return fail(HRKAN_EUNSUPPORTED, "k=%d, m=%d: this build has k=3 and m in [2, 6]", c->k, c->m);
     if (!(c->grid_lo < c->grid_hi) || !std::isfinite(c->grid_lo) || !std::isfinite(c->grid_hi))
         return fail(HRKAN_EINVAL, "grid [%g, %g]", c->grid_lo, c->grid_hi);
     if (c->n_instances < 1) return fail(HRKAN_EINVAL, "n_instances=%d", c->n_instances);
@@ -557,6 +558,10 @@ int hrkan_init(hrkan_t* out, const hrkan_cfg* cfg) {
     for (int l = 1; l < L; ++l) uniform_hidden &= (cfg->widths[l] == cfg->widths[1]);
     if (uniform_hidden) net_id = narrow_net_id(L, cfg->widths[1]);
     if (cfg->flags & HRKAN_FLAG_LAYERWISE) net_id = -1;
+    if (cfg->m != 4) net_id = -1;   // the fused narrow kernels are built for m = 4
+    if (cfg->prec != HRKAN_FP32 && cfg->m != 4)
+        return fail(HRKAN_EUNSUPPORTED, "precision %d: the tensor-core kernels are built for m = 4 (m=%d)", cfg->prec,
+                    cfg->m);
     if (net_id < 0 && cfg->n_instances != 1)
         return fail(HRKAN_EUNSUPPORTED, "several instances need a fused shape ([2,W,1] or [2,W,W,1], W in 5,10,16)");
     if (cfg->prec != HRKAN_FP32 && net_id >= 0)
@@ -575,6 +580,7 @@ int hrkan_init(hrkan_t* out, const hrkan_cfg* cfg) {
     h->grid.h = float(hh);
     h->grid.inv_h = float(1.0 / hh);
     h->grid.inv_a = float(2.0 / ((cfg->k + 1) * hh));
+    h->grid.m = cfg->m;
     h->grid.n = h->n;
 
     cudaError_t e;

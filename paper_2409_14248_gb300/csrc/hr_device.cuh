@@ -16,6 +16,7 @@ struct Grid {
     float inv_h;   // G / (grid_hi - grid_lo)
     float inv_a;   // 1 / half-width of a support = 2 / ((k+1) h)
     int n;         // number of bases G + k
+    int m;         // HR order of Eq. 2
 };
 
 // Active bases of one input value.

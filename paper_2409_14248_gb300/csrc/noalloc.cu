@@ -95,6 +95,7 @@ extern "C" int hrkan_backward_noalloc(const hrkan_cfg* cfg, const float* W, cons
     p.grid.h = float(hh);
     p.grid.inv_h = float(1.0 / hh);
     p.grid.inv_a = float(2.0 / ((cfg->k + 1) * hh));
+    p.grid.m = cfg->m;
     p.grid.n = cfg->G + cfg->k;
     p.P = P;
     p.x0 = x;

@@ -1,385 +1,45 @@
-// Layer-wise kernels for wide HRKANs (hidden widths up to 64, any number of
-// layers): the KAN layer of Sections 1-3 with Eq. 2 bases, its input-jet
-// forward, the input adjoint through v''' and the weight gradient.
-//
-// Jets live in HBM between layers as [J][units][N] float32 (one row per jet
-// component and unit, points contiguous), so every per-point access of a warp
-// is one coalesced 128-byte line.  Only the k+1 active bases of each unit are
-// evaluated and contracted (Eq. 2 has compact support):
-//   forward      y[r][o] = sum_j sum_q W[o][j][c_j+q] A_r[j][q]
-//   adjoint      dA[j][r][q] = sum_o gy[r][o] W[o][j][c_j+q], then through v'''
-//   weight grad  dW[o][j][c_j+q] += sum_r gy[r][o] A_r[j][q]  (summed over points)
-#include <algorithm>
-
-#include "internal.h"
-#include "narrow.cuh"
+// Dispatch of the layer-wise kernels (wide_kernels.cuh) by the HR order m of
+// Eq. 2; each order is compiled in its own translation unit (wide_m*.cu).
 #include "wide.cuh"
 
 namespace hrkan {
 
-constexpr int WB = 256;      // threads (= points) per block of the point-parallel kernels
-constexpr int KW = 3;        // k
-constexpr int MW = 4;        // m
-constexpr int KPW = KW + 1;
-
-// Jets of input unit j of a layer: from the tape, or (first layer) the
-// coordinate x_j itself with dx_j/dx_j = 1 and no other derivative.
-template <unsigned MASK, bool FIRST>
-__device__ __forceinline__ void load_unit_jets(const float* __restrict__ z, int I, int j, int64_t N, int64_t p,
-                                               float* zj) {
-    using JT = Jet<MASK>;
-    if constexpr (FIRST) {
-        zj[0] = z[j * N + p];
-        if constexpr (JT::F0) zj[JT::RF0] = (j == 0) ? 1.0f : 0.0f;
-        if constexpr (JT::F1) zj[JT::RF1] = (j == 1) ? 1.0f : 0.0f;
-        if constexpr (JT::S0) zj[JT::RS0] = 0.0f;
-        if constexpr (JT::S1) zj[JT::RS1] = 0.0f;
-    } else {
-#pragma unroll
-        for (int r = 0; r < JT::J; ++r) zj[r] = z[(int64_t(r) * I + j) * N + p];
-    }
-}
-
-// ------------------------------------------------------------------ forward
-// grid (ceil(N / WB), ceil(O / OT)); the block's weights W[o0 .. o0+OT) sit in
-// shared memory as [j][i][OT] so an active basis reads its OT outputs as float4.
-template <unsigned MASK, int OT, bool FIRST>
-__global__ void __launch_bounds__(WB) wide_fwd_kernel(WideLayer p) {
-    using JT = Jet<MASK>;
-    constexpr int J = JT::J;
-    extern __shared__ __align__(16) float wt[];
-    const int I = p.I, O = p.O, n = p.g.n;
-    const int o0 = blockIdx.y * OT;
-    for (int t = threadIdx.x; t < I * n * OT; t += blockDim.x) {
-        const int oo = t % OT, ji = t / OT;
-        wt[t] = (o0 + oo < O) ? p.W[int64_t(o0 + oo) * I * n + ji] : 0.0f;
-    }
-    __syncthreads();
-    const int64_t N = p.N;
-    const int64_t pt = int64_t(blockIdx.x) * WB + threadIdx.x;
-    if (pt >= N) return;
-    float acc[OT][J];
-#pragma unroll
-    for (int o = 0; o < OT; ++o)
-#pragma unroll
-        for (int r = 0; r < J; ++r) acc[o][r] = 0.0f;
-#pragma unroll 1
-    for (int j = 0; j < I; ++j) {
-        float z[J];
-        load_unit_jets<MASK, FIRST>(p.z, I, j, N, pt, z);
-        Active<KW, MW, 2> b;
-        b.eval(z[0], p.g);
-        float a[J][KPW];
-        JT::template rows<KPW>(z, b.v, b.d1, b.d2, a);
-#pragma unroll
-        for (int q = 0; q < KPW; ++q) {
-            const float* wr = wt + (j * n + b.idx(q, n)) * OT;
-            if constexpr (OT % 4 == 0) {
-#pragma unroll
-                for (int o4 = 0; o4 < OT / 4; ++o4) {
-                    const float4 w4 = reinterpret_cast<const float4*>(wr)[o4];
-                    const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-#pragma unroll
-                        for (int r = 0; r < J; ++r) acc[o4 * 4 + e][r] = fmaf(wv[e], a[r][q], acc[o4 * 4 + e][r]);
-                }
-            } else {
-#pragma unroll
-                for (int o = 0; o < OT; ++o)
-#pragma unroll
-                    for (int r = 0; r < J; ++r) acc[o][r] = fmaf(wr[o], a[r][q], acc[o][r]);
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 0; o < OT; ++o)
-        if (o0 + o < O)
-#pragma unroll
-            for (int r = 0; r < J; ++r) p.y[(int64_t(r) * O + o0 + o) * N + pt] = acc[o][r];
-}
-
-// ------------------------------------------------------------ input adjoint
-// grid (ceil(I / IT), ceil(N / WB)): the input-chunk index runs fastest so the
-// blocks sharing a point tile run together and reuse its gy lines from L2.
-// Shared memory holds W[all o][chunk][all i] as [jj][o][i] (basis fastest:
-// lanes with different cells hit different banks).
-template <unsigned MASK, int IT>
-__global__ void __launch_bounds__(WB) wide_adjoint_kernel(WideLayer p) {
-    using JT = Jet<MASK>;
-    constexpr int J = JT::J;
-    extern __shared__ __align__(16) float ws[];
-    const int I = p.I, O = p.O, n = p.g.n;
-    const int j0 = blockIdx.x * IT;
-    for (int t = threadIdx.x; t < IT * O * n; t += blockDim.x) {
-        const int i = t % n, rest = t / n, o = rest % O, jj = rest / O;
-        ws[t] = (j0 + jj < I) ? p.W[(int64_t(o) * I + j0 + jj) * n + i] : 0.0f;
-    }
-    __syncthreads();
-    const int64_t N = p.N;
-    const int64_t pt = int64_t(blockIdx.y) * WB + threadIdx.x;
-    if (pt >= N) return;
-    float z[IT][J];
-    int cb[IT];
-#pragma unroll
-    for (int jj = 0; jj < IT; ++jj) {
-        const int j = (j0 + jj < I) ? j0 + jj : I - 1;
-        load_unit_jets<MASK, false>(p.z, I, j, N, pt, z[jj]);
-        Active<KW, MW, 2> b;
-        b.eval(z[jj][0], p.g);
-        cb[jj] = b.c;
-    }
-    float dA[IT][J][KPW];
-#pragma unroll
-    for (int jj = 0; jj < IT; ++jj)
-#pragma unroll
-        for (int r = 0; r < J; ++r)
-#pragma unroll
-            for (int q = 0; q < KPW; ++q) dA[jj][r][q] = 0.0f;
-    // gy of output o + GPF is loaded while output o is contracted (hides the load latency)
-    constexpr int GPF = 4;
-    float gq[GPF][J];
-#pragma unroll
-    for (int u = 0; u < GPF; ++u)
-#pragma unroll
-        for (int r = 0; r < J; ++r) gq[u][r] = u < O ? p.gy[(int64_t(r) * O + u) * N + pt] : 0.0f;
-#pragma unroll 1
-    for (int ob = 0; ob < O; ob += GPF) {
-#pragma unroll
-      for (int u = 0; u < GPF; ++u) {
-        const int o = ob + u;
-        if (o >= O) break;
-        float g[J];
-#pragma unroll
-        for (int r = 0; r < J; ++r) g[r] = gq[u][r];
-        if (o + GPF < O) {
-#pragma unroll
-            for (int r = 0; r < J; ++r) gq[u][r] = p.gy[(int64_t(r) * O + o + GPF) * N + pt];
-        }
-#pragma unroll
-        for (int jj = 0; jj < IT; ++jj) {
-            const float* wr = ws + (jj * O + o) * n;
-#pragma unroll
-            for (int q = 0; q < KPW; ++q) {
-                int i = cb[jj] + q;
-                i = i < 0 ? 0 : (i >= n ? n - 1 : i);
-                const float w = wr[i];
-#pragma unroll
-                for (int r = 0; r < J; ++r) dA[jj][r][q] = fmaf(g[r], w, dA[jj][r][q]);
-            }
-        }
-      }
-    }
-#pragma unroll
-    for (int jj = 0; jj < IT; ++jj) {
-        if (j0 + jj >= I) break;
-        Active<KW, MW, 3> b;
-        b.eval(z[jj][0], p.g);
-        // bases that do not exist contribute nothing (their dA used a clamped weight)
-        float gz[J];
-        JT::template rows_adjoint<KPW>(z[jj], b.d1, b.d2, b.d3, dA[jj], gz);
-#pragma unroll
-        for (int r = 0; r < J; ++r) p.gz[(int64_t(r) * I + j0 + jj) * N + pt] = gz[r];
-    }
-}
-
-// ------------------------------------------------------------ weight gradient
-// grid NJC x GP (chunk fastest).  Block (jc, gp) owns the gradient of input
-// units [jc*JC, +JC) and walks point tiles gp, gp + GP, ... : it stages the
-// tile's gy [PB][J][O] and basis rows [PB][JC][J][4] (+ cells) in shared
-// memory, then each thread exclusively owns whole (unit, output) rows of the
-// gradient (with fewer rows than threads, a copy of a row and every S-th point),
-// so the accumulation needs no atomics and is deterministic.  At the end the
-// block writes its rows into partial row gp (columns of its units).
-template <unsigned MASK, int JC, int PB, bool FIRST>
-__global__ void __launch_bounds__(WB) wide_dw_kernel(WideDw p) {
-    using JT = Jet<MASK>;
-    constexpr int J = JT::J;
-    extern __shared__ __align__(16) float sm[];
-    const int I = p.I, O = p.O, n = p.g.n;
-    const int NP = n | 1;                       // odd row stride: lanes with consecutive o hit distinct banks
-    const int njc = (I + JC - 1) / JC;
-    const int jc = blockIdx.x % njc, gp = blockIdx.x / njc;
-    const int j0 = jc * JC;
-    const int nj = min(JC, I - j0);
-    // outputs [o0, o0 + Ob) of this block (blockIdx.y slices the outputs when the
-    // unit chunks alone give too few blocks, e.g. the 2-input first layer)
-    const int OS = (O + gridDim.y - 1) / gridDim.y;
-    const int o0 = blockIdx.y * OS, Ob = min(OS, O - o0);
-    // R owned rows; with fewer rows than threads, S threads share a row, each
-    // accumulating every S-th point of a tile into its own copy (summed at the end)
-    const int R = nj * Ob, S = max(1, int(blockDim.x) / max(R, 1));
-    const int cap = max(JC * O, WB);                  // rows of gradient storage
-    const int sz_dw = (cap * NP + 3) & ~3, sz_gy = (PB * J * O + 3) & ~3;
-    float* dws = sm;                                  // [S][R][NP]
-    float* gys = dws + sz_dw;                         // [PB][J][O]
-    float* as = gys + sz_gy;                          // [PB][JC][J][4] (16-byte aligned)
-    int* cs = reinterpret_cast<int*>(as + PB * JC * J * KPW);   // [PB][JC]
-    for (int t = threadIdx.x; t < S * R * NP; t += blockDim.x) dws[t] = 0.0f;
-    const int64_t N = p.N;
-    const int64_t tiles = (N + PB - 1) / PB;
-    for (int64_t tile = gp; tile < tiles; tile += p.GP) {
-        const int64_t base = tile * PB;
-        __syncthreads();
-        // stage gy: element (pp, r, o) = gy[r][o][base + pp]
-        for (int t = threadIdx.x; t < PB * J * Ob; t += blockDim.x) {
-            const int pp = t % PB, ro = t / PB;   // ro = r * Ob + o
-            const int r = ro / Ob, o = ro % Ob;
-            const int64_t pt = base + pp;
-            gys[pp * J * Ob + ro] = (pt < N) ? p.gy[(int64_t(r) * O + o0 + o) * N + pt] : 0.0f;
-        }
-        // stage basis rows of the chunk's units
-        for (int t = threadIdx.x; t < PB * JC; t += blockDim.x) {
-            const int pp = t % PB, jj = t / PB;
-            const int64_t pt = base + pp;
-            int c = -(1 << 20);   // no basis: all four slots out of range
-            float a[J][KPW];
-            if (pt < N && jj < nj) {
-                float z[J];
-                load_unit_jets<MASK, FIRST>(p.z, I, j0 + jj, N, pt, z);
-                Active<KW, MW, 2> b;
-                b.eval(z[0], p.g);
-                JT::template rows<KPW>(z, b.v, b.d1, b.d2, a);
-                c = b.c;
-            } else {
-#pragma unroll
-                for (int r = 0; r < J; ++r)
-#pragma unroll
-                    for (int q = 0; q < KPW; ++q) a[r][q] = 0.0f;
-            }
-            float* dst = as + (pp * JC + jj) * J * KPW;
-#pragma unroll
-            for (int r = 0; r < J; ++r)
-                reinterpret_cast<float4*>(dst)[r] = make_float4(a[r][0], a[r][1], a[r][2], a[r][3]);
-            cs[pp * JC + jj] = c;
-        }
-        __syncthreads();
-        // owners: row (jj, o) of the gradient, copy `sub`
-        for (int k = threadIdx.x; k < R * S; k += blockDim.x) {
-            const int rk = k % R, sub = k / R;
-            const int o = rk % Ob, jj = rk / Ob;
-            float* row = dws + (sub * R + rk) * NP;
-#pragma unroll 4
-            for (int pp = sub; pp < PB; pp += S) {
-                const int c = cs[pp * JC + jj];
-                const float* ar = as + (pp * JC + jj) * J * KPW;
-                const float* gr = gys + pp * J * Ob + o;
-                float gq[KPW] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-                for (int r = 0; r < J; ++r) {
-                    const float gv = gr[r * Ob];
-                    const float4 a4 = reinterpret_cast<const float4*>(ar)[r];
-                    gq[0] = fmaf(gv, a4.x, gq[0]);
-                    gq[1] = fmaf(gv, a4.y, gq[1]);
-                    gq[2] = fmaf(gv, a4.z, gq[2]);
-                    gq[3] = fmaf(gv, a4.w, gq[3]);
-                }
-#pragma unroll
-                for (int q = 0; q < KPW; ++q)
-                    if ((unsigned)(c + q) < (unsigned)n) row[c + q] += gq[q];
-            }
-        }
-    }
-    __syncthreads();
-    float* out = p.partial + int64_t(p.row0 + gp) * p.P + p.col0;
-    for (int t = threadIdx.x; t < nj * Ob * n; t += blockDim.x) {
-        const int i = t % n, rest = t / n, o = rest % Ob, jj = rest / Ob;
-        float v = 0.0f;
-        for (int sub = 0; sub < S; ++sub) v += dws[(sub * R + jj * Ob + o) * NP + i];   // fixed order
-        out[(int64_t(o0 + o) * I + j0 + jj) * n + i] = v;
-    }
-}
-
-// ------------------------------------------------------------------ launch
-
-static cudaError_t smem_optin(const void* kern, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-    if (e != cudaSuccess) cudaGetLastError();
-    return e;
-}
-
-template <unsigned MASK>
-static cudaError_t fwd_mask(const WideLayer& p, bool first, cudaStream_t s) {
-    const int n = p.g.n;
-    const unsigned gx = unsigned((p.N + WB - 1) / WB);
-    auto go = [&](auto kern, int ot) -> cudaError_t {
-        const size_t sm = size_t(p.I) * n * ot * sizeof(float);
-        cudaError_t e = smem_optin((const void*)kern, sm);
-        if (e != cudaSuccess) return e;
-        kern<<<dim3(gx, unsigned((p.O + ot - 1) / ot)), WB, sm, s>>>(p);
-        return cudaGetLastError();
-    };
-    if (p.O == 1) return first ? go(wide_fwd_kernel<MASK, 1, true>, 1) : go(wide_fwd_kernel<MASK, 1, false>, 1);
-    if (p.O <= 8) return first ? go(wide_fwd_kernel<MASK, 8, true>, 8) : go(wide_fwd_kernel<MASK, 8, false>, 8);
-    return first ? go(wide_fwd_kernel<MASK, 16, true>, 16) : go(wide_fwd_kernel<MASK, 16, false>, 16);
-}
-
-template <unsigned MASK>
-static cudaError_t adj_mask(const WideLayer& p, cudaStream_t s) {
-    constexpr int IT = 2;   // measured best of 2 / 4 / 8 (registers vs gy reuse)
-    const size_t sm = size_t(IT) * p.O * p.g.n * sizeof(float);
-    auto kern = wide_adjoint_kernel<MASK, IT>;
-    cudaError_t e = smem_optin((const void*)kern, sm);
-    if (e != cudaSuccess) return e;
-    kern<<<dim3(unsigned((p.I + IT - 1) / IT), unsigned((p.N + WB - 1) / WB)), WB, sm, s>>>(p);
-    return cudaGetLastError();
-}
-
-template <unsigned MASK, int JC, int PB, bool FIRST>
-static size_t dw_smem(int O, int n) {
-    constexpr int J = Jet<MASK>::J;
-    return sizeof(float) * (((std::max<size_t>(size_t(JC) * O, WB) * (n | 1) + 3) & ~size_t(3)) +
-                            ((size_t(PB) * J * O + 3) & ~size_t(3)) +
-                            size_t(PB) * JC * J * KPW) +
-           sizeof(int) * size_t(PB) * JC;
-}
-
-template <unsigned MASK>
-static cudaError_t dw_mask(const WideDw& p, bool first, cudaStream_t s) {
-    constexpr int PB = 32;
-    auto go = [&](auto kern, int jc, size_t sm) -> cudaError_t {
-        cudaError_t e = smem_optin((const void*)kern, sm);
-        if (e != cudaSuccess) return e;
-        const int njc = (p.I + jc - 1) / jc;
-        int dev = 0, nsm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        // slice the outputs until there are about two blocks per SM (at least 8 outputs a slice)
-        const int want = (2 * nsm + njc * p.GP - 1) / (njc * p.GP);
-        const int nos = std::max(1, std::min(want, p.O / 8));
-        kern<<<dim3(unsigned(njc * p.GP), unsigned(nos)), WB, sm, s>>>(p);
-        return cudaGetLastError();
-    };
-    if (first) return go(wide_dw_kernel<MASK, 2, PB, true>, 2, dw_smem<MASK, 2, PB, true>(p.O, p.g.n));
-    return go(wide_dw_kernel<MASK, 8, PB, false>, 8, dw_smem<MASK, 8, PB, false>(p.O, p.g.n));
-}
+template <int MW>
+cudaError_t wide_forward_layer_m(const WideLayer& p, unsigned mask, bool first, cudaStream_t s);
+template <int MW>
+cudaError_t wide_adjoint_layer_m(const WideLayer& p, unsigned mask, cudaStream_t s);
+template <int MW>
+cudaError_t wide_dw_layer_m(const WideDw& p, unsigned mask, bool first, cudaStream_t s);
 
 cudaError_t wide_forward_layer(const WideLayer& p, unsigned mask, bool first, cudaStream_t s) {
-    if (p.N == 0) return cudaSuccess;
-    switch (mask) {
-        case 0x01u: return fwd_mask<0x01u>(p, first, s);
-        case 0x0Fu: return fwd_mask<0x0Fu>(p, first, s);
-        case 0x1Fu: return fwd_mask<0x1Fu>(p, first, s);
+    switch (p.g.m) {
+        case 2: return wide_forward_layer_m<2>(p, mask, first, s);
+        case 3: return wide_forward_layer_m<3>(p, mask, first, s);
+        case 4: return wide_forward_layer_m<4>(p, mask, first, s);
+        case 5: return wide_forward_layer_m<5>(p, mask, first, s);
+        case 6: return wide_forward_layer_m<6>(p, mask, first, s);
     }
     return cudaErrorNotSupported;
 }
 
 cudaError_t wide_adjoint_layer(const WideLayer& p, unsigned mask, cudaStream_t s) {
-    if (p.N == 0) return cudaSuccess;
-    switch (mask) {
-        case 0x01u: return adj_mask<0x01u>(p, s);
-        case 0x0Fu: return adj_mask<0x0Fu>(p, s);
-        case 0x1Fu: return adj_mask<0x1Fu>(p, s);
+    switch (p.g.m) {
+        case 2: return wide_adjoint_layer_m<2>(p, mask, s);
+        case 3: return wide_adjoint_layer_m<3>(p, mask, s);
+        case 4: return wide_adjoint_layer_m<4>(p, mask, s);
+        case 5: return wide_adjoint_layer_m<5>(p, mask, s);
+        case 6: return wide_adjoint_layer_m<6>(p, mask, s);
     }
     return cudaErrorNotSupported;
 }
 
 cudaError_t wide_dw_layer(const WideDw& p, unsigned mask, bool first, cudaStream_t s) {
-    switch (mask) {
-        case 0x01u: return dw_mask<0x01u>(p, first, s);
-        case 0x0Fu: return dw_mask<0x0Fu>(p, first, s);
-        case 0x1Fu: return dw_mask<0x1Fu>(p, first, s);
+    switch (p.g.m) {
+        case 2: return wide_dw_layer_m<2>(p, mask, first, s);
+        case 3: return wide_dw_layer_m<3>(p, mask, first, s);
+        case 4: return wide_dw_layer_m<4>(p, mask, first, s);
+        case 5: return wide_dw_layer_m<5>(p, mask, first, s);
+        case 6: return wide_dw_layer_m<6>(p, mask, first, s);
     }
     return cudaErrorNotSupported;
 }

@@ -57,7 +57,11 @@ def test_param_count(lib):
     (dict(widths=[2, 5, 1], G=5, n_instances=0), capi.HRKAN_EINVAL),
     (dict(widths=[2, 5, 1], G=5, prec=7), capi.HRKAN_EINVAL),
     (dict(widths=[3, 5, 1], G=5), capi.HRKAN_EUNSUPPORTED),    # D = 3
-    (dict(widths=[2, 5, 1], G=5, m=6), capi.HRKAN_EUNSUPPORTED),
+    (dict(widths=[2, 5, 1], G=5, m=7), capi.HRKAN_EUNSUPPORTED),   # HR orders 2..6 are built
+    (dict(widths=[2, 5, 1], G=5, m=1), capi.HRKAN_EUNSUPPORTED),   # u_xx needs m >= 2
+    (dict(widths=[2, 5, 1], G=5, m=0), capi.HRKAN_EINVAL),
+    (dict(widths=[2, 64, 1], G=5, m=6, prec=capi.HRKAN_BF16), capi.HRKAN_EUNSUPPORTED),  # tensor cores: m = 4
+    (dict(widths=[2, 10, 1], G=5, m=3, n_instances=4), capi.HRKAN_EUNSUPPORTED),  # batched: fused m = 4 only
 ])
 def test_bad_configuration_is_rejected_before_the_device(lib, kw, code):
     with pytest.raises(capi.HRKANError) as ei:

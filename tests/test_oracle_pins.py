@@ -150,16 +150,18 @@ def _sympy_network_at(widths, G, k, m, lo, hi, W, point):
     return X, z[0]
 
 
-def test_forward_jets_match_symbolic_differentiation():
-    """Brute force on 8 points: jets of a [2,2,1] net vs sympy derivatives of its definition."""
+@pytest.mark.parametrize("m", [2, 3, 4, 6])
+def test_forward_jets_match_symbolic_differentiation(m):
+    """Brute force on 8 points: jets of a [2,2,1] net vs sympy derivatives of its definition,
+    for each HR order m the layer-wise kernels accept."""
     sp = pytest.importorskip("sympy")
-    net = dict(widths=[2, 2, 1], G=5, k=3, m=4, lo=-1.0, hi=1.0)
+    net = dict(widths=[2, 2, 1], G=5, k=3, m=m, lo=-1.0, hi=1.0)
     P = oracle.param_count(net)
     W = np.random.default_rng(3).normal(0, 0.5, P)
     x = np.random.default_rng(4).uniform(-1, 1, (2, 8))
     jets = oracle.forward(net, W, x, 0x1F)
     for p in range(8):
-        X, u = _sympy_network_at(net["widths"], 5, 3, 4, -1.0, 1.0, W, x[:, p])
+        X, u = _sympy_network_at(net["widths"], 5, 3, m, -1.0, 1.0, W, x[:, p])
         exprs = [u, sp.diff(u, X[0]), sp.diff(u, X[1]), sp.diff(u, X[0], 2), sp.diff(u, X[1], 2)]
         sub = {X[0]: x[0, p], X[1]: x[1, p]}
         want = np.array([float(e.evalf(subs=sub)) for e in exprs])
@@ -308,18 +310,18 @@ def _total_loss(net, prob, W, x_int, mask, x_bnd, g_bnd):
     return loss[0], dj, du
 
 
-@pytest.mark.parametrize("case", ["poisson", "burgers"])
-def test_weight_gradient_matches_central_differences(case):
+@pytest.mark.parametrize("case,m", [("poisson", 4), ("burgers", 4), ("poisson", 3), ("burgers", 6)])
+def test_weight_gradient_matches_central_differences(case, m):
     """Hand-written backward vs central FD (h = 1e-6, FP64) on 64 random weights."""
     rng = np.random.default_rng(16)
     if case == "poisson":
-        net = dict(widths=[2, 4, 3, 1], G=5, k=3, m=4, lo=-1.0, hi=1.0)
+        net = dict(widths=[2, 4, 3, 1], G=5, k=3, m=m, lo=-1.0, hi=1.0)
         prob = dict(kind=oracle.POISSON, a=1, b=2, alpha=0.5)
         mask = 0x1F
         x_int = rng.uniform(-1, 1, (2, 40))
         x_bnd = np.stack([rng.choice([-1.0, 1.0], 12), rng.uniform(-1, 1, 12)])
     else:
-        net = dict(widths=[2, 3, 3, 1], G=6, k=3, m=4, lo=-1.0, hi=1.0)
+        net = dict(widths=[2, 3, 3, 1], G=6, k=3, m=m, lo=-1.0, hi=1.0)
         prob = dict(kind=oracle.BURGERS, lam=1.0, nu=0.01 / np.pi, alpha=1.0)
         mask = inputs.MASK_BURGERS
         x_int = np.stack([rng.uniform(-1, 1, 40), rng.uniform(0, 1, 40)])
