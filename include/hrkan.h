@@ -59,7 +59,8 @@ enum hrkan_status {
     HRKAN_ECUDA = -3,         /* a CUDA call or kernel launch failed */
     HRKAN_EUNSUPPORTED = -4,  /* valid request that this build does not implement */
     HRKAN_ETIMEOUT = -5,      /* a bounded device-side wait gave up */
-    HRKAN_ENONFINITE = -6     /* the loss became NaN or infinite */
+    HRKAN_ENONFINITE = -6,    /* the loss became NaN or infinite */
+    HRKAN_EIO = -7            /* a checkpoint file could not be written, or read back whole */
 };
 
 enum hrkan_prec { HRKAN_FP32 = 0, HRKAN_BF16 = 1, HRKAN_TF32 = 2 };
@@ -337,6 +338,42 @@ enum hrkan_kernel_class {
 };
 int hrkan_profile_enable(hrkan_t h, int enable);
 int hrkan_profile_read(hrkan_t h, int kernel_class, double* total_ms, int64_t* launches, int reset);
+
+/*
+ * Checkpoint / resume of the training state that Section 4's Adam runs carry
+ * from step to step: the weights, both Adam moments and the step counts.
+ *
+ * File layout (host byte order, little-endian on every supported host):
+ *   bytes 0-7    magic "HRKANCK1"
+ *   uint32       version (1)
+ *   uint32       n_instances
+ *   int64        P (weights per instance, hrkan_param_count)
+ *   int64        t (the caller's Adam step count, stored as given)
+ *   int64        t_device (steps taken with t = 0, the handle's device counter)
+ *   float32      W [n_instances * P]
+ *   float64      m [n_instances * P]  (first moment)
+ *   float64      v [n_instances * P]  (second moment)
+ * The file is written to "<path>.part" and renamed onto path, so a failed write
+ * never leaves a partial checkpoint under path.
+ *
+ * hrkan_checkpoint_write / _read work on HOST buffers (W, m, v of n_instances
+ * * P elements; the caller owns them); _read checks the magic, the version and
+ * that P and n_instances match (HRKAN_EINVAL otherwise), and fails with
+ * HRKAN_EIO on a missing, short or over-long file.
+ *
+ * hrkan_save / hrkan_load move the state of a handle: W is the DEVICE weight
+ * buffer [n_instances * P] float32, the moments and the device step counter
+ * are the handle's.  Both synchronise `stream` (file I/O is blocking) and
+ * allocate temporary host buffers (HRKAN_ENOMEM if that fails).  hrkan_load
+ * writes W, the moments and the counter, and returns the stored caller step
+ * count in *t (may be NULL); a failed load leaves the handle and W unchanged.
+ */
+int hrkan_checkpoint_write(const char* path, int64_t P, int n_instances, int64_t t, int64_t t_device,
+                           const float* W, const double* m, const double* v);
+int hrkan_checkpoint_read(const char* path, int64_t P, int n_instances, int64_t* t, int64_t* t_device,
+                          float* W, double* m, double* v);
+int hrkan_save(hrkan_t h, const float* W, int64_t t, const char* path, hrkan_stream_t stream);
+int hrkan_load(hrkan_t h, float* W, int64_t* t, const char* path, hrkan_stream_t stream);
 
 #ifdef __cplusplus
 }

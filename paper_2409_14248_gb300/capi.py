@@ -16,8 +16,8 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhrkan.so")
 
-HRKAN_OK, HRKAN_EINVAL, HRKAN_ENOMEM, HRKAN_ECUDA, HRKAN_EUNSUPPORTED, HRKAN_ETIMEOUT, HRKAN_ENONFINITE = \
-    0, -1, -2, -3, -4, -5, -6
+HRKAN_OK, HRKAN_EINVAL, HRKAN_ENOMEM, HRKAN_ECUDA, HRKAN_EUNSUPPORTED, HRKAN_ETIMEOUT, HRKAN_ENONFINITE, HRKAN_EIO = \
+    0, -1, -2, -3, -4, -5, -6, -7
 HRKAN_FP32, HRKAN_BF16, HRKAN_TF32 = 0, 1, 2
 HRKAN_POISSON, HRKAN_BURGERS = 0, 1
 HRKAN_MAX_WIDTHS = 8
@@ -27,7 +27,8 @@ EXPORTS = ("hrkan_param_count", "hrkan_init", "hrkan_destroy", "hrkan_last_error
            "hrkan_forward_jets", "pinn_residual_loss", "hrkan_backward", "adam_step", "hrkan_reset_moments",
            "hrkan_train_step", "hrkan_profile_enable", "hrkan_profile_read", "hrkan_backward_noalloc",
            "hrkan_train_step_batched", "hrkan_forward_jets_batched", "hrkan_set_batch_items", "hrkan_sync_status",
-           "hrkan_layer_jets", "hrkan_layer_dw", "hrkan_layer_adjoint", "hrkan_autotune_batch")
+           "hrkan_layer_jets", "hrkan_layer_dw", "hrkan_layer_adjoint", "hrkan_autotune_batch",
+           "hrkan_checkpoint_write", "hrkan_checkpoint_read", "hrkan_save", "hrkan_load")
 HRKAN_KERNEL_FUSED, HRKAN_KERNEL_REDUCE, HRKAN_KERNEL_FORWARD, HRKAN_KERNEL_RESIDUAL, HRKAN_KERNEL_TENSOR = 0, 1, 2, 3, 4
 
 
@@ -96,6 +97,10 @@ def load_library(path: str = LIB_PATH):
         lib.hrkan_layer_adjoint.argtypes = [_vp, _i32, _vp, _vp, _vp, _i64, _u32, _vp, _vp]
         lib.hrkan_profile_enable.argtypes = [_vp, _i32]
         lib.hrkan_profile_read.argtypes = [_vp, _i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
+        lib.hrkan_checkpoint_write.argtypes = [ctypes.c_char_p, _i64, _i32, _i64, _i64, _vp, _vp, _vp]
+        lib.hrkan_checkpoint_read.argtypes = [ctypes.c_char_p, _i64, _i32, _i64p, _i64p, _vp, _vp, _vp]
+        lib.hrkan_save.argtypes = [_vp, _vp, _i64, ctypes.c_char_p, _vp]
+        lib.hrkan_load.argtypes = [_vp, _vp, _i64p, ctypes.c_char_p, _vp]
         for name in EXPORTS:
             if name not in ("hrkan_destroy", "hrkan_last_error", "hrkan_param_count", "hrkan_tape_floats"):
                 getattr(lib, name).restype = _i32
@@ -199,6 +204,50 @@ def adam_step(h, W, dW, lr, b1=0.9, b2=0.999, eps=1e-8, t=1, stream=None):
 
 def hrkan_reset_moments(h, stream=None):
     _check(load_library().hrkan_reset_moments(h, _stream(stream)))
+
+
+def hrkan_checkpoint_write(path, P, n_instances, t, t_device, W, m, v):
+    """Write a checkpoint from host arrays (W float32, m and v float64, n_instances * P each)."""
+    import numpy as np
+    W = np.ascontiguousarray(W, dtype=np.float32)
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    n = int(P) * int(n_instances)
+    if W.size != n or m.size != n or v.size != n:
+        raise ValueError("W, m and v need n_instances * P elements")
+    _check(load_library().hrkan_checkpoint_write(os.fsencode(path), ctypes.c_int64(int(P)), int(n_instances),
+                                                 ctypes.c_int64(int(t)), ctypes.c_int64(int(t_device)),
+                                                 W.ctypes.data_as(ctypes.c_void_p), m.ctypes.data_as(ctypes.c_void_p),
+                                                 v.ctypes.data_as(ctypes.c_void_p)))
+
+
+def hrkan_checkpoint_read(path, P, n_instances):
+    """Read a checkpoint into new host arrays: returns (t, t_device, W, m, v)."""
+    import numpy as np
+    n = int(P) * int(n_instances)
+    W = np.empty(n, dtype=np.float32)
+    m = np.empty(n, dtype=np.float64)
+    v = np.empty(n, dtype=np.float64)
+    t, td = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load_library().hrkan_checkpoint_read(os.fsencode(path), ctypes.c_int64(int(P)), int(n_instances),
+                                                ctypes.byref(t), ctypes.byref(td), W.ctypes.data_as(ctypes.c_void_p),
+                                                m.ctypes.data_as(ctypes.c_void_p), v.ctypes.data_as(ctypes.c_void_p)))
+    return t.value, td.value, W, m, v
+
+
+def hrkan_save(h, W, t, path, stream=None):
+    """Save the weights (device tensor), the handle's Adam moments and step counts."""
+    import torch
+    _check(load_library().hrkan_save(h, _ptr(W, torch.float32), ctypes.c_int64(int(t)), os.fsencode(path),
+                                     _stream(stream)))
+
+
+def hrkan_load(h, W, path, stream=None):
+    """Load a checkpoint into W (device tensor) and the handle; returns the stored step count t."""
+    import torch
+    t = ctypes.c_int64(0)
+    _check(load_library().hrkan_load(h, _ptr(W, torch.float32), ctypes.byref(t), os.fsencode(path), _stream(stream)))
+    return t.value
 
 
 def hrkan_train_step(h, prob, W, x_int, N_int, x_bnd, g_bnd, N_bnd, lr, b1, b2, eps, t, loss, dW=None,

@@ -805,6 +805,57 @@ int hrkan_reset_moments(hrkan_t h, hrkan_stream_t stream) {
     return HRKAN_OK;
 }
 
+int hrkan_save(hrkan_t h, const float* W, int64_t t, const char* path, hrkan_stream_t stream) {
+    if (!h || !W || !path) return fail(HRKAN_EINVAL, "hrkan_save: null argument");
+    if (int rc = use_device(h)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = size_t(h->P) * h->cfg.n_instances;
+    std::vector<float> w;
+    std::vector<double> m, v;
+    try {
+        w.resize(n);
+        m.resize(n);
+        v.resize(n);
+    } catch (...) {
+        return fail(HRKAN_ENOMEM, "hrkan_save: host buffers");
+    }
+    int tc[2] = {0, 0};
+    HR_CUDA(cudaMemcpyAsync(w.data(), W, n * sizeof(float), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
+    HR_CUDA(cudaMemcpyAsync(m.data(), h->m1, n * sizeof(double), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
+    HR_CUDA(cudaMemcpyAsync(v.data(), h->m2, n * sizeof(double), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
+    HR_CUDA(cudaMemcpyAsync(tc, h->t_counter, sizeof tc, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
+    HR_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    return hrkan_checkpoint_write(path, h->P, h->cfg.n_instances, t, int64_t(tc[0]), w.data(), m.data(), v.data());
+}
+
+int hrkan_load(hrkan_t h, float* W, int64_t* t, const char* path, hrkan_stream_t stream) {
+    if (!h || !W || !path) return fail(HRKAN_EINVAL, "hrkan_load: null argument");
+    if (int rc = use_device(h)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = size_t(h->P) * h->cfg.n_instances;
+    std::vector<float> w;
+    std::vector<double> m, v;
+    try {
+        w.resize(n);
+        m.resize(n);
+        v.resize(n);
+    } catch (...) {
+        return fail(HRKAN_ENOMEM, "hrkan_load: host buffers");
+    }
+    int64_t ts = 0, td = 0;
+    if (int rc = hrkan_checkpoint_read(path, h->P, h->cfg.n_instances, &ts, &td, w.data(), m.data(), v.data()))
+        return rc;
+    if (td < 0 || td > INT32_MAX) return fail(HRKAN_EINVAL, "hrkan_load: device step count %lld", (long long)td);
+    const int tc[2] = {int(td), int(td)};
+    HR_CUDA(cudaMemcpyAsync(W, w.data(), n * sizeof(float), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync");
+    HR_CUDA(cudaMemcpyAsync(h->m1, m.data(), n * sizeof(double), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync");
+    HR_CUDA(cudaMemcpyAsync(h->m2, v.data(), n * sizeof(double), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync");
+    HR_CUDA(cudaMemcpyAsync(h->t_counter, tc, sizeof tc, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync");
+    HR_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");   // the host buffers die here
+    if (t) *t = ts;
+    return HRKAN_OK;
+}
+
 int hrkan_profile_enable(hrkan_t h, int enable) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
     h->prof = enable != 0;
