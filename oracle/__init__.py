@@ -106,9 +106,9 @@ def support(G, k, lo, hi):
 
 
 def hr_basis(m, s, e, x):
-    """[v, v', v'', v'''] of the order-m HR basis on [s, e] at x (Eq. 2)."""
+    """Value and first to fourth derivatives of the order-m HR basis on [s, e] at x (Eq. 2)."""
     lib = _load()
-    out = np.zeros(4)
+    out = np.zeros(5)
     lib.orc_hr_basis(int(m), float(s), float(e), float(x), out.ctypes.data_as(_dp))
     return out
 
@@ -120,7 +120,7 @@ def param_count(net):
 
 
 def n_rows(mask, D=2):
-    return bin(int(mask) & ((1 << (1 + 2 * D)) - 1)).count("1")
+    return bin(int(mask) & ((1 << (1 + 3 * D)) - 1)).count("1")
 
 
 def forward(net, W, x, mask):

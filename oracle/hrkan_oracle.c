@@ -15,13 +15,15 @@
  *              intervals [s_i, e_i] with s_i = lo + (i-k)h, e_i = lo + (i+1)h,
  *              h = (hi-lo)/g.
  *   basis      Section 3, Eq. 2: v_{m,i}(x) = ReLU(e_i-x)^m ReLU(x-s_i)^m c_m,
- *              c_m = (2/(e_i-s_i))^{2m}; first to third derivatives are the
+ *              c_m = (2/(e_i-s_i))^{2m}; first to fourth derivatives are the
  *              derivatives of that polynomial inside (s_i, e_i), zero outside.
  *   layer      Sections 1-3 (KAN layer as a matrix operation): output unit o of
  *              a layer is sum_j sum_i W[o][j][i] v_i(z_j), summed densely over
  *              all n bases; no bias, no base branch, no normalisation.
  *   jets       the input derivatives the PDE residuals need (Eq. 3: Laplacian;
- *              Eq. 6-8: u_t, u_x, u_xx) by the forward-mode chain rule.
+ *              Eq. 6-8: u_t, u_x, u_xx), and third derivatives along each input
+ *              (the higher-order terms Section 3 motivates the order m with),
+ *              by the forward-mode chain rule.
  *   loss       Eq. 4 (Poisson) and Eq. 8 (Burgers): L = alpha L_pde + L_bnd,
  *              L_bnd the pooled mean over all boundary/initial points.
  *   backward   hand-written reverse mode of the above.
@@ -60,12 +62,13 @@ static double ipow(double b, int p)
 }
 
 /*
- * out[0..3] = v, v', v'', v''' of the order-m HR basis on [s, e] at x.
- * With p(x) = (e-x)(x-s), p' = e+s-2x, p'' = -2, inside (s, e):
+ * out[0..4] = v, v', v'', v''', v'''' of the order-m HR basis on [s, e] at x.
+ * With p(x) = (e-x)(x-s), p' = e+s-2x, p'' = -2, p''' = 0, inside (s, e):
  *   v    = c p^m
  *   v'   = c m p^{m-1} p'
  *   v''  = c [m(m-1) p^{m-2} p'^2 - 2m p^{m-1}]
  *   v''' = c [m(m-1)(m-2) p^{m-3} p'^3 - 6m(m-1) p^{m-2} p']
+ *   v''''= c [m(m-1)(m-2)(m-3) p^{m-4} p'^4 - 12m(m-1)(m-2) p^{m-3} p'^2 + 12m(m-1) p^{m-2}]
  * The value is the literal ReLU product of Eq. 2 everywhere; the derivatives
  * are taken as 0 at and outside the end points.
  */
@@ -75,7 +78,7 @@ void orc_hr_basis(int m, double s, double e, double x, double* out)
     double A = relu(e - x), B = relu(x - s);
     out[0] = ipow(A, m) * ipow(B, m) * c;
     if (!(x > s && x < e)) {
-        out[1] = out[2] = out[3] = 0.0;
+        out[1] = out[2] = out[3] = out[4] = 0.0;
         return;
     }
     double p = A * B, dp = e + s - 2.0 * x;
@@ -84,6 +87,9 @@ void orc_hr_basis(int m, double s, double e, double x, double* out)
     out[2] = c * (md * (md - 1.0) * ipow(p, m - 2) * dp * dp - 2.0 * md * ipow(p, m - 1));
     out[3] = c * (md * (md - 1.0) * (md - 2.0) * ipow(p, m - 3) * dp * dp * dp
                   - 6.0 * md * (md - 1.0) * ipow(p, m - 2) * dp);
+    out[4] = c * (md * (md - 1.0) * (md - 2.0) * (md - 3.0) * ipow(p, m - 4) * dp * dp * dp * dp
+                  - 12.0 * md * (md - 1.0) * (md - 2.0) * ipow(p, m - 3) * dp * dp
+                  + 12.0 * md * (md - 1.0) * ipow(p, m - 2));
 }
 
 /* ------------------------------------------------------ reduced precision */
@@ -150,28 +156,31 @@ static int max_width(const orc_net* net)
 
 /*
  * One layer, one point, full jets over D input dims.
- * z[j], dz[j*D+d] = dz_j/dx_d, d2z[j*D+d] = d2z_j/dx_d^2  ->  y, dy, d2y.
+ * z[j], dz[j*D+d] = dz_j/dx_d, d2z[j*D+d] = d2z_j/dx_d^2, d3z = d3z_j/dx_d^3
+ *   ->  y, dy, d2y, d3y, by the chain rule for y = sum W v(z):
+ *   y_d = v' z_d,  y_dd = v'' z_d^2 + v' z_dd,  y_ddd = v''' z_d^3 + 3 v'' z_d z_dd + v' z_ddd.
  */
 static void layer_forward(const orc_net* net, int l, const double* Wl, int D,
                           const double* s, const double* e,
-                          const double* z, const double* dz, const double* d2z,
-                          double* y, double* dy, double* d2y, int fmt)
+                          const double* z, const double* dz, const double* d2z, const double* d3z,
+                          double* y, double* dy, double* d2y, double* d3y, int fmt)
 {
     int I = net->widths[l], O = net->widths[l + 1], n = orc_nbasis(net);
     for (int o = 0; o < O; ++o) {
         y[o] = 0.0;
-        for (int d = 0; d < D; ++d) dy[o * D + d] = d2y[o * D + d] = 0.0;
+        for (int d = 0; d < D; ++d) dy[o * D + d] = d2y[o * D + d] = d3y[o * D + d] = 0.0;
     }
     for (int j = 0; j < I; ++j) {
         for (int i = 0; i < n; ++i) {
-            double b[4];
+            double b[5];
             orc_hr_basis(net->m, s[i], e[i], z[j], b);
             /* the basis-matrix entries (jet rows) of this input unit and basis */
-            double a0 = round_to(b[0], fmt), a1[8], a2[8];
+            double a0 = round_to(b[0], fmt), a1[8], a2[8], a3[8];
             for (int d = 0; d < D; ++d) {
-                double zd = dz[j * D + d];
+                double zd = dz[j * D + d], zdd = d2z[j * D + d], zddd = d3z[j * D + d];
                 a1[d] = round_to(b[1] * zd, fmt);
-                a2[d] = round_to(b[2] * zd * zd + b[1] * d2z[j * D + d], fmt);
+                a2[d] = round_to(b[2] * zd * zd + b[1] * zdd, fmt);
+                a3[d] = round_to(b[3] * zd * zd * zd + 3.0 * b[2] * zd * zdd + b[1] * zddd, fmt);
             }
             for (int o = 0; o < O; ++o) {
                 double w = round_to(Wl[((long)o * I + j) * n + i], fmt);
@@ -179,26 +188,27 @@ static void layer_forward(const orc_net* net, int l, const double* Wl, int D,
                 for (int d = 0; d < D; ++d) {
                     dy[o * D + d] += w * a1[d];
                     d2y[o * D + d] += w * a2[d];
+                    d3y[o * D + d] += w * a3[d];
                 }
             }
         }
     }
 }
 
-/* jet rows selected by mask: bit 0 = u, bit 1+d = du/dx_d, bit 1+D+d = d2u/dx_d^2 */
+/* jet rows selected by mask: bit 0 = u, bit 1+d = du/dx_d, bit 1+D+d = d2u/dx_d^2,
+ * bit 1+2D+d = d3u/dx_d^3 */
 static int mask_rows(unsigned mask, int D, int* bit_of_row)
 {
     int J = 0;
-    for (int b = 0; b < 1 + 2 * D; ++b)
+    for (int b = 0; b < 1 + 3 * D; ++b)
         if (mask & (1u << b)) bit_of_row[J++] = b;
     return J;
 }
 
 /* Scratch holding the per-layer input jets of one point. */
 typedef struct {
-    double *z, *dz, *d2z; /* [layer][maxw], [layer][maxw*D] */
-    double *y, *dy, *d2y;
-    int stride;           /* maxw */
+    double *z, *dz, *d2z, *d3z; /* [layer][maxw], [layer][maxw*D] */
+    int stride;                 /* maxw */
 } point_tape;
 
 static int tape_alloc(point_tape* t, const orc_net* net, int D)
@@ -208,15 +218,13 @@ static int tape_alloc(point_tape* t, const orc_net* net, int D)
     t->z = calloc((size_t)(L + 1) * w, sizeof(double));
     t->dz = calloc((size_t)(L + 1) * w * D, sizeof(double));
     t->d2z = calloc((size_t)(L + 1) * w * D, sizeof(double));
-    t->y = calloc((size_t)w, sizeof(double));
-    t->dy = calloc((size_t)w * D, sizeof(double));
-    t->d2y = calloc((size_t)w * D, sizeof(double));
-    return (t->z && t->dz && t->d2z && t->y && t->dy && t->d2y) ? 0 : -1;
+    t->d3z = calloc((size_t)(L + 1) * w * D, sizeof(double));
+    return (t->z && t->dz && t->d2z && t->d3z) ? 0 : -1;
 }
 
 static void tape_free(point_tape* t)
 {
-    free(t->z); free(t->dz); free(t->d2z); free(t->y); free(t->dy); free(t->d2y);
+    free(t->z); free(t->dz); free(t->d2z); free(t->d3z);
 }
 
 /* Forward of one point through all layers; layer l's input jets land in the tape row l,
@@ -230,14 +238,15 @@ static void point_forward(const orc_net* net, const double* W, int D, const doub
         for (int d = 0; d < D; ++d) {
             t->dz[j * D + d] = (j == d) ? 1.0 : 0.0;
             t->d2z[j * D + d] = 0.0;
+            t->d3z[j * D + d] = 0.0;
         }
     }
     for (int l = 0; l < L; ++l) {
         const double* Wl = W + layer_offset(net, l);
         layer_forward(net, l, Wl, D, s, e, t->z + (long)l * w, t->dz + (long)l * w * D,
-                      t->d2z + (long)l * w * D, t->z + (long)(l + 1) * w,
+                      t->d2z + (long)l * w * D, t->d3z + (long)l * w * D, t->z + (long)(l + 1) * w,
                       t->dz + (long)(l + 1) * w * D, t->d2z + (long)(l + 1) * w * D,
-                      ((round_layers >> l) & 1u) ? fmt : ORC_EXACT);
+                      t->d3z + (long)(l + 1) * w * D, ((round_layers >> l) & 1u) ? fmt : ORC_EXACT);
     }
 }
 
@@ -268,9 +277,10 @@ int orc_forward_rounded(int n_widths, const int* widths, int G, int k, int m, do
         const double* u = t.z + (long)L * w;
         const double* du = t.dz + (long)L * w * D;
         const double* d2u = t.d2z + (long)L * w * D;
+        const double* d3u = t.d3z + (long)L * w * D;
         for (int r = 0; r < J; ++r) {
             int b = rows[r];
-            double v = (b == 0) ? u[0] : (b <= D) ? du[b - 1] : d2u[b - 1 - D];
+            double v = (b == 0) ? u[0] : (b <= D) ? du[b - 1] : (b <= 2 * D) ? d2u[b - 1 - D] : d3u[b - 1 - 2 * D];
             jets[(long)r * N + p] = v;
         }
     }
@@ -287,8 +297,8 @@ int orc_forward(int n_widths, const int* widths, int G, int k, int m, double lo,
 
 /*
  * One layer (Sections 1-3) applied to given input jets, D = 2:
- *   zin[r][j][p] for the jet rows r of mask (value, first, second derivatives
- *   in bit order), units j < I, points p < N; rows not in mask are zero.
+ *   zin[r][j][p] for the jet rows r of mask (value, first, second, third
+ *   derivatives in bit order), units j < I, points p < N; rows not in mask are zero.
  *   yout[r][o][p], the same rows for the O outputs.
  * Basis-matrix entries and weights rounded to fmt (ORC_EXACT: none).
  */
@@ -307,31 +317,35 @@ int orc_layer_forward(int I, int O, int G, int k, int m, double lo, double hi, c
     double* z = malloc(sizeof(double) * I);
     double* dz = calloc((size_t)I * D, sizeof(double));
     double* d2z = calloc((size_t)I * D, sizeof(double));
+    double* d3z = calloc((size_t)I * D, sizeof(double));
     double* y = malloc(sizeof(double) * O);
     double* dy = malloc(sizeof(double) * O * D);
     double* d2y = malloc(sizeof(double) * O * D);
+    double* d3y = malloc(sizeof(double) * O * D);
     orc_support(G, k, lo, hi, s, e);
     for (long p = 0; p < N; ++p) {
         for (int j = 0; j < I; ++j) {
             z[j] = 0.0;
-            for (int d = 0; d < D; ++d) dz[j * D + d] = d2z[j * D + d] = 0.0;
+            for (int d = 0; d < D; ++d) dz[j * D + d] = d2z[j * D + d] = d3z[j * D + d] = 0.0;
             for (int r = 0; r < J; ++r) {
                 double v = zin[((long)r * I + j) * N + p];
                 int b = rows[r];
                 if (b == 0) z[j] = v;
                 else if (b <= D) dz[j * D + b - 1] = v;
-                else d2z[j * D + b - 1 - D] = v;
+                else if (b <= 2 * D) d2z[j * D + b - 1 - D] = v;
+                else d3z[j * D + b - 1 - 2 * D] = v;
             }
         }
-        layer_forward(&net, 0, Wl, D, s, e, z, dz, d2z, y, dy, d2y, fmt);
+        layer_forward(&net, 0, Wl, D, s, e, z, dz, d2z, d3z, y, dy, d2y, d3y, fmt);
         for (int o = 0; o < O; ++o)
             for (int r = 0; r < J; ++r) {
                 int b = rows[r];
-                double v = (b == 0) ? y[o] : (b <= D) ? dy[o * D + b - 1] : d2y[o * D + b - 1 - D];
+                double v = (b == 0) ? y[o] : (b <= D) ? dy[o * D + b - 1]
+                         : (b <= 2 * D) ? d2y[o * D + b - 1 - D] : d3y[o * D + b - 1 - 2 * D];
                 yout[((long)r * O + o) * N + p] = v;
             }
     }
-    free(s); free(e); free(z); free(dz); free(d2z); free(y); free(dy); free(d2y);
+    free(s); free(e); free(z); free(dz); free(d2z); free(d3z); free(y); free(dy); free(d2y); free(d3y);
     return 0;
 }
 
@@ -339,8 +353,8 @@ int orc_layer_forward(int I, int O, int G, int k, int m, double lo, double hi, c
  * Weight gradient of one layer for given output-jet gradients (the
  * contraction of Sections 2-3 differentiated w.r.t. W):
  *   dW[o][j][i] = sum_p sum_r gy[r][o][p] * A_r[p][j][i]
- * with the basis-matrix entries A_r of layer_forward (value, first and second
- * derivative rows of input unit j and basis i).  fmt rounds the A entries and
+ * with the basis-matrix entries A_r of layer_forward (value, first, second and
+ * third derivative rows of input unit j and basis i).  fmt rounds the A entries and
  * gy to BF16/TF32 before the FP64 products and sums (the reduced-precision
  * contraction's inputs); ORC_EXACT rounds nothing.  zin [J][I][N], gy [J][O][N],
  * dW [O][I][n] overwritten.
@@ -360,23 +374,32 @@ int orc_layer_dw(int I, int O, int G, int k, int m, double lo, double hi, const 
     double a[16];
     for (long p = 0; p < N; ++p) {
         for (int j = 0; j < I; ++j) {
-            double z = 0.0, dz[2] = {0.0, 0.0}, d2z[2] = {0.0, 0.0};
+            double z = 0.0, dz[2] = {0.0, 0.0}, d2z[2] = {0.0, 0.0}, d3z[2] = {0.0, 0.0};
             for (int r = 0; r < J; ++r) {
                 double v = zin[((long)r * I + j) * N + p];
                 int b = rows[r];
                 if (b == 0) z = v;
                 else if (b <= D) dz[b - 1] = v;
-                else d2z[b - 1 - D] = v;
+                else if (b <= 2 * D) d2z[b - 1 - D] = v;
+                else d3z[b - 1 - 2 * D] = v;
             }
             for (int i = 0; i < n; ++i) {
-                double b[4];
+                double b[5];
                 orc_hr_basis(m, s[i], e[i], z, b);
                 for (int r = 0; r < J; ++r) {
                     int bit = rows[r];
                     double v;
-                    if (bit == 0) v = b[0];
-                    else if (bit <= D) v = b[1] * dz[bit - 1];
-                    else v = b[2] * dz[bit - 1 - D] * dz[bit - 1 - D] + b[1] * d2z[bit - 1 - D];
+                    if (bit == 0) {
+                        v = b[0];
+                    } else if (bit <= D) {
+                        v = b[1] * dz[bit - 1];
+                    } else if (bit <= 2 * D) {
+                        int d = bit - 1 - D;
+                        v = b[2] * dz[d] * dz[d] + b[1] * d2z[d];
+                    } else {
+                        int d = bit - 1 - 2 * D;
+                        v = b[3] * dz[d] * dz[d] * dz[d] + 3.0 * b[2] * dz[d] * d2z[d] + b[1] * d3z[d];
+                    }
                     a[r] = round_to(v, fmt);
                 }
                 for (int o = 0; o < O; ++o) {
@@ -401,6 +424,10 @@ int orc_layer_dw(int I, int O, int G, int k, int m, double lo, double hi, const 
  *   dd-row (A = v2 z_d^2 + v1 z_dd):
  *                     d/dz += dA_dd (v3 z_d^2 + v2 z_dd),   d/dz_d += dA_dd 2 v2 z_d,
  *                     d/dz_dd += dA_dd v1
+ *   ddd-row (A = v3 z_d^3 + 3 v2 z_d z_dd + v1 z_ddd), through the fourth derivative v4:
+ *                     d/dz += dA (v4 z_d^3 + 3 v3 z_d z_dd + v2 z_ddd),
+ *                     d/dz_d += dA (3 v3 z_d^2 + 3 v2 z_dd),  d/dz_dd += dA 3 v2 z_d,
+ *                     d/dz_ddd += dA v1
  * fmt rounds gy and W before the FP64 sum over o (the reduced-precision
  * contraction's inputs); ORC_EXACT rounds nothing.  zin [J][I][N],
  * gy [J][O][N], gz [J][I][N] written.
@@ -418,17 +445,18 @@ int orc_layer_adjoint(int I, int O, int G, int k, int m, double lo, double hi, c
     orc_support(G, k, lo, hi, s, e);
     for (long p = 0; p < N; ++p) {
         for (int j = 0; j < I; ++j) {
-            double z = 0.0, dz[2] = {0.0, 0.0}, d2z[2] = {0.0, 0.0};
+            double z = 0.0, dz[2] = {0.0, 0.0}, d2z[2] = {0.0, 0.0}, d3z[2] = {0.0, 0.0};
             for (int r = 0; r < J; ++r) {
                 double v = zin[((long)r * I + j) * N + p];
                 int b = rows[r];
                 if (b == 0) z = v;
                 else if (b <= D) dz[b - 1] = v;
-                else d2z[b - 1 - D] = v;
+                else if (b <= 2 * D) d2z[b - 1 - D] = v;
+                else d3z[b - 1 - 2 * D] = v;
             }
-            double g_z = 0.0, g_d[2] = {0.0, 0.0}, g_dd[2] = {0.0, 0.0};
+            double g_z = 0.0, g_d[2] = {0.0, 0.0}, g_dd[2] = {0.0, 0.0}, g_ddd[2] = {0.0, 0.0};
             for (int i = 0; i < n; ++i) {
-                double b[4];
+                double b[5];
                 orc_hr_basis(m, s[i], e[i], z, b);
                 for (int r = 0; r < J; ++r) {
                     double dA = 0.0;
@@ -442,17 +470,24 @@ int orc_layer_adjoint(int I, int O, int G, int k, int m, double lo, double hi, c
                         int d = bit - 1;
                         g_z += dA * b[2] * dz[d];
                         g_d[d] += dA * b[1];
-                    } else {
+                    } else if (bit <= 2 * D) {
                         int d = bit - 1 - D;
                         g_z += dA * (b[3] * dz[d] * dz[d] + b[2] * d2z[d]);
                         g_d[d] += dA * 2.0 * b[2] * dz[d];
                         g_dd[d] += dA * b[1];
+                    } else {
+                        int d = bit - 1 - 2 * D;
+                        g_z += dA * (b[4] * dz[d] * dz[d] * dz[d] + 3.0 * b[3] * dz[d] * d2z[d] + b[2] * d3z[d]);
+                        g_d[d] += dA * (3.0 * b[3] * dz[d] * dz[d] + 3.0 * b[2] * d2z[d]);
+                        g_dd[d] += dA * 3.0 * b[2] * dz[d];
+                        g_ddd[d] += dA * b[1];
                     }
                 }
             }
             for (int r = 0; r < J; ++r) {
                 int bit = rows[r];
-                double v = (bit == 0) ? g_z : (bit <= D) ? g_d[bit - 1] : g_dd[bit - 1 - D];
+                double v = (bit == 0) ? g_z : (bit <= D) ? g_d[bit - 1]
+                         : (bit <= 2 * D) ? g_dd[bit - 1 - D] : g_ddd[bit - 1 - 2 * D];
                 gz[((long)r * I + j) * N + p] = v;
             }
         }
@@ -467,18 +502,18 @@ int orc_layer_adjoint(int I, int O, int G, int k, int m, double lo, double hi, c
  */
 static void layer_backward(const orc_net* net, int l, const double* Wl, double* dWl, int D,
                            const double* s, const double* e, const double* z,
-                           const double* dz, const double* d2z, const double* gy,
-                           const double* gdy, const double* gd2y, double* gz, double* gdz,
-                           double* gd2z)
+                           const double* dz, const double* d2z, const double* d3z, const double* gy,
+                           const double* gdy, const double* gd2y, const double* gd3y, double* gz,
+                           double* gdz, double* gd2z, double* gd3z)
 {
     int I = net->widths[l], O = net->widths[l + 1], n = orc_nbasis(net);
     for (int j = 0; j < I; ++j) {
         gz[j] = 0.0;
-        for (int d = 0; d < D; ++d) gdz[j * D + d] = gd2z[j * D + d] = 0.0;
+        for (int d = 0; d < D; ++d) gdz[j * D + d] = gd2z[j * D + d] = gd3z[j * D + d] = 0.0;
     }
     for (int j = 0; j < I; ++j) {
         for (int i = 0; i < n; ++i) {
-            double b[4];
+            double b[5];
             orc_hr_basis(net->m, s[i], e[i], z[j], b);
             for (int o = 0; o < O; ++o) {
                 long wi = ((long)o * I + j) * n + i;
@@ -486,12 +521,16 @@ static void layer_backward(const orc_net* net, int l, const double* Wl, double* 
                 double gW = gy[o] * b[0];
                 double acc_z = gy[o] * b[1];
                 for (int d = 0; d < D; ++d) {
-                    double zd = dz[j * D + d], zdd = d2z[j * D + d];
-                    double g1 = gdy[o * D + d], g2 = gd2y[o * D + d];
-                    gW += g1 * b[1] * zd + g2 * (b[2] * zd * zd + b[1] * zdd);
-                    acc_z += g1 * b[2] * zd + g2 * (b[3] * zd * zd + b[2] * zdd);
-                    gdz[j * D + d] += w * (g1 * b[1] + g2 * 2.0 * b[2] * zd);
-                    gd2z[j * D + d] += w * g2 * b[1];
+                    double zd = dz[j * D + d], zdd = d2z[j * D + d], zddd = d3z[j * D + d];
+                    double g1 = gdy[o * D + d], g2 = gd2y[o * D + d], g3 = gd3y[o * D + d];
+                    gW += g1 * b[1] * zd + g2 * (b[2] * zd * zd + b[1] * zdd)
+                        + g3 * (b[3] * zd * zd * zd + 3.0 * b[2] * zd * zdd + b[1] * zddd);
+                    acc_z += g1 * b[2] * zd + g2 * (b[3] * zd * zd + b[2] * zdd)
+                           + g3 * (b[4] * zd * zd * zd + 3.0 * b[3] * zd * zdd + b[2] * zddd);
+                    gdz[j * D + d] += w * (g1 * b[1] + g2 * 2.0 * b[2] * zd
+                                           + g3 * (3.0 * b[3] * zd * zd + 3.0 * b[2] * zdd));
+                    gd2z[j * D + d] += w * (g2 * b[1] + g3 * 3.0 * b[2] * zd);
+                    gd3z[j * D + d] += w * g3 * b[1];
                 }
                 dWl[wi] += gW;
                 gz[j] += w * acc_z;
@@ -523,34 +562,36 @@ int orc_backward(int n_widths, const int* widths, int G, int k, int m, double lo
     if (tape_alloc(&t, &net, D)) return -1;
     int w = t.stride;
     double *g = calloc(w, sizeof(double)), *gd = calloc((size_t)w * D, sizeof(double)),
-           *gd2 = calloc((size_t)w * D, sizeof(double));
+           *gd2 = calloc((size_t)w * D, sizeof(double)), *gd3 = calloc((size_t)w * D, sizeof(double));
     double *h = calloc(w, sizeof(double)), *hd = calloc((size_t)w * D, sizeof(double)),
-           *hd2 = calloc((size_t)w * D, sizeof(double));
+           *hd2 = calloc((size_t)w * D, sizeof(double)), *hd3 = calloc((size_t)w * D, sizeof(double));
     double xp[8];
     for (long p = 0; p < N; ++p) {
         for (int d = 0; d < D; ++d) xp[d] = x[(long)d * N + p];
         point_forward(&net, W, D, s, e, xp, &t, 0u, ORC_EXACT);
         g[0] = 0.0;
-        for (int d = 0; d < D; ++d) gd[d] = gd2[d] = 0.0;
+        for (int d = 0; d < D; ++d) gd[d] = gd2[d] = gd3[d] = 0.0;
         for (int r = 0; r < J; ++r) {
             int b = rows[r];
             double v = dL_djets[(long)r * N + p];
             if (b == 0) g[0] = v;
             else if (b <= D) gd[b - 1] = v;
-            else gd2[b - 1 - D] = v;
+            else if (b <= 2 * D) gd2[b - 1 - D] = v;
+            else gd3[b - 1 - 2 * D] = v;
         }
         for (int l = L - 1; l >= 0; --l) {
             long off = layer_offset(&net, l);
             layer_backward(&net, l, W + off, dW + off, D, s, e, t.z + (long)l * w,
-                           t.dz + (long)l * w * D, t.d2z + (long)l * w * D, g, gd, gd2, h, hd,
-                           hd2);
+                           t.dz + (long)l * w * D, t.d2z + (long)l * w * D, t.d3z + (long)l * w * D,
+                           g, gd, gd2, gd3, h, hd, hd2, hd3);
             int I = widths[l];
             memcpy(g, h, sizeof(double) * I);
             memcpy(gd, hd, sizeof(double) * I * D);
             memcpy(gd2, hd2, sizeof(double) * I * D);
+            memcpy(gd3, hd3, sizeof(double) * I * D);
         }
     }
-    free(g); free(gd); free(gd2); free(h); free(hd); free(hd2);
+    free(g); free(gd); free(gd2); free(gd3); free(h); free(hd); free(hd2); free(hd3);
     tape_free(&t);
     free(s); free(e);
     return 0;

@@ -44,7 +44,7 @@ def test_basis_golden_values_m4():
     """Section 3, Eq. 2: hand-derived exact values of v_{4,4} and derivatives."""
     gold = np.loadtxt(os.path.join(GOLD, "hr_basis_m4.txt"))
     for row in gold:
-        got = oracle.hr_basis(4, -0.6, 1.0, row[0])
+        got = oracle.hr_basis(4, -0.6, 1.0, row[0])[:4]
         np.testing.assert_allclose(got, row[1:], rtol=1e-13, atol=1e-12)
 
 
@@ -64,7 +64,7 @@ def test_basis_matches_polynomial_expansion(m):
     c = (2.0 / (e - s)) ** (2 * m)
     p = np.polynomial.Polynomial([-e * s, e + s, -1.0])  # (e-x)(x-s)
     P = c * p ** m
-    ders = [P, P.deriv(1), P.deriv(2), P.deriv(3)]
+    ders = [P, P.deriv(1), P.deriv(2), P.deriv(3), P.deriv(4)]
     # the monomial expansion cancels near the knots: compare on each derivative's own scale
     scale = np.array([np.abs(d(np.linspace(s, e, 401))).max() for d in ders])
     for x in np.random.default_rng(m).uniform(s + 1e-3, e - 1e-3, 40):
@@ -99,12 +99,13 @@ def test_basis_symmetry_and_smoothness_at_knots():
     for x in np.random.default_rng(1).uniform(s, e, 30):
         a = oracle.hr_basis(m, s, e, x)
         b = oracle.hr_basis(m, s, e, s + e - x)
-        np.testing.assert_allclose(a * np.array([1, -1, 1, -1]), b, rtol=1e-10, atol=1e-10)
+        np.testing.assert_allclose(a * np.array([1, -1, 1, -1, 1]), b, rtol=1e-10, atol=1e-10)
     # the r-th derivative vanishes like delta^{m-r} next to each knot
     for knot, sign in ((s, 1.0), (e, -1.0)):
         a = np.abs(oracle.hr_basis(m, s, e, knot + sign * 1e-6))
         b = np.abs(oracle.hr_basis(m, s, e, knot + sign * 1e-7))
-        np.testing.assert_allclose(a / b, [1e4, 1e3, 1e2, 1e1], rtol=1e-4)
+        # (the fourth derivative tends to a nonzero constant: m - 4 = 0)
+        np.testing.assert_allclose(a / b, [1e4, 1e3, 1e2, 1e1, 1.0], rtol=1e-4)
 
 
 def test_m2_second_derivative_jumps_at_support_end():
@@ -200,6 +201,67 @@ def test_forward_jets_match_central_differences(widths, G):
         fd2 = (u(x + h2 * e) - 2 * u(x) + u(x - h2 * e)) / h2 ** 2
         np.testing.assert_allclose(jets[1 + d], fd1, rtol=1e-6, atol=1e-7)
         np.testing.assert_allclose(jets[3 + d], fd2, rtol=1e-4, atol=1e-4 * np.abs(fd2).max())
+
+
+@pytest.mark.parametrize("m", [3, 6])
+def test_third_order_jets_match_symbolic_differentiation(m):
+    """Third derivatives (mask bits 5, 6) of a [2,2,1] net vs sympy on the polynomial pieces."""
+    sp = pytest.importorskip("sympy")
+    net = dict(widths=[2, 2, 1], G=5, k=3, m=m, lo=-1.0, hi=1.0)
+    W = np.random.default_rng(30 + m).normal(0, 0.5, oracle.param_count(net))
+    x = np.random.default_rng(31).uniform(-1, 1, (2, 3))
+    jets = oracle.forward(net, W, x, 0x7F)
+    for p in range(3):
+        X, u = _sympy_network_at(net["widths"], 5, 3, m, -1.0, 1.0, W, x[:, p])
+        exprs = [u, sp.diff(u, X[0]), sp.diff(u, X[1]), sp.diff(u, X[0], 2), sp.diff(u, X[1], 2),
+                 sp.diff(u, X[0], 3), sp.diff(u, X[1], 3)]
+        sub = {X[0]: x[0, p], X[1]: x[1, p]}
+        want = np.array([float(e.evalf(subs=sub)) for e in exprs])
+        # sympy evaluates the expanded degree-2m(m+1) pieces in floating point: ~1e-9 cancellation
+        np.testing.assert_allclose(jets[:, p], want, rtol=1e-8, atol=1e-8)
+
+
+def test_third_order_jets_match_central_differences():
+    """u_ddd equals central differences of the oracle's own u_dd (a check independent of sympy)."""
+    net = dict(widths=[2, 4, 3, 1], G=6, k=3, m=4, lo=-1.0, hi=1.0)
+    W = np.random.default_rng(32).normal(0, 0.3, oracle.param_count(net))
+    x = np.random.default_rng(33).uniform(-0.9, 0.9, (2, 16))
+    jets = oracle.forward(net, W, x, 0x7F)
+    for d in range(2):
+        e = np.zeros((2, 1)); e[d] = 1.0
+        h = 1e-5
+        udd = lambda xx: oracle.forward(net, W, xx, 0x1F)[3 + d]
+        fd = (udd(x + h * e) - udd(x - h * e)) / (2 * h)
+        np.testing.assert_allclose(jets[5 + d], fd, rtol=1e-5, atol=1e-6 * np.abs(fd).max())
+
+
+@pytest.mark.parametrize("m", [4, 6])
+def test_third_order_weight_gradient_matches_central_differences(m):
+    """Backward through the third-derivative rows (which needs the basis's fourth derivative) vs central FD of
+    L(W) = sum(R * jets) over all seven rows, on 48 random weights."""
+    net = dict(widths=[2, 3, 3, 1], G=5, k=3, m=m, lo=-1.0, hi=1.0)
+    rng = np.random.default_rng(34 + m)
+    W = rng.normal(0, 0.4, oracle.param_count(net))
+    x = rng.uniform(-1, 1, (2, 25))
+    R = rng.normal(0, 1, (7, 25))
+    dW = oracle.backward(net, W, x, 0x7F, R)
+    loss = lambda Wv: float((R * oracle.forward(net, Wv, x, 0x7F)).sum())
+    h = 1e-6
+    for i in rng.choice(W.size, 48, replace=False):
+        Wp, Wm = W.copy(), W.copy()
+        Wp[i] += h; Wm[i] -= h
+        fd = (loss(Wp) - loss(Wm)) / (2 * h)
+        assert dW[i] == pytest.approx(fd, rel=2e-5, abs=2e-8 * max(1.0, np.abs(dW).max()))
+
+
+def test_third_order_rows_leave_lower_rows_unchanged():
+    """Adding bits 5, 6 to a mask appends rows; the value, first and second rows are unchanged."""
+    net = dict(widths=[2, 3, 1], G=5, k=3, m=4, lo=-1.0, hi=1.0)
+    W = np.random.default_rng(36).normal(0, 0.3, oracle.param_count(net))
+    x = np.random.default_rng(37).uniform(-1, 1, (2, 9))
+    full = oracle.forward(net, W, x, 0x7F)
+    np.testing.assert_array_equal(oracle.forward(net, W, x, 0x1F), full[:5])
+    np.testing.assert_array_equal(oracle.forward(net, W, x, 0x2F), full[[0, 1, 2, 3, 5]])
 
 
 def test_mask_selects_rows_in_bit_order():
@@ -462,19 +524,21 @@ def test_layer_forward_composes_to_the_network_forward():
     np.testing.assert_allclose(z[:, 0, :], oracle.forward(net, W, x, 0x1F), rtol=1e-12, atol=1e-12)
 
 
-def test_layer_dw_matches_central_differences():
+@pytest.mark.parametrize("mask", [0x1F, 0x7F])
+def test_layer_dw_matches_central_differences(mask):
     """layer_dw is the gradient of sum(gy * layer_forward) w.r.t. the layer weights: the
     layer output is linear in W, so central differences are exact up to rounding."""
     I, O, G, N = 3, 4, 5, 7
     n = G + 3
+    J = oracle.n_rows(mask)
     rng = np.random.default_rng(70)
-    z = rng.normal(0, 0.5, (5, I, N))
-    gy = rng.normal(0, 1, (5, O, N))
+    z = rng.normal(0, 0.5, (J, I, N))
+    gy = rng.normal(0, 1, (J, O, N))
     W = rng.normal(0, 0.3, O * I * n)
-    dw = oracle.layer_dw(I, O, G, 3, 4, -1.0, 1.0, z, gy, 0x1F)
+    dw = oracle.layer_dw(I, O, G, 3, 4, -1.0, 1.0, z, gy, mask)
 
     def f(Wv):
-        return float((gy * oracle.layer_forward(I, O, G, 3, 4, -1.0, 1.0, Wv, z, 0x1F)).sum())
+        return float((gy * oracle.layer_forward(I, O, G, 3, 4, -1.0, 1.0, Wv, z, mask)).sum())
 
     h = 1e-3
     for i in rng.choice(W.size, 24, replace=False):
@@ -523,7 +587,7 @@ def test_layer_dw_rounding_is_a_no_op_on_representable_inputs():
                               oracle.layer_dw(I, O, G, 3, 4, lo, hi, z, gy2, 0x1F))
 
 
-@pytest.mark.parametrize("mask", [0x01, 0x0F, 0x1F])
+@pytest.mark.parametrize("mask", [0x01, 0x0F, 0x1F, 0x2F, 0x7F])
 def test_layer_adjoint_matches_central_differences(mask):
     """layer_adjoint is the gradient of sum(gy * layer_forward(z)) w.r.t. the input jets z."""
     I, O, G, N = 3, 4, 5, 6
