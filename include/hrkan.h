@@ -26,10 +26,14 @@
  *   no basis (all contributions are exactly zero).
  * - Coordinates x are structure-of-arrays float32 [D][N] (x[d*N + p]).
  * - Jet rows: bit 0 of a jet mask selects u, bit 1+d selects du/dx_d, bit 1+D+d
- *   selects d2u/dx_d^2 (D = 2: 0x1F = u,u_x,u_y,u_xx,u_yy; 0x0F = u,u_x,u_t,u_xx
- *   with coordinates (x, t)).  A second-order bit requires the first-order bit
- *   of the same dimension.  Jet arrays are float32 [J][N], rows in bit order,
- *   J = popcount(mask).
+ *   selects d2u/dx_d^2, bit 1+2D+d selects d3u/dx_d^3 (D = 2: 0x1F =
+ *   u,u_x,u_y,u_xx,u_yy; 0x0F = u,u_x,u_t,u_xx with coordinates (x, t); 0x2F =
+ *   u,u_x,u_t,u_xx,u_xxx; 0x7F = all seven).  A derivative bit requires the
+ *   bit one order lower of the same dimension.  Third-derivative rows run on
+ *   the layer-wise path in FP32 (masks 0x2F and 0x7F; the fused narrow kernels
+ *   and the tensor-core kernels take 0x01, 0x0F, 0x1F and return
+ *   HRKAN_EUNSUPPORTED, or fall back to the FP32 layer kernels, otherwise).
+ *   Jet arrays are float32 [J][N], rows in bit order, J = popcount(mask).
  * - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
  *   default stream).  Argument errors are detected before anything is
  *   enqueued and return HRKAN_EINVAL (or HRKAN_EUNSUPPORTED for valid but
@@ -171,7 +175,8 @@ int hrkan_layer_dw(hrkan_t h, int layer, const float* z, const float* gy, int64_
 
 /*
  * Input adjoint of one layer l >= 1 (reverse mode of hrkan_layer_jets w.r.t.
- * its input jets, through the third basis derivative of Eq. 2):
+ * its input jets, through the third basis derivative of Eq. 2, the fourth for
+ * third-derivative rows):
  * gz = d/dz of sum_{r,o,p} gy[r][o][p] * y_r[o][p] for W = that layer's
  * weights [O][I][n] (a pointer into the network's W), z = input jets
  * [J][I][N], gy [J][O][N], gz [J][I][N] (written).  Runs the kernel the

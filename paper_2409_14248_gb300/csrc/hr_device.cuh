@@ -32,6 +32,7 @@ struct Grid {
 //   v'   = -2M u Q^{M-1} / a
 //   v''  = (-2M Q^{M-1} + 4M(M-1) u^2 Q^{M-2}) / a^2
 //   v''' = (12M(M-1) u Q^{M-2} - 8M(M-1)(M-2) u^3 Q^{M-3}) / a^3
+//   v''''= (12M(M-1) Q^{M-2} - 48M(M-1)(M-2) u^2 Q^{M-3} + 16M(M-1)(M-2)(M-3) u^4 Q^{M-4}) / a^4
 // A basis index outside [0, n) gets all-zero values and a clamped index.
 template <int K, int M, int NDER>
 struct Active {
@@ -40,6 +41,7 @@ struct Active {
     float d1[K + 1];     // v'
     float d2[K + 1];     // v''
     float d3[K + 1];     // v''' (only when NDER >= 3)
+    float d4[K + 1];     // v'''' (only when NDER >= 4)
 
     __device__ __forceinline__ int idx(int q, int n) const {
         int i = c + q;
@@ -77,25 +79,45 @@ struct Active {
                 if constexpr (M >= 3) t3 -= (8.0f * M * (M - 1) * (M - 2)) * u2 * u * Qm3;
                 d3[q] = ok ? t3 * (a1 * a1 * a1) : 0.0f;
             }
+            if constexpr (NDER >= 4) {
+                float t4 = (12.0f * M * (M - 1)) * Qm2;
+                if constexpr (M >= 3) t4 -= (48.0f * M * (M - 1) * (M - 2)) * u2 * Qm3;
+                if constexpr (M >= 4) {
+                    float Qm4 = 1.0f;
+#pragma unroll
+                    for (int e = 0; e < M - 4; ++e) Qm4 *= Q;
+                    t4 += (16.0f * M * (M - 1) * (M - 2) * (M - 3)) * u2 * u2 * Qm4;
+                }
+                d4[q] = ok ? t4 * ((a1 * a1) * (a1 * a1)) : 0.0f;
+            }
         }
     }
 };
 
 // Jet-row structure selected by a mask over D = 2 input dimensions:
 // bit 0 = value, bit 1+d = first derivative along d, bit 3+d = second
-// derivative along d (which needs the first along d).  Rows are in bit order.
+// derivative along d (which needs the first along d), bit 5+d = third
+// derivative along d (which needs the first and second).  Rows are in bit order.
 template <unsigned MASK>
 struct Jet {
     static constexpr bool F0 = (MASK >> 1) & 1, F1 = (MASK >> 2) & 1;
     static constexpr bool S0 = (MASK >> 3) & 1, S1 = (MASK >> 4) & 1;
+    static constexpr bool T0 = (MASK >> 5) & 1, T1 = (MASK >> 6) & 1;
     static_assert(MASK & 1, "the value row is always present");
     static_assert(!S0 || F0, "u_x0x0 needs u_x0");
     static_assert(!S1 || F1, "u_x1x1 needs u_x1");
+    static_assert(!T0 || S0, "u_x0x0x0 needs u_x0x0");
+    static_assert(!T1 || S1, "u_x1x1x1 needs u_x1x1");
     static constexpr int NF = int(F0) + int(F1);
     static constexpr int NS = int(S0) + int(S1);
-    static constexpr int J = 1 + NF + NS;
+    static constexpr int NT = int(T0) + int(T1);
+    static constexpr int J = 1 + NF + NS + NT;
     static constexpr int RF0 = 1, RF1 = 1 + int(F0);
     static constexpr int RS0 = 1 + NF, RS1 = 1 + NF + int(S0);
+    static constexpr int RT0 = 1 + NF + NS, RT1 = 1 + NF + NS + int(T0);
+    // basis derivatives the rows need, and their reverse (one more)
+    static constexpr int NDER_ROWS = NT ? 3 : 2;
+    static constexpr int NDER_ADJ = NT ? 4 : 3;
 
     // Rows of the basis matrix A for one input unit with jets z[J] and the
     // active basis values (v, v', v'') of its value z[0]:
@@ -105,6 +127,7 @@ struct Jet {
     template <int KP>
     __device__ __forceinline__ static void rows(const float* z, const float* v, const float* d1,
                                                 const float* d2, float (*a)[KP]) {
+        static_assert(NT == 0, "third-derivative rows: use rows_b");
 #pragma unroll
         for (int q = 0; q < KP; ++q) {
             a[0][q] = v[q];
@@ -125,6 +148,7 @@ struct Jet {
     __device__ __forceinline__ static void rows_adjoint(const float* z, const float* d1,
                                                         const float* d2, const float* d3,
                                                         const float (*dA)[KP], float* gz) {
+        static_assert(NT == 0, "third-derivative rows: use adjoint_b");
 #pragma unroll
         for (int r = 0; r < J; ++r) gz[r] = 0.0f;
 #pragma unroll
@@ -150,6 +174,90 @@ struct Jet {
             }
             gz[0] += g0;
         }
+    }
+
+    // rows() plus the third-derivative rows (needs v'''):
+    //   ddd-row    v''' z_d^3 + 3 v'' z_d z_dd + v' z_ddd
+    template <int KP>
+    __device__ __forceinline__ static void rows3(const float* z, const float* v, const float* d1,
+                                                 const float* d2, const float* d3, float (*a)[KP]) {
+#pragma unroll
+        for (int q = 0; q < KP; ++q) {
+            a[0][q] = v[q];
+            if constexpr (F0) a[RF0][q] = d1[q] * z[RF0];
+            if constexpr (F1) a[RF1][q] = d1[q] * z[RF1];
+            if constexpr (S0) a[RS0][q] = fmaf(d2[q] * z[RF0], z[RF0], d1[q] * z[RS0]);
+            if constexpr (S1) a[RS1][q] = fmaf(d2[q] * z[RF1], z[RF1], d1[q] * z[RS1]);
+            if constexpr (T0)
+                a[RT0][q] = fmaf(d3[q] * z[RF0] * z[RF0], z[RF0],
+                                 fmaf(3.0f * d2[q] * z[RF0], z[RS0], d1[q] * z[RT0]));
+            if constexpr (T1)
+                a[RT1][q] = fmaf(d3[q] * z[RF1] * z[RF1], z[RF1],
+                                 fmaf(3.0f * d2[q] * z[RF1], z[RS1], d1[q] * z[RT1]));
+        }
+    }
+
+    // rows_adjoint() plus the reverse of the third-derivative rows (needs v''''):
+    //   dz      += dAddd (v'''' z_d^3 + 3 v''' z_d z_dd + v'' z_ddd)
+    //   dz_d    += dAddd (3 v''' z_d^2 + 3 v'' z_dd)
+    //   dz_dd   += dAddd 3 v'' z_d
+    //   dz_ddd  += dAddd v'
+    template <int KP>
+    __device__ __forceinline__ static void rows_adjoint3(const float* z, const float* d1, const float* d2,
+                                                         const float* d3, const float* d4,
+                                                         const float (*dA)[KP], float* gz) {
+#pragma unroll
+        for (int r = 0; r < J; ++r) gz[r] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < KP; ++q) {
+            float g0 = dA[0][q] * d1[q];
+            if constexpr (F0) {
+                g0 = fmaf(dA[RF0][q] * d2[q], z[RF0], g0);
+                gz[RF0] = fmaf(dA[RF0][q], d1[q], gz[RF0]);
+            }
+            if constexpr (F1) {
+                g0 = fmaf(dA[RF1][q] * d2[q], z[RF1], g0);
+                gz[RF1] = fmaf(dA[RF1][q], d1[q], gz[RF1]);
+            }
+            if constexpr (S0) {
+                g0 = fmaf(dA[RS0][q], fmaf(d3[q] * z[RF0], z[RF0], d2[q] * z[RS0]), g0);
+                gz[RF0] = fmaf(dA[RS0][q] * 2.0f * d2[q], z[RF0], gz[RF0]);
+                gz[RS0] = fmaf(dA[RS0][q], d1[q], gz[RS0]);
+            }
+            if constexpr (S1) {
+                g0 = fmaf(dA[RS1][q], fmaf(d3[q] * z[RF1], z[RF1], d2[q] * z[RS1]), g0);
+                gz[RF1] = fmaf(dA[RS1][q] * 2.0f * d2[q], z[RF1], gz[RF1]);
+                gz[RS1] = fmaf(dA[RS1][q], d1[q], gz[RS1]);
+            }
+            if constexpr (T0) {
+                const float g = dA[RT0][q], zd = z[RF0], zdd = z[RS0], zddd = z[RT0];
+                g0 = fmaf(g, fmaf(d4[q] * zd * zd, zd, fmaf(3.0f * d3[q] * zd, zdd, d2[q] * zddd)), g0);
+                gz[RF0] = fmaf(g, fmaf(3.0f * d3[q] * zd, zd, 3.0f * d2[q] * zdd), gz[RF0]);
+                gz[RS0] = fmaf(g * 3.0f * d2[q], zd, gz[RS0]);
+                gz[RT0] = fmaf(g, d1[q], gz[RT0]);
+            }
+            if constexpr (T1) {
+                const float g = dA[RT1][q], zd = z[RF1], zdd = z[RS1], zddd = z[RT1];
+                g0 = fmaf(g, fmaf(d4[q] * zd * zd, zd, fmaf(3.0f * d3[q] * zd, zdd, d2[q] * zddd)), g0);
+                gz[RF1] = fmaf(g, fmaf(3.0f * d3[q] * zd, zd, 3.0f * d2[q] * zdd), gz[RF1]);
+                gz[RS1] = fmaf(g * 3.0f * d2[q], zd, gz[RS1]);
+                gz[RT1] = fmaf(g, d1[q], gz[RT1]);
+            }
+            gz[0] += g0;
+        }
+    }
+
+    // The rows / their reverse for a basis evaluation b (Active<K, M, NDER_ROWS> /
+    // Active<K, M, NDER_ADJ>): the PDE masks keep the second-order formulas.
+    template <int KP, class B>
+    __device__ __forceinline__ static void rows_b(const float* z, const B& b, float (*a)[KP]) {
+        if constexpr (NT == 0) rows<KP>(z, b.v, b.d1, b.d2, a);
+        else rows3<KP>(z, b.v, b.d1, b.d2, b.d3, a);
+    }
+    template <int KP, class B>
+    __device__ __forceinline__ static void adjoint_b(const float* z, const B& b, const float (*dA)[KP], float* gz) {
+        if constexpr (NT == 0) rows_adjoint<KP>(z, b.d1, b.d2, b.d3, dA, gz);
+        else rows_adjoint3<KP>(z, b.d1, b.d2, b.d3, b.d4, dA, gz);
     }
 };
 

@@ -1,6 +1,8 @@
 // Layer-wise kernels for wide HRKANs (hidden widths up to 64, any number of
 // layers): the KAN layer of Sections 1-3 with Eq. 2 bases, its input-jet
-// forward, the input adjoint through v''' and the weight gradient.
+// forward, the input adjoint through v''' (v'''' for third-derivative rows) and
+// the weight gradient.  Jet masks: 0x01, 0x0F, 0x1F (the PDE rows) and 0x2F, 0x7F
+// (with third derivatives).
 //
 // Jets live in HBM between layers as [J][units][N] float32 (one row per jet
 // component and unit, points contiguous), so every per-point access of a warp
@@ -36,6 +38,8 @@ __device__ __forceinline__ void load_unit_jets(const float* __restrict__ z, int 
         if constexpr (JT::F1) zj[JT::RF1] = (j == 1) ? 1.0f : 0.0f;
         if constexpr (JT::S0) zj[JT::RS0] = 0.0f;
         if constexpr (JT::S1) zj[JT::RS1] = 0.0f;
+        if constexpr (JT::T0) zj[JT::RT0] = 0.0f;
+        if constexpr (JT::T1) zj[JT::RT1] = 0.0f;
     } else {
 #pragma unroll
         for (int r = 0; r < JT::J; ++r) zj[r] = z[(int64_t(r) * I + j) * N + p];
@@ -69,10 +73,10 @@ __global__ void __launch_bounds__(WB) wide_fwd_kernel(WideLayer p) {
     for (int j = 0; j < I; ++j) {
         float z[J];
         load_unit_jets<MASK, FIRST>(p.z, I, j, N, pt, z);
-        Active<KW, MW, 2> b;
+        Active<KW, MW, JT::NDER_ROWS> b;
         b.eval(z[0], p.g);
         float a[J][KPW];
-        JT::template rows<KPW>(z, b.v, b.d1, b.d2, a);
+        JT::template rows_b<KPW>(z, b, a);
 #pragma unroll
         for (int q = 0; q < KPW; ++q) {
             const float* wr = wt + (j * n + b.idx(q, n)) * OT;
@@ -175,11 +179,11 @@ __global__ void __launch_bounds__(WB) wide_adjoint_kernel(WideLayer p) {
 #pragma unroll
     for (int jj = 0; jj < IT; ++jj) {
         if (j0 + jj >= I) break;
-        Active<KW, MW, 3> b;
+        Active<KW, MW, JT::NDER_ADJ> b;
         b.eval(z[jj][0], p.g);
         // bases that do not exist contribute nothing (their dA used a clamped weight)
         float gz[J];
-        JT::template rows_adjoint<KPW>(z[jj], b.d1, b.d2, b.d3, dA[jj], gz);
+        JT::template adjoint_b<KPW>(z[jj], b, dA[jj], gz);
 #pragma unroll
         for (int r = 0; r < J; ++r) p.gz[(int64_t(r) * I + j0 + jj) * N + pt] = gz[r];
     }
@@ -239,9 +243,9 @@ __global__ void __launch_bounds__(WB) wide_dw_kernel(WideDw p) {
             if (pt < N && jj < nj) {
                 float z[J];
                 load_unit_jets<MASK, FIRST>(p.z, I, j0 + jj, N, pt, z);
-                Active<KW, MW, 2> b;
+                Active<KW, MW, JT::NDER_ROWS> b;
                 b.eval(z[0], p.g);
-                JT::template rows<KPW>(z, b.v, b.d1, b.d2, a);
+                JT::template rows_b<KPW>(z, b, a);
                 c = b.c;
             } else {
 #pragma unroll
@@ -364,6 +368,8 @@ cudaError_t wide_forward_layer_m(const WideLayer& p, unsigned mask, bool first, 
         case 0x01u: return fwd_mask<MW, 0x01u>(p, first, s);
         case 0x0Fu: return fwd_mask<MW, 0x0Fu>(p, first, s);
         case 0x1Fu: return fwd_mask<MW, 0x1Fu>(p, first, s);
+        case 0x2Fu: return fwd_mask<MW, 0x2Fu>(p, first, s);
+        case 0x7Fu: return fwd_mask<MW, 0x7Fu>(p, first, s);
     }
     return cudaErrorNotSupported;
 }
@@ -375,6 +381,8 @@ cudaError_t wide_adjoint_layer_m(const WideLayer& p, unsigned mask, cudaStream_t
         case 0x01u: return adj_mask<MW, 0x01u>(p, s);
         case 0x0Fu: return adj_mask<MW, 0x0Fu>(p, s);
         case 0x1Fu: return adj_mask<MW, 0x1Fu>(p, s);
+        case 0x2Fu: return adj_mask<MW, 0x2Fu>(p, s);
+        case 0x7Fu: return adj_mask<MW, 0x7Fu>(p, s);
     }
     return cudaErrorNotSupported;
 }
@@ -385,6 +393,8 @@ cudaError_t wide_dw_layer_m(const WideDw& p, unsigned mask, bool first, cudaStre
         case 0x01u: return dw_mask<MW, 0x01u>(p, first, s);
         case 0x0Fu: return dw_mask<MW, 0x0Fu>(p, first, s);
         case 0x1Fu: return dw_mask<MW, 0x1Fu>(p, first, s);
+        case 0x2Fu: return dw_mask<MW, 0x2Fu>(p, first, s);
+        case 0x7Fu: return dw_mask<MW, 0x7Fu>(p, first, s);
     }
     return cudaErrorNotSupported;
 }
