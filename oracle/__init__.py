@@ -120,7 +120,7 @@ def param_count(net):
 
 
 def n_rows(mask, D=2):
-    return bin(int(mask) & ((1 << (1 + 3 * D)) - 1)).count("1")
+    return bin(int(mask) & ((1 << (1 + 3 * D + (1 if D == 2 else 0))) - 1)).count("1")
 
 
 def forward(net, W, x, mask):

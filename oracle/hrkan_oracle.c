@@ -23,7 +23,8 @@
  *   jets       the input derivatives the PDE residuals need (Eq. 3: Laplacian;
  *              Eq. 6-8: u_t, u_x, u_xx), and third derivatives along each input
  *              (the higher-order terms Section 3 motivates the order m with),
- *              by the forward-mode chain rule.
+ *              and for D = 2 the mixed derivative u_x0x1, by the forward-mode
+ *              chain rule.
  *   loss       Eq. 4 (Poisson) and Eq. 8 (Burgers): L = alpha L_pde + L_bnd,
  *              L_bnd the pooled mean over all boundary/initial points.
  *   backward   hand-written reverse mode of the above.
@@ -156,18 +157,22 @@ static int max_width(const orc_net* net)
 
 /*
  * One layer, one point, full jets over D input dims.
- * z[j], dz[j*D+d] = dz_j/dx_d, d2z[j*D+d] = d2z_j/dx_d^2, d3z = d3z_j/dx_d^3
- *   ->  y, dy, d2y, d3y, by the chain rule for y = sum W v(z):
- *   y_d = v' z_d,  y_dd = v'' z_d^2 + v' z_dd,  y_ddd = v''' z_d^3 + 3 v'' z_d z_dd + v' z_ddd.
+ * z[j], dz[j*D+d] = dz_j/dx_d, d2z[j*D+d] = d2z_j/dx_d^2, d3z = d3z_j/dx_d^3,
+ * mz[j] = d2z_j/dx_0dx_1 (D = 2)
+ *   ->  y, dy, d2y, d3y, my, by the chain rule for y = sum W v(z):
+ *   y_d = v' z_d,  y_dd = v'' z_d^2 + v' z_dd,  y_ddd = v''' z_d^3 + 3 v'' z_d z_dd + v' z_ddd,
+ *   y_01 = v'' z_0 z_1 + v' z_01.
  */
 static void layer_forward(const orc_net* net, int l, const double* Wl, int D,
                           const double* s, const double* e,
                           const double* z, const double* dz, const double* d2z, const double* d3z,
-                          double* y, double* dy, double* d2y, double* d3y, int fmt)
+                          const double* mz, double* y, double* dy, double* d2y, double* d3y, double* my,
+                          int fmt)
 {
     int I = net->widths[l], O = net->widths[l + 1], n = orc_nbasis(net);
     for (int o = 0; o < O; ++o) {
         y[o] = 0.0;
+        my[o] = 0.0;
         for (int d = 0; d < D; ++d) dy[o * D + d] = d2y[o * D + d] = d3y[o * D + d] = 0.0;
     }
     for (int j = 0; j < I; ++j) {
@@ -182,9 +187,11 @@ static void layer_forward(const orc_net* net, int l, const double* Wl, int D,
                 a2[d] = round_to(b[2] * zd * zd + b[1] * zdd, fmt);
                 a3[d] = round_to(b[3] * zd * zd * zd + 3.0 * b[2] * zd * zdd + b[1] * zddd, fmt);
             }
+            double am = D == 2 ? round_to(b[2] * dz[j * D] * dz[j * D + 1] + b[1] * mz[j], fmt) : 0.0;
             for (int o = 0; o < O; ++o) {
                 double w = round_to(Wl[((long)o * I + j) * n + i], fmt);
                 y[o] += w * a0;
+                my[o] += w * am;
                 for (int d = 0; d < D; ++d) {
                     dy[o * D + d] += w * a1[d];
                     d2y[o * D + d] += w * a2[d];
@@ -196,19 +203,19 @@ static void layer_forward(const orc_net* net, int l, const double* Wl, int D,
 }
 
 /* jet rows selected by mask: bit 0 = u, bit 1+d = du/dx_d, bit 1+D+d = d2u/dx_d^2,
- * bit 1+2D+d = d3u/dx_d^3 */
+ * bit 1+2D+d = d3u/dx_d^3, and for D = 2 bit 1+3D = 7 = d2u/dx_0dx_1 */
 static int mask_rows(unsigned mask, int D, int* bit_of_row)
 {
     int J = 0;
-    for (int b = 0; b < 1 + 3 * D; ++b)
+    for (int b = 0; b < 1 + 3 * D + (D == 2 ? 1 : 0); ++b)
         if (mask & (1u << b)) bit_of_row[J++] = b;
     return J;
 }
 
 /* Scratch holding the per-layer input jets of one point. */
 typedef struct {
-    double *z, *dz, *d2z, *d3z; /* [layer][maxw], [layer][maxw*D] */
-    int stride;                 /* maxw */
+    double *z, *dz, *d2z, *d3z, *mz; /* [layer][maxw], [layer][maxw*D], mixed [layer][maxw] */
+    int stride;                      /* maxw */
 } point_tape;
 
 static int tape_alloc(point_tape* t, const orc_net* net, int D)
@@ -219,12 +226,13 @@ static int tape_alloc(point_tape* t, const orc_net* net, int D)
     t->dz = calloc((size_t)(L + 1) * w * D, sizeof(double));
     t->d2z = calloc((size_t)(L + 1) * w * D, sizeof(double));
     t->d3z = calloc((size_t)(L + 1) * w * D, sizeof(double));
-    return (t->z && t->dz && t->d2z && t->d3z) ? 0 : -1;
+    t->mz = calloc((size_t)(L + 1) * w, sizeof(double));
+    return (t->z && t->dz && t->d2z && t->d3z && t->mz) ? 0 : -1;
 }
 
 static void tape_free(point_tape* t)
 {
-    free(t->z); free(t->dz); free(t->d2z); free(t->d3z);
+    free(t->z); free(t->dz); free(t->d2z); free(t->d3z); free(t->mz);
 }
 
 /* Forward of one point through all layers; layer l's input jets land in the tape row l,
@@ -240,13 +248,15 @@ static void point_forward(const orc_net* net, const double* W, int D, const doub
             t->d2z[j * D + d] = 0.0;
             t->d3z[j * D + d] = 0.0;
         }
+        t->mz[j] = 0.0;
     }
     for (int l = 0; l < L; ++l) {
         const double* Wl = W + layer_offset(net, l);
         layer_forward(net, l, Wl, D, s, e, t->z + (long)l * w, t->dz + (long)l * w * D,
-                      t->d2z + (long)l * w * D, t->d3z + (long)l * w * D, t->z + (long)(l + 1) * w,
-                      t->dz + (long)(l + 1) * w * D, t->d2z + (long)(l + 1) * w * D,
-                      t->d3z + (long)(l + 1) * w * D, ((round_layers >> l) & 1u) ? fmt : ORC_EXACT);
+                      t->d2z + (long)l * w * D, t->d3z + (long)l * w * D, t->mz + (long)l * w,
+                      t->z + (long)(l + 1) * w, t->dz + (long)(l + 1) * w * D, t->d2z + (long)(l + 1) * w * D,
+                      t->d3z + (long)(l + 1) * w * D, t->mz + (long)(l + 1) * w,
+                      ((round_layers >> l) & 1u) ? fmt : ORC_EXACT);
     }
 }
 
@@ -278,9 +288,11 @@ int orc_forward_rounded(int n_widths, const int* widths, int G, int k, int m, do
         const double* du = t.dz + (long)L * w * D;
         const double* d2u = t.d2z + (long)L * w * D;
         const double* d3u = t.d3z + (long)L * w * D;
+        const double* mu = t.mz + (long)L * w;
         for (int r = 0; r < J; ++r) {
             int b = rows[r];
-            double v = (b == 0) ? u[0] : (b <= D) ? du[b - 1] : (b <= 2 * D) ? d2u[b - 1 - D] : d3u[b - 1 - 2 * D];
+            double v = (b == 0) ? u[0] : (b <= D) ? du[b - 1] : (b <= 2 * D) ? d2u[b - 1 - D]
+                     : (b <= 3 * D) ? d3u[b - 1 - 2 * D] : mu[0];
             jets[(long)r * N + p] = v;
         }
     }
@@ -318,14 +330,17 @@ int orc_layer_forward(int I, int O, int G, int k, int m, double lo, double hi, c
     double* dz = calloc((size_t)I * D, sizeof(double));
     double* d2z = calloc((size_t)I * D, sizeof(double));
     double* d3z = calloc((size_t)I * D, sizeof(double));
+    double* mz = calloc((size_t)I, sizeof(double));
     double* y = malloc(sizeof(double) * O);
     double* dy = malloc(sizeof(double) * O * D);
     double* d2y = malloc(sizeof(double) * O * D);
     double* d3y = malloc(sizeof(double) * O * D);
+    double* my = malloc(sizeof(double) * O);
     orc_support(G, k, lo, hi, s, e);
     for (long p = 0; p < N; ++p) {
         for (int j = 0; j < I; ++j) {
             z[j] = 0.0;
+            mz[j] = 0.0;
             for (int d = 0; d < D; ++d) dz[j * D + d] = d2z[j * D + d] = d3z[j * D + d] = 0.0;
             for (int r = 0; r < J; ++r) {
                 double v = zin[((long)r * I + j) * N + p];
@@ -333,19 +348,21 @@ int orc_layer_forward(int I, int O, int G, int k, int m, double lo, double hi, c
                 if (b == 0) z[j] = v;
                 else if (b <= D) dz[j * D + b - 1] = v;
                 else if (b <= 2 * D) d2z[j * D + b - 1 - D] = v;
-                else d3z[j * D + b - 1 - 2 * D] = v;
+                else if (b <= 3 * D) d3z[j * D + b - 1 - 2 * D] = v;
+                else mz[j] = v;
             }
         }
-        layer_forward(&net, 0, Wl, D, s, e, z, dz, d2z, d3z, y, dy, d2y, d3y, fmt);
+        layer_forward(&net, 0, Wl, D, s, e, z, dz, d2z, d3z, mz, y, dy, d2y, d3y, my, fmt);
         for (int o = 0; o < O; ++o)
             for (int r = 0; r < J; ++r) {
                 int b = rows[r];
                 double v = (b == 0) ? y[o] : (b <= D) ? dy[o * D + b - 1]
-                         : (b <= 2 * D) ? d2y[o * D + b - 1 - D] : d3y[o * D + b - 1 - 2 * D];
+                         : (b <= 2 * D) ? d2y[o * D + b - 1 - D] : (b <= 3 * D) ? d3y[o * D + b - 1 - 2 * D] : my[o];
                 yout[((long)r * O + o) * N + p] = v;
             }
     }
-    free(s); free(e); free(z); free(dz); free(d2z); free(d3z); free(y); free(dy); free(d2y); free(d3y);
+    free(s); free(e); free(z); free(dz); free(d2z); free(d3z); free(mz); free(y); free(dy); free(d2y); free(d3y);
+    free(my);
     return 0;
 }
 
@@ -374,14 +391,15 @@ int orc_layer_dw(int I, int O, int G, int k, int m, double lo, double hi, const 
     double a[16];
     for (long p = 0; p < N; ++p) {
         for (int j = 0; j < I; ++j) {
-            double z = 0.0, dz[2] = {0.0, 0.0}, d2z[2] = {0.0, 0.0}, d3z[2] = {0.0, 0.0};
+            double z = 0.0, dz[2] = {0.0, 0.0}, d2z[2] = {0.0, 0.0}, d3z[2] = {0.0, 0.0}, mz = 0.0;
             for (int r = 0; r < J; ++r) {
                 double v = zin[((long)r * I + j) * N + p];
                 int b = rows[r];
                 if (b == 0) z = v;
                 else if (b <= D) dz[b - 1] = v;
                 else if (b <= 2 * D) d2z[b - 1 - D] = v;
-                else d3z[b - 1 - 2 * D] = v;
+                else if (b <= 3 * D) d3z[b - 1 - 2 * D] = v;
+                else mz = v;
             }
             for (int i = 0; i < n; ++i) {
                 double b[5];
@@ -396,9 +414,11 @@ int orc_layer_dw(int I, int O, int G, int k, int m, double lo, double hi, const 
                     } else if (bit <= 2 * D) {
                         int d = bit - 1 - D;
                         v = b[2] * dz[d] * dz[d] + b[1] * d2z[d];
-                    } else {
+                    } else if (bit <= 3 * D) {
                         int d = bit - 1 - 2 * D;
                         v = b[3] * dz[d] * dz[d] * dz[d] + 3.0 * b[2] * dz[d] * d2z[d] + b[1] * d3z[d];
+                    } else {
+                        v = b[2] * dz[0] * dz[1] + b[1] * mz;
                     }
                     a[r] = round_to(v, fmt);
                 }
@@ -428,6 +448,9 @@ int orc_layer_dw(int I, int O, int G, int k, int m, double lo, double hi, const 
  *                     d/dz += dA (v4 z_d^3 + 3 v3 z_d z_dd + v2 z_ddd),
  *                     d/dz_d += dA (3 v3 z_d^2 + 3 v2 z_dd),  d/dz_dd += dA 3 v2 z_d,
  *                     d/dz_ddd += dA v1
+ *   01-row (A = v2 z_0 z_1 + v1 z_01):
+ *                     d/dz += dA (v3 z_0 z_1 + v2 z_01),  d/dz_0 += dA v2 z_1,
+ *                     d/dz_1 += dA v2 z_0,  d/dz_01 += dA v1
  * fmt rounds gy and W before the FP64 sum over o (the reduced-precision
  * contraction's inputs); ORC_EXACT rounds nothing.  zin [J][I][N],
  * gy [J][O][N], gz [J][I][N] written.
@@ -445,16 +468,17 @@ int orc_layer_adjoint(int I, int O, int G, int k, int m, double lo, double hi, c
     orc_support(G, k, lo, hi, s, e);
     for (long p = 0; p < N; ++p) {
         for (int j = 0; j < I; ++j) {
-            double z = 0.0, dz[2] = {0.0, 0.0}, d2z[2] = {0.0, 0.0}, d3z[2] = {0.0, 0.0};
+            double z = 0.0, dz[2] = {0.0, 0.0}, d2z[2] = {0.0, 0.0}, d3z[2] = {0.0, 0.0}, mz = 0.0;
             for (int r = 0; r < J; ++r) {
                 double v = zin[((long)r * I + j) * N + p];
                 int b = rows[r];
                 if (b == 0) z = v;
                 else if (b <= D) dz[b - 1] = v;
                 else if (b <= 2 * D) d2z[b - 1 - D] = v;
-                else d3z[b - 1 - 2 * D] = v;
+                else if (b <= 3 * D) d3z[b - 1 - 2 * D] = v;
+                else mz = v;
             }
-            double g_z = 0.0, g_d[2] = {0.0, 0.0}, g_dd[2] = {0.0, 0.0}, g_ddd[2] = {0.0, 0.0};
+            double g_z = 0.0, g_d[2] = {0.0, 0.0}, g_dd[2] = {0.0, 0.0}, g_ddd[2] = {0.0, 0.0}, g_m = 0.0;
             for (int i = 0; i < n; ++i) {
                 double b[5];
                 orc_hr_basis(m, s[i], e[i], z, b);
@@ -475,19 +499,24 @@ int orc_layer_adjoint(int I, int O, int G, int k, int m, double lo, double hi, c
                         g_z += dA * (b[3] * dz[d] * dz[d] + b[2] * d2z[d]);
                         g_d[d] += dA * 2.0 * b[2] * dz[d];
                         g_dd[d] += dA * b[1];
-                    } else {
+                    } else if (bit <= 3 * D) {
                         int d = bit - 1 - 2 * D;
                         g_z += dA * (b[4] * dz[d] * dz[d] * dz[d] + 3.0 * b[3] * dz[d] * d2z[d] + b[2] * d3z[d]);
                         g_d[d] += dA * (3.0 * b[3] * dz[d] * dz[d] + 3.0 * b[2] * d2z[d]);
                         g_dd[d] += dA * 3.0 * b[2] * dz[d];
                         g_ddd[d] += dA * b[1];
+                    } else {
+                        g_z += dA * (b[3] * dz[0] * dz[1] + b[2] * mz);
+                        g_d[0] += dA * b[2] * dz[1];
+                        g_d[1] += dA * b[2] * dz[0];
+                        g_m += dA * b[1];
                     }
                 }
             }
             for (int r = 0; r < J; ++r) {
                 int bit = rows[r];
                 double v = (bit == 0) ? g_z : (bit <= D) ? g_d[bit - 1]
-                         : (bit <= 2 * D) ? g_dd[bit - 1 - D] : g_ddd[bit - 1 - 2 * D];
+                         : (bit <= 2 * D) ? g_dd[bit - 1 - D] : (bit <= 3 * D) ? g_ddd[bit - 1 - 2 * D] : g_m;
                 gz[((long)r * I + j) * N + p] = v;
             }
         }
@@ -502,13 +531,14 @@ int orc_layer_adjoint(int I, int O, int G, int k, int m, double lo, double hi, c
  */
 static void layer_backward(const orc_net* net, int l, const double* Wl, double* dWl, int D,
                            const double* s, const double* e, const double* z,
-                           const double* dz, const double* d2z, const double* d3z, const double* gy,
-                           const double* gdy, const double* gd2y, const double* gd3y, double* gz,
-                           double* gdz, double* gd2z, double* gd3z)
+                           const double* dz, const double* d2z, const double* d3z, const double* mz,
+                           const double* gy, const double* gdy, const double* gd2y, const double* gd3y,
+                           const double* gmy, double* gz, double* gdz, double* gd2z, double* gd3z, double* gmz)
 {
     int I = net->widths[l], O = net->widths[l + 1], n = orc_nbasis(net);
     for (int j = 0; j < I; ++j) {
         gz[j] = 0.0;
+        gmz[j] = 0.0;
         for (int d = 0; d < D; ++d) gdz[j * D + d] = gd2z[j * D + d] = gd3z[j * D + d] = 0.0;
     }
     for (int j = 0; j < I; ++j) {
@@ -531,6 +561,14 @@ static void layer_backward(const orc_net* net, int l, const double* Wl, double* 
                                            + g3 * (3.0 * b[3] * zd * zd + 3.0 * b[2] * zdd));
                     gd2z[j * D + d] += w * (g2 * b[1] + g3 * 3.0 * b[2] * zd);
                     gd3z[j * D + d] += w * g3 * b[1];
+                }
+                if (D == 2) {
+                    double z0 = dz[j * D], z1 = dz[j * D + 1], gm = gmy[o];
+                    gW += gm * (b[2] * z0 * z1 + b[1] * mz[j]);
+                    acc_z += gm * (b[3] * z0 * z1 + b[2] * mz[j]);
+                    gdz[j * D] += w * gm * b[2] * z1;
+                    gdz[j * D + 1] += w * gm * b[2] * z0;
+                    gmz[j] += w * gm * b[1];
                 }
                 dWl[wi] += gW;
                 gz[j] += w * acc_z;
@@ -562,14 +600,17 @@ int orc_backward(int n_widths, const int* widths, int G, int k, int m, double lo
     if (tape_alloc(&t, &net, D)) return -1;
     int w = t.stride;
     double *g = calloc(w, sizeof(double)), *gd = calloc((size_t)w * D, sizeof(double)),
-           *gd2 = calloc((size_t)w * D, sizeof(double)), *gd3 = calloc((size_t)w * D, sizeof(double));
+           *gd2 = calloc((size_t)w * D, sizeof(double)), *gd3 = calloc((size_t)w * D, sizeof(double)),
+           *gm = calloc(w, sizeof(double));
     double *h = calloc(w, sizeof(double)), *hd = calloc((size_t)w * D, sizeof(double)),
-           *hd2 = calloc((size_t)w * D, sizeof(double)), *hd3 = calloc((size_t)w * D, sizeof(double));
+           *hd2 = calloc((size_t)w * D, sizeof(double)), *hd3 = calloc((size_t)w * D, sizeof(double)),
+           *hm = calloc(w, sizeof(double));
     double xp[8];
     for (long p = 0; p < N; ++p) {
         for (int d = 0; d < D; ++d) xp[d] = x[(long)d * N + p];
         point_forward(&net, W, D, s, e, xp, &t, 0u, ORC_EXACT);
         g[0] = 0.0;
+        gm[0] = 0.0;
         for (int d = 0; d < D; ++d) gd[d] = gd2[d] = gd3[d] = 0.0;
         for (int r = 0; r < J; ++r) {
             int b = rows[r];
@@ -577,21 +618,23 @@ int orc_backward(int n_widths, const int* widths, int G, int k, int m, double lo
             if (b == 0) g[0] = v;
             else if (b <= D) gd[b - 1] = v;
             else if (b <= 2 * D) gd2[b - 1 - D] = v;
-            else gd3[b - 1 - 2 * D] = v;
+            else if (b <= 3 * D) gd3[b - 1 - 2 * D] = v;
+            else gm[0] = v;
         }
         for (int l = L - 1; l >= 0; --l) {
             long off = layer_offset(&net, l);
             layer_backward(&net, l, W + off, dW + off, D, s, e, t.z + (long)l * w,
                            t.dz + (long)l * w * D, t.d2z + (long)l * w * D, t.d3z + (long)l * w * D,
-                           g, gd, gd2, gd3, h, hd, hd2, hd3);
+                           t.mz + (long)l * w, g, gd, gd2, gd3, gm, h, hd, hd2, hd3, hm);
             int I = widths[l];
             memcpy(g, h, sizeof(double) * I);
+            memcpy(gm, hm, sizeof(double) * I);
             memcpy(gd, hd, sizeof(double) * I * D);
             memcpy(gd2, hd2, sizeof(double) * I * D);
             memcpy(gd3, hd3, sizeof(double) * I * D);
         }
     }
-    free(g); free(gd); free(gd2); free(gd3); free(h); free(hd); free(hd2); free(hd3);
+    free(g); free(gd); free(gd2); free(gd3); free(gm); free(h); free(hd); free(hd2); free(hd3); free(hm);
     tape_free(&t);
     free(s); free(e);
     return 0;

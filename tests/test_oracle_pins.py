@@ -205,16 +205,17 @@ def test_forward_jets_match_central_differences(widths, G):
 
 @pytest.mark.parametrize("m", [3, 6])
 def test_third_order_jets_match_symbolic_differentiation(m):
-    """Third derivatives (mask bits 5, 6) of a [2,2,1] net vs sympy on the polynomial pieces."""
+    """Third derivatives (mask bits 5, 6) and the mixed derivative (bit 7) of a [2,2,1] net
+    vs sympy on the polynomial pieces."""
     sp = pytest.importorskip("sympy")
     net = dict(widths=[2, 2, 1], G=5, k=3, m=m, lo=-1.0, hi=1.0)
     W = np.random.default_rng(30 + m).normal(0, 0.5, oracle.param_count(net))
     x = np.random.default_rng(31).uniform(-1, 1, (2, 3))
-    jets = oracle.forward(net, W, x, 0x7F)
+    jets = oracle.forward(net, W, x, 0xFF)
     for p in range(3):
         X, u = _sympy_network_at(net["widths"], 5, 3, m, -1.0, 1.0, W, x[:, p])
         exprs = [u, sp.diff(u, X[0]), sp.diff(u, X[1]), sp.diff(u, X[0], 2), sp.diff(u, X[1], 2),
-                 sp.diff(u, X[0], 3), sp.diff(u, X[1], 3)]
+                 sp.diff(u, X[0], 3), sp.diff(u, X[1], 3), sp.diff(u, X[0], X[1])]
         sub = {X[0]: x[0, p], X[1]: x[1, p]}
         want = np.array([float(e.evalf(subs=sub)) for e in exprs])
         # sympy evaluates the expanded degree-2m(m+1) pieces in floating point: ~1e-9 cancellation
@@ -222,30 +223,35 @@ def test_third_order_jets_match_symbolic_differentiation(m):
 
 
 def test_third_order_jets_match_central_differences():
-    """u_ddd equals central differences of the oracle's own u_dd (a check independent of sympy)."""
+    """u_ddd and u_01 equal central differences of the oracle's own u_dd and u_0 (a check
+    independent of sympy)."""
     net = dict(widths=[2, 4, 3, 1], G=6, k=3, m=4, lo=-1.0, hi=1.0)
     W = np.random.default_rng(32).normal(0, 0.3, oracle.param_count(net))
     x = np.random.default_rng(33).uniform(-0.9, 0.9, (2, 16))
-    jets = oracle.forward(net, W, x, 0x7F)
+    jets = oracle.forward(net, W, x, 0xFF)
+    h = 1e-5
     for d in range(2):
         e = np.zeros((2, 1)); e[d] = 1.0
-        h = 1e-5
         udd = lambda xx: oracle.forward(net, W, xx, 0x1F)[3 + d]
         fd = (udd(x + h * e) - udd(x - h * e)) / (2 * h)
         np.testing.assert_allclose(jets[5 + d], fd, rtol=1e-5, atol=1e-6 * np.abs(fd).max())
+    e1 = np.array([[0.0], [1.0]])
+    ux = lambda xx: oracle.forward(net, W, xx, 0x07)[1]
+    fd = (ux(x + h * e1) - ux(x - h * e1)) / (2 * h)
+    np.testing.assert_allclose(jets[7], fd, rtol=1e-5, atol=1e-6 * np.abs(fd).max())
 
 
 @pytest.mark.parametrize("m", [4, 6])
 def test_third_order_weight_gradient_matches_central_differences(m):
-    """Backward through the third-derivative rows (which needs the basis's fourth derivative) vs central FD of
-    L(W) = sum(R * jets) over all seven rows, on 48 random weights."""
+    """Backward through the third-derivative rows (which needs the basis's fourth derivative) and
+    the mixed row vs central FD of L(W) = sum(R * jets) over all eight rows, on 48 random weights."""
     net = dict(widths=[2, 3, 3, 1], G=5, k=3, m=m, lo=-1.0, hi=1.0)
     rng = np.random.default_rng(34 + m)
     W = rng.normal(0, 0.4, oracle.param_count(net))
     x = rng.uniform(-1, 1, (2, 25))
-    R = rng.normal(0, 1, (7, 25))
-    dW = oracle.backward(net, W, x, 0x7F, R)
-    loss = lambda Wv: float((R * oracle.forward(net, Wv, x, 0x7F)).sum())
+    R = rng.normal(0, 1, (8, 25))
+    dW = oracle.backward(net, W, x, 0xFF, R)
+    loss = lambda Wv: float((R * oracle.forward(net, Wv, x, 0xFF)).sum())
     h = 1e-6
     for i in rng.choice(W.size, 48, replace=False):
         Wp, Wm = W.copy(), W.copy()
@@ -262,6 +268,9 @@ def test_third_order_rows_leave_lower_rows_unchanged():
     full = oracle.forward(net, W, x, 0x7F)
     np.testing.assert_array_equal(oracle.forward(net, W, x, 0x1F), full[:5])
     np.testing.assert_array_equal(oracle.forward(net, W, x, 0x2F), full[[0, 1, 2, 3, 5]])
+    mixed = oracle.forward(net, W, x, 0xFF)
+    np.testing.assert_array_equal(mixed[:7], full)
+    np.testing.assert_array_equal(oracle.forward(net, W, x, 0x87), mixed[[0, 1, 2, 7]])
 
 
 def test_mask_selects_rows_in_bit_order():
@@ -524,7 +533,7 @@ def test_layer_forward_composes_to_the_network_forward():
     np.testing.assert_allclose(z[:, 0, :], oracle.forward(net, W, x, 0x1F), rtol=1e-12, atol=1e-12)
 
 
-@pytest.mark.parametrize("mask", [0x1F, 0x7F])
+@pytest.mark.parametrize("mask", [0x1F, 0x7F, 0xFF])
 def test_layer_dw_matches_central_differences(mask):
     """layer_dw is the gradient of sum(gy * layer_forward) w.r.t. the layer weights: the
     layer output is linear in W, so central differences are exact up to rounding."""
@@ -587,7 +596,7 @@ def test_layer_dw_rounding_is_a_no_op_on_representable_inputs():
                               oracle.layer_dw(I, O, G, 3, 4, lo, hi, z, gy2, 0x1F))
 
 
-@pytest.mark.parametrize("mask", [0x01, 0x0F, 0x1F, 0x2F, 0x7F])
+@pytest.mark.parametrize("mask", [0x01, 0x0F, 0x1F, 0x2F, 0x7F, 0x87, 0xFF])
 def test_layer_adjoint_matches_central_differences(mask):
     """layer_adjoint is the gradient of sum(gy * layer_forward(z)) w.r.t. the input jets z."""
     I, O, G, N = 3, 4, 5, 6
