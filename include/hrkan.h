@@ -26,13 +26,15 @@
  *   no basis (all contributions are exactly zero).
  * - Coordinates x are structure-of-arrays float32 [D][N] (x[d*N + p]).
  * - Jet rows: bit 0 of a jet mask selects u, bit 1+d selects du/dx_d, bit 1+D+d
- *   selects d2u/dx_d^2, bit 1+2D+d selects d3u/dx_d^3 (D = 2: 0x1F =
- *   u,u_x,u_y,u_xx,u_yy; 0x0F = u,u_x,u_t,u_xx with coordinates (x, t); 0x2F =
- *   u,u_x,u_t,u_xx,u_xxx; 0x7F = all seven).  A derivative bit requires the
- *   bit one order lower of the same dimension.  Third-derivative rows run on
- *   the layer-wise path in FP32 (masks 0x2F and 0x7F; the fused narrow kernels
- *   and the tensor-core kernels take 0x01, 0x0F, 0x1F and return
- *   HRKAN_EUNSUPPORTED, or fall back to the FP32 layer kernels, otherwise).
+ *   selects d2u/dx_d^2, bit 1+2D+d selects d3u/dx_d^3, bit 1+3D = 7 selects
+ *   the mixed d2u/dx_0dx_1 (D = 2: 0x1F = u,u_x,u_y,u_xx,u_yy; 0x0F =
+ *   u,u_x,u_t,u_xx with coordinates (x, t); 0x2F = u,u_x,u_t,u_xx,u_xxx; 0x87 =
+ *   u,u_x,u_y,u_xy; 0xFF = all eight).  A derivative bit requires the bit one
+ *   order lower of the same dimension (the mixed bit: both first-order bits).
+ *   Third-derivative and mixed rows run on the layer-wise path in FP32 (masks
+ *   0x2F, 0x7F, 0x87, 0xFF; the fused narrow kernels and the tensor-core
+ *   kernels take 0x01, 0x0F, 0x1F and return HRKAN_EUNSUPPORTED, or fall back
+ *   to the FP32 layer kernels, otherwise).
  *   Jet arrays are float32 [J][N], rows in bit order, J = popcount(mask).
  * - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
  *   default stream).  Argument errors are detected before anything is

@@ -115,11 +115,12 @@ int check_cfg(const hrkan_cfg* c) {
 }
 
 bool valid_mask(unsigned m) {
-    if (!(m & 1u) || (m & ~0x7Fu)) return false;
+    if (!(m & 1u) || (m & ~0xFFu)) return false;
     if ((m & 0x08u) && !(m & 0x02u)) return false;
     if ((m & 0x10u) && !(m & 0x04u)) return false;
     if ((m & 0x20u) && !(m & 0x08u)) return false;
     if ((m & 0x40u) && !(m & 0x10u)) return false;
+    if ((m & 0x80u) && (m & 0x06u) != 0x06u) return false;
     return true;
 }
 
@@ -297,7 +298,7 @@ float* ws_get(hrkan_t h, int slot, size_t floats, int* rc) {
     return w.first;
 }
 
-int jets_of(unsigned mask) { return __builtin_popcount(mask & 0x7Fu); }
+int jets_of(unsigned mask) { return __builtin_popcount(mask & 0xFFu); }
 
 // Offset (floats) of layer l's input jets (l >= 1) inside a tape for N points.
 int64_t tape_offset(hrkan_t h, int l, int64_t N, int J) {

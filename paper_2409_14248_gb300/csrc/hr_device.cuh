@@ -97,24 +97,30 @@ struct Active {
 // Jet-row structure selected by a mask over D = 2 input dimensions:
 // bit 0 = value, bit 1+d = first derivative along d, bit 3+d = second
 // derivative along d (which needs the first along d), bit 5+d = third
-// derivative along d (which needs the first and second).  Rows are in bit order.
+// derivative along d (which needs the first and second), bit 7 = the mixed
+// derivative u_x0x1 (which needs both first derivatives).  Rows are in bit order.
 template <unsigned MASK>
 struct Jet {
     static constexpr bool F0 = (MASK >> 1) & 1, F1 = (MASK >> 2) & 1;
     static constexpr bool S0 = (MASK >> 3) & 1, S1 = (MASK >> 4) & 1;
     static constexpr bool T0 = (MASK >> 5) & 1, T1 = (MASK >> 6) & 1;
+    static constexpr bool X01 = (MASK >> 7) & 1;
     static_assert(MASK & 1, "the value row is always present");
     static_assert(!S0 || F0, "u_x0x0 needs u_x0");
     static_assert(!S1 || F1, "u_x1x1 needs u_x1");
     static_assert(!T0 || S0, "u_x0x0x0 needs u_x0x0");
     static_assert(!T1 || S1, "u_x1x1x1 needs u_x1x1");
+    static_assert(!X01 || (F0 && F1), "u_x0x1 needs u_x0 and u_x1");
     static constexpr int NF = int(F0) + int(F1);
     static constexpr int NS = int(S0) + int(S1);
     static constexpr int NT = int(T0) + int(T1);
-    static constexpr int J = 1 + NF + NS + NT;
+    static constexpr int J = 1 + NF + NS + NT + int(X01);
     static constexpr int RF0 = 1, RF1 = 1 + int(F0);
     static constexpr int RS0 = 1 + NF, RS1 = 1 + NF + int(S0);
     static constexpr int RT0 = 1 + NF + NS, RT1 = 1 + NF + NS + int(T0);
+    static constexpr int RX = 1 + NF + NS + NT;
+    // rows beyond the PDE masks' value / first / second derivatives
+    static constexpr bool GENERAL = NT > 0 || X01;
     // basis derivatives the rows need, and their reverse (one more)
     static constexpr int NDER_ROWS = NT ? 3 : 2;
     static constexpr int NDER_ADJ = NT ? 4 : 3;
@@ -127,7 +133,7 @@ struct Jet {
     template <int KP>
     __device__ __forceinline__ static void rows(const float* z, const float* v, const float* d1,
                                                 const float* d2, float (*a)[KP]) {
-        static_assert(NT == 0, "third-derivative rows: use rows_b");
+        static_assert(!GENERAL, "third-derivative or mixed rows: use rows_b");
 #pragma unroll
         for (int q = 0; q < KP; ++q) {
             a[0][q] = v[q];
@@ -148,7 +154,7 @@ struct Jet {
     __device__ __forceinline__ static void rows_adjoint(const float* z, const float* d1,
                                                         const float* d2, const float* d3,
                                                         const float (*dA)[KP], float* gz) {
-        static_assert(NT == 0, "third-derivative rows: use adjoint_b");
+        static_assert(!GENERAL, "third-derivative or mixed rows: use adjoint_b");
 #pragma unroll
         for (int r = 0; r < J; ++r) gz[r] = 0.0f;
 #pragma unroll
@@ -176,8 +182,9 @@ struct Jet {
         }
     }
 
-    // rows() plus the third-derivative rows (needs v'''):
+    // rows() plus the third-derivative rows (needs v''') and the mixed row:
     //   ddd-row    v''' z_d^3 + 3 v'' z_d z_dd + v' z_ddd
+    //   01-row     v'' z_0 z_1 + v' z_01
     template <int KP>
     __device__ __forceinline__ static void rows3(const float* z, const float* v, const float* d1,
                                                  const float* d2, const float* d3, float (*a)[KP]) {
@@ -194,14 +201,17 @@ struct Jet {
             if constexpr (T1)
                 a[RT1][q] = fmaf(d3[q] * z[RF1] * z[RF1], z[RF1],
                                  fmaf(3.0f * d2[q] * z[RF1], z[RS1], d1[q] * z[RT1]));
+            if constexpr (X01) a[RX][q] = fmaf(d2[q] * z[RF0], z[RF1], d1[q] * z[RX]);
         }
     }
 
-    // rows_adjoint() plus the reverse of the third-derivative rows (needs v''''):
-    //   dz      += dAddd (v'''' z_d^3 + 3 v''' z_d z_dd + v'' z_ddd)
-    //   dz_d    += dAddd (3 v''' z_d^2 + 3 v'' z_dd)
+    // rows_adjoint() plus the reverse of the third-derivative rows (needs v'''')
+    // and of the mixed row:
+    //   dz      += dAddd (v'''' z_d^3 + 3 v''' z_d z_dd + v'' z_ddd) + dA01 (v''' z_0 z_1 + v'' z_01)
+    //   dz_d    += dAddd (3 v''' z_d^2 + 3 v'' z_dd) + dA01 v'' z_(1-d)
     //   dz_dd   += dAddd 3 v'' z_d
     //   dz_ddd  += dAddd v'
+    //   dz_01   += dA01 v'
     template <int KP>
     __device__ __forceinline__ static void rows_adjoint3(const float* z, const float* d1, const float* d2,
                                                          const float* d3, const float* d4,
@@ -243,6 +253,13 @@ struct Jet {
                 gz[RS1] = fmaf(g * 3.0f * d2[q], zd, gz[RS1]);
                 gz[RT1] = fmaf(g, d1[q], gz[RT1]);
             }
+            if constexpr (X01) {
+                const float g = dA[RX][q];
+                g0 = fmaf(g, fmaf(d3[q] * z[RF0], z[RF1], d2[q] * z[RX]), g0);
+                gz[RF0] = fmaf(g * d2[q], z[RF1], gz[RF0]);
+                gz[RF1] = fmaf(g * d2[q], z[RF0], gz[RF1]);
+                gz[RX] = fmaf(g, d1[q], gz[RX]);
+            }
             gz[0] += g0;
         }
     }
@@ -251,12 +268,12 @@ struct Jet {
     // Active<K, M, NDER_ADJ>): the PDE masks keep the second-order formulas.
     template <int KP, class B>
     __device__ __forceinline__ static void rows_b(const float* z, const B& b, float (*a)[KP]) {
-        if constexpr (NT == 0) rows<KP>(z, b.v, b.d1, b.d2, a);
+        if constexpr (!GENERAL) rows<KP>(z, b.v, b.d1, b.d2, a);
         else rows3<KP>(z, b.v, b.d1, b.d2, b.d3, a);
     }
     template <int KP, class B>
     __device__ __forceinline__ static void adjoint_b(const float* z, const B& b, const float (*dA)[KP], float* gz) {
-        if constexpr (NT == 0) rows_adjoint<KP>(z, b.d1, b.d2, b.d3, dA, gz);
+        if constexpr (!GENERAL) rows_adjoint<KP>(z, b.d1, b.d2, b.d3, dA, gz);
         else rows_adjoint3<KP>(z, b.d1, b.d2, b.d3, b.d4, dA, gz);
     }
 };

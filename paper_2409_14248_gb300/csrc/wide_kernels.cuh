@@ -1,8 +1,8 @@
 // Layer-wise kernels for wide HRKANs (hidden widths up to 64, any number of
 // layers): the KAN layer of Sections 1-3 with Eq. 2 bases, its input-jet
 // forward, the input adjoint through v''' (v'''' for third-derivative rows) and
-// the weight gradient.  Jet masks: 0x01, 0x0F, 0x1F (the PDE rows) and 0x2F, 0x7F
-// (with third derivatives).
+// the weight gradient.  Jet masks: 0x01, 0x0F, 0x1F (the PDE rows), 0x2F, 0x7F
+// (with third derivatives), 0x87, 0xFF (with the mixed derivative u_x0x1).
 //
 // Jets live in HBM between layers as [J][units][N] float32 (one row per jet
 // component and unit, points contiguous), so every per-point access of a warp
@@ -40,6 +40,7 @@ __device__ __forceinline__ void load_unit_jets(const float* __restrict__ z, int 
         if constexpr (JT::S1) zj[JT::RS1] = 0.0f;
         if constexpr (JT::T0) zj[JT::RT0] = 0.0f;
         if constexpr (JT::T1) zj[JT::RT1] = 0.0f;
+        if constexpr (JT::X01) zj[JT::RX] = 0.0f;
     } else {
 #pragma unroll
         for (int r = 0; r < JT::J; ++r) zj[r] = z[(int64_t(r) * I + j) * N + p];
@@ -370,6 +371,8 @@ cudaError_t wide_forward_layer_m(const WideLayer& p, unsigned mask, bool first, 
         case 0x1Fu: return fwd_mask<MW, 0x1Fu>(p, first, s);
         case 0x2Fu: return fwd_mask<MW, 0x2Fu>(p, first, s);
         case 0x7Fu: return fwd_mask<MW, 0x7Fu>(p, first, s);
+        case 0x87u: return fwd_mask<MW, 0x87u>(p, first, s);
+        case 0xFFu: return fwd_mask<MW, 0xFFu>(p, first, s);
     }
     return cudaErrorNotSupported;
 }
@@ -383,6 +386,8 @@ cudaError_t wide_adjoint_layer_m(const WideLayer& p, unsigned mask, cudaStream_t
         case 0x1Fu: return adj_mask<MW, 0x1Fu>(p, s);
         case 0x2Fu: return adj_mask<MW, 0x2Fu>(p, s);
         case 0x7Fu: return adj_mask<MW, 0x7Fu>(p, s);
+        case 0x87u: return adj_mask<MW, 0x87u>(p, s);
+        case 0xFFu: return adj_mask<MW, 0xFFu>(p, s);
     }
     return cudaErrorNotSupported;
 }
@@ -395,6 +400,8 @@ cudaError_t wide_dw_layer_m(const WideDw& p, unsigned mask, bool first, cudaStre
         case 0x1Fu: return dw_mask<MW, 0x1Fu>(p, first, s);
         case 0x2Fu: return dw_mask<MW, 0x2Fu>(p, first, s);
         case 0x7Fu: return dw_mask<MW, 0x7Fu>(p, first, s);
+        case 0x87u: return dw_mask<MW, 0x87u>(p, first, s);
+        case 0xFFu: return dw_mask<MW, 0xFFu>(p, first, s);
     }
     return cudaErrorNotSupported;
 }

@@ -1,6 +1,7 @@
-"""Third-derivative jet rows (mask bits 5, 6: u_x0x0x0, u_x1x1x1) on the
-layer-wise FP32 path vs the FP64 oracle: network forward and backward (stored
-and recomputed layer jets), the single-layer calls, a KdV-type residual built
+"""Third-derivative jet rows (mask bits 5, 6: u_x0x0x0, u_x1x1x1) and the mixed
+derivative (bit 7: u_x0x1) on the layer-wise FP32 path vs the FP64 oracle:
+network forward and backward (stored and recomputed layer jets), the
+single-layer calls, a KdV-type and an anisotropic second-order residual built
 in torch on top of the autograd wrapper, and the masks the other paths refuse.
 Shapes: Burgers [2,32,32,1] G=20 (m = 4) and a [2,24,24,1] G=12 net with m = 6
 (Section 3: a larger order for higher derivatives), points over several
@@ -18,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-MASKS = [0x2F, 0x7F]
+MASKS = [0x2F, 0x7F, 0x87, 0xFF]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -64,7 +65,7 @@ def test_third_order_forward_matches_oracle(name, mask):
 def test_third_order_backward_stored_and_recomputed_match_oracle(name):
     w = _workload(name)
     N = 777
-    mask = 0x7F
+    mask = 0xFF
     d = inputs.make(w, n_int=N, n_bnd=40, n_ic=20, n_bc=20)
     J = oracle.n_rows(mask)
     g = np.random.default_rng(95).standard_normal((J, N)).astype(np.float32)
@@ -86,11 +87,11 @@ def test_third_order_backward_stored_and_recomputed_match_oracle(name):
 
 
 def test_third_order_single_layer_calls_match_oracle():
-    """hrkan_layer_jets / _dw / _adjoint of a hidden 32 -> 32 layer under mask 0x7F."""
+    """hrkan_layer_jets / _dw / _adjoint of a hidden 32 -> 32 layer under mask 0xFF."""
     w = _workload("burgers")
     I = O = 32
     N = 600
-    mask = 0x7F
+    mask = 0xFF
     J = oracle.n_rows(mask)
     rng = np.random.default_rng(96)
     z = rng.normal(0, 0.4, (J, I, N)).astype(np.float32)
@@ -146,6 +147,37 @@ def test_kdv_residual_gradient_through_autograd_matches_oracle():
         assert relerr(got[sl], want[sl]) < tol
 
 
+def test_mixed_derivative_residual_gradient_through_autograd_matches_oracle():
+    """An anisotropic second-order residual r = u_xx + u_yy + c u_xy + f (mask 0xFF rows) built in
+    torch on the autograd wrapper: loss and weight gradient equal the oracle's."""
+    from paper_2409_14248_gb300.autograd import HRKAN
+    w = _workload("m6")
+    N, c = 800, 0.7
+    d = inputs.make(w, n_int=N, n_bnd=40)
+    x = d["x_int"].astype(np.float64)
+    f = np.sin(np.pi * x[0]) * np.cos(np.pi * x[1])
+    net = HRKAN(w.widths, w.G, m=w.m)
+    try:
+        W = torch.tensor(d["W"], device="cuda", requires_grad=True)
+        jets = net(W, _dev(d["x_int"]), 0xFF)
+        r = jets[3].double() + jets[4].double() + c * jets[7].double() + torch.tensor(f, device="cuda")
+        loss = (r ** 2).mean()
+        loss.backward()
+        got = W.grad.cpu().numpy()
+    finally:
+        net.close()
+    J = oracle.forward(w.net, d["W"], d["x_int"], 0xFF)
+    r = J[3] + J[4] + c * J[7] + f
+    assert loss.item() == pytest.approx(float((r ** 2).mean()), rel=1e-4)
+    g = 2.0 * r / N
+    dL = np.zeros((8, N))
+    dL[3], dL[4], dL[7] = g, g, c * g
+    want = oracle.backward(w.net, d["W"], d["x_int"], 0xFF, dL)
+    tol = max(TOL_D, 8.0 * fp32_floor(w, d["W"], d["x_int"], 0xFF).max())
+    for sl in layer_slices(w.widths, w.G):
+        assert relerr(got[sl], want[sl]) < tol
+
+
 def test_third_order_masks_are_checked_and_refused_where_unsupported():
     w = inputs.WORKLOADS["burgers_2_10_10_1"]   # a fused narrow shape
     d = inputs.make(w, n_int=300, n_ic=20, n_bc=20)
@@ -155,8 +187,9 @@ def test_third_order_masks_are_checked_and_refused_where_unsupported():
         with pytest.raises(capi.HRKANError) as ei:
             capi.hrkan_forward_jets(h, _dev(d["W"]), _dev(d["x_int"]), 300, 0x2F, jets)
         assert ei.value.code == capi.HRKAN_EUNSUPPORTED
-        # a third-derivative bit without the second-derivative bit of its dimension
-        for bad in (0x23, 0x47, 0x80 | 0x1F):
+        # a third-derivative bit without the second-derivative bit of its dimension, the mixed
+        # bit without both first-derivative bits, a bit past the mixed one
+        for bad in (0x23, 0x47, 0x83, 0x85, 0x100 | 0x1F):
             with pytest.raises(capi.HRKANError) as ei:
                 capi.hrkan_forward_jets(h, _dev(d["W"]), _dev(d["x_int"]), 300, bad, jets)
             assert ei.value.code == capi.HRKAN_EINVAL
