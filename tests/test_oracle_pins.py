@@ -273,6 +273,39 @@ def test_third_order_rows_leave_lower_rows_unchanged():
     np.testing.assert_array_equal(oracle.forward(net, W, x, 0x87), mixed[[0, 1, 2, 7]])
 
 
+def test_three_input_jets_match_symbolic_differentiation():
+    """D = 3 (a [3,2,1] net): u, the three first and three second derivatives (mask bits
+    0, 1+d, 4+d) vs sympy on the polynomial pieces."""
+    sp = pytest.importorskip("sympy")
+    net = dict(widths=[3, 2, 1], G=4, k=3, m=4, lo=-1.0, hi=1.0)
+    W = np.random.default_rng(38).normal(0, 0.5, oracle.param_count(net))
+    x = np.random.default_rng(39).uniform(-1, 1, (3, 3))
+    jets = oracle.forward(net, W, x, 0x7F)
+    for p in range(3):
+        X, u = _sympy_network_at(net["widths"], 4, 3, 4, -1.0, 1.0, W, x[:, p])
+        exprs = [u] + [sp.diff(u, X[d]) for d in range(3)] + [sp.diff(u, X[d], 2) for d in range(3)]
+        sub = {X[d]: x[d, p] for d in range(3)}
+        want = np.array([float(e.evalf(subs=sub)) for e in exprs])
+        np.testing.assert_allclose(jets[:, p], want, rtol=1e-8, atol=1e-8)
+
+
+def test_three_input_weight_gradient_matches_central_differences():
+    """D = 3 backward vs central FD of L(W) = sum(R * jets) over the seven rows."""
+    net = dict(widths=[3, 4, 3, 1], G=5, k=3, m=4, lo=-1.0, hi=1.0)
+    rng = np.random.default_rng(40)
+    W = rng.normal(0, 0.4, oracle.param_count(net))
+    x = rng.uniform(-1, 1, (3, 20))
+    R = rng.normal(0, 1, (7, 20))
+    dW = oracle.backward(net, W, x, 0x7F, R)
+    loss = lambda Wv: float((R * oracle.forward(net, Wv, x, 0x7F)).sum())
+    h = 1e-6
+    for i in rng.choice(W.size, 40, replace=False):
+        Wp, Wm = W.copy(), W.copy()
+        Wp[i] += h; Wm[i] -= h
+        fd = (loss(Wp) - loss(Wm)) / (2 * h)
+        assert dW[i] == pytest.approx(fd, rel=2e-5, abs=2e-8 * max(1.0, np.abs(dW).max()))
+
+
 def test_mask_selects_rows_in_bit_order():
     net = dict(widths=[2, 3, 1], G=5, k=3, m=4, lo=-1.0, hi=1.0)
     W = np.random.default_rng(9).normal(0, 0.3, oracle.param_count(net))
