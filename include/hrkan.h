@@ -24,7 +24,10 @@
  *   h = (grid_hi - grid_lo)/G, s_i = grid_lo + (i-k)h, e_i = grid_lo + (i+1)h,
  *   i = 0..n-1, the same for every layer.  Inputs outside [s_0, e_{n-1}] touch
  *   no basis (all contributions are exactly zero).
- * - Coordinates x are structure-of-arrays float32 [D][N] (x[d*N + p]).
+ * - Coordinates x are structure-of-arrays float32 [D][N] (x[d*N + p]), D = 2,
+ *   or D = 3 for FP32 single networks (hrkan_forward_jets and hrkan_backward
+ *   only; their jet mask has bit 0 = u, bit 1+d = du/dx_d, bit 4+d =
+ *   d2u/dx_d^2; the other calls return HRKAN_EUNSUPPORTED).
  * - Jet rows: bit 0 of a jet mask selects u, bit 1+d selects du/dx_d, bit 1+D+d
  *   selects d2u/dx_d^2, bit 1+2D+d selects d3u/dx_d^3, bit 1+3D = 7 selects
  *   the mixed d2u/dx_0dx_1 (D = 2: 0x1F = u,u_x,u_y,u_xx,u_yy; 0x0F =

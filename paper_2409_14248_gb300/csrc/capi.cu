@@ -34,6 +34,9 @@ struct hrkan_ctx {
     double* m2 = nullptr;
     int* t_counter = nullptr;        // [2] device Adam step counter (t = 0 mode)
     int* status = nullptr;           // device error word written by bounded waits
+    // first layer: coordinates that jet directions 0 and 1 differentiate along
+    // (a three-input network runs its jets as two passes: x and y, then z)
+    int seed0 = 0, seed1 = 1;
     // multi-instance work lists (rebuilt only when the offsets or problems change)
     struct Batch {
         std::vector<int64_t> off0, off1;
@@ -100,7 +103,8 @@ int check_cfg(const hrkan_cfg* c) {
     for (int l = 0; l < c->n_widths; ++l)
         if (c->widths[l] < 1 || c->widths[l] > 64)
             return fail(HRKAN_EINVAL, "widths[%d]=%d outside [1, 64]", l, c->widths[l]);
-    if (c->widths[0] != 2) return fail(HRKAN_EUNSUPPORTED, "widths[0]=%d: only D = 2 inputs", c->widths[0]);
+    if (c->widths[0] != 2 && c->widths[0] != 3)
+        return fail(HRKAN_EUNSUPPORTED, "widths[0]=%d: D = 2 or 3 inputs", c->widths[0]);
     if (c->widths[c->n_widths - 1] != 1)
         return fail(HRKAN_EINVAL, "last width %d: the network has one output", c->widths[c->n_widths - 1]);
     if (c->G < 1 || c->G > 4096) return fail(HRKAN_EINVAL, "G=%d outside [1, 4096]", c->G);
@@ -316,6 +320,8 @@ WideLayer wide_layer(hrkan_t h, const float* W, int l, int64_t N) {
     p.O = h->cfg.widths[l + 1];
     p.N = N;
     p.g = h->grid;
+    p.seed0 = h->seed0;
+    p.seed1 = h->seed1;
     return p;
 }
 
@@ -426,6 +432,8 @@ int wide_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsi
         d.row0 = row0;
         d.GP = h->wide_gp;
         d.g = h->grid;
+        d.seed0 = h->seed0;
+        d.seed1 = h->seed1;
         if ((rc = layer_dw(h, d, l, mask, s))) return rc;
         cudaError_t e;
         if (l > 0) {
@@ -541,6 +549,103 @@ int set_last_error(int code, const char* msg) {
 }
 }  // namespace hrkan
 
+// Three-input networks (D = 3).  The jet mask has bit 0 = u, bit 1+d =
+// du/dx_d, bit 4+d = d2u/dx_d^2 (d = 0, 1, 2).  A jet row along direction d
+// depends only on derivatives along d, so the network runs as two passes of
+// the two-direction kernels: directions (x, y) with the first layer's seeds
+// (0, 1), then direction z with seeds (2, none); the rows are then gathered in
+// the mask's bit order.
+bool valid_mask3(unsigned m) {
+    if (!(m & 1u) || (m & ~0x7Fu)) return false;
+    return !((m & 0x10u) && !(m & 0x02u)) && !((m & 0x20u) && !(m & 0x04u)) && !((m & 0x40u) && !(m & 0x08u));
+}
+
+// The layer kernels' two-direction mask that covers m2 (0x01, 0x0F or 0x1F;
+// a pass computes its extra rows and leaves them unused).
+unsigned covering_mask(unsigned m2) { return m2 == 1u ? 1u : (m2 & ~0x0Fu) ? 0x1Fu : 0x0Fu; }
+
+// Pass masks (two-direction encoding) of a three-input mask; mb = 0: no z pass.
+void split3(unsigned m, unsigned* ma, unsigned* mb) {
+    *ma = covering_mask(1u | (m & 0x02u) | (m & 0x04u) | ((m & 0x10u) ? 0x08u : 0u) | ((m & 0x20u) ? 0x10u : 0u));
+    *mb = (m & 0x48u) ? covering_mask(1u | ((m & 0x08u) ? 0x02u : 0u) | ((m & 0x40u) ? 0x08u : 0u)) : 0u;
+}
+
+// For bit b of a three-input mask: which pass holds it (0 = xy, 1 = z) and its bit there.
+void bit3_source(int b, int* pass, int* bit2) {
+    static const int P[7] = {0, 0, 0, 1, 0, 0, 1}, B[7] = {0, 1, 2, 1, 3, 4, 3};
+    *pass = P[b];
+    *bit2 = B[b];
+}
+
+int row_of_bit(unsigned mask, int bit) { return __builtin_popcount(mask & ((1u << bit) - 1u)); }
+
+int forward3(hrkan_t h, const float* W, const float* x, int64_t N, unsigned m, float* jets, cudaStream_t s) {
+    unsigned ma, mb;
+    split3(m, &ma, &mb);
+    int rc = HRKAN_OK;
+    float* y[2] = {ws_get(h, 16, size_t(jets_of(ma)) * N, &rc), nullptr};
+    if (!y[0]) return rc;
+    if (mb && !(y[1] = ws_get(h, 17, size_t(jets_of(mb)) * N, &rc))) return rc;
+    h->seed0 = 0;
+    h->seed1 = 1;
+    rc = wide_forward_set(h, W, x, N, ma, y[0], nullptr, 0, s);
+    if (!rc && mb) {
+        h->seed0 = 2;
+        h->seed1 = -1;
+        rc = wide_forward_set(h, W, x, N, mb, y[1], nullptr, 0, s);
+    }
+    h->seed0 = 0;
+    h->seed1 = 1;
+    if (rc) return rc;
+    int r = 0;
+    for (int b = 0; b < 7; ++b) {
+        if (!(m & (1u << b))) continue;
+        int pass, b2;
+        bit3_source(b, &pass, &b2);
+        const float* src = y[pass] + size_t(row_of_bit(pass ? mb : ma, b2)) * N;
+        HR_CUDA(cudaMemcpyAsync(jets + size_t(r) * N, src, size_t(N) * sizeof(float), cudaMemcpyDeviceToDevice, s),
+                "cudaMemcpyAsync");
+        ++r;
+    }
+    return HRKAN_OK;
+}
+
+// Weight-gradient partial rows of both passes: [0, GP) and, with a z pass, [GP, 2 GP).
+int backward3(hrkan_t h, const float* W, const float* x, int64_t N, unsigned m, const float* dL, int* rows,
+              cudaStream_t s) {
+    unsigned ma, mb;
+    split3(m, &ma, &mb);
+    int rc = HRKAN_OK;
+    float* g[2] = {ws_get(h, 18, size_t(jets_of(ma)) * N, &rc), nullptr};
+    if (!g[0]) return rc;
+    if (mb && !(g[1] = ws_get(h, 19, size_t(jets_of(mb)) * N, &rc))) return rc;
+    int r = 0;
+    // rows the mask does not request (and the z pass's u row) get zero gradient
+    HR_CUDA(cudaMemsetAsync(g[0], 0, size_t(jets_of(ma)) * N * sizeof(float), s), "cudaMemsetAsync");
+    if (mb) HR_CUDA(cudaMemsetAsync(g[1], 0, size_t(jets_of(mb)) * N * sizeof(float), s), "cudaMemsetAsync");
+    for (int b = 0; b < 7; ++b) {
+        if (!(m & (1u << b))) continue;
+        int pass, b2;
+        bit3_source(b, &pass, &b2);
+        float* dst = g[pass] + size_t(row_of_bit(pass ? mb : ma, b2)) * N;
+        HR_CUDA(cudaMemcpyAsync(dst, dL + size_t(r) * N, size_t(N) * sizeof(float), cudaMemcpyDeviceToDevice, s),
+                "cudaMemcpyAsync");
+        ++r;
+    }
+    h->seed0 = 0;
+    h->seed1 = 1;
+    rc = wide_backward_set(h, W, x, N, ma, nullptr, g[0], 0, s);
+    if (!rc && mb) {
+        h->seed0 = 2;
+        h->seed1 = -1;
+        rc = wide_backward_set(h, W, x, N, mb, nullptr, g[1], h->wide_gp, s);
+    }
+    h->seed0 = 0;
+    h->seed1 = 1;
+    *rows = mb ? 2 * h->wide_gp : h->wide_gp;
+    return rc;
+}
+
 extern "C" {
 
 int64_t hrkan_param_count(const hrkan_cfg* cfg) {
@@ -562,6 +667,11 @@ int hrkan_init(hrkan_t* out, const hrkan_cfg* cfg) {
     if (uniform_hidden) net_id = narrow_net_id(L, cfg->widths[1]);
     if (cfg->flags & HRKAN_FLAG_LAYERWISE) net_id = -1;
     if (cfg->m != 4) net_id = -1;   // the fused narrow kernels are built for m = 4
+    if (cfg->widths[0] == 3) {
+        net_id = -1;                  // three inputs: layer-wise path, FP32, one network
+        if (cfg->prec != HRKAN_FP32 || cfg->n_instances != 1)
+            return fail(HRKAN_EUNSUPPORTED, "three-input networks run in FP32 with one instance");
+    }
     if (cfg->prec != HRKAN_FP32 && cfg->m != 4)
         return fail(HRKAN_EUNSUPPORTED, "precision %d: the tensor-core kernels are built for m = 4 (m=%d)", cfg->prec,
                     cfg->m);
@@ -644,7 +754,7 @@ void hrkan_destroy(hrkan_t h) {
 }
 
 int64_t hrkan_tape_floats(hrkan_t h, int64_t N, unsigned jet_mask) {
-    if (!h || N <= 0 || !valid_mask(jet_mask) || h->net_id >= 0) return 0;   // fused shapes recompute
+    if (!h || N <= 0 || !valid_mask(jet_mask) || h->net_id >= 0 || h->cfg.widths[0] == 3) return 0;   // recompute
     return tape_total(h, N, jets_of(jet_mask));
 }
 
@@ -653,10 +763,15 @@ int hrkan_forward_jets(hrkan_t h, const float* W, const float* x, int64_t N, uns
     (void)tape;
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
     if (N < 0) return fail(HRKAN_EINVAL, "N=%lld", (long long)N);
-    if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
+    const bool d3 = h->cfg.widths[0] == 3;
+    if (!(d3 ? valid_mask3(jet_mask) : valid_mask(jet_mask))) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
     if (N == 0) return HRKAN_OK;
     if (!W || !x || !jets) return fail(HRKAN_EINVAL, "NULL device pointer");
     if (int rc = use_device(h)) return rc;
+    if (d3) {
+        ProfScope ps(h, HRKAN_KERNEL_FORWARD, (cudaStream_t)stream);
+        return forward3(h, W, x, N, jet_mask, jets, (cudaStream_t)stream);
+    }
     if (h->net_id < 0) {
         ProfScope ps(h, HRKAN_KERNEL_FORWARD, (cudaStream_t)stream);
         return wide_forward_set(h, W, x, N, jet_mask, jets, tape, 0, (cudaStream_t)stream);
@@ -680,6 +795,7 @@ int pinn_residual_loss(hrkan_t h, const pinn_problem* prob, const float* x_int, 
                        const float* jets_int, const float* u_bnd, const float* g_bnd, int64_t N_bnd, double* loss,
                        float* dL_djets_int, float* dL_du_bnd, hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: hrkan_forward_jets and hrkan_backward only");
     if (int rc = check_problem(prob)) return rc;
     if (N_int < 0 || N_bnd < 0) return fail(HRKAN_EINVAL, "negative point count");
     if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
@@ -733,7 +849,8 @@ int hrkan_backward(hrkan_t h, const float* W, const float* x, int64_t N, unsigne
     (void)tape;
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
     if (N < 0) return fail(HRKAN_EINVAL, "N=%lld", (long long)N);
-    if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
+    const bool d3 = h->cfg.widths[0] == 3;
+    if (!(d3 ? valid_mask3(jet_mask) : valid_mask(jet_mask))) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
     if (!W || !dW) return fail(HRKAN_EINVAL, "NULL device pointer");
     if (N > 0 && (!x || !dL_djets)) return fail(HRKAN_EINVAL, "NULL device pointer");
     if (int rc = use_device(h)) return rc;
@@ -744,7 +861,9 @@ int hrkan_backward(hrkan_t h, const float* W, const float* x, int64_t N, unsigne
     }
     int grid = 0;
     cudaError_t e = cudaSuccess;
-    if (h->net_id < 0) {
+    if (d3) {
+        if (int rc = backward3(h, W, x, N, jet_mask, dL_djets, &grid, s)) return rc;
+    } else if (h->net_id < 0) {
         if (int rc = wide_backward_set(h, W, x, N, jet_mask, tape, dL_djets, 0, s)) return rc;
         grid = h->wide_gp;
     } else {
@@ -892,6 +1011,7 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
                      const float* x_bnd, const float* g_bnd, int64_t N_bnd, double lr, double b1, double b2,
                      double eps, int t, double* loss, float* dW, hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: hrkan_forward_jets and hrkan_backward only");
     if (int rc = check_problem(prob)) return rc;
     if (N_int < 0 || N_bnd < 0) return fail(HRKAN_EINVAL, "negative point count");
     if (N_int + N_bnd == 0) return fail(HRKAN_EINVAL, "no collocation points");
@@ -1143,6 +1263,7 @@ int hrkan_sync_status(hrkan_t h) {
 int hrkan_layer_jets(hrkan_t h, int layer, const float* W, const float* z, int64_t N, unsigned jet_mask, float* y,
                      hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: hrkan_forward_jets and hrkan_backward only");
     if (layer < 0 || layer >= h->L) return fail(HRKAN_EINVAL, "layer %d outside [0, %d)", layer, h->L);
     if (N < 0) return fail(HRKAN_EINVAL, "N=%lld", (long long)N);
     if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
@@ -1156,6 +1277,7 @@ int hrkan_layer_jets(hrkan_t h, int layer, const float* W, const float* z, int64
 int hrkan_layer_dw(hrkan_t h, int layer, const float* z, const float* gy, int64_t N, unsigned jet_mask, float* dW,
                    hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: hrkan_forward_jets and hrkan_backward only");
     if (layer < 0 || layer >= h->L) return fail(HRKAN_EINVAL, "layer %d outside [0, %d)", layer, h->L);
     if (N < 0) return fail(HRKAN_EINVAL, "N=%lld", (long long)N);
     if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
@@ -1188,6 +1310,7 @@ int hrkan_layer_dw(hrkan_t h, int layer, const float* z, const float* gy, int64_
 int hrkan_layer_adjoint(hrkan_t h, int layer, const float* W, const float* z, const float* gy, int64_t N,
                         unsigned jet_mask, float* gz, hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: hrkan_forward_jets and hrkan_backward only");
     if (layer < 1 || layer >= h->L) return fail(HRKAN_EINVAL, "layer %d outside [1, %d)", layer, h->L);
     if (N < 0) return fail(HRKAN_EINVAL, "N=%lld", (long long)N);
     if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);

@@ -12,12 +12,15 @@ namespace hrkan {
 struct WideLayer {
     const float* W;
     int I, O;
-    const float* z;    // input jets [J][I][N] (first layer: coordinates [2][N])
+    const float* z;    // input jets [J][I][N] (first layer: coordinates [D][N])
     float* y;          // forward: output jets [J][O][N]
     const float* gy;   // adjoint: dL/d(output jets) [J][O][N]
     float* gz;         // adjoint: dL/d(input jets) [J][I][N]
     int64_t N;
     Grid g;
+    // first layer: the coordinates that jet directions 0 and 1 differentiate
+    // along (-1: none); a three-input network runs as passes over direction pairs
+    int seed0 = 0, seed1 = 1;
 };
 
 // Weight gradient of one layer into partial rows [row0, row0 + GP) of a
@@ -33,6 +36,7 @@ struct WideDw {
     int row0;
     int GP;            // point groups = partial rows written
     Grid g;
+    int seed0 = 0, seed1 = 1;   // first layer: as in WideLayer
 };
 
 cudaError_t wide_forward_layer(const WideLayer& p, unsigned mask, bool first, cudaStream_t s);

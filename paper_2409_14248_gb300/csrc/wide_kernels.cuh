@@ -27,15 +27,16 @@ constexpr int KPW = KW + 1;
 // The HR order m (Eq. 2) is the template parameter MW of every kernel below.
 
 // Jets of input unit j of a layer: from the tape, or (first layer) the
-// coordinate x_j itself with dx_j/dx_j = 1 and no other derivative.
+// coordinate x_j itself with derivative 1 along the jet direction that
+// differentiates along it (seed0 / seed1) and no other derivative.
 template <unsigned MASK, bool FIRST>
 __device__ __forceinline__ void load_unit_jets(const float* __restrict__ z, int I, int j, int64_t N, int64_t p,
-                                               float* zj) {
+                                               float* zj, int seed0 = 0, int seed1 = 1) {
     using JT = Jet<MASK>;
     if constexpr (FIRST) {
         zj[0] = z[j * N + p];
-        if constexpr (JT::F0) zj[JT::RF0] = (j == 0) ? 1.0f : 0.0f;
-        if constexpr (JT::F1) zj[JT::RF1] = (j == 1) ? 1.0f : 0.0f;
+        if constexpr (JT::F0) zj[JT::RF0] = (j == seed0) ? 1.0f : 0.0f;
+        if constexpr (JT::F1) zj[JT::RF1] = (j == seed1) ? 1.0f : 0.0f;
         if constexpr (JT::S0) zj[JT::RS0] = 0.0f;
         if constexpr (JT::S1) zj[JT::RS1] = 0.0f;
         if constexpr (JT::T0) zj[JT::RT0] = 0.0f;
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(WB) wide_fwd_kernel(WideLayer p) {
 #pragma unroll 1
     for (int j = 0; j < I; ++j) {
         float z[J];
-        load_unit_jets<MASK, FIRST>(p.z, I, j, N, pt, z);
+        load_unit_jets<MASK, FIRST>(p.z, I, j, N, pt, z, p.seed0, p.seed1);
         Active<KW, MW, JT::NDER_ROWS> b;
         b.eval(z[0], p.g);
         float a[J][KPW];
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(WB) wide_dw_kernel(WideDw p) {
             float a[J][KPW];
             if (pt < N && jj < nj) {
                 float z[J];
-                load_unit_jets<MASK, FIRST>(p.z, I, j0 + jj, N, pt, z);
+                load_unit_jets<MASK, FIRST>(p.z, I, j0 + jj, N, pt, z, p.seed0, p.seed1);
                 Active<KW, MW, JT::NDER_ROWS> b;
                 b.eval(z[0], p.g);
                 JT::template rows_b<KPW>(z, b, a);

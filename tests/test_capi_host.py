@@ -56,7 +56,8 @@ def test_param_count(lib):
     (dict(widths=[2, 5, 1], G=5, lo=1.0, hi=-1.0), capi.HRKAN_EINVAL),
     (dict(widths=[2, 5, 1], G=5, n_instances=0), capi.HRKAN_EINVAL),
     (dict(widths=[2, 5, 1], G=5, prec=7), capi.HRKAN_EINVAL),
-    (dict(widths=[3, 5, 1], G=5), capi.HRKAN_EUNSUPPORTED),    # D = 3
+    (dict(widths=[4, 5, 1], G=5), capi.HRKAN_EUNSUPPORTED),    # D = 4
+    (dict(widths=[3, 5, 1], G=5, prec=capi.HRKAN_BF16), capi.HRKAN_EUNSUPPORTED),   # D = 3 runs in FP32
     (dict(widths=[2, 5, 1], G=5, m=7), capi.HRKAN_EUNSUPPORTED),   # HR orders 2..6 are built
     (dict(widths=[2, 5, 1], G=5, m=1), capi.HRKAN_EUNSUPPORTED),   # u_xx needs m >= 2
     (dict(widths=[2, 5, 1], G=5, m=0), capi.HRKAN_EINVAL),
