@@ -33,6 +33,7 @@ _lib = None
 
 POISSON = 0
 BURGERS = 1
+KDV = 2
 EXACT, BF16, TF32 = 0, 1, 2
 
 

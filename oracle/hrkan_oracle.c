@@ -642,7 +642,7 @@ int orc_backward(int n_widths, const int* widths, int G, int k, int m, double lo
 
 /* ------------------------------------------------------------------- loss */
 
-enum { ORC_POISSON = 0, ORC_BURGERS = 1 };
+enum { ORC_POISSON = 0, ORC_BURGERS = 1, ORC_KDV = 2 };
 
 static int row_of(unsigned mask, int bit)
 {
@@ -658,6 +658,9 @@ static int row_of(unsigned mask, int bit)
  *       r = u_xx + u_yy + (a^2+b^2) pi^2 sin(a pi x) sin(b pi y)
  *   Burgers (Eq. 6-8 form, coordinates (x, t)):
  *       r = u_t + lam u u_x - nu u_xx
+ *   KdV (a third-order equation of the kind Section 3 picks a larger m for,
+ *   coordinates (x, t)):
+ *       r = u_t + lam u u_x + nu u_xxx
  *   L_pde = mean_int r^2, L_bnd = mean_bnd (u - g)^2 (pooled over all edges /
  *   initial points), L = alpha L_pde + L_bnd.
  * loss[0] = L, loss[1] = L_pde, loss[2] = L_bnd.
@@ -702,6 +705,23 @@ int orc_residual_loss(int kind, double a, double b, double lam, double nu, doubl
                 dL_djets_int[(long)ru * N_int + p] = g * lam * ux;
                 dL_djets_int[(long)rx * N_int + p] = g * lam * u;
                 dL_djets_int[(long)rxx * N_int + p] = -g * nu;
+            }
+        }
+    } else if (kind == ORC_KDV) {
+        int ru = row_of(mask, 0), rx = row_of(mask, 1), rt = row_of(mask, 2),
+            rxxx = row_of(mask, 1 + 2 * D + 0);
+        if (ru < 0 || rx < 0 || rt < 0 || rxxx < 0) return -1;
+        for (long p = 0; p < N_int; ++p) {
+            double u = jets_int[(long)ru * N_int + p], ux = jets_int[(long)rx * N_int + p];
+            double ut = jets_int[(long)rt * N_int + p], uxxx = jets_int[(long)rxxx * N_int + p];
+            double r = ut + lam * u * ux + nu * uxxx;
+            Lp += r * r;
+            if (dL_djets_int) {
+                double g = 2.0 * alpha * r / (double)N_int;
+                dL_djets_int[(long)rt * N_int + p] = g;
+                dL_djets_int[(long)ru * N_int + p] = g * lam * ux;
+                dL_djets_int[(long)rx * N_int + p] = g * lam * u;
+                dL_djets_int[(long)rxxx * N_int + p] = g * nu;
             }
         }
     } else {

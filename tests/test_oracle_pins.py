@@ -362,6 +362,25 @@ def test_burgers_residual_zero_on_cole_hopf_solution():
     assert loss[1] < 1e-26
 
 
+def test_kdv_residual_zero_on_the_soliton():
+    """u = (c/2) sech^2(sqrt(c)/2 (x - c t - x0)) solves u_t + 6 u u_x + u_xxx = 0 exactly
+    (the KdV soliton); sympy supplies its jets (u, u_x, u_t, u_xx, u_xxx: mask 0x2F)."""
+    sp = pytest.importorskip("sympy")
+    X, T = sp.symbols("x t", real=True)
+    c, x0 = 1.7, 0.2
+    u = c / 2 * sp.sech(sp.sqrt(c) / 2 * (X - c * T - x0)) ** 2
+    fs = [sp.lambdify((X, T), f, "numpy")
+          for f in (u, sp.diff(u, X), sp.diff(u, T), sp.diff(u, X, 2), sp.diff(u, X, 3))]
+    x = np.random.default_rng(16).uniform([[-1], [0]], [[1], [1]], (2, 64))
+    jets = np.stack([f(x[0], x[1]) for f in fs])
+    prob = dict(kind=oracle.KDV, lam=6.0, nu=1.0, alpha=1.0)
+    loss, _, _ = oracle.residual_loss(prob, x, 0x2F, jets, np.zeros(1), np.zeros(1))
+    assert loss[1] < 1e-24
+    # a wrong coefficient leaves a residual of the size of the dropped term
+    bad, _, _ = oracle.residual_loss(dict(prob, lam=5.0), x, 0x2F, jets, np.zeros(1), np.zeros(1))
+    assert bad[1] > 1e-4
+
+
 def test_loss_of_zero_network_is_mean_source_squared():
     """W = 0 gives u = 0: L = alpha mean(f^2) + mean(g^2)."""
     w = inputs.WORKLOADS["poisson_2_5_1"]
@@ -378,10 +397,10 @@ def test_loss_of_zero_network_is_mean_source_squared():
     assert loss[0] == pytest.approx(alpha * np.mean(f ** 2) + np.mean(g ** 2), rel=1e-13)
 
 
-@pytest.mark.parametrize("kind", [oracle.POISSON, oracle.BURGERS])
+@pytest.mark.parametrize("kind", [oracle.POISSON, oracle.BURGERS, oracle.KDV])
 def test_loss_gradient_wrt_jets_matches_central_differences(kind):
     rng = np.random.default_rng(15)
-    mask = 0x1F if kind == oracle.POISSON else inputs.MASK_BURGERS
+    mask = {oracle.POISSON: 0x1F, oracle.BURGERS: inputs.MASK_BURGERS, oracle.KDV: 0x2F}[kind]
     J = oracle.n_rows(mask)
     x = rng.uniform(-1, 1, (2, 12))
     jets = rng.normal(size=(J, 12))
