@@ -73,7 +73,7 @@ enum hrkan_status {
 };
 
 enum hrkan_prec { HRKAN_FP32 = 0, HRKAN_BF16 = 1, HRKAN_TF32 = 2 };
-enum hrkan_pde { HRKAN_POISSON = 0, HRKAN_BURGERS = 1 };
+enum hrkan_pde { HRKAN_POISSON = 0, HRKAN_BURGERS = 1, HRKAN_KDV = 2 };
 
 #define HRKAN_MAX_WIDTHS 8
 /* Use the layer-wise kernels even where a fused whole-network kernel exists. */
@@ -114,7 +114,7 @@ typedef struct pinn_problem {
     int kind;       /* enum hrkan_pde */
     int reserved;
     double a, b;    /* Poisson source frequencies */
-    double lam, nu; /* Burgers advection and viscosity coefficients */
+    double lam, nu; /* Burgers: r = u_t + lam u u_x - nu u_xx; KdV: r = u_t + lam u u_x + nu u_xxx */
     double alpha;   /* weight of the PDE term */
 } pinn_problem;
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libhrkan.so")
 HRKAN_OK, HRKAN_EINVAL, HRKAN_ENOMEM, HRKAN_ECUDA, HRKAN_EUNSUPPORTED, HRKAN_ETIMEOUT, HRKAN_ENONFINITE, HRKAN_EIO = \
     0, -1, -2, -3, -4, -5, -6, -7
 HRKAN_FP32, HRKAN_BF16, HRKAN_TF32 = 0, 1, 2
-HRKAN_POISSON, HRKAN_BURGERS = 0, 1
+HRKAN_POISSON, HRKAN_BURGERS, HRKAN_KDV = 0, 1, 2
 HRKAN_MAX_WIDTHS = 8
 
 # every symbol include/hrkan.h declares

@@ -150,7 +150,8 @@ PdeParams make_pde(const pinn_problem* p) {
 
 int check_problem(const pinn_problem* p) {
     if (!p) return fail(HRKAN_EINVAL, "problem is NULL");
-    if (p->kind != HRKAN_POISSON && p->kind != HRKAN_BURGERS) return fail(HRKAN_EINVAL, "problem kind %d", p->kind);
+    if (p->kind != HRKAN_POISSON && p->kind != HRKAN_BURGERS && p->kind != HRKAN_KDV)
+        return fail(HRKAN_EINVAL, "problem kind %d", p->kind);
     if (!std::isfinite(p->a) || !std::isfinite(p->b) || !std::isfinite(p->lam) || !std::isfinite(p->nu) ||
         !std::isfinite(p->alpha))
         return fail(HRKAN_EINVAL, "non-finite problem coefficient");
@@ -467,7 +468,7 @@ int wide_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsi
 int wide_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float* x_int, int64_t N_int,
                     const float* x_bnd, const float* g_bnd, int64_t N_bnd, double lr, double b1, double b2,
                     double eps, int t, double* loss, float* dW, cudaStream_t s) {
-    const unsigned mask = prob->kind == HRKAN_POISSON ? 0x1Fu : 0x0Fu;
+    const unsigned mask = pde_mask(prob->kind);
     const int J = jets_of(mask);
     int rc = HRKAN_OK;
     float* jets = ws_get(h, 4, size_t(J) * std::max<int64_t>(N_int, 1), &rc);
@@ -1023,7 +1024,7 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
         return fail(HRKAN_EINVAL, "Adam hyper-parameters lr=%g b1=%g b2=%g eps=%g", lr, b1, b2, eps);
     if (int rc = use_device(h)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    const unsigned mask = prob->kind == HRKAN_POISSON ? 0x1Fu : 0x0Fu;
+    const unsigned mask = pde_mask(prob->kind);
     if (h->net_id < 0) return wide_train_step(h, prob, W, x_int, N_int, x_bnd, g_bnd, N_bnd, lr, b1, b2, eps, t, loss,
                                               dW, s);
     NarrowParams p = base_params(h, W);
@@ -1102,7 +1103,7 @@ int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, con
     auto& b = h->train_batch;
     cudaStream_t s = (cudaStream_t)stream;
     if (int rc = build_batch(h, b, n_inst, probs, off_int, off_bnd, true, s)) return rc;
-    const unsigned mask = probs[0].kind == HRKAN_POISSON ? 0x1Fu : 0x0Fu;
+    const unsigned mask = pde_mask(probs[0].kind);
     BatchParams p{};
     p.W = W;
     p.P = h->P;

@@ -281,6 +281,7 @@ struct Jet {
 // Residual of one interior point and dL/d(jets) (Eq. 4, Eq. 8):
 //   Poisson: r = u_xx + u_yy + (a^2+b^2) pi^2 sin(a pi x) sin(b pi y)
 //   Burgers: r = u_t + lam u u_x - nu u_xx
+//   KdV:     r = u_t + lam u u_x + nu u_xxx (a third-order equation, mask 0x2F)
 // gu[r] = dL/d jet row r for L = alpha mean(r^2): scale = 2 alpha / N_int.
 struct PdeParams {
     int kind;
@@ -298,9 +299,14 @@ __device__ __forceinline__ float pde_residual(const PdeParams& P, float x0, floa
             return u[JT::RS0] + u[JT::RS1] + f;
         }
         return 0.0f;
-    } else {
+    } else if (P.kind == 1) {
         if constexpr (JT::F0 && JT::F1 && JT::S0) {
             return u[JT::RF1] + P.lam * u[0] * u[JT::RF0] - P.nu * u[JT::RS0];
+        }
+        return 0.0f;
+    } else {
+        if constexpr (JT::F0 && JT::F1 && JT::T0) {
+            return u[JT::RF1] + P.lam * u[0] * u[JT::RF0] + P.nu * u[JT::RT0];
         }
         return 0.0f;
     }
@@ -315,19 +321,30 @@ __device__ __forceinline__ void pde_residual_grad(const PdeParams& P, float r, c
     float g = scale * r;
     if (P.kind == 0) {
         if constexpr (JT::S0 && JT::S1) { gu[JT::RS0] = g; gu[JT::RS1] = g; }
-    } else {
+    } else if (P.kind == 1) {
         if constexpr (JT::F0 && JT::F1 && JT::S0) {
             gu[JT::RF1] = g;
             gu[0] = g * P.lam * u[JT::RF0];
             gu[JT::RF0] = g * P.lam * u[0];
             gu[JT::RS0] = -g * P.nu;
         }
+    } else {
+        if constexpr (JT::F0 && JT::F1 && JT::T0) {
+            gu[JT::RF1] = g;
+            gu[0] = g * P.lam * u[JT::RF0];
+            gu[JT::RF0] = g * P.lam * u[0];
+            gu[JT::RT0] = g * P.nu;
+        }
     }
 }
 
-// Masks for which a residual exists.
+// Masks for which a residual exists: Poisson u_xx, u_yy; Burgers u, u_x, u_t,
+// u_xx; KdV u, u_x, u_t, u_xxx.
 __host__ __device__ constexpr bool mask_has_rows(unsigned mask, int kind) {
-    return kind == 0 ? ((mask & 0x18u) == 0x18u) : ((mask & 0x0Fu) == 0x0Fu);
+    return kind == 0 ? ((mask & 0x18u) == 0x18u) : kind == 1 ? ((mask & 0x0Fu) == 0x0Fu) : ((mask & 0x27u) == 0x27u);
 }
+
+// The interior jet mask the training step uses for a problem kind.
+__host__ __device__ constexpr unsigned pde_mask(int kind) { return kind == 0 ? 0x1Fu : kind == 1 ? 0x0Fu : 0x2Fu; }
 
 }  // namespace hrkan

@@ -163,12 +163,13 @@ __global__ void __launch_bounds__(RES_BLOCK) residual_kernel(ResidualParams p) {
     }
 }
 
-bool residual_mask_supported(unsigned mask) { return mask == 0x0Fu || mask == 0x1Fu; }
+bool residual_mask_supported(unsigned mask) { return mask == 0x0Fu || mask == 0x1Fu || mask == 0x2Fu; }
 
 cudaError_t launch_residual(const ResidualParams& p, int grid, cudaStream_t s) {
     switch (p.mask) {
         case 0x0Fu: residual_kernel<0x0Fu><<<grid, RES_BLOCK, 0, s>>>(p); break;
         case 0x1Fu: residual_kernel<0x1Fu><<<grid, RES_BLOCK, 0, s>>>(p); break;
+        case 0x2Fu: residual_kernel<0x2Fu><<<grid, RES_BLOCK, 0, s>>>(p); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
