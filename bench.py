@@ -397,7 +397,7 @@ def run_ours(args, ws, rank, local):
                 kms = total_ms / args.steps
             # DRAM bytes of one launch of the fused kernel from one ncu capture of this workload
             # (its inputs and weights only); unknown for the other shapes
-            traffic = 783616 if fused and args.workload == WORKLOAD else None
+            traffic = 801365 if fused and args.workload == WORKLOAD else None
             roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": kernel, "kernel_ms": kms,
                         "reduce_adam_ms": red_ms / max(1, red_n),
