@@ -235,9 +235,21 @@ int adam_step(hrkan_t h, float* W, const float* dW, double lr, double b1, double
  * Synchronise the device and report device-side failures recorded since the
  * last call: HRKAN_ETIMEOUT if a bounded wait inside a tensor-core kernel gave
  * up (the kernel then skipped its output, freed its tensor memory and
- * returned).  Clears the record.
+ * returned); HRKAN_ENONFINITE if a loss computed by pinn_residual_loss or a
+ * training step was NaN or infinite.  The first failure is kept.  Clears the
+ * record.
  */
 int hrkan_sync_status(hrkan_t h);
+
+/*
+ * Limit of the tensor-core kernels' bounded waits in GPU clock cycles (0 =
+ * the default, about one second).  A small value makes those waits give up
+ * early, so that a test can exercise the timeout path (the kernel records
+ * HRKAN_ETIMEOUT, waits with the default limit for its own copies and MMAs,
+ * frees its tensor memory and returns; the handle stays usable).  Synchronises
+ * the device.
+ */
+int hrkan_set_wait_cycles(hrkan_t h, int64_t cycles);
 
 /* Zero the Adam moments and the device step counter of the handle. */
 int hrkan_reset_moments(hrkan_t h, hrkan_stream_t stream);

@@ -28,7 +28,7 @@ EXPORTS = ("hrkan_param_count", "hrkan_init", "hrkan_destroy", "hrkan_last_error
            "hrkan_train_step", "hrkan_profile_enable", "hrkan_profile_read", "hrkan_backward_noalloc",
            "hrkan_train_step_batched", "hrkan_forward_jets_batched", "hrkan_set_batch_items", "hrkan_sync_status",
            "hrkan_layer_jets", "hrkan_layer_dw", "hrkan_layer_adjoint", "hrkan_autotune_batch",
-           "hrkan_checkpoint_write", "hrkan_checkpoint_read", "hrkan_save", "hrkan_load")
+           "hrkan_checkpoint_write", "hrkan_checkpoint_read", "hrkan_save", "hrkan_load", "hrkan_set_wait_cycles")
 HRKAN_KERNEL_FUSED, HRKAN_KERNEL_REDUCE, HRKAN_KERNEL_FORWARD, HRKAN_KERNEL_RESIDUAL, HRKAN_KERNEL_TENSOR = 0, 1, 2, 3, 4
 
 
@@ -101,6 +101,7 @@ def load_library(path: str = LIB_PATH):
         lib.hrkan_checkpoint_read.argtypes = [ctypes.c_char_p, _i64, _i32, _i64p, _i64p, _vp, _vp, _vp]
         lib.hrkan_save.argtypes = [_vp, _vp, _i64, ctypes.c_char_p, _vp]
         lib.hrkan_load.argtypes = [_vp, _vp, _i64p, ctypes.c_char_p, _vp]
+        lib.hrkan_set_wait_cycles.argtypes = [_vp, _i64]
         for name in EXPORTS:
             if name not in ("hrkan_destroy", "hrkan_last_error", "hrkan_param_count", "hrkan_tape_floats"):
                 getattr(lib, name).restype = _i32
@@ -200,6 +201,11 @@ def adam_step(h, W, dW, lr, b1=0.9, b2=0.999, eps=1e-8, t=1, stream=None):
     import torch
     _check(load_library().adam_step(h, _ptr(W, torch.float32), _ptr(dW, torch.float32), float(lr), float(b1),
                                     float(b2), float(eps), int(t), _stream(stream)))
+
+
+def hrkan_set_wait_cycles(h, cycles):
+    """Limit of the tensor-core kernels' bounded waits (0 = default); for fault-injection tests."""
+    _check(load_library().hrkan_set_wait_cycles(h, ctypes.c_int64(int(cycles))))
 
 
 def hrkan_reset_moments(h, stream=None):
@@ -329,7 +335,7 @@ def hrkan_set_batch_items(h, points_per_item):
 
 
 def hrkan_sync_status(h):
-    """Synchronise; raise HRKANError(HRKAN_ETIMEOUT) if a bounded device wait gave up."""
+    """Synchronise; raise HRKANError(HRKAN_ETIMEOUT / HRKAN_ENONFINITE) for a recorded device-side failure."""
     _check(load_library().hrkan_sync_status(h))
 
 

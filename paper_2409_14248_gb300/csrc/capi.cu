@@ -530,6 +530,7 @@ int wide_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float* 
     q.loss_partial = h->loss_partial;
     q.Gl = int(rg);
     q.loss = loss;
+    q.status = h->status;
     q.alpha = prob->alpha;
     q.n0 = N_int;
     q.n1 = N_bnd;
@@ -715,14 +716,14 @@ int hrkan_init(hrkan_t* out, const hrkan_cfg* cfg) {
         (e = cudaMalloc(&h->m1, size_t(h->P) * cfg->n_instances * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&h->m2, size_t(h->P) * cfg->n_instances * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&h->t_counter, 2 * sizeof(int))) != cudaSuccess ||
-        (e = cudaMalloc(&h->status, sizeof(int))) != cudaSuccess) {
+        (e = cudaMalloc(&h->status, 4 * sizeof(int))) != cudaSuccess) {
         hrkan_destroy(h);
         return fail(HRKAN_ENOMEM, "cudaMalloc of the workspace: %s", cudaGetErrorString(e));
     }
     if ((e = cudaMemset(h->m1, 0, size_t(h->P) * cfg->n_instances * sizeof(double))) != cudaSuccess ||
         (e = cudaMemset(h->m2, 0, size_t(h->P) * cfg->n_instances * sizeof(double))) != cudaSuccess ||
         (e = cudaMemset(h->t_counter, 0, 2 * sizeof(int))) != cudaSuccess ||
-        (e = cudaMemset(h->status, 0, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(h->status, 0, 4 * sizeof(int))) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess) {
         hrkan_destroy(h);
         return cuda_fail(e, "zeroing the Adam moments");
@@ -835,6 +836,7 @@ int pinn_residual_loss(hrkan_t h, const pinn_problem* prob, const float* x_int, 
     q.loss_partial = h->loss_partial;
     q.Gl = (int)grid;
     q.loss = loss;
+    q.status = h->status;
     q.alpha = prob->alpha;
     q.n0 = N_int;
     q.n1 = N_bnd;
@@ -1062,6 +1064,7 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
     q.loss_partial = h->loss_partial;
     q.Gl = grid;
     q.loss = loss;
+    q.status = h->status;
     q.alpha = prob->alpha;
     q.n0 = N_int;
     q.n1 = N_bnd;
@@ -1145,6 +1148,7 @@ int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, con
     q.loss_partial = b.loss_partial;
     q.counts = b.counts;
     q.loss = loss;
+    q.status = h->status;
     q.dW = dW;
     q.alpha = probs[0].alpha;
     {
@@ -1256,8 +1260,19 @@ int hrkan_sync_status(hrkan_t h) {
     HR_CUDA(cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
     if (st != 0) {
         HR_CUDA(cudaMemset(h->status, 0, sizeof(int)), "status reset");
-        return fail(st, "a device-side wait gave up (status %d)", st);
+        return fail(st, st == HRKAN_ENONFINITE ? "a loss became NaN or infinite (status %d)"
+                                               : "a device-side wait gave up (status %d)", st);
     }
+    return HRKAN_OK;
+}
+
+int hrkan_set_wait_cycles(hrkan_t h, int64_t cycles) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (cycles < 0) return fail(HRKAN_EINVAL, "cycles=%lld", (long long)cycles);
+    if (int rc = use_device(h)) return rc;
+    const long long w = cycles;
+    HR_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    HR_CUDA(cudaMemcpy(h->status + 2, &w, sizeof w, cudaMemcpyHostToDevice), "wait limit write");
     return HRKAN_OK;
 }
 

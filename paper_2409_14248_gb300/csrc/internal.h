@@ -45,6 +45,7 @@ struct ReduceParams {
     double* loss;                     // [3]
     double alpha;
     int64_t n0, n1;
+    int* status;                      // optional device error word: HRKAN_ENONFINITE for a non-finite loss
 };
 cudaError_t launch_reduce(const ReduceParams& p, cudaStream_t s);
 
@@ -65,6 +66,7 @@ struct BatchReduceParams {
     double* loss;                // [n_inst][3]
     float* dW;                   // optional [n_inst][P]
     double alpha;
+    int* status;                 // optional device error word: HRKAN_ENONFINITE for a non-finite loss
 };
 cudaError_t launch_batch_reduce(const BatchReduceParams& p, cudaStream_t s);
 

@@ -7,6 +7,7 @@
 // fixed-order pairwise float64 tree.
 #include <algorithm>
 
+#include "../../include/hrkan.h"
 #include "internal.h"
 
 namespace hrkan {
@@ -109,6 +110,8 @@ __global__ void __launch_bounds__(RED_LANES * RED_WARPS) reduce_kernel(ReducePar
             p.loss[0] = p.alpha * lp + lb;
             p.loss[1] = lp;
             p.loss[2] = lb;
+            // a non-finite loss (NaN or infinite inputs, a diverged run) is recorded for hrkan_sync_status
+            if (p.status && !isfinite(p.alpha * lp + lb)) atomicCAS(p.status, 0, int(HRKAN_ENONFINITE));
         }
     }
 }
@@ -233,6 +236,7 @@ __global__ void __launch_bounds__(RED_LANES * RED_WARPS) batch_reduce_kernel(Bat
             p.loss[3 * inst] = p.alpha * lp + lb;
             p.loss[3 * inst + 1] = lp;
             p.loss[3 * inst + 2] = lb;
+            if (p.status && !isfinite(p.alpha * lp + lb)) atomicCAS(p.status, 0, int(HRKAN_ENONFINITE));
         }
     }
 }

@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
     volatile int* abort = &abort_sh;
+    const long long wl = tck::wait_limit(p.status);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int O = p.O, I = p.I;
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int r = 0; r < J; ++r, ++q) {
                 const int b = q & 1;
-                if (!__all_sync(0xffffffffu, mbar_wait(&bar_dfull[b], uint32_t(q >> 1) & 1u, abort))) goto done;
+                if (!__all_sync(0xffffffffu, mbar_wait(&bar_dfull[b], uint32_t(q >> 1) & 1u, abort, wl))) goto done;
                 tc_fence_after();
                 const uint32_t col0 = uint32_t(b * NC + half * UH * NP);
 #pragma unroll
@@ -224,14 +225,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
                                    (uint32_t(NC >> 3) << 17) | (uint32_t(TILE >> 4) << 24);
             bool issued = false;
-            if (mbar_wait(&bar_wfull, 0u, abort)) {
+            if (mbar_wait(&bar_wfull, 0u, abort, wl)) {
                 tc_fence_after();
                 const uint32_t wbase = smem_u32(wtile);
                 const int total = nt * J;
                 for (int q = 0; q < total; ++q) {
                     const int gb = q % NSB, db = q & 1;
-                    if (!mbar_wait(&bar_gfull[gb], uint32_t(q / NSB) & 1u, abort)) break;
-                    if (!mbar_wait(&bar_dempty[db], (uint32_t(q >> 1) & 1u) ^ 1u, abort)) break;
+                    if (!mbar_wait(&bar_gfull[gb], uint32_t(q / NSB) & 1u, abort, wl)) break;
+                    if (!mbar_wait(&bar_dempty[db], (uint32_t(q >> 1) & 1u) ^ 1u, abort, wl)) break;
                     tc_fence_after();
                     const uint32_t gbase = smem_u32(gring + size_t(gb) * g_bytes);
                     for (int s = 0; s < O / 16; ++s) {
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int q = 0; q < total; ++q) {
                 const int b = q % NSB, ti = q / J, r = q % J;
                 const uint32_t ph = uint32_t(q / NSB) & 1u;
-                if (!mbar_wait(&bar_gempty[b], ph ^ 1u, abort)) break;
+                if (!mbar_wait(&bar_gempty[b], ph ^ 1u, abort, wl)) break;
                 mbar_expect_tx(&bar_gfull[b], g_bytes);
                 uint8_t* dst = gring + size_t(b) * g_bytes;
                 const int x = (t0 + ti) * TILE;

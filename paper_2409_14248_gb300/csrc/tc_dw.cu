@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
     volatile int* abort = &abort_sh;
+    const long long wl = tck::wait_limit(p.status);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int O = p.O, I = p.I;
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
             for (int r = 0; r < J; ++r) {
                 const int b = (q + r) % NSB;
                 const uint32_t ph = uint32_t((q + r) / NSB) & 1u;
-                ok = ok && mbar_wait(&bar_empty[b], ph ^ 1u, abort);
+                ok = ok && mbar_wait(&bar_empty[b], ph ^ 1u, abort, wl);
             }
             if (!__all_sync(0xffffffffu, ok)) goto done;
 #pragma unroll
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
         }
         // ---- epilogue: D (lanes = k of the range) -> partial row
         if (ng > 0) {
-            if (!__all_sync(0xffffffffu, mbar_wait(&bar_accfull, 0u, abort))) goto done;
+            if (!__all_sync(0xffffffffu, mbar_wait(&bar_accfull, 0u, abort, wl))) goto done;
         }
         tc_fence_after();
         {
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
             const int total = ng * J;
             for (int q = 0; q < total; ++q) {
                 const int b = q % NSB;
-                if (!mbar_wait(&bar_full[b], uint32_t(q / NSB) & 1u, abort)) break;
+                if (!mbar_wait(&bar_full[b], uint32_t(q / NSB) & 1u, abort, wl)) break;
                 tc_fence_after();
                 const uint32_t abase = smem_u32(smem + size_t(b) * buf_bytes);
                 const uint64_t bd = sdesc(abase + A_BYTES, 16, 1024);
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
             for (int q = 0; q < total; ++q) {
                 const int b = q % NSB, gi = q / J, r = q % J;
                 const uint32_t ph = uint32_t(q / NSB) & 1u;
-                if (!mbar_wait(&bar_empty[b], ph ^ 1u, abort)) break;
+                if (!mbar_wait(&bar_empty[b], ph ^ 1u, abort, wl)) break;
                 mbar_expect_tx(&bar_full[b], b_bytes);
                 tck::tma_load_2d(smem + size_t(b) * buf_bytes + A_BYTES, &gmap, &bar_full[b], (g0 + gi) * GROUP,
                                  r * O);

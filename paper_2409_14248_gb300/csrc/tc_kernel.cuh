@@ -74,20 +74,30 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Wait for the phase of the given parity.  Gives up (false) after WAIT_CYCLES,
-// raising *abort, or as soon as *abort is raised by another thread.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+// Wait for the phase of the given parity.  Gives up (false) after `limit`
+// cycles, raising *abort, or as soon as *abort is raised by another thread.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                          long long limit = WAIT_CYCLES) {
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_test(bar, parity)) {
         if (*abort) return false;
-        if (clock64() - t0 > WAIT_CYCLES) {
+        if (clock64() - t0 > limit) {
             *abort = 1;
             return false;
         }
     }
     return true;
 }
+// The handle's device status block is int[4]: [0] the error word the kernels
+// set, [2..3] the limit of their waits in clock cycles (int64; 0 = WAIT_CYCLES).
+// A small limit makes the waits give up early (fault-injection tests); the
+// drains on the way out keep WAIT_CYCLES.
+__device__ __forceinline__ long long wait_limit(const int* status) {
+    const long long w = *reinterpret_cast<const volatile long long*>(status + 2);
+    return w > 0 ? w : WAIT_CYCLES;
+}
+
 // Bounded wait that ignores *abort (draining own work on the way out).
 __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
     const long long t0 = clock64();
@@ -318,6 +328,7 @@ __device__ __forceinline__ void produce(const TcLayer& p, TcShared& sh, uint32_t
     constexpr int HU = PU / PARTS;   // units of this warp per period: u = PARTS * i + PART
     using Win = UnitWin<J>;
     volatile int* abort = &sh.abort;
+    const long long wl = wait_limit(p.status);
     const int O = p.O, I = p.I, RS = p.ring, KS = p.ks;
     const int64_t N = p.N;
     const int ntiles = p.ntiles;
@@ -401,7 +412,7 @@ __device__ __forceinline__ void produce(const TcLayer& p, TcShared& sh, uint32_t
                         __syncwarp();
                         mbar_arrive_if(&sh.full[pend_slot], lane == 0);
                     }
-                    if (!__all_sync(0xffffffffu, mbar_wait(&sh.empty[slot], ph ^ 1u, abort))) return;
+                    if (!__all_sync(0xffffffffu, mbar_wait(&sh.empty[slot], ph ^ 1u, abort, wl))) return;
                     tc_fence_after();
                     const uint32_t col = tbase + lane_base + A0 + uint32_t(slot * 8);
 #define OWN(w) ((((S * 8 + (w)) / NW) % PARTS) == PART)
@@ -437,7 +448,7 @@ __device__ __forceinline__ void produce(const TcLayer& p, TcShared& sh, uint32_t
             pend_slot = -1;
         }
         // ---- epilogue: this warp's jet rows of the accumulators -> y [J][O][N]
-        if (!__all_sync(0xffffffffu, mbar_wait(&sh.accfull, uint32_t(it & 1), abort))) return;
+        if (!__all_sync(0xffffffffu, mbar_wait(&sh.accfull, uint32_t(it & 1), abort, wl))) return;
         tc_fence_after();
 #pragma unroll 1
         for (int r = PART; r < J; r += PARTS) {
@@ -485,6 +496,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_fwd_kernel(TcLayer p, const __g
     const uint32_t A0 = uint32_t(J * O);            // first A column; accumulators at r * O
     const uint32_t RW = uint32_t(RS * 8);           // ring words per jet row
     volatile int* abort = &sh.abort;
+    const long long wl = wait_limit(p.status);
 
     if (tid == 0) {
         for (int s = 0; s < RS_MAX; ++s) {
@@ -524,15 +536,15 @@ __global__ void __launch_bounds__(THREADS, 1) tc_fwd_kernel(TcLayer p, const __g
             bool issued = false;
             int it = 0;
             for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-                if (!mbar_wait(&sh.accempty, uint32_t(it & 1) ^ 1u, abort)) break;
+                if (!mbar_wait(&sh.accempty, uint32_t(it & 1) ^ 1u, abort, wl)) break;
                 tc_fence_after();
                 uint64_t bd = 0;
                 for (int t = 0; t < KS; ++t) {
                     if ((t & 3) == 0) {
-                        if (!mbar_wait(&sh.wfull[wb], wph, abort)) goto mma_out;
+                        if (!mbar_wait(&sh.wfull[wb], wph, abort, wl)) goto mma_out;
                         bd = sdesc_sw128(smem_u32(smem + size_t(wb) * b_bytes));
                     }
-                    if (!mbar_wait(&sh.full[slot], ph, abort)) goto mma_out;
+                    if (!mbar_wait(&sh.full[slot], ph, abort, wl)) goto mma_out;
                     tc_fence_after();
 #pragma unroll
                     for (int r = 0; r < J; ++r)
@@ -564,7 +576,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_fwd_kernel(TcLayer p, const __g
             uint32_t used = 0u, last_par = 0u;   // bit b: buffer b has had a load / parity of its last one
             for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
                 for (int bx = 0; bx < nbox; ++bx) {
-                    if (!mbar_wait(&sh.wempty[wb], wph ^ 1u, abort)) goto tma_out;
+                    if (!mbar_wait(&sh.wempty[wb], wph ^ 1u, abort, wl)) goto tma_out;
                     mbar_expect_tx(&sh.wfull[wb], b_bytes);
                     tma_load_2d(smem + size_t(wb) * b_bytes, &tmap, &sh.wfull[wb], bx * E::BOX, 0);
                     used |= 1u << wb;
