@@ -35,3 +35,18 @@ def test_hr_basis_beats_square_of_relu_on_the_poisson_experiment():
     assert min(r["test_mse"] for r in hr["runs"]) * 100.0 < 0.1
     # every run trains: the loss ends 10x below its starting value (about alpha * mean f^2 = 0.05 pi^4 = 4.9)
     assert all(r["train_loss"] < 0.49 for r in hr["runs"])
+
+
+@pytest.mark.gpu
+def test_burgers_experiment_trains_to_the_papers_error_level():
+    """The Burgers experiment (Section 4.2, Eq. 7-8, [2,3,3,3,1], g = 7, 3000 epochs) for 4 seeds at
+    lr 1e-2.  The FP64 oracle, run on the same sets and initial weights, ends at test MSE 0.088-0.156 %
+    (mean 0.119 %; the paper's HRKAN mean is 0.229 %) and training loss 2e-5 to 1.3e-4; FP32 runs
+    follow other trajectories, so the bounds are medians with a margin of 2.5x and more."""
+    pytest.importorskip("torch")
+    build.build()
+    capi.load_library()
+    t = replica.burgers_table(runs=4, m=4, lr=1e-2)
+    assert t["median_mse_pct"] < 0.3, t
+    assert np.median([r["train_loss"] for r in t["runs"]]) < 1e-3, t
+    assert all(np.isfinite(r["test_mse"]) for r in t["runs"])
