@@ -164,6 +164,22 @@ def emit(obj):
     print(json.dumps(obj), flush=True)
 
 
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest of one float per rank (the job takes as long as its slowest rank)."""
+    if ws == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ws: int, steps: int, units_per_step: int, seconds: float) -> float:
+    """Units all ranks processed per second: every rank trains its own replica of the whole
+    workload (weak scaling), over the slowest rank's time."""
+    return ws * steps * units_per_step / seconds
+
+
 # --------------------------------------------------------------- reference
 
 
@@ -328,14 +344,14 @@ def run_ours(args, ws, rank, local):
     sampler.start()
     time.sleep(0.3)
     total_ms = time_steps(torch, capi, h, step, args.warmup + 1, args.steps, flush)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
     clocks = sampler.stop()
     capi.hrkan_profile_enable(h, False)
     prof = {c: capi.hrkan_profile_read(h, c) for c in range(5)}
     fused = prof[capi.HRKAN_KERNEL_FUSED][1] > 0 and prof[capi.HRKAN_KERNEL_FORWARD][1] == 0
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, ws, "cuda")
 
     # end to end through the C ABI with host buffers: H2D of the inputs, the step, D2H of the loss
     pin = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32).pin_memory()
@@ -352,10 +368,7 @@ def run_ours(args, ws, rank, local):
         hloss.copy_(loss, non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, ws, "cuda")
     h2d = (hxi.numel() + hxb.numel() + hgb.numel()) * 4
     capi.hrkan_destroy(h)
 
@@ -369,9 +382,9 @@ def run_ours(args, ws, rank, local):
             step32(t)
         torch.cuda.synchronize()
         k32 = max(3, min(args.steps, 20))
-        ms32 = time_steps(torch, capi, h32, step32, 4, k32, flush)
+        ms32 = max_over_ranks(time_steps(torch, capi, h32, step32, 4, k32, flush), ws, "cuda")
         capi.hrkan_destroy(h32)
-        fp32_path = {"value": ws * k32 * pts / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32 / k32,
+        fp32_path = {"value": job_throughput(ws, k32, pts, ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32 / k32,
                      "steps": k32}
 
     if rank == 0:
@@ -417,7 +430,8 @@ def run_ours(args, ws, rank, local):
                         "flops_per_step": flops, "peak_source": ("bf16 dense sustained " if prec == PRECS["bf16"]
                                                                  else "bf16 dense sustained x 0.5 (tf32) ")
                         + pk["source"]}
-        out = {"metric": METRIC, "value": ws * args.steps * pts / (total_ms / 1e3), "unit": UNIT, "n_gpus": ws,
+        out = {"metric": METRIC, "value": job_throughput(ws, args.steps, pts, total_ms / 1e3), "unit": UNIT,
+               "n_gpus": ws,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
                "data": "synthetic",
@@ -426,7 +440,7 @@ def run_ours(args, ws, rank, local):
                           "parallelism": "replicas" if ws > 1 else "single",
                           "l2": "flushed before every timed step (256 MiB device write, outside the step events)"},
                "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
-               "e2e": {"value": ws * e2e_steps * pts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "e2e": {"value": job_throughput(ws, e2e_steps, pts, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": 24}}
         if fp32_path is not None:
             out["fp32_path"] = fp32_path
