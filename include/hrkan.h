@@ -292,13 +292,17 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
  * uploaded only when the offsets or problems change (that call synchronises
  * the stream); calls with unchanged arguments only enqueue the two kernels, so
  * they can be captured in a CUDA graph after one warm-up call.
+ * HRKAN_EUNSUPPORTED on a handle without a fused shape ([2,W,1] or
+ * [2,W,W,1], W in 5, 10, 16; m = 4; not HRKAN_FLAG_LAYERWISE), and for a
+ * problem kind whose residual needs third derivatives.
  */
 int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, const float* x_int,
                              const int64_t* off_int, const float* x_bnd, const float* g_bnd,
                              const int64_t* off_bnd, double lr, double b1, double b2, double eps, int t,
                              double* loss, float* dW, hrkan_stream_t stream);
 
-/* Output jets of every instance at its points (x [2][N], offsets host [I+1], jets [J][N]). */
+/* Output jets of every instance at its points (x [2][N], offsets host [I+1], jets [J][N]);
+ * the same handle requirement as hrkan_train_step_batched. */
 int hrkan_forward_jets_batched(hrkan_t h, const float* W, const float* x, const int64_t* offsets,
                                unsigned jet_mask, float* jets, hrkan_stream_t stream);
 

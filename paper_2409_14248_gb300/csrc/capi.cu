@@ -42,7 +42,7 @@ struct hrkan_ctx {
         std::vector<int64_t> off0, off1;
         std::vector<double> ab;
         int items_points = 0;
-        int n_items = 0, cap_items = 0, n_inst = 0;
+        int n_items = 0, cap_items = 0, n_inst = 0, cap_inst = 0;
         BatchItem* items = nullptr;
         BatchInst* inst = nullptr;
         int* item_off = nullptr;
@@ -169,7 +169,10 @@ struct ProfScope {
         if (!h->pool.empty()) {
             ev = h->pool.back();
             h->pool.pop_back();
-        } else if (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess) {
+        } else if (cudaEventCreate(&ev.a) != cudaSuccess) {
+            return;
+        } else if (cudaEventCreate(&ev.b) != cudaSuccess) {
+            cudaEventDestroy(ev.a);
             return;
         }
         ev.cls = cls;
@@ -221,6 +224,13 @@ int build_batch(hrkan_t h, hrkan_ctx::Batch& b, int n_inst, const pinn_problem* 
         cudaError_t se = cudaStreamSynchronize(stream);
         if (se != cudaSuccess) return cuda_fail(se, "cudaStreamSynchronize before rebuilding the work list");
     }
+    // forget the cached key first: if the rebuild fails part-way, no later call may reuse the old list
+    b.off0.clear();
+    b.off1.clear();
+    b.ab.clear();
+    b.items_points = 0;
+    b.n_items = 0;
+    b.n_inst = 0;
     std::vector<BatchItem> items;
     std::vector<BatchInst> inst(n_inst);
     std::vector<int> item_off(n_inst + 1, 0);
@@ -243,7 +253,7 @@ int build_batch(hrkan_t h, hrkan_ctx::Batch& b, int n_inst, const pinn_problem* 
     item_off[n_inst] = int(items.size());
     const int n_items = int(items.size());
     cudaError_t e;
-    if (n_items > b.cap_items || n_inst > b.n_inst || !b.inst) {
+    if (n_items > b.cap_items || n_inst > b.cap_inst || !b.inst) {
         cudaFree(b.items); cudaFree(b.loss_partial); cudaFree(b.inst); cudaFree(b.item_off); cudaFree(b.counts);
         b.items = nullptr; b.loss_partial = nullptr; b.inst = nullptr; b.item_off = nullptr; b.counts = nullptr;
         const int cap = std::max(n_items, 1);
@@ -253,10 +263,11 @@ int build_batch(hrkan_t h, hrkan_ctx::Batch& b, int n_inst, const pinn_problem* 
             (e = cudaMalloc(&b.item_off, sizeof(int) * (n_inst + 1))) != cudaSuccess ||
             (e = cudaMalloc(&b.counts, sizeof(float) * 2 * std::max(n_inst, 1))) != cudaSuccess) {
             b.cap_items = 0;
-            b.n_inst = 0;
+            b.cap_inst = 0;
             return fail(HRKAN_ENOMEM, "cudaMalloc of the work list: %s", cudaGetErrorString(e));
         }
         b.cap_items = cap;
+        b.cap_inst = std::max(n_inst, 1);
     }
     if (train && size_t(n_items) * size_t(h->P) > b.partial_cap) {
         cudaFree(b.partial);
@@ -992,15 +1003,20 @@ int hrkan_profile_read(hrkan_t h, int kernel_class, double* total_ms, int64_t* l
     if (kernel_class < 0 || kernel_class >= HRKAN_KERNEL_CLASSES)
         return fail(HRKAN_EINVAL, "kernel class %d", kernel_class);
     if (int rc = use_device(h)) return rc;
-    for (auto& ev : h->pending) {
+    size_t done = 0;
+    cudaError_t e = cudaSuccess;
+    for (; done < h->pending.size(); ++done) {
+        const auto& ev = h->pending[done];
         float ms = 0.0f;
-        HR_CUDA(cudaEventSynchronize(ev.b), "cudaEventSynchronize");
-        HR_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b), "cudaEventElapsedTime");
+        if ((e = cudaEventSynchronize(ev.b)) != cudaSuccess || (e = cudaEventElapsedTime(&ms, ev.a, ev.b)) != cudaSuccess)
+            break;
         h->prof_ms[ev.cls] += ms;
         h->prof_n[ev.cls] += 1;
         h->pool.push_back(ev);
     }
-    h->pending.clear();
+    // events already counted leave the pending list even when a later one fails
+    h->pending.erase(h->pending.begin(), h->pending.begin() + done);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel timing events");
     if (total_ms) *total_ms = h->prof_ms[kernel_class];
     if (launches) *launches = h->prof_n[kernel_class];
     if (reset) {
@@ -1088,6 +1104,8 @@ int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, con
                              double lr, double b1, double b2, double eps, int t, double* loss, float* dW,
                              hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (h->net_id < 0)
+        return fail(HRKAN_EUNSUPPORTED, "multi-instance calls need a fused shape ([2,W,1] or [2,W,W,1], W in 5,10,16)");
     const int n_inst = h->cfg.n_instances;
     if (!probs || !off_int || !off_bnd) return fail(HRKAN_EINVAL, "NULL host array");
     for (int i = 0; i < n_inst; ++i) {
@@ -1223,6 +1241,8 @@ int hrkan_autotune_batch(hrkan_t h, const pinn_problem* probs, float* W, const f
 int hrkan_forward_jets_batched(hrkan_t h, const float* W, const float* x, const int64_t* offsets, unsigned jet_mask,
                                float* jets, hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (h->net_id < 0)
+        return fail(HRKAN_EUNSUPPORTED, "multi-instance calls need a fused shape ([2,W,1] or [2,W,W,1], W in 5,10,16)");
     if (!offsets) return fail(HRKAN_EINVAL, "offsets is NULL");
     if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
     const int n_inst = h->cfg.n_instances;

@@ -212,6 +212,28 @@ def test_batched_rejects_inconsistent_problems():
         capi.hrkan_destroy(h)
 
 
+
+def test_batched_calls_refuse_a_handle_without_a_fused_shape():
+    """A layer-wise handle (one instance) has no multi-instance kernels: both batched calls return
+    HRKAN_EUNSUPPORTED before any work list is built."""
+    h = capi.hrkan_init(capi.make_cfg([2, 16, 16, 1], 10, flags=capi.HRKAN_FLAG_LAYERWISE))
+    try:
+        P = capi.hrkan_param_count(capi.make_cfg([2, 16, 16, 1], 10))
+        W = torch.zeros(P, device="cuda")
+        x = torch.zeros((2, 64), device="cuda")
+        off = np.array([0, 64], dtype=np.int64)
+        probs = [capi.make_problem(capi.HRKAN_POISSON, 1, 1)]
+        loss = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
+        with pytest.raises(capi.HRKANError) as ei:
+            capi.hrkan_train_step_batched(h, probs, W, x, off, x, torch.zeros(64, device="cuda"), off, 1e-2, 0.9,
+                                          0.999, 1e-8, 1, loss)
+        assert ei.value.code == capi.HRKAN_EUNSUPPORTED
+        with pytest.raises(capi.HRKANError) as ei:
+            capi.hrkan_forward_jets_batched(h, W, x, off, 0x1F, torch.zeros((5, 64), device="cuda"))
+        assert ei.value.code == capi.HRKAN_EUNSUPPORTED
+    finally:
+        capi.hrkan_destroy(h)
+
 def test_autotune_picks_a_candidate_and_leaves_weights_and_moments_fresh():
     """hrkan_autotune_batch times each item size with lr = 0 (W keeps its values), keeps the
     fastest and resets the Adam state: the next step equals a fresh handle's step."""
