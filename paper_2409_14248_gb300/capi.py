@@ -159,10 +159,46 @@ def hrkan_param_count(cfg):
     return int(load_library().hrkan_param_count(ctypes.byref(cfg)))
 
 
+class Handle(ctypes.c_void_p):
+    """An hrkan_t together with the network shape.  The C ABI sees bare pointers, so the
+    wrappers below check each tensor's element count against what the call reads or writes
+    and raise HRKANError(HRKAN_EINVAL) before a short buffer reaches a kernel."""
+
+
 def hrkan_init(cfg):
-    h = ctypes.c_void_p()
+    h = Handle()
     _check(load_library().hrkan_init(ctypes.byref(h), ctypes.byref(cfg)))
+    h.widths = [int(cfg.widths[i]) for i in range(cfg.n_widths)]
+    h.D = h.widths[0]
+    h.n = int(cfg.G) + int(cfg.k)
+    h.P = hrkan_param_count(cfg)
+    h.n_inst = int(cfg.n_instances)
     return h
+
+
+def _jets(mask):
+    return bin(int(mask) & 0xFF).count("1")
+
+
+def _need(t, n, what):
+    """Raise unless tensor (or array) t is absent or holds at least n elements."""
+    if t is not None and t.numel() < n:
+        raise HRKANError(HRKAN_EINVAL, f"{what} holds {t.numel()} elements, the call needs {n}")
+
+
+def _shaped(h):
+    return getattr(h, "P", None) is not None
+
+
+def _layer_in(h, layer, J, N):
+    """Floats of a single-layer call's input: jets [J][I][N], for layer 0 the coordinates [2][N]."""
+    return 2 * N if int(layer) == 0 else J * h.widths[int(layer)] * N
+
+
+def _layer_io(h, layer):
+    """(I, O) of layer `layer`, or None when the index is out of range (the library reports it)."""
+    L = len(h.widths) - 1
+    return (h.widths[layer], h.widths[layer + 1]) if 0 <= int(layer) < L else None
 
 
 def hrkan_destroy(h):
@@ -175,6 +211,12 @@ def hrkan_tape_floats(h, N, jet_mask):
 
 def hrkan_forward_jets(h, W, x, N, jet_mask, jets, tape=None, stream=None):
     import torch
+    if _shaped(h) and N > 0:
+        _need(W, h.P, "W")
+        _need(x, h.D * N, "x")
+        _need(jets, _jets(jet_mask) * N, "jets")
+        if tape is not None:
+            _need(tape, hrkan_tape_floats(h, N, jet_mask), "tape")
     _check(load_library().hrkan_forward_jets(h, _ptr(W, torch.float32), _ptr(x, torch.float32), int(N),
                                              int(jet_mask), _ptr(jets, torch.float32), _ptr(tape, torch.float32),
                                              _stream(stream)))
@@ -184,6 +226,17 @@ def pinn_residual_loss(h, prob, x_int, N_int, jet_mask, jets_int, u_bnd, g_bnd, 
                        dL_du_bnd=None, stream=None):
     import torch
     f = torch.float32
+    if _shaped(h):
+        J = _jets(jet_mask)
+        _need(loss, 3, "loss")
+        if N_int > 0:
+            _need(x_int, 2 * N_int, "x_int")
+            _need(jets_int, J * N_int, "jets_int")
+            _need(dL_djets_int, J * N_int, "dL_djets_int")
+        if N_bnd > 0:
+            _need(u_bnd, N_bnd, "u_bnd")
+            _need(g_bnd, N_bnd, "g_bnd")
+            _need(dL_du_bnd, N_bnd, "dL_du_bnd")
     _check(load_library().pinn_residual_loss(h, ctypes.byref(prob), _ptr(x_int, f), int(N_int), int(jet_mask),
                                              _ptr(jets_int, f), _ptr(u_bnd, f), _ptr(g_bnd, f), int(N_bnd),
                                              _ptr(loss, torch.float64), _ptr(dL_djets_int, f), _ptr(dL_du_bnd, f),
@@ -193,12 +246,23 @@ def pinn_residual_loss(h, prob, x_int, N_int, jet_mask, jets_int, u_bnd, g_bnd, 
 def hrkan_backward(h, W, x, N, jet_mask, tape, dL_djets, dW, accumulate=False, stream=None):
     import torch
     f = torch.float32
+    if _shaped(h):
+        _need(dW, h.P, "dW")
+        if N > 0:
+            _need(W, h.P, "W")
+            _need(x, h.D * N, "x")
+            _need(dL_djets, _jets(jet_mask) * N, "dL_djets")
+            if tape is not None:
+                _need(tape, hrkan_tape_floats(h, N, jet_mask), "tape")
     _check(load_library().hrkan_backward(h, _ptr(W, f), _ptr(x, f), int(N), int(jet_mask), _ptr(tape, f),
                                          _ptr(dL_djets, f), _ptr(dW, f), int(bool(accumulate)), _stream(stream)))
 
 
 def adam_step(h, W, dW, lr, b1=0.9, b2=0.999, eps=1e-8, t=1, stream=None):
     import torch
+    if _shaped(h):
+        _need(W, h.P, "W")
+        _need(dW, h.P, "dW")
     _check(load_library().adam_step(h, _ptr(W, torch.float32), _ptr(dW, torch.float32), float(lr), float(b1),
                                     float(b2), float(eps), int(t), _stream(stream)))
 
@@ -244,6 +308,8 @@ def hrkan_checkpoint_read(path, P, n_instances):
 def hrkan_save(h, W, t, path, stream=None):
     """Save the weights (device tensor), the handle's Adam moments and step counts."""
     import torch
+    if _shaped(h):
+        _need(W, h.n_inst * h.P, "W")
     _check(load_library().hrkan_save(h, _ptr(W, torch.float32), ctypes.c_int64(int(t)), os.fsencode(path),
                                      _stream(stream)))
 
@@ -251,6 +317,8 @@ def hrkan_save(h, W, t, path, stream=None):
 def hrkan_load(h, W, path, stream=None):
     """Load a checkpoint into W (device tensor) and the handle; returns the stored step count t."""
     import torch
+    if _shaped(h):
+        _need(W, h.n_inst * h.P, "W")
     t = ctypes.c_int64(0)
     _check(load_library().hrkan_load(h, _ptr(W, torch.float32), ctypes.byref(t), os.fsencode(path), _stream(stream)))
     return t.value
@@ -260,6 +328,15 @@ def hrkan_train_step(h, prob, W, x_int, N_int, x_bnd, g_bnd, N_bnd, lr, b1, b2, 
                      stream=None):
     import torch
     f = torch.float32
+    if _shaped(h):
+        _need(W, h.P, "W")
+        _need(dW, h.P, "dW")
+        _need(loss, 3, "loss")
+        if N_int > 0:
+            _need(x_int, 2 * N_int, "x_int")
+        if N_bnd > 0:
+            _need(x_bnd, 2 * N_bnd, "x_bnd")
+            _need(g_bnd, N_bnd, "g_bnd")
     _check(load_library().hrkan_train_step(h, ctypes.byref(prob), _ptr(W, f), _ptr(x_int, f), int(N_int),
                                            _ptr(x_bnd, f), _ptr(g_bnd, f), int(N_bnd), float(lr), float(b1),
                                            float(b2), float(eps), int(t), _ptr(loss, torch.float64),
@@ -292,6 +369,30 @@ def _i64_array(a):
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
 
 
+def _batch_sizes(h, probs, offsets, what):
+    """The library reads n_instances problems and n_instances + 1 offsets from host memory."""
+    I = h.n_inst
+    if probs is not None and len(probs) < I:
+        raise HRKANError(HRKAN_EINVAL, f"{len(probs)} problems for {I} instances")
+    for name, off in zip(what, offsets):
+        if len(off) < I + 1:
+            raise HRKANError(HRKAN_EINVAL, f"{name} has {len(off)} entries, {I + 1} are needed")
+
+
+def _check_batched_train(h, probs, W, x_int, oi, x_bnd, g_bnd, ob, loss, dW):
+    _batch_sizes(h, probs, (oi, ob), ("off_int", "off_bnd"))
+    I = h.n_inst
+    n0, n1 = int(oi[I]), int(ob[I])
+    _need(W, I * h.P, "W")
+    _need(dW, I * h.P, "dW")
+    _need(loss, 3 * I, "loss")
+    if n0 > 0:
+        _need(x_int, 2 * n0, "x_int")
+    if n1 > 0:
+        _need(x_bnd, 2 * n1, "x_bnd")
+        _need(g_bnd, n1, "g_bnd")
+
+
 def hrkan_train_step_batched(h, probs, W, x_int, off_int, x_bnd, g_bnd, off_bnd, lr, b1, b2, eps, t, loss,
                              dW=None, stream=None):
     """probs: sequence of pinn_problem (one per instance); offsets: host int arrays [I+1]."""
@@ -300,6 +401,8 @@ def hrkan_train_step_batched(h, probs, W, x_int, off_int, x_bnd, g_bnd, off_bnd,
     arr = (pinn_problem * len(probs))(*probs)
     oi, oip = _i64_array(off_int)
     ob, obp = _i64_array(off_bnd)
+    if _shaped(h):
+        _check_batched_train(h, probs, W, x_int, oi, x_bnd, g_bnd, ob, loss, dW)
     _check(load_library().hrkan_train_step_batched(h, arr, _ptr(W, f), _ptr(x_int, f), oip, _ptr(x_bnd, f),
                                                    _ptr(g_bnd, f), obp, float(lr), float(b1), float(b2), float(eps),
                                                    int(t), _ptr(loss, torch.float64), _ptr(dW, f), _stream(stream)))
@@ -309,6 +412,13 @@ def hrkan_forward_jets_batched(h, W, x, offsets, jet_mask, jets, stream=None):
     import torch
     f = torch.float32
     o, op = _i64_array(offsets)
+    if _shaped(h):
+        _batch_sizes(h, None, (o,), ("offsets",))
+        n = int(o[h.n_inst])
+        _need(W, h.n_inst * h.P, "W")
+        if n > 0:
+            _need(x, 2 * n, "x")
+            _need(jets, _jets(jet_mask) * n, "jets")
     _check(load_library().hrkan_forward_jets_batched(h, _ptr(W, f), _ptr(x, f), op, int(jet_mask), _ptr(jets, f),
                                                      _stream(stream)))
 
@@ -322,6 +432,8 @@ def hrkan_autotune_batch(h, probs, W, x_int, off_int, x_bnd, g_bnd, off_bnd, can
     arr = (pinn_problem * len(probs))(*probs)
     oi, oip = _i64_array(off_int)
     ob, obp = _i64_array(off_bnd)
+    if _shaped(h):
+        _check_batched_train(h, probs, W, x_int, oi, x_bnd, g_bnd, ob, None, None)
     cand = None if candidates is None else (ctypes.c_int * len(candidates))(*[int(c) for c in candidates])
     chosen, ms = ctypes.c_int(0), ctypes.c_double(0.0)
     _check(load_library().hrkan_autotune_batch(h, arr, _ptr(W, f), _ptr(x_int, f), oip, _ptr(x_bnd, f),
@@ -343,6 +455,14 @@ def hrkan_layer_dw(h, layer, z, gy, N, jet_mask, dW, stream=None):
     """Weight gradient [O][I][n] of one layer from input jets z [J][I][N] and gy [J][O][N]."""
     import torch
     f = torch.float32
+    io = _layer_io(h, layer) if _shaped(h) else None
+    if io is not None:
+        I, O = io
+        J = _jets(jet_mask)
+        _need(dW, O * I * h.n, "dW")
+        if N > 0:
+            _need(z, _layer_in(h, layer, J, N), "z")
+            _need(gy, J * O * N, "gy")
     _check(load_library().hrkan_layer_dw(h, int(layer), _ptr(z, f), _ptr(gy, f), int(N), int(jet_mask), _ptr(dW, f),
                                          _stream(stream)))
 
@@ -351,6 +471,14 @@ def hrkan_layer_adjoint(h, layer, W_layer, z, gy, N, jet_mask, gz, stream=None):
     """Input adjoint gz [J][I][N] of layer >= 1 from z [J][I][N] and gy [J][O][N]."""
     import torch
     f = torch.float32
+    io = _layer_io(h, layer) if _shaped(h) else None
+    if io is not None and N > 0:
+        I, O = io
+        J = _jets(jet_mask)
+        _need(W_layer, O * I * h.n, "W_layer")
+        _need(z, J * I * N, "z")
+        _need(gy, J * O * N, "gy")
+        _need(gz, J * I * N, "gz")
     _check(load_library().hrkan_layer_adjoint(h, int(layer), _ptr(W_layer, f), _ptr(z, f), _ptr(gy, f), int(N),
                                               int(jet_mask), _ptr(gz, f), _stream(stream)))
 
@@ -359,5 +487,12 @@ def hrkan_layer_jets(h, layer, W_layer, z, N, jet_mask, y, stream=None):
     """One layer on given input jets z [J][I][N] -> y [J][O][N]."""
     import torch
     f = torch.float32
+    io = _layer_io(h, layer) if _shaped(h) else None
+    if io is not None and N > 0:
+        I, O = io
+        J = _jets(jet_mask)
+        _need(W_layer, O * I * h.n, "W_layer")
+        _need(z, _layer_in(h, layer, J, N), "z")
+        _need(y, J * O * N, "y")
     _check(load_library().hrkan_layer_jets(h, int(layer), _ptr(W_layer, f), _ptr(z, f), int(N), int(jet_mask),
                                            _ptr(y, f), _stream(stream)))
