@@ -18,9 +18,9 @@ pooled boundary mean in the loss (Eq. 8) with alpha = 0.05; a [2,3,3,3,1]
 network with g = 7, k = 3; Adam for 3000 epochs; test set: the 200 x 200 grid.
 The paper's reference solution comes from a Fourier solver; here it is the
 Cole-Hopf solution of the same initial value problem on the whole line
-(`burgers_truth`).  At y = 0 and y = 2.5 it keeps the initial value's tail
-(sech 5 = 0.0135) instead of the Dirichlet zero, which moves the test MSE by
-about 2e-6 (0.0002 %).
+(`burgers_truth`, by truth.burgers_sech).  At y = 0 and y = 2.5 it keeps the
+initial value's tail (sech 5 = 0.0135) instead of the Dirichlet zero, which
+moves the test MSE by about 2e-6 (0.0002 %).
 
 The paper reports the mean and standard deviation of the test MSE over 10
 runs and the mean training time (Tables 1 and 2; the ReLU-KAN column is the
@@ -30,8 +30,7 @@ or the initial weights: they are parameters here (defaults lr = 1e-3, betas
 
 Every training step and the test-set forward run in libhrkan.so
 (hrkan_train_step on the layer-wise path for these widths, hrkan_forward_jets);
-torch only holds device memory.  The reference solution is plain numpy: it is
-the experiment's ground truth, not a step of the training path.
+torch only holds device memory.
 """
 from __future__ import annotations
 
@@ -40,7 +39,7 @@ import time
 
 import numpy as np
 
-from . import capi, inputs
+from . import capi, inputs, truth
 
 BURGERS_NU = 1e-3
 BURGERS_SIDE = 2.5
@@ -61,43 +60,9 @@ def poisson_sets(seed: int):
             x_test.astype(np.float32), u_test)
 
 
-def cole_hopf_sech(x, t, nu: float = BURGERS_NU, nodes: int = 3001):
-    """u(x, t) of u_t + u u_x = nu u_xx on the whole line with u(x, 0) = sech(x).
-
-    The Cole-Hopf substitution u = -2 nu (log phi)_x turns the equation into
-    the heat equation for phi, whose solution is a Gaussian average of
-    phi(., 0) = exp(-F / (2 nu)), F(s) = integral_0^s sech = atan(sinh s).  So
-        u(x, t) = <(x - s) / t>,  weights exp(-E(s)),
-        E(s) = F(s) / (2 nu) + (x - s)^2 / (4 nu t).
-    E has its minimum where s + t sech(s) = x (the characteristic through x),
-    so s in [x - t, x]; the average runs over s in [x - t - 12 sigma,
-    x + 12 sigma], sigma = sqrt(2 nu t), on `nodes` equally spaced nodes
-    (the weights there are below exp(-70)), shifted by min E so nothing
-    underflows.  t = 0 returns sech(x).
-    """
-    x, t = np.broadcast_arrays(np.asarray(x, np.float64), np.asarray(t, np.float64))
-    u = 1.0 / np.cosh(x)
-    pos = t > 0
-    xs, ts = x[pos], t[pos]
-    sig = np.sqrt(2.0 * nu * ts)
-    lo, hi = xs - ts - 12.0 * sig, xs + 12.0 * sig
-    frac = np.linspace(0.0, 1.0, nodes)
-    res = np.empty(xs.size)
-    chunk = max(1, (1 << 22) // nodes)
-    for a in range(0, xs.size, chunk):
-        sl = slice(a, a + chunk)
-        s = lo[sl, None] + (hi[sl] - lo[sl])[:, None] * frac[None, :]
-        d = xs[sl, None] - s
-        E = np.arctan(np.sinh(s)) / (2.0 * nu) + d * d / (4.0 * nu * ts[sl, None])
-        w = np.exp(-(E - E.min(axis=1, keepdims=True)))
-        res[sl] = (w * d).sum(axis=1) / (w.sum(axis=1) * ts[sl])
-    u[pos] = res
-    return u
-
-
 def burgers_truth(y, t, nu: float = BURGERS_NU):
     """Reference solution of the rescaled problem (Eq. 7) at (y, t) in [0, 2.5]^2: u(4y - 5, t)."""
-    return cole_hopf_sech(4.0 * np.asarray(y, np.float64) - 5.0, t, nu)
+    return truth.burgers_sech(4.0 * np.asarray(y, np.float64) - 5.0, t, nu)
 
 
 def burgers_sets(seed: int, n_test: int = 200):

@@ -4,8 +4,12 @@ Runs full-batch Adam steps (Section 4) of one workload through
 hrkan_train_step, and every `log_every` steps appends one JSON line:
 
     {"step": t, "loss": L, "loss_pde": L_pde, "loss_bnd": L_bnd,
-     "points_per_s": ..., "ms_per_step": ..., "test_rel_l2": ... (Poisson: against
-     the exact solution sin(a pi x) sin(b pi y) on a test grid; else null)}
+     "points_per_s": ..., "ms_per_step": ..., "test_rel_l2": ...}
+
+test_rel_l2 is the relative L2 error of u on a test grid against the exact
+solution: sin(a pi x) sin(b pi y) for Poisson; for Burgers with lam = 1 on
+x in [-1, 1], t in [0, 1] and u(x, 0) = -sin(pi x) the Cole-Hopf solution
+(truth.burgers_sine); null otherwise.
 
 `checkpoint_every` writes a checkpoint (hrkan_save: weights, Adam moments, step
 count) and `resume` continues from one, so an interrupted run can be restarted
@@ -19,7 +23,7 @@ import json
 
 import numpy as np
 
-from . import capi, inputs
+from . import capi, inputs, truth
 
 
 def _dev(a):
@@ -44,11 +48,17 @@ class Trainer:
         self.loss = torch.zeros(3, dtype=torch.float64, device="cuda")
         self.t = 0
         self.x_test = self.u_test = None
+        g = np.linspace(self.w.lo, self.w.hi, test_grid)
         if self.w.pde == inputs.POISSON:
-            g = np.linspace(self.w.lo, self.w.hi, test_grid)
             X, Y = np.meshgrid(g, g, indexing="ij")
-            self.x_test = _dev(np.stack([X.ravel(), Y.ravel()]))
-            self.u_test = np.sin(self.w.a * np.pi * X.ravel()) * np.sin(self.w.b * np.pi * Y.ravel())
+            pts = np.stack([X.ravel(), Y.ravel()]).astype(np.float32)
+            self.u_test = truth.poisson(pts[0], pts[1], self.w.a, self.w.b)
+            self.x_test = _dev(pts)
+        elif self.w.pde == inputs.BURGERS and self.w.lam == 1.0 and (self.w.lo, self.w.hi) == (-1.0, 1.0):
+            X, T = np.meshgrid(g, np.linspace(0.0, 1.0, test_grid), indexing="ij")
+            pts = np.stack([X.ravel(), T.ravel()]).astype(np.float32)
+            self.u_test = truth.burgers_sine(pts[0], pts[1], self.w.nu)
+            self.x_test = _dev(pts)
 
     def test_rel_l2(self):
         """Relative L2 error of u on the test grid (None without an exact solution)."""

@@ -1,4 +1,5 @@
-"""Host logic of the experiment drivers (Sections 4.1 and 4.2) on the CPU.
+"""Host logic of the experiment drivers (Sections 4.1 and 4.2) and of the
+training driver's test error, on the CPU.
 
 The library is replaced by a fake that records every call and carries out the
 training step and the forward with the FP64 oracle (test infrastructure; the
@@ -11,7 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_2409_14248_gb300 import capi, inputs, replica
+from paper_2409_14248_gb300 import capi, inputs, replica, trainer, truth
 
 torch = pytest.importorskip("torch")
 
@@ -115,3 +116,25 @@ def test_tables_summarise_runs_in_percent(fake):
     assert [r["seed"] for r in t["runs"]] == [0, 1]
     assert t["mean_mse_pct"] == pytest.approx(mse.mean()) and t["std_mse_pct"] == pytest.approx(mse.std())
     assert t["median_mse_pct"] == pytest.approx(np.median(mse))
+
+
+@pytest.mark.parametrize("name", ["burgers_2_10_10_1", "poisson_2_5_1"])
+def test_trainer_test_error_is_against_the_exact_solution(fake, name):
+    """At the initial weights the Trainer's test_rel_l2 is the oracle network's relative L2 error
+    against the exact solution on the grid: for Burgers (x, t) in [-1, 1] x [0, 1] against the
+    Cole-Hopf solution with u(x, 0) = -sin(pi x), for Poisson against sin(pi x) sin(pi y)."""
+    w = inputs.WORKLOADS[name]
+    data = inputs.make(w, n_int=64, n_bnd=16, n_ic=8, n_bc=8)
+    tr = trainer.Trainer(w, data=data, test_grid=12)
+    g = np.linspace(-1.0, 1.0, 12)
+    if w.pde == inputs.BURGERS:
+        A, B = np.meshgrid(g, np.linspace(0.0, 1.0, 12), indexing="ij")
+        exact = truth.burgers_sine(A.ravel(), B.ravel(), w.nu)
+    else:
+        A, B = np.meshgrid(g, g, indexing="ij")
+        exact = np.sin(np.pi * A.ravel()) * np.sin(np.pi * B.ravel())
+    pts = np.stack([A.ravel(), B.ravel()]).astype(np.float32)
+    pred = oracle.forward(w.net, data["W"], pts, 0x01)[0]
+    want = np.linalg.norm(pred - exact) / np.linalg.norm(exact)
+    assert tr.test_rel_l2() == pytest.approx(want, rel=1e-5)
+    assert fake.forwards[-1] == dict(N=144, mask=0x01)
