@@ -71,8 +71,50 @@ def test_bad_configuration_is_rejected_before_the_device(lib, kw, code):
     assert lib.hrkan_last_error().decode()
 
 
-def test_null_handle_is_rejected(lib):
-    assert lib.hrkan_forward_jets(None, None, None, 0, 1, None, None, None) == capi.HRKAN_EINVAL
-    assert lib.hrkan_backward(None, None, None, 0, 1, None, None, None, 0, None) == capi.HRKAN_EINVAL
-    assert lib.adam_step(None, None, None, 1e-3, 0.9, 0.999, 1e-8, 1, None) == capi.HRKAN_EINVAL
+# entry points whose first argument is an hrkan_t
+HANDLE_CALLS = sorted(set(capi.EXPORTS) - {"hrkan_param_count", "hrkan_init", "hrkan_destroy", "hrkan_last_error",
+                                           "hrkan_tape_floats", "hrkan_backward_noalloc", "hrkan_checkpoint_write",
+                                           "hrkan_checkpoint_read"})
+
+
+def _zero_args(fn):
+    """NULL for every pointer, 0 for every number, in the order of the function's argtypes."""
+    out = []
+    for t in fn.argtypes:
+        if t in (ctypes.c_int, ctypes.c_uint, ctypes.c_int64, ctypes.c_size_t):
+            out.append(0)
+        elif t is ctypes.c_double:
+            out.append(0.0)
+        else:
+            out.append(None)
+    return out
+
+
+@pytest.mark.parametrize("name", HANDLE_CALLS)
+def test_null_handle_is_rejected(lib, name):
+    """Every call taking a handle returns HRKAN_EINVAL for a NULL one, with a message, before any device work."""
+    fn = getattr(lib, name)
+    assert fn(*_zero_args(fn)) == capi.HRKAN_EINVAL
+    assert lib.hrkan_last_error().decode()
+
+
+def test_null_handle_calls_without_a_status():
+    lib = capi.load_library()
     lib.hrkan_destroy(None)
+    assert lib.hrkan_tape_floats(None, 100, 0x1F) == 0
+
+
+@pytest.mark.parametrize("cfg,mask,W,code", [
+    (None, 0x1, 1, capi.HRKAN_EINVAL),                                                   # no configuration
+    (dict(widths=[2, 10, 10, 1], G=10, m=6), 0x1, 1, capi.HRKAN_EUNSUPPORTED),           # fused kernels: m = 4
+    (dict(widths=[2, 32, 32, 1], G=20), 0x1, 1, capi.HRKAN_EUNSUPPORTED),                # no fused kernel
+    (dict(widths=[2, 10, 10, 1], G=10), 0x09, 1, capi.HRKAN_EINVAL),                     # u_xx without u_x
+    (dict(widths=[2, 10, 10, 1], G=10), 0x2F, 1, capi.HRKAN_EINVAL),                     # third order: not here
+    (dict(widths=[2, 10, 10, 1], G=10), 0x1F, None, capi.HRKAN_EINVAL),                  # NULL weights
+])
+def test_noalloc_backward_rejects_arguments_before_the_device(lib, cfg, mask, W, code):
+    c = None if cfg is None else ctypes.byref(capi.make_cfg(**cfg))
+    buf = (ctypes.c_float * 65536)()                   # a real host buffer; validation fails before any use
+    w = None if W is None else ctypes.cast(buf, ctypes.c_void_p)
+    assert lib.hrkan_backward_noalloc(c, w, w, 4, mask, w, w, 0, None) == code
+    assert lib.hrkan_last_error().decode().startswith("hrkan_backward_noalloc")
