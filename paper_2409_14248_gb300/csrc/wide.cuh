@@ -21,6 +21,9 @@ struct WideLayer {
     // first layer: the coordinates that jet directions 0 and 1 differentiate
     // along (-1: none); a three-input network runs as passes over direction pairs
     int seed0 = 0, seed1 = 1;
+    // adjoint: first point of this launch (point sets above the grid's y limit
+    // run as several launches)
+    int64_t p0 = 0;
 };
 
 // Weight gradient of one layer into partial rows [row0, row0 + GP) of a

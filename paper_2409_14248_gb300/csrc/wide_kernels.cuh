@@ -108,8 +108,10 @@ __global__ void __launch_bounds__(WB) wide_fwd_kernel(WideLayer p) {
 }
 
 // ------------------------------------------------------------ input adjoint
-// grid (ceil(I / IT), ceil(N / WB)): the input-chunk index runs fastest so the
-// blocks sharing a point tile run together and reuse its gy lines from L2.
+// grid (ceil(I / IT), point blocks): the input-chunk index runs fastest so the
+// blocks sharing a point tile run together and reuse its gy lines from L2.  A
+// grid's y extent is at most 65535, so a launch covers at most 65535 * WB
+// points starting at p.p0 and larger sets take several launches.
 // Shared memory holds W[all o][chunk][all i] as [jj][o][i] (basis fastest:
 // lanes with different cells hit different banks).
 template <int MW, unsigned MASK, int IT>
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(WB) wide_adjoint_kernel(WideLayer p) {
     }
     __syncthreads();
     const int64_t N = p.N;
-    const int64_t pt = int64_t(blockIdx.y) * WB + threadIdx.x;
+    const int64_t pt = p.p0 + int64_t(blockIdx.y) * WB + threadIdx.x;
     if (pt >= N) return;
     float z[IT][J];
     int cb[IT];
@@ -330,8 +332,16 @@ static cudaError_t adj_mask(const WideLayer& p, cudaStream_t s) {
     auto kern = wide_adjoint_kernel<MW, MASK, IT>;
     cudaError_t e = smem_optin((const void*)kern, sm);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(unsigned((p.I + IT - 1) / IT), unsigned((p.N + WB - 1) / WB)), WB, sm, s>>>(p);
-    return cudaGetLastError();
+    constexpr int64_t kMaxBlocksY = 65535;
+    const int64_t blocks = (p.N + WB - 1) / WB;
+    for (int64_t b0 = 0; b0 < blocks; b0 += kMaxBlocksY) {
+        WideLayer q = p;
+        q.p0 = b0 * WB;
+        const unsigned by = unsigned(std::min<int64_t>(kMaxBlocksY, blocks - b0));
+        kern<<<dim3(unsigned((p.I + IT - 1) / IT), by), WB, sm, s>>>(q);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <unsigned MASK, int JC, int PB, bool FIRST>
