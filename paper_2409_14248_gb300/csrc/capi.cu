@@ -773,7 +773,6 @@ int64_t hrkan_tape_floats(hrkan_t h, int64_t N, unsigned jet_mask) {
 
 int hrkan_forward_jets(hrkan_t h, const float* W, const float* x, int64_t N, unsigned jet_mask, float* jets,
                        float* tape, hrkan_stream_t stream) {
-    (void)tape;
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
     if (N < 0) return fail(HRKAN_EINVAL, "N=%lld", (long long)N);
     const bool d3 = h->cfg.widths[0] == 3;
@@ -860,7 +859,6 @@ int pinn_residual_loss(hrkan_t h, const pinn_problem* prob, const float* x_int, 
 
 int hrkan_backward(hrkan_t h, const float* W, const float* x, int64_t N, unsigned jet_mask, const float* tape,
                    const float* dL_djets, float* dW, int accumulate, hrkan_stream_t stream) {
-    (void)tape;
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
     if (N < 0) return fail(HRKAN_EINVAL, "N=%lld", (long long)N);
     const bool d3 = h->cfg.widths[0] == 3;

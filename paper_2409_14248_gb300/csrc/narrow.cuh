@@ -44,9 +44,6 @@ struct NarrowNet {
         return 2 * WH * n + (NL == 3 ? WH * n * WHP : 0);
     }
     __host__ __device__ static int smem_floats(int n) { return (off_wl(n) + WH * n + 3) & ~3; }
-    __host__ __device__ static int64_t params(int n) {
-        return int64_t(2) * WH * n + (NL == 3 ? int64_t(WH) * WH * n : 0) + int64_t(WH) * n;
-    }
 };
 
 // Global W (natural [o][j][i] per layer, concatenated) -> shared layout.
