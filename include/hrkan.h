@@ -81,7 +81,7 @@ enum hrkan_pde { HRKAN_POISSON = 0, HRKAN_BURGERS = 1, HRKAN_KDV = 2 };
 
 typedef struct hrkan_cfg {
     int n_widths;                    /* L + 1, in [2, HRKAN_MAX_WIDTHS] */
-    int widths[HRKAN_MAX_WIDTHS];    /* widths[0] = 2 (D), widths[n_widths-1] = 1, all <= 64 */
+    int widths[HRKAN_MAX_WIDTHS];    /* widths[0] = D = 2 or 3 inputs, widths[n_widths-1] = 1, all <= 64 */
     int G;                           /* grid intervals on [grid_lo, grid_hi], >= 1 */
     int k;                           /* support width in cells minus one (B-spline order); 3 */
     int m;                           /* HR order of Eq. 2: 2..6 (FP32); the fused narrow and tensor-core kernels need 4 */
