@@ -8,7 +8,7 @@ precision); this module only compiles it with gcc and marshals numpy arrays.
 
 What each function follows (paper sections/equations):
   support        Section 2.1-2.2 (n = g + k bases, B-spline supports)
-  hr_basis       Section 3, Eq. 2 and its derivatives
+  hr_basis       Section 3, Eq. 2 and its derivatives (hr_basis6: up to the sixth)
   forward        KAN layer as a matrix operation (Sections 1-3) + chain-rule jets
   residual_loss  Eq. 3-4 (Poisson), Eq. 6-8 (Burgers)
   backward       reverse mode of forward (training with Adam, Section 4)
@@ -57,6 +57,7 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.orc_support.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp]
             lib.orc_hr_basis.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]
+            lib.orc_hr_basis6.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]
             lib.orc_param_count.argtypes = [ctypes.c_int, _ip, ctypes.c_int, ctypes.c_int]
             lib.orc_param_count.restype = ctypes.c_long
             net = [ctypes.c_int, _ip, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
@@ -114,6 +115,15 @@ def hr_basis(m, s, e, x):
     return out
 
 
+def hr_basis6(m, s, e, x):
+    """Value and first to sixth derivatives of the order-m HR basis on [s, e] at x (Eq. 2, from its
+    expansion in the support coordinate)."""
+    lib = _load()
+    out = np.zeros(7)
+    lib.orc_hr_basis6(int(m), float(s), float(e), float(x), out.ctypes.data_as(_dp))
+    return out
+
+
 def param_count(net):
     lib = _load()
     w, args = _net_args(net)
@@ -121,7 +131,9 @@ def param_count(net):
 
 
 def n_rows(mask, D=2):
-    return bin(int(mask) & ((1 << (1 + 3 * D + (1 if D == 2 else 0))) - 1)).count("1")
+    """Rows a mask selects: D = 2 has 12 jet bits (u, three orders of pure derivatives, the mixed
+    u_x0x1, then the fourth and fifth orders), D = 3 has 16 (u and five orders)."""
+    return bin(int(mask) & ((1 << (12 if D == 2 else 1 + 5 * D)) - 1)).count("1")
 
 
 def forward(net, W, x, mask):

@@ -21,10 +21,11 @@
  *              a layer is sum_j sum_i W[o][j][i] v_i(z_j), summed densely over
  *              all n bases; no bias, no base branch, no normalisation.
  *   jets       the input derivatives the PDE residuals need (Eq. 3: Laplacian;
- *              Eq. 6-8: u_t, u_x, u_xx), and third derivatives along each input
- *              (the higher-order terms Section 3 motivates the order m with),
- *              and for D = 2 the mixed derivative u_x0x1, by the forward-mode
- *              chain rule.
+ *              Eq. 6-8: u_t, u_x, u_xx), third to fifth derivatives along each
+ *              input (the higher-order terms Section 3 motivates the order m
+ *              with; it picks m = 6 for a fifth derivative), and for D = 2 the
+ *              mixed derivative u_x0x1, by the forward-mode chain rule (Faa di
+ *              Bruno's formula for the fourth and fifth orders).
  *   loss       Eq. 4 (Poisson) and Eq. 8 (Burgers): L = alpha L_pde + L_bnd,
  *              L_bnd the pooled mean over all boundary/initial points.
  *   backward   hand-written reverse mode of the above.
@@ -93,6 +94,78 @@ void orc_hr_basis(int m, double s, double e, double x, double* out)
                   + 12.0 * md * (md - 1.0) * ipow(p, m - 2));
 }
 
+/*
+ * out[0..6] = v and its first to sixth derivatives at x.  Eq. 2 in the
+ * coordinate u = (2x - s - e)/(e - s) of the support reads c p^m = (1 - u^2)^m,
+ * because p = (e-x)(x-s) = ((e-s)/2)^2 (1 - u^2) and c = (2/(e-s))^{2m}.
+ * Expanding (1 - u^2)^m = sum_q C(m,q) (-1)^q u^{2q} and differentiating term
+ * by term, inside (s, e):
+ *   v^(r)(x) = (2/(e-s))^r sum_{2q >= r} C(m,q) (-1)^q (2q)!/(2q-r)! u^{2q-r}.
+ * out[0] is the literal ReLU product of Eq. 2; the derivatives are 0 at and
+ * outside the end points, as in orc_hr_basis.
+ */
+void orc_hr_basis6(int m, double s, double e, double x, double* out)
+{
+    double A = relu(e - x), B = relu(x - s);
+    out[0] = ipow(A, m) * ipow(B, m) * pow(2.0 / (e - s), 2.0 * m);
+    for (int r = 1; r <= 6; ++r) out[r] = 0.0;
+    if (!(x > s && x < e)) return;
+    double a = 2.0 / (e - s), u = (2.0 * x - s - e) / (e - s);
+    double binom = 1.0;                       /* C(m, q) */
+    for (int q = 0; q <= m; ++q) {
+        double sign = (q % 2) ? -1.0 : 1.0;
+        for (int r = 1; r <= 6 && r <= 2 * q; ++r) {
+            double falling = 1.0;                 /* (2q)! / (2q - r)! */
+            for (int t = 0; t < r; ++t) falling *= (double)(2 * q - t);
+            out[r] += binom * sign * falling * ipow(u, 2 * q - r) * ipow(a, r);
+        }
+        binom = binom * (double)(m - q) / (double)(q + 1);
+    }
+}
+
+/*
+ * Fourth and fifth derivatives of v(z(x)) along one input, by Faa di Bruno's
+ * formula: f[r] = v^(r)(z), g[q] = d^q z / dx^q (q = 1..5):
+ *   R4 = f4 g1^4 + 6 f3 g1^2 g2 + 3 f2 g2^2 + 4 f2 g1 g3 + f1 g4
+ *   R5 = f5 g1^5 + 10 f4 g1^3 g2 + 15 f3 g1 g2^2 + 10 f3 g1^2 g3 + 10 f2 g2 g3
+ *        + 5 f2 g1 g4 + f1 g5
+ * d/dz of R is the same polynomial with every f[r] replaced by f[r+1]; the
+ * partial derivatives in g are written out in row4_dg / row5_dg.
+ */
+static double row4(const double* f, const double* g)
+{
+    return f[4] * g[1] * g[1] * g[1] * g[1] + 6.0 * f[3] * g[1] * g[1] * g[2] + 3.0 * f[2] * g[2] * g[2]
+         + 4.0 * f[2] * g[1] * g[3] + f[1] * g[4];
+}
+
+static double row5(const double* f, const double* g)
+{
+    return f[5] * g[1] * g[1] * g[1] * g[1] * g[1] + 10.0 * f[4] * g[1] * g[1] * g[1] * g[2]
+         + 15.0 * f[3] * g[1] * g[2] * g[2] + 10.0 * f[3] * g[1] * g[1] * g[3] + 10.0 * f[2] * g[2] * g[3]
+         + 5.0 * f[2] * g[1] * g[4] + f[1] * g[5];
+}
+
+/* dg[q] = dR4/dg_q, q = 1..4 */
+static void row4_dg(const double* f, const double* g, double* dg)
+{
+    dg[1] = 4.0 * f[4] * g[1] * g[1] * g[1] + 12.0 * f[3] * g[1] * g[2] + 4.0 * f[2] * g[3];
+    dg[2] = 6.0 * f[3] * g[1] * g[1] + 6.0 * f[2] * g[2];
+    dg[3] = 4.0 * f[2] * g[1];
+    dg[4] = f[1];
+    dg[5] = 0.0;
+}
+
+/* dg[q] = dR5/dg_q, q = 1..5 */
+static void row5_dg(const double* f, const double* g, double* dg)
+{
+    dg[1] = 5.0 * f[5] * g[1] * g[1] * g[1] * g[1] + 30.0 * f[4] * g[1] * g[1] * g[2] + 15.0 * f[3] * g[2] * g[2]
+          + 20.0 * f[3] * g[1] * g[3] + 5.0 * f[2] * g[4];
+    dg[2] = 10.0 * f[4] * g[1] * g[1] * g[1] + 30.0 * f[3] * g[1] * g[2] + 10.0 * f[2] * g[3];
+    dg[3] = 10.0 * f[3] * g[1] * g[1] + 10.0 * f[2] * g[2];
+    dg[4] = 5.0 * f[2] * g[1];
+    dg[5] = f[1];
+}
+
 /* ------------------------------------------------------ reduced precision */
 
 /*
@@ -158,22 +231,26 @@ static int max_width(const orc_net* net)
 /*
  * One layer, one point, full jets over D input dims.
  * z[j], dz[j*D+d] = dz_j/dx_d, d2z[j*D+d] = d2z_j/dx_d^2, d3z = d3z_j/dx_d^3,
- * mz[j] = d2z_j/dx_0dx_1 (D = 2)
- *   ->  y, dy, d2y, d3y, my, by the chain rule for y = sum W v(z):
+ * mz[j] = d2z_j/dx_0dx_1 (D = 2), and when hi != 0 also d4z, d5z (fourth and
+ * fifth derivatives along each input)
+ *   ->  y, dy, d2y, d3y, my (d4y, d5y), by the chain rule for y = sum W v(z):
  *   y_d = v' z_d,  y_dd = v'' z_d^2 + v' z_dd,  y_ddd = v''' z_d^3 + 3 v'' z_d z_dd + v' z_ddd,
- *   y_01 = v'' z_0 z_1 + v' z_01.
+ *   y_01 = v'' z_0 z_1 + v' z_01,  y_dddd = R4,  y_ddddd = R5 (Faa di Bruno, above).
  */
 static void layer_forward(const orc_net* net, int l, const double* Wl, int D,
                           const double* s, const double* e,
                           const double* z, const double* dz, const double* d2z, const double* d3z,
-                          const double* mz, double* y, double* dy, double* d2y, double* d3y, double* my,
-                          int fmt)
+                          const double* mz, const double* d4z, const double* d5z,
+                          double* y, double* dy, double* d2y, double* d3y, double* my, double* d4y, double* d5y,
+                          int hi, int fmt)
 {
     int I = net->widths[l], O = net->widths[l + 1], n = orc_nbasis(net);
     for (int o = 0; o < O; ++o) {
         y[o] = 0.0;
         my[o] = 0.0;
         for (int d = 0; d < D; ++d) dy[o * D + d] = d2y[o * D + d] = d3y[o * D + d] = 0.0;
+        if (hi)
+            for (int d = 0; d < D; ++d) d4y[o * D + d] = d5y[o * D + d] = 0.0;
     }
     for (int j = 0; j < I; ++j) {
         for (int i = 0; i < n; ++i) {
@@ -188,6 +265,17 @@ static void layer_forward(const orc_net* net, int l, const double* Wl, int D,
                 a3[d] = round_to(b[3] * zd * zd * zd + 3.0 * b[2] * zd * zdd + b[1] * zddd, fmt);
             }
             double am = D == 2 ? round_to(b[2] * dz[j * D] * dz[j * D + 1] + b[1] * mz[j], fmt) : 0.0;
+            double a4[8], a5[8];
+            if (hi) {
+                double f[7];
+                orc_hr_basis6(net->m, s[i], e[i], z[j], f);
+                for (int d = 0; d < D; ++d) {
+                    double g[6] = {0.0, dz[j * D + d], d2z[j * D + d], d3z[j * D + d], d4z[j * D + d],
+                                   d5z[j * D + d]};
+                    a4[d] = round_to(row4(f, g), fmt);
+                    a5[d] = round_to(row5(f, g), fmt);
+                }
+            }
             for (int o = 0; o < O; ++o) {
                 double w = round_to(Wl[((long)o * I + j) * n + i], fmt);
                 y[o] += w * a0;
@@ -197,24 +285,53 @@ static void layer_forward(const orc_net* net, int l, const double* Wl, int D,
                     d2y[o * D + d] += w * a2[d];
                     d3y[o * D + d] += w * a3[d];
                 }
+                if (hi)
+                    for (int d = 0; d < D; ++d) {
+                        d4y[o * D + d] += w * a4[d];
+                        d5y[o * D + d] += w * a5[d];
+                    }
             }
         }
     }
 }
 
 /* jet rows selected by mask: bit 0 = u, bit 1+d = du/dx_d, bit 1+D+d = d2u/dx_d^2,
- * bit 1+2D+d = d3u/dx_d^3, and for D = 2 bit 1+3D = 7 = d2u/dx_0dx_1 */
+ * bit 1+2D+d = d3u/dx_d^3; for D = 2 bit 7 = d2u/dx_0dx_1, bits 8+d the fourth and
+ * bits 10+d the fifth derivatives; for D = 3 bits 10+d the fourth and 13+d the fifth. */
+static int jet_bits(int D) { return D == 2 ? 12 : 1 + 5 * D; }
+
+/* Order of the derivative bit b stands for (0 = u, 1..5, 6 = the mixed row) and its input *d. */
+static int bit_order(int b, int D, int* d)
+{
+    *d = 0;
+    if (b == 0) return 0;
+    if (D == 2 && b == 7) return 6;
+    int c = (D == 2 && b > 7) ? b - 2 : b - 1;
+    *d = c % D;
+    return c / D + 1;
+}
+
 static int mask_rows(unsigned mask, int D, int* bit_of_row)
 {
     int J = 0;
-    for (int b = 0; b < 1 + 3 * D + (D == 2 ? 1 : 0); ++b)
+    for (int b = 0; b < jet_bits(D); ++b)
         if (mask & (1u << b)) bit_of_row[J++] = b;
     return J;
+}
+
+/* Whether mask asks for a fourth or fifth derivative. */
+static int mask_higher(unsigned mask, int D)
+{
+    int d;
+    for (int b = 0; b < jet_bits(D); ++b)
+        if ((mask & (1u << b)) && bit_order(b, D, &d) >= 4 && bit_order(b, D, &d) <= 5) return 1;
+    return 0;
 }
 
 /* Scratch holding the per-layer input jets of one point. */
 typedef struct {
     double *z, *dz, *d2z, *d3z, *mz; /* [layer][maxw], [layer][maxw*D], mixed [layer][maxw] */
+    double *d4z, *d5z;               /* [layer][maxw*D] */
     int stride;                      /* maxw */
 } point_tape;
 
@@ -227,18 +344,21 @@ static int tape_alloc(point_tape* t, const orc_net* net, int D)
     t->d2z = calloc((size_t)(L + 1) * w * D, sizeof(double));
     t->d3z = calloc((size_t)(L + 1) * w * D, sizeof(double));
     t->mz = calloc((size_t)(L + 1) * w, sizeof(double));
-    return (t->z && t->dz && t->d2z && t->d3z && t->mz) ? 0 : -1;
+    t->d4z = calloc((size_t)(L + 1) * w * D, sizeof(double));
+    t->d5z = calloc((size_t)(L + 1) * w * D, sizeof(double));
+    return (t->z && t->dz && t->d2z && t->d3z && t->mz && t->d4z && t->d5z) ? 0 : -1;
 }
 
 static void tape_free(point_tape* t)
 {
-    free(t->z); free(t->dz); free(t->d2z); free(t->d3z); free(t->mz);
+    free(t->z); free(t->dz); free(t->d2z); free(t->d3z); free(t->mz); free(t->d4z); free(t->d5z);
 }
 
 /* Forward of one point through all layers; layer l's input jets land in the tape row l,
  * the network output in row L. */
 static void point_forward(const orc_net* net, const double* W, int D, const double* s,
-                          const double* e, const double* xp, point_tape* t, unsigned round_layers, int fmt)
+                          const double* e, const double* xp, point_tape* t, unsigned round_layers, int fmt,
+                          int hi)
 {
     int L = net->n_widths - 1, w = t->stride;
     for (int j = 0; j < D; ++j) {
@@ -247,16 +367,18 @@ static void point_forward(const orc_net* net, const double* W, int D, const doub
             t->dz[j * D + d] = (j == d) ? 1.0 : 0.0;
             t->d2z[j * D + d] = 0.0;
             t->d3z[j * D + d] = 0.0;
+            t->d4z[j * D + d] = 0.0;
+            t->d5z[j * D + d] = 0.0;
         }
         t->mz[j] = 0.0;
     }
     for (int l = 0; l < L; ++l) {
         const double* Wl = W + layer_offset(net, l);
-        layer_forward(net, l, Wl, D, s, e, t->z + (long)l * w, t->dz + (long)l * w * D,
-                      t->d2z + (long)l * w * D, t->d3z + (long)l * w * D, t->mz + (long)l * w,
-                      t->z + (long)(l + 1) * w, t->dz + (long)(l + 1) * w * D, t->d2z + (long)(l + 1) * w * D,
-                      t->d3z + (long)(l + 1) * w * D, t->mz + (long)(l + 1) * w,
-                      ((round_layers >> l) & 1u) ? fmt : ORC_EXACT);
+        long a = (long)l * w, b = (long)(l + 1) * w;
+        layer_forward(net, l, Wl, D, s, e, t->z + a, t->dz + a * D, t->d2z + a * D, t->d3z + a * D, t->mz + a,
+                      t->d4z + a * D, t->d5z + a * D,
+                      t->z + b, t->dz + b * D, t->d2z + b * D, t->d3z + b * D, t->mz + b, t->d4z + b * D,
+                      t->d5z + b * D, hi, ((round_layers >> l) & 1u) ? fmt : ORC_EXACT);
     }
 }
 
@@ -272,7 +394,7 @@ int orc_forward_rounded(int n_widths, const int* widths, int G, int k, int m, do
     int D = widths[0], L = n_widths - 1;
     if (widths[L] != 1 || !(mask & 1u)) return -1;
     int rows[16];
-    int J = mask_rows(mask, D, rows);
+    int J = mask_rows(mask, D, rows), higher = mask_higher(mask, D);
     int n = G + k;
     double* s = malloc(sizeof(double) * n);
     double* e = malloc(sizeof(double) * n);
@@ -283,17 +405,13 @@ int orc_forward_rounded(int n_widths, const int* widths, int G, int k, int m, do
     int w = t.stride;
     for (long p = 0; p < N; ++p) {
         for (int d = 0; d < D; ++d) xp[d] = x[(long)d * N + p];
-        point_forward(&net, W, D, s, e, xp, &t, round_layers, fmt);
-        const double* u = t.z + (long)L * w;
-        const double* du = t.dz + (long)L * w * D;
-        const double* d2u = t.d2z + (long)L * w * D;
-        const double* d3u = t.d3z + (long)L * w * D;
-        const double* mu = t.mz + (long)L * w;
+        point_forward(&net, W, D, s, e, xp, &t, round_layers, fmt, higher);
+        long a = (long)L * w;
+        const double* by_order[7] = {t.z + a, t.dz + a * D, t.d2z + a * D, t.d3z + a * D, t.d4z + a * D,
+                                     t.d5z + a * D, t.mz + a};
         for (int r = 0; r < J; ++r) {
-            int b = rows[r];
-            double v = (b == 0) ? u[0] : (b <= D) ? du[b - 1] : (b <= 2 * D) ? d2u[b - 1 - D]
-                     : (b <= 3 * D) ? d3u[b - 1 - 2 * D] : mu[0];
-            jets[(long)r * N + p] = v;
+            int d, q = bit_order(rows[r], D, &d);
+            jets[(long)r * N + p] = (q == 0 || q == 6) ? by_order[q][0] : by_order[q][d];
         }
     }
     tape_free(&t);
@@ -307,10 +425,27 @@ int orc_forward(int n_widths, const int* widths, int G, int k, int m, double lo,
     return orc_forward_rounded(n_widths, widths, G, k, m, lo, hi, W, x, N, mask, jets, 0u, ORC_EXACT);
 }
 
+/* One point's jets of unit j from rows [J][I][N] into per-order arrays (rows not in mask: zero).
+ * q[0] = value [I], q[1..5] = derivatives of that order [I*D], q[6] = mixed [I]. */
+static void unpack_unit(const double* zin, const int* rows, int J, int I, int D, long N, long p, int j,
+                        double* const* q)
+{
+    q[0][j] = 0.0;
+    q[6][j] = 0.0;
+    for (int o = 1; o <= 5; ++o)
+        for (int d = 0; d < D; ++d) q[o][j * D + d] = 0.0;
+    for (int r = 0; r < J; ++r) {
+        int d, o = bit_order(rows[r], D, &d);
+        double v = zin[((long)r * I + j) * N + p];
+        if (o == 0 || o == 6) q[o][j] = v;
+        else q[o][j * D + d] = v;
+    }
+}
+
 /*
  * One layer (Sections 1-3) applied to given input jets, D = 2:
- *   zin[r][j][p] for the jet rows r of mask (value, first, second, third
- *   derivatives in bit order), units j < I, points p < N; rows not in mask are zero.
+ *   zin[r][j][p] for the jet rows r of mask (value and derivatives in bit
+ *   order), units j < I, points p < N; rows not in mask are zero.
  *   yout[r][o][p], the same rows for the O outputs.
  * Basis-matrix entries and weights rounded to fmt (ORC_EXACT: none).
  */
@@ -321,48 +456,31 @@ int orc_layer_forward(int I, int O, int G, int k, int m, double lo, double hi, c
     int widths[2] = {I, O};
     orc_net net = {2, widths, G, k, m, lo, hi};
     int rows[16];
-    int J = mask_rows(mask, D, rows);
+    int J = mask_rows(mask, D, rows), higher = mask_higher(mask, D);
     if (!(mask & 1u)) return -1;
     int n = G + k;
     double* s = malloc(sizeof(double) * n);
     double* e = malloc(sizeof(double) * n);
-    double* z = malloc(sizeof(double) * I);
-    double* dz = calloc((size_t)I * D, sizeof(double));
-    double* d2z = calloc((size_t)I * D, sizeof(double));
-    double* d3z = calloc((size_t)I * D, sizeof(double));
-    double* mz = calloc((size_t)I, sizeof(double));
-    double* y = malloc(sizeof(double) * O);
-    double* dy = malloc(sizeof(double) * O * D);
-    double* d2y = malloc(sizeof(double) * O * D);
-    double* d3y = malloc(sizeof(double) * O * D);
-    double* my = malloc(sizeof(double) * O);
+    double* q[7];
+    double* out[7];
+    for (int o = 0; o < 7; ++o) {
+        size_t per = (o == 0 || o == 6) ? 1 : D;
+        q[o] = calloc((size_t)I * per, sizeof(double));
+        out[o] = calloc((size_t)O * per, sizeof(double));
+    }
     orc_support(G, k, lo, hi, s, e);
     for (long p = 0; p < N; ++p) {
-        for (int j = 0; j < I; ++j) {
-            z[j] = 0.0;
-            mz[j] = 0.0;
-            for (int d = 0; d < D; ++d) dz[j * D + d] = d2z[j * D + d] = d3z[j * D + d] = 0.0;
-            for (int r = 0; r < J; ++r) {
-                double v = zin[((long)r * I + j) * N + p];
-                int b = rows[r];
-                if (b == 0) z[j] = v;
-                else if (b <= D) dz[j * D + b - 1] = v;
-                else if (b <= 2 * D) d2z[j * D + b - 1 - D] = v;
-                else if (b <= 3 * D) d3z[j * D + b - 1 - 2 * D] = v;
-                else mz[j] = v;
-            }
-        }
-        layer_forward(&net, 0, Wl, D, s, e, z, dz, d2z, d3z, mz, y, dy, d2y, d3y, my, fmt);
+        for (int j = 0; j < I; ++j) unpack_unit(zin, rows, J, I, D, N, p, j, q);
+        layer_forward(&net, 0, Wl, D, s, e, q[0], q[1], q[2], q[3], q[6], q[4], q[5],
+                      out[0], out[1], out[2], out[3], out[6], out[4], out[5], higher, fmt);
         for (int o = 0; o < O; ++o)
             for (int r = 0; r < J; ++r) {
-                int b = rows[r];
-                double v = (b == 0) ? y[o] : (b <= D) ? dy[o * D + b - 1]
-                         : (b <= 2 * D) ? d2y[o * D + b - 1 - D] : (b <= 3 * D) ? d3y[o * D + b - 1 - 2 * D] : my[o];
-                yout[((long)r * O + o) * N + p] = v;
+                int d, b = bit_order(rows[r], D, &d);
+                yout[((long)r * O + o) * N + p] = (b == 0 || b == 6) ? out[b][o] : out[b][o * D + d];
             }
     }
-    free(s); free(e); free(z); free(dz); free(d2z); free(d3z); free(mz); free(y); free(dy); free(d2y); free(d3y);
-    free(my);
+    for (int o = 0; o < 7; ++o) { free(q[o]); free(out[o]); }
+    free(s); free(e);
     return 0;
 }
 
@@ -381,7 +499,7 @@ int orc_layer_dw(int I, int O, int G, int k, int m, double lo, double hi, const 
 {
     const int D = 2;
     int rows[16];
-    int J = mask_rows(mask, D, rows);
+    int J = mask_rows(mask, D, rows), higher = mask_higher(mask, D);
     if (!(mask & 1u)) return -1;
     int n = G + k;
     double* s = malloc(sizeof(double) * n);
@@ -392,22 +510,25 @@ int orc_layer_dw(int I, int O, int G, int k, int m, double lo, double hi, const 
     for (long p = 0; p < N; ++p) {
         for (int j = 0; j < I; ++j) {
             double z = 0.0, dz[2] = {0.0, 0.0}, d2z[2] = {0.0, 0.0}, d3z[2] = {0.0, 0.0}, mz = 0.0;
+            double d4z[2] = {0.0, 0.0}, d5z[2] = {0.0, 0.0};
+            double* q[7] = {&z, dz, d2z, d3z, d4z, d5z, &mz};
             for (int r = 0; r < J; ++r) {
+                int d, o = bit_order(rows[r], D, &d);
                 double v = zin[((long)r * I + j) * N + p];
-                int b = rows[r];
-                if (b == 0) z = v;
-                else if (b <= D) dz[b - 1] = v;
-                else if (b <= 2 * D) d2z[b - 1 - D] = v;
-                else if (b <= 3 * D) d3z[b - 1 - 2 * D] = v;
-                else mz = v;
+                if (o == 0 || o == 6) *q[o] = v;
+                else q[o][d] = v;
             }
             for (int i = 0; i < n; ++i) {
-                double b[5];
+                double b[5], f[7];
                 orc_hr_basis(m, s[i], e[i], z, b);
+                if (higher) orc_hr_basis6(m, s[i], e[i], z, f);
                 for (int r = 0; r < J; ++r) {
-                    int bit = rows[r];
+                    int bit = rows[r], dd, ord = bit_order(bit, D, &dd);
                     double v;
-                    if (bit == 0) {
+                    if (ord == 4 || ord == 5) {
+                        double g[6] = {0.0, dz[dd], d2z[dd], d3z[dd], d4z[dd], d5z[dd]};
+                        v = ord == 4 ? row4(f, g) : row5(f, g);
+                    } else if (bit == 0) {
                         v = b[0];
                     } else if (bit <= D) {
                         v = b[1] * dz[bit - 1];
@@ -451,6 +572,8 @@ int orc_layer_dw(int I, int O, int G, int k, int m, double lo, double hi, const 
  *   01-row (A = v2 z_0 z_1 + v1 z_01):
  *                     d/dz += dA (v3 z_0 z_1 + v2 z_01),  d/dz_0 += dA v2 z_1,
  *                     d/dz_1 += dA v2 z_0,  d/dz_01 += dA v1
+ *   fourth / fifth rows (A = R4 / R5): d/dz += dA R with v^(r) -> v^(r+1) (through
+ *                     the sixth derivative), d/dz_d^(q) += dA dR/dg_q
  * fmt rounds gy and W before the FP64 sum over o (the reduced-precision
  * contraction's inputs); ORC_EXACT rounds nothing.  zin [J][I][N],
  * gy [J][O][N], gz [J][I][N] written.
@@ -460,7 +583,7 @@ int orc_layer_adjoint(int I, int O, int G, int k, int m, double lo, double hi, c
 {
     const int D = 2;
     int rows[16];
-    int J = mask_rows(mask, D, rows);
+    int J = mask_rows(mask, D, rows), higher = mask_higher(mask, D);
     if (!(mask & 1u)) return -1;
     int n = G + k;
     double* s = malloc(sizeof(double) * n);
@@ -469,26 +592,38 @@ int orc_layer_adjoint(int I, int O, int G, int k, int m, double lo, double hi, c
     for (long p = 0; p < N; ++p) {
         for (int j = 0; j < I; ++j) {
             double z = 0.0, dz[2] = {0.0, 0.0}, d2z[2] = {0.0, 0.0}, d3z[2] = {0.0, 0.0}, mz = 0.0;
+            double d4z[2] = {0.0, 0.0}, d5z[2] = {0.0, 0.0};
+            double* q[7] = {&z, dz, d2z, d3z, d4z, d5z, &mz};
             for (int r = 0; r < J; ++r) {
+                int d, o = bit_order(rows[r], D, &d);
                 double v = zin[((long)r * I + j) * N + p];
-                int b = rows[r];
-                if (b == 0) z = v;
-                else if (b <= D) dz[b - 1] = v;
-                else if (b <= 2 * D) d2z[b - 1 - D] = v;
-                else if (b <= 3 * D) d3z[b - 1 - 2 * D] = v;
-                else mz = v;
+                if (o == 0 || o == 6) *q[o] = v;
+                else q[o][d] = v;
             }
             double g_z = 0.0, g_d[2] = {0.0, 0.0}, g_dd[2] = {0.0, 0.0}, g_ddd[2] = {0.0, 0.0}, g_m = 0.0;
+            double g_4[2] = {0.0, 0.0}, g_5[2] = {0.0, 0.0};
             for (int i = 0; i < n; ++i) {
-                double b[5];
+                double b[5], f[7];
                 orc_hr_basis(m, s[i], e[i], z, b);
+                if (higher) orc_hr_basis6(m, s[i], e[i], z, f);
                 for (int r = 0; r < J; ++r) {
                     double dA = 0.0;
                     for (int o = 0; o < O; ++o)
                         dA += round_to(gy[((long)r * O + o) * N + p], fmt) *
                               round_to(Wl[((long)o * I + j) * n + i], fmt);
-                    int bit = rows[r];
-                    if (bit == 0) {
+                    int bit = rows[r], dd, ord = bit_order(bit, D, &dd);
+                    if (ord == 4 || ord == 5) {
+                        /* d/dz through v^(r+1); d/dz_d^(q) from the partials of R4 / R5 */
+                        double g[6] = {0.0, dz[dd], d2z[dd], d3z[dd], d4z[dd], d5z[dd]}, dg[6];
+                        g_z += dA * (ord == 4 ? row4(f + 1, g) : row5(f + 1, g));
+                        if (ord == 4) row4_dg(f, g, dg);
+                        else row5_dg(f, g, dg);
+                        g_d[dd] += dA * dg[1];
+                        g_dd[dd] += dA * dg[2];
+                        g_ddd[dd] += dA * dg[3];
+                        g_4[dd] += dA * dg[4];
+                        g_5[dd] += dA * dg[5];
+                    } else if (bit == 0) {
                         g_z += dA * b[1];
                     } else if (bit <= D) {
                         int d = bit - 1;
@@ -513,11 +648,10 @@ int orc_layer_adjoint(int I, int O, int G, int k, int m, double lo, double hi, c
                     }
                 }
             }
+            const double* by_order[7] = {&g_z, g_d, g_dd, g_ddd, g_4, g_5, &g_m};
             for (int r = 0; r < J; ++r) {
-                int bit = rows[r];
-                double v = (bit == 0) ? g_z : (bit <= D) ? g_d[bit - 1]
-                         : (bit <= 2 * D) ? g_dd[bit - 1 - D] : (bit <= 3 * D) ? g_ddd[bit - 1 - 2 * D] : g_m;
-                gz[((long)r * I + j) * N + p] = v;
+                int d, o = bit_order(rows[r], D, &d);
+                gz[((long)r * I + j) * N + p] = (o == 0 || o == 6) ? *by_order[o] : by_order[o][d];
             }
         }
     }
@@ -532,19 +666,24 @@ int orc_layer_adjoint(int I, int O, int G, int k, int m, double lo, double hi, c
 static void layer_backward(const orc_net* net, int l, const double* Wl, double* dWl, int D,
                            const double* s, const double* e, const double* z,
                            const double* dz, const double* d2z, const double* d3z, const double* mz,
+                           const double* d4z, const double* d5z,
                            const double* gy, const double* gdy, const double* gd2y, const double* gd3y,
-                           const double* gmy, double* gz, double* gdz, double* gd2z, double* gd3z, double* gmz)
+                           const double* gmy, const double* gd4y, const double* gd5y,
+                           double* gz, double* gdz, double* gd2z, double* gd3z, double* gmz, double* gd4z,
+                           double* gd5z, int hi)
 {
     int I = net->widths[l], O = net->widths[l + 1], n = orc_nbasis(net);
     for (int j = 0; j < I; ++j) {
         gz[j] = 0.0;
         gmz[j] = 0.0;
         for (int d = 0; d < D; ++d) gdz[j * D + d] = gd2z[j * D + d] = gd3z[j * D + d] = 0.0;
+        for (int d = 0; d < D; ++d) gd4z[j * D + d] = gd5z[j * D + d] = 0.0;
     }
     for (int j = 0; j < I; ++j) {
         for (int i = 0; i < n; ++i) {
-            double b[5];
+            double b[5], f[7];
             orc_hr_basis(net->m, s[i], e[i], z[j], b);
+            if (hi) orc_hr_basis6(net->m, s[i], e[i], z[j], f);
             for (int o = 0; o < O; ++o) {
                 long wi = ((long)o * I + j) * n + i;
                 double w = Wl[wi];
@@ -570,6 +709,21 @@ static void layer_backward(const orc_net* net, int l, const double* Wl, double* 
                     gdz[j * D + 1] += w * gm * b[2] * z0;
                     gmz[j] += w * gm * b[1];
                 }
+                if (hi)
+                    for (int d = 0; d < D; ++d) {
+                        int c = j * D + d;
+                        double g[6] = {0.0, dz[c], d2z[c], d3z[c], d4z[c], d5z[c]}, p4[6], p5[6];
+                        double g4 = gd4y[o * D + d], g5 = gd5y[o * D + d];
+                        row4_dg(f, g, p4);
+                        row5_dg(f, g, p5);
+                        gW += g4 * row4(f, g) + g5 * row5(f, g);
+                        acc_z += g4 * row4(f + 1, g) + g5 * row5(f + 1, g);
+                        gdz[c] += w * (g4 * p4[1] + g5 * p5[1]);
+                        gd2z[c] += w * (g4 * p4[2] + g5 * p5[2]);
+                        gd3z[c] += w * (g4 * p4[3] + g5 * p5[3]);
+                        gd4z[c] += w * (g4 * p4[4] + g5 * p5[4]);
+                        gd5z[c] += w * g5 * p5[5];
+                    }
                 dWl[wi] += gW;
                 gz[j] += w * acc_z;
             }
@@ -589,7 +743,7 @@ int orc_backward(int n_widths, const int* widths, int G, int k, int m, double lo
     int D = widths[0], L = n_widths - 1;
     if (widths[L] != 1 || !(mask & 1u)) return -1;
     int rows[16];
-    int J = mask_rows(mask, D, rows);
+    int J = mask_rows(mask, D, rows), higher = mask_higher(mask, D);
     int n = G + k;
     long P = orc_param_count(n_widths, widths, G, k);
     if (!accumulate) memset(dW, 0, sizeof(double) * P);
@@ -605,36 +759,37 @@ int orc_backward(int n_widths, const int* widths, int G, int k, int m, double lo
     double *h = calloc(w, sizeof(double)), *hd = calloc((size_t)w * D, sizeof(double)),
            *hd2 = calloc((size_t)w * D, sizeof(double)), *hd3 = calloc((size_t)w * D, sizeof(double)),
            *hm = calloc(w, sizeof(double));
+    double *gd4 = calloc((size_t)w * D, sizeof(double)), *gd5 = calloc((size_t)w * D, sizeof(double)),
+           *hd4 = calloc((size_t)w * D, sizeof(double)), *hd5 = calloc((size_t)w * D, sizeof(double));
     double xp[8];
     for (long p = 0; p < N; ++p) {
         for (int d = 0; d < D; ++d) xp[d] = x[(long)d * N + p];
-        point_forward(&net, W, D, s, e, xp, &t, 0u, ORC_EXACT);
+        point_forward(&net, W, D, s, e, xp, &t, 0u, ORC_EXACT, higher);
         g[0] = 0.0;
         gm[0] = 0.0;
-        for (int d = 0; d < D; ++d) gd[d] = gd2[d] = gd3[d] = 0.0;
+        for (int d = 0; d < D; ++d) gd[d] = gd2[d] = gd3[d] = gd4[d] = gd5[d] = 0.0;
+        double* by_order[7] = {g, gd, gd2, gd3, gd4, gd5, gm};
         for (int r = 0; r < J; ++r) {
-            int b = rows[r];
-            double v = dL_djets[(long)r * N + p];
-            if (b == 0) g[0] = v;
-            else if (b <= D) gd[b - 1] = v;
-            else if (b <= 2 * D) gd2[b - 1 - D] = v;
-            else if (b <= 3 * D) gd3[b - 1 - 2 * D] = v;
-            else gm[0] = v;
+            int d, o = bit_order(rows[r], D, &d);
+            by_order[o][(o == 0 || o == 6) ? 0 : d] = dL_djets[(long)r * N + p];
         }
         for (int l = L - 1; l >= 0; --l) {
-            long off = layer_offset(&net, l);
-            layer_backward(&net, l, W + off, dW + off, D, s, e, t.z + (long)l * w,
-                           t.dz + (long)l * w * D, t.d2z + (long)l * w * D, t.d3z + (long)l * w * D,
-                           t.mz + (long)l * w, g, gd, gd2, gd3, gm, h, hd, hd2, hd3, hm);
+            long off = layer_offset(&net, l), a = (long)l * w;
+            layer_backward(&net, l, W + off, dW + off, D, s, e, t.z + a, t.dz + a * D, t.d2z + a * D,
+                           t.d3z + a * D, t.mz + a, t.d4z + a * D, t.d5z + a * D,
+                           g, gd, gd2, gd3, gm, gd4, gd5, h, hd, hd2, hd3, hm, hd4, hd5, higher);
             int I = widths[l];
             memcpy(g, h, sizeof(double) * I);
             memcpy(gm, hm, sizeof(double) * I);
             memcpy(gd, hd, sizeof(double) * I * D);
             memcpy(gd2, hd2, sizeof(double) * I * D);
             memcpy(gd3, hd3, sizeof(double) * I * D);
+            memcpy(gd4, hd4, sizeof(double) * I * D);
+            memcpy(gd5, hd5, sizeof(double) * I * D);
         }
     }
     free(g); free(gd); free(gd2); free(gd3); free(gm); free(h); free(hd); free(hd2); free(hd3); free(hm);
+    free(gd4); free(gd5); free(hd4); free(hd5);
     tape_free(&t);
     free(s); free(e);
     return 0;
