@@ -1,0 +1,51 @@
+"""The work counts behind bench.py's roofline fractions, against numbers
+derived by hand from the layer shapes.
+
+* Algorithmic FP32 flops per point of a fused training step: the sparse
+  contraction 2 (k+1) J I O per layer and pass (forward and weight gradient
+  everywhere, the input adjoint past the first layer) plus 45 flops per active
+  basis and unit (20 forward, 25 backward).
+* Dense tensor-core flops of a step: 2 x rows x K x N with rows = J x points,
+  K = I (G + k) and N = O, for every contraction that runs on the tensor cores.
+* Launches of a layer-wise step: per point set a forward per layer, a weight
+  gradient per layer and an input adjoint past the first layer, plus the
+  residual and the reduction/Adam."""
+import bench
+
+
+def test_fp32_peak_from_unit_counts():
+    assert abs(bench.FP32_PEAK_TFLOPS - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
+    assert abs(bench.FP32_PEAK_TFLOPS - 80.5) < 0.1
+
+
+def test_algorithmic_flops_per_point_of_the_burgers_workload():
+    # [2,10,10,1], k = 3, interior J = 4:
+    #   contraction 2*4*4 * (2*10*2 + 10*10*3 + 10*1*3) = 32 * 370 = 11840
+    #   bases 45 * 4 * (2 + 10 + 10) = 3960
+    assert bench.alg_flops_per_point([2, 10, 10, 1], 3, 4) == 11840 + 3960
+    # boundary points, J = 1: 2*4*1 * 370 + 3960
+    assert bench.alg_flops_per_point([2, 10, 10, 1], 3, 1) == 8 * 370 + 3960
+
+
+def test_dense_tensor_core_flops_of_the_precision_workload():
+    # [2,64,64,64,1] G=32 (K = 64 * 35 = 2240, N = 64), 262144 interior points x 5 rows + 16384 boundary
+    rows_all, rows_int = 5 * 262144 + 16384, 5 * 262144
+    fwd = 2 * rows_all * 2240 * 64            # one hidden layer's forward: 380.5 GFLOP
+    adj = 2 * rows_int * 2240 * 64            # its input adjoint (interior rows): 375.8 GFLOP
+    assert fwd == 380_507_258_880 and adj == 375_809_638_400
+    w = ([2, 64, 64, 64, 1], 32, 3, 262144, 5, 16384)
+    assert bench.dense_tc_flops(*w, False) == 2 * fwd                       # TF32: forward of 2 hidden layers
+    first_dw = 2 * rows_all * (2 * 35) * 64                                # first layer's gradient, K = 2 * 35
+    assert bench.dense_tc_flops(*w, True) == 2 * (fwd + fwd + adj) + first_dw   # BF16: + dW and adjoint
+
+
+def test_launches_of_a_layer_wise_step():
+    widths = [2, 32, 32, 1]
+    none = lambda l: False
+    # per point set: 3 forwards + 3 weight gradients + 2 adjoints = 8; two sets; residual; reduction
+    assert bench.launches_per_step(widths, 0, none, none, False) == 2 * 8 + 2
+    assert bench.launches_per_step(widths, 0, none, none, True) == 2     # fused kernel + reduction
+    # BF16 on the hidden layer: its forward and gradient each add a conversion launch, and the
+    # interior set's adjoint of that layer is a tensor-core launch reusing the gradient's conversion
+    hid = lambda l: l == 1
+    assert bench.launches_per_step(widths, 1, hid, hid, False) == 2 * (4 + 6) + 1 + 2
