@@ -118,7 +118,9 @@ typedef struct pinn_problem {
     double alpha;   /* weight of the PDE term */
 } pinn_problem;
 
-/* Number of float weights P of one network of this shape (0 on a bad cfg). */
+/* Number of float weights P of one network of this shape: sum over layers of
+ * I * O * n with n = G + k bases per input unit (Sections 2.1-2.2).  0 on an
+ * invalid cfg (no status: the count is the return value). */
 int64_t hrkan_param_count(const hrkan_cfg* cfg);
 
 /*
@@ -151,6 +153,10 @@ int64_t hrkan_tape_floats(hrkan_t h, int64_t N, unsigned jet_mask);
  *   tape  NULL, or hrkan_tape_floats(h, N, jet_mask) floats to keep the layer
  *         jets for hrkan_backward.
  * N = 0 is a valid no-op.
+ * Errors: HRKAN_EINVAL for a NULL handle, N < 0, an invalid mask (a bit
+ * without the bit it requires, bit 0 missing, bits above 7, or above 6 for
+ * D = 3) or NULL W / x / jets with N > 0; HRKAN_EUNSUPPORTED for a mask the
+ * handle's kernels lack (third-order and mixed rows on the fused shapes).
  */
 int hrkan_forward_jets(hrkan_t h, const float* W, const float* x, int64_t N, unsigned jet_mask,
                        float* jets, float* tape, hrkan_stream_t stream);
@@ -162,6 +168,9 @@ int hrkan_forward_jets(hrkan_t h, const float* W, const float* x, int64_t N, uns
  * l = 0: the coordinates [2][N]), y = output jets [J][O][N] (written).  Runs
  * the same kernel the network forward would use for that layer under the
  * handle's precision (tensor cores for BF16/TF32 hidden layers).
+ * Errors (also of hrkan_layer_dw and hrkan_layer_adjoint): HRKAN_EINVAL for a
+ * NULL handle or pointer, N < 0, an invalid mask or a layer index outside
+ * [0, L) ([1, L) for the adjoint); HRKAN_EUNSUPPORTED on a three-input handle.
  */
 int hrkan_layer_jets(hrkan_t h, int layer, const float* W, const float* z, int64_t N, unsigned jet_mask,
                      float* y, hrkan_stream_t stream);
@@ -216,6 +225,8 @@ int pinn_residual_loss(hrkan_t h, const pinn_problem* prob, const float* x_int, 
  *   dW          [P] float32: overwritten (accumulate = 0) or added to (1).
  * Cross-block sums run in a fixed order; within a block float32 atomics in
  * shared memory make the last bits order-dependent.
+ * Errors: as hrkan_forward_jets; W and dW are required even for N = 0, when
+ * dW is zeroed (accumulate = 0) or left as it is (1).
  */
 int hrkan_backward(hrkan_t h, const float* W, const float* x, int64_t N, unsigned jet_mask,
                    const float* tape, const float* dL_djets, float* dW, int accumulate,
@@ -227,6 +238,8 @@ int hrkan_backward(hrkan_t h, const float* W, const float* x, int64_t N, unsigne
  * float64 (zeroed by hrkan_init and hrkan_reset_moments):
  *   m <- b1 m + (1-b1) g;  v <- b2 v + (1-b2) g^2;
  *   W <- W - lr (m/(1-b1^t)) / (sqrt(v/(1-b2^t)) + eps)
+ * Errors: HRKAN_EINVAL for a NULL handle or pointer, t < 1, b1 or b2 outside
+ * [0, 1), eps < 0 or a non-finite lr.
  */
 int adam_step(hrkan_t h, float* W, const float* dW, double lr, double b1, double b2, double eps,
               int t, hrkan_stream_t stream);
@@ -251,15 +264,17 @@ int hrkan_sync_status(hrkan_t h);
  */
 int hrkan_set_wait_cycles(hrkan_t h, int64_t cycles);
 
-/* Zero the Adam moments and the device step counter of the handle. */
+/* Zero the Adam moments and the device step counter of the handle (a fresh
+ * start of the Adam training of Section 4).  HRKAN_EINVAL for a NULL handle. */
 int hrkan_reset_moments(hrkan_t h, hrkan_stream_t stream);
 
 /*
- * One full-batch training step, fused: forward jets at the interior and
- * boundary points, residual and loss, backward, cross-block reduction and
- * Adam.  Same arithmetic as hrkan_forward_jets + pinn_residual_loss +
- * hrkan_backward + adam_step; the interior mask is 0x1F for Poisson and 0x0F
- * for Burgers.
+ * One full-batch training step (Section 4: the loss of Eq. 4 / Eq. 8
+ * minimised by Adam), fused: forward jets at the interior and boundary
+ * points, residual and loss, backward, cross-block reduction and Adam.  Same
+ * arithmetic as hrkan_forward_jets + pinn_residual_loss + hrkan_backward +
+ * adam_step; the interior mask is 0x1F for Poisson, 0x0F for Burgers and 0x2F
+ * for KdV.
  *   W      [P] float32, updated in place.
  *   t      Adam step >= 1, or 0: take the step from a device-side counter of
  *          the handle (zeroed by hrkan_init / hrkan_reset_moments) and advance
@@ -269,6 +284,10 @@ int hrkan_reset_moments(hrkan_t h, hrkan_stream_t stream);
  *   dW     NULL, or [P] float32 receiving the gradient.
  * No host synchronisation; capturable in a CUDA graph after one warm-up call
  * (with profiling disabled).
+ * Errors: HRKAN_EINVAL for a NULL handle or pointer, a bad problem (kind,
+ * non-finite coefficient), N_int + N_bnd = 0, t < 0 or bad Adam
+ * hyper-parameters; HRKAN_EUNSUPPORTED on a three-input handle and for KdV on
+ * the fused shapes.
  */
 int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float* x_int,
                      int64_t N_int, const float* x_bnd, const float* g_bnd, int64_t N_bnd,
@@ -292,9 +311,12 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
  * uploaded only when the offsets or problems change (that call synchronises
  * the stream); calls with unchanged arguments only enqueue the two kernels, so
  * they can be captured in a CUDA graph after one warm-up call.
- * HRKAN_EUNSUPPORTED on a handle without a fused shape ([2,W,1] or
- * [2,W,W,1], W in 5, 10, 16; m = 4; not HRKAN_FLAG_LAYERWISE), and for a
- * problem kind whose residual needs third derivatives.
+ * Errors: HRKAN_EINVAL for a NULL handle, array or (with points) pointer,
+ * problems that disagree in kind, lam, nu or alpha, offsets that decrease or
+ * do not start at 0, t < 0 or bad Adam hyper-parameters; HRKAN_EUNSUPPORTED
+ * on a handle without a fused shape ([2,W,1] or [2,W,W,1], W in 5, 10, 16;
+ * m = 4; not HRKAN_FLAG_LAYERWISE), and for a problem kind whose residual
+ * needs third derivatives.
  */
 int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, const float* x_int,
                              const int64_t* off_int, const float* x_bnd, const float* g_bnd,
@@ -302,11 +324,14 @@ int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, con
                              double* loss, float* dW, hrkan_stream_t stream);
 
 /* Output jets of every instance at its points (x [2][N], offsets host [I+1], jets [J][N]);
- * the same handle requirement as hrkan_train_step_batched. */
+ * the same handle requirement as hrkan_train_step_batched.  HRKAN_EINVAL for a
+ * NULL handle, offsets or (with points) pointer, decreasing offsets or an
+ * invalid mask. */
 int hrkan_forward_jets_batched(hrkan_t h, const float* W, const float* x, const int64_t* offsets,
                                unsigned jet_mask, float* jets, hrkan_stream_t stream);
 
-/* Points per work item of the multi-instance calls (default 1024); a tuning knob. */
+/* Points per work item of the multi-instance calls (default 1024); a tuning knob.
+ * HRKAN_EINVAL for a NULL handle or points_per_item < 1. */
 int hrkan_set_batch_items(hrkan_t h, int points_per_item);
 
 /*
@@ -318,6 +343,8 @@ int hrkan_set_batch_items(hrkan_t h, int points_per_item);
  * Synchronises the stream; resets the Adam moments and the device step
  * counter (call it before training).  chosen / ms_per_step (host, may be
  * NULL) receive the winner and its time per step.
+ * Errors: those of hrkan_train_step_batched, and HRKAN_EINVAL for
+ * n_candidates < 1 or a candidate below 1 point.
  */
 int hrkan_autotune_batch(hrkan_t h, const pinn_problem* probs, float* W, const float* x_int,
                          const int64_t* off_int, const float* x_bnd, const float* g_bnd,
