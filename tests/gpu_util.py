@@ -2,7 +2,7 @@
 import numpy as np
 
 import oracle
-from paper_2409_14248_gb300 import capi, inputs
+from paper_2409_14248_gb300 import capi
 
 
 def relerr(got, want):
