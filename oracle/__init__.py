@@ -34,7 +34,7 @@ _lib = None
 POISSON = 0
 BURGERS = 1
 KDV = 2
-EXACT, BF16, TF32 = 0, 1, 2
+EXACT, BF16, TF32, BF16W2 = 0, 1, 2, 3   # BF16W2: BF16 operands, weights as bf16 hi + lo
 
 
 def build(force: bool = False) -> str:

@@ -173,9 +173,11 @@ static void row5_dg(const double* f, const double* g, double* dg)
  * paper: the precision the contraction's inputs are rounded to).  The value is
  * first rounded to float32, then
  *   ORC_BF16: to bfloat16, round to nearest even (8-bit significand);
- *   ORC_TF32: to TF32, round to nearest with ties away from zero (11-bit significand).
+ *   ORC_TF32: to TF32, round to nearest with ties away from zero (11-bit significand);
+ *   ORC_BF16W2: operands as ORC_BF16, weights as the sum of two bfloat16
+ *   values (round_w below: a contraction split into A_hi W_hi + A_hi W_lo).
  */
-enum { ORC_EXACT = 0, ORC_BF16 = 1, ORC_TF32 = 2 };
+enum { ORC_EXACT = 0, ORC_BF16 = 1, ORC_TF32 = 2, ORC_BF16W2 = 3 };
 
 static double round_to(double x, int fmt)
 {
@@ -183,7 +185,7 @@ static double round_to(double x, int fmt)
     float f = (float)x;
     uint32_t u;
     memcpy(&u, &f, 4);
-    if (fmt == ORC_BF16) {
+    if (fmt == ORC_BF16 || fmt == ORC_BF16W2) {
         u += 0x7FFFu + ((u >> 16) & 1u);
         u &= 0xFFFF0000u;
     } else {
@@ -195,6 +197,18 @@ static double round_to(double x, int fmt)
 }
 
 double orc_round(double x, int fmt) { return round_to(x, fmt); }
+
+/* A weight as the contraction sees it: round_to, except under ORC_BF16W2 the
+ * float32 weight w is carried as hi + lo with hi = bf16(w), lo = bf16(w - hi)
+ * (w - hi is exact in float32: it has at most 16 significant bits). */
+static double round_w(double x, int fmt)
+{
+    if (fmt != ORC_BF16W2) return round_to(x, fmt);
+    float w = (float)x;
+    float hi = (float)round_to(w, ORC_BF16);
+    float lo = (float)round_to(w - hi, ORC_BF16);
+    return (double)hi + (double)lo;
+}
 
 /* ---------------------------------------------------------------- network */
 
@@ -277,7 +291,7 @@ static void layer_forward(const orc_net* net, int l, const double* Wl, int D,
                 }
             }
             for (int o = 0; o < O; ++o) {
-                double w = round_to(Wl[((long)o * I + j) * n + i], fmt);
+                double w = round_w(Wl[((long)o * I + j) * n + i], fmt);
                 y[o] += w * a0;
                 my[o] += w * am;
                 for (int d = 0; d < D; ++d) {
@@ -610,7 +624,7 @@ int orc_layer_adjoint(int I, int O, int G, int k, int m, double lo, double hi, c
                     double dA = 0.0;
                     for (int o = 0; o < O; ++o)
                         dA += round_to(gy[((long)r * O + o) * N + p], fmt) *
-                              round_to(Wl[((long)o * I + j) * n + i], fmt);
+                              round_w(Wl[((long)o * I + j) * n + i], fmt);
                     int bit = rows[r], dd, ord = bit_order(bit, D, &dd);
                     if (ord == 4 || ord == 5) {
                         /* d/dz through v^(r+1); d/dz_d^(q) from the partials of R4 / R5 */

@@ -691,3 +691,23 @@ def test_layer_adjoint_chains_to_the_network_backward():
     g1 = oracle.layer_adjoint(4, 3, 6, 3, 4, -1.0, 1.0, W1, z1, g2, 0x1F)
     first = oracle.layer_dw(2, 4, 6, 3, 4, -1.0, 1.0, z0, g1, 0x1F)
     np.testing.assert_allclose(first, full[:4 * 2 * n], rtol=1e-11, atol=1e-11)
+
+
+def test_bf16_weight_split_mode():
+    """ORC_BF16W2 (BF16 operands, each weight as bf16 hi + bf16 lo): (a) weights exactly
+    representable in BF16 give the BF16 mode bit for bit; (b) weights with at most 16 significant
+    bits are carried exactly, so the layer output is the exact weights applied to BF16-rounded
+    basis-matrix entries, read out one by one with one-hot weights (the layer is linear in W)."""
+    I, O, G, N = 2, 1, 4, 5
+    n = G + 3
+    rng = np.random.default_rng(90)
+    z = rng.normal(0, 0.4, (1, I, N))
+    w_bf = np.array([oracle.round_to(v, oracle.BF16) for v in rng.normal(0, 0.5, O * I * n)])
+    lf = lambda W, fmt: oracle.layer_forward(I, O, G, 3, 4, -1.0, 1.0, W, z, 0x01, fmt)
+    np.testing.assert_array_equal(lf(w_bf, oracle.BF16W2), lf(w_bf, oracle.BF16))
+    # 16-bit weights: integers below 2^16 scaled by a power of two
+    w16 = rng.integers(-(1 << 15), 1 << 15, O * I * n) / float(1 << 17)
+    A = np.stack([lf(np.eye(O * I * n)[c], oracle.EXACT)[0, 0] for c in range(O * I * n)])     # [I*n][N]
+    A_bf = np.vectorize(lambda v: oracle.round_to(v, oracle.BF16))(A)
+    np.testing.assert_allclose(lf(w16, oracle.BF16W2)[0, 0], w16 @ A_bf, rtol=1e-14, atol=1e-15)
+    assert not np.allclose(lf(w16, oracle.BF16)[0, 0], w16 @ A_bf, rtol=1e-6, atol=0)   # plain BF16 rounds W too
