@@ -1,7 +1,8 @@
 // Device building blocks of the HRKAN hot path: the HR basis with its first
-// three derivatives on the k+1 active supports (Section 3, Eq. 2), and the
+// four derivatives on the k+1 active supports (Section 3, Eq. 2), and the
 // jet-row structure that the PDE residuals need (Eq. 3: the Laplacian; Eq. 6:
-// u_t, u_x, u_xx).
+// u_t, u_x, u_xx).  The basis evaluation and the row formulas are also
+// callable on the host, where a test compares them with the FP64 oracle.
 #pragma once
 
 #include <cstdint>
@@ -43,12 +44,12 @@ struct Active {
     float d3[K + 1];     // v''' (only when NDER >= 3)
     float d4[K + 1];     // v'''' (only when NDER >= 4)
 
-    __device__ __forceinline__ int idx(int q, int n) const {
+    __host__ __device__ __forceinline__ int idx(int q, int n) const {
         int i = c + q;
         return (i < 0) ? 0 : (i >= n ? n - 1 : i);
     }
 
-    __device__ __forceinline__ void eval(float z, const Grid& g) {
+    __host__ __device__ __forceinline__ void eval(float z, const Grid& g) {
         static_assert(M >= 2, "the jets need M >= 2");
         float t = (z - g.lo) * g.inv_h;
         // Beyond +-2^30 cells nothing is active; keep floorf's result in int range.
@@ -131,7 +132,7 @@ struct Jet {
     //   d-row      v' z_d
     //   dd-row     v'' z_d^2 + v' z_dd
     template <int KP>
-    __device__ __forceinline__ static void rows(const float* z, const float* v, const float* d1,
+    __host__ __device__ __forceinline__ static void rows(const float* z, const float* v, const float* d1,
                                                 const float* d2, float (*a)[KP]) {
         static_assert(!GENERAL, "third-derivative or mixed rows: use rows_b");
 #pragma unroll
@@ -151,7 +152,7 @@ struct Jet {
     //   dz_d    += sum_q dAd v' + dAdd 2 v'' z_d
     //   dz_dd   += sum_q dAdd v'
     template <int KP>
-    __device__ __forceinline__ static void rows_adjoint(const float* z, const float* d1,
+    __host__ __device__ __forceinline__ static void rows_adjoint(const float* z, const float* d1,
                                                         const float* d2, const float* d3,
                                                         const float (*dA)[KP], float* gz) {
         static_assert(!GENERAL, "third-derivative or mixed rows: use adjoint_b");
@@ -186,7 +187,7 @@ struct Jet {
     //   ddd-row    v''' z_d^3 + 3 v'' z_d z_dd + v' z_ddd
     //   01-row     v'' z_0 z_1 + v' z_01
     template <int KP>
-    __device__ __forceinline__ static void rows3(const float* z, const float* v, const float* d1,
+    __host__ __device__ __forceinline__ static void rows3(const float* z, const float* v, const float* d1,
                                                  const float* d2, const float* d3, float (*a)[KP]) {
 #pragma unroll
         for (int q = 0; q < KP; ++q) {
@@ -213,7 +214,7 @@ struct Jet {
     //   dz_ddd  += dAddd v'
     //   dz_01   += dA01 v'
     template <int KP>
-    __device__ __forceinline__ static void rows_adjoint3(const float* z, const float* d1, const float* d2,
+    __host__ __device__ __forceinline__ static void rows_adjoint3(const float* z, const float* d1, const float* d2,
                                                          const float* d3, const float* d4,
                                                          const float (*dA)[KP], float* gz) {
 #pragma unroll
@@ -267,12 +268,12 @@ struct Jet {
     // The rows / their reverse for a basis evaluation b (Active<K, M, NDER_ROWS> /
     // Active<K, M, NDER_ADJ>): the PDE masks keep the second-order formulas.
     template <int KP, class B>
-    __device__ __forceinline__ static void rows_b(const float* z, const B& b, float (*a)[KP]) {
+    __host__ __device__ __forceinline__ static void rows_b(const float* z, const B& b, float (*a)[KP]) {
         if constexpr (!GENERAL) rows<KP>(z, b.v, b.d1, b.d2, a);
         else rows3<KP>(z, b.v, b.d1, b.d2, b.d3, a);
     }
     template <int KP, class B>
-    __device__ __forceinline__ static void adjoint_b(const float* z, const B& b, const float (*dA)[KP], float* gz) {
+    __host__ __device__ __forceinline__ static void adjoint_b(const float* z, const B& b, const float (*dA)[KP], float* gz) {
         if constexpr (!GENERAL) rows_adjoint<KP>(z, b.d1, b.d2, b.d3, dA, gz);
         else rows_adjoint3<KP>(z, b.d1, b.d2, b.d3, b.d4, dA, gz);
     }

@@ -1,0 +1,76 @@
+// Host harness for the device basis and jet-row formulas (csrc/hr_device.cuh):
+// prints the kernels' own float32 values for a fixed set of inputs so that a
+// CPU test can compare them with the FP64 oracle.  Output lines:
+//   B m z c v0..v3 d1_0..d1_3 d2_.. d3_.. d4_..          (Active<3, m, 4>)
+//   R mask m z c <J rows x 4 entries> <J adjoint values>  (Jet rows and their reverse)
+// Inputs of the R lines: jets z[r] = zr[r] (z[0] = the value), dA[r][q] =
+// gy[r] * w[c + q] with w[i] = wv(i) (a rank-1 gradient, as a one-output layer has).
+#include <cstdio>
+
+#include "../../paper_2409_14248_gb300/csrc/hr_device.cuh"
+
+using namespace hrkan;
+
+static const int G = 6, K = 3;
+static const float ZS[] = {-1.3f, -1.0f, -0.95f, -2.0f / 3.0f, -0.5f, -0.31f, -0.1f, 0.0f, 0.07f,
+                           1.0f / 3.0f, 0.42f, 0.8f, 0.999f, 1.0f, 1.2f};
+static const float ZR[8] = {0.0f, 0.7f, -1.3f, 0.45f, -0.8f, 2.1f, -0.6f, 0.35f};   // z[0] replaced per line
+static const float GY[8] = {0.9f, -0.4f, 1.7f, 0.25f, -1.1f, 0.6f, 1.3f, -0.75f};
+static float wv(int i) { return 0.5f - 0.17f * float(i) + 0.03f * float(i * i); }
+
+static Grid grid(int m) {
+    Grid g;
+    g.lo = -1.0f;
+    g.h = 2.0f / G;
+    g.inv_h = G / 2.0f;
+    g.inv_a = 2.0f / ((K + 1) * g.h);
+    g.n = G + K;
+    g.m = m;
+    return g;
+}
+
+template <int M>
+static void basis() {
+    const Grid g = grid(M);
+    for (float z : ZS) {
+        Active<K, M, 4> a;
+        a.eval(z, g);
+        printf("B %d %.9g %d", M, (double)z, a.c);
+        const float* arr[5] = {a.v, a.d1, a.d2, a.d3, a.d4};
+        for (auto* p : arr)
+            for (int q = 0; q <= K; ++q) printf(" %.9g", (double)p[q]);
+        printf("\n");
+    }
+}
+
+template <unsigned MASK, int M>
+static void rows() {
+    using JT = Jet<MASK>;
+    const Grid g = grid(M);
+    for (float z0 : ZS) {
+        Active<K, M, 4> a;
+        a.eval(z0, g);
+        float z[8], gz[8], A[8][K + 1], dA[8][K + 1];
+        int r = 0;
+        for (int b = 0; b < 8; ++b)
+            if (MASK & (1u << b)) z[r++] = (b == 0) ? z0 : ZR[b];
+        for (int rr = 0; rr < JT::J; ++rr)
+            for (int q = 0; q <= K; ++q) {
+                const int i = a.c + q;
+                dA[rr][q] = (i >= 0 && i < g.n) ? GY[rr] * wv(i) : 0.0f;
+            }
+        JT::template rows_b<K + 1>(z, a, A);
+        JT::template adjoint_b<K + 1>(z, a, dA, gz);
+        printf("R %u %d %.9g %d", MASK, M, (double)z0, a.c);
+        for (int rr = 0; rr < JT::J; ++rr)
+            for (int q = 0; q <= K; ++q) printf(" %.9g", (double)A[rr][q]);
+        for (int rr = 0; rr < JT::J; ++rr) printf(" %.9g", (double)gz[rr]);
+        printf("\n");
+    }
+}
+
+int main() {
+    basis<2>(); basis<3>(); basis<4>(); basis<5>(); basis<6>();
+    rows<0x1Fu, 4>(); rows<0x0Fu, 4>(); rows<0xFFu, 4>(); rows<0xFFu, 6>(); rows<0x2Fu, 3>();
+    return 0;
+}

@@ -1,0 +1,117 @@
+"""The kernels' basis and jet-row formulas (csrc/hr_device.cuh), compiled for
+the host by nvcc and run on the CPU, against the FP64 oracle.
+
+tests/device_host/hr_device_host.cu prints, in float32:
+* B lines: the k + 1 active bases of Active<3, m, 4> (v and its first four
+  derivatives) for m = 2..6 at points across and beyond the grid;
+* R lines: the basis-matrix rows of one input unit (Jet<mask>::rows_b) and
+  their reverse (adjoint_b) for masks 0x1F, 0x0F, 0xFF (m = 4 and 6) and 0x2F
+  (m = 3), with given jets and a rank-1 dA = gy[r] w[i].
+
+The oracle gives the same quantities: hr_basis for the bases, a one-input,
+one-output oracle layer with one-hot weights for each row entry, and its
+input adjoint for the reverse.  At a support end the derivatives of order >= m
+jump (the kernels take the limit from inside, the oracle takes 0), so those
+orders are compared only away from the knots."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_14248_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+G, K, LO, HI = 6, 3, -1.0, 1.0
+H = (HI - LO) / G
+KNOTS = LO + H * np.arange(-K, G + K + 1)
+ZR = [0.0, 0.7, -1.3, 0.45, -0.8, 2.1, -0.6, 0.35]
+GY = [0.9, -0.4, 1.7, 0.25, -1.1, 0.6, 1.3, -0.75]
+
+
+def wv(i):
+    return np.float32(0.5 - 0.17 * i + 0.03 * i * i)
+
+
+def near_knot(z):
+    return np.abs(KNOTS - z).min() < 1e-5
+
+
+@pytest.fixture(scope="module")
+def lines(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc is not installed")
+    exe = str(tmp_path_factory.mktemp("hdh") / "hr_device_host")
+    src = os.path.join(ROOT, "tests", "device_host", "hr_device_host.cu")
+    r = subprocess.run([nvcc, "-std=c++17", "-O1", *build.ARCH, src, "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0
+    return [ln.split() for ln in out.stdout.splitlines()]
+
+
+def test_basis_values_and_derivatives_match_the_oracle(lines):
+    s, e = oracle.support(G, K, LO, HI)
+    blines = [ln for ln in lines if ln[0] == "B"]
+    assert len(blines) == 5 * 15
+    for m in range(2, 7):
+        rows = [ln for ln in blines if int(ln[1]) == m]
+        got_all, want_all, keep_all = [], [], []
+        for ln in rows:
+            z, c = float(ln[2]), int(ln[3])
+            vals = np.array(ln[4:], dtype=np.float64).reshape(5, K + 1)     # [order][q]
+            for q in range(K + 1):
+                i = c + q
+                if not 0 <= i < G + K:
+                    assert np.all(vals[:, q] == 0.0)
+                    continue
+                want = oracle.hr_basis(m, s[i], e[i], z)
+                keep = np.array([r < m or not near_knot(z) for r in range(5)])
+                got_all.append(vals[:, q]); want_all.append(want); keep_all.append(keep)
+        got, want, keep = np.array(got_all), np.array(want_all), np.array(keep_all)
+        for r in range(5):
+            scale = np.abs(want[:, r]).max()
+            err = np.abs(got[keep[:, r], r] - want[keep[:, r], r]).max()
+            assert err <= 2e-5 * scale + 1e-30, (m, r, err, scale)
+
+
+def _tol(z):
+    """float32 evaluation error of the kernels' formulas: 2e-5 of the row scale, and near a support
+    end the resolution of z itself, ulp(z) over the distance to the end (Q = 1 - u^2 is that small)."""
+    d = np.abs(KNOTS - z).min()
+    return max(2e-5, 4.0 * np.spacing(np.float32(z)) / max(d, 1e-12))
+
+
+def test_jet_rows_and_their_reverse_match_the_oracle(lines):
+    rlines = [ln for ln in lines if ln[0] == "R"]
+    assert len(rlines) == 5 * 15
+    n = G + K
+    for ln in rlines:
+        mask, m, z0, c = int(ln[1]), int(ln[2]), float(ln[3]), int(ln[4])
+        bits = [b for b in range(8) if mask >> b & 1]
+        J = len(bits)
+        A = np.array(ln[5: 5 + J * (K + 1)], dtype=np.float64).reshape(J, K + 1)
+        gz = np.array(ln[5 + J * (K + 1): 5 + J * (K + 1) + J], dtype=np.float64)
+        max_order = 1 + max(3 if b in (5, 6) else 2 if b in (3, 4, 7) else 1 for b in bits)   # the reverse
+        if max_order >= m and near_knot(z0):
+            continue
+        zin = np.array([[[z0 if b == 0 else ZR[b]]] for b in bits], dtype=np.float64)     # [J][1][1]
+        zin = zin.astype(np.float32).astype(np.float64)
+        tol = _tol(z0)
+        for q in range(K + 1):
+            i = c + q
+            if not 0 <= i < n:
+                continue
+            onehot = np.zeros(n)
+            onehot[i] = 1.0
+            want = oracle.layer_forward(1, 1, G, K, m, LO, HI, onehot, zin, mask)[:, 0, 0]
+            scale = max(1.0, np.abs(want).max())
+            assert np.abs(A[:, q] - want).max() <= tol * scale, (mask, m, z0, q, A[:, q], want)
+        w = np.array([wv(i) for i in range(n)], dtype=np.float64)
+        gy = np.array([[[np.float32(GY[r])]] for r in range(J)], dtype=np.float64)
+        want = oracle.layer_adjoint(1, 1, G, K, m, LO, HI, w, zin, gy, mask)[:, 0, 0]
+        scale = max(1.0, np.abs(want).max())
+        assert np.abs(gz - want).max() <= tol * scale, (mask, m, z0, gz, want)
