@@ -34,7 +34,28 @@ struct Grid {
 //   v''  = (-2M Q^{M-1} + 4M(M-1) u^2 Q^{M-2}) / a^2
 //   v''' = (12M(M-1) u Q^{M-2} - 8M(M-1)(M-2) u^3 Q^{M-3}) / a^3
 //   v''''= (12M(M-1) Q^{M-2} - 48M(M-1)(M-2) u^2 Q^{M-3} + 16M(M-1)(M-2)(M-3) u^4 Q^{M-4}) / a^4
+// and in general, because Q is quadratic in u (Faa di Bruno's formula with
+// Q' = -2u, Q'' = -2 and (M)_j = M(M-1)...(M-j+1), zero for j > M),
+//   d^r/du^r Q^M = sum_{j <= r/2} r!/(j!(r-2j)!) (-1)^j (M)_{r-j} (-2u)^{r-2j} Q^{M-r+j},
+// which gives the fifth and sixth derivatives
+//   v^(5) = (-120(M)_3 u Q^{M-3} + 160(M)_4 u^3 Q^{M-4} - 32(M)_5 u^5 Q^{M-5}) / a^5
+//   v^(6) = (-120(M)_3 Q^{M-3} + 720(M)_4 u^2 Q^{M-4} - 480(M)_5 u^4 Q^{M-5} + 64(M)_6 u^6 Q^{M-6}) / a^6
 // A basis index outside [0, n) gets all-zero values and a clamped index.
+template <int E>
+__host__ __device__ __forceinline__ float qpow(float Q) {
+    float r = 1.0f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) r *= Q;
+    return r;
+}
+
+// (M)_j = M (M-1) ... (M-j+1), zero once j > M.
+__host__ __device__ constexpr float falling(int M, int j) {
+    float r = 1.0f;
+    for (int t = 0; t < j; ++t) r *= float(M - t);
+    return r;
+}
+
 template <int K, int M, int NDER>
 struct Active {
     int c;               // first active basis index (may be < 0 or > n-1-K)
@@ -43,6 +64,8 @@ struct Active {
     float d2[K + 1];     // v''
     float d3[K + 1];     // v''' (only when NDER >= 3)
     float d4[K + 1];     // v'''' (only when NDER >= 4)
+    float d5[K + 1];     // v^(5) (only when NDER >= 5)
+    float d6[K + 1];     // v^(6) (only when NDER >= 6)
 
     __host__ __device__ __forceinline__ int idx(int q, int n) const {
         int i = c + q;
@@ -91,6 +114,21 @@ struct Active {
                 }
                 d4[q] = ok ? t4 * ((a1 * a1) * (a1 * a1)) : 0.0f;
             }
+            if constexpr (NDER >= 5) {
+                float t5 = 0.0f;
+                if constexpr (M >= 3) t5 -= (120.0f * falling(M, 3)) * u * qpow<M - 3>(Q);
+                if constexpr (M >= 4) t5 += (160.0f * falling(M, 4)) * u2 * u * qpow<M - 4>(Q);
+                if constexpr (M >= 5) t5 -= (32.0f * falling(M, 5)) * (u2 * u2) * u * qpow<M - 5>(Q);
+                d5[q] = ok ? t5 * ((a1 * a1) * (a1 * a1) * a1) : 0.0f;
+            }
+            if constexpr (NDER >= 6) {
+                float t6 = 0.0f;
+                if constexpr (M >= 3) t6 -= (120.0f * falling(M, 3)) * qpow<M - 3>(Q);
+                if constexpr (M >= 4) t6 += (720.0f * falling(M, 4)) * u2 * qpow<M - 4>(Q);
+                if constexpr (M >= 5) t6 -= (480.0f * falling(M, 5)) * (u2 * u2) * qpow<M - 5>(Q);
+                if constexpr (M >= 6) t6 += (64.0f * falling(M, 6)) * (u2 * u2) * u2 * qpow<M - 6>(Q);
+                d6[q] = ok ? t6 * ((a1 * a1) * (a1 * a1) * (a1 * a1)) : 0.0f;
+            }
         }
     }
 };
@@ -99,32 +137,47 @@ struct Active {
 // bit 0 = value, bit 1+d = first derivative along d, bit 3+d = second
 // derivative along d (which needs the first along d), bit 5+d = third
 // derivative along d (which needs the first and second), bit 7 = the mixed
-// derivative u_x0x1 (which needs both first derivatives).  Rows are in bit order.
+// derivative u_x0x1 (which needs both first derivatives), bit 8+d = fourth
+// derivative along d (which needs the third), bit 10+d = fifth derivative
+// along d (which needs the fourth).  Rows are in bit order.
 template <unsigned MASK>
 struct Jet {
     static constexpr bool F0 = (MASK >> 1) & 1, F1 = (MASK >> 2) & 1;
     static constexpr bool S0 = (MASK >> 3) & 1, S1 = (MASK >> 4) & 1;
     static constexpr bool T0 = (MASK >> 5) & 1, T1 = (MASK >> 6) & 1;
     static constexpr bool X01 = (MASK >> 7) & 1;
+    static constexpr bool P0 = (MASK >> 8) & 1, P1 = (MASK >> 9) & 1;     // fourth derivatives
+    static constexpr bool Q0 = (MASK >> 10) & 1, Q1 = (MASK >> 11) & 1;   // fifth derivatives
     static_assert(MASK & 1, "the value row is always present");
+    static_assert((MASK >> 12) == 0, "two inputs have twelve jet bits");
     static_assert(!S0 || F0, "u_x0x0 needs u_x0");
     static_assert(!S1 || F1, "u_x1x1 needs u_x1");
     static_assert(!T0 || S0, "u_x0x0x0 needs u_x0x0");
     static_assert(!T1 || S1, "u_x1x1x1 needs u_x1x1");
     static_assert(!X01 || (F0 && F1), "u_x0x1 needs u_x0 and u_x1");
+    static_assert(!P0 || T0, "the fourth derivative along x0 needs the third");
+    static_assert(!P1 || T1, "the fourth derivative along x1 needs the third");
+    static_assert(!Q0 || P0, "the fifth derivative along x0 needs the fourth");
+    static_assert(!Q1 || P1, "the fifth derivative along x1 needs the fourth");
     static constexpr int NF = int(F0) + int(F1);
     static constexpr int NS = int(S0) + int(S1);
     static constexpr int NT = int(T0) + int(T1);
-    static constexpr int J = 1 + NF + NS + NT + int(X01);
+    static constexpr int NP = int(P0) + int(P1);
+    static constexpr int NQ = int(Q0) + int(Q1);
+    static constexpr int J = 1 + NF + NS + NT + int(X01) + NP + NQ;
     static constexpr int RF0 = 1, RF1 = 1 + int(F0);
     static constexpr int RS0 = 1 + NF, RS1 = 1 + NF + int(S0);
     static constexpr int RT0 = 1 + NF + NS, RT1 = 1 + NF + NS + int(T0);
     static constexpr int RX = 1 + NF + NS + NT;
+    static constexpr int RP0 = RX + int(X01), RP1 = RP0 + int(P0);
+    static constexpr int RQ0 = RP0 + NP, RQ1 = RQ0 + int(Q0);
     // rows beyond the PDE masks' value / first / second derivatives
-    static constexpr bool GENERAL = NT > 0 || X01;
+    static constexpr bool GENERAL = NT > 0 || X01 || NP > 0;
+    // the fourth / fifth derivative rows
+    static constexpr bool HIGH = NP > 0;
     // basis derivatives the rows need, and their reverse (one more)
-    static constexpr int NDER_ROWS = NT ? 3 : 2;
-    static constexpr int NDER_ADJ = NT ? 4 : 3;
+    static constexpr int NDER_ROWS = NQ ? 5 : NP ? 4 : NT ? 3 : 2;
+    static constexpr int NDER_ADJ = NDER_ROWS + 1;
 
     // Rows of the basis matrix A for one input unit with jets z[J] and the
     // active basis values (v, v', v'') of its value z[0]:
@@ -265,17 +318,110 @@ struct Jet {
         }
     }
 
+    // Fourth and fifth derivatives of v(z(x)) along one input from the
+    // derivatives f1..f5 of v at z and the jets g1..g5 of z along that input
+    // (Faa di Bruno's formula):
+    //   4-row  f4 g1^4 + 6 f3 g1^2 g2 + f2 (3 g2^2 + 4 g1 g3) + f1 g4
+    //   5-row  f5 g1^5 + 10 f4 g1^3 g2 + f3 (15 g1 g2^2 + 10 g1^2 g3)
+    //          + f2 (10 g2 g3 + 5 g1 g4) + f1 g5
+    // d/dz of a row is the same polynomial with every f_r moved to f_{r+1}.
+    __host__ __device__ __forceinline__ static float row4(float f1, float f2, float f3, float f4, float g1,
+                                                          float g2, float g3, float g4) {
+        const float g11 = g1 * g1;
+        float r = fmaf(f4 * g11, g11, 6.0f * f3 * g11 * g2);
+        r = fmaf(f2, fmaf(3.0f * g2, g2, 4.0f * g1 * g3), r);
+        return fmaf(f1, g4, r);
+    }
+    __host__ __device__ __forceinline__ static float row5(float f1, float f2, float f3, float f4, float f5,
+                                                          float g1, float g2, float g3, float g4, float g5) {
+        const float g11 = g1 * g1;
+        float r = fmaf(f5 * g11 * g11, g1, 10.0f * f4 * g11 * g1 * g2);
+        r = fmaf(f3, fmaf(15.0f * g1 * g2, g2, 10.0f * g11 * g3), r);
+        r = fmaf(f2, fmaf(10.0f * g2, g3, 5.0f * g1 * g4), r);
+        return fmaf(f1, g5, r);
+    }
+
+    // The fourth / fifth derivative rows of rows3's layout (bits 8..11).
+    template <int KP, class B>
+    __host__ __device__ __forceinline__ static void rows_high(const float* z, const B& b, float (*a)[KP]) {
+#pragma unroll
+        for (int q = 0; q < KP; ++q) {
+            if constexpr (P0) a[RP0][q] = row4(b.d1[q], b.d2[q], b.d3[q], b.d4[q], z[RF0], z[RS0], z[RT0], z[RP0]);
+            if constexpr (P1) a[RP1][q] = row4(b.d1[q], b.d2[q], b.d3[q], b.d4[q], z[RF1], z[RS1], z[RT1], z[RP1]);
+            if constexpr (Q0)
+                a[RQ0][q] = row5(b.d1[q], b.d2[q], b.d3[q], b.d4[q], b.d5[q], z[RF0], z[RS0], z[RT0], z[RP0], z[RQ0]);
+            if constexpr (Q1)
+                a[RQ1][q] = row5(b.d1[q], b.d2[q], b.d3[q], b.d4[q], b.d5[q], z[RF1], z[RS1], z[RT1], z[RP1], z[RQ1]);
+        }
+    }
+
+    // Reverse of one input direction's 4-row (weight g4r = dL/dA) and 5-row
+    // (g5r; 0 without one) into the gradients of z and its jets g1..g5:
+    //   4-row: dg1 4 f4 g1^3 + 12 f3 g1 g2 + 4 f2 g3, dg2 6 f3 g1^2 + 6 f2 g2,
+    //          dg3 4 f2 g1, dg4 f1
+    //   5-row: dg1 5 f5 g1^4 + 30 f4 g1^2 g2 + f3 (15 g2^2 + 20 g1 g3) + 5 f2 g4,
+    //          dg2 10 f4 g1^3 + 30 f3 g1 g2 + 10 f2 g3, dg3 10 f3 g1^2 + 10 f2 g2,
+    //          dg4 5 f2 g1, dg5 f1
+    template <bool FIFTH>
+    __host__ __device__ __forceinline__ static void high_adjoint(const float* f, float g4r, float g5r,
+                                                                 const float* g, float& gz0, float* gg) {
+        const float g1 = g[1], g2 = g[2], g3 = g[3], g4 = g[4], g11 = g1 * g1;
+        gz0 = fmaf(g4r, row4(f[2], f[3], f[4], f[5], g1, g2, g3, g4), gz0);
+        gg[1] = fmaf(g4r, fmaf(4.0f * f[4] * g11, g1, fmaf(12.0f * f[3] * g1, g2, 4.0f * f[2] * g3)), gg[1]);
+        gg[2] = fmaf(g4r, fmaf(6.0f * f[3], g11, 6.0f * f[2] * g2), gg[2]);
+        gg[3] = fmaf(g4r * 4.0f * f[2], g1, gg[3]);
+        gg[4] = fmaf(g4r, f[1], gg[4]);
+        if constexpr (FIFTH) {
+            const float g5 = g[5];
+            gz0 = fmaf(g5r, row5(f[2], f[3], f[4], f[5], f[6], g1, g2, g3, g4, g5), gz0);
+            float t = fmaf(5.0f * f[5] * g11, g11, 30.0f * f[4] * g11 * g2);
+            t = fmaf(f[3], fmaf(15.0f * g2, g2, 20.0f * g1 * g3), t);
+            gg[1] = fmaf(g5r, fmaf(5.0f * f[2], g4, t), gg[1]);
+            gg[2] = fmaf(g5r, fmaf(10.0f * f[4] * g11, g1, fmaf(30.0f * f[3] * g1, g2, 10.0f * f[2] * g3)), gg[2]);
+            gg[3] = fmaf(g5r, fmaf(10.0f * f[3], g11, 10.0f * f[2] * g2), gg[3]);
+            gg[4] = fmaf(g5r * 5.0f * f[2], g1, gg[4]);
+            gg[5] = fmaf(g5r, f[1], gg[5]);
+        }
+    }
+
+    // Reverse of rows_high(), added to gz (rows_adjoint3 zeroes and fills the rest first).
+    template <int KP, class B>
+    __host__ __device__ __forceinline__ static void adjoint_high(const float* z, const B& b, const float (*dA)[KP],
+                                                                 float* gz) {
+#pragma unroll
+        for (int q = 0; q < KP; ++q) {
+            const float f[7] = {b.v[q], b.d1[q], b.d2[q], b.d3[q], b.d4[q],
+                                NDER_ADJ >= 5 ? b.d5[q] : 0.0f, NDER_ADJ >= 6 ? b.d6[q] : 0.0f};
+            if constexpr (P0) {
+                const float g[6] = {0.0f, z[RF0], z[RS0], z[RT0], z[RP0], Q0 ? z[RQ0] : 0.0f};
+                float gg[6] = {0.0f, gz[RF0], gz[RS0], gz[RT0], gz[RP0], Q0 ? gz[RQ0] : 0.0f};
+                high_adjoint<Q0>(f, dA[RP0][q], Q0 ? dA[RQ0][q] : 0.0f, g, gz[0], gg);
+                gz[RF0] = gg[1]; gz[RS0] = gg[2]; gz[RT0] = gg[3]; gz[RP0] = gg[4];
+                if constexpr (Q0) gz[RQ0] = gg[5];
+            }
+            if constexpr (P1) {
+                const float g[6] = {0.0f, z[RF1], z[RS1], z[RT1], z[RP1], Q1 ? z[RQ1] : 0.0f};
+                float gg[6] = {0.0f, gz[RF1], gz[RS1], gz[RT1], gz[RP1], Q1 ? gz[RQ1] : 0.0f};
+                high_adjoint<Q1>(f, dA[RP1][q], Q1 ? dA[RQ1][q] : 0.0f, g, gz[0], gg);
+                gz[RF1] = gg[1]; gz[RS1] = gg[2]; gz[RT1] = gg[3]; gz[RP1] = gg[4];
+                if constexpr (Q1) gz[RQ1] = gg[5];
+            }
+        }
+    }
+
     // The rows / their reverse for a basis evaluation b (Active<K, M, NDER_ROWS> /
     // Active<K, M, NDER_ADJ>): the PDE masks keep the second-order formulas.
     template <int KP, class B>
     __host__ __device__ __forceinline__ static void rows_b(const float* z, const B& b, float (*a)[KP]) {
         if constexpr (!GENERAL) rows<KP>(z, b.v, b.d1, b.d2, a);
         else rows3<KP>(z, b.v, b.d1, b.d2, b.d3, a);
+        if constexpr (HIGH) rows_high<KP>(z, b, a);
     }
     template <int KP, class B>
     __host__ __device__ __forceinline__ static void adjoint_b(const float* z, const B& b, const float (*dA)[KP], float* gz) {
         if constexpr (!GENERAL) rows_adjoint<KP>(z, b.d1, b.d2, b.d3, dA, gz);
         else rows_adjoint3<KP>(z, b.d1, b.d2, b.d3, b.d4, dA, gz);
+        if constexpr (HIGH) adjoint_high<KP>(z, b, dA, gz);
     }
 };
 

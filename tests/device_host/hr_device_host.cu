@@ -1,7 +1,7 @@
 // Host harness for the device basis and jet-row formulas (csrc/hr_device.cuh):
 // prints the kernels' own float32 values for a fixed set of inputs so that a
 // CPU test can compare them with the FP64 oracle.  Output lines:
-//   B m z c v0..v3 d1_0..d1_3 d2_.. d3_.. d4_..          (Active<3, m, 4>)
+//   B m z c v0..v3 d1_0..d1_3 d2_.. d3_.. d4_.. d5_.. d6_..  (Active<3, m, 6>)
 //   R mask m z c <J rows x 4 entries> <J adjoint values>  (Jet rows and their reverse)
 // Inputs of the R lines: jets z[r] = zr[r] (z[0] = the value), dA[r][q] =
 // gy[r] * w[c + q] with w[i] = wv(i) (a rank-1 gradient, as a one-output layer has).
@@ -14,8 +14,9 @@ using namespace hrkan;
 static const int G = 6, K = 3;
 static const float ZS[] = {-1.3f, -1.0f, -0.95f, -2.0f / 3.0f, -0.5f, -0.31f, -0.1f, 0.0f, 0.07f,
                            1.0f / 3.0f, 0.42f, 0.8f, 0.999f, 1.0f, 1.2f};
-static const float ZR[8] = {0.0f, 0.7f, -1.3f, 0.45f, -0.8f, 2.1f, -0.6f, 0.35f};   // z[0] replaced per line
-static const float GY[8] = {0.9f, -0.4f, 1.7f, 0.25f, -1.1f, 0.6f, 1.3f, -0.75f};
+// z[0] replaced per line
+static const float ZR[12] = {0.0f, 0.7f, -1.3f, 0.45f, -0.8f, 2.1f, -0.6f, 0.35f, -1.7f, 0.9f, 2.4f, -0.55f};
+static const float GY[12] = {0.9f, -0.4f, 1.7f, 0.25f, -1.1f, 0.6f, 1.3f, -0.75f, 0.5f, -0.95f, 0.3f, 1.15f};
 static float wv(int i) { return 0.5f - 0.17f * float(i) + 0.03f * float(i * i); }
 
 static Grid grid(int m) {
@@ -33,10 +34,10 @@ template <int M>
 static void basis() {
     const Grid g = grid(M);
     for (float z : ZS) {
-        Active<K, M, 4> a;
+        Active<K, M, 6> a;
         a.eval(z, g);
         printf("B %d %.9g %d", M, (double)z, a.c);
-        const float* arr[5] = {a.v, a.d1, a.d2, a.d3, a.d4};
+        const float* arr[7] = {a.v, a.d1, a.d2, a.d3, a.d4, a.d5, a.d6};
         for (auto* p : arr)
             for (int q = 0; q <= K; ++q) printf(" %.9g", (double)p[q]);
         printf("\n");
@@ -48,11 +49,11 @@ static void rows() {
     using JT = Jet<MASK>;
     const Grid g = grid(M);
     for (float z0 : ZS) {
-        Active<K, M, 4> a;
+        Active<K, M, 6> a;
         a.eval(z0, g);
-        float z[8], gz[8], A[8][K + 1], dA[8][K + 1];
+        float z[12], gz[12], A[12][K + 1], dA[12][K + 1];
         int r = 0;
-        for (int b = 0; b < 8; ++b)
+        for (int b = 0; b < 12; ++b)
             if (MASK & (1u << b)) z[r++] = (b == 0) ? z0 : ZR[b];
         for (int rr = 0; rr < JT::J; ++rr)
             for (int q = 0; q <= K; ++q) {
@@ -72,5 +73,6 @@ static void rows() {
 int main() {
     basis<2>(); basis<3>(); basis<4>(); basis<5>(); basis<6>();
     rows<0x1Fu, 4>(); rows<0x0Fu, 4>(); rows<0xFFu, 4>(); rows<0xFFu, 6>(); rows<0x2Fu, 3>();
+    rows<0x12Fu, 5>(); rows<0x52Fu, 6>(); rows<0x3FFu, 4>(); rows<0xFFFu, 6>();
     return 0;
 }

@@ -2,13 +2,17 @@
 the host by nvcc and run on the CPU, against the FP64 oracle.
 
 tests/device_host/hr_device_host.cu prints, in float32:
-* B lines: the k + 1 active bases of Active<3, m, 4> (v and its first four
+* B lines: the k + 1 active bases of Active<3, m, 6> (v and its first six
   derivatives) for m = 2..6 at points across and beyond the grid;
 * R lines: the basis-matrix rows of one input unit (Jet<mask>::rows_b) and
-  their reverse (adjoint_b) for masks 0x1F, 0x0F, 0xFF (m = 4 and 6) and 0x2F
-  (m = 3), with given jets and a rank-1 dA = gy[r] w[i].
+  their reverse (adjoint_b) for masks 0x1F, 0x0F, 0xFF (m = 4 and 6), 0x2F
+  (m = 3), 0x12F (fourth derivative along x0, m = 5), 0x52F (fourth and fifth,
+  m = 6), 0x3FF (fourth along both inputs, m = 4) and 0xFFF (every row, m = 6),
+  with given jets and a rank-1 dA = gy[r] w[i].
 
-The oracle gives the same quantities: hr_basis for the bases, a one-input,
+The oracle gives the same quantities: hr_basis / hr_basis6 for the bases (a
+term-by-term expansion of (1 - u^2)^m, where the kernels use powers of
+1 - u^2), a one-input,
 one-output oracle layer with one-hot weights for each row entry, and its
 input adjoint for the reverse.  At a support end the derivatives of order >= m
 jump (the kernels take the limit from inside, the oracle takes 0), so those
@@ -27,8 +31,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 G, K, LO, HI = 6, 3, -1.0, 1.0
 H = (HI - LO) / G
 KNOTS = LO + H * np.arange(-K, G + K + 1)
-ZR = [0.0, 0.7, -1.3, 0.45, -0.8, 2.1, -0.6, 0.35]
-GY = [0.9, -0.4, 1.7, 0.25, -1.1, 0.6, 1.3, -0.75]
+ZR = [0.0, 0.7, -1.3, 0.45, -0.8, 2.1, -0.6, 0.35, -1.7, 0.9, 2.4, -0.55]
+GY = [0.9, -0.4, 1.7, 0.25, -1.1, 0.6, 1.3, -0.75, 0.5, -0.95, 0.3, 1.15]
+NDER = 6
 
 
 def wv(i):
@@ -62,20 +67,23 @@ def test_basis_values_and_derivatives_match_the_oracle(lines):
         got_all, want_all, keep_all = [], [], []
         for ln in rows:
             z, c = float(ln[2]), int(ln[3])
-            vals = np.array(ln[4:], dtype=np.float64).reshape(5, K + 1)     # [order][q]
+            vals = np.array(ln[4:], dtype=np.float64).reshape(NDER + 1, K + 1)     # [order][q]
             for q in range(K + 1):
                 i = c + q
                 if not 0 <= i < G + K:
                     assert np.all(vals[:, q] == 0.0)
                     continue
-                want = oracle.hr_basis(m, s[i], e[i], z)
-                keep = np.array([r < m or not near_knot(z) for r in range(5)])
+                want = np.concatenate([oracle.hr_basis(m, s[i], e[i], z), oracle.hr_basis6(m, s[i], e[i], z)[5:]])
+                keep = np.array([r < m or not near_knot(z) for r in range(NDER + 1)])
                 got_all.append(vals[:, q]); want_all.append(want); keep_all.append(keep)
         got, want, keep = np.array(got_all), np.array(want_all), np.array(keep_all)
-        for r in range(5):
+        for r in range(NDER + 1):
             scale = np.abs(want[:, r]).max()
+            if scale == 0.0:                       # derivatives above 2m vanish
+                assert np.all(got[:, r] == 0.0), (m, r)
+                continue
             err = np.abs(got[keep[:, r], r] - want[keep[:, r], r]).max()
-            assert err <= 2e-5 * scale + 1e-30, (m, r, err, scale)
+            assert err <= 2e-5 * scale, (m, r, err, scale)
 
 
 def _tol(z):
@@ -87,15 +95,16 @@ def _tol(z):
 
 def test_jet_rows_and_their_reverse_match_the_oracle(lines):
     rlines = [ln for ln in lines if ln[0] == "R"]
-    assert len(rlines) == 5 * 15
+    assert len(rlines) == 9 * 15
     n = G + K
     for ln in rlines:
         mask, m, z0, c = int(ln[1]), int(ln[2]), float(ln[3]), int(ln[4])
-        bits = [b for b in range(8) if mask >> b & 1]
+        bits = [b for b in range(12) if mask >> b & 1]
         J = len(bits)
         A = np.array(ln[5: 5 + J * (K + 1)], dtype=np.float64).reshape(J, K + 1)
         gz = np.array(ln[5 + J * (K + 1): 5 + J * (K + 1) + J], dtype=np.float64)
-        max_order = 1 + max(3 if b in (5, 6) else 2 if b in (3, 4, 7) else 1 for b in bits)   # the reverse
+        order = {0: 0, 1: 1, 2: 1, 3: 2, 4: 2, 7: 2, 5: 3, 6: 3, 8: 4, 9: 4, 10: 5, 11: 5}
+        max_order = 1 + max(order[b] for b in bits)   # the reverse needs one more basis derivative
         if max_order >= m and near_knot(z0):
             continue
         zin = np.array([[[z0 if b == 0 else ZR[b]]] for b in bits], dtype=np.float64)     # [J][1][1]
