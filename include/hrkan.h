@@ -66,7 +66,7 @@ enum hrkan_status {
     HRKAN_EINVAL = -1,        /* bad argument (null pointer, bad size or mask) */
     HRKAN_ENOMEM = -2,        /* device or host allocation failed */
     HRKAN_ECUDA = -3,         /* a CUDA call or kernel launch failed */
-    HRKAN_EUNSUPPORTED = -4,  /* valid request that this build does not implement */
+    HRKAN_EUNSUPPORTED = -4,  /* valid request that this library does not implement */
     HRKAN_ETIMEOUT = -5,      /* a bounded device-side wait gave up */
     HRKAN_ENONFINITE = -6,    /* the loss became NaN or infinite */
     HRKAN_EIO = -7            /* a checkpoint file could not be written, or read back whole */
@@ -128,7 +128,7 @@ int64_t hrkan_param_count(const hrkan_cfg* cfg);
  * Section 4: widths, grid g, order k, HR order m).  Allocates the device
  * workspace and the FP64 Adam moments (zeroed) on the current device.
  * Returns HRKAN_EINVAL for an invalid cfg, HRKAN_EUNSUPPORTED for a valid
- * shape this build has no kernels for, HRKAN_ENOMEM if allocation fails.
+ * shape this library has no kernels for, HRKAN_ENOMEM if allocation fails.
  */
 int hrkan_init(hrkan_t* out, const hrkan_cfg* cfg);
 

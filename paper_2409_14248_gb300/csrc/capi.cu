@@ -110,7 +110,7 @@ int check_cfg(const hrkan_cfg* c) {
     if (c->G < 1 || c->G > 4096) return fail(HRKAN_EINVAL, "G=%d outside [1, 4096]", c->G);
     if (c->k < 0 || c->m < 1) return fail(HRKAN_EINVAL, "k=%d, m=%d", c->k, c->m);
     if (c->k != 3 || c->m < 2 || c->m > 6)
-        return fail(HRKAN_EUNSUPPORTED, "k=%d, m=%d: this build has k=3 and m in [2, 6]", c->k, c->m);
+        return fail(HRKAN_EUNSUPPORTED, "k=%d, m=%d: this library has k=3 and m in [2, 6]", c->k, c->m);
     if (!(c->grid_lo < c->grid_hi) || !std::isfinite(c->grid_lo) || !std::isfinite(c->grid_hi))
         return fail(HRKAN_EINVAL, "grid [%g, %g]", c->grid_lo, c->grid_hi);
     if (c->n_instances < 1) return fail(HRKAN_EINVAL, "n_instances=%d", c->n_instances);
