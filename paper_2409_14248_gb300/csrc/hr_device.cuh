@@ -1,8 +1,8 @@
 // Device building blocks of the HRKAN hot path: the HR basis with its first
-// four derivatives on the k+1 active supports (Section 3, Eq. 2), and the
+// six derivatives on the k+1 active supports (Section 3, Eq. 2), and the
 // jet-row structure that the PDE residuals need (Eq. 3: the Laplacian; Eq. 6:
-// u_t, u_x, u_xx).  The basis evaluation and the row formulas are also
-// callable on the host, where a test compares them with the FP64 oracle.
+// u_t, u_x, u_xx).  The basis evaluation, the row formulas and the residuals
+// are also callable on the host, where a test compares them with the FP64 oracle.
 #pragma once
 
 #include <cstdint>
@@ -438,7 +438,7 @@ struct PdeParams {
 };
 
 template <unsigned MASK>
-__device__ __forceinline__ float pde_residual(const PdeParams& P, float x0, float x1, const float* u) {
+__host__ __device__ __forceinline__ float pde_residual(const PdeParams& P, float x0, float x1, const float* u) {
     using JT = Jet<MASK>;
     if (P.kind == 0) {
         if constexpr (JT::S0 && JT::S1) {
@@ -460,7 +460,7 @@ __device__ __forceinline__ float pde_residual(const PdeParams& P, float x0, floa
 }
 
 template <unsigned MASK>
-__device__ __forceinline__ void pde_residual_grad(const PdeParams& P, float r, const float* u,
+__host__ __device__ __forceinline__ void pde_residual_grad(const PdeParams& P, float r, const float* u,
                                                   float scale, float* gu) {
     using JT = Jet<MASK>;
 #pragma unroll

@@ -42,6 +42,10 @@ __device__ __forceinline__ void load_unit_jets(const float* __restrict__ z, int 
         if constexpr (JT::T0) zj[JT::RT0] = 0.0f;
         if constexpr (JT::T1) zj[JT::RT1] = 0.0f;
         if constexpr (JT::X01) zj[JT::RX] = 0.0f;
+        if constexpr (JT::P0) zj[JT::RP0] = 0.0f;
+        if constexpr (JT::P1) zj[JT::RP1] = 0.0f;
+        if constexpr (JT::Q0) zj[JT::RQ0] = 0.0f;
+        if constexpr (JT::Q1) zj[JT::RQ1] = 0.0f;
     } else {
 #pragma unroll
         for (int r = 0; r < JT::J; ++r) zj[r] = z[(int64_t(r) * I + j) * N + p];

@@ -3,6 +3,7 @@
 // CPU test can compare them with the FP64 oracle.  Output lines:
 //   B m z c v0..v3 d1_0..d1_3 d2_.. d3_.. d4_.. d5_.. d6_..  (Active<3, m, 6>)
 //   R mask m z c <J rows x 4 entries> <J adjoint values>  (Jet rows and their reverse)
+//   P kind mask x0 x1 u r <J values of gu>               (pde_residual, pde_residual_grad)
 // Inputs of the R lines: jets z[r] = zr[r] (z[0] = the value), dA[r][q] =
 // gy[r] * w[c + q] with w[i] = wv(i) (a rank-1 gradient, as a one-output layer has).
 #include <cstdio>
@@ -70,9 +71,46 @@ static void rows() {
     }
 }
 
+// Residual r of one interior point and gu = dL/d(jets) for L = alpha r^2
+// (scale 2 alpha: one point), with the point's jets taken from ZR and a
+// varying value row.  Problem constants as make_pde in csrc/capi.cu sets them.
+static const double PI = 3.14159265358979323846;
+static PdeParams problem(int kind) {
+    PdeParams P{};
+    P.kind = kind;
+    P.a = 2.0f;
+    P.b = 3.0f;
+    P.src = float((2.0 * 2.0 + 3.0 * 3.0) * PI * PI);
+    P.lam = kind == 1 ? 1.0f : 6.0f;
+    P.nu = kind == 1 ? float(0.01 / PI) : 1.0f;
+    P.alpha = 0.5f;
+    return P;
+}
+
+template <unsigned MASK>
+static void residual(int kind) {
+    using JT = Jet<MASK>;
+    const PdeParams P = problem(kind);
+    static const float X0[] = {-0.9f, -0.37f, 0.0f, 0.21f, 0.64f};
+    static const float X1[] = {0.15f, -0.8f, 0.5f, 0.93f, -0.05f};
+    for (int t = 0; t < 5; ++t) {
+        float u[12], gu[12];
+        int r = 0;
+        for (int b = 0; b < 12; ++b)
+            if (MASK & (1u << b)) u[r++] = (b == 0) ? 0.3f * float(t) - 0.55f : ZR[b];
+        const float res = pde_residual<MASK>(P, X0[t], X1[t], u);
+        pde_residual_grad<MASK>(P, res, u, 2.0f * P.alpha, gu);
+        printf("P %d %u %.9g %.9g %.9g %.9g", kind, MASK, (double)X0[t], (double)X1[t], (double)u[0], (double)res);
+        for (int rr = 0; rr < JT::J; ++rr) printf(" %.9g", (double)gu[rr]);
+        printf("\n");
+    }
+}
+
 int main() {
     basis<2>(); basis<3>(); basis<4>(); basis<5>(); basis<6>();
     rows<0x1Fu, 4>(); rows<0x0Fu, 4>(); rows<0xFFu, 4>(); rows<0xFFu, 6>(); rows<0x2Fu, 3>();
     rows<0x12Fu, 5>(); rows<0x52Fu, 6>(); rows<0x3FFu, 4>(); rows<0xFFFu, 6>();
+    residual<0x1Fu>(0); residual<0xFFu>(0); residual<0x0Fu>(1); residual<0xFFu>(1); residual<0x2Fu>(2);
+    residual<0x7Fu>(2);
     return 0;
 }

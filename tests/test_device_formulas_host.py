@@ -124,3 +124,35 @@ def test_jet_rows_and_their_reverse_match_the_oracle(lines):
         want = oracle.layer_adjoint(1, 1, G, K, m, LO, HI, w, zin, gy, mask)[:, 0, 0]
         scale = max(1.0, np.abs(want).max())
         assert np.abs(gz - want).max() <= tol * scale, (mask, m, z0, gz, want)
+
+
+
+def test_residuals_and_their_jet_gradients_match_the_oracle(lines):
+    """P lines: the kernels' residual r and gu = dL/d(jets) of one point (L = alpha r^2, so gu is
+    the oracle's dL_djets for a one-point set) for Poisson (Eq. 3), Burgers (Eq. 6) and the KdV
+    residual, on the residual's own mask and on wider ones.  The oracle's gradient of the
+    residual's first row (u_xx for Poisson, u_t otherwise) is 2 alpha r, which gives its r."""
+    plines = [ln for ln in lines if ln[0] == "P"]
+    assert len(plines) == 6 * 5
+    alpha = 0.5
+    for ln in plines:
+        kind, mask = int(ln[1]), int(ln[2])
+        x0, x1, u0, r = (float(v) for v in ln[3:7])
+        bits = [b for b in range(12) if mask >> b & 1]
+        gu = np.array(ln[7:], dtype=np.float64)
+        assert gu.size == len(bits)
+        jets = np.array([[u0 if b == 0 else float(np.float32(ZR[b]))] for b in bits])
+        prob = dict(kind=kind, a=2.0, b=3.0, lam=1.0 if kind == 1 else 6.0,
+                    nu=0.01 / np.pi if kind == 1 else 1.0, alpha=alpha)
+        _, dj, _ = oracle.residual_loss(prob, np.array([[x0], [x1]]), mask, jets, np.zeros(0), np.zeros(0))
+        dj = dj[:, 0]
+        first = bits.index(3 if kind == 0 else 2)
+        r_want = dj[first] / (2.0 * alpha)
+        # float32 evaluation: a few ulps of the residual's largest term
+        terms = np.abs(jets[:, 0]).max() * max(1.0, prob["lam"] * np.abs(jets[:, 0]).max(), prob["nu"])
+        scale = terms + (13.0 * np.pi ** 2 if kind == 0 else 0.0)
+        assert abs(r - r_want) <= 2e-6 * scale, (kind, mask, r, r_want)
+        dr = np.abs(dj) / (2.0 * alpha * max(abs(r_want), 1e-30))      # |dr/d jet row|
+        tol = 2.0 * alpha * (2e-6 * scale * dr + 2e-6 * abs(r_want) * dr) + 1e-30
+        assert np.all(np.abs(gu - dj) <= tol), (kind, mask, gu, dj)
+        assert np.all((gu == 0.0) == (dj == 0.0)), (kind, mask, gu, dj)
