@@ -1,0 +1,126 @@
+// Host harness: a whole network's input jets in float32, composed from the
+// device formulas of csrc/hr_device.cuh (Active, Jet::rows_b) in the order the
+// layer-wise forward kernel accumulates them (per output and row: over input
+// units, then over the k+1 active bases, one fmaf each).  A CPU test compares
+// the result with the FP64 oracle, which shows the float32 error level of the
+// formulas through several layers, including the jet rows no kernel has been
+// instantiated for yet.
+//
+// usage: hr_net_host <in> <out>
+//   in:  int32 m, mask, n_widths, widths[n_widths], G, N; float32 lo, hi,
+//        W[params] ([layer][O][I][G+3]), x[2][N]
+//   out: float32 jets[J][N] (rows in mask-bit order)
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "../../paper_2409_14248_gb300/csrc/hr_device.cuh"
+
+using namespace hrkan;
+
+static const int K = 3, KP = K + 1, MAXW = 64;
+
+template <int M, unsigned MASK>
+static void net_forward(const std::vector<int>& widths, const Grid& g, const float* W, const float* x, long N,
+                        float* out) {
+    using JT = Jet<MASK>;
+    constexpr int J = JT::J;
+    const int L = int(widths.size()) - 1, n = g.n;
+    std::vector<float> z(size_t(J) * MAXW), y(size_t(J) * MAXW);
+    for (long p = 0; p < N; ++p) {
+        // first layer: the coordinates, with derivative 1 along their own direction
+        const int I0 = widths[0];
+        for (int r = 0; r < J; ++r)
+            for (int j = 0; j < I0; ++j) z[r * MAXW + j] = 0.0f;
+        for (int j = 0; j < I0; ++j) z[j] = x[j * N + p];
+        if constexpr (JT::F0) z[JT::RF0 * MAXW + 0] = 1.0f;
+        if constexpr (JT::F1) z[JT::RF1 * MAXW + 1] = 1.0f;
+        const float* Wl = W;
+        for (int l = 0; l < L; ++l) {
+            const int I = widths[l], O = widths[l + 1];
+            float acc[MAXW][J];
+            for (int o = 0; o < O; ++o)
+                for (int r = 0; r < J; ++r) acc[o][r] = 0.0f;
+            for (int j = 0; j < I; ++j) {
+                float zj[J];
+                for (int r = 0; r < J; ++r) zj[r] = z[r * MAXW + j];
+                Active<K, M, JT::NDER_ROWS> b;
+                b.eval(zj[0], g);
+                float a[J][KP];
+                JT::template rows_b<KP>(zj, b, a);
+                for (int q = 0; q < KP; ++q) {
+                    const int i = b.idx(q, n);
+                    for (int o = 0; o < O; ++o) {
+                        const float w = Wl[(long(o) * I + j) * n + i];
+                        for (int r = 0; r < J; ++r) acc[o][r] = fmaf(w, a[r][q], acc[o][r]);
+                    }
+                }
+            }
+            for (int r = 0; r < J; ++r)
+                for (int o = 0; o < O; ++o) y[r * MAXW + o] = acc[o][r];
+            z.swap(y);
+            Wl += long(O) * I * n;
+        }
+        for (int r = 0; r < J; ++r) out[r * N + p] = z[r * MAXW];
+    }
+}
+
+template <int M>
+static bool by_mask(unsigned mask, const std::vector<int>& w, const Grid& g, const float* W, const float* x, long N,
+                    float* out) {
+    switch (mask) {
+        case 0x0Fu: net_forward<M, 0x0Fu>(w, g, W, x, N, out); return true;
+        case 0x1Fu: net_forward<M, 0x1Fu>(w, g, W, x, N, out); return true;
+        case 0x2Fu: net_forward<M, 0x2Fu>(w, g, W, x, N, out); return true;
+        case 0xFFu: net_forward<M, 0xFFu>(w, g, W, x, N, out); return true;
+        case 0x12Fu: net_forward<M, 0x12Fu>(w, g, W, x, N, out); return true;
+        case 0x52Fu: net_forward<M, 0x52Fu>(w, g, W, x, N, out); return true;
+        case 0xFFFu: net_forward<M, 0xFFFu>(w, g, W, x, N, out); return true;
+    }
+    return false;
+}
+
+static bool rd(FILE* f, void* p, size_t bytes) { return fread(p, 1, bytes, f) == bytes; }
+
+int main(int argc, char** argv) {
+    if (argc != 3) return 2;
+    FILE* f = fopen(argv[1], "rb");
+    if (!f) return 3;
+    int m = 0, nw = 0, G = 0, N = 0;
+    unsigned mask = 0;
+    if (!rd(f, &m, 4) || !rd(f, &mask, 4) || !rd(f, &nw, 4) || nw < 2 || nw > 16) return 4;
+    std::vector<int> widths(nw);
+    if (!rd(f, widths.data(), 4 * size_t(nw)) || !rd(f, &G, 4) || !rd(f, &N, 4) || G < 1 || N < 1) return 4;
+    if (widths[0] != 2 || widths[nw - 1] != 1) return 4;
+    for (int w : widths)
+        if (w < 1 || w > MAXW) return 4;
+    float lo = 0.0f, hi = 0.0f;
+    if (!rd(f, &lo, 4) || !rd(f, &hi, 4)) return 4;
+    const int n = G + K;
+    long P = 0;
+    for (int l = 0; l + 1 < nw; ++l) P += long(widths[l]) * widths[l + 1] * n;
+    std::vector<float> W(P), x(2 * size_t(N));
+    if (!rd(f, W.data(), 4 * size_t(P)) || !rd(f, x.data(), 8 * size_t(N))) return 4;
+    fclose(f);
+    Grid g;   // as the library's handle sets it up
+    const double hh = (double(hi) - double(lo)) / G;
+    g.lo = lo;
+    g.h = float(hh);
+    g.inv_h = float(1.0 / hh);
+    g.inv_a = float(2.0 / ((K + 1) * hh));
+    g.m = m;
+    g.n = n;
+    int J = 0;
+    for (int b = 0; b < 12; ++b) J += (mask >> b) & 1;
+    std::vector<float> out(size_t(J) * N);
+    bool ok = false;
+    switch (m) {
+        case 4: ok = by_mask<4>(mask, widths, g, W.data(), x.data(), N, out.data()); break;
+        case 6: ok = by_mask<6>(mask, widths, g, W.data(), x.data(), N, out.data()); break;
+    }
+    if (!ok) return 5;
+    FILE* o = fopen(argv[2], "wb");
+    if (!o || fwrite(out.data(), 4, out.size(), o) != out.size()) return 6;
+    fclose(o);
+    return 0;
+}

@@ -1,0 +1,73 @@
+"""Whole-network float32 jets composed from the kernels' own formulas, on the CPU,
+against the FP64 oracle.
+
+tests/device_host/hr_net_host.cu runs a network forward with the device code of
+csrc/hr_device.cuh (Active basis evaluation, Jet rows) compiled for the host, in
+the order the layer-wise forward kernel accumulates (per output and row: over
+input units, then the k+1 active bases, one fmaf each), first-layer jets seeded
+as the kernels seed them.  This checks that the float32 formulas compose through
+several layers to the FP32 bar (1e-5 on u, 1e-4 on every derivative row,
+normwise per row) for the PDE masks, the third/mixed-derivative masks and the
+fourth/fifth-derivative masks (0x12F, 0x52F, 0xFFF) that no kernel is
+instantiated for yet.  Shapes: Burgers [2,32,32,1] G=20 m=4 and a [2,24,24,1]
+G=12 m=6 net (Section 3 picks m = 6 for a fifth derivative), workload weights
+N(0, 0.1^2), 300 interior points."""
+import dataclasses
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import TOL_D, TOL_U, relerr
+from paper_2409_14248_gb300 import build, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+MASKS = [0x0F, 0x1F, 0x2F, 0xFF, 0x12F, 0x52F, 0xFFF]
+
+
+@pytest.fixture(scope="module")
+def exe(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc is not installed")
+    path = str(tmp_path_factory.mktemp("hnh") / "hr_net_host")
+    src = os.path.join(ROOT, "tests", "device_host", "hr_net_host.cu")
+    r = subprocess.run([nvcc, "-std=c++17", "-O1", *build.ARCH, src, "-o", path], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return path
+
+
+def _workload(name):
+    if name == "m6":
+        return dataclasses.replace(inputs.WORKLOADS["poisson_2_64x3_1"], widths=[2, 24, 24, 1], G=12, m=6)
+    return inputs.WORKLOADS["burgers_2_32_32_1"]
+
+
+def _run(exe, tmp_path, w, W, x, mask):
+    N = x.shape[1]
+    fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
+    with open(fin, "wb") as f:
+        f.write(np.array([w.m, mask, len(w.widths), *w.widths, w.G, N], dtype=np.int32).tobytes())
+        f.write(np.array([w.lo, w.hi], dtype=np.float32).tobytes())
+        f.write(np.ascontiguousarray(W, dtype=np.float32).tobytes())
+        f.write(np.ascontiguousarray(x, dtype=np.float32).tobytes())
+    r = subprocess.run([exe, fin, fout], capture_output=True, timeout=120)
+    assert r.returncode == 0, r.returncode
+    return np.fromfile(fout, dtype=np.float32).reshape(oracle.n_rows(mask), N)
+
+
+@pytest.mark.parametrize("mask", MASKS)
+@pytest.mark.parametrize("name", ["burgers", "m6"])
+def test_float32_network_jets_reach_the_fp32_bar(exe, tmp_path, name, mask):
+    w = _workload(name)
+    d = inputs.make(w, n_int=300, n_bnd=40, n_ic=20, n_bc=20)
+    x = np.asarray(d["x_int"], dtype=np.float32)
+    got = _run(exe, tmp_path, w, d["W"], x, mask)
+    want = oracle.forward(w.net, np.asarray(d["W"], dtype=np.float64), x.astype(np.float64), mask)
+    for r in range(want.shape[0]):
+        tol = TOL_U if r == 0 else TOL_D
+        assert relerr(got[r], want[r]) < tol, (name, hex(mask), r, relerr(got[r], want[r]))
+        assert relerr(got[r], want[r]) > 0.0       # float32 arithmetic, not a copy of the oracle
