@@ -6,10 +6,10 @@
 // formulas through several layers, including the jet rows no kernel has been
 // instantiated for yet.
 //
-// usage: hr_net_host <in> <out>
+// usage: hr_net_host <in> <out> [bwd]
 //   in:  int32 m, mask, n_widths, widths[n_widths], G, N; float32 lo, hi,
-//        W[params] ([layer][O][I][G+3]), x[2][N]
-//   out: float32 jets[J][N] (rows in mask-bit order)
+//        W[params] ([layer][O][I][G+3]), x[2][N], and with bwd gy[J][N]
+//   out: float32 jets[J][N] (rows in mask-bit order), or with bwd float64 dW[params]
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -65,6 +65,101 @@ static void net_forward(const std::vector<int>& widths, const Grid& g, const flo
     }
 }
 
+// Weight gradient for output-jet gradients gy[J][N]: per point, the forward
+// with its layer inputs kept, then from the last layer down dW += gy^T A (the
+// rows of rows_b) and dA = gy W, taken to the layer's input jets by adjoint_b.
+// Per point everything is float32 (fmaf); the sum over points is float64, so
+// the result shows the formulas' error rather than a summation order's.
+template <int M, unsigned MASK>
+static void net_backward(const std::vector<int>& widths, const Grid& g, const float* W, const float* x, long N,
+                         const float* gy, double* dW) {
+    using JT = Jet<MASK>;
+    constexpr int J = JT::J;
+    const int L = int(widths.size()) - 1, n = g.n;
+    std::vector<long> off(L + 1, 0);
+    for (int l = 0; l < L; ++l) off[l + 1] = off[l] + long(widths[l]) * widths[l + 1] * n;
+    for (long i = 0; i < off[L]; ++i) dW[i] = 0.0;
+    std::vector<float> tape(size_t(L) * J * MAXW), gcur(size_t(J) * MAXW), gnext(size_t(J) * MAXW);
+    for (long p = 0; p < N; ++p) {
+        float* z0 = tape.data();
+        for (int r = 0; r < J; ++r)
+            for (int j = 0; j < MAXW; ++j) z0[r * MAXW + j] = 0.0f;
+        for (int j = 0; j < widths[0]; ++j) z0[j] = x[j * N + p];
+        if constexpr (JT::F0) z0[JT::RF0 * MAXW + 0] = 1.0f;
+        if constexpr (JT::F1) z0[JT::RF1 * MAXW + 1] = 1.0f;
+        for (int l = 0; l + 1 < L; ++l) {      // inputs of layers 1 .. L-1
+            const int I = widths[l], O = widths[l + 1];
+            const float* z = tape.data() + size_t(l) * J * MAXW;
+            float* y = tape.data() + size_t(l + 1) * J * MAXW;
+            float acc[MAXW][J];
+            for (int o = 0; o < O; ++o)
+                for (int r = 0; r < J; ++r) acc[o][r] = 0.0f;
+            for (int j = 0; j < I; ++j) {
+                float zj[J];
+                for (int r = 0; r < J; ++r) zj[r] = z[r * MAXW + j];
+                Active<K, M, JT::NDER_ROWS> b;
+                b.eval(zj[0], g);
+                float a[J][KP];
+                JT::template rows_b<KP>(zj, b, a);
+                for (int q = 0; q < KP; ++q)
+                    for (int o = 0; o < O; ++o) {
+                        const float w = W[off[l] + (long(o) * I + j) * n + b.idx(q, n)];
+                        for (int r = 0; r < J; ++r) acc[o][r] = fmaf(w, a[r][q], acc[o][r]);
+                    }
+            }
+            for (int r = 0; r < J; ++r)
+                for (int o = 0; o < O; ++o) y[r * MAXW + o] = acc[o][r];
+        }
+        for (int r = 0; r < J; ++r) gcur[r * MAXW] = gy[r * N + p];
+        for (int l = L - 1; l >= 0; --l) {
+            const int I = widths[l], O = widths[l + 1];
+            const float* z = tape.data() + size_t(l) * J * MAXW;
+            for (int j = 0; j < I; ++j) {
+                float zj[J];
+                for (int r = 0; r < J; ++r) zj[r] = z[r * MAXW + j];
+                Active<K, M, JT::NDER_ADJ> b;
+                b.eval(zj[0], g);
+                float a[J][KP], dA[J][KP];
+                JT::template rows_b<KP>(zj, b, a);
+                for (int q = 0; q < KP; ++q) {
+                    const int i = b.idx(q, n);
+                    for (int r = 0; r < J; ++r) dA[r][q] = 0.0f;
+                    for (int o = 0; o < O; ++o) {
+                        const long wi = off[l] + (long(o) * I + j) * n + i;
+                        float gw = 0.0f;
+                        for (int r = 0; r < J; ++r) {
+                            gw = fmaf(gcur[r * MAXW + o], a[r][q], gw);
+                            dA[r][q] = fmaf(gcur[r * MAXW + o], W[wi], dA[r][q]);
+                        }
+                        dW[wi] += double(gw);
+                    }
+                }
+                if (l > 0) {
+                    float gz[J];
+                    JT::template adjoint_b<KP>(zj, b, dA, gz);
+                    for (int r = 0; r < J; ++r) gnext[r * MAXW + j] = gz[r];
+                }
+            }
+            gcur.swap(gnext);
+        }
+    }
+}
+
+template <int M>
+static bool by_mask_bwd(unsigned mask, const std::vector<int>& w, const Grid& g, const float* W, const float* x,
+                        long N, const float* gy, double* dW) {
+    switch (mask) {
+        case 0x0Fu: net_backward<M, 0x0Fu>(w, g, W, x, N, gy, dW); return true;
+        case 0x1Fu: net_backward<M, 0x1Fu>(w, g, W, x, N, gy, dW); return true;
+        case 0x2Fu: net_backward<M, 0x2Fu>(w, g, W, x, N, gy, dW); return true;
+        case 0xFFu: net_backward<M, 0xFFu>(w, g, W, x, N, gy, dW); return true;
+        case 0x12Fu: net_backward<M, 0x12Fu>(w, g, W, x, N, gy, dW); return true;
+        case 0x52Fu: net_backward<M, 0x52Fu>(w, g, W, x, N, gy, dW); return true;
+        case 0xFFFu: net_backward<M, 0xFFFu>(w, g, W, x, N, gy, dW); return true;
+    }
+    return false;
+}
+
 template <int M>
 static bool by_mask(unsigned mask, const std::vector<int>& w, const Grid& g, const float* W, const float* x, long N,
                     float* out) {
@@ -83,7 +178,8 @@ static bool by_mask(unsigned mask, const std::vector<int>& w, const Grid& g, con
 static bool rd(FILE* f, void* p, size_t bytes) { return fread(p, 1, bytes, f) == bytes; }
 
 int main(int argc, char** argv) {
-    if (argc != 3) return 2;
+    if (argc != 3 && argc != 4) return 2;
+    const bool bwd = argc == 4;
     FILE* f = fopen(argv[1], "rb");
     if (!f) return 3;
     int m = 0, nw = 0, G = 0, N = 0;
@@ -101,6 +197,10 @@ int main(int argc, char** argv) {
     for (int l = 0; l + 1 < nw; ++l) P += long(widths[l]) * widths[l + 1] * n;
     std::vector<float> W(P), x(2 * size_t(N));
     if (!rd(f, W.data(), 4 * size_t(P)) || !rd(f, x.data(), 8 * size_t(N))) return 4;
+    int J = 0;
+    for (int b = 0; b < 12; ++b) J += (mask >> b) & 1;
+    std::vector<float> gy(bwd ? size_t(J) * N : 0);
+    if (bwd && !rd(f, gy.data(), 4 * gy.size())) return 4;
     fclose(f);
     Grid g;   // as the library's handle sets it up
     const double hh = (double(hi) - double(lo)) / G;
@@ -110,8 +210,19 @@ int main(int argc, char** argv) {
     g.inv_a = float(2.0 / ((K + 1) * hh));
     g.m = m;
     g.n = n;
-    int J = 0;
-    for (int b = 0; b < 12; ++b) J += (mask >> b) & 1;
+    if (bwd) {
+        std::vector<double> dW(P);
+        bool ok = false;
+        switch (m) {
+            case 4: ok = by_mask_bwd<4>(mask, widths, g, W.data(), x.data(), N, gy.data(), dW.data()); break;
+            case 6: ok = by_mask_bwd<6>(mask, widths, g, W.data(), x.data(), N, gy.data(), dW.data()); break;
+        }
+        if (!ok) return 5;
+        FILE* o = fopen(argv[2], "wb");
+        if (!o || fwrite(dW.data(), 8, dW.size(), o) != dW.size()) return 6;
+        fclose(o);
+        return 0;
+    }
     std::vector<float> out(size_t(J) * N);
     bool ok = false;
     switch (m) {

@@ -9,8 +9,10 @@ as the kernels seed them.  This checks that the float32 formulas compose through
 several layers to the FP32 bar (1e-5 on u, 1e-4 on every derivative row,
 normwise per row) for the PDE masks, the third/mixed-derivative masks and the
 fourth/fifth-derivative masks (0x12F, 0x52F, 0xFFF) that no kernel is
-instantiated for yet.  Shapes: Burgers [2,32,32,1] G=20 m=4 and a [2,24,24,1]
-G=12 m=6 net (Section 3 picks m = 6 for a fifth derivative), workload weights
+instantiated for yet.  The backward takes seeded output-jet gradients through
+the same formulas in reverse (Jet::adjoint_b for the input adjoint, the rows
+for the weight gradient) and meets the 1e-4 weight-gradient bar per layer.
+Shapes: Burgers [2,32,32,1] G=20 m=4 and a [2,24,24,1] G=12 m=6 net (Section 3 picks m = 6 for a fifth derivative), workload weights
 N(0, 0.1^2), 300 interior points."""
 import dataclasses
 import os
@@ -21,7 +23,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import TOL_D, TOL_U, relerr
+from gpu_util import TOL_D, TOL_U, layer_slices, relerr
 from paper_2409_14248_gb300 import build, inputs
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -46,7 +48,7 @@ def _workload(name):
     return inputs.WORKLOADS["burgers_2_32_32_1"]
 
 
-def _run(exe, tmp_path, w, W, x, mask):
+def _run(exe, tmp_path, w, W, x, mask, gy=None):
     N = x.shape[1]
     fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
     with open(fin, "wb") as f:
@@ -54,8 +56,12 @@ def _run(exe, tmp_path, w, W, x, mask):
         f.write(np.array([w.lo, w.hi], dtype=np.float32).tobytes())
         f.write(np.ascontiguousarray(W, dtype=np.float32).tobytes())
         f.write(np.ascontiguousarray(x, dtype=np.float32).tobytes())
-    r = subprocess.run([exe, fin, fout], capture_output=True, timeout=120)
+        if gy is not None:
+            f.write(np.ascontiguousarray(gy, dtype=np.float32).tobytes())
+    r = subprocess.run([exe, fin, fout] + ([] if gy is None else ["bwd"]), capture_output=True, timeout=120)
     assert r.returncode == 0, r.returncode
+    if gy is not None:
+        return np.fromfile(fout, dtype=np.float64)
     return np.fromfile(fout, dtype=np.float32).reshape(oracle.n_rows(mask), N)
 
 
@@ -71,3 +77,17 @@ def test_float32_network_jets_reach_the_fp32_bar(exe, tmp_path, name, mask):
         tol = TOL_U if r == 0 else TOL_D
         assert relerr(got[r], want[r]) < tol, (name, hex(mask), r, relerr(got[r], want[r]))
         assert relerr(got[r], want[r]) > 0.0       # float32 arithmetic, not a copy of the oracle
+
+
+@pytest.mark.parametrize("mask", MASKS)
+@pytest.mark.parametrize("name", ["burgers", "m6"])
+def test_float32_network_weight_gradient_reaches_the_fp32_bar(exe, tmp_path, name, mask):
+    w = _workload(name)
+    d = inputs.make(w, n_int=300, n_bnd=40, n_ic=20, n_bc=20)
+    x = np.asarray(d["x_int"], dtype=np.float32)
+    gy = np.random.default_rng(5).standard_normal((oracle.n_rows(mask), x.shape[1])).astype(np.float32)
+    got = _run(exe, tmp_path, w, d["W"], x, mask, gy)
+    want = oracle.backward(w.net, np.asarray(d["W"], dtype=np.float64), x.astype(np.float64), mask,
+                           gy.astype(np.float64))
+    for l, sl in enumerate(layer_slices(w.widths, w.G)):
+        assert 0.0 < relerr(got[sl], want[sl]) < TOL_D, (name, hex(mask), l, relerr(got[sl], want[sl]))
