@@ -7,8 +7,11 @@
 // instantiated for yet.
 //
 // usage: hr_net_host <in> <out> [bwd]
-//   in:  int32 m, mask, n_widths, widths[n_widths], G, N; float32 lo, hi,
-//        W[params] ([layer][O][I][G+3]), x[2][N], and with bwd gy[J][N]
+//   in:  int32 m, mask, n_widths, widths[n_widths], G, N, seed0, seed1;
+//        float32 lo, hi, W[params] ([layer][O][I][G+3]), x[widths[0]][N], and
+//        with bwd gy[J][N].  The first layer's derivative rows differentiate
+//        along inputs seed0 and seed1 (-1: along none), as the kernels seed
+//        them: three-input networks run as a pass along (x, y) and one along z.
 //   out: float32 jets[J][N] (rows in mask-bit order), or with bwd float64 dW[params]
 #include <cstdio>
 #include <cstdlib>
@@ -22,19 +25,19 @@ static const int K = 3, KP = K + 1, MAXW = 64;
 
 template <int M, unsigned MASK>
 static void net_forward(const std::vector<int>& widths, const Grid& g, const float* W, const float* x, long N,
-                        float* out) {
+                        int seed0, int seed1, float* out) {
     using JT = Jet<MASK>;
     constexpr int J = JT::J;
     const int L = int(widths.size()) - 1, n = g.n;
     std::vector<float> z(size_t(J) * MAXW), y(size_t(J) * MAXW);
     for (long p = 0; p < N; ++p) {
-        // first layer: the coordinates, with derivative 1 along their own direction
+        // first layer: the coordinates, with derivative 1 along the seeded directions
         const int I0 = widths[0];
         for (int r = 0; r < J; ++r)
             for (int j = 0; j < I0; ++j) z[r * MAXW + j] = 0.0f;
         for (int j = 0; j < I0; ++j) z[j] = x[j * N + p];
-        if constexpr (JT::F0) z[JT::RF0 * MAXW + 0] = 1.0f;
-        if constexpr (JT::F1) z[JT::RF1 * MAXW + 1] = 1.0f;
+        if constexpr (JT::F0) if (seed0 >= 0) z[JT::RF0 * MAXW + seed0] = 1.0f;
+        if constexpr (JT::F1) if (seed1 >= 0) z[JT::RF1 * MAXW + seed1] = 1.0f;
         const float* Wl = W;
         for (int l = 0; l < L; ++l) {
             const int I = widths[l], O = widths[l + 1];
@@ -72,7 +75,7 @@ static void net_forward(const std::vector<int>& widths, const Grid& g, const flo
 // the result shows the formulas' error rather than a summation order's.
 template <int M, unsigned MASK>
 static void net_backward(const std::vector<int>& widths, const Grid& g, const float* W, const float* x, long N,
-                         const float* gy, double* dW) {
+                         int seed0, int seed1, const float* gy, double* dW) {
     using JT = Jet<MASK>;
     constexpr int J = JT::J;
     const int L = int(widths.size()) - 1, n = g.n;
@@ -85,8 +88,8 @@ static void net_backward(const std::vector<int>& widths, const Grid& g, const fl
         for (int r = 0; r < J; ++r)
             for (int j = 0; j < MAXW; ++j) z0[r * MAXW + j] = 0.0f;
         for (int j = 0; j < widths[0]; ++j) z0[j] = x[j * N + p];
-        if constexpr (JT::F0) z0[JT::RF0 * MAXW + 0] = 1.0f;
-        if constexpr (JT::F1) z0[JT::RF1 * MAXW + 1] = 1.0f;
+        if constexpr (JT::F0) if (seed0 >= 0) z0[JT::RF0 * MAXW + seed0] = 1.0f;
+        if constexpr (JT::F1) if (seed1 >= 0) z0[JT::RF1 * MAXW + seed1] = 1.0f;
         for (int l = 0; l + 1 < L; ++l) {      // inputs of layers 1 .. L-1
             const int I = widths[l], O = widths[l + 1];
             const float* z = tape.data() + size_t(l) * J * MAXW;
@@ -147,30 +150,30 @@ static void net_backward(const std::vector<int>& widths, const Grid& g, const fl
 
 template <int M>
 static bool by_mask_bwd(unsigned mask, const std::vector<int>& w, const Grid& g, const float* W, const float* x,
-                        long N, const float* gy, double* dW) {
+                        long N, int s0, int s1, const float* gy, double* dW) {
     switch (mask) {
-        case 0x0Fu: net_backward<M, 0x0Fu>(w, g, W, x, N, gy, dW); return true;
-        case 0x1Fu: net_backward<M, 0x1Fu>(w, g, W, x, N, gy, dW); return true;
-        case 0x2Fu: net_backward<M, 0x2Fu>(w, g, W, x, N, gy, dW); return true;
-        case 0xFFu: net_backward<M, 0xFFu>(w, g, W, x, N, gy, dW); return true;
-        case 0x12Fu: net_backward<M, 0x12Fu>(w, g, W, x, N, gy, dW); return true;
-        case 0x52Fu: net_backward<M, 0x52Fu>(w, g, W, x, N, gy, dW); return true;
-        case 0xFFFu: net_backward<M, 0xFFFu>(w, g, W, x, N, gy, dW); return true;
+        case 0x0Fu: net_backward<M, 0x0Fu>(w, g, W, x, N, s0, s1, gy, dW); return true;
+        case 0x1Fu: net_backward<M, 0x1Fu>(w, g, W, x, N, s0, s1, gy, dW); return true;
+        case 0x2Fu: net_backward<M, 0x2Fu>(w, g, W, x, N, s0, s1, gy, dW); return true;
+        case 0xFFu: net_backward<M, 0xFFu>(w, g, W, x, N, s0, s1, gy, dW); return true;
+        case 0x12Fu: net_backward<M, 0x12Fu>(w, g, W, x, N, s0, s1, gy, dW); return true;
+        case 0x52Fu: net_backward<M, 0x52Fu>(w, g, W, x, N, s0, s1, gy, dW); return true;
+        case 0xFFFu: net_backward<M, 0xFFFu>(w, g, W, x, N, s0, s1, gy, dW); return true;
     }
     return false;
 }
 
 template <int M>
 static bool by_mask(unsigned mask, const std::vector<int>& w, const Grid& g, const float* W, const float* x, long N,
-                    float* out) {
+                    int s0, int s1, float* out) {
     switch (mask) {
-        case 0x0Fu: net_forward<M, 0x0Fu>(w, g, W, x, N, out); return true;
-        case 0x1Fu: net_forward<M, 0x1Fu>(w, g, W, x, N, out); return true;
-        case 0x2Fu: net_forward<M, 0x2Fu>(w, g, W, x, N, out); return true;
-        case 0xFFu: net_forward<M, 0xFFu>(w, g, W, x, N, out); return true;
-        case 0x12Fu: net_forward<M, 0x12Fu>(w, g, W, x, N, out); return true;
-        case 0x52Fu: net_forward<M, 0x52Fu>(w, g, W, x, N, out); return true;
-        case 0xFFFu: net_forward<M, 0xFFFu>(w, g, W, x, N, out); return true;
+        case 0x0Fu: net_forward<M, 0x0Fu>(w, g, W, x, N, s0, s1, out); return true;
+        case 0x1Fu: net_forward<M, 0x1Fu>(w, g, W, x, N, s0, s1, out); return true;
+        case 0x2Fu: net_forward<M, 0x2Fu>(w, g, W, x, N, s0, s1, out); return true;
+        case 0xFFu: net_forward<M, 0xFFu>(w, g, W, x, N, s0, s1, out); return true;
+        case 0x12Fu: net_forward<M, 0x12Fu>(w, g, W, x, N, s0, s1, out); return true;
+        case 0x52Fu: net_forward<M, 0x52Fu>(w, g, W, x, N, s0, s1, out); return true;
+        case 0xFFFu: net_forward<M, 0xFFFu>(w, g, W, x, N, s0, s1, out); return true;
     }
     return false;
 }
@@ -186,8 +189,11 @@ int main(int argc, char** argv) {
     unsigned mask = 0;
     if (!rd(f, &m, 4) || !rd(f, &mask, 4) || !rd(f, &nw, 4) || nw < 2 || nw > 16) return 4;
     std::vector<int> widths(nw);
+    int seed0 = 0, seed1 = 1;
     if (!rd(f, widths.data(), 4 * size_t(nw)) || !rd(f, &G, 4) || !rd(f, &N, 4) || G < 1 || N < 1) return 4;
-    if (widths[0] != 2 || widths[nw - 1] != 1) return 4;
+    if (!rd(f, &seed0, 4) || !rd(f, &seed1, 4)) return 4;
+    if (widths[0] < 2 || widths[0] > 3 || widths[nw - 1] != 1) return 4;
+    if (seed0 < -1 || seed0 >= widths[0] || seed1 < -1 || seed1 >= widths[0]) return 4;
     for (int w : widths)
         if (w < 1 || w > MAXW) return 4;
     float lo = 0.0f, hi = 0.0f;
@@ -195,8 +201,8 @@ int main(int argc, char** argv) {
     const int n = G + K;
     long P = 0;
     for (int l = 0; l + 1 < nw; ++l) P += long(widths[l]) * widths[l + 1] * n;
-    std::vector<float> W(P), x(2 * size_t(N));
-    if (!rd(f, W.data(), 4 * size_t(P)) || !rd(f, x.data(), 8 * size_t(N))) return 4;
+    std::vector<float> W(P), x(size_t(widths[0]) * N);
+    if (!rd(f, W.data(), 4 * size_t(P)) || !rd(f, x.data(), 4 * x.size())) return 4;
     int J = 0;
     for (int b = 0; b < 12; ++b) J += (mask >> b) & 1;
     std::vector<float> gy(bwd ? size_t(J) * N : 0);
@@ -214,8 +220,8 @@ int main(int argc, char** argv) {
         std::vector<double> dW(P);
         bool ok = false;
         switch (m) {
-            case 4: ok = by_mask_bwd<4>(mask, widths, g, W.data(), x.data(), N, gy.data(), dW.data()); break;
-            case 6: ok = by_mask_bwd<6>(mask, widths, g, W.data(), x.data(), N, gy.data(), dW.data()); break;
+            case 4: ok = by_mask_bwd<4>(mask, widths, g, W.data(), x.data(), N, seed0, seed1, gy.data(), dW.data()); break;
+            case 6: ok = by_mask_bwd<6>(mask, widths, g, W.data(), x.data(), N, seed0, seed1, gy.data(), dW.data()); break;
         }
         if (!ok) return 5;
         FILE* o = fopen(argv[2], "wb");
@@ -226,8 +232,8 @@ int main(int argc, char** argv) {
     std::vector<float> out(size_t(J) * N);
     bool ok = false;
     switch (m) {
-        case 4: ok = by_mask<4>(mask, widths, g, W.data(), x.data(), N, out.data()); break;
-        case 6: ok = by_mask<6>(mask, widths, g, W.data(), x.data(), N, out.data()); break;
+        case 4: ok = by_mask<4>(mask, widths, g, W.data(), x.data(), N, seed0, seed1, out.data()); break;
+        case 6: ok = by_mask<6>(mask, widths, g, W.data(), x.data(), N, seed0, seed1, out.data()); break;
     }
     if (!ok) return 5;
     FILE* o = fopen(argv[2], "wb");
