@@ -175,9 +175,12 @@ static void row5_dg(const double* f, const double* g, double* dg)
  *   ORC_BF16: to bfloat16, round to nearest even (8-bit significand);
  *   ORC_TF32: to TF32, round to nearest with ties away from zero (11-bit significand);
  *   ORC_BF16W2: operands as ORC_BF16, weights as the sum of two bfloat16
- *   values (round_w below: a contraction split into A_hi W_hi + A_hi W_lo).
+ *   values (round_w below: a contraction split into A_hi W_hi + A_hi W_lo);
+ *   ORC_BF16X3: both factors of every product as the sum of two bfloat16
+ *   values, x = x_hi + x_lo, and the product taken as
+ *   x_hi y_hi + x_hi y_lo + x_lo y_hi (the x_lo y_lo term dropped; prod3 below).
  */
-enum { ORC_EXACT = 0, ORC_BF16 = 1, ORC_TF32 = 2, ORC_BF16W2 = 3 };
+enum { ORC_EXACT = 0, ORC_BF16 = 1, ORC_TF32 = 2, ORC_BF16W2 = 3, ORC_BF16X3 = 4 };
 
 static double round_to(double x, int fmt)
 {
@@ -185,7 +188,7 @@ static double round_to(double x, int fmt)
     float f = (float)x;
     uint32_t u;
     memcpy(&u, &f, 4);
-    if (fmt == ORC_BF16 || fmt == ORC_BF16W2) {
+    if (fmt == ORC_BF16 || fmt == ORC_BF16W2 || fmt == ORC_BF16X3) {
         u += 0x7FFFu + ((u >> 16) & 1u);
         u &= 0xFFFF0000u;
     } else {
@@ -208,6 +211,41 @@ static double round_w(double x, int fmt)
     float hi = (float)round_to(w, ORC_BF16);
     float lo = (float)round_to(w - hi, ORC_BF16);
     return (double)hi + (double)lo;
+}
+
+/* x rounded to float32 and carried as hi + lo: hi = bf16(x), lo = bf16(x - hi)
+ * (x - hi is exact in float32). */
+static void split_bf16(double x, double* hi, double* lo)
+{
+    float f = (float)x;
+    float h = (float)round_to(f, ORC_BF16);
+    *hi = (double)h;
+    *lo = round_to(f - h, ORC_BF16);
+}
+
+/* The product x y as a contraction in format fmt sees it: under ORC_BF16X3 the
+ * three-term split of both factors, otherwise x rounded by round_to and y by
+ * wround (round_to, or round_w for weights). */
+static double prod3(double x, double y)
+{
+    double xh, xl, yh, yl;
+    split_bf16(x, &xh, &xl);
+    split_bf16(y, &yh, &yl);
+    return xh * yh + xh * yl + xl * yh;
+}
+
+/* A weight w times a basis-matrix entry a (or an output-jet gradient a) under fmt. */
+static double wmul(double w, double a, int fmt)
+{
+    if (fmt == ORC_BF16X3) return prod3(a, w);
+    return round_w(w, fmt) * round_to(a, fmt);
+}
+
+/* An output-jet gradient g times a basis-matrix entry a under fmt (weight gradient). */
+static double gmul(double g, double a, int fmt)
+{
+    if (fmt == ORC_BF16X3) return prod3(g, a);
+    return round_to(g, fmt) * round_to(a, fmt);
 }
 
 /* ---------------------------------------------------------------- network */
@@ -271,14 +309,14 @@ static void layer_forward(const orc_net* net, int l, const double* Wl, int D,
             double b[5];
             orc_hr_basis(net->m, s[i], e[i], z[j], b);
             /* the basis-matrix entries (jet rows) of this input unit and basis */
-            double a0 = round_to(b[0], fmt), a1[8], a2[8], a3[8];
+            double a0 = b[0], a1[8], a2[8], a3[8];
             for (int d = 0; d < D; ++d) {
                 double zd = dz[j * D + d], zdd = d2z[j * D + d], zddd = d3z[j * D + d];
-                a1[d] = round_to(b[1] * zd, fmt);
-                a2[d] = round_to(b[2] * zd * zd + b[1] * zdd, fmt);
-                a3[d] = round_to(b[3] * zd * zd * zd + 3.0 * b[2] * zd * zdd + b[1] * zddd, fmt);
+                a1[d] = b[1] * zd;
+                a2[d] = b[2] * zd * zd + b[1] * zdd;
+                a3[d] = b[3] * zd * zd * zd + 3.0 * b[2] * zd * zdd + b[1] * zddd;
             }
-            double am = D == 2 ? round_to(b[2] * dz[j * D] * dz[j * D + 1] + b[1] * mz[j], fmt) : 0.0;
+            double am = D == 2 ? b[2] * dz[j * D] * dz[j * D + 1] + b[1] * mz[j] : 0.0;
             double a4[8], a5[8];
             if (hi) {
                 double f[7];
@@ -286,23 +324,23 @@ static void layer_forward(const orc_net* net, int l, const double* Wl, int D,
                 for (int d = 0; d < D; ++d) {
                     double g[6] = {0.0, dz[j * D + d], d2z[j * D + d], d3z[j * D + d], d4z[j * D + d],
                                    d5z[j * D + d]};
-                    a4[d] = round_to(row4(f, g), fmt);
-                    a5[d] = round_to(row5(f, g), fmt);
+                    a4[d] = row4(f, g);
+                    a5[d] = row5(f, g);
                 }
             }
             for (int o = 0; o < O; ++o) {
-                double w = round_w(Wl[((long)o * I + j) * n + i], fmt);
-                y[o] += w * a0;
-                my[o] += w * am;
+                double w = Wl[((long)o * I + j) * n + i];
+                y[o] += wmul(w, a0, fmt);
+                my[o] += wmul(w, am, fmt);
                 for (int d = 0; d < D; ++d) {
-                    dy[o * D + d] += w * a1[d];
-                    d2y[o * D + d] += w * a2[d];
-                    d3y[o * D + d] += w * a3[d];
+                    dy[o * D + d] += wmul(w, a1[d], fmt);
+                    d2y[o * D + d] += wmul(w, a2[d], fmt);
+                    d3y[o * D + d] += wmul(w, a3[d], fmt);
                 }
                 if (hi)
                     for (int d = 0; d < D; ++d) {
-                        d4y[o * D + d] += w * a4[d];
-                        d5y[o * D + d] += w * a5[d];
+                        d4y[o * D + d] += wmul(w, a4[d], fmt);
+                        d5y[o * D + d] += wmul(w, a5[d], fmt);
                     }
             }
         }
@@ -505,7 +543,7 @@ int orc_layer_forward(int I, int O, int G, int k, int m, double lo, double hi, c
  * with the basis-matrix entries A_r of layer_forward (value, first, second and
  * third derivative rows of input unit j and basis i).  fmt rounds the A entries and
  * gy to BF16/TF32 before the FP64 products and sums (the reduced-precision
- * contraction's inputs); ORC_EXACT rounds nothing.  zin [J][I][N], gy [J][O][N],
+ * contraction's inputs; ORC_BF16X3 splits both, prod3); ORC_EXACT rounds nothing.  zin [J][I][N], gy [J][O][N],
  * dW [O][I][n] overwritten.
  */
 int orc_layer_dw(int I, int O, int G, int k, int m, double lo, double hi, const double* zin,
@@ -555,11 +593,11 @@ int orc_layer_dw(int I, int O, int G, int k, int m, double lo, double hi, const 
                     } else {
                         v = b[2] * dz[0] * dz[1] + b[1] * mz;
                     }
-                    a[r] = round_to(v, fmt);
+                    a[r] = v;
                 }
                 for (int o = 0; o < O; ++o) {
                     double acc = 0.0;
-                    for (int r = 0; r < J; ++r) acc += round_to(gy[((long)r * O + o) * N + p], fmt) * a[r];
+                    for (int r = 0; r < J; ++r) acc += gmul(gy[((long)r * O + o) * N + p], a[r], fmt);
                     dW[((long)o * I + j) * n + i] += acc;
                 }
             }
@@ -589,7 +627,7 @@ int orc_layer_dw(int I, int O, int G, int k, int m, double lo, double hi, const 
  *   fourth / fifth rows (A = R4 / R5): d/dz += dA R with v^(r) -> v^(r+1) (through
  *                     the sixth derivative), d/dz_d^(q) += dA dR/dg_q
  * fmt rounds gy and W before the FP64 sum over o (the reduced-precision
- * contraction's inputs); ORC_EXACT rounds nothing.  zin [J][I][N],
+ * contraction's inputs; ORC_BF16X3 splits both, prod3); ORC_EXACT rounds nothing.  zin [J][I][N],
  * gy [J][O][N], gz [J][I][N] written.
  */
 int orc_layer_adjoint(int I, int O, int G, int k, int m, double lo, double hi, const double* Wl,
@@ -623,8 +661,7 @@ int orc_layer_adjoint(int I, int O, int G, int k, int m, double lo, double hi, c
                 for (int r = 0; r < J; ++r) {
                     double dA = 0.0;
                     for (int o = 0; o < O; ++o)
-                        dA += round_to(gy[((long)r * O + o) * N + p], fmt) *
-                              round_w(Wl[((long)o * I + j) * n + i], fmt);
+                        dA += wmul(Wl[((long)o * I + j) * n + i], gy[((long)r * O + o) * N + p], fmt);
                     int bit = rows[r], dd, ord = bit_order(bit, D, &dd);
                     if (ord == 4 || ord == 5) {
                         /* d/dz through v^(r+1); d/dz_d^(q) from the partials of R4 / R5 */

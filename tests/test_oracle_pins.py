@@ -711,3 +711,54 @@ def test_bf16_weight_split_mode():
     A_bf = np.vectorize(lambda v: oracle.round_to(v, oracle.BF16))(A)
     np.testing.assert_allclose(lf(w16, oracle.BF16W2)[0, 0], w16 @ A_bf, rtol=1e-14, atol=1e-15)
     assert not np.allclose(lf(w16, oracle.BF16)[0, 0], w16 @ A_bf, rtol=1e-6, atol=0)   # plain BF16 rounds W too
+
+
+def test_bf16_three_term_split_mode():
+    """ORC_BF16X3 (each factor as bf16 hi + bf16 lo, products hi*hi + hi*lo + lo*hi; a precision
+    variant of the contraction, not from the paper).  Read out with one-hot weights (the layer is
+    linear in W, so a one-hot weight of 1 returns the exact basis-matrix entries A):
+    (a) entries and weights exact in BF16: the mode equals the exact layer bit for bit;
+    (b) BF16-exact entries (one-hot readouts use the value row of knot inputs, 81/256, 1, 0) with
+        16-bit weights, and (c) 16-bit entries with BF16-exact weights: the split carries both
+        factors exactly and only the lo*lo term is dropped, which is zero here, so the output is
+        exact, while one BF16 rounding of each factor is not;
+    (d) general inputs: every product is within 2^-15 of its exact value relative to |a w|
+        (hi + lo carries a float32 value to 2^-17; the dropped lo*lo term is below 2^-16), so
+        |out - exact| <= 2^-15 sum |a| |w| per output, far inside the 2^-8 of a dropped cross term."""
+    I, O, G, N = 2, 1, 4, 7
+    n = G + 3
+    rng = np.random.default_rng(91)
+    h = 2.0 / G
+    lf = lambda W, z, fmt, mask=0x01: oracle.layer_forward(I, O, G, 3, 4, -1.0, 1.0, W, z, mask, fmt)
+    onehot = lambda z, mask: np.stack([lf(np.eye(O * I * n)[c], z, oracle.EXACT, mask)[:, 0]
+                                       for c in range(O * I * n)])    # [I*n][J][N]
+    # (a) knot inputs (value row entries 81/256, 1, 81/256, 0) and BF16 weights
+    zk = (-1.0 + rng.integers(-3, G + 3, (1, I, N)) * h)
+    w_bf = np.array([oracle.round_to(v, oracle.BF16) for v in rng.normal(0, 0.5, O * I * n)])
+    np.testing.assert_array_equal(lf(w_bf, zk, oracle.BF16X3), lf(w_bf, zk, oracle.EXACT))
+    # (b) the same entries with 16-bit weights
+    w16 = rng.integers(-(1 << 15), 1 << 15, O * I * n) / float(1 << 17)
+    np.testing.assert_array_equal(lf(w16, zk, oracle.BF16X3), lf(w16, zk, oracle.EXACT))
+    assert not np.allclose(lf(w16, zk, oracle.BF16), lf(w16, zk, oracle.EXACT), rtol=1e-6, atol=0)
+    # (c) first-derivative entries v'(z) z_d with 16 significant bits: knot inputs (v' = +-27/(8a)
+    #     with a = 2h = 1, five bits) times z_d = k / 2^11 (11 bits), BF16-exact weights
+    J = 3
+    zc = np.zeros((J, I, N))
+    zc[0] = zk[0]
+    zc[1:] = rng.integers(-(1 << 11), 1 << 11, (2, I, N)) / float(1 << 11)
+    A = onehot(zc, 0x07)
+    assert any(oracle.round_to(a, oracle.BF16) != a for a in A[:, 1].ravel())   # entries need the lo part
+    np.testing.assert_array_equal(lf(w_bf, zc, oracle.BF16X3, 0x07), lf(w_bf, zc, oracle.EXACT, 0x07))
+    assert not np.allclose(lf(w_bf, zc, oracle.BF16, 0x07)[1:], lf(w_bf, zc, oracle.EXACT, 0x07)[1:],
+                           rtol=1e-6, atol=0)
+    # (d) general inputs and weights: the error bound
+    zg = np.zeros((J, I, N))
+    zg[0] = rng.uniform(-1.2, 1.2, (I, N))
+    zg[1:] = rng.normal(0, 1.0, (2, I, N))
+    wg = rng.normal(0, 0.5, O * I * n)
+    A = onehot(zg, 0x07)                                       # [I*n][J][N]
+    bound = 2.0 ** -15 * np.einsum("c,cjn->jn", np.abs(wg), np.abs(A))
+    err = np.abs(lf(wg, zg, oracle.BF16X3, 0x07)[:, 0] - lf(wg, zg, oracle.EXACT, 0x07)[:, 0])
+    assert np.all(err <= bound), (err / np.maximum(bound, 1e-300)).max()
+    err1 = np.abs(lf(wg, zg, oracle.BF16, 0x07)[:, 0] - lf(wg, zg, oracle.EXACT, 0x07)[:, 0])
+    assert np.any(err1 > 10 * bound)        # one BF16 rounding per factor is far outside it
