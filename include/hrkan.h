@@ -86,10 +86,15 @@ typedef struct hrkan_cfg {
     int k;                           /* support width in cells minus one (B-spline order); 3 */
     int m;                           /* HR order of Eq. 2: 2..6 (FP32); the fused narrow and tensor-core kernels need 4 */
     int prec;                        /* enum hrkan_prec: arithmetic of the jet contraction.  BF16 /
-                                        TF32: hidden layers with 16 <= O <= 64 (O % 16 == 0) contract
-                                        on tcgen05 tensor cores (FP32 accumulation in TMEM) when
-                                        G + k >= 13 (BF16) or >= 7 (TF32); the first and last layers,
-                                        other hidden layers and the backward stay FP32
+                                        TF32: hidden layers with 16 <= O <= 64 (O % 16 == 0) and
+                                        G + k <= 64 contract on tcgen05 tensor cores (FP32
+                                        accumulation in TMEM).  BF16 forward: every input of a
+                                        product carried as two bfloat16 values (x = x_hi + x_lo) and
+                                        the product as a_hi w_hi + a_lo w_hi + a_hi w_lo; BF16 weight
+                                        gradient and input adjoint: inputs rounded to bfloat16 once;
+                                        TF32: the forward's inputs rounded to TF32 once.  The first
+                                        and last layers (but for the BF16 weight gradient of the first
+                                        layer) and the other hidden layers stay FP32
                                         (hrkan_profile_read(HRKAN_KERNEL_TENSOR) counts the tensor
                                         launches).  Needs the layer-wise path (a shape without a
                                         fused kernel, or HRKAN_FLAG_LAYERWISE) */
@@ -363,8 +368,10 @@ int hrkan_autotune_batch(hrkan_t h, const pinn_problem* probs, float* W, const f
  *   - Networks with more than 1 Mi weights are rejected with HRKAN_EINVAL;
  *     only the fused narrow shapes are supported (else HRKAN_EUNSUPPORTED).
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current, and looks it up again
+ *     whenever the current context differs from the one of the cached address
+ *     (after cudaDeviceReset the module, and with it the array, is loaded
+ *     anew); make the first call in each context before any stream capture.
  *   - Every call shares the one array and leaves its partials there; each
  *     call overwrites the rows it reads, so nothing needs clearing, but calls
  *     whose work overlaps on the GPU (other streams, other threads) race.

@@ -9,6 +9,8 @@
 // shape directly and keeps its per-block gradient partials in a file-scope
 // static device array instead of a handle's workspace.  It allocates nothing:
 // no cudaMalloc, no cudaFree, no allocating library routine.
+#include <cuda.h>
+
 #include <cstdio>
 #include <mutex>
 
@@ -27,28 +29,71 @@ static __device__ __align__(256) float g_scratch[kScratchFloats];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-float* g_scratch_ptr[kMaxDevices] = {};
+// Per device: the scratch address and the id of the context it was looked up
+// in.  A module-scope __device__ array lives in the context's copy of the
+// module: after cudaDeviceReset, or when the primary context is released and
+// created again, the module is loaded anew and the array may sit elsewhere,
+// so the address is looked up again whenever the current context's id differs.
+struct ScratchAddr {
+    float* ptr;
+    unsigned long long ctx_id;
+};
+ScratchAddr g_scratch_addr[kMaxDevices] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Id of the current driver context (0: none, or the driver lacks cuCtxGetId).
+unsigned long long current_ctx_id() {
+    static std::once_flag once;
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        else
+            cudaGetLastError();
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+        else
+            cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 // Device address of g_scratch on the current device.  The name g_scratch in
-// host code is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// host code is only a host-side stand-in, so the address is looked up (with
+// that device current) on the first call in each context and cached with the
+// context's id.
 int scratch_on_current_device(float** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_last_error(HRKAN_ECUDA, "hrkan_backward_noalloc: cudaGetDevice failed");
     if (dev < 0 || dev >= kMaxDevices) return set_last_error(HRKAN_EUNSUPPORTED, "hrkan_backward_noalloc: device ordinal >= 64");
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    ScratchAddr& a = g_scratch_addr[dev];
+    const unsigned long long id = current_ctx_id();
+    if (!a.ptr || id == 0 || id != a.ctx_id) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
+        e = cudaGetSymbolAddress(&p, g_scratch);   // makes the device's primary context current if needed
         if (e != cudaSuccess || !p) {
             char buf[256];
             snprintf(buf, sizeof buf, "hrkan_backward_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
             return set_last_error(HRKAN_ECUDA, buf);
         }
-        g_scratch_ptr[dev] = static_cast<float*>(p);
+        a.ptr = static_cast<float*>(p);
+        a.ctx_id = current_ctx_id();
     }
-    *out = g_scratch_ptr[dev];
+    *out = a.ptr;
     return HRKAN_OK;
 }
 

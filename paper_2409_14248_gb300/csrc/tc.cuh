@@ -9,6 +9,13 @@
 
 namespace hrkan {
 
+// Template precision of the forward kernel for HRKAN_BF16 layers: each
+// contraction input x is carried as two bfloat16 values, x = x_hi + x_lo
+// (x_hi = bf16(x), x_lo = bf16(x - x_hi)), and every product as
+// a_hi w_hi + a_lo w_hi + a_hi w_lo (the a_lo w_lo term dropped), with FP32
+// accumulation.  The values of this enum continue hrkan_prec's.
+constexpr int TC_BF16X3 = 3;
+
 struct TcLayer {
     const float* z;   // input jets [J][I][N]
     float* y;         // output jets [J][O][N]

@@ -14,9 +14,9 @@ namespace tck {
 
 template <unsigned MASK, int PREC, int NP>
 cudaError_t launch_one(const TcLayer& p, const CUtensorMap& map, cudaStream_t s) {
-    // NB W tiles + alignment slack; at least 120 KB so that one CTA holds an SM
-    // (each CTA allocates all 512 TMEM columns)
-    const size_t want = std::max<size_t>(size_t(NB) * p.O * 128 + 1024, 120 * 1024);
+    // NB W buffers (TERMS tiles of O rows each) + alignment slack; at least
+    // 120 KB so that one CTA holds an SM (each CTA allocates all 512 TMEM columns)
+    const size_t want = std::max<size_t>(size_t(NB) * Elem<PREC>::TERMS * p.O * 128 + 1024, 120 * 1024);
     auto kern = tc_fwd_kernel<MASK, PREC, NP>;
     static std::mutex mu;
     static std::unordered_map<const void*, size_t> set;
@@ -44,11 +44,11 @@ cudaError_t launch_one(const TcLayer& p, const CUtensorMap& map, cudaStream_t s)
 cudaError_t HRKAN_TC_CAT(tc_launch_np, HRKAN_TC_NP)(const TcLayer& p, const CUtensorMap& map, int prec,
                                                      unsigned mask, cudaStream_t s) {
     constexpr int NP = HRKAN_TC_NP;
-    if (prec == HRKAN_BF16) {
+    if (prec == HRKAN_BF16) {   // the three-term split (TC_BF16X3)
         switch (mask) {
-            case 0x01u: return tck::launch_one<0x01u, HRKAN_BF16, NP>(p, map, s);
-            case 0x0Fu: return tck::launch_one<0x0Fu, HRKAN_BF16, NP>(p, map, s);
-            case 0x1Fu: return tck::launch_one<0x1Fu, HRKAN_BF16, NP>(p, map, s);
+            case 0x01u: return tck::launch_one<0x01u, TC_BF16X3, NP>(p, map, s);
+            case 0x0Fu: return tck::launch_one<0x0Fu, TC_BF16X3, NP>(p, map, s);
+            case 0x1Fu: return tck::launch_one<0x1Fu, TC_BF16X3, NP>(p, map, s);
         }
     } else if (prec == HRKAN_TF32) {
         switch (mask) {

@@ -30,28 +30,38 @@ int np_of(int n) {
         if (n <= np) return np;
     return 0;
 }
-int slot_elems(int prec) { return prec == HRKAN_BF16 ? 16 : 8; }
-int box_elems(int prec) { return prec == HRKAN_BF16 ? 64 : 32; }
+// Basis positions per slot (one MMA) and per 128-byte W row: 8 and 32 for
+// TF32 and for the BF16 pair layout (one 32-bit word per basis).
+int slot_elems(int) { return 8; }
+int box_elems(int) { return 32; }
+// Weight tiles of O rows per W buffer: (w_hi, w_hi) and (w_lo, 0) for BF16.
+int w_terms(int prec) { return prec == HRKAN_BF16 ? 2 : 1; }
 // A ring slots left in TMEM after the J * O accumulator columns (8 columns per slot and jet row).
 int ring_slots(int J, int O) { return std::min(RING_MAX, (TMEM_COLS - J * O) / (8 * J)); }
 
-// W [O][I][n] float32 -> [O][Kt] in the MMA's element type (BF16 bits, or
-// TF32-rounded float32): element k = j * NP + pos holds W[o][j][i], i = 4 *
-// (pos mod NP/4) + pos / (NP/4) (the bases of a unit stored by residue mod 4),
-// for i < n and j < I, zero elsewhere.
+// W [O][I][n] float32 -> 32-bit words [TERMS][O][Kt]: word k = j * NP + pos
+// holds W[o][j][i], i = 4 * (pos mod NP/4) + pos / (NP/4) (the bases of a unit
+// stored by residue mod 4), for i < n and j < I, zero elsewhere.  TF32: the
+// TF32-rounded float32.  BF16 (three-term split): tile 0 holds (w_hi, w_hi) in
+// the word's low and high halves, tile 1 (w_lo, 0), w_hi = bf16(w),
+// w_lo = bf16(w - w_hi).
 template <int PREC>
-__global__ void tc_prep_w_kernel(const float* __restrict__ W, void* out, int O, int I, int n, int NP, int Kt) {
+__global__ void tc_prep_w_kernel(const float* __restrict__ W, uint32_t* out, int O, int I, int n, int NP, int Kt) {
     const int64_t total = int64_t(O) * Kt;
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
         const int o = int(t / Kt), k = int(t % Kt);
         const int j = k / NP, pos = k % NP, q = NP / 4, i = 4 * (pos % q) + pos / q;
         const float w = (j < I && i < n) ? W[(int64_t(o) * I + j) * n + i] : 0.0f;
         if constexpr (PREC == HRKAN_BF16) {
-            static_cast<uint16_t*>(out)[t] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
+            const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+            const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(w - __bfloat162float(hi)));
+            const uint32_t hb = __bfloat16_as_ushort(hi);
+            out[t] = hb | (hb << 16);
+            out[total + t] = lo;
         } else {
             uint32_t r;
             asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(w));
-            static_cast<uint32_t*>(out)[t] = r;
+            out[t] = r;
         }
     }
 }
@@ -101,7 +111,7 @@ bool tc_layer_supported(int prec, int I, int O, int n, unsigned mask) {
     return I >= 1 && (mask == 0x01u || mask == 0x0Fu || mask == 0x1Fu);
 }
 
-int64_t tc_w_elems(int O, int I, int n, int prec) { return int64_t(O) * k_layout(I, n, prec).kt; }
+int64_t tc_w_elems(int O, int I, int n, int prec) { return int64_t(w_terms(prec)) * O * k_layout(I, n, prec).kt; }
 
 cudaError_t tc_forward_layer(const float* W, void* w_prep, const float* z, float* y, int I, int O, int64_t N,
                              const Grid& g, int prec, unsigned mask, int* status, cudaStream_t s) {
@@ -110,22 +120,26 @@ cudaError_t tc_forward_layer(const float* W, void* w_prep, const float* z, float
     const KLayout L = k_layout(I, n, prec);
     const int64_t total = int64_t(O) * L.kt;
     const int pb = int(std::min<int64_t>((total + 255) / 256, 4096));
+    uint32_t* wp = static_cast<uint32_t*>(w_prep);
     if (prec == HRKAN_BF16)
-        tc_prep_w_kernel<HRKAN_BF16><<<pb, 256, 0, s>>>(W, w_prep, O, I, n, L.np, L.kt);
+        tc_prep_w_kernel<HRKAN_BF16><<<pb, 256, 0, s>>>(W, wp, O, I, n, L.np, L.kt);
     else
-        tc_prep_w_kernel<HRKAN_TF32><<<pb, 256, 0, s>>>(W, w_prep, O, I, n, L.np, L.kt);
+        tc_prep_w_kernel<HRKAN_TF32><<<pb, 256, 0, s>>>(W, wp, O, I, n, L.np, L.kt);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
+    // rows of 32-bit words: the TERMS tiles of O rows each stacked, one box
+    // (32 words x TERMS*O rows) per W buffer of the kernel
+    const int rows = w_terms(prec) * O;
     CUtensorMap map;
-    const cuuint64_t dims[2] = {cuuint64_t(L.kt), cuuint64_t(O)};
-    const cuuint64_t strides[1] = {cuuint64_t(L.kt) * (prec == HRKAN_BF16 ? 2 : 4)};
-    const cuuint32_t box[2] = {cuuint32_t(box_elems(prec)), cuuint32_t(O)};
+    const cuuint64_t dims[2] = {cuuint64_t(L.kt), cuuint64_t(rows)};
+    const cuuint64_t strides[1] = {cuuint64_t(L.kt) * 4};
+    const cuuint32_t box[2] = {cuuint32_t(box_elems(prec)), cuuint32_t(rows)};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(&map, prec == HRKAN_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                     w_prep, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, w_prep, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     const int J = __builtin_popcount(mask & 0x1Fu);
     TcLayer p{};

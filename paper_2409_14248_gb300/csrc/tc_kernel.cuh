@@ -170,7 +170,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         : "memory");
 }
 
-// Element type of the contraction.
+// Element type of the contraction.  An "element" is one basis position of
+// the K layout; TERMS is the number of MMAs per slot and jet row (and of
+// O-row weight tiles per W buffer).
 template <int PREC>
 struct Elem;
 template <>
@@ -179,10 +181,20 @@ struct Elem<HRKAN_BF16> {
     static constexpr int SLOT = 16;      // K elements per MMA (one slot)
     static constexpr int BOX = 64;       // K elements per 128-byte W row tile
     static constexpr int FMT = 1;
+    static constexpr int TERMS = 1;
 };
 template <>
 struct Elem<HRKAN_TF32> {
-    static constexpr int PER_WORD = 1, SLOT = 8, BOX = 32, FMT = 2;
+    static constexpr int PER_WORD = 1, SLOT = 8, BOX = 32, FMT = 2, TERMS = 1;
+};
+// Three-term BF16 split in a pair layout: the 32-bit word of a basis holds
+// (a_hi, a_lo) in its low and high halves, the two weight tiles hold
+// (w_hi, w_hi) and (w_lo, 0) per basis, so the two BF16 MMAs of a slot add
+// a_hi w_hi + a_lo w_hi and a_hi w_lo.  One basis per word, 8 per slot (the
+// MMA's K of 16 BF16 elements), 32 per 128-byte W row.
+template <>
+struct Elem<TC_BF16X3> {
+    static constexpr int PER_WORD = 1, SLOT = 8, BOX = 32, FMT = 1, TERMS = 2;
 };
 
 __device__ __forceinline__ uint32_t tf32_bits(float x) {
@@ -255,7 +267,7 @@ __device__ __forceinline__ void unit_window(const float* z, const Grid& g, bool 
         d1[k] = ok ? -8.0f * u * Q3 * g.inv_a : 0.0f;
         d2[k] = ok ? (-8.0f * Q3 + 48.0f * u * u * Q2) * (g.inv_a * g.inv_a) : 0.0f;
         const int tk = base + (k < s ? 1 : 0);
-        if constexpr (PREC == HRKAN_BF16) w.tw[k] = live ? (tk >> 1) : -(1 << 24);
+        if constexpr (Elem<PREC>::PER_WORD == 2) w.tw[k] = live ? (tk >> 1) : -(1 << 24);
         else w.tw[k] = live ? tk : -(1 << 24);
     }
     float a[J][4];
@@ -265,10 +277,16 @@ __device__ __forceinline__ void unit_window(const float* z, const Grid& g, bool 
         const int tk = base + (k < s ? 1 : 0);
 #pragma unroll
         for (int r = 0; r < J; ++r) {
-            if constexpr (PREC == HRKAN_BF16)
+            if constexpr (PREC == HRKAN_BF16) {
                 w.y[r][k] = uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(a[r][k]))) << ((tk & 1) * 16);
-            else
+            } else if constexpr (PREC == TC_BF16X3) {
+                // hi = bf16(a); a - hi is exact in float32, lo = bf16(a - hi)
+                const __nv_bfloat16 hi = __float2bfloat16_rn(a[r][k]);
+                const __nv_bfloat16 lo = __float2bfloat16_rn(a[r][k] - __bfloat162float(hi));
+                w.y[r][k] = uint32_t(__bfloat16_as_ushort(hi)) | (uint32_t(__bfloat16_as_ushort(lo)) << 16);
+            } else {
                 w.y[r][k] = tf32_bits(a[r][k]);
+            }
         }
     }
     // bases outside [0, n) are zero already; a unit past the layer's inputs places nothing
@@ -485,7 +503,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_fwd_kernel(TcLayer p, const __g
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int O = p.O, RS = p.ring, KS = p.ks;
-    const uint32_t b_bytes = uint32_t(O) * 128u;
+    const uint32_t b_bytes = uint32_t(E::TERMS * O) * 128u;   // one W buffer: TERMS tiles of O rows
     const uint32_t A0 = uint32_t(J * O);            // first A column; accumulators at r * O
     const uint32_t RW = uint32_t(RS * 8);           // ring words per jet row
     volatile int* abort = &sh.abort;
@@ -531,19 +549,24 @@ __global__ void __launch_bounds__(THREADS, 1) tc_fwd_kernel(TcLayer p, const __g
             for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
                 if (!mbar_wait(&sh.accempty, uint32_t(it & 1) ^ 1u, abort, wl)) break;
                 tc_fence_after();
-                uint64_t bd = 0;
+                uint64_t bd = 0, bd2 = 0;
                 for (int t = 0; t < KS; ++t) {
                     if ((t & 3) == 0) {
                         if (!mbar_wait(&sh.wfull[wb], wph, abort, wl)) goto mma_out;
                         bd = sdesc_sw128(smem_u32(smem + size_t(wb) * b_bytes));
+                        // second tile of the buffer (w_lo): O rows of 128 bytes further
+                        bd2 = sdesc_sw128(smem_u32(smem + size_t(wb) * b_bytes + size_t(O) * 128));
                     }
                     if (!mbar_wait(&sh.full[slot], ph, abort, wl)) goto mma_out;
                     tc_fence_after();
 #pragma unroll
-                    for (int r = 0; r < J; ++r)
-                        mma_ts<PREC>(tbase + uint32_t(r * O), tbase + A0 + uint32_t(r) * RW + uint32_t(slot * 8),
-                                     bd + uint64_t((t & 3) * 2),   // +32 bytes per slot (descriptor counts 16 B)
+                    for (int r = 0; r < J; ++r) {
+                        const uint32_t d = tbase + uint32_t(r * O);
+                        const uint32_t a = tbase + A0 + uint32_t(r) * RW + uint32_t(slot * 8);
+                        mma_ts<PREC>(d, a, bd + uint64_t((t & 3) * 2),   // +32 bytes per slot (descriptor counts 16 B)
                                      idesc, t > 0 ? 1u : 0u);
+                        if constexpr (E::TERMS == 2) mma_ts<PREC>(d, a, bd2 + uint64_t((t & 3) * 2), idesc, 1u);
+                    }
                     issued = true;
                     mma_commit(&sh.empty[slot]);
                     if (++slot == RS) { slot = 0; ph ^= 1u; }

@@ -14,6 +14,23 @@ def relerr(got, want):
     return d / n if n > 0 else d
 
 
+def maxrel(got, want):
+    """Per-point error max_p |got_p - want_p| / max_p |want_p| (absolute if want is 0)."""
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    d = np.abs(got - want).max() if got.size else 0.0
+    n = np.abs(want).max() if want.size else 0.0
+    return d / n if n > 0 else d
+
+
+def assert_close(got, want, bar, pt_bar=None, what=""):
+    """Normwise relerr below bar and per-point maxrel below pt_bar (default: bar)."""
+    e, m = relerr(got, want), maxrel(got, want)
+    pt = bar if pt_bar is None else pt_bar
+    assert e < bar and m < pt, f"{what}: normwise {e:.3e} (bar {bar:.1e}), per point {m:.3e} (bar {pt:.1e})"
+    return e, m
+
+
 # FP32 path tolerances: 1e-5 on u, 1e-4 on derivative rows, the loss gradient
 # and the weight gradient (normwise, per jet row / per layer), at the
 # workloads' own N(0, 0.1^2) weights.

@@ -1,31 +1,40 @@
-"""Tensor-core (tcgen05) forward of the hidden layers in BF16 / TF32.
+"""Tensor-core (tcgen05) contractions of the hidden layers in BF16 / TF32.
+
+Forward.  BF16 layers run the three-term split: every contraction input x is
+carried as x_hi + x_lo (two bfloat16 values) and each product as
+a_hi w_hi + a_lo w_hi + a_hi w_lo with FP32 accumulation (oracle mode
+BF16X3); TF32 layers round each input once (oracle mode TF32).  The weight
+gradient and the input adjoint round their inputs to BF16 once (oracle mode
+BF16).
 
 Two questions, kept apart:
 
-1. Does the kernel compute the BF16 / TF32 contraction correctly?  It is
-   compared with the oracle's forward in which the basis-matrix entries and
-   weights of the same layers are rounded to BF16 (nearest even) or TF32
-   (nearest, ties away) and everything else is exact: the kernel must sit far
-   closer to that than the rounding moves the result (a wrong operand layout
-   or K order gives an O(1) difference).
-2. How accurate is the precision itself?  The error against the exact FP64
-   oracle per jet order (value, first, second derivatives).  The 2e-2 bar for
-   BF16 jets holds on the [2,32,32,1] network; the [2,64,64,64,1] G=32
-   network at its initial weights amplifies input rounding ~600x (measured in
-   FP32), so there BF16 gives ~0.4 and TF32 ~5e-2: reported, not asserted.
+1. Does the kernel compute its contraction correctly?  It is compared with the
+   oracle's layer or network in which the same inputs are rounded the same way
+   and everything else is exact: the kernel must sit far closer to that than
+   the rounding moves the result (a wrong operand layout, K order or a missing
+   split term gives a difference of the size of the rounding or O(1)).  Inputs
+   that the rounding leaves exact must give the exact oracle's result.
+2. How accurate is the path?  The network's jets against the exact FP64 oracle,
+   per jet order: the BF16 path meets the 2e-2 bar on every row, normwise and per
+   point, on [2,32,32,1] G=20 and on [2,64,64,64,1] G=32 at the workloads'
+   weights.  TF32 (single rounding) meets it on [2,32,32,1]; the [2,64,64,64,1]
+   G=32 network amplifies input rounding ~600x, so TF32 lands at ~0.1 there
+   (bounded, not held to the bar).
 """
 import numpy as np
 import pytest
 
 import oracle
-from gpu_util import conditioned_tolerances, relerr
+from gpu_util import assert_close, conditioned_tolerances, maxrel, relerr
 from paper_2409_14248_gb300 import build, capi, inputs
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-BAR = {capi.HRKAN_BF16: 2e-2, capi.HRKAN_TF32: 2e-2}
+BAR = 2e-2          # jets of the reduced-precision path vs the FP64 oracle (normwise and per point)
+TF32_ILL_BOUND = 0.25   # TF32 on the ~600x-amplifying [2,64,64,64,1] G=32 network (measured ~0.12)
 # The kernel rounds basis-matrix entries computed in float32, the oracle the same entries
 # computed in float64.  An entry whose two versions straddle a rounding boundary rounds to
 # neighbouring values: with float32 entry errors of a few 2^-24 and a format ulp of 2^-7
@@ -33,7 +42,7 @@ BAR = {capi.HRKAN_BF16: 2e-2, capi.HRKAN_TF32: 2e-2}
 # rms rounding error of ulp/sqrt(12) on every entry: the flips alone make the kernel differ from
 # the rounded oracle by up to ~0.1x the rounding's own effect (measured 0.097 on a TF32 layer).
 FLIP = 0.25
-FMT = {capi.HRKAN_BF16: oracle.BF16, capi.HRKAN_TF32: oracle.TF32}
+FMT = {capi.HRKAN_BF16: oracle.BF16X3, capi.HRKAN_TF32: oracle.TF32}   # the forward's rounding
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -59,10 +68,10 @@ def _forward(w, prec, W, x, mask, flags=0):
 
 
 def _check(w, prec, d, mask, check_impl=True):
-    """Returns the per-jet-order error vs exact FP64, after checking the kernel
-    against the rounding-aware oracle (skipped where two or more rounded layers
-    make that comparison chaotic: the rounded oracle itself then moves by ~1e-2
-    under 1e-7 weight noise)."""
+    """Returns the per-jet-order (normwise, per-point) error vs exact FP64, after checking
+    the kernel against the rounding-aware oracle of the same layers (skipped where two or
+    more singly rounded layers make that comparison chaotic: the rounded oracle itself then
+    moves by ~1e-2 under 1e-7 weight noise)."""
     x = d["x_int"]
     got = _forward(w, prec, d["W"], x, mask)
     assert np.all(np.isfinite(got))
@@ -76,8 +85,8 @@ def _check(w, prec, d, mask, check_impl=True):
         e_impl = relerr(got[r], rounded[r])
         if check_impl:
             assert e_impl < 0.05 * e_fmt + floor[r], (r, e_impl, e_fmt)
-        errs.append(relerr(got[r], exact[r]))
-    print(f"\nper-jet-order relative error, prec {prec}, mask {mask:#x}: {np.array(errs)}")
+        errs.append((relerr(got[r], exact[r]), maxrel(got[r], exact[r])))
+    print(f"\nper-jet-order (normwise, per-point) error, prec {prec}, mask {mask:#x}: {errs}")
     return errs
 
 
@@ -116,10 +125,63 @@ def test_tc_single_layer_matches_rounding_aware_oracle(prec, shape, mask):
     got = _layer(prec, I, O, G, z, Wl, mask, N)
     exact = oracle.layer_forward(I, O, G, 3, 4, -1.0, 1.0, Wl, z, mask)
     rounded = oracle.layer_forward(I, O, G, 3, 4, -1.0, 1.0, Wl, z, mask, FMT[prec])
+    single = oracle.layer_forward(I, O, G, 3, 4, -1.0, 1.0, Wl, z, mask, oracle.BF16)
     for r in range(J):
         e_impl, e_fmt = relerr(got[r], rounded[r]), relerr(rounded[r], exact[r])
         assert e_impl < 2e-5 + FLIP * e_fmt, (r, e_impl, e_fmt)
-        assert e_fmt > 4 * e_impl      # the contraction really ran in the reduced precision
+        assert maxrel(got[r], rounded[r]) < 1e-4 + 4 * FLIP * maxrel(rounded[r], exact[r]), r
+        if prec == capi.HRKAN_TF32:
+            assert e_fmt > 4 * e_impl      # the contraction really ran in the reduced precision
+        else:
+            # the split terms ran: far below the error of one BF16 rounding of each input
+            assert relerr(got[r], exact[r]) < 0.05 * relerr(single[r], exact[r]), r
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 32, -1.0, 1.0), (13, 32, 24, -1.5, 1.5), (16, 16, 8, -1.0, 1.0)])
+@pytest.mark.parametrize("term", ["w_lo", "a_lo"])
+def test_tc_bf16_split_terms_exact(shape, term):
+    """Each split term on its own, on inputs the split carries exactly.  Unit values on knots
+    lo + c*h (h a power of two) give basis values 81/256, 1, 81/256, 0 and derivatives with five
+    significant bits.  'w_lo': jet factors +-1/2 (entries of at most 8 bits: a_lo = 0) and
+    weights with 16 significant bits (w = w_hi + w_lo exactly), so the result is exact only if
+    the a_hi w_lo MMA ran.  'a_lo': jet factors k/8 (|k| <= 8) and second jets in
+    {0, +-2, +-4}, so every entry has at most 13 significant bits (a = a_hi + a_lo exactly), and
+    weights of 7 bits (w_lo = 0), so the result is exact only if the a_lo w_hi MMA ran.  Either
+    way the kernel equals the exact oracle up to float32 accumulation (the products carry up to
+    24 significant bits, so the accumulation rounds: ~2e-6 normwise over 256 non-zero terms),
+    while one BF16 rounding of each input misses it by ~1e-3."""
+    I, O, G, lo, hi = shape
+    n = G + 3
+    N = 389
+    h = (hi - lo) / G
+    rng = np.random.default_rng(I * 13 + G + (term == "a_lo"))
+    z = np.zeros((5, I, N), np.float32)
+    z[0] = lo + rng.integers(-5, G + 5, (I, N)) * h
+    if term == "w_lo":
+        z[1:3] = rng.choice([-0.5, 0.5], (2, I, N))
+        z[3:5] = rng.choice([0.0, -2.0, 2.0], (2, I, N))
+        Wl = (rng.integers(-2 ** 15, 2 ** 15, O * I * n) / 2.0 ** 15).astype(np.float32)
+    else:
+        z[1:3] = rng.integers(-8, 9, (2, I, N)) / 8.0
+        z[3:5] = rng.choice([0.0, -2.0, 2.0, -4.0, 4.0], (2, I, N))
+        Wl = (rng.integers(-127, 128, O * I * n) / 128.0).astype(np.float32)
+    cfg = capi.make_cfg([2, I, O, 1], G, lo=lo, hi=hi, prec=capi.HRKAN_BF16, flags=capi.HRKAN_FLAG_LAYERWISE)
+    hd = capi.hrkan_init(cfg)
+    try:
+        y = torch.full((5, O, N), float("nan"), device="cuda")
+        capi.hrkan_layer_jets(hd, 1, _dev(Wl), _dev(z), N, 0x1F, y)
+        capi.hrkan_sync_status(hd)
+        got = y.cpu().numpy()
+    finally:
+        capi.hrkan_destroy(hd)
+    exact = oracle.layer_forward(I, O, G, 3, 4, lo, hi, Wl, z, 0x1F)
+    assert np.array_equal(oracle.layer_forward(I, O, G, 3, 4, lo, hi, Wl, z, 0x1F, oracle.BF16X3), exact)
+    single = oracle.layer_forward(I, O, G, 3, 4, lo, hi, Wl, z, 0x1F, oracle.BF16)
+    for r in range(5):
+        assert relerr(got[r], exact[r]) < 1e-5, r
+        assert maxrel(got[r], exact[r]) < 1e-5, r
+    # the inputs do exercise the term: one BF16 rounding moves at least one row far more
+    assert max(relerr(single[r], exact[r]) for r in range(5)) > 1e-4
 
 
 # (I, O, G, lo, hi): grid spacings h = 1/4, 1/16, 1/8, 1/8, 1/8, 1/16 -> units padded to 16, 40, 32,
@@ -189,26 +251,33 @@ def test_tc_layer_persistent_tiles(prec):
 @pytest.mark.parametrize("prec", [capi.HRKAN_BF16, capi.HRKAN_TF32])
 @pytest.mark.parametrize("mask", [0x01, 0x1F])
 def test_tc_forward_poisson_64x3(prec, mask):
-    """Network level: per-jet-order error of the two tensor-core hidden layers vs exact FP64
-    (reported).  This network amplifies input rounding ~600x; only the value row is checked
-    against the rounding-aware oracle."""
+    """[2,64,64,64,1] G=32 (the precision workload's network, its N(0, 0.1^2) weights), 300
+    points: BF16 meets the 2e-2 bar on every jet row, normwise and per point, against the
+    exact FP64 oracle, and sits on the rounding-aware oracle; TF32 is bounded."""
     w = inputs.WORKLOADS["poisson_2_64x3_1"]
-    errs = _check(w, prec, inputs.make(w, n_int=300, n_bnd=40), 0x01, check_impl=True)
-    if mask != 0x01:
-        errs = _check(w, prec, inputs.make(w, n_int=300, n_bnd=40), mask, check_impl=False)
-    assert np.all(np.isfinite(errs))
+    d = inputs.make(w, n_int=300, n_bnd=40)
+    errs = _check(w, prec, d, mask, check_impl=(prec == capi.HRKAN_BF16 or mask == 0x01))
+    for r, (e, m) in enumerate(errs):
+        if prec == capi.HRKAN_BF16:
+            assert e < BAR and m < BAR, (r, e, m)
+        else:
+            assert e < TF32_ILL_BOUND, (r, e)
 
 
 @pytest.mark.parametrize("prec", [capi.HRKAN_BF16, capi.HRKAN_TF32])
 def test_tc_forward_burgers_32_meets_the_jet_bar(prec):
-    """[2,32,32,1], G=20 (n = 23: up to four units per K step), 389 points (ragged last tile)."""
+    """[2,32,32,1], G=20 (n = 23: up to four units per K step), 389 points (ragged last tile):
+    every jet row within 2e-2 of the exact oracle, normwise and per point."""
     w = inputs.WORKLOADS["burgers_2_32_32_1"]
     errs = _check(w, prec, inputs.make(w, n_int=389, n_ic=8, n_bc=8), 0x0F)
-    assert errs[0] < BAR[prec], errs        # value row; derivative rows reported
+    for r, (e, m) in enumerate(errs):
+        assert e < BAR and m < BAR, (r, e, m)
 
 
 def test_tc_full_size_forward_sampled():
-    """[2,64,64,64,1] at its full 262144 interior points in BF16; 96 sampled points vs the rounding-aware oracle."""
+    """[2,64,64,64,1] at its full 262144 interior points in BF16 (the bench's launch shape):
+    96 sampled points, the first and the last included, meet the 2e-2 bar on every jet row
+    against the exact oracle and sit on the rounding-aware one."""
     w = inputs.WORKLOADS["poisson_2_64x3_1"]
     d = inputs.make(w)
     N = d["x_int"].shape[1]
@@ -222,9 +291,11 @@ def test_tc_full_size_forward_sampled():
         xs = d["x_int"][:, idx]
         got = jets.cpu().numpy()[:, idx]
         exact = oracle.forward(w.net, d["W"], xs, 0x1F)
-        rounded = oracle.forward_rounded(w.net, d["W"], xs, 0x1F, {1, 2}, oracle.BF16)
-        floor = conditioned_tolerances(w, d["W"], xs, 0x1)
-        assert relerr(got[0], rounded[0]) < 0.05 * relerr(rounded[0], exact[0]) + floor[0]
+        rounded = oracle.forward_rounded(w.net, d["W"], xs, 0x1F, {1, 2}, oracle.BF16X3)
+        floor = conditioned_tolerances(w, d["W"], xs, 0x1F)
+        for r in range(5):
+            assert relerr(got[r], rounded[r]) < 0.05 * relerr(rounded[r], exact[r]) + floor[r], r
+            assert_close(got[r], exact[r], BAR, what=f"row {r}")
     finally:
         capi.hrkan_destroy(h)
 

@@ -9,6 +9,7 @@ is named so that pytest collects it last.
 import numpy as np
 import pytest
 
+import oracle
 from gpu_util import TOL_D, cfg_of, random_weights, relerr
 from paper_2409_14248_gb300 import build, capi, inputs
 
@@ -64,3 +65,51 @@ def test_noalloc_rejects_bad_arguments():
     with pytest.raises(capi.HRKANError) as ei:
         capi.hrkan_backward_noalloc(big, z, z, 4, 0x1, z, z)
     assert ei.value.code == capi.HRKAN_EUNSUPPORTED
+
+
+def test_noalloc_row_cap_matches_handle_backward_and_oracle():
+    """[2,16,16,1] with G = 30 has P = 10032 weights, so only 104 partial rows fit the static
+    scratch: with 38400 points (300 blocks of 128) the grid is capped below the occupancy grid
+    (one block per SM on 152 SMs), and each block walks several point blocks.  Two calls in a
+    row equal hrkan_backward, and the oracle's gradient."""
+    w = inputs.WORKLOADS["poisson_batch256"]
+    G, N, mask = 30, 128 * 300, inputs.MASK_POISSON
+    cfg = capi.make_cfg(w.widths, G, w.k, w.m, w.lo, w.hi)
+    P = capi.hrkan_param_count(cfg)
+    assert P == 10032 and (1 << 20) // P == 104
+    h = capi.hrkan_init(cfg)
+    try:
+        rng = np.random.default_rng(31)
+        Wn = (0.1 * rng.standard_normal(P)).astype(np.float32)
+        x = rng.uniform(-1, 1, (2, N)).astype(np.float32)
+        dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+        W, xd = dev(Wn), dev(x)
+        for call in range(2):
+            g = rng.standard_normal((5, N)).astype(np.float32)
+            want = torch.zeros(P, device="cuda")
+            capi.hrkan_backward(h, W, xd, N, mask, None, dev(g), want)
+            got = torch.full((P,), float("nan"), device="cuda")
+            capi.hrkan_backward_noalloc(cfg, W, xd, N, mask, dev(g), got)
+            torch.cuda.synchronize()
+            assert relerr(got.cpu().numpy(), want.cpu().numpy()) < TOL_D, call
+            if call == 0:   # the oracle on a 2048-point prefix (the same entry point, fewer points)
+                n = 2048
+                sub = torch.full((P,), float("nan"), device="cuda")
+                capi.hrkan_backward_noalloc(cfg, W, dev(x[:, :n]), n, mask, dev(g[:, :n]), sub)
+                torch.cuda.synchronize()
+                net = dict(w.net, G=G)
+                ref = oracle.backward(net, Wn.astype(np.float64), x[:, :n], mask, g[:, :n])
+                assert relerr(sub.cpu().numpy(), ref) < TOL_D
+    finally:
+        capi.hrkan_destroy(h)
+
+
+def test_noalloc_refuses_networks_above_the_scratch_size():
+    """[2,16,16,1] with G = 4096: 1.3 M weights exceed the 1 Mi floats of static scratch; the
+    call is refused on the host, before anything is enqueued."""
+    cfg = capi.make_cfg([2, 16, 16, 1], 4096)
+    assert capi.hrkan_param_count(cfg) > (1 << 20)
+    z = torch.zeros(16, device="cuda")
+    with pytest.raises(capi.HRKANError) as ei:
+        capi.hrkan_backward_noalloc(cfg, z, z, 4, 0x1F, z, z)
+    assert ei.value.code == capi.HRKAN_EINVAL
