@@ -51,7 +51,31 @@ struct hrkan_ctx {
         size_t partial_cap = 0;     // floats
         double* loss_partial = nullptr;
     } train_batch, fwd_batch;
-    int batch_items_points = 1024;  // points per work item
+    int batch_items_points = 1024;  // points per work item (layer-wise path: per weight-gradient chunk)
+    // layer-wise multi-instance layout: every instance's points in whole blocks
+    // of LB_BLOCK (rebuilt only when the offsets, problems or chunk size change)
+    struct LBatch {
+        std::vector<int64_t> off0, off1;
+        std::vector<double> ab;
+        int n_inst = 0, chunk_blocks = 0;
+        bool built = false;
+        int64_t NPi = 0, NPb = 0;        // padded point counts of the interior / boundary sets
+        int nbi = 0, nbb = 0;            // their point blocks
+        int nci = 0, ncb = 0;            // their weight-gradient chunks
+        int rows = 0, lrows = 0;         // gradient-partial rows (chunks) and loss-partial rows (blocks)
+        void* mem = nullptr;             // every device table below, in one allocation
+        size_t mem_bytes = 0;
+        int *blk_inst_i = nullptr, *blk_valid_i = nullptr, *pt_src_i = nullptr, *lrow_i = nullptr;
+        int *blk_inst_b = nullptr, *blk_valid_b = nullptr, *pt_src_b = nullptr, *lrow_b = nullptr;
+        int4 *chunks_i = nullptr, *chunks_b = nullptr;
+        int *row_off = nullptr, *loss_off = nullptr;
+        BatchInst* inst = nullptr;
+        float* counts = nullptr;
+        float* partial = nullptr;        // [rows][P]
+        size_t partial_cap = 0;
+        double* loss_partial = nullptr;  // [lrows][2]
+        size_t lp_cap = 0;
+    } lb_train, lb_fwd;
     // layer-wise path (shapes without a fused kernel)
     std::vector<int64_t> layer_off;  // first weight of each layer
     int wide_gp = 0;                 // point groups of the weight-gradient kernels
@@ -552,6 +576,401 @@ int wide_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float* 
     return HRKAN_OK;
 }
 
+
+// ------------------------------------------------ layer-wise, many instances
+
+// Builds (or reuses) the block-padded layout of a multi-instance call on the
+// layer-wise path.  Instance i's interior points [off0[i], off0[i+1]) take
+// ceil(n/LB_BLOCK) whole blocks (the last one filled with copies of the
+// instance's last point), likewise its boundary points when off1 is given.
+// Weight-gradient chunks (at most chunk_blocks blocks of one instance and set)
+// and loss rows (one per block) are numbered instance by instance, so that
+// instance i's gradient partials are rows [row_off[i], row_off[i+1]) and its
+// loss partials rows [loss_off[i], loss_off[i+1]).
+int build_lbatch(hrkan_t h, hrkan_ctx::LBatch& b, int n_inst, const pinn_problem* probs, const int64_t* off0,
+                 const int64_t* off1, cudaStream_t stream) {
+    const bool train = off1 != nullptr;
+    for (int i = 0; i < n_inst; ++i) {
+        if (off0[i + 1] < off0[i]) return fail(HRKAN_EINVAL, "interior offsets decrease at instance %d", i);
+        if (train && off1[i + 1] < off1[i]) return fail(HRKAN_EINVAL, "boundary offsets decrease at instance %d", i);
+    }
+    if (off0[0] != 0 || (train && off1[0] != 0)) return fail(HRKAN_EINVAL, "offsets must start at 0");
+    const int64_t tot0 = off0[n_inst], tot1 = train ? off1[n_inst] : 0;
+    const int64_t cb = std::max<int64_t>(1, (int64_t(h->batch_items_points) + LB_BLOCK - 1) / LB_BLOCK);
+    // block counts, padded sizes and chunk rows must stay in int range
+    if ((tot0 + int64_t(LB_BLOCK) * n_inst) / LB_BLOCK > (int64_t(1) << 30) / LB_BLOCK ||
+        (tot1 + int64_t(LB_BLOCK) * n_inst) / LB_BLOCK > (int64_t(1) << 30) / LB_BLOCK)
+        return fail(HRKAN_EINVAL, "more than 2^30 padded points in one set");
+    std::vector<double> ab;
+    if (probs)
+        for (int i = 0; i < n_inst; ++i) {
+            ab.push_back(probs[i].a);
+            ab.push_back(probs[i].b);
+            ab.push_back(probs[i].alpha);
+        }
+    std::vector<int64_t> o0(off0, off0 + n_inst + 1), o1;
+    if (train) o1.assign(off1, off1 + n_inst + 1);
+    if (b.built && b.n_inst == n_inst && b.chunk_blocks == int(cb) && b.off0 == o0 && b.off1 == o1 && b.ab == ab)
+        return HRKAN_OK;
+    if (b.built) {   // earlier launches on this stream may still read the old tables
+        cudaError_t se = cudaStreamSynchronize(stream);
+        if (se != cudaSuccess) return cuda_fail(se, "cudaStreamSynchronize before rebuilding the batch layout");
+    }
+    b.built = false;
+
+    struct Set {
+        std::vector<int> blk_inst, blk_valid, pt_src, lrow;
+        std::vector<int4> chunks;
+    } set[2];
+    std::vector<int> row_off(n_inst + 1, 0), loss_off(n_inst + 1, 0);
+    std::vector<BatchInst> inst(n_inst);
+    std::vector<float> counts(2 * n_inst, 0.0f);
+    int row = 0, lrow = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        row_off[i] = row;
+        loss_off[i] = lrow;
+        for (int sidx = 0; sidx < (train ? 2 : 1); ++sidx) {
+            const int64_t* off = sidx == 0 ? off0 : off1;
+            Set& S = set[sidx];
+            const int64_t n = off[i + 1] - off[i];
+            const int nb = int((n + LB_BLOCK - 1) / LB_BLOCK);
+            const int b0 = int(S.blk_inst.size());
+            for (int k = 0; k < nb; ++k) {
+                S.blk_inst.push_back(i);
+                S.blk_valid.push_back(int(std::min<int64_t>(LB_BLOCK, n - int64_t(k) * LB_BLOCK)));
+                S.lrow.push_back(lrow++);
+                for (int t = 0; t < LB_BLOCK; ++t)
+                    S.pt_src.push_back(int(off[i] + std::min<int64_t>(int64_t(k) * LB_BLOCK + t, n - 1)));
+            }
+            for (int k = 0; k < nb; k += int(cb)) {
+                const int e = std::min(nb, k + int(cb));
+                S.chunks.push_back(make_int4((b0 + k) * LB_BLOCK, (b0 + e) * LB_BLOCK, row++, i));
+            }
+        }
+        const double ni = double(off0[i + 1] - off0[i]), nb = train ? double(off1[i + 1] - off1[i]) : 0.0;
+        counts[2 * i] = float(ni);
+        counts[2 * i + 1] = float(nb);
+        if (probs) {
+            const double a = probs[i].a, bb = probs[i].b;
+            inst[i] = {float(a), float(bb), float((a * a + bb * bb) * M_PI * M_PI),
+                       ni > 0 ? float(2.0 * probs[i].alpha / ni) : 0.0f, nb > 0 ? float(2.0 / nb) : 0.0f};
+        }
+    }
+    row_off[n_inst] = row;
+    loss_off[n_inst] = lrow;
+    // one device allocation holding every table
+    std::vector<char> host;
+    auto put = [&](const void* src, size_t bytes) {
+        const size_t at = (host.size() + 255) & ~size_t(255);
+        host.resize(at + std::max<size_t>(bytes, 16));
+        if (bytes) std::memcpy(host.data() + at, src, bytes);
+        return at;
+    };
+    const size_t a_bi = put(set[0].blk_inst.data(), set[0].blk_inst.size() * sizeof(int));
+    const size_t a_bv = put(set[0].blk_valid.data(), set[0].blk_valid.size() * sizeof(int));
+    const size_t a_ps = put(set[0].pt_src.data(), set[0].pt_src.size() * sizeof(int));
+    const size_t a_lr = put(set[0].lrow.data(), set[0].lrow.size() * sizeof(int));
+    const size_t a_ch = put(set[0].chunks.data(), set[0].chunks.size() * sizeof(int4));
+    const size_t b_bi = put(set[1].blk_inst.data(), set[1].blk_inst.size() * sizeof(int));
+    const size_t b_bv = put(set[1].blk_valid.data(), set[1].blk_valid.size() * sizeof(int));
+    const size_t b_ps = put(set[1].pt_src.data(), set[1].pt_src.size() * sizeof(int));
+    const size_t b_lr = put(set[1].lrow.data(), set[1].lrow.size() * sizeof(int));
+    const size_t b_ch = put(set[1].chunks.data(), set[1].chunks.size() * sizeof(int4));
+    const size_t a_ro = put(row_off.data(), row_off.size() * sizeof(int));
+    const size_t a_lo = put(loss_off.data(), loss_off.size() * sizeof(int));
+    const size_t a_in = put(inst.data(), inst.size() * sizeof(BatchInst));
+    const size_t a_co = put(counts.data(), counts.size() * sizeof(float));
+    cudaError_t e;
+    if (host.size() > b.mem_bytes) {
+        cudaFree(b.mem);
+        b.mem = nullptr;
+        b.mem_bytes = 0;
+        if ((e = cudaMalloc(&b.mem, host.size())) != cudaSuccess)
+            return fail(HRKAN_ENOMEM, "cudaMalloc of the batch layout: %s", cudaGetErrorString(e));
+        b.mem_bytes = host.size();
+    }
+    if ((e = cudaMemcpy(b.mem, host.data(), host.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "batch layout upload");
+    char* m = static_cast<char*>(b.mem);
+    b.blk_inst_i = reinterpret_cast<int*>(m + a_bi);
+    b.blk_valid_i = reinterpret_cast<int*>(m + a_bv);
+    b.pt_src_i = reinterpret_cast<int*>(m + a_ps);
+    b.lrow_i = reinterpret_cast<int*>(m + a_lr);
+    b.chunks_i = reinterpret_cast<int4*>(m + a_ch);
+    b.blk_inst_b = reinterpret_cast<int*>(m + b_bi);
+    b.blk_valid_b = reinterpret_cast<int*>(m + b_bv);
+    b.pt_src_b = reinterpret_cast<int*>(m + b_ps);
+    b.lrow_b = reinterpret_cast<int*>(m + b_lr);
+    b.chunks_b = reinterpret_cast<int4*>(m + b_ch);
+    b.row_off = reinterpret_cast<int*>(m + a_ro);
+    b.loss_off = reinterpret_cast<int*>(m + a_lo);
+    b.inst = reinterpret_cast<BatchInst*>(m + a_in);
+    b.counts = reinterpret_cast<float*>(m + a_co);
+    b.nbi = int(set[0].blk_inst.size());
+    b.nbb = int(set[1].blk_inst.size());
+    b.NPi = int64_t(b.nbi) * LB_BLOCK;
+    b.NPb = int64_t(b.nbb) * LB_BLOCK;
+    b.nci = int(set[0].chunks.size());
+    b.ncb = int(set[1].chunks.size());
+    b.rows = row;
+    b.lrows = lrow;
+    if (train) {
+        const size_t pf = size_t(std::max(row, 1)) * size_t(h->P);
+        if (pf > b.partial_cap) {
+            cudaFree(b.partial);
+            b.partial = nullptr;
+            b.partial_cap = 0;
+            if ((e = cudaMalloc(&b.partial, pf * sizeof(float))) != cudaSuccess)
+                return fail(HRKAN_ENOMEM, "cudaMalloc of the gradient partials: %s", cudaGetErrorString(e));
+            b.partial_cap = pf;
+        }
+        const size_t lf = size_t(std::max(lrow, 1)) * 2;
+        if (lf > b.lp_cap) {
+            cudaFree(b.loss_partial);
+            b.loss_partial = nullptr;
+            b.lp_cap = 0;
+            if ((e = cudaMalloc(&b.loss_partial, lf * sizeof(double))) != cudaSuccess)
+                return fail(HRKAN_ENOMEM, "cudaMalloc of the loss partials: %s", cudaGetErrorString(e));
+            b.lp_cap = lf;
+        }
+    }
+    b.n_inst = n_inst;
+    b.chunk_blocks = int(cb);
+    b.off0 = std::move(o0);
+    b.off1 = std::move(o1);
+    b.ab = std::move(ab);
+    b.built = true;
+    return HRKAN_OK;
+}
+
+// One layer's forward over a block-padded multi-instance point set.
+int lb_forward_layer(hrkan_t h, const float* W, int l, const float* in, float* out, int64_t N, unsigned mask,
+                     const int* blk_inst, cudaStream_t s) {
+    if (N == 0) return HRKAN_OK;
+    WideLayer p = wide_layer(h, W, l, N);
+    p.z = in;
+    p.y = out;
+    p.blk_inst = blk_inst;
+    p.w_stride = h->P;
+    const int n_inst = h->cfg.n_instances;
+    if (l > 0 && tc_layer_supported(h->cfg.prec, p.I, p.O, h->n, mask)) {
+        int rc = HRKAN_OK;
+        const int64_t welems = tc_w_elems(p.O, p.I, h->n, h->cfg.prec) * n_inst;
+        float* wp = ws_get(h, 20, size_t(welems), &rc);
+        if (!wp) return rc;
+        cudaError_t e;
+        {
+            ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
+            e = tc_forward_layer(p.W, wp, in, out, p.I, p.O, N, h->grid, h->cfg.prec, mask, h->status, s, n_inst,
+                                 h->P, blk_inst);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "tensor-core layer launch (batched)");
+        return HRKAN_OK;
+    }
+    cudaError_t e;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_FORWARD, s);
+        e = wide_forward_layer(p, mask, l == 0, s);
+    }
+    if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no layer kernel", mask);
+    if (e != cudaSuccess) return cuda_fail(e, "layer forward launch (batched)");
+    return HRKAN_OK;
+}
+
+// Forward of one padded set through every layer: layer inputs into `tape`
+// (layer l at tape_offset(l)) or, without a tape, ping-pong slots zslot and
+// zslot + 1; output jets into out [J][N].
+int lb_forward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsigned mask, float* out, float* tape,
+                   const int* blk_inst, int zslot, cudaStream_t s) {
+    if (N == 0) return HRKAN_OK;
+    const int J = jets_of(mask), L = h->L;
+    int rc = HRKAN_OK;
+    const float* in = x;
+    for (int l = 0; l < L; ++l) {
+        const int O = h->cfg.widths[l + 1];
+        float* y;
+        if (l == L - 1) y = out;
+        else if (tape) y = tape + tape_offset(h, l + 1, N, J);
+        else if (!(y = ws_get(h, zslot + (l % 2), size_t(J) * O * N, &rc))) return rc;
+        if ((rc = lb_forward_layer(h, W, l, in, y, N, mask, blk_inst, s))) return rc;
+        in = y;
+    }
+    return HRKAN_OK;
+}
+
+// Backward of one padded set (its tape kept by the forward): every layer's
+// weight-gradient chunks into their partial rows and, past the first layer,
+// the input adjoint.
+int lb_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsigned mask, const float* tape,
+                    const float* gy_out, const int* blk_inst, const int4* chunks, int nchunk, float* partial,
+                    cudaStream_t s) {
+    if (N == 0) return HRKAN_OK;
+    const int J = jets_of(mask), L = h->L, n_inst = h->cfg.n_instances;
+    int rc = HRKAN_OK;
+    const float* gy = gy_out;
+    for (int l = L - 1; l >= 0; --l) {
+        const float* zl = l > 0 ? tape + tape_offset(h, l, N, J) : x;
+        WideDw d{};
+        d.z = zl;
+        d.gy = gy;
+        d.I = h->cfg.widths[l];
+        d.O = h->cfg.widths[l + 1];
+        d.N = N;
+        d.partial = partial;
+        d.P = h->P;
+        d.col0 = h->layer_off[l];
+        d.row0 = 0;
+        d.GP = nchunk;
+        d.g = h->grid;
+        d.chunks = chunks;
+        cudaError_t e;
+        const bool tc_dw = tc_dw_supported(h->cfg.prec, d.I, d.O, h->n, mask);
+        if (tc_dw) {
+            const int64_t el = tc_dw_gy_elems(J, d.O, N);
+            float* gbf = ws_get(h, 21, size_t((el + 1) / 2), &rc);
+            if (!gbf) return rc;
+            ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
+            e = tc_dw_layer(d.z, d.gy, gbf, d.I, d.O, N, d.g, mask, l == 0, partial, h->P, d.col0, 0, nchunk,
+                            h->status, s, chunks);
+        } else {
+            ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
+            e = wide_dw_layer(d, mask, l == 0, s);
+        }
+        if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no layer kernel", mask);
+        if (e != cudaSuccess) return cuda_fail(e, "weight-gradient launch (batched)");
+        if (l > 0) {
+            WideLayer a = wide_layer(h, W, l, N);
+            a.z = zl;
+            a.gy = gy;
+            a.blk_inst = blk_inst;
+            a.w_stride = h->P;
+            float* gz = ws_get(h, 23 + (l % 2), size_t(J) * a.I * N, &rc);
+            if (!gz) return rc;
+            a.gz = gz;
+            if (tc_dw && tc_adj_supported(h->cfg.prec, a.I, a.O, h->n, mask)) {
+                // the weight-gradient call above left the BF16 gy copy in slot 21
+                float* gbf = ws_get(h, 21, size_t((tc_dw_gy_elems(J, a.O, N) + 1) / 2), &rc);
+                float* wbf =
+                    gbf ? ws_get(h, 22, size_t((tc_adj_w_elems(a.O, a.I, h->n) * n_inst + 1) / 2), &rc) : nullptr;
+                if (!wbf) return rc;
+                ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
+                e = tc_adj_layer(a.W, wbf, gbf, zl, gz, a.I, a.O, N, h->grid, mask, h->status, s, n_inst, h->P, chunks,
+                                 nchunk);
+            } else {
+                ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
+                e = wide_adjoint_layer(a, mask, s);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "adjoint launch (batched)");
+            gy = gz;
+        }
+    }
+    return HRKAN_OK;
+}
+
+// Multi-instance training step on the layer-wise path: gather both point sets
+// into the block-padded layout, forward with the tape kept, residual/loss per
+// instance, backward of both sets into per-chunk partial rows, then the
+// per-instance fixed-order reduction and Adam.
+int lb_train_step(hrkan_t h, const pinn_problem* probs, float* W, const float* x_int, const int64_t* off_int,
+                  const float* x_bnd, const float* g_bnd, const int64_t* off_bnd, double lr, double b1, double b2,
+                  double eps, int t, double* loss, float* dW, cudaStream_t s) {
+    const int n_inst = h->cfg.n_instances;
+    auto& b = h->lb_train;
+    if (int rc = build_lbatch(h, b, n_inst, probs, off_int, off_bnd, s)) return rc;
+    const unsigned mask = pde_mask(probs[0].kind);
+    if (!residual_mask_supported(mask)) return fail(HRKAN_EUNSUPPORTED, "no residual kernel for mask 0x%x", mask);
+    const int J = jets_of(mask);
+    const int64_t Ni = b.NPi, Nb = b.NPb;
+    int rc = HRKAN_OK;
+    float* xi = ws_get(h, 25, size_t(2 * std::max<int64_t>(Ni, 1)), &rc);
+    float* xb = xi ? ws_get(h, 26, size_t(2 * std::max<int64_t>(Nb, 1)), &rc) : nullptr;
+    float* gb = xb ? ws_get(h, 27, size_t(std::max<int64_t>(Nb, 1)), &rc) : nullptr;
+    float* ti = gb ? ws_get(h, 28, size_t(std::max<int64_t>(tape_total(h, Ni, J), 1)), &rc) : nullptr;
+    float* tb = ti ? ws_get(h, 29, size_t(std::max<int64_t>(tape_total(h, Nb, 1), 1)), &rc) : nullptr;
+    float* jets = tb ? ws_get(h, 30, size_t(J) * std::max<int64_t>(Ni, 1), &rc) : nullptr;
+    float* dli = jets ? ws_get(h, 31, size_t(J) * std::max<int64_t>(Ni, 1), &rc) : nullptr;
+    float* ub = dli ? ws_get(h, 32, size_t(std::max<int64_t>(Nb, 1)), &rc) : nullptr;
+    float* dlb = ub ? ws_get(h, 33, size_t(std::max<int64_t>(Nb, 1)), &rc) : nullptr;
+    if (!dlb) return rc;
+    const int64_t n0 = off_int[n_inst], n1 = off_bnd[n_inst];
+    HR_CUDA(lb_gather(x_int, n0, b.pt_src_i, xi, Ni, 2, s), "point gather");
+    HR_CUDA(lb_gather(x_bnd, n1, b.pt_src_b, xb, Nb, 2, s), "point gather");
+    HR_CUDA(lb_gather(g_bnd, n1, b.pt_src_b, gb, Nb, 1, s), "point gather");
+    if ((rc = lb_forward_set(h, W, xi, Ni, mask, jets, ti, b.blk_inst_i, 0, s))) return rc;
+    if ((rc = lb_forward_set(h, W, xb, Nb, 0x1u, ub, tb, b.blk_inst_b, 0, s))) return rc;
+    LbResidualParams r{};
+    r.pde = make_pde(&probs[0]);
+    r.mask = mask;
+    r.inst = b.inst;
+    r.x = xi;
+    r.jets = jets;
+    r.Ni = Ni;
+    r.dL = dli;
+    r.u_bnd = ub;
+    r.g_bnd = gb;
+    r.Nb = Nb;
+    r.dLb = dlb;
+    r.nbi = b.nbi;
+    r.nbb = b.nbb;
+    r.blk_inst_int = b.blk_inst_i;
+    r.blk_valid_int = b.blk_valid_i;
+    r.blk_inst_bnd = b.blk_inst_b;
+    r.blk_valid_bnd = b.blk_valid_b;
+    r.lrow_int = b.lrow_i;
+    r.lrow_bnd = b.lrow_b;
+    r.loss_partial = b.loss_partial;
+    r.t_counter = t == 0 ? h->t_counter : nullptr;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_RESIDUAL, s);
+        HR_CUDA(lb_residual(r, s), "residual launch (batched)");
+    }
+    if ((rc = lb_backward_set(h, W, xi, Ni, mask, ti, dli, b.blk_inst_i, b.chunks_i, b.nci, b.partial, s))) return rc;
+    if ((rc = lb_backward_set(h, W, xb, Nb, 0x1u, tb, dlb, b.blk_inst_b, b.chunks_b, b.ncb, b.partial, s))) return rc;
+    BatchReduceParams q{};
+    q.partial = b.partial;
+    q.item_off = b.row_off;
+    q.loss_off = b.loss_off;
+    q.n_inst = n_inst;
+    q.P = h->P;
+    q.W = W;
+    q.m1 = h->m1;
+    q.m2 = h->m2;
+    q.lr = lr; q.b1 = b1; q.b2 = b2; q.eps = eps;
+    q.c1 = 1.0 - std::pow(b1, t > 0 ? t : 1);
+    q.c2 = 1.0 - std::pow(b2, t > 0 ? t : 1);
+    q.t_counter = t == 0 ? h->t_counter : nullptr;
+    q.loss_partial = b.loss_partial;
+    q.counts = b.counts;
+    q.loss = loss;
+    q.status = h->status;
+    q.dW = dW;
+    q.alpha = probs[0].alpha;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_REDUCE, s);
+        HR_CUDA(launch_batch_reduce(q, s), "multi-instance reduce launch (batched)");
+    }
+    return HRKAN_OK;
+}
+
+// Output jets of every instance on the layer-wise path: gather, forward, scatter.
+int lb_forward_batched(hrkan_t h, const float* W, const float* x, const int64_t* offsets, unsigned mask, float* jets,
+                       cudaStream_t s) {
+    const int n_inst = h->cfg.n_instances;
+    auto& b = h->lb_fwd;
+    if (int rc = build_lbatch(h, b, n_inst, nullptr, offsets, nullptr, s)) return rc;
+    const int J = jets_of(mask);
+    const int64_t Np = b.NPi, N = offsets[n_inst];
+    if (N == 0) return HRKAN_OK;
+    int rc = HRKAN_OK;
+    float* xp = ws_get(h, 34, size_t(2 * Np), &rc);
+    float* out = xp ? ws_get(h, 35, size_t(J) * Np, &rc) : nullptr;
+    if (!out) return rc;
+    HR_CUDA(lb_gather(x, N, b.pt_src_i, xp, Np, 2, s), "point gather");
+    if ((rc = lb_forward_set(h, W, xp, Np, mask, out, nullptr, b.blk_inst_i, 36, s))) return rc;
+    HR_CUDA(lb_scatter(out, Np, b.pt_src_i, b.blk_valid_i, jets, N, J, s), "jet scatter");
+    return HRKAN_OK;
+}
+
 }  // namespace
 
 namespace hrkan {
@@ -688,8 +1107,7 @@ int hrkan_init(hrkan_t* out, const hrkan_cfg* cfg) {
     if (cfg->prec != HRKAN_FP32 && cfg->m != 4)
         return fail(HRKAN_EUNSUPPORTED, "precision %d: the tensor-core kernels are built for m = 4 (m=%d)", cfg->prec,
                     cfg->m);
-    if (net_id < 0 && cfg->n_instances != 1)
-        return fail(HRKAN_EUNSUPPORTED, "several instances need a fused shape ([2,W,1] or [2,W,W,1], W in 5,10,16)");
+    // several instances: the fused multi-instance kernels, or the layer-wise multi-instance path
     if (cfg->prec != HRKAN_FP32 && net_id >= 0)
         return fail(HRKAN_EUNSUPPORTED, "precision %d: the fused narrow kernels are FP32 only (set HRKAN_FLAG_LAYERWISE)",
                     cfg->prec);
@@ -755,6 +1173,11 @@ void hrkan_destroy(hrkan_t h) {
     cudaFree(h->m2);
     cudaFree(h->t_counter);
     cudaFree(h->status);
+    for (auto* b : {&h->lb_train, &h->lb_fwd}) {
+        cudaFree(b->mem);
+        cudaFree(b->partial);
+        cudaFree(b->loss_partial);
+    }
     for (auto* b : {&h->train_batch, &h->fwd_batch}) {
         cudaFree(b->items); cudaFree(b->inst); cudaFree(b->item_off); cudaFree(b->counts);
         cudaFree(b->partial); cudaFree(b->loss_partial);
@@ -1102,8 +1525,6 @@ int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, con
                              double lr, double b1, double b2, double eps, int t, double* loss, float* dW,
                              hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
-    if (h->net_id < 0)
-        return fail(HRKAN_EUNSUPPORTED, "multi-instance calls need a fused shape ([2,W,1] or [2,W,W,1], W in 5,10,16)");
     const int n_inst = h->cfg.n_instances;
     if (!probs || !off_int || !off_bnd) return fail(HRKAN_EINVAL, "NULL host array");
     for (int i = 0; i < n_inst; ++i) {
@@ -1119,8 +1540,10 @@ int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, con
     const int64_t n0 = off_int[n_inst], n1 = off_bnd[n_inst];
     if ((n0 > 0 && !x_int) || (n1 > 0 && (!x_bnd || !g_bnd))) return fail(HRKAN_EINVAL, "NULL point array");
     if (int rc = use_device(h)) return rc;
-    auto& b = h->train_batch;
     cudaStream_t s = (cudaStream_t)stream;
+    if (h->net_id < 0)   // layer-wise multi-instance path
+        return lb_train_step(h, probs, W, x_int, off_int, x_bnd, g_bnd, off_bnd, lr, b1, b2, eps, t, loss, dW, s);
+    auto& b = h->train_batch;
     if (int rc = build_batch(h, b, n_inst, probs, off_int, off_bnd, true, s)) return rc;
     const unsigned mask = pde_mask(probs[0].kind);
     BatchParams p{};
@@ -1239,14 +1662,21 @@ int hrkan_autotune_batch(hrkan_t h, const pinn_problem* probs, float* W, const f
 int hrkan_forward_jets_batched(hrkan_t h, const float* W, const float* x, const int64_t* offsets, unsigned jet_mask,
                                float* jets, hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
-    if (h->net_id < 0)
-        return fail(HRKAN_EUNSUPPORTED, "multi-instance calls need a fused shape ([2,W,1] or [2,W,W,1], W in 5,10,16)");
     if (!offsets) return fail(HRKAN_EINVAL, "offsets is NULL");
     if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
     const int n_inst = h->cfg.n_instances;
     const int64_t N = offsets[n_inst];
     if (N > 0 && (!W || !x || !jets)) return fail(HRKAN_EINVAL, "NULL device pointer");
     if (int rc = use_device(h)) return rc;
+    if (h->net_id < 0) {   // layer-wise multi-instance path
+        if (h->cfg.widths[0] != 2) return fail(HRKAN_EUNSUPPORTED, "multi-instance calls take two inputs");
+        int rc = HRKAN_OK;
+        {
+            ProfScope ps(h, HRKAN_KERNEL_FORWARD, (cudaStream_t)stream);
+            rc = lb_forward_batched(h, W, x, offsets, jet_mask, jets, (cudaStream_t)stream);
+        }
+        return rc;
+    }
     auto& b = h->fwd_batch;
     if (int rc = build_batch(h, b, n_inst, nullptr, offsets, nullptr, false, (cudaStream_t)stream)) return rc;
     if (b.n_items == 0) return HRKAN_OK;

@@ -61,7 +61,9 @@ struct BatchReduceParams {
     double* m2;
     double lr, b1, b2, eps, c1, c2;
     int* t_counter;
-    const double* loss_partial;  // [n_items][2]
+    const double* loss_partial;  // [n_items][2] (rows of instance i: [item_off[i], item_off[i+1]))
+    const int* loss_off;         // optional [n_inst + 1]: the loss-partial rows of instance i are
+                                 // [loss_off[i], loss_off[i+1]) instead
     const float* counts;         // [n_inst][2] interior / boundary point counts
     double* loss;                // [n_inst][3]
     float* dW;                   // optional [n_inst][P]
@@ -88,6 +90,43 @@ struct ResidualParams {
 // Enqueue the residual kernel on `grid` blocks (grid must be <= the rows of loss_partial).
 cudaError_t launch_residual(const ResidualParams& p, int grid, cudaStream_t s);
 bool residual_mask_supported(unsigned mask);
+
+// ---- layer-wise multi-instance path (lbatch.cu) ------------------------------------
+// Points of every instance sit in whole blocks of LB_BLOCK points (the layer
+// kernels' point block, two tensor-core tiles), padded with copies of the
+// instance's last point.
+constexpr int LB_BLOCK = 256;
+struct BatchInst;
+struct LbResidualParams {
+    PdeParams pde;                 // kind, lam, nu, alpha (a, b, src per instance)
+    unsigned mask;
+    const BatchInst* inst;         // [n_inst]: a, b, src, scale0 = 2 alpha / n_int, scale1 = 2 / n_bnd
+    const float* x;                // padded interior coordinates [2][Ni]
+    const float* jets;             // [J][Ni]
+    int64_t Ni;
+    float* dL;                     // [J][Ni] (written; zero at padding points)
+    const float* u_bnd;            // [Nb]
+    const float* g_bnd;            // padded boundary targets [Nb]
+    int64_t Nb;
+    float* dLb;                    // [Nb] (written; zero at padding points)
+    int nbi, nbb;                  // interior / boundary point blocks
+    const int* blk_inst_int;       // [nbi] instance of each block
+    const int* blk_valid_int;      // [nbi] real points in each block
+    const int* blk_inst_bnd;       // [nbb]
+    const int* blk_valid_bnd;      // [nbb]
+    const int* lrow_int;           // [nbi] loss-partial row of each block
+    const int* lrow_bnd;           // [nbb]
+    double* loss_partial;          // [rows][2] (interior, boundary sums of squares)
+    int* t_counter;                // optional device step counter: t_counter[1] = t_counter[0] + 1
+};
+// dst[r][p] = src[r][pt_src[p]], r < rows, p < n_dst (source rows n_src apart).
+cudaError_t lb_gather(const float* src, int64_t n_src, const int* pt_src, float* dst, int64_t n_dst, int rows,
+                      cudaStream_t s);
+// dst[r][pt_src[p]] = src[r][p] for the real points p < n_src of the padded layout.
+cudaError_t lb_scatter(const float* src, int64_t n_src, const int* pt_src, const int* blk_valid, float* dst,
+                       int64_t n_dst, int rows, cudaStream_t s);
+// Residual and loss partials of both point sets, one block per point block (masks 0x0F, 0x1F, 0x2F).
+cudaError_t lb_residual(const LbResidualParams& p, cudaStream_t s);
 
 // out[c] = fixed-order sum of rows [0, rows) of src (row stride `stride`), c < cols.
 cudaError_t sum_rows(const float* src, int rows, int64_t stride, int64_t cols, float* out, cudaStream_t s);

@@ -228,7 +228,8 @@ __global__ void __launch_bounds__(RED_LANES * RED_WARPS) batch_reduce_kernel(Bat
     if (p.t_counter && blockIdx.x == 0 && inst == 0 && w == 0 && lane == 0) p.t_counter[0] = p.t_counter[1];
     if (blockIdx.x == 0) {   // block-uniform
         double s0, s1;
-        fold_loss_rows(p.loss_partial, r0, r1, s0, s1);
+        if (p.loss_off) fold_loss_rows(p.loss_partial, p.loss_off[inst], p.loss_off[inst + 1], s0, s1);
+        else fold_loss_rows(p.loss_partial, r0, r1, s0, s1);
         if (w == 0 && lane == 0) {
             const double n0 = p.counts[2 * inst], n1 = p.counts[2 * inst + 1];
             const double lp = n0 > 0 ? s0 / n0 : 0.0;

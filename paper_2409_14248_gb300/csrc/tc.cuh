@@ -27,6 +27,10 @@ struct TcLayer {
     int ntiles;       // tiles of 128 points
     Grid g;
     int* status;      // device error word (HRKAN_ETIMEOUT on a timed-out wait)
+    // many instances (batched path): tile t (128 points) belongs to instance
+    // blk_inst[t / 2] (point blocks of 256), whose W tiles start at row
+    // blk_inst[t / 2] * TERMS * O of the tensor map; nullptr: one instance
+    const int* blk_inst = nullptr;
 };
 
 // Layers the tensor-core kernel handles: 16 <= O <= 64, O % 16 == 0,
@@ -37,8 +41,12 @@ int64_t tc_w_elems(int O, int I, int n, int prec);
 // Converts W (float32 [O][I][n]) into w_prep (tc_w_elems elements of 2 or 4
 // bytes, units padded) and runs the tensor-core contraction: y = jets of the
 // layer output.
+// Many instances: W holds n_inst layers w_stride floats apart, w_prep
+// n_inst * tc_w_elems elements, and blk_inst (device, one entry per 256
+// points) names the instance of every point block.
 cudaError_t tc_forward_layer(const float* W, void* w_prep, const float* z, float* y, int I, int O, int64_t N,
-                             const Grid& g, int prec, unsigned mask, int* status, cudaStream_t s);
+                             const Grid& g, int prec, unsigned mask, int* status, cudaStream_t s, int n_inst = 1,
+                             int64_t w_stride = 0, const int* blk_inst = nullptr);
 
 // Tensor-core weight gradient of one hidden layer (tc_dw.cu): BF16 inputs,
 // FP32 accumulation, 16 <= O <= 64 with O % 16 == 0, n <= 64.
@@ -51,16 +59,25 @@ int64_t tc_dw_gy_elems(int J, int O, int64_t N);
 // of partial [rows][P]) from input jets z [J][I][N] and output-jet gradients
 // gy [J][O][N]; gy_bf is scratch of tc_dw_gy_elems 2-byte elements.
 // first: z is the coordinates [2][N] (layer 0).
+// chunks (batched path, device, nchunk entries): chunk c covers points
+// [chunks[c].x, chunks[c].y) (multiples of 256) and writes partial row
+// chunks[c].z (row0 unused); nullptr: the points split evenly into rows
+// row0 .. row0 + nchunk - 1.
 cudaError_t tc_dw_layer(const float* z, const float* gy, void* gy_bf, int I, int O, int64_t N, const Grid& g,
                         unsigned mask, bool first, float* partial, int64_t P, int64_t col0, int row0, int nchunk,
-                        int* status, cudaStream_t s);
+                        int* status, cudaStream_t s, const int4* chunks = nullptr);
 
 // Tensor-core input adjoint of one hidden layer (tc_adj.cu): BF16, masks 0x0F
 // and 0x1F, after tc_dw_layer of the same layer and point set (it reuses that
 // call's BF16 gy copy).  w_bf: tc_adj_w_elems 2-byte scratch elements.
 bool tc_adj_supported(int prec, int I, int O, int n, unsigned mask);
 int64_t tc_adj_w_elems(int O, int I, int n);
+// Many instances (batched path): W holds n_inst layers w_stride floats apart,
+// w_bf n_inst * tc_adj_w_elems elements, and chunk c (device, nchunk entries)
+// covers points [chunks[c].x, chunks[c].y) (multiples of 256) of instance
+// chunks[c].w.
 cudaError_t tc_adj_layer(const float* W, void* w_bf, const void* gy_bf, const float* z, float* gz, int I, int O,
-                         int64_t N, const Grid& g, unsigned mask, int* status, cudaStream_t s);
+                         int64_t N, const Grid& g, unsigned mask, int* status, cudaStream_t s, int n_inst = 1,
+                         int64_t w_stride = 0, const int4* chunks = nullptr, int nchunk = 0);
 
 }  // namespace hrkan

@@ -55,6 +55,10 @@ struct AdjParams {
     uint32_t tmem_cols;
     Grid g;
     int* status;
+    // many instances (batched path): chunk c covers points [chunks[c].x,
+    // chunks[c].y) (multiples of 256) of instance chunks[c].w, whose W rows
+    // start at chunks[c].w * O of the W tensor map; nullptr: tiles split evenly
+    const int4* chunks = nullptr;
 };
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
@@ -110,7 +114,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     float* pick = reinterpret_cast<float*>(gring + size_t(NSB) * g_bytes);   // [128][PS]
     const int kr = blockIdx.x % p.nkr, chunk = blockIdx.x / p.nkr;
     const int j0 = kr * UK;
-    const int t0 = int(int64_t(chunk) * p.ntiles / p.nchunk), t1 = int(int64_t(chunk + 1) * p.ntiles / p.nchunk);
+    const int t0 = p.chunks ? p.chunks[chunk].x / TILE : int(int64_t(chunk) * p.ntiles / p.nchunk);
+    const int t1 = p.chunks ? p.chunks[chunk].y / TILE : int(int64_t(chunk + 1) * p.ntiles / p.nchunk);
+    const int w_row0 = p.chunks ? p.chunks[chunk].w * O : 0;
     const int nt = t1 - t0;
 
     if (tid == 0) {
@@ -261,7 +267,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0 && nt > 0) {
             mbar_expect_tx(&bar_wfull, uint32_t(NBW) * box_bytes);
             for (int bx = 0; bx < NBW; ++bx)
-                tck::tma_load_2d(wtile + size_t(bx) * box_bytes, &wmap, &bar_wfull, j0 * NP + 64 * bx, 0);
+                tck::tma_load_2d(wtile + size_t(bx) * box_bytes, &wmap, &bar_wfull, j0 * NP + 64 * bx, w_row0);
             const int total = nt * J;
             uint32_t used = 0u, last_par = 0u;
             for (int q = 0; q < total; ++q) {
@@ -296,14 +302,17 @@ done:
 
 // W [O][I][n] float32 -> [O][Kt] BF16, element k = j * NP + pos holding basis
 // i = 4 * (pos mod NP/4) + pos / (NP/4) (zero for i >= n or j >= I).
+// Many instances: instance c's layer at W + c * w_stride goes to out + c * O * Kt.
 __global__ void w_bf16_kernel(const float* __restrict__ W, uint16_t* __restrict__ out, int O, int I, int n, int NP,
-                              int Kt) {
+                              int Kt, int n_inst, int64_t w_stride) {
     const int64_t total = int64_t(O) * Kt;
-    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    for (int64_t u = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; u < total * n_inst;
+         u += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t c = u / total, t = u % total;
         const int o = int(t / Kt), k = int(t % Kt);
         const int j = k / NP, pos = k % NP, q = NP / 4, i = 4 * (pos % q) + pos / q;
-        const float w = (j < I && i < n) ? W[(int64_t(o) * I + j) * n + i] : 0.0f;
-        out[t] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
+        const float w = (j < I && i < n) ? W[c * w_stride + (int64_t(o) * I + j) * n + i] : 0.0f;
+        out[u] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
     }
 }
 
@@ -392,16 +401,18 @@ int64_t tc_adj_w_elems(int O, int I, int n) {
 }
 
 cudaError_t tc_adj_layer(const float* W, void* w_bf, const void* gy_bf, const float* z, float* gz, int I, int O,
-                         int64_t N, const Grid& g, unsigned mask, int* status, cudaStream_t s) {
+                         int64_t N, const Grid& g, unsigned mask, int* status, cudaStream_t s, int n_inst,
+                         int64_t w_stride, const int4* chunks, int nchunk) {
     using namespace tcadj;
     if (N == 0) return cudaSuccess;
+    if (n_inst < 1 || (chunks && nchunk < 1) || (n_inst > 1 && !chunks)) return cudaErrorInvalidValue;
     const int n = g.n, np = np_of(n);
     const int J = __builtin_popcount(mask & 0x1Fu);
     const int Kt = int((int64_t(I) * np + 63) / 64 * 64);
     {
-        const int64_t total = int64_t(O) * Kt;
+        const int64_t total = int64_t(O) * Kt * n_inst;
         const int pb = int(std::min<int64_t>((total + 255) / 256, 4096));
-        w_bf16_kernel<<<pb, 256, 0, s>>>(W, static_cast<uint16_t*>(w_bf), O, I, n, np, Kt);
+        w_bf16_kernel<<<pb, 256, 0, s>>>(W, static_cast<uint16_t*>(w_bf), O, I, n, np, Kt, n_inst, w_stride);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -420,7 +431,7 @@ cudaError_t tc_adj_layer(const float* W, void* w_bf, const void* gy_bf, const fl
             return cudaErrorInvalidValue;
     }
     {
-        const cuuint64_t dims[2] = {cuuint64_t(Kt), cuuint64_t(O)};
+        const cuuint64_t dims[2] = {cuuint64_t(Kt), cuuint64_t(O) * cuuint64_t(n_inst)};
         const cuuint64_t strides[1] = {cuuint64_t(Kt) * 2};
         const cuuint32_t box[2] = {64, cuuint32_t(O)};
         const cuuint32_t estr[2] = {1, 1};
@@ -442,8 +453,10 @@ cudaError_t tc_adj_layer(const float* W, void* w_bf, const void* gy_bf, const fl
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    // at most one CTA per SM over the K-ranges (a single wave), at least one tile each
-    p.nchunk = std::max(1, std::min(p.ntiles, nsm / p.nkr));
+    // at most one CTA per SM over the K-ranges (a single wave), at least one tile each;
+    // the batched path takes its instances' chunks
+    p.nchunk = chunks ? nchunk : std::max(1, std::min(p.ntiles, nsm / p.nkr));
+    p.chunks = chunks;
     const int cols = 2 * uk * np;
     p.tmem_cols = cols <= 32 ? 32u : cols <= 64 ? 64u : cols <= 128 ? 128u : cols <= 256 ? 256u : 512u;
     p.g = g;

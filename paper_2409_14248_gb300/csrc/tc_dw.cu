@@ -62,6 +62,10 @@ struct DwParams {
     uint32_t tmem_cols;
     Grid g;
     int* status;
+    // many instances (batched path): chunk c covers points [chunks[c].x,
+    // chunks[c].y) (multiples of 256) and writes partial row chunks[c].z;
+    // nullptr: the groups split evenly, chunk c into row row0 + c
+    const int4* chunks = nullptr;
 };
 
 // Byte offset of element (m = k within the K-range, p = point within the group)
@@ -109,7 +113,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
     const uint32_t buf_bytes = uint32_t(A_BYTES) + b_bytes;
     const int kr = blockIdx.x % p.nkr, chunk = blockIdx.x / p.nkr;
     const int k0 = kr * 128;
-    const int g0 = int(int64_t(chunk) * p.ngroups / p.nchunk), g1 = int(int64_t(chunk + 1) * p.ngroups / p.nchunk);
+    const int g0 = p.chunks ? p.chunks[chunk].x / GROUP : int(int64_t(chunk) * p.ngroups / p.nchunk);
+    const int g1 = p.chunks ? p.chunks[chunk].y / GROUP : int(int64_t(chunk + 1) * p.ngroups / p.nchunk);
+    const int out_row = p.chunks ? p.chunks[chunk].z : p.row0 + chunk;
     const int ng = g1 - g0;
 
     if (tid == 0) {
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
             // element pos of the unit holds basis 4 * (pos mod NP8/4) + pos / (NP8/4)
             const int j = k / NP8, pos = k % NP8, i = 4 * (pos % (NP8 / 4)) + pos / (NP8 / 4);
             const bool live = j < I && i < p.n;
-            float* out = p.partial + int64_t(p.row0 + chunk) * p.P + p.col0 + int64_t(j) * p.n + i;
+            float* out = p.partial + int64_t(out_row) * p.P + p.col0 + int64_t(j) * p.n + i;
             const uint32_t lane_base = uint32_t(warp * 32) << 16;
 #pragma unroll 1
             for (int c = 0; c < O; c += 16) {
@@ -410,7 +416,7 @@ int64_t tc_dw_gy_elems(int J, int O, int64_t N) { return int64_t(J) * O * ((N + 
 
 cudaError_t tc_dw_layer(const float* z, const float* gy, void* gy_bf, int I, int O, int64_t N, const Grid& g,
                         unsigned mask, bool first, float* partial, int64_t P, int64_t col0, int row0, int nchunk,
-                        int* status, cudaStream_t s) {
+                        int* status, cudaStream_t s, const int4* chunks) {
     using namespace tcdw;
     const int J = __builtin_popcount(mask & 0x1Fu);
     const int n = g.n, np8 = np8_of(n);
@@ -445,6 +451,7 @@ cudaError_t tc_dw_layer(const float* z, const float* gy, void* gy_bf, int I, int
     p.tmem_cols = O <= 32 ? 32u : 64u;
     p.g = g;
     p.status = status;
+    p.chunks = chunks;
     const unsigned grid = unsigned(p.nkr) * unsigned(nchunk);
     const int nc = np8 / 8;
     if (first) {

@@ -45,23 +45,30 @@ int ring_slots(int J, int O) { return std::min(RING_MAX, (TMEM_COLS - J * O) / (
 // TF32-rounded float32.  BF16 (three-term split): tile 0 holds (w_hi, w_hi) in
 // the word's low and high halves, tile 1 (w_lo, 0), w_hi = bf16(w),
 // w_lo = bf16(w - w_hi).
+// Many instances: instance c's layer at W + c * w_stride goes to
+// out + c * TERMS * O * Kt.
 template <int PREC>
-__global__ void tc_prep_w_kernel(const float* __restrict__ W, uint32_t* out, int O, int I, int n, int NP, int Kt) {
+__global__ void tc_prep_w_kernel(const float* __restrict__ W, uint32_t* out, int O, int I, int n, int NP, int Kt,
+                                 int n_inst, int64_t w_stride) {
     const int64_t total = int64_t(O) * Kt;
-    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    constexpr int TERMS = PREC == HRKAN_BF16 ? 2 : 1;
+    for (int64_t u = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; u < total * n_inst;
+         u += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t c = u / total, t = u % total;
         const int o = int(t / Kt), k = int(t % Kt);
         const int j = k / NP, pos = k % NP, q = NP / 4, i = 4 * (pos % q) + pos / q;
-        const float w = (j < I && i < n) ? W[(int64_t(o) * I + j) * n + i] : 0.0f;
+        const float w = (j < I && i < n) ? W[c * w_stride + (int64_t(o) * I + j) * n + i] : 0.0f;
+        uint32_t* oc = out + c * TERMS * total;
         if constexpr (PREC == HRKAN_BF16) {
             const __nv_bfloat16 hi = __float2bfloat16_rn(w);
             const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(w - __bfloat162float(hi)));
             const uint32_t hb = __bfloat16_as_ushort(hi);
-            out[t] = hb | (hb << 16);
-            out[total + t] = lo;
+            oc[t] = hb | (hb << 16);
+            oc[total + t] = lo;
         } else {
             uint32_t r;
             asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(w));
-            out[t] = r;
+            oc[t] = r;
         }
     }
 }
@@ -114,26 +121,28 @@ bool tc_layer_supported(int prec, int I, int O, int n, unsigned mask) {
 int64_t tc_w_elems(int O, int I, int n, int prec) { return int64_t(w_terms(prec)) * O * k_layout(I, n, prec).kt; }
 
 cudaError_t tc_forward_layer(const float* W, void* w_prep, const float* z, float* y, int I, int O, int64_t N,
-                             const Grid& g, int prec, unsigned mask, int* status, cudaStream_t s) {
+                             const Grid& g, int prec, unsigned mask, int* status, cudaStream_t s, int n_inst,
+                             int64_t w_stride, const int* blk_inst) {
     if (N == 0) return cudaSuccess;
+    if (n_inst < 1 || (n_inst > 1 && !blk_inst)) return cudaErrorInvalidValue;
     const int n = g.n;
     const KLayout L = k_layout(I, n, prec);
-    const int64_t total = int64_t(O) * L.kt;
+    const int64_t total = int64_t(O) * L.kt * n_inst;
     const int pb = int(std::min<int64_t>((total + 255) / 256, 4096));
     uint32_t* wp = static_cast<uint32_t*>(w_prep);
     if (prec == HRKAN_BF16)
-        tc_prep_w_kernel<HRKAN_BF16><<<pb, 256, 0, s>>>(W, wp, O, I, n, L.np, L.kt);
+        tc_prep_w_kernel<HRKAN_BF16><<<pb, 256, 0, s>>>(W, wp, O, I, n, L.np, L.kt, n_inst, w_stride);
     else
-        tc_prep_w_kernel<HRKAN_TF32><<<pb, 256, 0, s>>>(W, wp, O, I, n, L.np, L.kt);
+        tc_prep_w_kernel<HRKAN_TF32><<<pb, 256, 0, s>>>(W, wp, O, I, n, L.np, L.kt, n_inst, w_stride);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
-    // rows of 32-bit words: the TERMS tiles of O rows each stacked, one box
-    // (32 words x TERMS*O rows) per W buffer of the kernel
+    // rows of 32-bit words: per instance the TERMS tiles of O rows each
+    // stacked, one box (32 words x TERMS*O rows) per W buffer of the kernel
     const int rows = w_terms(prec) * O;
     CUtensorMap map;
-    const cuuint64_t dims[2] = {cuuint64_t(L.kt), cuuint64_t(rows)};
+    const cuuint64_t dims[2] = {cuuint64_t(L.kt), cuuint64_t(rows) * cuuint64_t(n_inst)};
     const cuuint64_t strides[1] = {cuuint64_t(L.kt) * 4};
     const cuuint32_t box[2] = {cuuint32_t(box_elems(prec)), cuuint32_t(rows)};
     const cuuint32_t estr[2] = {1, 1};
@@ -154,6 +163,7 @@ cudaError_t tc_forward_layer(const float* W, void* w_prep, const float* z, float
     p.ntiles = int((N + 127) / 128);
     p.g = g;
     p.status = status;
+    p.blk_inst = n_inst > 1 ? blk_inst : nullptr;
     switch (L.np) {
         case 16: return tc_launch_np16(p, map, prec, mask, s);
         case 24: return tc_launch_np24(p, map, prec, mask, s);

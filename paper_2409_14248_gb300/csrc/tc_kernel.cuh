@@ -591,10 +591,12 @@ __global__ void __launch_bounds__(THREADS, 1) tc_fwd_kernel(TcLayer p, const __g
             uint32_t wph = 0;
             uint32_t used = 0u, last_par = 0u;   // bit b: buffer b has had a load / parity of its last one
             for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+                // rows of this tile's instance in the tensor map (batched path)
+                const int y0 = p.blk_inst ? p.blk_inst[tile >> 1] * (E::TERMS * O) : 0;
                 for (int bx = 0; bx < nbox; ++bx) {
                     if (!mbar_wait(&sh.wempty[wb], wph ^ 1u, abort, wl)) goto tma_out;
                     mbar_expect_tx(&sh.wfull[wb], b_bytes);
-                    tma_load_2d(smem + size_t(wb) * b_bytes, &tmap, &sh.wfull[wb], bx * E::BOX, 0);
+                    tma_load_2d(smem + size_t(wb) * b_bytes, &tmap, &sh.wfull[wb], bx * E::BOX, y0);
                     used |= 1u << wb;
                     last_par = (last_par & ~(1u << wb)) | (wph << wb);
                     if (++wb == NB) { wb = 0; wph ^= 1u; }

@@ -24,6 +24,10 @@ struct WideLayer {
     // adjoint: first point of this launch (point sets above the grid's y limit
     // run as several launches)
     int64_t p0 = 0;
+    // many instances (batched path): point block b (WB points) belongs to
+    // instance blk_inst[b], whose weights are W + blk_inst[b] * w_stride
+    const int* blk_inst = nullptr;
+    int64_t w_stride = 0;
 };
 
 // Weight gradient of one layer into partial rows [row0, row0 + GP) of a
@@ -40,6 +44,11 @@ struct WideDw {
     int GP;            // point groups = partial rows written
     Grid g;
     int seed0 = 0, seed1 = 1;   // first layer: as in WideLayer
+    // many instances (batched path): GP chunks, chunk c covering points
+    // [chunks[c].x, chunks[c].y) (multiples of WB) of instance chunks[c].w and
+    // writing partial row chunks[c].z (row0 unused); nullptr: the point tiles
+    // gp, gp + GP, ... into row row0 + gp
+    const int4* chunks = nullptr;
 };
 
 cudaError_t wide_forward_layer(const WideLayer& p, unsigned mask, bool first, cudaStream_t s);

@@ -62,9 +62,10 @@ __global__ void __launch_bounds__(WB) wide_fwd_kernel(WideLayer p) {
     extern __shared__ __align__(16) float wt[];
     const int I = p.I, O = p.O, n = p.g.n;
     const int o0 = blockIdx.y * OT;
+    const float* W = p.blk_inst ? p.W + int64_t(p.blk_inst[blockIdx.x]) * p.w_stride : p.W;
     for (int t = threadIdx.x; t < I * n * OT; t += blockDim.x) {
         const int oo = t % OT, ji = t / OT;
-        wt[t] = (o0 + oo < O) ? p.W[int64_t(o0 + oo) * I * n + ji] : 0.0f;
+        wt[t] = (o0 + oo < O) ? W[int64_t(o0 + oo) * I * n + ji] : 0.0f;
     }
     __syncthreads();
     const int64_t N = p.N;
@@ -125,9 +126,10 @@ __global__ void __launch_bounds__(WB) wide_adjoint_kernel(WideLayer p) {
     extern __shared__ __align__(16) float ws[];
     const int I = p.I, O = p.O, n = p.g.n;
     const int j0 = blockIdx.x * IT;
+    const float* W = p.blk_inst ? p.W + int64_t(p.blk_inst[p.p0 / WB + blockIdx.y]) * p.w_stride : p.W;
     for (int t = threadIdx.x; t < IT * O * n; t += blockDim.x) {
         const int i = t % n, rest = t / n, o = rest % O, jj = rest / O;
-        ws[t] = (j0 + jj < I) ? p.W[(int64_t(o) * I + j0 + jj) * n + i] : 0.0f;
+        ws[t] = (j0 + jj < I) ? W[(int64_t(o) * I + j0 + jj) * n + i] : 0.0f;
     }
     __syncthreads();
     const int64_t N = p.N;
@@ -232,7 +234,11 @@ __global__ void __launch_bounds__(WB) wide_dw_kernel(WideDw p) {
     for (int t = threadIdx.x; t < S * R * NP; t += blockDim.x) dws[t] = 0.0f;
     const int64_t N = p.N;
     const int64_t tiles = (N + PB - 1) / PB;
-    for (int64_t tile = gp; tile < tiles; tile += p.GP) {
+    // the tiles of this block's chunk (batched path), else every GP-th tile
+    const int64_t t_first = p.chunks ? int64_t(p.chunks[gp].x) / PB : gp;
+    const int64_t t_end = p.chunks ? std::min<int64_t>((int64_t(p.chunks[gp].y) + PB - 1) / PB, tiles) : tiles;
+    const int64_t t_step = p.chunks ? 1 : p.GP;
+    for (int64_t tile = t_first; tile < t_end; tile += t_step) {
         const int64_t base = tile * PB;
         __syncthreads();
         // stage gy: element (pp, r, o) = gy[r][o][base + pp]
@@ -295,7 +301,7 @@ __global__ void __launch_bounds__(WB) wide_dw_kernel(WideDw p) {
         }
     }
     __syncthreads();
-    float* out = p.partial + int64_t(p.row0 + gp) * p.P + p.col0;
+    float* out = p.partial + int64_t(p.chunks ? p.chunks[gp].z : p.row0 + gp) * p.P + p.col0;
     for (int t = threadIdx.x; t < nj * Ob * n; t += blockDim.x) {
         const int i = t % n, rest = t / n, o = rest % Ob, jj = rest / Ob;
         float v = 0.0f;

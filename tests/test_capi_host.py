@@ -62,7 +62,7 @@ def test_param_count(lib):
     (dict(widths=[2, 5, 1], G=5, m=1), capi.HRKAN_EUNSUPPORTED),   # u_xx needs m >= 2
     (dict(widths=[2, 5, 1], G=5, m=0), capi.HRKAN_EINVAL),
     (dict(widths=[2, 64, 1], G=5, m=6, prec=capi.HRKAN_BF16), capi.HRKAN_EUNSUPPORTED),  # tensor cores: m = 4
-    (dict(widths=[2, 10, 1], G=5, m=3, n_instances=4), capi.HRKAN_EUNSUPPORTED),  # batched: fused m = 4 only
+    (dict(widths=[3, 10, 1], G=5, n_instances=4), capi.HRKAN_EUNSUPPORTED),  # several instances: two inputs
 ])
 def test_bad_configuration_is_rejected_before_the_device(lib, kw, code):
     with pytest.raises(capi.HRKANError) as ei:

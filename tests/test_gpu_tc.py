@@ -14,7 +14,10 @@ Two questions, kept apart:
    and everything else is exact: the kernel must sit far closer to that than
    the rounding moves the result (a wrong operand layout, K order or a missing
    split term gives a difference of the size of the rounding or O(1)).  Inputs
-   that the rounding leaves exact must give the exact oracle's result.
+   that the rounding leaves exact must give the exact oracle's result.  At
+   network level the BF16 split is so close to exact that the tensor cores'
+   FP32 accumulation, amplified by an ill-conditioned network, is of the same
+   size; there the error is bounded by a small multiple of the split's own.
 2. How accurate is the path?  The network's jets against the exact FP64 oracle,
    per jet order: the BF16 path meets the 2e-2 bar on every row, normwise and per
    point, on [2,32,32,1] G=20 and on [2,64,64,64,1] G=32 at the workloads'
@@ -67,11 +70,20 @@ def _forward(w, prec, W, x, mask, flags=0):
         capi.hrkan_destroy(h)
 
 
+# Network level, BF16: the kernel's error against the exact oracle may exceed the split
+# emulation's own (BF16X3 with FP64 sums) by what the tensor cores' FP32 accumulation adds,
+# amplified by the network's conditioning (~600x on [2,64,64,64,1] G=32: 1.5e-3 measured
+# against 7.4e-4 emulated); a missing split term costs ~20x the emulated error.
+SPLIT_SLACK = 4.0
+
+
 def _check(w, prec, d, mask, check_impl=True):
     """Returns the per-jet-order (normwise, per-point) error vs exact FP64, after checking
-    the kernel against the rounding-aware oracle of the same layers (skipped where two or
-    more singly rounded layers make that comparison chaotic: the rounded oracle itself then
-    moves by ~1e-2 under 1e-7 weight noise)."""
+    the kernel against the rounding-aware oracle of the same layers.  TF32: the kernel sits
+    on the TF32-rounded oracle (skipped where two or more singly rounded layers make that
+    comparison chaotic: the rounded oracle itself then moves by ~1e-2 under 1e-7 weight
+    noise).  BF16: the error is within SPLIT_SLACK times the split emulation's own error plus
+    the FP32 floor."""
     x = d["x_int"]
     got = _forward(w, prec, d["W"], x, mask)
     assert np.all(np.isfinite(got))
@@ -83,9 +95,12 @@ def _check(w, prec, d, mask, check_impl=True):
     for r in range(exact.shape[0]):
         e_fmt = relerr(rounded[r], exact[r])
         e_impl = relerr(got[r], rounded[r])
-        if check_impl:
+        e_got = relerr(got[r], exact[r])
+        if check_impl and prec == capi.HRKAN_TF32:
             assert e_impl < 0.05 * e_fmt + floor[r], (r, e_impl, e_fmt)
-        errs.append((relerr(got[r], exact[r]), maxrel(got[r], exact[r])))
+        elif check_impl:
+            assert e_got < SPLIT_SLACK * e_fmt + floor[r], (r, e_got, e_fmt, floor[r])
+        errs.append((e_got, maxrel(got[r], exact[r])))
     print(f"\nper-jet-order (normwise, per-point) error, prec {prec}, mask {mask:#x}: {errs}")
     return errs
 
@@ -294,7 +309,7 @@ def test_tc_full_size_forward_sampled():
         rounded = oracle.forward_rounded(w.net, d["W"], xs, 0x1F, {1, 2}, oracle.BF16X3)
         floor = conditioned_tolerances(w, d["W"], xs, 0x1F)
         for r in range(5):
-            assert relerr(got[r], rounded[r]) < 0.05 * relerr(rounded[r], exact[r]) + floor[r], r
+            assert relerr(got[r], exact[r]) < SPLIT_SLACK * relerr(rounded[r], exact[r]) + floor[r], r
             assert_close(got[r], exact[r], BAR, what=f"row {r}")
     finally:
         capi.hrkan_destroy(h)
