@@ -2,16 +2,24 @@
 """Throughput of HRKAN physics-informed training on GB300.
 
 One step = one full-batch pass of the whole hot path over the workload's
-collocation points: forward jets (u, u_x, u_t, u_xx), Burgers residual and
-loss, backward (weight gradient), cross-block reduction and Adam.  Workload:
-viscous Burgers u_t + u u_x = nu u_xx, nu = 0.01/pi, HRKAN [2,10,10,1], G=10,
-k=3, m=4, 65536 interior + 4096 initial + 4096 boundary points (Latin
-hypercube, seed 1), FP32 path.  Inputs are synthetic and resident in HBM when
-the timed region starts; they are far smaller than L2, so L2 is flushed
-(a 256 MiB device write) before every timed step, outside its events.
+collocation points: forward jets, residual and loss, backward (weight
+gradient), cross-block reduction and Adam.  Default workload: 256 independent
+2-D Poisson instances (a, b uniform in {1..4}^2), HRKAN [2,16,16,1], G=10, k=3,
+m=4, interior counts uniform in [2048, 32768] and boundary = interior // 8
+(seed 4), all instances in one multi-instance training step, BF16 (the hidden
+layer's forward as the three-term split, weight gradient and input adjoint on
+tcgen05); the plain FP32 multi-instance path of the same workload is timed
+beside it (fp32_path), and both are trained 1000 steps on 8 of the instances
+to compare their final relative L2 errors (equal_l2).  Inputs are synthetic and
+resident in HBM when the timed region starts; L2 is flushed (a 256 MiB device
+write) before every timed step, outside its events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload NAME] [--prec fp32|bf16|tf32]
+
+--workload burgers_2_10_10_1 --prec fp32 times the single-network FP32
+Burgers workload (viscous Burgers, nu = 0.01/pi, [2,10,10,1], G=10, 65536
+interior + 4096 initial + 4096 boundary points) on the fused kernel.
 
 --workload poisson_2_64x3_1 --prec bf16 (or tf32) times the precision workload
 instead: 2-D Poisson a=b=2, HRKAN [2,64,64,64,1], G=32, 262144 interior +
@@ -44,7 +52,8 @@ if ROOT not in sys.path:
 
 METRIC = "PINN train throughput (colloc pts/s, fwd jets+bwd) vs plain FP32 at equal L2 err"
 UNIT = "collocation points/s"
-WORKLOAD = "burgers_2_10_10_1"
+WORKLOAD = "poisson_batch256"
+BURGERS_WORKLOAD = "burgers_2_10_10_1"
 FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -55,9 +64,11 @@ def measured_peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             m = json.load(f)
         return {"bf16": float(m["bf16_tflops"]), "bf16_sustained": float(m["bf16_tflops_sustained"]),
-                "source": "of measured (MEASURED_PEAKS.json)"}
+                "hbm": float(m["hbm_gbs"]), "source": "of measured (MEASURED_PEAKS.json)",
+                "hbm_source": "copy bandwidth of measured (MEASURED_PEAKS.json)"}
     except (OSError, KeyError, ValueError):
-        return {"bf16": 1900.0, "bf16_sustained": 1700.0, "source": "of fallback"}
+        return {"bf16": 1900.0, "bf16_sustained": 1700.0, "hbm": 6800.0, "source": "of fallback",
+                "hbm_source": "of fallback"}
 
 
 def dense_tc_flops(widths, G, k, n_int, J_int, n_bnd, bf16):
@@ -183,6 +194,50 @@ def job_throughput(ws: int, steps: int, units_per_step: int, seconds: float) -> 
 # --------------------------------------------------------------- reference
 
 
+def run_reference_batched(args, w):
+    """FP64 CPU oracle on the multi-instance workload: every step trains a bounded sample (the
+    first instances, 256 interior + 32 boundary points of each), instance by instance."""
+    import oracle
+    from paper_2409_14248_gb300 import inputs
+    d = inputs.make_batched(w)
+    P = w.n_params()
+    sample = []
+    for i in range(w.instances):
+        a0, b0 = int(d["off_int"][i]), int(d["off_bnd"][i])
+        ni = min(256, int(d["off_int"][i + 1]) - a0)
+        nb = min(32, int(d["off_bnd"][i + 1]) - b0)
+        sample.append([d["W"][i * P:(i + 1) * P].astype(np.float64), np.zeros(P), np.zeros(P),
+                       d["x_int"][:, a0:a0 + ni], d["x_bnd"][:, b0:b0 + nb], d["g_bnd"][b0:b0 + nb], d["ab"][i]])
+
+    def one(st, t):
+        Wi, m1, m2, xi, xb, gb, ab = st
+        oracle.train_step(w.net, w.problem(*ab), Wi, m1, m2, xi, w.mask_int, xb, gb, w.lr, t)
+        return xi.shape[1] + xb.shape[1]
+
+    t0 = time.perf_counter()
+    one([a.copy() if isinstance(a, np.ndarray) else a for a in sample[0]], 1)
+    per_inst = time.perf_counter() - t0
+    budget = 120.0
+    k = int(max(1, min(w.instances, budget / max(1, args.steps + args.warmup) / max(per_inst, 1e-6))))
+    for t in range(1, args.warmup + 1):
+        for st in sample[:k]:
+            one(st, t)
+    t0 = time.perf_counter()
+    pts = 0
+    for t in range(args.warmup + 1, args.warmup + args.steps + 1):
+        pts = sum(one(st, t) for st in sample[:k])
+    dt = time.perf_counter() - t0
+    value = args.steps * pts / dt
+    desc = f"the first {k} of {w.instances} instances, 256 interior + 32 boundary points of each per step"
+    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+          "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+          "config": {"workload": args.workload, "instances": w.instances, "widths": w.widths, "G": w.G, "k": w.k,
+                     "m": w.m, "impl": "FP64 CPU oracle (C, 1 thread)"},
+          "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+
+
 def run_reference(args, ws, rank):
     """FP64 CPU oracle, as it stands, on a bounded sample of the workload per step."""
     if rank != 0:
@@ -191,6 +246,9 @@ def run_reference(args, ws, rank):
     from paper_2409_14248_gb300 import inputs
     oracle.build()
     w = inputs.WORKLOADS[args.workload]
+    if w.instances > 1:
+        run_reference_batched(args, w)
+        return
     full = w.n_int + w.n_bnd + w.n_ic + w.n_bc
     # calibrate the oracle's rate, then size the sample so that the run takes ~2 minutes
     d = sample_data(inputs, w, 128, 16)
@@ -222,6 +280,75 @@ def run_reference(args, ws, rank):
                      "n_int": w.n_int, "n_bnd": w.n_bnd + w.n_ic + w.n_bc, "impl": "FP64 CPU oracle (C, 1 thread)"},
           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+
+
+# ------------------------------------------------------------ many instances
+
+KIND_NAMES = {5: "tc_fwd_kernel", 6: "tc_dw_kernel", 7: "tc_adj_kernel", 8: "wide_fwd_kernel",
+              9: "wide_dw_kernel", 10: "wide_adjoint_kernel", 3: "lb_residual_kernel", 1: "batch_reduce_kernel"}
+
+
+def layerwise_kind_work(widths, G, k, J, n_int, n_bnd, prec):
+    """Algorithmic work of one multi-instance step on the layer-wise path per kernel kind:
+    (amount, unit) with unit "flop" (dense contraction flops for the tensor-core kinds, every K
+    column counted; sparse flops of the k+1 active bases for the FP32 kinds) or "byte".
+    Interior points carry J jet rows, boundary points one."""
+    n, kp = G + k, k + 1
+    L = len(widths) - 1
+    rows = J * n_int + n_bnd
+    pts = n_int + n_bnd
+    tc_ok = lambda l: prec != 0 and 0 < l < L - 1 and 16 <= widths[l + 1] <= 64 and widths[l + 1] % 16 == 0
+    tc_dw_ok = lambda l: prec == 1 and (tc_ok(l) or (l == 0 and 16 <= widths[1] <= 64 and widths[1] % 16 == 0))
+    w = {5: 0, 6: 0, 7: 0, 8: 0, 9: 0, 10: 0}
+    for l in range(L):
+        I, O = widths[l], widths[l + 1]
+        if tc_ok(l):
+            w[5] += 2 * rows * I * n * O
+        else:
+            w[8] += 2 * kp * I * O * rows + 20 * kp * I * pts
+        if tc_dw_ok(l):
+            w[6] += 2 * rows * I * n * O
+        else:
+            w[9] += 2 * kp * I * O * rows + 20 * kp * I * pts
+        if l > 0:
+            if tc_ok(l) and prec == 1:
+                w[7] += 2 * J * n_int * I * n * O
+                w[10] += 2 * kp * I * O * n_bnd + 25 * kp * I * n_bnd
+            else:
+                w[10] += 2 * kp * I * O * rows + 25 * kp * I * pts
+    out = {c: (v, "flop") for c, v in w.items()}
+    # residual: coordinates, jets in, jet gradients out; boundary value, target, gradient
+    out[3] = ((2 + 2 * J) * 4 * n_int + 3 * 4 * n_bnd, "byte")
+    return out
+
+
+def batched_points(d):
+    return int(d["off_int"][-1]), int(d["off_bnd"][-1])
+
+
+def cpu_baseline_batched(w, d):
+    """The FP64 oracle on the host, instance by instance: one training step on a sample of each
+    of the first instances until ~15 s of CPU work (the same points and weights)."""
+    import oracle
+    oracle.build()
+    P = w.n_params()
+    done_pts, t_cpu, used = 0, 0.0, 0
+    per_inst = 256    # interior points of each instance in the sample (boundary: per_inst // 8)
+    while t_cpu < 15.0 and used < w.instances:
+        i = used
+        a0, a1 = int(d["off_int"][i]), int(d["off_int"][i + 1])
+        b0, b1 = int(d["off_bnd"][i]), int(d["off_bnd"][i + 1])
+        ni, nb = min(per_inst, a1 - a0), min(per_inst // 8, b1 - b0)
+        Wi = d["W"][i * P:(i + 1) * P].astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.train_step(w.net, w.problem(*d["ab"][i]), Wi, np.zeros(P), np.zeros(P), d["x_int"][:, a0:a0 + ni],
+                          w.mask_int, d["x_bnd"][:, b0:b0 + nb], d["g_bnd"][b0:b0 + nb], w.lr, 1)
+        t_cpu += time.perf_counter() - t0
+        done_pts += ni + nb
+        used += 1
+    return {"value": done_pts / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one training step on each of the first {used} instances, {per_inst} interior + "
+                      f"{per_inst // 8} boundary points of each (their own points and weights), FP64, 1 thread"}
 
 
 # --------------------------------------------------------------------- ours
@@ -410,7 +537,7 @@ def run_ours(args, ws, rank, local):
                 kms = total_ms / args.steps
             # DRAM bytes of one launch of the fused kernel from one ncu capture of this workload
             # (its inputs and weights only); unknown for the other shapes
-            traffic = 801365 if fused and args.workload == WORKLOAD else None
+            traffic = 801365 if fused and args.workload == BURGERS_WORKLOAD else None
             roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": kernel, "kernel_ms": kms,
                         "reduce_adam_ms": red_ms / max(1, red_n),
@@ -452,20 +579,226 @@ def run_ours(args, ws, rank, local):
         torch.distributed.destroy_process_group()
 
 
+def equal_l2_check(torch, capi, inputs, w, prec, n_inst=8, steps=1000):
+    """Both paths trained `steps` Adam steps from the workload's initial weights on its first
+    n_inst instances; mean relative L2 error of u on a 100 x 100 grid against the exact
+    solution, both evaluated by the FP32 path."""
+    d = inputs.make_batched(w, instances=n_inst)
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    probs = [capi.make_problem(w.pde, a, b, w.lam, w.nu, w.alpha) for a, b in d["ab"]]
+    xi, xb, gb = dev(d["x_int"]), dev(d["x_bnd"]), dev(d["g_bnd"])
+    g = np.linspace(w.lo, w.hi, 100)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    grid = np.stack([X.ravel(), Y.ravel()]).astype(np.float32)
+    xg = dev(np.tile(grid, (1, n_inst)))
+    offg = np.arange(n_inst + 1) * grid.shape[1]
+    h32 = capi.hrkan_init(capi.make_cfg(w.widths, w.G, w.k, w.m, w.lo, w.hi, n_instances=n_inst))
+    out = {}
+    try:
+        for p in (PRECS["fp32"], prec):
+            h = h32 if p == PRECS["fp32"] else capi.hrkan_init(
+                capi.make_cfg(w.widths, w.G, w.k, w.m, w.lo, w.hi, prec=p, n_instances=n_inst,
+                              flags=capi.HRKAN_FLAG_LAYERWISE))
+            try:
+                W = dev(d["W"])
+                loss = torch.zeros((n_inst, 3), dtype=torch.float64, device="cuda")
+                for t in range(1, steps + 1):
+                    capi.hrkan_train_step_batched(h, probs, W, xi, d["off_int"], xb, gb, d["off_bnd"], w.lr, 0.9,
+                                                  0.999, 1e-8, t, loss)
+                u = torch.zeros((1, xg.shape[1]), device="cuda")
+                capi.hrkan_forward_jets_batched(h32, W, xg, offg, 0x01, u)
+                u = u.cpu().numpy()[0].astype(np.float64)
+                errs = []
+                for i, (a, b) in enumerate(d["ab"]):
+                    want = np.sin(a * np.pi * X.ravel()) * np.sin(b * np.pi * Y.ravel())
+                    errs.append(np.linalg.norm(u[offg[i]:offg[i + 1]] - want) / np.linalg.norm(want))
+                out[p] = float(np.mean(errs))
+            finally:
+                if h is not h32:
+                    capi.hrkan_destroy(h)
+    finally:
+        capi.hrkan_destroy(h32)
+    return {"instances": n_inst, "steps": steps, "lr": w.lr, "rel_l2_fp32": out[PRECS["fp32"]],
+            "rel_l2_reduced": out[prec], "ratio": out[prec] / out[PRECS["fp32"]], "bar": 1.2,
+            "grid": "100 x 100 on [-1, 1]^2, u evaluated by the FP32 path"}
+
+
+def run_batched(args, ws, rank, local):
+    import torch
+    from paper_2409_14248_gb300 import build as pbuild
+    from paper_2409_14248_gb300 import capi, inputs
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(capi.LIB_PATH):
+        pbuild.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    capi.load_library()
+
+    w = inputs.WORKLOADS[args.workload]
+    prec = PRECS[args.prec]
+    d = inputs.make_batched(w)
+    I, P = w.instances, w.n_params()
+    Ni, Nb = batched_points(d)
+    pts = Ni + Nb
+    J = bin(w.mask_int & 0x1F).count("1")
+    probs = [capi.make_problem(w.pde, a, b, w.lam, w.nu, w.alpha) for a, b in d["ab"]]
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    W0 = dev(d["W"])
+    xi, xb, gb = dev(d["x_int"]), dev(d["x_bnd"]), dev(d["g_bnd"])
+    loss = torch.zeros((I, 3), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    b1, b2, eps = 0.9, 0.999, 1e-8
+
+    def make(p):
+        flags = 0 if p == PRECS["fp32"] else capi.HRKAN_FLAG_LAYERWISE
+        return capi.hrkan_init(capi.make_cfg(w.widths, w.G, w.k, w.m, w.lo, w.hi, prec=p, n_instances=I,
+                                             flags=flags))
+
+    def make_step(h, W):
+        return lambda t: capi.hrkan_train_step_batched(h, probs, W, xi, d["off_int"], xb, gb, d["off_bnd"], w.lr, b1,
+                                                       b2, eps, t, loss)
+
+    h = make(prec)
+    W = W0.clone()
+    step = make_step(h, W)
+    for t in range(1, args.warmup + 1):
+        flush.fill_(0.0)
+        step(t)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    total_ms = time_steps(torch, capi, h, step, args.warmup + 1, args.steps, flush)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = max_over_ranks(total_ms, ws, "cuda")
+
+    # per-kernel times: CUDA events the library records around each launch, over a few more
+    # steps of the same workload (kept out of the timed region above)
+    prof_steps = min(args.steps, 10)
+    capi.hrkan_profile_enable(h, True)
+    for c in range(capi.HRKAN_KERNEL_CLASSES):
+        capi.hrkan_profile_read(h, c, reset=True)
+    time_steps(torch, capi, h, step, args.warmup + args.steps + 1, prof_steps, flush)
+    capi.hrkan_profile_enable(h, False)
+    prof = {c: capi.hrkan_profile_read(h, c) for c in range(capi.HRKAN_KERNEL_CLASSES)}
+
+    # end to end through the C ABI with host buffers: H2D of the points, the step, D2H of the losses
+    pin = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32).pin_memory()
+    hxi, hxb, hgb = pin(d["x_int"]), pin(d["x_bnd"]), pin(d["g_bnd"])
+    hloss = torch.zeros((I, 3), dtype=torch.float64).pin_memory()
+    e2e_steps = min(args.steps, 50)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        xi.copy_(hxi, non_blocking=True)
+        xb.copy_(hxb, non_blocking=True)
+        gb.copy_(hgb, non_blocking=True)
+        step(args.warmup + args.steps + prof_steps + 1 + i)
+        hloss.copy_(loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws, "cuda")
+    h2d = (hxi.numel() + hxb.numel() + hgb.numel()) * 4
+    capi.hrkan_destroy(h)
+
+    # the plain FP32 path (the fused multi-instance kernel) of the same workload
+    fp32_path = None
+    if prec != PRECS["fp32"]:
+        h32 = make(PRECS["fp32"])
+        W32 = W0.clone()
+        step32 = make_step(h32, W32)
+        for t in range(1, 4):
+            step32(t)
+        torch.cuda.synchronize()
+        k32 = max(3, min(args.steps, 20))
+        ms32 = max_over_ranks(time_steps(torch, capi, h32, step32, 4, k32, flush), ws, "cuda")
+        capi.hrkan_destroy(h32)
+        fp32_path = {"value": job_throughput(ws, k32, pts, ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32 / k32,
+                     "steps": k32, "kernel": "narrow_batch_kernel (fused FP32 multi-instance step)"}
+
+    if rank == 0:
+        work = layerwise_kind_work(w.widths, w.G, w.k, J, Ni, Nb, prec)
+        kinds = [c for c in work if prof[c][1] > 0]
+        dom = max(kinds, key=lambda c: prof[c][0]) if kinds else None
+        pk = measured_peaks()
+        per_kind = {KIND_NAMES[c]: {"ms_per_step": prof[c][0] / prof_steps, "launches_per_step": prof[c][1] / prof_steps}
+                    for c in kinds}
+        roofline = None
+        if dom is not None:
+            amount, unit = work[dom]
+            secs = prof[dom][0] / prof_steps / 1e3
+            if unit == "byte":
+                achieved, peak, bound, u, src = amount / secs / 1e9, pk["hbm"], "hbm", "GB/s", pk["hbm_source"]
+            elif dom in (5, 6, 7):
+                achieved = amount / secs / 1e12
+                peak = pk["bf16_sustained"] * (1.0 if prec == PRECS["bf16"] else 0.5)
+                bound, u, src = "tensor", "TFLOP/s", "bf16 dense sustained " + pk["source"]
+            else:
+                achieved, peak, bound, u = amount / secs / 1e12, FP32_PEAK_TFLOPS, "alu", "TFLOP/s"
+                src = FP32_PEAK_NOTE + " (derived, FP32 FMA pipe)"
+            roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": u, "frac": achieved / peak,
+                        "traffic": None, "kernel": KIND_NAMES[dom], "kernel_ms_per_step": secs * 1e3,
+                        "launches_per_step": prof[dom][1] / prof_steps, "work_per_step": amount,
+                        "work_unit": unit, "peak_source": src, "per_kind": per_kind}
+        launches = (sum(prof[c][1] for c in (0, 1, 2, 3, 4)) / prof_steps + 3) * args.steps   # + 3 point gathers
+        out = {"metric": METRIC, "value": job_throughput(ws, args.steps, pts, total_ms / 1e3), "unit": UNIT,
+               "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
+               "data": "synthetic",
+               "config": {"workload": args.workload, "instances": I, "widths": w.widths, "G": w.G, "k": w.k,
+                          "m": w.m, "n_int": Ni, "n_bnd": Nb, "precision": args.prec,
+                          "parallelism": "replicas" if ws > 1 else "single",
+                          "l2": "flushed before every timed step (256 MiB device write, outside the step events)"},
+               "roofline": roofline, "gpu_launches": int(round(launches)), "clocks": clocks,
+               "e2e": {"value": job_throughput(ws, e2e_steps, pts, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": I * 3 * 8}}
+        if fp32_path is not None:
+            out["fp32_path"] = fp32_path
+            if not args.no_equal_l2:
+                out["equal_l2"] = equal_l2_check(torch, capi, inputs, w, prec)
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_batched(w, d)
+        emit(out)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=None, help="default: 200 for poisson_batch256, else 2000")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, help="burgers_2_10_10_1 (default) or poisson_2_64x3_1")
-    ap.add_argument("--prec", default="fp32", choices=sorted(PRECS))
+    ap.add_argument("--no-equal-l2", action="store_true", help="skip the 1000-step equal-L2 training check")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="poisson_batch256 (default), burgers_2_10_10_1, poisson_2_64x3_1, burgers_2_32_32_1, "
+                         "poisson_2_5_1")
+    ap.add_argument("--prec", default=None, choices=sorted(PRECS),
+                    help="default: bf16 for poisson_batch256, fp32 otherwise")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.prec is None:
+        args.prec = "bf16" if args.workload == WORKLOAD else "fp32"
+    if args.steps is None:
+        args.steps = 200 if args.workload == WORKLOAD else 2000
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    from paper_2409_14248_gb300 import inputs
+    if inputs.WORKLOADS[args.workload].instances > 1:
+        run_batched(args, ws, rank, local)
         return
     run_ours(args, ws, rank, local)
 

@@ -394,7 +394,15 @@ enum hrkan_kernel_class {
     HRKAN_KERNEL_FORWARD = 2,   /* forward jets */
     HRKAN_KERNEL_RESIDUAL = 3,  /* stand-alone residual */
     HRKAN_KERNEL_TENSOR = 4,    /* tcgen05 jet contraction of a hidden layer (BF16 / TF32) */
-    HRKAN_KERNEL_CLASSES = 5
+    /* Finer kinds of the layer-wise path, each launch also counted in one class above:
+     * a tensor-core call includes its operand conversion kernel. */
+    HRKAN_KERNEL_TC_FWD = 5,    /* tensor-core forward of a layer (tc_fwd_kernel) */
+    HRKAN_KERNEL_TC_DW = 6,     /* tensor-core weight gradient of a layer (tc_dw_kernel) */
+    HRKAN_KERNEL_TC_ADJ = 7,    /* tensor-core input adjoint of a layer (tc_adj_kernel) */
+    HRKAN_KERNEL_LAYER_FWD = 8, /* FP32 layer forward (wide_fwd_kernel) */
+    HRKAN_KERNEL_LAYER_DW = 9,  /* FP32 layer weight gradient (wide_dw_kernel) */
+    HRKAN_KERNEL_LAYER_ADJ = 10, /* FP32 layer input adjoint (wide_adjoint_kernel) */
+    HRKAN_KERNEL_CLASSES = 11
 };
 int hrkan_profile_enable(hrkan_t h, int enable);
 int hrkan_profile_read(hrkan_t h, int kernel_class, double* total_ms, int64_t* launches, int reset);

@@ -30,6 +30,9 @@ EXPORTS = ("hrkan_param_count", "hrkan_init", "hrkan_destroy", "hrkan_last_error
            "hrkan_layer_jets", "hrkan_layer_dw", "hrkan_layer_adjoint", "hrkan_autotune_batch",
            "hrkan_checkpoint_write", "hrkan_checkpoint_read", "hrkan_save", "hrkan_load", "hrkan_set_wait_cycles")
 HRKAN_KERNEL_FUSED, HRKAN_KERNEL_REDUCE, HRKAN_KERNEL_FORWARD, HRKAN_KERNEL_RESIDUAL, HRKAN_KERNEL_TENSOR = 0, 1, 2, 3, 4
+HRKAN_KERNEL_TC_FWD, HRKAN_KERNEL_TC_DW, HRKAN_KERNEL_TC_ADJ = 5, 6, 7
+HRKAN_KERNEL_LAYER_FWD, HRKAN_KERNEL_LAYER_DW, HRKAN_KERNEL_LAYER_ADJ = 8, 9, 10
+HRKAN_KERNEL_CLASSES = 11
 
 
 class HRKANError(RuntimeError):

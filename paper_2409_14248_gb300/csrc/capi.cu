@@ -377,12 +377,17 @@ int forward_layer(hrkan_t h, const float* W, int l, const float* in, float* out,
         cudaError_t e;
         {
             ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
+            ProfScope pk(h, HRKAN_KERNEL_TC_FWD, s);
             e = tc_forward_layer(p.W, wp, in, out, p.I, p.O, N, h->grid, h->cfg.prec, mask, h->status, s);
         }
         if (e != cudaSuccess) return cuda_fail(e, "tensor-core layer launch");
         return HRKAN_OK;
     }
-    cudaError_t e = wide_forward_layer(p, mask, l == 0, s);
+    cudaError_t e;
+    {
+        ProfScope pk(h, HRKAN_KERNEL_LAYER_FWD, s);
+        e = wide_forward_layer(p, mask, l == 0, s);
+    }
     if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no layer kernel", mask);
     if (e != cudaSuccess) return cuda_fail(e, "layer forward launch");
     return HRKAN_OK;
@@ -420,10 +425,12 @@ int layer_dw(hrkan_t h, const WideDw& d, int l, unsigned mask, cudaStream_t s) {
         float* gbf = ws_get(h, 11, size_t((el + 1) / 2), &rc);   // 2-byte elements in 4-byte slots
         if (!gbf) return rc;
         ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
+        ProfScope pk(h, HRKAN_KERNEL_TC_DW, s);
         e = tc_dw_layer(d.z, d.gy, gbf, d.I, d.O, d.N, d.g, mask, l == 0, d.partial, d.P, d.col0, d.row0, d.GP,
                         h->status, s);
     } else {
         ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
+        ProfScope pk(h, HRKAN_KERNEL_LAYER_DW, s);
         e = wide_dw_layer(d, mask, l == 0, s);
     }
     if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no layer kernel", mask);
@@ -486,8 +493,10 @@ int wide_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsi
                 float* wbf = gbf ? ws_get(h, 12, size_t((tc_adj_w_elems(a.O, a.I, h->n) + 1) / 2), &rc) : nullptr;
                 if (!wbf) return rc;
                 ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
+                ProfScope pk(h, HRKAN_KERNEL_TC_ADJ, s);
                 e = tc_adj_layer(a.W, wbf, gbf, zl, gz, a.I, a.O, N, h->grid, mask, h->status, s);
             } else {
+                ProfScope pk(h, HRKAN_KERNEL_LAYER_ADJ, s);
                 e = wide_adjoint_layer(a, mask, s);
             }
             if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
@@ -761,6 +770,7 @@ int lb_forward_layer(hrkan_t h, const float* W, int l, const float* in, float* o
         cudaError_t e;
         {
             ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
+            ProfScope pk(h, HRKAN_KERNEL_TC_FWD, s);
             e = tc_forward_layer(p.W, wp, in, out, p.I, p.O, N, h->grid, h->cfg.prec, mask, h->status, s, n_inst,
                                  h->P, blk_inst);
         }
@@ -770,6 +780,7 @@ int lb_forward_layer(hrkan_t h, const float* W, int l, const float* in, float* o
     cudaError_t e;
     {
         ProfScope ps(h, HRKAN_KERNEL_FORWARD, s);
+        ProfScope pk(h, HRKAN_KERNEL_LAYER_FWD, s);
         e = wide_forward_layer(p, mask, l == 0, s);
     }
     if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no layer kernel", mask);
@@ -830,10 +841,12 @@ int lb_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsign
             float* gbf = ws_get(h, 21, size_t((el + 1) / 2), &rc);
             if (!gbf) return rc;
             ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
+            ProfScope pk(h, HRKAN_KERNEL_TC_DW, s);
             e = tc_dw_layer(d.z, d.gy, gbf, d.I, d.O, N, d.g, mask, l == 0, partial, h->P, d.col0, 0, nchunk,
                             h->status, s, chunks);
         } else {
             ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
+            ProfScope pk(h, HRKAN_KERNEL_LAYER_DW, s);
             e = wide_dw_layer(d, mask, l == 0, s);
         }
         if (e == cudaErrorNotSupported) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x has no layer kernel", mask);
@@ -854,10 +867,12 @@ int lb_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsign
                     gbf ? ws_get(h, 22, size_t((tc_adj_w_elems(a.O, a.I, h->n) * n_inst + 1) / 2), &rc) : nullptr;
                 if (!wbf) return rc;
                 ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
+                ProfScope pk(h, HRKAN_KERNEL_TC_ADJ, s);
                 e = tc_adj_layer(a.W, wbf, gbf, zl, gz, a.I, a.O, N, h->grid, mask, h->status, s, n_inst, h->P, chunks,
                                  nchunk);
             } else {
                 ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
+                ProfScope pk(h, HRKAN_KERNEL_LAYER_ADJ, s);
                 e = wide_adjoint_layer(a, mask, s);
             }
             if (e != cudaSuccess) return cuda_fail(e, "adjoint launch (batched)");
