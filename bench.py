@@ -284,6 +284,7 @@ def run_reference(args, ws, rank):
 
 # ------------------------------------------------------------ many instances
 
+LB_CHUNK_CANDIDATES = (1024, 2048, 4096, 8192, 16384)
 KIND_NAMES = {5: "tc_fwd_kernel", 6: "tc_dw_kernel", 7: "tc_adj_kernel", 8: "wide_fwd_kernel",
               9: "wide_dw_kernel", 10: "wide_adjoint_kernel", 3: "lb_residual_kernel", 1: "batch_reduce_kernel"}
 
@@ -662,8 +663,16 @@ def run_batched(args, ws, rank, local):
         return lambda t: capi.hrkan_train_step_batched(h, probs, W, xi, d["off_int"], xb, gb, d["off_bnd"], w.lr, b1,
                                                        b2, eps, t, loss)
 
+    def tune(h, W, p):
+        # the layer-wise path tunes its weight-gradient chunk, the fused path its work item
+        cands = LB_CHUNK_CANDIDATES if p != PRECS["fp32"] else None
+        chosen, ms = capi.hrkan_autotune_batch(h, probs, W, xi, d["off_int"], xb, gb, d["off_bnd"], candidates=cands)
+        return {"points": chosen, "ms_per_step": ms, "knob": "weight-gradient chunk (points)"
+                if p != PRECS["fp32"] else "work item (points)"}
+
     h = make(prec)
     W = W0.clone()
+    tuned = tune(h, W, prec)
     step = make_step(h, W)
     for t in range(1, args.warmup + 1):
         flush.fill_(0.0)
@@ -715,6 +724,7 @@ def run_batched(args, ws, rank, local):
     if prec != PRECS["fp32"]:
         h32 = make(PRECS["fp32"])
         W32 = W0.clone()
+        tuned32 = tune(h32, W32, PRECS["fp32"])
         step32 = make_step(h32, W32)
         for t in range(1, 4):
             step32(t)
@@ -723,7 +733,8 @@ def run_batched(args, ws, rank, local):
         ms32 = max_over_ranks(time_steps(torch, capi, h32, step32, 4, k32, flush), ws, "cuda")
         capi.hrkan_destroy(h32)
         fp32_path = {"value": job_throughput(ws, k32, pts, ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32 / k32,
-                     "steps": k32, "kernel": "narrow_batch_kernel (fused FP32 multi-instance step)"}
+                     "steps": k32, "kernel": "narrow_batch_kernel (fused FP32 multi-instance step)",
+                     "autotune": tuned32}
 
     if rank == 0:
         work = layerwise_kind_work(w.widths, w.G, w.k, J, Ni, Nb, prec)
@@ -758,7 +769,7 @@ def run_batched(args, ws, rank, local):
                           "m": w.m, "n_int": Ni, "n_bnd": Nb, "precision": args.prec,
                           "parallelism": "replicas" if ws > 1 else "single",
                           "l2": "flushed before every timed step (256 MiB device write, outside the step events)"},
-               "roofline": roofline, "gpu_launches": int(round(launches)), "clocks": clocks,
+               "roofline": roofline, "gpu_launches": int(round(launches)), "clocks": clocks, "autotune": tuned,
                "e2e": {"value": job_throughput(ws, e2e_steps, pts, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": I * 3 * 8}}
         if fp32_path is not None:

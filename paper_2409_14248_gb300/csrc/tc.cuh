@@ -15,6 +15,8 @@ namespace hrkan {
 // a_hi w_hi + a_lo w_hi + a_hi w_lo (the a_lo w_lo term dropped), with FP32
 // accumulation.  The values of this enum continue hrkan_prec's.
 constexpr int TC_BF16X3 = 3;
+// W tiles (128-byte rows, TERMS tiles of O rows each) the forward kernel keeps in flight.
+constexpr int TC_W_BUFFERS = 8;
 
 struct TcLayer {
     const float* z;   // input jets [J][I][N]
@@ -31,6 +33,8 @@ struct TcLayer {
     // blk_inst[t / 2] (point blocks of 256), whose W tiles start at row
     // blk_inst[t / 2] * TERMS * O of the tensor map; nullptr: one instance
     const int* blk_inst = nullptr;
+    // TMEM columns each CTA allocates (512, or 256 when two CTAs share an SM)
+    uint32_t tmem_cols = 512;
 };
 
 // Layers the tensor-core kernel handles: 16 <= O <= 64, O % 16 == 0,

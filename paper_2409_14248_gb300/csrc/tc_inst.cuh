@@ -14,9 +14,12 @@ namespace tck {
 
 template <unsigned MASK, int PREC, int NP>
 cudaError_t launch_one(const TcLayer& p, const CUtensorMap& map, cudaStream_t s) {
-    // NB W buffers (TERMS tiles of O rows each) + alignment slack; at least
-    // 120 KB so that one CTA holds an SM (each CTA allocates all 512 TMEM columns)
-    const size_t want = std::max<size_t>(size_t(NB) * Elem<PREC>::TERMS * p.O * 128 + 1024, 120 * 1024);
+    // NB W buffers (TERMS tiles of O rows each) + alignment slack.  A CTA that
+    // allocates all 512 TMEM columns asks for at least 120 KB so that it holds
+    // an SM alone; with 256 columns two CTAs share an SM
+    const size_t wbytes = size_t(NB) * Elem<PREC>::TERMS * p.O * 128 + 1024;
+    const size_t want = p.tmem_cols >= 512 ? std::max<size_t>(wbytes, 120 * 1024) : wbytes;
+    const int per_sm = p.tmem_cols >= 512 ? 1 : 2;   // the host picks 256 columns only when two fit
     auto kern = tc_fwd_kernel<MASK, PREC, NP>;
     static std::mutex mu;
     static std::unordered_map<const void*, size_t> set;
@@ -32,7 +35,7 @@ cudaError_t launch_one(const TcLayer& p, const CUtensorMap& map, cudaStream_t s)
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const unsigned grid = unsigned(std::max(1, std::min(p.ntiles, nsm)));
+    const unsigned grid = unsigned(std::max(1, std::min(p.ntiles, per_sm * nsm)));
     kern<<<grid, THREADS, want, s>>>(p, map);
     return cudaGetLastError();
 }

@@ -36,8 +36,17 @@ int slot_elems(int) { return 8; }
 int box_elems(int) { return 32; }
 // Weight tiles of O rows per W buffer: (w_hi, w_hi) and (w_lo, 0) for BF16.
 int w_terms(int prec) { return prec == HRKAN_BF16 ? 2 : 1; }
-// A ring slots left in TMEM after the J * O accumulator columns (8 columns per slot and jet row).
-int ring_slots(int J, int O) { return std::min(RING_MAX, (TMEM_COLS - J * O) / (8 * J)); }
+// A ring slots left in `cols` TMEM columns after the J * O accumulator columns
+// (8 columns per slot and jet row).
+int ring_slots(int J, int O, int cols = TMEM_COLS) { return std::min(RING_MAX, (cols - J * O) / (8 * J)); }
+// Small layers (J * O + 4 ring slots within 256 columns) allocate half of TMEM
+// so that two CTAs share an SM: twice the producer warps per SM to hide the
+// latency of the per-slot hand-offs, and one CTA's tile boundary (the drain of
+// the MMA pipe before its epilogue) overlaps the other's work.
+int tmem_cols_for(int J, int O, int prec) {
+    const size_t wbytes = size_t(TC_W_BUFFERS) * w_terms(prec) * O * 128 + 1024;   // shared memory of one CTA
+    return ring_slots(J, O, 256) >= 4 && 2 * wbytes <= 200 * 1024 ? 256 : TMEM_COLS;
+}
 
 // W [O][I][n] float32 -> 32-bit words [TERMS][O][Kt]: word k = j * NP + pos
 // holds W[o][j][i], i = 4 * (pos mod NP/4) + pos / (NP/4) (the bases of a unit
@@ -159,7 +168,8 @@ cudaError_t tc_forward_layer(const float* W, void* w_prep, const float* z, float
     p.N = N;
     p.ks = L.ks;
     p.nbox = L.nbox;
-    p.ring = ring_slots(J, O);
+    p.tmem_cols = uint32_t(tmem_cols_for(J, O, prec));
+    p.ring = ring_slots(J, O, int(p.tmem_cols));
     p.ntiles = int((N + 127) / 128);
     p.g = g;
     p.status = status;

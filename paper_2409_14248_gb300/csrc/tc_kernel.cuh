@@ -41,8 +41,7 @@ namespace hrkan {
 namespace tck {
 
 constexpr int TILE_M = 128;
-constexpr int TMEM_COLS = 512;
-constexpr int NB = 8;            // W tiles (4 slots each) in flight
+constexpr int NB = TC_W_BUFFERS;  // W tiles (4 slots each) in flight
 constexpr int RS_MAX = 8;        // A ring slots
 constexpr int PARTS = 1;                  // producer warps per TMEM lane quarter
 constexpr int PRODUCER_WARPS = 4 * PARTS;
@@ -526,7 +525,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_fwd_kernel(TcLayer p, const __g
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
-                     "r"(TMEM_COLS)
+                     "r"(p.tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -614,7 +613,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_fwd_kernel(TcLayer p, const __g
     __syncthreads();
     if (tid == 0 && *abort) atomicExch(p.status, ERR_TIMEOUT);
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(p.tmem_cols) : "memory");
 }
 
 // Host side: launch one instantiation (tc_np*.cu).

@@ -245,3 +245,31 @@ def test_bf16_batched_training_reaches_fp32_l2_error():
           f"\nrel-L2 BF16 {e16} mean {e16.mean():.4f} ratio {e16.mean() / e32.mean():.3f}")
     assert np.all(np.isfinite(e16)) and np.all(np.isfinite(e32))
     assert e16.mean() <= 1.2 * e32.mean()
+
+
+def test_layerwise_batched_autotune_picks_a_chunk_and_trains_like_untuned():
+    """hrkan_autotune_batch on the layer-wise BF16 path times the candidate weight-gradient chunk
+    sizes (lr = 0), keeps one of them and resets the Adam state: the tuned handle's first step
+    then equals an untuned handle's with that chunk size set by hand."""
+    cands = [256, 1024, 4096]
+    d, I, h, probs = _setup(capi.HRKAN_BF16, items=1024)
+    try:
+        W = _dev(d["W"])
+        chosen, ms = capi.hrkan_autotune_batch(h, probs, W, _dev(d["x_int"]), d["off_int"], _dev(d["x_bnd"]),
+                                               _dev(d["g_bnd"]), d["off_bnd"], candidates=cands, reps=2)
+        assert chosen in cands and ms > 0
+        np.testing.assert_array_equal(W.cpu().numpy(), d["W"])      # lr = 0 left W as it was
+        loss = torch.zeros((I, 3), dtype=torch.float64, device="cuda")
+        _step(h, probs, d, W, 1, loss)
+        tuned = (W.cpu().numpy(), loss.cpu().numpy())
+    finally:
+        capi.hrkan_destroy(h)
+    d, I, h, probs = _setup(capi.HRKAN_BF16, items=chosen)
+    try:
+        W = _dev(d["W"])
+        loss = torch.zeros((I, 3), dtype=torch.float64, device="cuda")
+        _step(h, probs, d, W, 1, loss)
+        np.testing.assert_array_equal(tuned[0], W.cpu().numpy())
+        np.testing.assert_array_equal(tuned[1], loss.cpu().numpy())
+    finally:
+        capi.hrkan_destroy(h)
