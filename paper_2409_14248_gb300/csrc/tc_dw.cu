@@ -46,7 +46,7 @@ using tck::tc_fence_before;
 using tck::tmem_ld16;
 
 constexpr int GROUP = 64;        // points per group (the gy tile's 128 bytes)
-constexpr int NSB = 8;           // ring buffers (one per group and jet row)
+constexpr int NSB = 8;           // most ring buffers (one per group and jet row); p.nsb of them are used
 constexpr int A_BYTES = 128 * GROUP * 2;   // 128 k x 64 points BF16
 constexpr int THREADS = 192;
 
@@ -66,6 +66,8 @@ struct DwParams {
     // chunks[c].y) (multiples of 256) and writes partial row chunks[c].z;
     // nullptr: the groups split evenly, chunk c into row row0 + c
     const int4* chunks = nullptr;
+    // ring buffers in use, J <= nsb <= NSB (a group takes J of them at once)
+    int nsb = NSB;
 };
 
 // Byte offset of element (m = k within the K-range, p = point within the group)
@@ -113,6 +115,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
     const uint32_t buf_bytes = uint32_t(A_BYTES) + b_bytes;
     const int kr = blockIdx.x % p.nkr, chunk = blockIdx.x / p.nkr;
     const int k0 = kr * 128;
+    const int nsb = p.nsb;
     const int g0 = p.chunks ? p.chunks[chunk].x / GROUP : int(int64_t(chunk) * p.ngroups / p.nchunk);
     const int g1 = p.chunks ? p.chunks[chunk].y / GROUP : int(int64_t(chunk + 1) * p.ngroups / p.nchunk);
     const int out_row = p.chunks ? p.chunks[chunk].z : p.row0 + chunk;
@@ -185,8 +188,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
             bool ok = true;
 #pragma unroll
             for (int r = 0; r < J; ++r) {
-                const int b = (q + r) % NSB;
-                const uint32_t ph = uint32_t((q + r) / NSB) & 1u;
+                const int b = (q + r) % nsb;
+                const uint32_t ph = uint32_t((q + r) / nsb) & 1u;
                 ok = ok && mbar_wait(&bar_empty[b], ph ^ 1u, abort, wl);
             }
             if (!__all_sync(0xffffffffu, ok)) goto done;
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
                                     const int lw = 4 * ci + e, qr = lw / QW, qo = lw % QW;
                                     v[e] = w.tw[qr] == qo ? w.y[r][qr] : 0u;
                                 }
-                                const int b = (q + r) % NSB;
+                                const int b = (q + r) % nsb;
                                 st_shared_v4(smem_u32(smem + size_t(b) * buf_bytes) + off, v[0], v[1], v[2], v[3]);
                             }
                         }
@@ -222,13 +225,13 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
                     if (m < 0) continue;
 #pragma unroll
                     for (int r = 0; r < J; ++r)
-                        st_shared_v4(smem_u32(smem + size_t((q + r) % NSB) * buf_bytes) + a_off(m, pp), 0u, 0u, 0u, 0u);
+                        st_shared_v4(smem_u32(smem + size_t((q + r) % nsb) * buf_bytes) + a_off(m, pp), 0u, 0u, 0u, 0u);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
 #pragma unroll
-            for (int r = 0; r < J; ++r) mbar_arrive_if(&bar_full[(q + r) % NSB], lane == 0);
+            for (int r = 0; r < J; ++r) mbar_arrive_if(&bar_full[(q + r) % nsb], lane == 0);
             q += J;
         }
         // ---- epilogue: D (lanes = k of the range) -> partial row
@@ -267,8 +270,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
             bool issued = false;
             const int total = ng * J;
             for (int q = 0; q < total; ++q) {
-                const int b = q % NSB;
-                if (!mbar_wait(&bar_full[b], uint32_t(q / NSB) & 1u, abort, wl)) break;
+                const int b = q % nsb;
+                if (!mbar_wait(&bar_full[b], uint32_t(q / nsb) & 1u, abort, wl)) break;
                 tc_fence_after();
                 const uint32_t abase = smem_u32(smem + size_t(b) * buf_bytes);
                 const uint64_t bd = sdesc(abase + A_BYTES, 16, 1024);
@@ -297,8 +300,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
             const int total = ng * J;
             uint32_t used = 0u, last_par = 0u;
             for (int q = 0; q < total; ++q) {
-                const int b = q % NSB, gi = q / J, r = q % J;
-                const uint32_t ph = uint32_t(q / NSB) & 1u;
+                const int b = q % nsb, gi = q / J, r = q % J;
+                const uint32_t ph = uint32_t(q / nsb) & 1u;
                 if (!mbar_wait(&bar_empty[b], ph ^ 1u, abort, wl)) break;
                 mbar_expect_tx(&bar_full[b], b_bytes);
                 tck::tma_load_2d(smem + size_t(b) * buf_bytes + A_BYTES, &gmap, &bar_full[b], (g0 + gi) * GROUP,
@@ -307,7 +310,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
                 last_par = (last_par & ~(1u << b)) | (ph << b);
             }
             if (*abort)
-                for (int b = 0; b < NSB; ++b)
+                for (int b = 0; b < nsb; ++b)
                     if ((used >> b) & 1u) mbar_drain(&bar_full[b], (last_par >> b) & 1u);
         }
     }
@@ -365,7 +368,7 @@ int np8_of(int n) { return std::max(16, (n + 7) / 8 * 8); }
 
 template <unsigned MASK, int NC, bool FIRST>
 cudaError_t launch(const DwParams& p, const CUtensorMap& map, unsigned grid, cudaStream_t s) {
-    const size_t smem = size_t(NSB) * (A_BYTES + size_t(p.O) * 128) + 1024;
+    const size_t smem = size_t(p.nsb) * (A_BYTES + size_t(p.O) * 128) + 1024;
     auto kern = tc_dw_kernel<MASK, NC, FIRST>;
     static std::mutex mu;
     static std::unordered_map<const void*, size_t> set;
@@ -452,6 +455,10 @@ cudaError_t tc_dw_layer(const float* z, const float* gy, void* gy_bf, int I, int
     p.g = g;
     p.status = status;
     p.chunks = chunks;
+    // ring: all NSB buffers (measured on the 16-wide hidden layer: a ring of
+    // J = 5 buffers with two CTAs per SM took 5.1 ms per step against 4.05 ms
+    // with 8 buffers and one CTA, since a group waits for all J of them)
+    p.nsb = NSB;
     const unsigned grid = unsigned(p.nkr) * unsigned(nchunk);
     const int nc = np8 / 8;
     if (first) {
