@@ -32,12 +32,15 @@
  *   selects d2u/dx_d^2, bit 1+2D+d selects d3u/dx_d^3, bit 1+3D = 7 selects
  *   the mixed d2u/dx_0dx_1 (D = 2: 0x1F = u,u_x,u_y,u_xx,u_yy; 0x0F =
  *   u,u_x,u_t,u_xx with coordinates (x, t); 0x2F = u,u_x,u_t,u_xx,u_xxx; 0x87 =
- *   u,u_x,u_y,u_xy; 0xFF = all eight).  A derivative bit requires the bit one
- *   order lower of the same dimension (the mixed bit: both first-order bits).
- *   Third-derivative and mixed rows run on the layer-wise path in FP32 (masks
- *   0x2F, 0x7F, 0x87, 0xFF; the fused narrow kernels and the tensor-core
- *   kernels take 0x01, 0x0F, 0x1F and return HRKAN_EUNSUPPORTED, or fall back
- *   to the FP32 layer kernels, otherwise).
+ *   u,u_x,u_y,u_xy; 0xFF = all eight).  For D = 2, bits 8+d select
+ *   d4u/dx_d^4 and bits 10+d d5u/dx_d^5 (Section 3: a fifth derivative asks for
+ *   m = 6; 0x12F = u,u_x,u_t,u_xx,u_xxx,u_xxxx; 0x52F adds u_xxxxx).  A
+ *   derivative bit requires the bit one order lower of the same dimension (the
+ *   mixed bit: both first-order bits).  Third-derivative, mixed, fourth and
+ *   fifth rows run on the layer-wise path in FP32 (masks 0x2F, 0x7F, 0x87,
+ *   0xFF, 0x12F, 0x52F; the fused narrow kernels and the tensor-core kernels
+ *   take 0x01, 0x0F, 0x1F and return HRKAN_EUNSUPPORTED, or fall back to the
+ *   FP32 layer kernels, otherwise; other valid masks return HRKAN_EUNSUPPORTED).
  *   Jet arrays are float32 [J][N], rows in bit order, J = popcount(mask).
  * - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
  *   default stream).  Argument errors are detected before anything is
@@ -159,9 +162,10 @@ int64_t hrkan_tape_floats(hrkan_t h, int64_t N, unsigned jet_mask);
  *         jets for hrkan_backward.
  * N = 0 is a valid no-op.
  * Errors: HRKAN_EINVAL for a NULL handle, N < 0, an invalid mask (a bit
- * without the bit it requires, bit 0 missing, bits above 7, or above 6 for
+ * without the bit it requires, bit 0 missing, bits above 11, or above 6 for
  * D = 3) or NULL W / x / jets with N > 0; HRKAN_EUNSUPPORTED for a mask the
- * handle's kernels lack (third-order and mixed rows on the fused shapes).
+ * handle's kernels lack (third-order, mixed, fourth and fifth rows on the fused
+ * shapes; a mask without a layer kernel).
  */
 int hrkan_forward_jets(hrkan_t h, const float* W, const float* x, int64_t N, unsigned jet_mask,
                        float* jets, float* tape, hrkan_stream_t stream);

@@ -22,7 +22,7 @@ class _Jets(torch.autograd.Function):
     @staticmethod
     def forward(ctx, W, x, net, mask):
         N = x.shape[1]
-        J = bin(int(mask) & 0xFF).count("1")
+        J = bin(int(mask) & 0xFFF).count("1")
         jets = torch.empty((J, N), dtype=torch.float32, device=W.device)
         tape = None
         n_tape = capi.hrkan_tape_floats(net.handle, N, mask)

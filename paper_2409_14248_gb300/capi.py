@@ -180,7 +180,7 @@ def hrkan_init(cfg):
 
 
 def _jets(mask):
-    return bin(int(mask) & 0xFF).count("1")
+    return bin(int(mask) & 0xFFF).count("1")
 
 
 def _need(t, n, what):

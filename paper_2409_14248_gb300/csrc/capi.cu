@@ -143,12 +143,16 @@ int check_cfg(const hrkan_cfg* c) {
 }
 
 bool valid_mask(unsigned m) {
-    if (!(m & 1u) || (m & ~0xFFu)) return false;
+    if (!(m & 1u) || (m & ~0xFFFu)) return false;
     if ((m & 0x08u) && !(m & 0x02u)) return false;
     if ((m & 0x10u) && !(m & 0x04u)) return false;
     if ((m & 0x20u) && !(m & 0x08u)) return false;
     if ((m & 0x40u) && !(m & 0x10u)) return false;
     if ((m & 0x80u) && (m & 0x06u) != 0x06u) return false;
+    if ((m & 0x100u) && !(m & 0x20u)) return false;    // fourth derivative along x_0 needs the third
+    if ((m & 0x200u) && !(m & 0x40u)) return false;
+    if ((m & 0x400u) && !(m & 0x100u)) return false;   // fifth needs the fourth
+    if ((m & 0x800u) && !(m & 0x200u)) return false;
     return true;
 }
 
@@ -338,7 +342,7 @@ float* ws_get(hrkan_t h, int slot, size_t floats, int* rc) {
     return w.first;
 }
 
-int jets_of(unsigned mask) { return __builtin_popcount(mask & 0xFFu); }
+int jets_of(unsigned mask) { return __builtin_popcount(mask & 0xFFFu); }
 
 // Offset (floats) of layer l's input jets (l >= 1) inside a tape for N points.
 int64_t tape_offset(hrkan_t h, int l, int64_t N, int J) {

@@ -2,7 +2,9 @@
 // layers): the KAN layer of Sections 1-3 with Eq. 2 bases, its input-jet
 // forward, the input adjoint through v''' (v'''' for third-derivative rows) and
 // the weight gradient.  Jet masks: 0x01, 0x0F, 0x1F (the PDE rows), 0x2F, 0x7F
-// (with third derivatives), 0x87, 0xFF (with the mixed derivative u_x0x1).
+// (with third derivatives), 0x87, 0xFF (with the mixed derivative u_x0x1),
+// 0x12F (u, u_x, u_y, u_xx, u_xxx, u_xxxx) and 0x52F (and u_xxxxx): fourth and
+// fifth derivatives along x_0 (Section 3 picks m = 6 for a fifth derivative).
 //
 // Jets live in HBM between layers as [J][units][N] float32 (one row per jet
 // component and unit, points contiguous), so every per-point access of a warp
@@ -394,6 +396,8 @@ cudaError_t wide_forward_layer_m(const WideLayer& p, unsigned mask, bool first, 
         case 0x7Fu: return fwd_mask<MW, 0x7Fu>(p, first, s);
         case 0x87u: return fwd_mask<MW, 0x87u>(p, first, s);
         case 0xFFu: return fwd_mask<MW, 0xFFu>(p, first, s);
+        case 0x12Fu: return fwd_mask<MW, 0x12Fu>(p, first, s);
+        case 0x52Fu: return fwd_mask<MW, 0x52Fu>(p, first, s);
     }
     return cudaErrorNotSupported;
 }
@@ -409,6 +413,8 @@ cudaError_t wide_adjoint_layer_m(const WideLayer& p, unsigned mask, cudaStream_t
         case 0x7Fu: return adj_mask<MW, 0x7Fu>(p, s);
         case 0x87u: return adj_mask<MW, 0x87u>(p, s);
         case 0xFFu: return adj_mask<MW, 0xFFu>(p, s);
+        case 0x12Fu: return adj_mask<MW, 0x12Fu>(p, s);
+        case 0x52Fu: return adj_mask<MW, 0x52Fu>(p, s);
     }
     return cudaErrorNotSupported;
 }
@@ -423,6 +429,8 @@ cudaError_t wide_dw_layer_m(const WideDw& p, unsigned mask, bool first, cudaStre
         case 0x7Fu: return dw_mask<MW, 0x7Fu>(p, first, s);
         case 0x87u: return dw_mask<MW, 0x87u>(p, first, s);
         case 0xFFu: return dw_mask<MW, 0xFFu>(p, first, s);
+        case 0x12Fu: return dw_mask<MW, 0x12Fu>(p, first, s);
+        case 0x52Fu: return dw_mask<MW, 0x52Fu>(p, first, s);
     }
     return cudaErrorNotSupported;
 }
