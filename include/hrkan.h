@@ -304,6 +304,29 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
                      hrkan_stream_t stream);
 
 /*
+ * One shard's part of a data-parallel training step (the loss of Eq. 4 /
+ * Eq. 8 is a sum over points, so its gradient is the sum of the shards'
+ * contributions): forward jets at this shard's N_int interior and N_bnd
+ * boundary points, residual, backward and the fixed-order reduction, with the
+ * means taken over N_int_total / N_bnd_total points (the counts of all shards
+ * together), and no Adam update.
+ *   W      [P] float32, read only.
+ *   loss   [3] float64 device: this shard's contributions to L, mean r^2 and
+ *          mean (u-g)^2 (written); summed over the shards they are the loss.
+ *   dW     [P] float32 device: this shard's contribution to the gradient
+ *          (written); summed over the shards it is the step's gradient.
+ * A data-parallel step sums loss and dW over the shards (an all-reduce) and
+ * then calls adam_step with the same arguments on every replica.  A shard with
+ * no points writes zeros.
+ * Errors: as hrkan_train_step, and HRKAN_EINVAL for totals below this shard's
+ * counts or a NULL dW.
+ */
+int hrkan_train_step_partial(hrkan_t h, const pinn_problem* prob, const float* W, const float* x_int,
+                             int64_t N_int, const float* x_bnd, const float* g_bnd, int64_t N_bnd,
+                             int64_t N_int_total, int64_t N_bnd_total, double* loss, float* dW,
+                             hrkan_stream_t stream);
+
+/*
  * Many independent networks of the handle's shape trained together: one
  * persistent launch over all instances plus one per-instance reduction/Adam
  * launch (the multi-instance workload of the training experiments of

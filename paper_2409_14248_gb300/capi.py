@@ -28,7 +28,8 @@ EXPORTS = ("hrkan_param_count", "hrkan_init", "hrkan_destroy", "hrkan_last_error
            "hrkan_train_step", "hrkan_profile_enable", "hrkan_profile_read", "hrkan_backward_noalloc",
            "hrkan_train_step_batched", "hrkan_forward_jets_batched", "hrkan_set_batch_items", "hrkan_sync_status",
            "hrkan_layer_jets", "hrkan_layer_dw", "hrkan_layer_adjoint", "hrkan_autotune_batch",
-           "hrkan_checkpoint_write", "hrkan_checkpoint_read", "hrkan_save", "hrkan_load", "hrkan_set_wait_cycles")
+           "hrkan_checkpoint_write", "hrkan_checkpoint_read", "hrkan_save", "hrkan_load", "hrkan_set_wait_cycles",
+           "hrkan_train_step_partial")
 HRKAN_KERNEL_FUSED, HRKAN_KERNEL_REDUCE, HRKAN_KERNEL_FORWARD, HRKAN_KERNEL_RESIDUAL, HRKAN_KERNEL_TENSOR = 0, 1, 2, 3, 4
 HRKAN_KERNEL_TC_FWD, HRKAN_KERNEL_TC_DW, HRKAN_KERNEL_TC_ADJ = 5, 6, 7
 HRKAN_KERNEL_LAYER_FWD, HRKAN_KERNEL_LAYER_DW, HRKAN_KERNEL_LAYER_ADJ = 8, 9, 10
@@ -85,6 +86,8 @@ def load_library(path: str = LIB_PATH):
         lib.hrkan_reset_moments.argtypes = [_vp, _vp]
         lib.hrkan_train_step.argtypes = [_vp, ctypes.POINTER(pinn_problem), _vp, _vp, _i64, _vp, _vp, _i64, _d, _d,
                                          _d, _d, _i32, _vp, _vp, _vp]
+        lib.hrkan_train_step_partial.argtypes = [_vp, ctypes.POINTER(pinn_problem), _vp, _vp, _i64, _vp, _vp, _i64,
+                                                 _i64, _i64, _vp, _vp, _vp]
         lib.hrkan_backward_noalloc.argtypes = [ctypes.POINTER(hrkan_cfg), _vp, _vp, _i64, _u32, _vp, _vp, _i32, _vp]
         _i64p = ctypes.POINTER(_i64)
         lib.hrkan_autotune_batch.argtypes = [_vp, ctypes.POINTER(pinn_problem), _vp, _vp, _i64p, _vp, _vp, _i64p,
@@ -344,6 +347,26 @@ def hrkan_train_step(h, prob, W, x_int, N_int, x_bnd, g_bnd, N_bnd, lr, b1, b2, 
                                            _ptr(x_bnd, f), _ptr(g_bnd, f), int(N_bnd), float(lr), float(b1),
                                            float(b2), float(eps), int(t), _ptr(loss, torch.float64),
                                            _ptr(dW, f), _stream(stream)))
+
+
+def hrkan_train_step_partial(h, prob, W, x_int, N_int, x_bnd, g_bnd, N_bnd, N_int_total, N_bnd_total, loss, dW,
+                             stream=None):
+    """One shard's loss contributions and gradient (means over the totals of all shards), no Adam."""
+    import torch
+    f = torch.float32
+    if _shaped(h):
+        _need(W, h.P, "W")
+        _need(dW, h.P, "dW")
+        _need(loss, 3, "loss")
+        if N_int > 0:
+            _need(x_int, 2 * N_int, "x_int")
+        if N_bnd > 0:
+            _need(x_bnd, 2 * N_bnd, "x_bnd")
+            _need(g_bnd, N_bnd, "g_bnd")
+    _check(load_library().hrkan_train_step_partial(h, ctypes.byref(prob), _ptr(W, f), _ptr(x_int, f), int(N_int),
+                                                   _ptr(x_bnd, f), _ptr(g_bnd, f), int(N_bnd), int(N_int_total),
+                                                   int(N_bnd_total), _ptr(loss, torch.float64), _ptr(dW, f),
+                                                   _stream(stream)))
 
 
 def hrkan_profile_enable(h, enable=True):

@@ -513,9 +513,13 @@ int wide_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsi
 // Training step of the layer-wise path: forward (interior and boundary),
 // residual, backward of both sets into disjoint partial rows, then the same
 // fixed-order reduction + Adam as the fused path.
+// Ni_tot / Nb_tot: the point counts the loss means divide by (this call's own
+// counts, or a data-parallel step's totals over every shard); adam = false
+// leaves W and the moments alone (the shard's loss contributions and gradient only).
 int wide_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float* x_int, int64_t N_int,
                     const float* x_bnd, const float* g_bnd, int64_t N_bnd, double lr, double b1, double b2,
-                    double eps, int t, double* loss, float* dW, cudaStream_t s) {
+                    double eps, int t, double* loss, float* dW, cudaStream_t s, int64_t Ni_tot, int64_t Nb_tot,
+                    bool adam) {
     const unsigned mask = pde_mask(prob->kind);
     const int J = jets_of(mask);
     int rc = HRKAN_OK;
@@ -550,10 +554,10 @@ int wide_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float* 
     r.g_bnd = g_bnd;
     r.Nb = N_bnd;
     r.dLb = dlb;
-    r.scale0 = N_int > 0 ? float(2.0 * prob->alpha / double(N_int)) : 0.0f;
-    r.scale1 = N_bnd > 0 ? float(2.0 / double(N_bnd)) : 0.0f;
+    r.scale0 = Ni_tot > 0 ? float(2.0 * prob->alpha / double(Ni_tot)) : 0.0f;
+    r.scale1 = Nb_tot > 0 ? float(2.0 / double(Nb_tot)) : 0.0f;
     r.loss_partial = h->loss_partial;
-    r.t_counter = t == 0 ? h->t_counter : nullptr;
+    r.t_counter = adam && t == 0 ? h->t_counter : nullptr;
     int64_t rg = (std::max(N_int, N_bnd) + 255) / 256;
     rg = std::min<int64_t>(std::max<int64_t>(rg, 1), h->max_grid_l);
     {
@@ -567,21 +571,21 @@ int wide_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float* 
     q.G = 2 * h->wide_gp;
     q.P = h->P;
     q.dW = dW;
-    q.do_adam = 1;
+    q.do_adam = adam ? 1 : 0;
     q.W = W;
     q.m1 = h->m1;
     q.m2 = h->m2;
     q.lr = lr; q.b1 = b1; q.b2 = b2; q.eps = eps;
     q.c1 = 1.0 - std::pow(b1, t > 0 ? t : 1);
     q.c2 = 1.0 - std::pow(b2, t > 0 ? t : 1);
-    q.t_counter = t == 0 ? h->t_counter : nullptr;
+    q.t_counter = adam && t == 0 ? h->t_counter : nullptr;
     q.loss_partial = h->loss_partial;
     q.Gl = int(rg);
     q.loss = loss;
     q.status = h->status;
     q.alpha = prob->alpha;
-    q.n0 = N_int;
-    q.n1 = N_bnd;
+    q.n0 = Ni_tot;
+    q.n1 = Nb_tot;
     {
         ProfScope ps(h, HRKAN_KERNEL_REDUCE, s);
         HR_CUDA(launch_reduce(q, s), "reduce/Adam launch");
@@ -1466,9 +1470,14 @@ int hrkan_profile_read(hrkan_t h, int kernel_class, double* total_ms, int64_t* l
     return HRKAN_OK;
 }
 
-int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float* x_int, int64_t N_int,
-                     const float* x_bnd, const float* g_bnd, int64_t N_bnd, double lr, double b1, double b2,
-                     double eps, int t, double* loss, float* dW, hrkan_stream_t stream) {
+namespace {
+// The training step of hrkan_train_step (adam = true) and of
+// hrkan_train_step_partial (adam = false: the loss contributions and the
+// gradient of this shard, means over Ni_tot / Nb_tot points).
+int train_step_impl(hrkan_t h, const pinn_problem* prob, float* W, const float* x_int, int64_t N_int,
+                    const float* x_bnd, const float* g_bnd, int64_t N_bnd, int64_t Ni_tot, int64_t Nb_tot, bool adam,
+                    double lr, double b1, double b2, double eps, int t, double* loss, float* dW,
+                    hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
     if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: hrkan_forward_jets and hrkan_backward only");
     if (int rc = check_problem(prob)) return rc;
@@ -1484,7 +1493,7 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned mask = pde_mask(prob->kind);
     if (h->net_id < 0) return wide_train_step(h, prob, W, x_int, N_int, x_bnd, g_bnd, N_bnd, lr, b1, b2, eps, t, loss,
-                                              dW, s);
+                                              dW, s, Ni_tot, Nb_tot, adam);
     NarrowParams p = base_params(h, W);
     p.x0 = x_int;
     p.n0 = N_int;
@@ -1494,9 +1503,9 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
     p.partial = h->partial;
     p.loss_partial = h->loss_partial;
     p.pde = make_pde(prob);
-    p.scale0 = N_int > 0 ? float(2.0 * prob->alpha / double(N_int)) : 0.0f;
-    p.scale1 = N_bnd > 0 ? float(2.0 / double(N_bnd)) : 0.0f;
-    if (t == 0) p.t_counter = h->t_counter;
+    p.scale0 = Ni_tot > 0 ? float(2.0 * prob->alpha / double(Ni_tot)) : 0.0f;
+    p.scale1 = Nb_tot > 0 ? float(2.0 / double(Nb_tot)) : 0.0f;
+    if (adam && t == 0) p.t_counter = h->t_counter;
     int grid = 0;
     cudaError_t e;
     {
@@ -1510,7 +1519,7 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
     q.G = grid;
     q.P = h->P;
     q.dW = dW;
-    q.do_adam = 1;
+    q.do_adam = adam ? 1 : 0;
     q.W = W;
     q.m1 = h->m1;
     q.m2 = h->m2;
@@ -1522,14 +1531,45 @@ int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float*
     q.loss = loss;
     q.status = h->status;
     q.alpha = prob->alpha;
-    q.n0 = N_int;
-    q.n1 = N_bnd;
-    if (t == 0) q.t_counter = h->t_counter;
+    q.n0 = Ni_tot;
+    q.n1 = Nb_tot;
+    if (adam && t == 0) q.t_counter = h->t_counter;
     {
         ProfScope ps(h, HRKAN_KERNEL_REDUCE, s);
         HR_CUDA(launch_reduce(q, s), "reduce/Adam launch");
     }
     return HRKAN_OK;
+}
+}  // namespace
+
+int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float* x_int, int64_t N_int,
+                     const float* x_bnd, const float* g_bnd, int64_t N_bnd, double lr, double b1, double b2,
+                     double eps, int t, double* loss, float* dW, hrkan_stream_t stream) {
+    return train_step_impl(h, prob, W, x_int, N_int, x_bnd, g_bnd, N_bnd, N_int, N_bnd, true, lr, b1, b2, eps, t,
+                           loss, dW, stream);
+}
+
+int hrkan_train_step_partial(hrkan_t h, const pinn_problem* prob, const float* W, const float* x_int, int64_t N_int,
+                             const float* x_bnd, const float* g_bnd, int64_t N_bnd, int64_t N_int_total,
+                             int64_t N_bnd_total, double* loss, float* dW, hrkan_stream_t stream) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (N_int_total < N_int || N_bnd_total < N_bnd || N_int < 0 || N_bnd < 0)
+        return fail(HRKAN_EINVAL, "totals %lld / %lld below this shard's %lld / %lld points", (long long)N_int_total,
+                    (long long)N_bnd_total, (long long)N_int, (long long)N_bnd);
+    if (N_int_total + N_bnd_total == 0) return fail(HRKAN_EINVAL, "no collocation points");
+    if (!dW) return fail(HRKAN_EINVAL, "dW is NULL");
+    if (N_int + N_bnd == 0) {   // an empty shard contributes nothing
+        if (!loss) return fail(HRKAN_EINVAL, "NULL device pointer");
+        if (int rc = check_problem(prob)) return rc;
+        if (int rc = use_device(h)) return rc;
+        cudaStream_t s = (cudaStream_t)stream;
+        HR_CUDA(cudaMemsetAsync(dW, 0, size_t(h->P) * sizeof(float), s), "cudaMemsetAsync");
+        HR_CUDA(cudaMemsetAsync(loss, 0, 3 * sizeof(double), s), "cudaMemsetAsync");
+        return HRKAN_OK;
+    }
+    // W is read only (adam = false); the step's arguments for Adam are placeholders
+    return train_step_impl(h, prob, const_cast<float*>(W), x_int, N_int, x_bnd, g_bnd, N_bnd, N_int_total,
+                           N_bnd_total, false, 0.0, 0.9, 0.999, 1e-8, 1, loss, dW, stream);
 }
 
 int hrkan_set_batch_items(hrkan_t h, int points_per_item) {
