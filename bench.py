@@ -36,6 +36,7 @@ workload does not need a collective), and rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -640,6 +641,8 @@ def run_batched(args, ws, rank, local):
     capi.load_library()
 
     w = inputs.WORKLOADS[args.workload]
+    if args.instances:   # a K-instance case of the same recipe and seed (a smaller case, e.g. for a profiler)
+        w = dataclasses.replace(w, instances=min(args.instances, w.instances))
     prec = PRECS[args.prec]
     d = inputs.make_batched(w)
     I, P = w.instances, w.n_params()
@@ -792,6 +795,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-equal-l2", action="store_true", help="skip the 1000-step equal-L2 training check")
+    ap.add_argument("--instances", type=int, default=0,
+                    help="multi-instance workloads: K instances drawn by the same recipe and seed (0 = all)")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="poisson_batch256 (default), burgers_2_10_10_1, poisson_2_64x3_1, burgers_2_32_32_1, "
                          "poisson_2_5_1")
