@@ -799,13 +799,16 @@ int lb_forward_layer(hrkan_t h, const float* W, int l, const float* in, float* o
 // Forward of one padded set through every layer: layer inputs into `tape`
 // (layer l at tape_offset(l)) or, without a tape, ping-pong slots zslot and
 // zslot + 1; output jets into out [J][N].
+// nlayers < L stops before layer nlayers (its input jets are then the last
+// ones the tape receives).
 int lb_forward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsigned mask, float* out, float* tape,
-                   const int* blk_inst, int zslot, cudaStream_t s) {
+                   const int* blk_inst, int zslot, cudaStream_t s, int nlayers = -1) {
     if (N == 0) return HRKAN_OK;
     const int J = jets_of(mask), L = h->L;
     int rc = HRKAN_OK;
     const float* in = x;
-    for (int l = 0; l < L; ++l) {
+    const int stop = nlayers < 0 ? L : nlayers;
+    for (int l = 0; l < stop; ++l) {
         const int O = h->cfg.widths[l + 1];
         float* y;
         if (l == L - 1) y = out;
@@ -820,14 +823,16 @@ int lb_forward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsigne
 // Backward of one padded set (its tape kept by the forward): every layer's
 // weight-gradient chunks into their partial rows and, past the first layer,
 // the input adjoint.
+// l_top: the layer whose output gradient gy_out is (the last one by default;
+// L - 2 when the output layer's reverse ran in the fused output-layer kernel).
 int lb_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsigned mask, const float* tape,
                     const float* gy_out, const int* blk_inst, const int4* chunks, int nchunk, float* partial,
-                    cudaStream_t s) {
+                    cudaStream_t s, int l_top = -1) {
     if (N == 0) return HRKAN_OK;
     const int J = jets_of(mask), L = h->L, n_inst = h->cfg.n_instances;
     int rc = HRKAN_OK;
     const float* gy = gy_out;
-    for (int l = L - 1; l >= 0; --l) {
+    for (int l = l_top < 0 ? L - 1 : l_top; l >= 0; --l) {
         const float* zl = l > 0 ? tape + tape_offset(h, l, N, J) : x;
         WideDw d{};
         d.z = zl;
@@ -890,11 +895,10 @@ int lb_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsign
     return HRKAN_OK;
 }
 
-// Multi-instance training step on the layer-wise path: gather both point sets
-// into the block-padded layout, forward with the tape kept, residual/loss per
-// instance, backward of both sets into per-chunk partial rows, then the
-// per-instance fixed-order reduction and Adam.
-int lb_train_step(hrkan_t h, const pinn_problem* probs, float* W, const float* x_int, const int64_t* off_int,
+// The same step for networks of a single layer (no layer below the output
+// layer): the output layer's forward, the residual and its reverse as separate
+// launches.
+int lb_train_step_unfused(hrkan_t h, const pinn_problem* probs, float* W, const float* x_int, const int64_t* off_int,
                   const float* x_bnd, const float* g_bnd, const int64_t* off_bnd, double lr, double b1, double b2,
                   double eps, int t, double* loss, float* dW, cudaStream_t s) {
     const int n_inst = h->cfg.n_instances;
@@ -949,6 +953,110 @@ int lb_train_step(hrkan_t h, const pinn_problem* probs, float* W, const float* x
     }
     if ((rc = lb_backward_set(h, W, xi, Ni, mask, ti, dli, b.blk_inst_i, b.chunks_i, b.nci, b.partial, s))) return rc;
     if ((rc = lb_backward_set(h, W, xb, Nb, 0x1u, tb, dlb, b.blk_inst_b, b.chunks_b, b.ncb, b.partial, s))) return rc;
+    BatchReduceParams q{};
+    q.partial = b.partial;
+    q.item_off = b.row_off;
+    q.loss_off = b.loss_off;
+    q.n_inst = n_inst;
+    q.P = h->P;
+    q.W = W;
+    q.m1 = h->m1;
+    q.m2 = h->m2;
+    q.lr = lr; q.b1 = b1; q.b2 = b2; q.eps = eps;
+    q.c1 = 1.0 - std::pow(b1, t > 0 ? t : 1);
+    q.c2 = 1.0 - std::pow(b2, t > 0 ? t : 1);
+    q.t_counter = t == 0 ? h->t_counter : nullptr;
+    q.loss_partial = b.loss_partial;
+    q.counts = b.counts;
+    q.loss = loss;
+    q.status = h->status;
+    q.dW = dW;
+    q.alpha = probs[0].alpha;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_REDUCE, s);
+        HR_CUDA(launch_batch_reduce(q, s), "multi-instance reduce launch (batched)");
+    }
+    return HRKAN_OK;
+}
+
+// Multi-instance training step on the layer-wise path: gather both point sets
+// into the block-padded layout, forward of the layers below the output layer
+// with the tape kept, the output layer with the residual/loss per instance and
+// its reverse in one launch per set, backward of the layers below into
+// per-chunk partial rows, then the per-instance fixed-order reduction and Adam.
+int lb_train_step(hrkan_t h, const pinn_problem* probs, float* W, const float* x_int, const int64_t* off_int,
+                  const float* x_bnd, const float* g_bnd, const int64_t* off_bnd, double lr, double b1, double b2,
+                  double eps, int t, double* loss, float* dW, cudaStream_t s) {
+    const int n_inst = h->cfg.n_instances;
+    auto& b = h->lb_train;
+    if (int rc = build_lbatch(h, b, n_inst, probs, off_int, off_bnd, s)) return rc;
+    const unsigned mask = pde_mask(probs[0].kind);
+    if (!residual_mask_supported(mask)) return fail(HRKAN_EUNSUPPORTED, "no residual kernel for mask 0x%x", mask);
+    const int J = jets_of(mask);
+    const int64_t Ni = b.NPi, Nb = b.NPb;
+    const int L = h->L;
+    if (L < 2) return lb_train_step_unfused(h, probs, W, x_int, off_int, x_bnd, g_bnd, off_bnd, lr, b1, b2, eps, t,
+                                            loss, dW, s);
+    int rc = HRKAN_OK;
+    float* xi = ws_get(h, 25, size_t(2 * std::max<int64_t>(Ni, 1)), &rc);
+    float* xb = xi ? ws_get(h, 26, size_t(2 * std::max<int64_t>(Nb, 1)), &rc) : nullptr;
+    float* gb = xb ? ws_get(h, 27, size_t(std::max<int64_t>(Nb, 1)), &rc) : nullptr;
+    float* ti = gb ? ws_get(h, 28, size_t(std::max<int64_t>(tape_total(h, Ni, J), 1)), &rc) : nullptr;
+    float* tb = ti ? ws_get(h, 29, size_t(std::max<int64_t>(tape_total(h, Nb, 1), 1)), &rc) : nullptr;
+    if (!tb) return rc;
+    const int I_out = h->cfg.widths[L - 1];
+    // the output layer's input adjoint (the gradient the layers below start from)
+    float* gzi = ws_get(h, 23 + ((L - 1) % 2), size_t(J) * I_out * std::max<int64_t>(Ni, 1), &rc);
+    float* gzb = gzi ? ws_get(h, 30, size_t(I_out) * std::max<int64_t>(Nb, 1), &rc) : nullptr;
+    if (!gzb) return rc;
+    const int64_t n0 = off_int[n_inst], n1 = off_bnd[n_inst];
+    HR_CUDA(lb_gather(x_int, n0, b.pt_src_i, xi, Ni, 2, s), "point gather");
+    HR_CUDA(lb_gather(x_bnd, n1, b.pt_src_b, xb, Nb, 2, s), "point gather");
+    HR_CUDA(lb_gather(g_bnd, n1, b.pt_src_b, gb, Nb, 1, s), "point gather");
+    // layers below the output layer; their outputs (the output layer's inputs) go to the tape
+    if ((rc = lb_forward_set(h, W, xi, Ni, mask, nullptr, ti, b.blk_inst_i, 0, s, L - 1))) return rc;
+    if ((rc = lb_forward_set(h, W, xb, Nb, 0x1u, nullptr, tb, b.blk_inst_b, 0, s, L - 1))) return rc;
+    // the output layer, residual / boundary misfit, its reverse: one launch per set
+    LbTailParams tp{};
+    tp.W = W + h->layer_off[L - 1];
+    tp.w_stride = h->P;
+    tp.I = I_out;
+    tp.g = h->grid;
+    tp.pde = make_pde(&probs[0]);
+    tp.inst = b.inst;
+    tp.partial = b.partial;
+    tp.P = h->P;
+    tp.col0 = h->layer_off[L - 1];
+    tp.loss_partial = b.loss_partial;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_RESIDUAL, s);
+        LbTailParams ti_p = tp;
+        ti_p.z = ti + tape_offset(h, L - 1, Ni, J);
+        ti_p.gz = gzi;
+        ti_p.N = Ni;
+        ti_p.x = xi;
+        ti_p.blk_valid = b.blk_valid_i;
+        ti_p.lrow = b.lrow_i;
+        ti_p.chunks = b.chunks_i;
+        ti_p.t_counter = t == 0 && b.nci > 0 ? h->t_counter : nullptr;
+        HR_CUDA(lb_tail(ti_p, mask, false, b.nci, s), "output-layer launch (batched)");
+        LbTailParams tb_p = tp;
+        tb_p.z = tb + tape_offset(h, L - 1, Nb, 1);
+        tb_p.gz = gzb;
+        tb_p.N = Nb;
+        tb_p.g_bnd = gb;
+        tb_p.blk_valid = b.blk_valid_b;
+        tb_p.lrow = b.lrow_b;
+        tb_p.chunks = b.chunks_b;
+        tb_p.t_counter = t == 0 && b.nci == 0 ? h->t_counter : nullptr;
+        HR_CUDA(lb_tail(tb_p, mask, true, b.ncb, s), "output-layer launch (batched)");
+    }
+    if (L >= 2) {
+        if ((rc = lb_backward_set(h, W, xi, Ni, mask, ti, gzi, b.blk_inst_i, b.chunks_i, b.nci, b.partial, s, L - 2)))
+            return rc;
+        if ((rc = lb_backward_set(h, W, xb, Nb, 0x1u, tb, gzb, b.blk_inst_b, b.chunks_b, b.ncb, b.partial, s, L - 2)))
+            return rc;
+    }
     BatchReduceParams q{};
     q.partial = b.partial;
     q.item_off = b.row_off;

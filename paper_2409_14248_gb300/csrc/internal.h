@@ -127,6 +127,31 @@ cudaError_t lb_scatter(const float* src, int64_t n_src, const int* pt_src, const
                        int64_t n_dst, int rows, cudaStream_t s);
 // Residual and loss partials of both point sets, one block per point block (masks 0x0F, 0x1F, 0x2F).
 cudaError_t lb_residual(const LbResidualParams& p, cudaStream_t s);
+// The output layer (O = 1) of one point set: forward, residual (or boundary
+// misfit), loss partials, input adjoint and weight gradient in one launch,
+// one block per weight-gradient chunk.
+struct LbTailParams {
+    const float* W;                // instance 0's output layer [1][I][n]; instance i at W + i * w_stride
+    int64_t w_stride;
+    int I;                         // the layer's inputs
+    Grid g;
+    const float* z;                // its input jets [J][I][N] (the tape)
+    float* gz;                     // dL/d(input jets) [J][I][N] (written; zero at padding points)
+    int64_t N;                     // padded points of the set
+    const float* x;                // interior set: padded coordinates [2][N]
+    const float* g_bnd;            // boundary set: padded targets [N]
+    PdeParams pde;                 // kind, lam, nu, alpha (a, b, src per instance)
+    const BatchInst* inst;
+    const int* blk_valid;          // real points of each point block
+    const int* lrow;               // loss-partial row of each point block
+    const int4* chunks;            // points [x, y) of instance w, gradient partial row z
+    float* partial;                // [rows][P]: the layer's columns [col0, col0 + I*n) of row z
+    int64_t P, col0;
+    double* loss_partial;          // [rows][2]
+    int* t_counter;                // optional device step counter: t_counter[1] = t_counter[0] + 1
+};
+// mask: the interior jet mask (0x0F, 0x1F, 0x2F); bnd: the boundary set (value row only).
+cudaError_t lb_tail(const LbTailParams& p, unsigned mask, bool bnd, int nchunk, cudaStream_t s);
 
 // out[c] = fixed-order sum of rows [0, rows) of src (row stride `stride`), c < cols.
 cudaError_t sum_rows(const float* src, int rows, int64_t stride, int64_t cols, float* out, cudaStream_t s);

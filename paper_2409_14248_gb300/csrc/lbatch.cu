@@ -127,3 +127,193 @@ cudaError_t lb_residual(const LbResidualParams& p, cudaStream_t s) {
 }
 
 }  // namespace hrkan
+
+// ------------------------------------------------------------------ output layer
+// The last layer (O = 1) of every instance, its residual and its reverse in
+// one pass per point block: forward u jets from the layer's input jets z
+// (the tape), the residual (interior set) or the boundary misfit, the loss
+// partial of the block, then per input unit the input adjoint gz (written)
+// and the weight-gradient contributions.  Those are summed without atomics:
+// within a warp, lanes whose unit value falls in the same grid cell share the
+// four weight addresses, so the warp walks its distinct cells in lane order,
+// sums each cell's lanes with a butterfly and lets one lane add the sums into
+// the warp's own copy of the layer's gradient; the copies are summed in a
+// fixed order at the end (deterministic).  One block per weight-gradient
+// chunk of one instance (partial row chunks[c].z, the layer's columns).
+namespace hrkan {
+namespace {
+
+constexpr int TAIL_WARPS = LB_BLOCK / 32;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int MW, unsigned MASK, bool BND>
+__global__ void __launch_bounds__(LB_BLOCK) lb_tail_kernel(LbTailParams p) {
+    using JT = Jet<MASK>;
+    constexpr int J = JT::J, KP = 4;
+    extern __shared__ __align__(16) float sm[];
+    const int I = p.I, n = p.g.n, In = I * n;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int4 ch = p.chunks[blockIdx.x];
+    const int inst = ch.w;
+    float* w = sm;                       // [I][n] the instance's output-layer weights
+    float* dws = sm + ((In + 3) & ~3);   // [TAIL_WARPS][I][n]
+    const float* Wi = p.W + int64_t(inst) * p.w_stride;
+    for (int t = tid; t < In; t += LB_BLOCK) w[t] = Wi[t];
+    for (int t = tid; t < TAIL_WARPS * In; t += LB_BLOCK) dws[t] = 0.0f;
+    if (p.t_counter && blockIdx.x == 0 && tid == 0) p.t_counter[1] = p.t_counter[0] + 1;
+    __syncthreads();
+    float* dwm = dws + warp * In;
+    const BatchInst bi = p.inst[inst];
+    PdeParams pde = p.pde;
+    pde.a = bi.a;
+    pde.b = bi.b;
+    pde.src = bi.src;
+    const int64_t N = p.N;
+    for (int64_t b0 = ch.x; b0 < ch.y; b0 += LB_BLOCK) {
+        const int blk = int(b0 / LB_BLOCK);
+        const int64_t pt = b0 + tid;
+        const bool valid = tid < p.blk_valid[blk];
+        // forward: u jets
+        float u[J];
+#pragma unroll
+        for (int r = 0; r < J; ++r) u[r] = 0.0f;
+#pragma unroll 1
+        for (int j = 0; j < I; ++j) {
+            float z[J];
+#pragma unroll
+            for (int r = 0; r < J; ++r) z[r] = p.z[(int64_t(r) * I + j) * N + pt];
+            Active<3, MW, JT::NDER_ROWS> b;
+            b.eval(z[0], p.g);
+            float a[J][KP];
+            JT::template rows_b<KP>(z, b, a);
+#pragma unroll
+            for (int q = 0; q < KP; ++q) {
+                const float wq = w[j * n + b.idx(q, n)];
+#pragma unroll
+                for (int r = 0; r < J; ++r) u[r] = fmaf(wq, a[r][q], u[r]);
+            }
+        }
+        // residual / boundary misfit and dL/du
+        float gu[J];
+        double l = 0.0;
+        if constexpr (BND) {
+            const float d = u[0] - p.g_bnd[pt];
+            if (valid) l = double(d) * double(d);
+            gu[0] = valid ? bi.scale1 * d : 0.0f;
+        } else {
+            const float rr = pde_residual<MASK>(pde, p.x[pt], p.x[N + pt], u);
+            if (valid) {
+                l = double(rr) * double(rr);
+                pde_residual_grad<MASK>(pde, rr, u, bi.scale0, gu);
+            } else {
+#pragma unroll
+                for (int q = 0; q < J; ++q) gu[q] = 0.0f;
+            }
+        }
+        {
+            __shared__ double red[TAIL_WARPS];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+            if (lane == 0) red[warp] = l;
+            __syncthreads();
+            if (tid == 0) {
+                double s = 0.0;
+                for (int t = 0; t < TAIL_WARPS; ++t) s += red[t];   // fixed order
+                const int row = p.lrow[blk];
+                p.loss_partial[2 * int64_t(row) + (BND ? 1 : 0)] = s;
+                p.loss_partial[2 * int64_t(row) + (BND ? 0 : 1)] = 0.0;
+            }
+            __syncthreads();
+        }
+        // reverse: input adjoint and weight gradient, unit by unit
+#pragma unroll 1
+        for (int j = 0; j < I; ++j) {
+            float z[J];
+#pragma unroll
+            for (int r = 0; r < J; ++r) z[r] = p.z[(int64_t(r) * I + j) * N + pt];
+            Active<3, MW, JT::NDER_ADJ> b;
+            b.eval(z[0], p.g);
+            float a[J][KP], dA[J][KP], gw[KP];
+            JT::template rows_b<KP>(z, b, a);
+#pragma unroll
+            for (int q = 0; q < KP; ++q) {
+                const float wq = w[j * n + b.idx(q, n)];
+                float s = 0.0f;
+#pragma unroll
+                for (int r = 0; r < J; ++r) {
+                    s = fmaf(gu[r], a[r][q], s);
+                    dA[r][q] = gu[r] * wq;
+                }
+                gw[q] = s;
+            }
+            float gz[J];
+            JT::template adjoint_b<KP>(z, b, dA, gz);
+#pragma unroll
+            for (int r = 0; r < J; ++r) p.gz[(int64_t(r) * I + j) * N + pt] = gz[r];
+            // the warp's distinct cells in lane order, one butterfly sum per cell and basis
+            const int c = b.c;
+            unsigned todo = 0xffffffffu;
+            while (todo) {
+                const int leader = __ffs(todo) - 1;
+                const int cl = __shfl_sync(0xffffffffu, c, leader);
+                const bool in = c == cl;
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+#pragma unroll
+                for (int q = 0; q < KP; ++q) {
+                    const float v = warp_sum(in ? gw[q] : 0.0f);
+                    const int i = cl + q;
+                    if (lane == 0 && unsigned(i) < unsigned(n)) dwm[j * n + i] += v;
+                }
+                todo &= ~m;
+            }
+        }
+    }
+    __syncthreads();
+    float* out = p.partial + int64_t(ch.z) * p.P + p.col0;
+    for (int t = tid; t < In; t += LB_BLOCK) {
+        float s = 0.0f;
+        for (int k = 0; k < TAIL_WARPS; ++k) s += dws[k * In + t];   // fixed order
+        out[t] = s;
+    }
+}
+
+template <int MW>
+cudaError_t tail_m(const LbTailParams& p, unsigned mask, bool bnd, int nchunk, cudaStream_t s) {
+    const size_t smem = sizeof(float) * (((size_t(p.I) * p.g.n + 3) & ~size_t(3)) + size_t(TAIL_WARPS) * p.I * p.g.n);
+    auto go = [&](auto kern) -> cudaError_t {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            if (e != cudaSuccess) { cudaGetLastError(); return e; }
+        }
+        kern<<<nchunk, LB_BLOCK, smem, s>>>(p);
+        return cudaGetLastError();
+    };
+    if (bnd) return go(lb_tail_kernel<MW, 0x01u, true>);
+    switch (mask) {
+        case 0x0Fu: return go(lb_tail_kernel<MW, 0x0Fu, false>);
+        case 0x1Fu: return go(lb_tail_kernel<MW, 0x1Fu, false>);
+        case 0x2Fu: return go(lb_tail_kernel<MW, 0x2Fu, false>);
+    }
+    return cudaErrorNotSupported;
+}
+
+}  // namespace
+
+cudaError_t lb_tail(const LbTailParams& p, unsigned mask, bool bnd, int nchunk, cudaStream_t s) {
+    if (nchunk == 0) return cudaSuccess;
+    switch (p.g.m) {
+        case 2: return tail_m<2>(p, mask, bnd, nchunk, s);
+        case 3: return tail_m<3>(p, mask, bnd, nchunk, s);
+        case 4: return tail_m<4>(p, mask, bnd, nchunk, s);
+        case 5: return tail_m<5>(p, mask, bnd, nchunk, s);
+        case 6: return tail_m<6>(p, mask, bnd, nchunk, s);
+    }
+    return cudaErrorNotSupported;
+}
+
+}  // namespace hrkan

@@ -273,3 +273,37 @@ def test_layerwise_batched_autotune_picks_a_chunk_and_trains_like_untuned():
         np.testing.assert_array_equal(tuned[1], loss.cpu().numpy())
     finally:
         capi.hrkan_destroy(h)
+
+
+@pytest.mark.parametrize("widths,G,m", [([2, 16, 1], 10, 4), ([2, 24, 24, 1], 12, 3), ([2, 8, 8, 8, 1], 6, 6),
+                                        ([2, 1], 5, 4)])
+def test_layerwise_batched_step_other_shapes_match_oracle(widths, G, m):
+    """The FP32 layer-wise multi-instance step on other depths and HR orders (the fused output-layer
+    kernel for two or more layers, the separate launches for a single layer): per-instance loss
+    terms and weight gradient against the oracle at the FP32 bars (the loss squares a residual of
+    second-derivative rows, whose bar is 1e-4: 2e-4)."""
+    import dataclasses
+    w = dataclasses.replace(W_BATCH, widths=widths, G=G, m=m)
+    d = inputs.make_batched(w, counts=[700, 1, 300, 0], bnd_counts=[50, 4, 0, 9])
+    I, P = 4, w.n_params()
+    h = capi.hrkan_init(capi.make_cfg(widths, G, 3, m, n_instances=I, flags=capi.HRKAN_FLAG_LAYERWISE))
+    try:
+        probs = [problem_of(w, a, b) for a, b in d["ab"]]
+        W = _dev(d["W"])
+        loss = torch.zeros((I, 3), dtype=torch.float64, device="cuda")
+        dW = torch.full((I * P,), float("nan"), device="cuda")
+        capi.hrkan_train_step_batched(h, probs, W, _dev(d["x_int"]), d["off_int"], _dev(d["x_bnd"]),
+                                      _dev(d["g_bnd"]), d["off_bnd"], w.lr, 0.9, 0.999, 1e-8, 1, loss, dW)
+        capi.hrkan_sync_status(h)
+        got_l, got_g = loss.cpu().numpy(), dW.cpu().numpy()
+        for i in range(I):
+            Wi, xi, xb, gb = (d["W"][i * P:(i + 1) * P].astype(np.float64),
+                              d["x_int"][:, d["off_int"][i]:d["off_int"][i + 1]],
+                              d["x_bnd"][:, d["off_bnd"][i]:d["off_bnd"][i + 1]],
+                              d["g_bnd"][d["off_bnd"][i]:d["off_bnd"][i + 1]])
+            wl, wg = oracle.train_step(w.net, w.problem(*d["ab"][i]), Wi, np.zeros(P), np.zeros(P), xi, 0x1F, xb, gb,
+                                       w.lr, 1)
+            np.testing.assert_allclose(got_l[i], wl, rtol=2 * TOL_D, atol=1e-12, err_msg=f"instance {i}")
+            assert relerr(got_g[i * P:(i + 1) * P], wg) < TOL_D, (i, relerr(got_g[i * P:(i + 1) * P], wg))
+    finally:
+        capi.hrkan_destroy(h)
