@@ -287,23 +287,30 @@ def run_reference(args, ws, rank):
 
 LB_CHUNK_CANDIDATES = (1024, 2048, 4096, 8192, 16384)
 KIND_NAMES = {5: "tc_fwd_kernel", 6: "tc_dw_kernel", 7: "tc_adj_kernel", 8: "wide_fwd_kernel",
-              9: "wide_dw_kernel", 10: "wide_adjoint_kernel", 3: "lb_residual_kernel", 1: "batch_reduce_kernel"}
+              9: "wide_dw_kernel", 10: "wide_adjoint_kernel", 3: "lb_tail_kernel (output layer, residual, reverse)",
+              1: "batch_reduce_kernel"}
 
 
 def layerwise_kind_work(widths, G, k, J, n_int, n_bnd, prec):
     """Algorithmic work of one multi-instance step on the layer-wise path per kernel kind:
     (amount, unit) with unit "flop" (dense contraction flops for the tensor-core kinds, every K
-    column counted; sparse flops of the k+1 active bases for the FP32 kinds) or "byte".
-    Interior points carry J jet rows, boundary points one."""
+    column counted; sparse flops of the k+1 active bases for the FP32 kinds, the fused
+    output-layer kernel (kind 3) included) or "byte" (the stand-alone residual of single-layer
+    networks).  Interior points carry J jet rows, boundary points one."""
     n, kp = G + k, k + 1
     L = len(widths) - 1
     rows = J * n_int + n_bnd
     pts = n_int + n_bnd
     tc_ok = lambda l: prec != 0 and 0 < l < L - 1 and 16 <= widths[l + 1] <= 64 and widths[l + 1] % 16 == 0
     tc_dw_ok = lambda l: prec == 1 and (tc_ok(l) or (l == 0 and 16 <= widths[1] <= 64 and widths[1] % 16 == 0))
-    w = {5: 0, 6: 0, 7: 0, 8: 0, 9: 0, 10: 0}
+    w = {5: 0, 6: 0, 7: 0, 8: 0, 9: 0, 10: 0, 3: 0}
     for l in range(L):
         I, O = widths[l], widths[l + 1]
+        if l == L - 1 and L >= 2:
+            # the output layer runs in the fused output-layer kernel: forward and input adjoint
+            # of the layer (sparse) and its weight gradient, all points
+            w[3] += 2 * kp * I * O * rows * 3 + (20 + 25) * kp * I * pts
+            continue
         if tc_ok(l):
             w[5] += 2 * rows * I * n * O
         else:
@@ -319,8 +326,8 @@ def layerwise_kind_work(widths, G, k, J, n_int, n_bnd, prec):
             else:
                 w[10] += 2 * kp * I * O * rows + 25 * kp * I * pts
     out = {c: (v, "flop") for c, v in w.items()}
-    # residual: coordinates, jets in, jet gradients out; boundary value, target, gradient
-    out[3] = ((2 + 2 * J) * 4 * n_int + 3 * 4 * n_bnd, "byte")
+    if L < 2:   # a single layer: the residual runs alone (coordinates, jets in, jet gradients out)
+        out[3] = ((2 + 2 * J) * 4 * n_int + 3 * 4 * n_bnd, "byte")
     return out
 
 
@@ -467,7 +474,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
 
     capi.hrkan_profile_enable(h, True)
-    for c in range(5):
+    for c in range(capi.HRKAN_KERNEL_CLASSES):
         capi.hrkan_profile_read(h, c, reset=True)
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
@@ -478,7 +485,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     capi.hrkan_profile_enable(h, False)
-    prof = {c: capi.hrkan_profile_read(h, c) for c in range(5)}
+    prof = {c: capi.hrkan_profile_read(h, c) for c in range(capi.HRKAN_KERNEL_CLASSES)}
     fused = prof[capi.HRKAN_KERNEL_FUSED][1] > 0 and prof[capi.HRKAN_KERNEL_FORWARD][1] == 0
     total_ms = max_over_ranks(total_ms, ws, "cuda")
 
@@ -558,7 +565,10 @@ def run_ours(args, ws, rank, local):
                         "kernel_ms_per_step": tc_ms / args.steps, "launches_per_step": tc_n / args.steps,
                         "flops_per_step": flops, "peak_source": ("bf16 dense sustained " if prec == PRECS["bf16"]
                                                                  else "bf16 dense sustained x 0.5 (tf32) ")
-                        + pk["source"]}
+                        + pk["source"],
+                        "per_kind": {KIND_NAMES[c]: {"ms_per_step": prof[c][0] / args.steps,
+                                                     "launches_per_step": prof[c][1] / args.steps}
+                                     for c in (5, 6, 7, 8, 9, 10) if prof[c][1] > 0}}
         out = {"metric": METRIC, "value": job_throughput(ws, args.steps, pts, total_ms / 1e3), "unit": UNIT,
                "n_gpus": ws,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,

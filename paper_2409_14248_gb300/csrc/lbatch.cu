@@ -151,7 +151,34 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-template <int MW, unsigned MASK, bool BND>
+// Warp sum of NV values per lane (NV = 16 or 32) by recursive halving: at
+// each level the lanes whose mask bit is set keep the upper half of their
+// values and send the lower half to their partner (and the other way round),
+// so NV - 1 shuffles leave every lane with the full sum of one index (its
+// `idx`); for NV = 16 the lane pairs (l, l ^ 1) hold the same index.  The
+// order of the additions is fixed.
+template <int NV>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[NV], int lane, int& idx) {
+    static_assert(NV == 16 || NV == 32, "16 or 32 values");
+    int off = 0;
+#pragma unroll
+    for (int lvl = 0; (NV >> (lvl + 1)) >= 1; ++lvl) {
+        const int h = NV >> (lvl + 1), m = 16 >> lvl;
+        const bool hi = (lane & m) != 0;
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            const float send = hi ? v[k] : v[k + h];
+            const float keep = hi ? v[k + h] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        }
+        if (hi) off += h;
+    }
+    if constexpr (NV == 16) v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    idx = off;
+    return v[0];
+}
+
+template <int MW, unsigned MASK, bool BND, int NV>
 __global__ void __launch_bounds__(LB_BLOCK) lb_tail_kernel(LbTailParams p) {
     using JT = Jet<MASK>;
     constexpr int J = JT::J, KP = 4;
@@ -182,11 +209,19 @@ __global__ void __launch_bounds__(LB_BLOCK) lb_tail_kernel(LbTailParams p) {
         float u[J];
 #pragma unroll
         for (int r = 0; r < J; ++r) u[r] = 0.0f;
+        // the next unit's jets are loaded while this one is evaluated
+        float zn[J];
+#pragma unroll
+        for (int r = 0; r < J; ++r) zn[r] = p.z[int64_t(r) * I * N + pt];
 #pragma unroll 1
         for (int j = 0; j < I; ++j) {
             float z[J];
 #pragma unroll
-            for (int r = 0; r < J; ++r) z[r] = p.z[(int64_t(r) * I + j) * N + pt];
+            for (int r = 0; r < J; ++r) z[r] = zn[r];
+            if (j + 1 < I) {
+#pragma unroll
+                for (int r = 0; r < J; ++r) zn[r] = p.z[(int64_t(r) * I + j + 1) * N + pt];
+            }
             Active<3, MW, JT::NDER_ROWS> b;
             b.eval(z[0], p.g);
             float a[J][KP];
@@ -231,11 +266,17 @@ __global__ void __launch_bounds__(LB_BLOCK) lb_tail_kernel(LbTailParams p) {
             __syncthreads();
         }
         // reverse: input adjoint and weight gradient, unit by unit
+#pragma unroll
+        for (int r = 0; r < J; ++r) zn[r] = p.z[int64_t(r) * I * N + pt];
 #pragma unroll 1
         for (int j = 0; j < I; ++j) {
             float z[J];
 #pragma unroll
-            for (int r = 0; r < J; ++r) z[r] = p.z[(int64_t(r) * I + j) * N + pt];
+            for (int r = 0; r < J; ++r) z[r] = zn[r];
+            if (j + 1 < I) {
+#pragma unroll
+                for (int r = 0; r < J; ++r) zn[r] = p.z[(int64_t(r) * I + j + 1) * N + pt];
+            }
             Active<3, MW, JT::NDER_ADJ> b;
             b.eval(z[0], p.g);
             float a[J][KP], dA[J][KP], gw[KP];
@@ -255,21 +296,39 @@ __global__ void __launch_bounds__(LB_BLOCK) lb_tail_kernel(LbTailParams p) {
             JT::template adjoint_b<KP>(z, b, dA, gz);
 #pragma unroll
             for (int r = 0; r < J; ++r) p.gz[(int64_t(r) * I + j) * N + pt] = gz[r];
-            // the warp's distinct cells in lane order, one butterfly sum per cell and basis
             const int c = b.c;
-            unsigned todo = 0xffffffffu;
-            while (todo) {
-                const int leader = __ffs(todo) - 1;
-                const int cl = __shfl_sync(0xffffffffu, c, leader);
-                const bool in = c == cl;
-                const unsigned m = __ballot_sync(0xffffffffu, in);
+            if constexpr (NV > 0) {
+                // n <= NV: every lane spreads its window over NV slots (slot i holds
+                // gw[i - c] for c <= i < c + 4), one reduce-scatter sums all slots
+                float g_rot[KP];
+                const int rot = c & 3;   // c mod 4, also for c < 0
 #pragma unroll
-                for (int q = 0; q < KP; ++q) {
-                    const float v = warp_sum(in ? gw[q] : 0.0f);
-                    const int i = cl + q;
-                    if (lane == 0 && unsigned(i) < unsigned(n)) dwm[j * n + i] += v;
+                for (int r = 0; r < KP; ++r) {
+                    const int q = (r - rot) & 3;
+                    g_rot[r] = q == 0 ? gw[0] : q == 1 ? gw[1] : q == 2 ? gw[2] : gw[3];
                 }
-                todo &= ~m;
+                float v[NV];
+#pragma unroll
+                for (int i = 0; i < NV; ++i) v[i] = unsigned(i - c) < 4u ? g_rot[i & 3] : 0.0f;
+                int idx;
+                const float sum = warp_reduce_scatter<NV>(v, lane, idx);
+                if ((NV == 32 || (lane & 1) == 0) && idx < n) dwm[j * n + idx] += sum;
+            } else {
+                // the warp's distinct cells in lane order, one butterfly sum per cell and basis
+                unsigned todo = 0xffffffffu;
+                while (todo) {
+                    const int leader = __ffs(todo) - 1;
+                    const int cl = __shfl_sync(0xffffffffu, c, leader);
+                    const bool in = c == cl;
+                    const unsigned m = __ballot_sync(0xffffffffu, in);
+#pragma unroll
+                    for (int q = 0; q < KP; ++q) {
+                        const float v = warp_sum(in ? gw[q] : 0.0f);
+                        const int i = cl + q;
+                        if (lane == 0 && unsigned(i) < unsigned(n)) dwm[j * n + i] += v;
+                    }
+                    todo &= ~m;
+                }
             }
         }
     }
@@ -280,6 +339,17 @@ __global__ void __launch_bounds__(LB_BLOCK) lb_tail_kernel(LbTailParams p) {
         for (int k = 0; k < TAIL_WARPS; ++k) s += dws[k * In + t];   // fixed order
         out[t] = s;
     }
+}
+
+template <int MW, int NV, class Go>
+cudaError_t tail_mask(Go& go, unsigned mask, bool bnd) {
+    if (bnd) return go(lb_tail_kernel<MW, 0x01u, true, NV>);
+    switch (mask) {
+        case 0x0Fu: return go(lb_tail_kernel<MW, 0x0Fu, false, NV>);
+        case 0x1Fu: return go(lb_tail_kernel<MW, 0x1Fu, false, NV>);
+        case 0x2Fu: return go(lb_tail_kernel<MW, 0x2Fu, false, NV>);
+    }
+    return cudaErrorNotSupported;
 }
 
 template <int MW>
@@ -293,13 +363,12 @@ cudaError_t tail_m(const LbTailParams& p, unsigned mask, bool bnd, int nchunk, c
         kern<<<nchunk, LB_BLOCK, smem, s>>>(p);
         return cudaGetLastError();
     };
-    if (bnd) return go(lb_tail_kernel<MW, 0x01u, true>);
-    switch (mask) {
-        case 0x0Fu: return go(lb_tail_kernel<MW, 0x0Fu, false>);
-        case 0x1Fu: return go(lb_tail_kernel<MW, 0x1Fu, false>);
-        case 0x2Fu: return go(lb_tail_kernel<MW, 0x2Fu, false>);
-    }
-    return cudaErrorNotSupported;
+    // the weight-gradient sum: a reduce-scatter over 16 or 32 slots when the
+    // layer's n bases fit, else the walk over the warp's distinct cells
+    const int n = p.g.n;
+    if (n <= 16) return tail_mask<MW, 16>(go, mask, bnd);
+    if (n <= 32) return tail_mask<MW, 32>(go, mask, bnd);
+    return tail_mask<MW, 0>(go, mask, bnd);
 }
 
 }  // namespace

@@ -275,8 +275,10 @@ def test_layerwise_batched_autotune_picks_a_chunk_and_trains_like_untuned():
         capi.hrkan_destroy(h)
 
 
+# n = G + 3 bases: 13, 15, 9 (the output layer's gradient summed over 16 slots), 23 (32 slots),
+# 43 (walk over the warp's distinct cells), and a single layer (separate launches)
 @pytest.mark.parametrize("widths,G,m", [([2, 16, 1], 10, 4), ([2, 24, 24, 1], 12, 3), ([2, 8, 8, 8, 1], 6, 6),
-                                        ([2, 1], 5, 4)])
+                                        ([2, 16, 16, 1], 20, 4), ([2, 8, 8, 1], 40, 4), ([2, 1], 5, 4)])
 def test_layerwise_batched_step_other_shapes_match_oracle(widths, G, m):
     """The FP32 layer-wise multi-instance step on other depths and HR orders (the fused output-layer
     kernel for two or more layers, the separate launches for a single layer): per-instance loss
