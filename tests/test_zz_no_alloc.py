@@ -68,15 +68,17 @@ def test_noalloc_rejects_bad_arguments():
 
 
 def test_noalloc_row_cap_matches_handle_backward_and_oracle():
-    """[2,16,16,1] with G = 30 has P = 10032 weights, so only 104 partial rows fit the static
+    """[2,16,16,1] with G = 20 has P = 6992 weights, so only 149 partial rows fit the static
     scratch: with 38400 points (300 blocks of 128) the grid is capped below the occupancy grid
-    (one block per SM on 152 SMs), and each block walks several point blocks.  Two calls in a
-    row equal hrkan_backward, and the oracle's gradient."""
+    (one block per SM on 152 SMs at this shape's shared memory), and each block walks several
+    point blocks.  Two calls in a row equal hrkan_backward, and the oracle's gradient at the FP32
+    bar.  (At G = 30, 104 rows, the float32 formulas themselves land at 1.4e-4 of the oracle,
+    on the CPU as on the GPU: steep bases make that network too ill-conditioned for the bar.)"""
     w = inputs.WORKLOADS["poisson_batch256"]
-    G, N, mask = 30, 128 * 300, inputs.MASK_POISSON
+    G, N, mask = 20, 128 * 300, inputs.MASK_POISSON
     cfg = capi.make_cfg(w.widths, G, w.k, w.m, w.lo, w.hi)
     P = capi.hrkan_param_count(cfg)
-    assert P == 10032 and (1 << 20) // P == 104
+    assert P == 6992 and (1 << 20) // P == 149
     h = capi.hrkan_init(cfg)
     try:
         rng = np.random.default_rng(31)
@@ -99,7 +101,7 @@ def test_noalloc_row_cap_matches_handle_backward_and_oracle():
                 torch.cuda.synchronize()
                 net = dict(w.net, G=G)
                 ref = oracle.backward(net, Wn.astype(np.float64), x[:, :n], mask, g[:, :n])
-                assert relerr(sub.cpu().numpy(), ref) < TOL_D
+                assert relerr(sub.cpu().numpy(), ref) < TOL_D, relerr(sub.cpu().numpy(), ref)
     finally:
         capi.hrkan_destroy(h)
 
