@@ -825,13 +825,28 @@ int lb_forward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsigne
 // the input adjoint.
 // l_top: the layer whose output gradient gy_out is (the last one by default;
 // L - 2 when the output layer's reverse ran in the fused output-layer kernel).
+// gy_bf_in (optional): that gradient already in BF16 ([J * O][N], the
+// tensor-core operand layout) instead of gy_out.
+// A layer whose weight gradient and input adjoint both run on the tensor
+// cores reads its output gradient only in BF16; the layer above then writes
+// it so (lb_layer_takes_bf16).
+bool lb_layer_takes_bf16(hrkan_t h, int l, unsigned mask) {
+    const int I = h->cfg.widths[l], O = h->cfg.widths[l + 1];
+    if (!tc_dw_supported(h->cfg.prec, I, O, h->n, mask)) return false;
+    return l == 0 || tc_adj_supported(h->cfg.prec, I, O, h->n, mask);
+}
+
 int lb_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsigned mask, const float* tape,
                     const float* gy_out, const int* blk_inst, const int4* chunks, int nchunk, float* partial,
-                    cudaStream_t s, int l_top = -1) {
+                    cudaStream_t s, int l_top = -1, void* gy_bf_in = nullptr, int gy_bf_slot = 38) {
     if (N == 0) return HRKAN_OK;
     const int J = jets_of(mask), L = h->L, n_inst = h->cfg.n_instances;
     int rc = HRKAN_OK;
     const float* gy = gy_out;
+    void* gybf = gy_bf_in;          // non-null: this layer's output gradient is ready in BF16
+    // BF16 gradients alternate between slots 38 and 39; the first one written
+    // must not be the slot gy_bf_in lives in (the adjoint reads it meanwhile)
+    int bf_slot = gy_bf_in && gy_bf_slot == 38 ? 39 : 38;
     for (int l = l_top < 0 ? L - 1 : l_top; l >= 0; --l) {
         const float* zl = l > 0 ? tape + tape_offset(h, l, N, J) : x;
         WideDw d{};
@@ -849,14 +864,17 @@ int lb_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsign
         d.chunks = chunks;
         cudaError_t e;
         const bool tc_dw = tc_dw_supported(h->cfg.prec, d.I, d.O, h->n, mask);
+        if (!tc_dw && !gy) return fail(HRKAN_EUNSUPPORTED, "layer %d: FP32 weight gradient without an FP32 gradient", l);
+        void* gbf = gybf;
         if (tc_dw) {
-            const int64_t el = tc_dw_gy_elems(J, d.O, N);
-            float* gbf = ws_get(h, 21, size_t((el + 1) / 2), &rc);
-            if (!gbf) return rc;
+            if (!gbf) {   // convert the FP32 gradient into slot 21
+                const int64_t el = tc_dw_gy_elems(J, d.O, N);
+                if (!(gbf = ws_get(h, 21, size_t((el + 1) / 2), &rc))) return rc;
+            }
             ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
             ProfScope pk(h, HRKAN_KERNEL_TC_DW, s);
             e = tc_dw_layer(d.z, d.gy, gbf, d.I, d.O, N, d.g, mask, l == 0, partial, h->P, d.col0, 0, nchunk,
-                            h->status, s, chunks);
+                            h->status, s, chunks, gybf != nullptr);
         } else {
             ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
             ProfScope pk(h, HRKAN_KERNEL_LAYER_DW, s);
@@ -870,19 +888,27 @@ int lb_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsign
             a.gy = gy;
             a.blk_inst = blk_inst;
             a.w_stride = h->P;
-            float* gz = ws_get(h, 23 + (l % 2), size_t(J) * a.I * N, &rc);
-            if (!gz) return rc;
+            const bool tc_adj = tc_dw && tc_adj_supported(h->cfg.prec, a.I, a.O, h->n, mask);
+            if (!tc_adj && !gy) return fail(HRKAN_EUNSUPPORTED, "layer %d: FP32 adjoint without an FP32 gradient", l);
+            // the layer below takes its gradient in BF16 only: write it so (tensor-core adjoint)
+            const bool out_bf = tc_adj && lb_layer_takes_bf16(h, l - 1, mask);
+            float* gz = nullptr;
+            void* gz_bf = nullptr;
+            if (out_bf) {
+                const int64_t el = tc_dw_gy_elems(J, a.I, N);
+                if (!(gz_bf = ws_get(h, bf_slot, size_t((el + 1) / 2), &rc))) return rc;
+                bf_slot = bf_slot == 38 ? 39 : 38;
+            } else if (!(gz = ws_get(h, 23 + (l % 2), size_t(J) * a.I * N, &rc))) {
+                return rc;
+            }
             a.gz = gz;
-            if (tc_dw && tc_adj_supported(h->cfg.prec, a.I, a.O, h->n, mask)) {
-                // the weight-gradient call above left the BF16 gy copy in slot 21
-                float* gbf = ws_get(h, 21, size_t((tc_dw_gy_elems(J, a.O, N) + 1) / 2), &rc);
-                float* wbf =
-                    gbf ? ws_get(h, 22, size_t((tc_adj_w_elems(a.O, a.I, h->n) * n_inst + 1) / 2), &rc) : nullptr;
+            if (tc_adj) {
+                float* wbf = ws_get(h, 22, size_t((tc_adj_w_elems(a.O, a.I, h->n) * n_inst + 1) / 2), &rc);
                 if (!wbf) return rc;
                 ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
                 ProfScope pk(h, HRKAN_KERNEL_TC_ADJ, s);
                 e = tc_adj_layer(a.W, wbf, gbf, zl, gz, a.I, a.O, N, h->grid, mask, h->status, s, n_inst, h->P, chunks,
-                                 nchunk);
+                                 nchunk, gz_bf);
             } else {
                 ProfScope ps(h, HRKAN_KERNEL_FUSED, s);
                 ProfScope pk(h, HRKAN_KERNEL_LAYER_ADJ, s);
@@ -890,6 +916,7 @@ int lb_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsign
             }
             if (e != cudaSuccess) return cuda_fail(e, "adjoint launch (batched)");
             gy = gz;
+            gybf = gz_bf;
         }
     }
     return HRKAN_OK;
@@ -1005,9 +1032,18 @@ int lb_train_step(hrkan_t h, const pinn_problem* probs, float* W, const float* x
     float* tb = ti ? ws_get(h, 29, size_t(std::max<int64_t>(tape_total(h, Nb, 1), 1)), &rc) : nullptr;
     if (!tb) return rc;
     const int I_out = h->cfg.widths[L - 1];
-    // the output layer's input adjoint (the gradient the layers below start from)
-    float* gzi = ws_get(h, 23 + ((L - 1) % 2), size_t(J) * I_out * std::max<int64_t>(Ni, 1), &rc);
-    float* gzb = gzi ? ws_get(h, 30, size_t(I_out) * std::max<int64_t>(Nb, 1), &rc) : nullptr;
+    // the output layer's input adjoint (the gradient the layers below start
+    // from): BF16 for the interior set when the layer below reads it only so
+    const bool gzi_bf = lb_layer_takes_bf16(h, L - 2, mask);
+    float* gzi = nullptr;
+    void* gzi_b = nullptr;
+    if (gzi_bf) {
+        gzi_b = ws_get(h, 38, size_t((tc_dw_gy_elems(J, I_out, std::max<int64_t>(Ni, 1)) + 1) / 2), &rc);
+        if (!gzi_b) return rc;
+    } else if (!(gzi = ws_get(h, 23 + ((L - 1) % 2), size_t(J) * I_out * std::max<int64_t>(Ni, 1), &rc))) {
+        return rc;
+    }
+    float* gzb = ws_get(h, 30, size_t(I_out) * std::max<int64_t>(Nb, 1), &rc);
     if (!gzb) return rc;
     const int64_t n0 = off_int[n_inst], n1 = off_bnd[n_inst];
     HR_CUDA(lb_gather(x_int, n0, b.pt_src_i, xi, Ni, 2, s), "point gather");
@@ -1033,6 +1069,7 @@ int lb_train_step(hrkan_t h, const pinn_problem* probs, float* W, const float* x
         LbTailParams ti_p = tp;
         ti_p.z = ti + tape_offset(h, L - 1, Ni, J);
         ti_p.gz = gzi;
+        ti_p.gz_bf = static_cast<uint16_t*>(gzi_b);
         ti_p.N = Ni;
         ti_p.x = xi;
         ti_p.blk_valid = b.blk_valid_i;
@@ -1052,7 +1089,8 @@ int lb_train_step(hrkan_t h, const pinn_problem* probs, float* W, const float* x
         HR_CUDA(lb_tail(tb_p, mask, true, b.ncb, s), "output-layer launch (batched)");
     }
     if (L >= 2) {
-        if ((rc = lb_backward_set(h, W, xi, Ni, mask, ti, gzi, b.blk_inst_i, b.chunks_i, b.nci, b.partial, s, L - 2)))
+        if ((rc = lb_backward_set(h, W, xi, Ni, mask, ti, gzi, b.blk_inst_i, b.chunks_i, b.nci, b.partial, s, L - 2,
+                                  gzi_b, 38)))
             return rc;
         if ((rc = lb_backward_set(h, W, xb, Nb, 0x1u, tb, gzb, b.blk_inst_b, b.chunks_b, b.ncb, b.partial, s, L - 2)))
             return rc;

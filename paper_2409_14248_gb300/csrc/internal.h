@@ -137,6 +137,8 @@ struct LbTailParams {
     Grid g;
     const float* z;                // its input jets [J][I][N] (the tape)
     float* gz;                     // dL/d(input jets) [J][I][N] (written; zero at padding points)
+    uint16_t* gz_bf;               // non-null: gz goes out as BF16 [J * I][N] here instead (N is a
+                                   // multiple of 256: the layer below's tensor-core operand layout)
     int64_t N;                     // padded points of the set
     const float* x;                // interior set: padded coordinates [2][N]
     const float* g_bnd;            // boundary set: padded targets [N]

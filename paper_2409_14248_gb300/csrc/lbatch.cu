@@ -9,6 +9,8 @@
 #include <algorithm>
 #include <cstdint>
 
+#include <cuda_bf16.h>
+
 #include "internal.h"
 #include "narrow.cuh"
 
@@ -294,8 +296,14 @@ __global__ void __launch_bounds__(LB_BLOCK) lb_tail_kernel(LbTailParams p) {
             }
             float gz[J];
             JT::template adjoint_b<KP>(z, b, dA, gz);
+            if (p.gz_bf) {   // the BF16 operand layout of the layer below's tensor-core kernels
 #pragma unroll
-            for (int r = 0; r < J; ++r) p.gz[(int64_t(r) * I + j) * N + pt] = gz[r];
+                for (int r = 0; r < J; ++r)
+                    p.gz_bf[(int64_t(r) * I + j) * N + pt] = __bfloat16_as_ushort(__float2bfloat16_rn(gz[r]));
+            } else {
+#pragma unroll
+                for (int r = 0; r < J; ++r) p.gz[(int64_t(r) * I + j) * N + pt] = gz[r];
+            }
             const int c = b.c;
             if constexpr (NV > 0) {
                 // n <= NV: every lane spreads its window over NV slots (slot i holds

@@ -67,9 +67,11 @@ int64_t tc_dw_gy_elems(int J, int O, int64_t N);
 // [chunks[c].x, chunks[c].y) (multiples of 256) and writes partial row
 // chunks[c].z (row0 unused); nullptr: the points split evenly into rows
 // row0 .. row0 + nchunk - 1.
+// gy_ready: gy_bf already holds the BF16 copy (gy unused), e.g. written so by
+// the layer above's adjoint.
 cudaError_t tc_dw_layer(const float* z, const float* gy, void* gy_bf, int I, int O, int64_t N, const Grid& g,
                         unsigned mask, bool first, float* partial, int64_t P, int64_t col0, int row0, int nchunk,
-                        int* status, cudaStream_t s, const int4* chunks = nullptr);
+                        int* status, cudaStream_t s, const int4* chunks = nullptr, bool gy_ready = false);
 
 // Tensor-core input adjoint of one hidden layer (tc_adj.cu): BF16, masks 0x0F
 // and 0x1F, after tc_dw_layer of the same layer and point set (it reuses that
@@ -80,8 +82,10 @@ int64_t tc_adj_w_elems(int O, int I, int n);
 // w_bf n_inst * tc_adj_w_elems elements, and chunk c (device, nchunk entries)
 // covers points [chunks[c].x, chunks[c].y) (multiples of 256) of instance
 // chunks[c].w.
+// gz_bf (optional): write dL/d(input jets) as BF16 [J * I][N rounded up to
+// 64] (the tc_dw_layer operand layout, zero past N) instead of FP32 into gz.
 cudaError_t tc_adj_layer(const float* W, void* w_bf, const void* gy_bf, const float* z, float* gz, int I, int O,
                          int64_t N, const Grid& g, unsigned mask, int* status, cudaStream_t s, int n_inst = 1,
-                         int64_t w_stride = 0, const int4* chunks = nullptr, int nchunk = 0);
+                         int64_t w_stride = 0, const int4* chunks = nullptr, int nchunk = 0, void* gz_bf = nullptr);
 
 }  // namespace hrkan

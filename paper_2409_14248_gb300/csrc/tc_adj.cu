@@ -59,6 +59,10 @@ struct AdjParams {
     // chunks[c].y) (multiples of 256) of instance chunks[c].w, whose W rows
     // start at chunks[c].w * O of the W tensor map; nullptr: tiles split evenly
     const int4* chunks = nullptr;
+    // non-null: gz goes out as BF16 [J * I][npad] (zero past N), the operand
+    // layout of the layer below's tensor-core kernels, instead of FP32 into gz
+    uint16_t* gz_bf = nullptr;
+    int64_t npad = 0;
 };
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
@@ -219,9 +223,16 @@ __global__ void __launch_bounds__(THREADS, 1)
                 b.eval(z[u][0], p.g);
                 float g[J];
                 JT::template rows_adjoint<4>(z[u], b.d1, b.d2, b.d3, dA[u], g);
-                if (valid)
+                if (p.gz_bf) {
+                    if (pt < p.npad)
+#pragma unroll
+                        for (int r = 0; r < J; ++r)
+                            p.gz_bf[(int64_t(r) * I + ju + u) * p.npad + pt] =
+                                __bfloat16_as_ushort(__float2bfloat16_rn(valid ? g[r] : 0.0f));
+                } else if (valid) {
 #pragma unroll
                     for (int r = 0; r < J; ++r) p.gz[(int64_t(r) * I + ju + u) * N + pt] = g[r];
+                }
             }
         }
     } else if (warp == EPI_WARPS) {
@@ -402,7 +413,7 @@ int64_t tc_adj_w_elems(int O, int I, int n) {
 
 cudaError_t tc_adj_layer(const float* W, void* w_bf, const void* gy_bf, const float* z, float* gz, int I, int O,
                          int64_t N, const Grid& g, unsigned mask, int* status, cudaStream_t s, int n_inst,
-                         int64_t w_stride, const int4* chunks, int nchunk) {
+                         int64_t w_stride, const int4* chunks, int nchunk, void* gz_bf) {
     using namespace tcadj;
     if (N == 0) return cudaSuccess;
     if (n_inst < 1 || (chunks && nchunk < 1) || (n_inst > 1 && !chunks)) return cudaErrorInvalidValue;
@@ -457,6 +468,8 @@ cudaError_t tc_adj_layer(const float* W, void* w_bf, const void* gy_bf, const fl
     // the batched path takes its instances' chunks
     p.nchunk = chunks ? nchunk : std::max(1, std::min(p.ntiles, nsm / p.nkr));
     p.chunks = chunks;
+    p.gz_bf = static_cast<uint16_t*>(gz_bf);
+    p.npad = Npad;
     const int cols = 2 * uk * np;
     p.tmem_cols = cols <= 32 ? 32u : cols <= 64 ? 64u : cols <= 128 ? 128u : cols <= 256 ? 256u : 512u;
     p.g = g;

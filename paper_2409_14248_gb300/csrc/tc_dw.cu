@@ -419,13 +419,14 @@ int64_t tc_dw_gy_elems(int J, int O, int64_t N) { return int64_t(J) * O * ((N + 
 
 cudaError_t tc_dw_layer(const float* z, const float* gy, void* gy_bf, int I, int O, int64_t N, const Grid& g,
                         unsigned mask, bool first, float* partial, int64_t P, int64_t col0, int row0, int nchunk,
-                        int* status, cudaStream_t s, const int4* chunks) {
+                        int* status, cudaStream_t s, const int4* chunks, bool gy_ready) {
     using namespace tcdw;
     const int J = __builtin_popcount(mask & 0x1Fu);
     const int n = g.n, np8 = np8_of(n);
     const int64_t Npad = (std::max<int64_t>(N, 1) + 63) / 64 * 64;
     const int64_t rows = int64_t(J) * O;
-    if (cudaError_t e = tc_gy_to_bf16(gy, gy_bf, J, O, N, s)) return e;
+    if (!gy_ready)
+        if (cudaError_t e = tc_gy_to_bf16(gy, gy_bf, J, O, N, s)) return e;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;
