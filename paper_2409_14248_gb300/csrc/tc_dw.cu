@@ -174,6 +174,16 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
                     }
                 }
         };
+        // K-range entries of no unit (past the last one) must be zero: no unit
+        // ever writes them, so they are cleared once in every ring buffer (the
+        // first group's proxy fence publishes them to the MMAs)
+        if (par == 0) {
+            for (int m = (jhi + 1) * NP8 - k0; m < 128; m += 8) {
+                if (m < 0) continue;
+                for (int b = 0; b < nsb; ++b)
+                    st_shared_v4(smem_u32(smem + size_t(b) * buf_bytes) + a_off(m, pp), 0u, 0u, 0u, 0u);
+            }
+        }
         float zn[MAXU][J];
         if (ng > 0) load_z(g0, zn);
         int q = 0;   // (group, row) counter
@@ -217,15 +227,6 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
                             }
                         }
                     }
-                }
-            }
-            // K-range entries of no unit (past the last one) must be zero as well
-            if (par == 0) {
-                for (int m = (jhi + 1) * NP8 - k0; m < 128; m += 8) {
-                    if (m < 0) continue;
-#pragma unroll
-                    for (int r = 0; r < J; ++r)
-                        st_shared_v4(smem_u32(smem + size_t((q + r) % nsb) * buf_bytes) + a_off(m, pp), 0u, 0u, 0u, 0u);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
