@@ -331,6 +331,46 @@ def layerwise_kind_work(widths, G, k, J, n_int, n_bnd, prec):
     return out
 
 
+def layerwise_batched_launches(widths, G, k, prec, mask):
+    """Kernels one multi-instance step of the layer-wise path launches (both point sets present):
+    3 point gathers; per set the forward of every layer below the output layer (a tensor-core
+    layer adds its weight conversion); the fused output-layer kernel per set; per set the
+    backward of the layers below (a tensor-core weight gradient adds a BF16 conversion of its
+    gradient unless the layer above wrote it in BF16; a tensor-core adjoint adds its weight
+    conversion); the per-instance reduction.  Mirrors the library's kernel choice."""
+    n, L = G + k, len(widths) - 1
+    J = {0x0F: 4, 0x1F: 5, 0x2F: 5}.get(mask, bin(mask).count("1"))
+    np_ok = n <= 64
+
+    def tc_fwd(l, m):
+        O, Jm = widths[l + 1], (1 if m == 1 else J)
+        return (prec != 0 and 0 < l < L - 1 and 16 <= O <= 64 and O % 16 == 0 and Jm * O <= 320 and np_ok
+                and m in (0x01, 0x0F, 0x1F))
+
+    def tc_dw(l, m):
+        O = widths[l + 1]
+        return prec == 1 and 16 <= O <= 64 and O % 16 == 0 and np_ok and m in (0x01, 0x0F, 0x1F)
+
+    def tc_adj(l, m):
+        return tc_dw(l, m) and m != 0x01
+
+    def takes_bf16(l, m):
+        return tc_dw(l, m) and (l == 0 or tc_adj(l, m))
+
+    if L < 2:   # separate launches: forward, residual, weight gradient
+        return 3 + 2 * 1 + 1 + 2 * 1 + 1
+    count = 3 + 2 + 1            # gathers, output-layer kernels, reduction
+    for m in (mask, 0x01):
+        count += sum(2 if tc_fwd(l, m) else 1 for l in range(L - 1))
+        bf = m != 0x01 and takes_bf16(L - 2, m)          # the output-layer kernel's gradient format
+        for l in range(L - 2, -1, -1):
+            count += (1 if bf else 2) if tc_dw(l, m) else 1
+            if l > 0:
+                count += 2 if tc_adj(l, m) else 1
+                bf = tc_adj(l, m) and takes_bf16(l - 1, m)
+    return count
+
+
 def batched_points(d):
     return int(d["off_int"][-1]), int(d["off_bnd"][-1])
 
@@ -773,7 +813,7 @@ def run_batched(args, ws, rank, local):
                         "traffic": None, "kernel": KIND_NAMES[dom], "kernel_ms_per_step": secs * 1e3,
                         "launches_per_step": prof[dom][1] / prof_steps, "work_per_step": amount,
                         "work_unit": unit, "peak_source": src, "per_kind": per_kind}
-        launches = (sum(prof[c][1] for c in (0, 1, 2, 3, 4)) / prof_steps + 3) * args.steps   # + 3 point gathers
+        launches = layerwise_batched_launches(w.widths, w.G, w.k, prec, w.mask_int) * args.steps
         out = {"metric": METRIC, "value": job_throughput(ws, args.steps, pts, total_ms / 1e3), "unit": UNIT,
                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,

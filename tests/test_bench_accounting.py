@@ -49,3 +49,13 @@ def test_launches_of_a_layer_wise_step():
     # interior set's adjoint of that layer is a tensor-core launch reusing the gradient's conversion
     hid = lambda l: l == 1
     assert bench.launches_per_step(widths, 1, hid, hid, False) == 2 * (4 + 6) + 1 + 2
+
+
+def test_layerwise_batched_launch_count_matches_the_launch_list():
+    """The BF16 multi-instance step of [2,16,16,1] G=10 launches 21 kernels (ncu launch list of the
+    bench, profiles/batched_bf16_step_poisson_batch256.md): 3 gathers, forward 3 + 3, output-layer
+    kernels 2, backward 3 + 1 (interior: gradients handed over in BF16) and 3 + 2 (boundary), 1
+    reduction; FP32 replaces every tensor-core call by one SIMT launch."""
+    assert bench.layerwise_batched_launches([2, 16, 16, 1], 10, 3, 1, 0x1F) == 21
+    # FP32: 3 gathers, 2 x 2 forwards, 2 output-layer kernels, 2 x (2 + 1) backward, 1 reduction
+    assert bench.layerwise_batched_launches([2, 16, 16, 1], 10, 3, 0, 0x1F) == 3 + 2 * 2 + 2 + 2 * 3 + 1
