@@ -631,10 +631,11 @@ def run_ours(args, ws, rank, local):
         torch.distributed.destroy_process_group()
 
 
-def equal_l2_check(torch, capi, inputs, w, prec, n_inst=8, steps=1000):
+def equal_l2_check(torch, capi, inputs, w, prec, n_inst=8, steps=1000, fp32_layerwise=False):
     """Both paths trained `steps` Adam steps from the workload's initial weights on its first
-    n_inst instances; mean relative L2 error of u on a 100 x 100 grid against the exact
-    solution, both evaluated by the FP32 path."""
+    n_inst instances (the FP32 one on the kernel family the bench timed); mean relative L2
+    error of u on a 100 x 100 grid against the exact solution, both evaluated by the FP32
+    path."""
     d = inputs.make_batched(w, instances=n_inst)
     dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
     probs = [capi.make_problem(w.pde, a, b, w.lam, w.nu, w.alpha) for a, b in d["ab"]]
@@ -645,6 +646,7 @@ def equal_l2_check(torch, capi, inputs, w, prec, n_inst=8, steps=1000):
     xg = dev(np.tile(grid, (1, n_inst)))
     offg = np.arange(n_inst + 1) * grid.shape[1]
     h32 = capi.hrkan_init(capi.make_cfg(w.widths, w.G, w.k, w.m, w.lo, w.hi, n_instances=n_inst))
+    capi.hrkan_set_batch_path(h32, 1 if fp32_layerwise else 0)
     out = {}
     try:
         for p in (PRECS["fp32"], prec):
@@ -717,11 +719,14 @@ def run_batched(args, ws, rank, local):
                                                        b2, eps, t, loss)
 
     def tune(h, W, p):
-        # the layer-wise path tunes its weight-gradient chunk, the fused path its work item
-        cands = LB_CHUNK_CANDIDATES if p != PRECS["fp32"] else None
+        # the layer-wise path tunes its weight-gradient chunk, the fused path its work item;
+        # the FP32 handle (a fused shape) times both kernel families and keeps the faster
+        cands = LB_CHUNK_CANDIDATES if p != PRECS["fp32"] else (256, 1024, 2048, 4096, 8192)
         chosen, ms = capi.hrkan_autotune_batch(h, probs, W, xi, d["off_int"], xb, gb, d["off_bnd"], candidates=cands)
-        return {"points": chosen, "ms_per_step": ms, "knob": "weight-gradient chunk (points)"
-                if p != PRECS["fp32"] else "work item (points)"}
+        layerwise = capi.hrkan_batch_path(h) == 1
+        return {"points": chosen, "ms_per_step": ms,
+                "path": "layer-wise kernels" if layerwise else "fused multi-instance kernel",
+                "knob": "weight-gradient chunk (points)" if layerwise else "work item (points)"}
 
     h = make(prec)
     W = W0.clone()
@@ -786,7 +791,7 @@ def run_batched(args, ws, rank, local):
         ms32 = max_over_ranks(time_steps(torch, capi, h32, step32, 4, k32, flush), ws, "cuda")
         capi.hrkan_destroy(h32)
         fp32_path = {"value": job_throughput(ws, k32, pts, ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32 / k32,
-                     "steps": k32, "kernel": "narrow_batch_kernel (fused FP32 multi-instance step)",
+                     "steps": k32, "kernel": "FP32 multi-instance step, " + tuned32["path"] + " (autotuned)",
                      "autotune": tuned32}
 
     if rank == 0:
@@ -828,7 +833,8 @@ def run_batched(args, ws, rank, local):
         if fp32_path is not None:
             out["fp32_path"] = fp32_path
             if not args.no_equal_l2:
-                out["equal_l2"] = equal_l2_check(torch, capi, inputs, w, prec)
+                out["equal_l2"] = equal_l2_check(torch, capi, inputs, w, prec,
+                                                 fp32_layerwise=tuned32["path"].startswith("layer"))
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_batched(w, d)
         emit(out)

@@ -362,16 +362,30 @@ int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, con
 int hrkan_forward_jets_batched(hrkan_t h, const float* W, const float* x, const int64_t* offsets,
                                unsigned jet_mask, float* jets, hrkan_stream_t stream);
 
-/* Points per work item of the multi-instance calls (default 1024); a tuning knob.
+/* Points per work item of the multi-instance calls (default 1024; on the
+ * layer-wise path: points per weight-gradient chunk); a tuning knob.
  * HRKAN_EINVAL for a NULL handle or points_per_item < 1. */
 int hrkan_set_batch_items(hrkan_t h, int points_per_item);
+
+/* Kernel family of hrkan_train_step_batched: 0 = the fused multi-instance
+ * kernel (shapes with a fused kernel), 1 = the layer-wise kernels, one launch
+ * per layer kernel over all instances (every layer-wise handle; a fused shape
+ * may choose it too, and hrkan_autotune_batch may pick it).
+ * hrkan_set_batch_path: HRKAN_EINVAL for a NULL handle or a path other than 0
+ * and 1, HRKAN_EUNSUPPORTED for 0 on a shape without a fused kernel.
+ * hrkan_batch_path returns the current family (0 or 1), or HRKAN_EINVAL for a
+ * NULL handle. */
+int hrkan_set_batch_path(hrkan_t h, int layerwise);
+int hrkan_batch_path(hrkan_t h);
 
 /*
  * Picks the points per work item of the multi-instance training step by
  * timing it: for each candidate (NULL: 256, 512, 1024, 2048, 4096) one
  * untimed call, then `reps` (< 1: 3) calls timed with CUDA events on the
  * stream, all with lr = 0 so that W keeps its values; the fastest candidate
- * becomes the handle's item size.  Arguments as hrkan_train_step_batched.
+ * becomes the handle's item size.  On a shape with a fused kernel both kernel
+ * families are timed with every candidate (hrkan_set_batch_path) and the
+ * fastest pair is kept; a family without kernels for the problem is skipped.  Arguments as hrkan_train_step_batched.
  * Synchronises the stream; resets the Adam moments and the device step
  * counter (call it before training).  chosen / ms_per_step (host, may be
  * NULL) receive the winner and its time per step.

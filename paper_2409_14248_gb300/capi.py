@@ -29,7 +29,7 @@ EXPORTS = ("hrkan_param_count", "hrkan_init", "hrkan_destroy", "hrkan_last_error
            "hrkan_train_step_batched", "hrkan_forward_jets_batched", "hrkan_set_batch_items", "hrkan_sync_status",
            "hrkan_layer_jets", "hrkan_layer_dw", "hrkan_layer_adjoint", "hrkan_autotune_batch",
            "hrkan_checkpoint_write", "hrkan_checkpoint_read", "hrkan_save", "hrkan_load", "hrkan_set_wait_cycles",
-           "hrkan_train_step_partial")
+           "hrkan_train_step_partial", "hrkan_set_batch_path", "hrkan_batch_path")
 HRKAN_KERNEL_FUSED, HRKAN_KERNEL_REDUCE, HRKAN_KERNEL_FORWARD, HRKAN_KERNEL_RESIDUAL, HRKAN_KERNEL_TENSOR = 0, 1, 2, 3, 4
 HRKAN_KERNEL_TC_FWD, HRKAN_KERNEL_TC_DW, HRKAN_KERNEL_TC_ADJ = 5, 6, 7
 HRKAN_KERNEL_LAYER_FWD, HRKAN_KERNEL_LAYER_DW, HRKAN_KERNEL_LAYER_ADJ = 8, 9, 10
@@ -97,6 +97,8 @@ def load_library(path: str = LIB_PATH):
                                                  _d, _d, _d, _d, _i32, _vp, _vp, _vp]
         lib.hrkan_forward_jets_batched.argtypes = [_vp, _vp, _vp, _i64p, _u32, _vp, _vp]
         lib.hrkan_set_batch_items.argtypes = [_vp, _i32]
+        lib.hrkan_set_batch_path.argtypes = [_vp, _i32]
+        lib.hrkan_batch_path.argtypes = [_vp]
         lib.hrkan_sync_status.argtypes = [_vp]
         lib.hrkan_layer_jets.argtypes = [_vp, _i32, _vp, _vp, _i64, _u32, _vp, _vp]
         lib.hrkan_layer_dw.argtypes = [_vp, _i32, _vp, _vp, _i64, _u32, _vp, _vp]
@@ -470,6 +472,19 @@ def hrkan_autotune_batch(h, probs, W, x_int, off_int, x_bnd, g_bnd, off_bnd, can
 
 def hrkan_set_batch_items(h, points_per_item):
     _check(load_library().hrkan_set_batch_items(h, int(points_per_item)))
+
+
+def hrkan_set_batch_path(h, layerwise):
+    """Kernel family of the multi-instance step: 0 fused, 1 layer-wise."""
+    _check(load_library().hrkan_set_batch_path(h, int(layerwise)))
+
+
+def hrkan_batch_path(h):
+    """The multi-instance step's kernel family: 0 fused, 1 layer-wise."""
+    rc = load_library().hrkan_batch_path(h)
+    if rc < 0:
+        _check(rc)
+    return rc
 
 
 def hrkan_sync_status(h):

@@ -52,6 +52,7 @@ struct hrkan_ctx {
         double* loss_partial = nullptr;
     } train_batch, fwd_batch;
     int batch_items_points = 1024;  // points per work item (layer-wise path: per weight-gradient chunk)
+    bool batch_layerwise = false;   // fused shapes: run the multi-instance step on the layer-wise kernels
     // layer-wise multi-instance layout: every instance's points in whole blocks
     // of LB_BLOCK (rebuilt only when the offsets, problems or chunk size change)
     struct LBatch {
@@ -1718,6 +1719,19 @@ int hrkan_train_step_partial(hrkan_t h, const pinn_problem* prob, const float* W
                            N_bnd_total, false, 0.0, 0.9, 0.999, 1e-8, 1, loss, dW, stream);
 }
 
+int hrkan_set_batch_path(hrkan_t h, int layerwise) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (layerwise != 0 && layerwise != 1) return fail(HRKAN_EINVAL, "path %d (0 fused, 1 layer-wise)", layerwise);
+    if (!layerwise && h->net_id < 0) return fail(HRKAN_EUNSUPPORTED, "this shape has no fused multi-instance kernel");
+    h->batch_layerwise = layerwise == 1 && h->net_id >= 0;
+    return HRKAN_OK;
+}
+
+int hrkan_batch_path(hrkan_t h) {
+    if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    return (h->net_id < 0 || h->batch_layerwise) ? 1 : 0;
+}
+
 int hrkan_set_batch_items(hrkan_t h, int points_per_item) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
     if (points_per_item < 1) return fail(HRKAN_EINVAL, "points_per_item=%d", points_per_item);
@@ -1746,7 +1760,7 @@ int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, con
     if ((n0 > 0 && !x_int) || (n1 > 0 && (!x_bnd || !g_bnd))) return fail(HRKAN_EINVAL, "NULL point array");
     if (int rc = use_device(h)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    if (h->net_id < 0)   // layer-wise multi-instance path
+    if (h->net_id < 0 || h->batch_layerwise)   // layer-wise multi-instance path
         return lb_train_step(h, probs, W, x_int, off_int, x_bnd, g_bnd, off_bnd, lr, b1, b2, eps, t, loss, dW, s);
     auto& b = h->train_batch;
     if (int rc = build_batch(h, b, n_inst, probs, off_int, off_bnd, true, s)) return rc;
@@ -1827,36 +1841,53 @@ int hrkan_autotune_batch(hrkan_t h, const pinn_problem* probs, float* W, const f
         return cuda_fail(cudaGetLastError(), "cudaEventCreate");
     }
     const int saved = h->batch_items_points;
+    const bool saved_path = h->batch_layerwise;
     int best = saved;
+    bool best_path = saved_path, found = false;
     float best_ms = 0.0f;
-    for (int c = 0; c < n_candidates && rc == HRKAN_OK; ++c) {
-        h->batch_items_points = candidates[c];
-        // lr = 0 leaves W as it is; the first call builds this candidate's work list
-        auto step = [&]() {
-            return hrkan_train_step_batched(h, probs, W, x_int, off_int, x_bnd, g_bnd, off_bnd, 0.0, 0.9, 0.999, 1e-8,
-                                            1, loss, nullptr, stream);
-        };
-        if ((rc = step())) break;
-        cudaEventRecord(a, s);
-        for (int r = 0; r < reps && rc == HRKAN_OK; ++r) rc = step();
-        cudaEventRecord(b, s);
-        if (rc) break;
-        cudaError_t e = cudaEventSynchronize(b);
-        float ms = 0.0f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(e, "autotune timing");
-            break;
-        }
-        ms /= float(reps);
-        if (c == 0 || ms < best_ms) {
-            best_ms = ms;
-            best = candidates[c];
+    // a fused shape times both kernel families: the fused multi-instance kernel
+    // (candidate = points per work item) and the layer-wise path (candidate =
+    // points per weight-gradient chunk); a family that lacks the problem's
+    // kernels (EUNSUPPORTED) is skipped
+    const int n_paths = h->net_id >= 0 ? 2 : 1;
+    for (int path = 0; path < n_paths && rc == HRKAN_OK; ++path) {
+        h->batch_layerwise = h->net_id >= 0 && path == 1;
+        for (int c = 0; c < n_candidates && rc == HRKAN_OK; ++c) {
+            h->batch_items_points = candidates[c];
+            // lr = 0 leaves W as it is; the first call builds this candidate's work list
+            auto step = [&]() {
+                return hrkan_train_step_batched(h, probs, W, x_int, off_int, x_bnd, g_bnd, off_bnd, 0.0, 0.9, 0.999,
+                                                1e-8, 1, loss, nullptr, stream);
+            };
+            if ((rc = step())) {
+                if (rc == HRKAN_EUNSUPPORTED && n_paths == 2) rc = HRKAN_OK;   // try the other family
+                break;
+            }
+            cudaEventRecord(a, s);
+            for (int r = 0; r < reps && rc == HRKAN_OK; ++r) rc = step();
+            cudaEventRecord(b, s);
+            if (rc) break;
+            cudaError_t e = cudaEventSynchronize(b);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "autotune timing");
+                break;
+            }
+            ms /= float(reps);
+            if (!found || ms < best_ms) {
+                found = true;
+                best_ms = ms;
+                best = candidates[c];
+                best_path = h->batch_layerwise;
+            }
         }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    if (rc == HRKAN_OK && !found) rc = fail(HRKAN_EUNSUPPORTED, "no multi-instance kernels for this problem");
     h->batch_items_points = rc == HRKAN_OK ? best : saved;
+    h->batch_layerwise = rc == HRKAN_OK ? best_path : saved_path;
     if (rc) return rc;
     if ((rc = hrkan_reset_moments(h, stream))) return rc;
     if (chosen) *chosen = best;

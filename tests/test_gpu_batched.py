@@ -250,8 +250,9 @@ def test_batched_calls_on_a_single_layerwise_network_equal_the_single_calls():
 
 
 def test_autotune_picks_a_candidate_and_leaves_weights_and_moments_fresh():
-    """hrkan_autotune_batch times each item size with lr = 0 (W keeps its values), keeps the
-    fastest and resets the Adam state: the next step equals a fresh handle's step."""
+    """hrkan_autotune_batch times each item size (on this fused shape: with both kernel
+    families) with lr = 0 (W keeps its values), keeps the fastest and resets the Adam state:
+    the next step equals a fresh handle's step set to the same family and size."""
     d, I, h, probs = _setup()
     h2 = None
     try:
@@ -265,6 +266,7 @@ def test_autotune_picks_a_candidate_and_leaves_weights_and_moments_fresh():
         capi.hrkan_train_step_batched(h, probs, W, xi, d["off_int"], xb, gb, d["off_bnd"], W_BATCH.lr, 0.9, 0.999,
                                       1e-8, 1, loss)
         _, _, h2, _ = _setup(chosen)
+        capi.hrkan_set_batch_path(h2, capi.hrkan_batch_path(h))
         W2 = _dev(d["W"])
         loss2 = torch.zeros((I, 3), dtype=torch.float64, device="cuda")
         capi.hrkan_train_step_batched(h2, probs, W2, xi, d["off_int"], xb, gb, d["off_bnd"], W_BATCH.lr, 0.9, 0.999,

@@ -309,3 +309,50 @@ def test_layerwise_batched_step_other_shapes_match_oracle(widths, G, m):
             assert relerr(got_g[i * P:(i + 1) * P], wg) < TOL_D, (i, relerr(got_g[i * P:(i + 1) * P], wg))
     finally:
         capi.hrkan_destroy(h)
+
+
+def test_fused_shape_runs_either_kernel_family_and_autotune_picks_one():
+    """A fused-shape FP32 handle ([2,16,16,1]) runs the multi-instance step on the fused kernel
+    (path 0) or on the layer-wise kernels (path 1, hrkan_set_batch_path); both match the oracle per
+    instance, and hrkan_autotune_batch times both families and keeps one.  A shape without a fused
+    kernel refuses path 0."""
+    d = inputs.make_batched(W_BATCH, counts=COUNTS, bnd_counts=BND)
+    I, P = len(COUNTS), W_BATCH.n_params()
+    h = capi.hrkan_init(capi.make_cfg(W_BATCH.widths, W_BATCH.G, n_instances=I))
+    try:
+        probs = [problem_of(W_BATCH, a, b) for a, b in d["ab"]]
+        xi, xb, gb = _dev(d["x_int"]), _dev(d["x_bnd"]), _dev(d["g_bnd"])
+        assert capi.hrkan_batch_path(h) == 0
+        want = []
+        for i in range(I):
+            Wi, x_i, x_b, g_b = _inst(d, i)
+            want.append(oracle.train_step(W_BATCH.net, W_BATCH.problem(*d["ab"][i]), Wi, np.zeros(P), np.zeros(P),
+                                          x_i, 0x1F, x_b, g_b, W_BATCH.lr, 1))
+        for path in (0, 1):
+            capi.hrkan_set_batch_path(h, path)
+            assert capi.hrkan_batch_path(h) == path
+            capi.hrkan_reset_moments(h)
+            W = _dev(d["W"])
+            loss = torch.zeros((I, 3), dtype=torch.float64, device="cuda")
+            dW = torch.full((I * P,), float("nan"), device="cuda")
+            capi.hrkan_train_step_batched(h, probs, W, xi, d["off_int"], xb, gb, d["off_bnd"], W_BATCH.lr, 0.9,
+                                          0.999, 1e-8, 1, loss, dW)
+            got_l, got_g = loss.cpu().numpy(), dW.cpu().numpy()
+            for i in range(I):
+                np.testing.assert_allclose(got_l[i], want[i][0], rtol=1e-5, atol=1e-12, err_msg=f"path {path} {i}")
+                assert relerr(got_g[i * P:(i + 1) * P], want[i][1]) < TOL_D, (path, i)
+        W = _dev(d["W"])
+        chosen, ms = capi.hrkan_autotune_batch(h, probs, W, xi, d["off_int"], xb, gb, d["off_bnd"],
+                                               candidates=[256, 2048], reps=2)
+        assert chosen in (256, 2048) and ms > 0 and capi.hrkan_batch_path(h) in (0, 1)
+        np.testing.assert_array_equal(W.cpu().numpy(), d["W"])
+    finally:
+        capi.hrkan_destroy(h)
+    h = capi.hrkan_init(capi.make_cfg([2, 24, 24, 1], 12, n_instances=2))     # no fused kernel
+    try:
+        assert capi.hrkan_batch_path(h) == 1
+        with pytest.raises(capi.HRKANError) as ei:
+            capi.hrkan_set_batch_path(h, 0)
+        assert ei.value.code == capi.HRKAN_EUNSUPPORTED
+    finally:
+        capi.hrkan_destroy(h)
