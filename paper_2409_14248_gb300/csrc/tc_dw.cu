@@ -17,10 +17,19 @@
 // K-range and one chunk of points and writes its slice of one partial row;
 // the rows are summed in a fixed order afterwards (deterministic).
 //
-// Warp roles (192 threads): warps 0-3 produce (thread = point of a 64-point
-// group x unit parity), warp 4 issues the MMAs, warp 5 loads gy tiles.  A ring
-// of 8 buffers, one per (group, jet row): A tile 128 k x 64 points (16 KB) +
-// gy tile O x 64 points.  Every wait is bounded as in the forward kernel.
+// Warp roles (320 threads): warps 0-7 produce (thread = point of a 64-point
+// group x one of four unit classes), warp 8 issues the MMAs, warp 9 loads gy
+// tiles.  A ring of group slots, each holding one group's J A tiles (128 k x
+// 64 points, 16 KB each) and its J gy tiles (O x 64 points): one wait, one
+// proxy fence and one arrive per producer warp and group, one tcgen05.commit
+// per group.  Where only one slot fits (J = 5, O >= 48: EARLY) the producers
+// evaluate a group's unit windows before they wait for its slot, so that they
+// still overlap the MMAs; with two or more slots they evaluate and store unit
+// by unit (fewer live registers).  Measured on the weight gradients of the
+// batching workload ([2,16,16,1], four launches per step): 2.3 ms per step
+// against 3.8 with a slot per (group, jet row) and four producer warps; on
+// [2,64,64,64,1] (six launches, EARLY): 2.4 ms against 3.0.  Every wait is
+// bounded as in the forward kernel.
 #include <cuda.h>
 
 #include <algorithm>
@@ -46,9 +55,12 @@ using tck::tc_fence_before;
 using tck::tmem_ld16;
 
 constexpr int GROUP = 64;        // points per group (the gy tile's 128 bytes)
-constexpr int NSB = 8;           // most ring buffers (one per group and jet row); p.nsb of them are used
+constexpr int NPROD = 8;         // producer warps
+constexpr int NPAR = NPROD / 2;  // unit classes: two warps cover a group's points, a class takes every NPAR-th unit
+constexpr int NSB = 8;           // most group slots; p.nsb of them are used
 constexpr int A_BYTES = 128 * GROUP * 2;   // 128 k x 64 points BF16
-constexpr int THREADS = 192;
+constexpr int SLOT_BUDGET = 200 * 1024;    // shared memory for the group slots
+constexpr int THREADS = 32 * (NPROD + 2);
 
 struct DwParams {
     const float* z;        // layer input jets [J][I][N]
@@ -66,8 +78,7 @@ struct DwParams {
     // chunks[c].y) (multiples of 256) and writes partial row chunks[c].z;
     // nullptr: the groups split evenly, chunk c into row row0 + c
     const int4* chunks = nullptr;
-    // ring buffers in use, J <= nsb <= NSB (a group takes J of them at once)
-    int nsb = NSB;
+    int nsb = NSB;         // group slots in use
 };
 
 // Byte offset of element (m = k within the K-range, p = point within the group)
@@ -91,14 +102,14 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
-template <unsigned MASK, int NC, bool FIRST>
+template <unsigned MASK, int NC, bool FIRST, bool EARLY>
 __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __grid_constant__ CUtensorMap gmap) {
     using JT = Jet<MASK>;
     constexpr int J = JT::J;
-    constexpr int NP8 = 8 * NC;                               // elements per padded unit
-    constexpr int MAXU = ((127 / NP8) + 2 + 1) / 2;           // units of one parity overlapping 128 k
+    constexpr int NP8 = 8 * NC;                                  // elements per padded unit
+    constexpr int MAXU = ((127 / NP8) + 2 + NPAR - 1) / NPAR;    // units of one class overlapping 128 k
     using Win = tck::UnitWin<J>;
-    constexpr int QW = NP8 / 8;                               // words per residue quarter of a unit
+    constexpr int QW = NP8 / 8;                                  // words per residue quarter of a unit
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -112,10 +123,11 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int O = p.O, I = p.I;
     const uint32_t b_bytes = uint32_t(O) * 128u;
-    const uint32_t buf_bytes = uint32_t(A_BYTES) + b_bytes;
+    // one ring slot per group: J A tiles, then J gy tiles
+    const uint32_t slot_bytes = uint32_t(J) * (uint32_t(A_BYTES) + b_bytes);
     const int kr = blockIdx.x % p.nkr, chunk = blockIdx.x / p.nkr;
     const int k0 = kr * 128;
-    const int nsb = p.nsb;
+    const int nsg = p.nsb;
     const int g0 = p.chunks ? p.chunks[chunk].x / GROUP : int(int64_t(chunk) * p.ngroups / p.nchunk);
     const int g1 = p.chunks ? p.chunks[chunk].y / GROUP : int(int64_t(chunk + 1) * p.ngroups / p.nchunk);
     const int out_row = p.chunks ? p.chunks[chunk].z : p.row0 + chunk;
@@ -123,7 +135,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
 
     if (tid == 0) {
         for (int b = 0; b < NSB; ++b) {
-            mbar_init(&bar_full[b], 5);    // four producer warps + the TMA's expect_tx
+            mbar_init(&bar_full[b], NPROD + 1);   // the producer warps + the TMA's expect_tx
             mbar_init(&bar_empty[b], 1);
         }
         mbar_init(&bar_accfull, 1);
@@ -142,8 +154,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
     tc_fence_after();
     const uint32_t tbase = tmem_base_sh;
 
-    if (warp < 4) {
+    if (warp < NPROD) {
         // ------------------------------------------------------------ producers
+        // thread = point pp of the group x unit class par: units jlo + par + NPAR * u
         const int pp = tid & (GROUP - 1), par = tid >> 6;
         const int jlo = k0 / NP8;
         const int jhi = min(I - 1, (k0 + 127) / NP8);
@@ -151,7 +164,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
         int nu = 0;
 #pragma unroll
         for (int u = 0; u < MAXU; ++u) {
-            jn[u] = jlo + par + 2 * u;
+            jn[u] = jlo + par + NPAR * u;
             if (jn[u] <= jhi) nu = u + 1;
         }
         const int64_t N = p.N;
@@ -175,18 +188,19 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
                 }
         };
         // K-range entries of no unit (past the last one) must be zero: no unit
-        // ever writes them, so they are cleared once in every ring buffer (the
-        // first group's proxy fence publishes them to the MMAs)
+        // ever writes them, so they are cleared once in every A tile of every
+        // slot (the first publication of each slot makes them visible to the MMAs)
         if (par == 0) {
             for (int m = (jhi + 1) * NP8 - k0; m < 128; m += 8) {
                 if (m < 0) continue;
-                for (int b = 0; b < nsb; ++b)
-                    st_shared_v4(smem_u32(smem + size_t(b) * buf_bytes) + a_off(m, pp), 0u, 0u, 0u, 0u);
+                for (int b = 0; b < nsg; ++b)
+                    for (int r = 0; r < J; ++r)
+                        st_shared_v4(smem_u32(smem + size_t(b) * slot_bytes + size_t(r) * A_BYTES) + a_off(m, pp),
+                                     0u, 0u, 0u, 0u);
             }
         }
         float zn[MAXU][J];
         if (ng > 0) load_z(g0, zn);
-        int q = 0;   // (group, row) counter
         for (int gi = 0; gi < ng; ++gi) {
             float zc[MAXU][J];
 #pragma unroll
@@ -194,53 +208,60 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
 #pragma unroll
                 for (int r = 0; r < J; ++r) zc[u][r] = zn[u][r];
             if (gi + 1 < ng) load_z(g0 + gi + 1, zn);
-            // the group's J buffers must be free
-            bool ok = true;
+            // store unit u's J rows (its NC chunks of 8 elements that fall in the range) into the slot
+            auto store_unit = [&](int u, const Win& w, uint32_t sbase) {
+                const int kb = jn[u] * NP8 - k0;   // k of the unit's first element, relative to the range
 #pragma unroll
-            for (int r = 0; r < J; ++r) {
-                const int b = (q + r) % nsb;
-                const uint32_t ph = uint32_t((q + r) / nsb) & 1u;
-                ok = ok && mbar_wait(&bar_empty[b], ph ^ 1u, abort, wl);
-            }
-            if (!__all_sync(0xffffffffu, ok)) goto done;
+                for (int ci = 0; ci < NC; ++ci) {
+                    const int m = kb + 8 * ci;
+                    if (m >= 0 && m < 128) {
+                        const uint32_t off = a_off(m, pp);
 #pragma unroll
-            for (int u = 0; u < MAXU; ++u) {
-                if (u < nu) {
-                    Win w;
-                    tck::unit_window<MASK, HRKAN_BF16>(zc[u], p.g, true, w);
-                    const int kb = jn[u] * NP8 - k0;   // k of the unit's first element, relative to the range
+                        for (int r = 0; r < J; ++r) {
+                            uint32_t v[4];
 #pragma unroll
-                    for (int ci = 0; ci < NC; ++ci) {
-                        const int m = kb + 8 * ci;
-                        if (m >= 0 && m < 128) {
-                            const uint32_t off = a_off(m, pp);
-#pragma unroll
-                            for (int r = 0; r < J; ++r) {
-                                uint32_t v[4];
-#pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    const int lw = 4 * ci + e, qr = lw / QW, qo = lw % QW;
-                                    v[e] = w.tw[qr] == qo ? w.y[r][qr] : 0u;
-                                }
-                                const int b = (q + r) % nsb;
-                                st_shared_v4(smem_u32(smem + size_t(b) * buf_bytes) + off, v[0], v[1], v[2], v[3]);
+                            for (int e = 0; e < 4; ++e) {
+                                const int lw = 4 * ci + e, qr = lw / QW, qo = lw % QW;
+                                v[e] = w.tw[qr] == qo ? w.y[r][qr] : 0u;
                             }
+                            st_shared_v4(sbase + uint32_t(r) * A_BYTES + off, v[0], v[1], v[2], v[3]);
                         }
+                    }
+                }
+            };
+            const int b = gi % nsg;
+            const uint32_t ph = uint32_t(gi / nsg) & 1u;
+            const uint32_t sbase = smem_u32(smem + size_t(b) * slot_bytes);
+            if constexpr (EARLY) {
+                Win w[MAXU];
+#pragma unroll
+                for (int u = 0; u < MAXU; ++u)
+                    if (u < nu) tck::unit_window<MASK, HRKAN_BF16>(zc[u], p.g, true, w[u]);
+                if (!__all_sync(0xffffffffu, mbar_wait(&bar_empty[b], ph ^ 1u, abort, wl))) goto done;
+#pragma unroll
+                for (int u = 0; u < MAXU; ++u)
+                    if (u < nu) store_unit(u, w[u], sbase);
+            } else {
+                if (!__all_sync(0xffffffffu, mbar_wait(&bar_empty[b], ph ^ 1u, abort, wl))) goto done;
+#pragma unroll
+                for (int u = 0; u < MAXU; ++u) {
+                    if (u < nu) {
+                        Win w;
+                        tck::unit_window<MASK, HRKAN_BF16>(zc[u], p.g, true, w);
+                        store_unit(u, w, sbase);
                     }
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
-#pragma unroll
-            for (int r = 0; r < J; ++r) mbar_arrive_if(&bar_full[(q + r) % nsb], lane == 0);
-            q += J;
+            mbar_arrive_if(&bar_full[b], lane == 0);
         }
-        // ---- epilogue: D (lanes = k of the range) -> partial row
-        if (ng > 0) {
-            if (!__all_sync(0xffffffffu, mbar_wait(&bar_accfull, 0u, abort, wl))) goto done;
-        }
-        tc_fence_after();
-        {
+        // ---- epilogue (warps 0-3, one TMEM lane quarter each): D (lanes = k of the range) -> partial row
+        if (warp < 4) {
+            if (ng > 0) {
+                if (!__all_sync(0xffffffffu, mbar_wait(&bar_accfull, 0u, abort, wl))) goto done;
+            }
+            tc_fence_after();
             const int k = k0 + warp * 32 + lane;
             // element pos of the unit holds basis 4 * (pos mod NP8/4) + pos / (NP8/4)
             const int j = k / NP8, pos = k % NP8, i = 4 * (pos % (NP8 / 4)) + pos / (NP8 / 4);
@@ -262,29 +283,32 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
                     for (int e = 0; e < 16; ++e) out[int64_t(c + e) * I * p.n] = __uint_as_float(v[e]);
             }
         }
-    } else if (warp == 4) {
+    } else if (warp == NPROD) {
         // ------------------------------------------------------------ MMA issue
         if (lane == 0 && ng > 0) {
             // kind::f16, BF16 A (MN-major) and B (K-major), FP32 D, M = 128, N = O
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (uint32_t(O >> 3) << 17) |
                                    (uint32_t(128 >> 4) << 24);
             bool issued = false;
-            const int total = ng * J;
-            for (int q = 0; q < total; ++q) {
-                const int b = q % nsb;
-                if (!mbar_wait(&bar_full[b], uint32_t(q / nsb) & 1u, abort, wl)) break;
+            for (int gi = 0; gi < ng; ++gi) {
+                const int b = gi % nsg;
+                if (!mbar_wait(&bar_full[b], uint32_t(gi / nsg) & 1u, abort, wl)) break;
                 tc_fence_after();
-                const uint32_t abase = smem_u32(smem + size_t(b) * buf_bytes);
-                const uint64_t bd = sdesc(abase + A_BYTES, 16, 1024);
+                const uint32_t sbase = smem_u32(smem + size_t(b) * slot_bytes);
 #pragma unroll
-                for (int s = 0; s < GROUP / 16; ++s) {
-                    const uint64_t ad = sdesc(abase + uint32_t(s) * 4096u, 1024, 2048);
-                    const uint32_t acc = (q > 0 || s > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n\t.reg .pred pa;\n\tsetp.ne.b32 pa, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n\t}" ::"r"(tbase),
-                        "l"(ad), "l"(bd + uint64_t(2 * s)), "r"(idesc), "r"(acc)
-                        : "memory");
+                for (int r = 0; r < J; ++r) {
+                    const uint32_t abase = sbase + uint32_t(r) * A_BYTES;
+                    const uint64_t bd = sdesc(sbase + uint32_t(J) * A_BYTES + uint32_t(r) * b_bytes, 16, 1024);
+#pragma unroll
+                    for (int ks = 0; ks < GROUP / 16; ++ks) {
+                        const uint64_t ad = sdesc(abase + uint32_t(ks) * 4096u, 1024, 2048);
+                        const uint32_t acc = (gi > 0 || r > 0 || ks > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred pa;\n\tsetp.ne.b32 pa, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n\t}" ::"r"(tbase),
+                            "l"(ad), "l"(bd + uint64_t(2 * ks)), "r"(idesc), "r"(acc)
+                            : "memory");
+                    }
                 }
                 issued = true;
                 mma_commit(&bar_empty[b]);
@@ -296,22 +320,22 @@ __global__ void __launch_bounds__(THREADS, 1) tc_dw_kernel(DwParams p, const __g
             }
         }
     } else {
-        // ------------------------------------------------------------ gy tiles by TMA
+        // ------------------------------------------------------------ a group's J gy tiles by TMA
         if (lane == 0 && ng > 0) {
-            const int total = ng * J;
             uint32_t used = 0u, last_par = 0u;
-            for (int q = 0; q < total; ++q) {
-                const int b = q % nsb, gi = q / J, r = q % J;
-                const uint32_t ph = uint32_t(q / nsb) & 1u;
+            for (int gi = 0; gi < ng; ++gi) {
+                const int b = gi % nsg;
+                const uint32_t ph = uint32_t(gi / nsg) & 1u;
                 if (!mbar_wait(&bar_empty[b], ph ^ 1u, abort, wl)) break;
-                mbar_expect_tx(&bar_full[b], b_bytes);
-                tck::tma_load_2d(smem + size_t(b) * buf_bytes + A_BYTES, &gmap, &bar_full[b], (g0 + gi) * GROUP,
-                                 r * O);
+                mbar_expect_tx(&bar_full[b], uint32_t(J) * b_bytes);
+                uint8_t* gdst = smem + size_t(b) * slot_bytes + size_t(J) * A_BYTES;
+                for (int r = 0; r < J; ++r)
+                    tck::tma_load_2d(gdst + size_t(r) * b_bytes, &gmap, &bar_full[b], (g0 + gi) * GROUP, r * O);
                 used |= 1u << b;
                 last_par = (last_par & ~(1u << b)) | (ph << b);
             }
             if (*abort)
-                for (int b = 0; b < nsb; ++b)
+                for (int b = 0; b < nsg; ++b)
                     if ((used >> b) & 1u) mbar_drain(&bar_full[b], (last_par >> b) & 1u);
         }
     }
@@ -367,10 +391,11 @@ EncodeTiledFn encode_fn() {
 
 int np8_of(int n) { return std::max(16, (n + 7) / 8 * 8); }
 
-template <unsigned MASK, int NC, bool FIRST>
+template <unsigned MASK, int NC, bool FIRST, bool EARLY>
 cudaError_t launch(const DwParams& p, const CUtensorMap& map, unsigned grid, cudaStream_t s) {
-    const size_t smem = size_t(p.nsb) * (A_BYTES + size_t(p.O) * 128) + 1024;
-    auto kern = tc_dw_kernel<MASK, NC, FIRST>;
+    const int J = __builtin_popcount(MASK & 0x1Fu);
+    const size_t smem = size_t(p.nsb) * J * (A_BYTES + size_t(p.O) * 128) + 1024;
+    auto kern = tc_dw_kernel<MASK, NC, FIRST, EARLY>;
     static std::mutex mu;
     static std::unordered_map<const void*, size_t> set;
     {
@@ -386,16 +411,25 @@ cudaError_t launch(const DwParams& p, const CUtensorMap& map, unsigned grid, cud
     return cudaGetLastError();
 }
 
+template <unsigned MASK, int NC, bool FIRST>
+cudaError_t launch_e(bool early, const DwParams& p, const CUtensorMap& map, unsigned grid, cudaStream_t s) {
+    // a single slot only fits for J = 5 (mask 0x1F) and O >= 48
+    if constexpr (MASK == 0x1Fu)
+        if (early) return launch<MASK, NC, FIRST, true>(p, map, grid, s);
+    return launch<MASK, NC, FIRST, false>(p, map, grid, s);
+}
+
 template <unsigned MASK, bool FIRST>
 cudaError_t launch_nc(int nc, const DwParams& p, const CUtensorMap& map, unsigned grid, cudaStream_t s) {
+    const bool early = p.nsb == 1;
     switch (nc) {
-        case 2: return launch<MASK, 2, FIRST>(p, map, grid, s);
-        case 3: return launch<MASK, 3, FIRST>(p, map, grid, s);
-        case 4: return launch<MASK, 4, FIRST>(p, map, grid, s);
-        case 5: return launch<MASK, 5, FIRST>(p, map, grid, s);
-        case 6: return launch<MASK, 6, FIRST>(p, map, grid, s);
-        case 7: return launch<MASK, 7, FIRST>(p, map, grid, s);
-        case 8: return launch<MASK, 8, FIRST>(p, map, grid, s);
+        case 2: return launch_e<MASK, 2, FIRST>(early, p, map, grid, s);
+        case 3: return launch_e<MASK, 3, FIRST>(early, p, map, grid, s);
+        case 4: return launch_e<MASK, 4, FIRST>(early, p, map, grid, s);
+        case 5: return launch_e<MASK, 5, FIRST>(early, p, map, grid, s);
+        case 6: return launch_e<MASK, 6, FIRST>(early, p, map, grid, s);
+        case 7: return launch_e<MASK, 7, FIRST>(early, p, map, grid, s);
+        case 8: return launch_e<MASK, 8, FIRST>(early, p, map, grid, s);
     }
     return cudaErrorNotSupported;
 }
@@ -460,7 +494,8 @@ cudaError_t tc_dw_layer(const float* z, const float* gy, void* gy_bf, int I, int
     // ring: all NSB buffers (measured on the 16-wide hidden layer: a ring of
     // J = 5 buffers with two CTAs per SM took 5.1 ms per step against 4.05 ms
     // with 8 buffers and one CTA, since a group waits for all J of them)
-    p.nsb = NSB;
+    // one CTA per SM: as many group slots as SLOT_BUDGET holds (J = 5, O = 16: two)
+    p.nsb = std::max(1, std::min(NSB, int(SLOT_BUDGET / (size_t(J) * (A_BYTES + size_t(O) * 128)))));
     const unsigned grid = unsigned(p.nkr) * unsigned(nchunk);
     const int nc = np8 / 8;
     if (first) {
