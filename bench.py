@@ -331,6 +331,40 @@ def layerwise_kind_work(widths, G, k, J, n_int, n_bnd, prec):
     return out
 
 
+# DRAM bytes (read + write) of one BF16 step per kernel kind, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, the mean of three steps) of the 16-instance case
+# of the batching workload (293 920 interior + 36 734 boundary points; command and figures in
+# profiles/batched_bf16_step_poisson_batch256.md), scaled to a run by its points.  Only valid for
+# the kernels as captured: retake the capture when one of them changes.
+TRAFFIC_BATCH16 = {"points": 330654,
+                   "bytes": {5: 142.75e6, 6: 198.25e6, 7: 168.28e6, 3: 117.14e6}}
+
+
+def layerwise_tc_bytes(widths, G, k, J, n_int, n_bnd, prec):
+    """Algorithmic DRAM bytes of the tensor-core kinds of one multi-instance step on the
+    layer-wise path (each tensor read or written once): the forward (kind 5) reads the
+    layer's input jets and writes its output jets in FP32; the weight gradient (kind 6) reads
+    the input jets (the two coordinates for the first layer) and the BF16 output gradient; the
+    input adjoint (kind 7, interior points) reads the input jets and the BF16 output gradient
+    and writes the input gradient, in BF16 when the layer below runs on tensor cores, else
+    FP32.  Interior points carry J jet rows, boundary points one; weights are not counted."""
+    L = len(widths) - 1
+    rows = J * n_int + n_bnd
+    tc_ok = lambda l: prec != 0 and 0 < l < L - 1 and 16 <= widths[l + 1] <= 64 and widths[l + 1] % 16 == 0
+    tc_dw_ok = lambda l: prec == 1 and (tc_ok(l) or (l == 0 and 16 <= widths[1] <= 64 and widths[1] % 16 == 0))
+    b = {5: 0, 6: 0, 7: 0}
+    for l in range(L - 1):
+        I, O = widths[l], widths[l + 1]
+        if tc_ok(l):
+            b[5] += 4 * (I + O) * rows
+        if tc_dw_ok(l):
+            b[6] += (8 * (n_int + n_bnd) if l == 0 else 4 * I * rows) + 2 * O * rows
+        if l > 0 and tc_ok(l) and prec == 1:
+            gz = 2 if tc_dw_ok(l - 1) else 4
+            b[7] += (4 * I + 2 * O + gz * I) * J * n_int
+    return b
+
+
 def layerwise_batched_launches(widths, G, k, prec, mask):
     """Kernels one multi-instance step of the layer-wise path launches (both point sets present):
     3 point gathers; per set the forward of every layer below the output layer (a tensor-core
@@ -777,9 +811,9 @@ def run_batched(args, ws, rank, local):
     h2d = (hxi.numel() + hxb.numel() + hgb.numel()) * 4
     capi.hrkan_destroy(h)
 
-    # the plain FP32 path (the fused multi-instance kernel) of the same workload
+    # the plain FP32 path of the same workload (autotuned over both kernel families)
     fp32_path = None
-    if prec != PRECS["fp32"]:
+    if prec != PRECS["fp32"] and not args.no_fp32_path:
         h32 = make(PRECS["fp32"])
         W32 = W0.clone()
         tuned32 = tune(h32, W32, PRECS["fp32"])
@@ -805,12 +839,25 @@ def run_batched(args, ws, rank, local):
         if dom is not None:
             amount, unit = work[dom]
             secs = prof[dom][0] / prof_steps / 1e3
+            other = None
             if unit == "byte":
                 achieved, peak, bound, u, src = amount / secs / 1e9, pk["hbm"], "hbm", "GB/s", pk["hbm_source"]
             elif dom in (5, 6, 7):
-                achieved = amount / secs / 1e12
-                peak = pk["bf16_sustained"] * (1.0 if prec == PRECS["bf16"] else 0.5)
-                bound, u, src = "tensor", "TFLOP/s", "bf16 dense sustained " + pk["source"]
+                # a tensor-core kind: dense flops against the tensor peak and algorithmic bytes
+                # against HBM; the bound is the one whose time at peak is longer
+                tpeak = pk["bf16_sustained"] * (1.0 if prec == PRECS["bf16"] else 0.5)
+                nbytes = layerwise_tc_bytes(w.widths, w.G, w.k, J, Ni, Nb, prec)[dom]
+                t_tensor, t_hbm = amount / (tpeak * 1e12), nbytes / (pk["hbm"] * 1e9)
+                tensor = {"bound": "tensor", "achieved": amount / secs / 1e12, "peak": tpeak, "unit": "TFLOP/s",
+                          "work_per_step": amount, "work_unit": "flop",
+                          "peak_source": "bf16 dense sustained " + pk["source"]}
+                hbm = {"bound": "hbm", "achieved": nbytes / secs / 1e9, "peak": pk["hbm"], "unit": "GB/s",
+                       "work_per_step": nbytes, "work_unit": "byte", "peak_source": pk["hbm_source"]}
+                first, second = (hbm, tensor) if t_hbm >= t_tensor else (tensor, hbm)
+                bound, achieved, peak, u, src = (first["bound"], first["achieved"], first["peak"], first["unit"],
+                                                 first["peak_source"])
+                amount, unit = first["work_per_step"], first["work_unit"]
+                other = dict(second, frac=second["achieved"] / second["peak"])
             else:
                 achieved, peak, bound, u = amount / secs / 1e12, FP32_PEAK_TFLOPS, "alu", "TFLOP/s"
                 src = FP32_PEAK_NOTE + " (derived, FP32 FMA pipe)"
@@ -818,6 +865,12 @@ def run_batched(args, ws, rank, local):
                         "traffic": None, "kernel": KIND_NAMES[dom], "kernel_ms_per_step": secs * 1e3,
                         "launches_per_step": prof[dom][1] / prof_steps, "work_per_step": amount,
                         "work_unit": unit, "peak_source": src, "per_kind": per_kind}
+            if other is not None:
+                roofline["other_bound"] = other
+            if args.workload == WORKLOAD and prec == PRECS["bf16"] and dom in TRAFFIC_BATCH16["bytes"]:
+                roofline["traffic"] = TRAFFIC_BATCH16["bytes"][dom] * pts / TRAFFIC_BATCH16["points"]
+                roofline["traffic_note"] = ("DRAM bytes per step of this kernel kind, ncu on the 16-instance case "
+                                            "scaled by points (outputs partly still in L2 at that size)")
         launches = layerwise_batched_launches(w.widths, w.G, w.k, prec, w.mask_int) * args.steps
         out = {"metric": METRIC, "value": job_throughput(ws, args.steps, pts, total_ms / 1e3), "unit": UNIT,
                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -851,6 +904,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-equal-l2", action="store_true", help="skip the 1000-step equal-L2 training check")
+    ap.add_argument("--no-fp32-path", action="store_true",
+                    help="multi-instance workloads: skip timing the FP32 path beside the reduced-precision one "
+                         "(fp32_path is then null; e.g. for a profiler)")
     ap.add_argument("--instances", type=int, default=0,
                     help="multi-instance workloads: K instances drawn by the same recipe and seed (0 = all)")
     ap.add_argument("--workload", default=WORKLOAD,

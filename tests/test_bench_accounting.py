@@ -59,3 +59,18 @@ def test_layerwise_batched_launch_count_matches_the_launch_list():
     assert bench.layerwise_batched_launches([2, 16, 16, 1], 10, 3, 1, 0x1F) == 21
     # FP32: 3 gathers, 2 x 2 forwards, 2 output-layer kernels, 2 x (2 + 1) backward, 1 reduction
     assert bench.layerwise_batched_launches([2, 16, 16, 1], 10, 3, 0, 0x1F) == 3 + 2 * 2 + 2 + 2 * 3 + 1
+
+
+def test_tensor_core_bytes_of_a_layer_wise_step():
+    """Algorithmic bytes of the tensor-core kinds on [2,16,16,1], J = 5, 100 interior + 10 boundary
+    points (510 jet rows), written out by hand: forward of the hidden layer 4*(16+16)*510; weight
+    gradient of the first layer (coordinates 8 B/point, BF16 gradient 2*16*510) and of the hidden
+    layer (4*16*510 + 2*16*510); adjoint of the hidden layer on the interior jet rows, input
+    jets FP32, gradient BF16 in and out (the first layer's weight gradient runs on tensor cores)."""
+    b = bench.layerwise_tc_bytes([2, 16, 16, 1], 10, 3, 5, 100, 10, 1)
+    assert b[5] == 4 * 32 * 510
+    assert b[6] == (8 * 110 + 2 * 16 * 510) + (4 * 16 * 510 + 2 * 16 * 510)
+    assert b[7] == (4 * 16 + 2 * 16 + 2 * 16) * 5 * 100
+    # TF32 runs only the forward on tensor cores
+    b32 = bench.layerwise_tc_bytes([2, 16, 16, 1], 10, 3, 5, 100, 10, 2)
+    assert b32[5] == 4 * 32 * 510 and b32[6] == 0 and b32[7] == 0
