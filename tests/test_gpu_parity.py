@@ -300,6 +300,31 @@ def test_separate_calls_equal_fused_step(handles):
     capi.hrkan_reset_moments(h)
 
 
+def test_layerwise_flag_gives_a_bit_reproducible_step():
+    """The fused narrow kernel sums its weight gradient with shared-memory atomics (order-dependent
+    in the last bits); the same network on a HRKAN_FLAG_LAYERWISE handle sums in a fixed order, so
+    two steps from the same weights and moments give the same loss and the same updated weights,
+    bit for bit."""
+    w = inputs.WORKLOADS["burgers_2_10_10_1"]
+    h = capi.hrkan_init(capi.make_cfg(w.widths, w.G, w.k, w.m, w.lo, w.hi, flags=capi.HRKAN_FLAG_LAYERWISE))
+    try:
+        d = _points(w, 20000, 0)
+        W0 = random_weights(w, 11)
+        out = []
+        for _ in range(2):
+            capi.hrkan_reset_moments(h)
+            W = _t(W0)
+            loss = torch.zeros(3, dtype=torch.float64, device="cuda")
+            capi.hrkan_train_step(h, problem_of(w), W, _t(d["x_int"]), d["x_int"].shape[1], _t(d["x_bnd"]),
+                                  _t(d["g_bnd"]), d["x_bnd"].shape[1], 1e-3, 0.9, 0.999, 1e-8, 1, loss)
+            out.append((loss.cpu().numpy(), W.cpu().numpy()))
+        assert np.array_equal(out[0][0], out[1][0])
+        assert np.array_equal(out[0][1], out[1][1])
+        assert not np.array_equal(out[0][1], W0.astype(np.float32))   # the step moved the weights
+    finally:
+        capi.hrkan_destroy(h)
+
+
 def test_loss_is_reproducible(handles):
     w = inputs.WORKLOADS["burgers_2_10_10_1"]
     h = _handle(handles, w)
