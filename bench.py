@@ -291,12 +291,13 @@ KIND_NAMES = {5: "tc_fwd_kernel", 6: "tc_dw_kernel", 7: "tc_adj_kernel", 8: "wid
               1: "batch_reduce_kernel"}
 
 
-def layerwise_kind_work(widths, G, k, J, n_int, n_bnd, prec):
+def layerwise_kind_work(widths, G, k, J, n_int, n_bnd, prec, fwd_tc=True):
     """Algorithmic work of one multi-instance step on the layer-wise path per kernel kind:
     (amount, unit) with unit "flop" (dense contraction flops for the tensor-core kinds, every K
     column counted; sparse flops of the k+1 active bases for the FP32 kinds, the fused
     output-layer kernel (kind 3) included) or "byte" (the stand-alone residual of single-layer
-    networks).  Interior points carry J jet rows, boundary points one."""
+    networks).  Interior points carry J jet rows, boundary points one.  fwd_tc False: path 2, every
+    forward on the FP32 SIMT kernels."""
     n, kp = G + k, k + 1
     L = len(widths) - 1
     rows = J * n_int + n_bnd
@@ -311,7 +312,7 @@ def layerwise_kind_work(widths, G, k, J, n_int, n_bnd, prec):
             # of the layer (sparse) and its weight gradient, all points
             w[3] += 2 * kp * I * O * rows * 3 + (20 + 25) * kp * I * pts
             continue
-        if tc_ok(l):
+        if tc_ok(l) and fwd_tc:
             w[5] += 2 * rows * I * n * O
         else:
             w[8] += 2 * kp * I * O * rows + 20 * kp * I * pts
@@ -340,14 +341,15 @@ TRAFFIC_BATCH16 = {"points": 330654,
                    "bytes": {5: 142.75e6, 6: 198.25e6, 7: 168.28e6, 3: 117.14e6}}
 
 
-def layerwise_tc_bytes(widths, G, k, J, n_int, n_bnd, prec):
+def layerwise_tc_bytes(widths, G, k, J, n_int, n_bnd, prec, fwd_tc=True):
     """Algorithmic DRAM bytes of the tensor-core kinds of one multi-instance step on the
     layer-wise path (each tensor read or written once): the forward (kind 5) reads the
     layer's input jets and writes its output jets in FP32; the weight gradient (kind 6) reads
     the input jets (the two coordinates for the first layer) and the BF16 output gradient; the
     input adjoint (kind 7, interior points) reads the input jets and the BF16 output gradient
     and writes the input gradient, in BF16 when the layer below runs on tensor cores, else
-    FP32.  Interior points carry J jet rows, boundary points one; weights are not counted."""
+    FP32.  Interior points carry J jet rows, boundary points one; weights are not counted.
+    fwd_tc False: path 2, no tensor-core forward."""
     L = len(widths) - 1
     rows = J * n_int + n_bnd
     tc_ok = lambda l: prec != 0 and 0 < l < L - 1 and 16 <= widths[l + 1] <= 64 and widths[l + 1] % 16 == 0
@@ -355,7 +357,7 @@ def layerwise_tc_bytes(widths, G, k, J, n_int, n_bnd, prec):
     b = {5: 0, 6: 0, 7: 0}
     for l in range(L - 1):
         I, O = widths[l], widths[l + 1]
-        if tc_ok(l):
+        if tc_ok(l) and fwd_tc:
             b[5] += 4 * (I + O) * rows
         if tc_dw_ok(l):
             b[6] += (8 * (n_int + n_bnd) if l == 0 else 4 * I * rows) + 2 * O * rows
@@ -365,21 +367,22 @@ def layerwise_tc_bytes(widths, G, k, J, n_int, n_bnd, prec):
     return b
 
 
-def layerwise_batched_launches(widths, G, k, prec, mask):
+def layerwise_batched_launches(widths, G, k, prec, mask, fwd_tc=True):
     """Kernels one multi-instance step of the layer-wise path launches (both point sets present):
     3 point gathers; per set the forward of every layer below the output layer (a tensor-core
     layer adds its weight conversion); the fused output-layer kernel per set; per set the
     backward of the layers below (a tensor-core weight gradient adds a BF16 conversion of its
     gradient unless the layer above wrote it in BF16; a tensor-core adjoint adds its weight
-    conversion); the per-instance reduction.  Mirrors the library's kernel choice."""
+    conversion); the per-instance reduction.  Mirrors the library's kernel choice; fwd_tc False
+    is path 2 (every forward on the FP32 SIMT kernels)."""
     n, L = G + k, len(widths) - 1
     J = {0x0F: 4, 0x1F: 5, 0x2F: 5}.get(mask, bin(mask).count("1"))
     np_ok = n <= 64
 
     def tc_fwd(l, m):
         O, Jm = widths[l + 1], (1 if m == 1 else J)
-        return (prec != 0 and 0 < l < L - 1 and 16 <= O <= 64 and O % 16 == 0 and Jm * O <= 320 and np_ok
-                and m in (0x01, 0x0F, 0x1F))
+        return (fwd_tc and prec != 0 and 0 < l < L - 1 and 16 <= O <= 64 and O % 16 == 0 and Jm * O <= 320
+                and np_ok and m in (0x01, 0x0F, 0x1F))
 
     def tc_dw(l, m):
         O = widths[l + 1]
@@ -665,11 +668,12 @@ def run_ours(args, ws, rank, local):
         torch.distributed.destroy_process_group()
 
 
-def equal_l2_check(torch, capi, inputs, w, prec, n_inst=8, steps=1000, fp32_layerwise=False):
+def equal_l2_check(torch, capi, inputs, w, prec, n_inst=8, steps=1000, fp32_layerwise=False, reduced_path=1):
     """Both paths trained `steps` Adam steps from the workload's initial weights on its first
-    n_inst instances (the FP32 one on the kernel family the bench timed); mean relative L2
-    error of u on a 100 x 100 grid against the exact solution, both evaluated by the FP32
-    path."""
+    n_inst instances, each on the kernel family the bench timed (fp32_layerwise: the FP32 one
+    on the layer-wise kernels; reduced_path: hrkan_set_batch_path of the reduced-precision one);
+    mean relative L2 error of u on a 100 x 100 grid against the exact solution, both evaluated
+    by the FP32 path."""
     d = inputs.make_batched(w, instances=n_inst)
     dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
     probs = [capi.make_problem(w.pde, a, b, w.lam, w.nu, w.alpha) for a, b in d["ab"]]
@@ -688,6 +692,8 @@ def equal_l2_check(torch, capi, inputs, w, prec, n_inst=8, steps=1000, fp32_laye
                 capi.make_cfg(w.widths, w.G, w.k, w.m, w.lo, w.hi, prec=p, n_instances=n_inst,
                               flags=capi.HRKAN_FLAG_LAYERWISE))
             try:
+                if h is not h32:
+                    capi.hrkan_set_batch_path(h, reduced_path)
                 W = dev(d["W"])
                 loss = torch.zeros((n_inst, 3), dtype=torch.float64, device="cuda")
                 for t in range(1, steps + 1):
@@ -757,10 +763,11 @@ def run_batched(args, ws, rank, local):
         # the FP32 handle (a fused shape) times both kernel families and keeps the faster
         cands = LB_CHUNK_CANDIDATES if p != PRECS["fp32"] else (256, 1024, 2048, 4096, 8192)
         chosen, ms = capi.hrkan_autotune_batch(h, probs, W, xi, d["off_int"], xb, gb, d["off_bnd"], candidates=cands)
-        layerwise = capi.hrkan_batch_path(h) == 1
-        return {"points": chosen, "ms_per_step": ms,
-                "path": "layer-wise kernels" if layerwise else "fused multi-instance kernel",
-                "knob": "weight-gradient chunk (points)" if layerwise else "work item (points)"}
+        path = capi.hrkan_batch_path(h)
+        return {"points": chosen, "ms_per_step": ms, "path_id": path,
+                "path": {0: "fused multi-instance kernel", 1: "layer-wise kernels",
+                         2: "layer-wise kernels, every forward on the FP32 SIMT kernels"}[path],
+                "knob": "weight-gradient chunk (points)" if path else "work item (points)"}
 
     h = make(prec)
     W = W0.clone()
@@ -829,7 +836,8 @@ def run_batched(args, ws, rank, local):
                      "autotune": tuned32}
 
     if rank == 0:
-        work = layerwise_kind_work(w.widths, w.G, w.k, J, Ni, Nb, prec)
+        fwd_tc = tuned["path_id"] != 2
+        work = layerwise_kind_work(w.widths, w.G, w.k, J, Ni, Nb, prec, fwd_tc)
         kinds = [c for c in work if prof[c][1] > 0]
         dom = max(kinds, key=lambda c: prof[c][0]) if kinds else None
         pk = measured_peaks()
@@ -846,7 +854,7 @@ def run_batched(args, ws, rank, local):
                 # a tensor-core kind: dense flops against the tensor peak and algorithmic bytes
                 # against HBM; the bound is the one whose time at peak is longer
                 tpeak = pk["bf16_sustained"] * (1.0 if prec == PRECS["bf16"] else 0.5)
-                nbytes = layerwise_tc_bytes(w.widths, w.G, w.k, J, Ni, Nb, prec)[dom]
+                nbytes = layerwise_tc_bytes(w.widths, w.G, w.k, J, Ni, Nb, prec, fwd_tc)[dom]
                 t_tensor, t_hbm = amount / (tpeak * 1e12), nbytes / (pk["hbm"] * 1e9)
                 tensor = {"bound": "tensor", "achieved": amount / secs / 1e12, "peak": tpeak, "unit": "TFLOP/s",
                           "work_per_step": amount, "work_unit": "flop",
@@ -871,13 +879,17 @@ def run_batched(args, ws, rank, local):
                 roofline["traffic"] = TRAFFIC_BATCH16["bytes"][dom] * pts / TRAFFIC_BATCH16["points"]
                 roofline["traffic_note"] = ("DRAM bytes per step of this kernel kind, ncu on the 16-instance case "
                                             "scaled by points (outputs partly still in L2 at that size)")
-        launches = layerwise_batched_launches(w.widths, w.G, w.k, prec, w.mask_int) * args.steps
+        # the fused family: the multi-instance kernel and the per-instance reduction
+        per_step = 2 if tuned["path_id"] == 0 else layerwise_batched_launches(w.widths, w.G, w.k, prec, w.mask_int,
+                                                                               fwd_tc)
+        launches = per_step * args.steps
         out = {"metric": METRIC, "value": job_throughput(ws, args.steps, pts, total_ms / 1e3), "unit": UNIT,
                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
                "data": "synthetic",
                "config": {"workload": args.workload, "instances": I, "widths": w.widths, "G": w.G, "k": w.k,
                           "m": w.m, "n_int": Ni, "n_bnd": Nb, "precision": args.prec,
+                          "kernels": tuned["path"],
                           "parallelism": "replicas" if ws > 1 else "single",
                           "l2": "flushed before every timed step (256 MiB device write, outside the step events)"},
                "roofline": roofline, "gpu_launches": int(round(launches)), "clocks": clocks, "autotune": tuned,
@@ -886,8 +898,8 @@ def run_batched(args, ws, rank, local):
         if fp32_path is not None:
             out["fp32_path"] = fp32_path
             if not args.no_equal_l2:
-                out["equal_l2"] = equal_l2_check(torch, capi, inputs, w, prec,
-                                                 fp32_layerwise=tuned32["path"].startswith("layer"))
+                out["equal_l2"] = equal_l2_check(torch, capi, inputs, w, prec, fp32_layerwise=tuned32["path_id"] != 0,
+                                                 reduced_path=tuned["path_id"])
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_batched(w, d)
         emit(out)

@@ -367,15 +367,21 @@ int hrkan_forward_jets_batched(hrkan_t h, const float* W, const float* x, const 
  * HRKAN_EINVAL for a NULL handle or points_per_item < 1. */
 int hrkan_set_batch_items(hrkan_t h, int points_per_item);
 
-/* Kernel family of hrkan_train_step_batched: 0 = the fused multi-instance
- * kernel (shapes with a fused kernel), 1 = the layer-wise kernels, one launch
- * per layer kernel over all instances (every layer-wise handle; a fused shape
- * may choose it too, and hrkan_autotune_batch may pick it).
- * hrkan_set_batch_path: HRKAN_EINVAL for a NULL handle or a path other than 0
- * and 1, HRKAN_EUNSUPPORTED for 0 on a shape without a fused kernel.
- * hrkan_batch_path returns the current family (0 or 1), or HRKAN_EINVAL for a
- * NULL handle. */
-int hrkan_set_batch_path(hrkan_t h, int layerwise);
+/* Kernel family of the multi-instance calls (hrkan_train_step_batched,
+ * hrkan_forward_jets_batched): 0 = the fused multi-instance kernel (shapes
+ * with a fused kernel), 1 = the layer-wise kernels, one launch per layer
+ * kernel over all instances (every layer-wise handle; a fused shape may choose
+ * it too), 2 = the layer-wise kernels with every layer's forward on the FP32
+ * SIMT kernels, so that a BF16/TF32 handle uses the tensor cores for the
+ * weight gradient and the input adjoint only (on narrow layers, O = 16, the
+ * FP32 forward is the faster one, and it carries no rounding of the
+ * contraction's inputs; for an FP32 handle 2 runs the same kernels as 1).
+ * hrkan_autotune_batch may pick any of them.
+ * hrkan_set_batch_path: HRKAN_EINVAL for a NULL handle or a path other than
+ * 0, 1 and 2, HRKAN_EUNSUPPORTED for 0 on a shape without a fused kernel.
+ * hrkan_batch_path returns the current family (0, 1 or 2), or HRKAN_EINVAL
+ * for a NULL handle. */
+int hrkan_set_batch_path(hrkan_t h, int path);
 int hrkan_batch_path(hrkan_t h);
 
 /*
@@ -384,8 +390,9 @@ int hrkan_batch_path(hrkan_t h);
  * untimed call, then `reps` (< 1: 3) calls timed with CUDA events on the
  * stream, all with lr = 0 so that W keeps its values; the fastest candidate
  * becomes the handle's item size.  On a shape with a fused kernel both kernel
- * families are timed with every candidate (hrkan_set_batch_path) and the
- * fastest pair is kept; a family without kernels for the problem is skipped.  Arguments as hrkan_train_step_batched.
+ * families are timed with every candidate (hrkan_set_batch_path), on a
+ * BF16/TF32 handle also path 2, and the fastest pair is kept; a family without
+ * kernels for the problem is skipped.  Arguments as hrkan_train_step_batched.
  * Synchronises the stream; resets the Adam moments and the device step
  * counter (call it before training).  chosen / ms_per_step (host, may be
  * NULL) receive the winner and its time per step.

@@ -474,13 +474,15 @@ def hrkan_set_batch_items(h, points_per_item):
     _check(load_library().hrkan_set_batch_items(h, int(points_per_item)))
 
 
-def hrkan_set_batch_path(h, layerwise):
-    """Kernel family of the multi-instance step: 0 fused, 1 layer-wise."""
-    _check(load_library().hrkan_set_batch_path(h, int(layerwise)))
+def hrkan_set_batch_path(h, path):
+    """Kernel family of the multi-instance calls: 0 fused, 1 layer-wise, 2 layer-wise with every
+    layer's forward on the FP32 SIMT kernels (tensor cores for the backward only)."""
+    _check(load_library().hrkan_set_batch_path(h, int(path)))
 
 
 def hrkan_batch_path(h):
-    """The multi-instance step's kernel family: 0 fused, 1 layer-wise."""
+    """The multi-instance calls' kernel family: 0 fused, 1 layer-wise, 2 layer-wise with the FP32
+    forward."""
     rc = load_library().hrkan_batch_path(h)
     if rc < 0:
         _check(rc)

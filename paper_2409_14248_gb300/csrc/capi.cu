@@ -53,6 +53,9 @@ struct hrkan_ctx {
     } train_batch, fwd_batch;
     int batch_items_points = 1024;  // points per work item (layer-wise path: per weight-gradient chunk)
     bool batch_layerwise = false;   // fused shapes: run the multi-instance step on the layer-wise kernels
+    // multi-instance path 2: every layer's forward on the FP32 SIMT kernels (the
+    // tensor cores for the weight gradient and the input adjoint only)
+    bool batch_fwd_simt = false;
     // layer-wise multi-instance layout: every instance's points in whole blocks
     // of LB_BLOCK (rebuilt only when the offsets, problems or chunk size change)
     struct LBatch {
@@ -771,7 +774,7 @@ int lb_forward_layer(hrkan_t h, const float* W, int l, const float* in, float* o
     p.blk_inst = blk_inst;
     p.w_stride = h->P;
     const int n_inst = h->cfg.n_instances;
-    if (l > 0 && tc_layer_supported(h->cfg.prec, p.I, p.O, h->n, mask)) {
+    if (l > 0 && !h->batch_fwd_simt && tc_layer_supported(h->cfg.prec, p.I, p.O, h->n, mask)) {
         int rc = HRKAN_OK;
         const int64_t welems = tc_w_elems(p.O, p.I, h->n, h->cfg.prec) * n_inst;
         float* wp = ws_get(h, 20, size_t(welems), &rc);
@@ -1719,16 +1722,19 @@ int hrkan_train_step_partial(hrkan_t h, const pinn_problem* prob, const float* W
                            N_bnd_total, false, 0.0, 0.9, 0.999, 1e-8, 1, loss, dW, stream);
 }
 
-int hrkan_set_batch_path(hrkan_t h, int layerwise) {
+int hrkan_set_batch_path(hrkan_t h, int path) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
-    if (layerwise != 0 && layerwise != 1) return fail(HRKAN_EINVAL, "path %d (0 fused, 1 layer-wise)", layerwise);
-    if (!layerwise && h->net_id < 0) return fail(HRKAN_EUNSUPPORTED, "this shape has no fused multi-instance kernel");
-    h->batch_layerwise = layerwise == 1 && h->net_id >= 0;
+    if (path < 0 || path > 2)
+        return fail(HRKAN_EINVAL, "path %d (0 fused, 1 layer-wise, 2 layer-wise with the FP32 forward)", path);
+    if (path == 0 && h->net_id < 0) return fail(HRKAN_EUNSUPPORTED, "this shape has no fused multi-instance kernel");
+    h->batch_layerwise = path >= 1 && h->net_id >= 0;
+    h->batch_fwd_simt = path == 2;
     return HRKAN_OK;
 }
 
 int hrkan_batch_path(hrkan_t h) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (h->batch_fwd_simt) return 2;
     return (h->net_id < 0 || h->batch_layerwise) ? 1 : 0;
 }
 
@@ -1841,17 +1847,23 @@ int hrkan_autotune_batch(hrkan_t h, const pinn_problem* probs, float* W, const f
         return cuda_fail(cudaGetLastError(), "cudaEventCreate");
     }
     const int saved = h->batch_items_points;
-    const bool saved_path = h->batch_layerwise;
-    int best = saved;
-    bool best_path = saved_path, found = false;
+    const int saved_path = hrkan_batch_path(h);
+    int best = saved, best_path = saved_path;
+    bool found = false;
     float best_ms = 0.0f;
-    // a fused shape times both kernel families: the fused multi-instance kernel
-    // (candidate = points per work item) and the layer-wise path (candidate =
-    // points per weight-gradient chunk); a family that lacks the problem's
-    // kernels (EUNSUPPORTED) is skipped
-    const int n_paths = h->net_id >= 0 ? 2 : 1;
-    for (int path = 0; path < n_paths && rc == HRKAN_OK; ++path) {
-        h->batch_layerwise = h->net_id >= 0 && path == 1;
+    // the paths timed: a fused shape both kernel families, the fused
+    // multi-instance kernel (candidate = points per work item) and the
+    // layer-wise path (candidate = points per weight-gradient chunk); a
+    // tensor-core precision also the layer-wise path with every forward on the
+    // FP32 SIMT kernels (path 2: narrow layers can be faster there).  A family
+    // that lacks the problem's kernels (EUNSUPPORTED) is skipped
+    int paths[3], n_paths = 0;
+    if (h->net_id >= 0) paths[n_paths++] = 0;
+    paths[n_paths++] = 1;
+    if (h->cfg.prec != HRKAN_FP32) paths[n_paths++] = 2;
+    for (int pi = 0; pi < n_paths && rc == HRKAN_OK; ++pi) {
+        h->batch_layerwise = h->net_id >= 0 && paths[pi] >= 1;
+        h->batch_fwd_simt = paths[pi] == 2;
         for (int c = 0; c < n_candidates && rc == HRKAN_OK; ++c) {
             h->batch_items_points = candidates[c];
             // lr = 0 leaves W as it is; the first call builds this candidate's work list
@@ -1860,7 +1872,7 @@ int hrkan_autotune_batch(hrkan_t h, const pinn_problem* probs, float* W, const f
                                                 1e-8, 1, loss, nullptr, stream);
             };
             if ((rc = step())) {
-                if (rc == HRKAN_EUNSUPPORTED && n_paths == 2) rc = HRKAN_OK;   // try the other family
+                if (rc == HRKAN_EUNSUPPORTED && n_paths > 1) rc = HRKAN_OK;   // try the other families
                 break;
             }
             cudaEventRecord(a, s);
@@ -1879,7 +1891,7 @@ int hrkan_autotune_batch(hrkan_t h, const pinn_problem* probs, float* W, const f
                 found = true;
                 best_ms = ms;
                 best = candidates[c];
-                best_path = h->batch_layerwise;
+                best_path = paths[pi];
             }
         }
     }
@@ -1887,7 +1899,9 @@ int hrkan_autotune_batch(hrkan_t h, const pinn_problem* probs, float* W, const f
     cudaEventDestroy(b);
     if (rc == HRKAN_OK && !found) rc = fail(HRKAN_EUNSUPPORTED, "no multi-instance kernels for this problem");
     h->batch_items_points = rc == HRKAN_OK ? best : saved;
-    h->batch_layerwise = rc == HRKAN_OK ? best_path : saved_path;
+    const int keep = rc == HRKAN_OK ? best_path : saved_path;
+    h->batch_layerwise = keep >= 1 && h->net_id >= 0;
+    h->batch_fwd_simt = keep == 2;
     if (rc) return rc;
     if ((rc = hrkan_reset_moments(h, stream))) return rc;
     if (chosen) *chosen = best;

@@ -333,12 +333,12 @@ static cudaError_t fwd_mask(const WideLayer& p, bool first, cudaStream_t s) {
         return cudaGetLastError();
     };
     if (p.O == 1) return first ? go(wide_fwd_kernel<MW, MASK, 1, true>, 1) : go(wide_fwd_kernel<MW, MASK, 1, false>, 1);
-    if (p.O <= 8) return first ? go(wide_fwd_kernel<MW, MASK, 8, true>, 8) : go(wide_fwd_kernel<MW, MASK, 8, false>, 8);
-    // the first layer's two coordinates cost little to evaluate twice, so its
-    // outputs go 8 per block (fewer accumulators, more resident warps): on the
+    // eight outputs per block: fewer accumulators and more resident warps pay
+    // for evaluating a point's bases once per eight outputs (measured: the
     // batching workload's 2 -> 16 layer 0.47 ms per step against 0.68 with 16
-    // and 0.56 with 4
-    return first ? go(wide_fwd_kernel<MW, MASK, 8, true>, 8) : go(wide_fwd_kernel<MW, MASK, 16, false>, 16);
+    // outputs per block and 0.56 with 4; its 16 -> 16 layer ~2.0 against ~3.0;
+    // the FP32 step of [2,64,64,64,1] 39.1 ms against 42.2)
+    return first ? go(wide_fwd_kernel<MW, MASK, 8, true>, 8) : go(wide_fwd_kernel<MW, MASK, 8, false>, 8);
 }
 
 template <int MW, unsigned MASK>

@@ -59,6 +59,8 @@ def test_layerwise_batched_launch_count_matches_the_launch_list():
     assert bench.layerwise_batched_launches([2, 16, 16, 1], 10, 3, 1, 0x1F) == 21
     # FP32: 3 gathers, 2 x 2 forwards, 2 output-layer kernels, 2 x (2 + 1) backward, 1 reduction
     assert bench.layerwise_batched_launches([2, 16, 16, 1], 10, 3, 0, 0x1F) == 3 + 2 * 2 + 2 + 2 * 3 + 1
+    # path 2 (every forward on the FP32 SIMT kernels): the forward's two weight conversions go
+    assert bench.layerwise_batched_launches([2, 16, 16, 1], 10, 3, 1, 0x1F, fwd_tc=False) == 19
 
 
 def test_tensor_core_bytes_of_a_layer_wise_step():
@@ -74,3 +76,6 @@ def test_tensor_core_bytes_of_a_layer_wise_step():
     # TF32 runs only the forward on tensor cores
     b32 = bench.layerwise_tc_bytes([2, 16, 16, 1], 10, 3, 5, 100, 10, 2)
     assert b32[5] == 4 * 32 * 510 and b32[6] == 0 and b32[7] == 0
+    # path 2: no tensor-core forward, the backward's bytes as before
+    b2 = bench.layerwise_tc_bytes([2, 16, 16, 1], 10, 3, 5, 100, 10, 1, fwd_tc=False)
+    assert b2[5] == 0 and b2[6] == b[6] and b2[7] == b[7]

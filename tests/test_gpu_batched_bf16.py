@@ -167,6 +167,57 @@ def test_layerwise_batched_bf16_graph_replay_equals_eager():
     np.testing.assert_array_equal(res[0][1], res[1][1])
 
 
+def test_path_2_runs_the_forward_in_fp32_and_the_backward_on_tensor_cores():
+    """Path 2 (hrkan_set_batch_path) on a BF16 handle: every layer's forward on the FP32 SIMT
+    kernels, the weight gradient and the input adjoint on the tensor cores.  The forward jets then
+    meet the FP32 bars (1e-5 / 1e-4, normwise and per point), the step's loss terms the FP32 one,
+    and its gradient the BF16 bar (the backward still rounds its inputs once); no tensor-core
+    forward runs, the tensor-core weight gradient does.  Paths outside 0..2 are refused."""
+    d, I, h, probs = _setup(capi.HRKAN_BF16)
+    try:
+        assert capi.hrkan_batch_path(h) == 1
+        capi.hrkan_set_batch_path(h, 2)
+        assert capi.hrkan_batch_path(h) == 2
+        with pytest.raises(capi.HRKANError) as ei:
+            capi.hrkan_set_batch_path(h, 3)
+        assert ei.value.code == capi.HRKAN_EINVAL
+        assert capi.hrkan_batch_path(h) == 2
+        capi.hrkan_profile_enable(h, True)
+        for c in range(capi.HRKAN_KERNEL_CLASSES):
+            capi.hrkan_profile_read(h, c, reset=True)
+        N = int(d["off_int"][-1])
+        jets = torch.full((5, N), float("nan"), device="cuda")
+        capi.hrkan_forward_jets_batched(h, _dev(d["W"]), _dev(d["x_int"]), d["off_int"], 0x1F, jets)
+        capi.hrkan_sync_status(h)
+        assert capi.hrkan_profile_read(h, capi.HRKAN_KERNEL_TC_FWD)[1] == 0
+        got = jets.cpu().numpy()
+        for i in range(I):
+            Wi, xi, _, _ = _inst(d, i)
+            if xi.shape[1] == 0:
+                continue
+            want = oracle.forward(W_BATCH.net, Wi, xi, 0x1F)
+            g = got[:, d["off_int"][i]:d["off_int"][i + 1]]
+            for r in range(5):
+                assert_close(g[r], want[r], TOL_U if r == 0 else TOL_D, what=f"instance {i} row {r}")
+        P = W_BATCH.n_params()
+        W = _dev(d["W"])
+        loss = torch.zeros((I, 3), dtype=torch.float64, device="cuda")
+        dW = torch.full((I * P,), float("nan"), device="cuda")
+        _step(h, probs, d, W, 1, loss, dW)
+        capi.hrkan_sync_status(h)
+        assert capi.hrkan_profile_read(h, capi.HRKAN_KERNEL_TC_FWD)[1] == 0
+        assert capi.hrkan_profile_read(h, capi.HRKAN_KERNEL_TC_DW)[1] > 0
+        got_l, got_g = loss.cpu().numpy(), dW.cpu().numpy()
+        for i in range(I):
+            Wi, xi, xb, gb = _inst(d, i)
+            wl, wg = oracle.train_step(W_BATCH.net, W_BATCH.problem(*d["ab"][i]), Wi, np.zeros(P), np.zeros(P), xi,
+                                       0x1F, xb, gb, W_BATCH.lr, 1)
+            np.testing.assert_allclose(got_l[i], wl, rtol=1e-5, atol=1e-12, err_msg=f"instance {i}")
+            assert relerr(got_g[i * P:(i + 1) * P], wg) < BAR, (i, relerr(got_g[i * P:(i + 1) * P], wg))
+    finally:
+        capi.hrkan_destroy(h)
+
+
 def test_layerwise_batched_chunk_size_changes_only_summation_order():
     """The weight-gradient chunk size (the knob hrkan_autotune_batch tunes on this path) moves the
     gradient only by the order of float32 sums; the loss not at all."""
@@ -210,9 +261,10 @@ def test_bf16_batched_training_reaches_fp32_l2_error():
     """The metric's equal-L2 condition on the batching workload's own instances: 8 of the 256
     instances of 2-D Poisson (their (a, b) and point counts drawn by the workload's generator,
     seed 4), [2,16,16,1] G=10, the workload's N(0, 0.1^2) initial weights, 1000 Adam steps at
-    lr 1e-2 on both paths.  The plain FP32 path (the fused multi-instance kernel) and the BF16
-    tensor-core path end with mean relative L2 errors (100 x 100 grid, evaluated in FP32) whose
-    ratio BF16 / FP32 is at most 1.2."""
+    lr 1e-2 on every path.  The plain FP32 path (the fused multi-instance kernel) and the BF16
+    tensor-core path, on path 1 (split forward on the tensor cores) and on path 2 (FP32 forward,
+    tensor-core backward), end with mean relative L2 errors (100 x 100 grid, evaluated in FP32)
+    whose ratio BF16 / FP32 is at most 1.2."""
     I, steps = 8, 1000
     d = inputs.make_batched(W_BATCH, instances=I)
     probs = [problem_of(W_BATCH, a, b) for a, b in d["ab"]]
@@ -220,12 +272,13 @@ def test_bf16_batched_training_reaches_fp32_l2_error():
     finals = {}
     h32 = capi.hrkan_init(capi.make_cfg(W_BATCH.widths, W_BATCH.G, n_instances=I))
     try:
-        for prec in (capi.HRKAN_FP32, capi.HRKAN_BF16):
-            if prec == capi.HRKAN_FP32:
+        for arm in ("fp32", 1, 2):
+            if arm == "fp32":
                 h = h32
             else:
-                h = capi.hrkan_init(capi.make_cfg(W_BATCH.widths, W_BATCH.G, n_instances=I, prec=prec,
+                h = capi.hrkan_init(capi.make_cfg(W_BATCH.widths, W_BATCH.G, n_instances=I, prec=capi.HRKAN_BF16,
                                                   flags=capi.HRKAN_FLAG_LAYERWISE))
+                capi.hrkan_set_batch_path(h, arm)
             try:
                 W = _dev(d["W"])
                 loss = torch.zeros((I, 3), dtype=torch.float64, device="cuda")
@@ -233,24 +286,28 @@ def test_bf16_batched_training_reaches_fp32_l2_error():
                     capi.hrkan_train_step_batched(h, probs, W, xi, d["off_int"], xb, gb, d["off_bnd"], W_BATCH.lr,
                                                   0.9, 0.999, 1e-8, t, loss)
                 capi.hrkan_sync_status(h)
-                finals[prec] = (loss.cpu().numpy()[:, 0], _grid_rel_l2(h32, W, d["ab"]))
+                finals[arm] = (loss.cpu().numpy()[:, 0], _grid_rel_l2(h32, W, d["ab"]))
             finally:
                 if h is not h32:
                     capi.hrkan_destroy(h)
     finally:
         capi.hrkan_destroy(h32)
-    l32, e32 = finals[capi.HRKAN_FP32]
-    l16, e16 = finals[capi.HRKAN_BF16]
-    print(f"\nfinal loss FP32 {l32}\nfinal loss BF16 {l16}\nrel-L2 FP32 {e32} mean {e32.mean():.4f}"
-          f"\nrel-L2 BF16 {e16} mean {e16.mean():.4f} ratio {e16.mean() / e32.mean():.3f}")
-    assert np.all(np.isfinite(e16)) and np.all(np.isfinite(e32))
-    assert e16.mean() <= 1.2 * e32.mean()
+    l32, e32 = finals["fp32"]
+    assert np.all(np.isfinite(e32))
+    print(f"\nfinal loss FP32 {l32}\nrel-L2 FP32 {e32} mean {e32.mean():.4f}")
+    for path in (1, 2):
+        l16, e16 = finals[path]
+        print(f"final loss BF16 path {path} {l16}\nrel-L2 BF16 path {path} {e16} mean {e16.mean():.4f} "
+              f"ratio {e16.mean() / e32.mean():.3f}")
+        assert np.all(np.isfinite(e16))
+        assert e16.mean() <= 1.2 * e32.mean(), path
 
 
 def test_layerwise_batched_autotune_picks_a_chunk_and_trains_like_untuned():
     """hrkan_autotune_batch on the layer-wise BF16 path times the candidate weight-gradient chunk
-    sizes (lr = 0), keeps one of them and resets the Adam state: the tuned handle's first step
-    then equals an untuned handle's with that chunk size set by hand."""
+    sizes on path 1 and path 2 (lr = 0), keeps one pair and resets the Adam state: the tuned
+    handle's first step then equals an untuned handle's with that chunk size and path set by
+    hand."""
     cands = [256, 1024, 4096]
     d, I, h, probs = _setup(capi.HRKAN_BF16, items=1024)
     try:
@@ -258,6 +315,8 @@ def test_layerwise_batched_autotune_picks_a_chunk_and_trains_like_untuned():
         chosen, ms = capi.hrkan_autotune_batch(h, probs, W, _dev(d["x_int"]), d["off_int"], _dev(d["x_bnd"]),
                                                _dev(d["g_bnd"]), d["off_bnd"], candidates=cands, reps=2)
         assert chosen in cands and ms > 0
+        path = capi.hrkan_batch_path(h)
+        assert path in (1, 2)
         np.testing.assert_array_equal(W.cpu().numpy(), d["W"])      # lr = 0 left W as it was
         loss = torch.zeros((I, 3), dtype=torch.float64, device="cuda")
         _step(h, probs, d, W, 1, loss)
@@ -266,6 +325,7 @@ def test_layerwise_batched_autotune_picks_a_chunk_and_trains_like_untuned():
         capi.hrkan_destroy(h)
     d, I, h, probs = _setup(capi.HRKAN_BF16, items=chosen)
     try:
+        capi.hrkan_set_batch_path(h, path)
         W = _dev(d["W"])
         loss = torch.zeros((I, 3), dtype=torch.float64, device="cuda")
         _step(h, probs, d, W, 1, loss)
