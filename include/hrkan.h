@@ -327,28 +327,32 @@ int hrkan_train_step_partial(hrkan_t h, const pinn_problem* prob, const float* W
                              hrkan_stream_t stream);
 
 /*
- * Many independent networks of the handle's shape trained together: one
- * persistent launch over all instances plus one per-instance reduction/Adam
- * launch (the multi-instance workload of the training experiments of
- * Section 4, run as a batch).  cfg.n_instances = I networks; W is [I][P];
- * instance i owns interior points [off_int[i], off_int[i+1]) of x_int [2][N]
- * and boundary points [off_bnd[i], off_bnd[i+1]) of x_bnd / g_bnd.
+ * Many independent networks of the handle's shape trained together (the
+ * multi-instance workload of the training experiments of Section 4, run as a
+ * batch).  cfg.n_instances = I networks; W is [I][P]; instance i owns interior
+ * points [off_int[i], off_int[i+1]) of x_int [2][N] and boundary points
+ * [off_bnd[i], off_bnd[i+1]) of x_bnd / g_bnd.
  *   probs      host [I]: kind, lam, nu and alpha must agree; a, b may differ.
  *   off_int, off_bnd  host [I+1], non-decreasing, starting at 0.
  *   t          Adam step >= 1, or 0 for the device step counter (as in
  *              hrkan_train_step); the moments of instance i are its own.
  *   loss       device [I][3] float64 (L, mean r^2, mean (u-g)^2 per instance).
  *   dW         NULL, or device [I][P] float32 receiving each instance's gradient.
- * The work list (items of hrkan_set_batch_items points each) is rebuilt and
- * uploaded only when the offsets or problems change (that call synchronises
- * the stream); calls with unchanged arguments only enqueue the two kernels, so
- * they can be captured in a CUDA graph after one warm-up call.
+ * Kernel families (hrkan_set_batch_path): path 0, the fused shapes' persistent
+ * multi-instance kernel plus one per-instance reduction/Adam launch (work
+ * items of hrkan_set_batch_items points); paths 1 and 2, the layer-wise
+ * kernels, each launched once over all instances (weight-gradient chunks of
+ * hrkan_set_batch_items points), the boundary set's kernels on a side stream
+ * of the handle that is forked from `stream` and joined back into it before
+ * the reduction (in order on `stream` while hrkan_profile_enable is on).
+ * The work layout is rebuilt and uploaded only when the offsets or problems
+ * change (that call synchronises the stream); calls with unchanged arguments
+ * only enqueue kernels, so they can be captured in a CUDA graph after one
+ * warm-up call (which also creates the side stream and the scratch).
  * Errors: HRKAN_EINVAL for a NULL handle, array or (with points) pointer,
  * problems that disagree in kind, lam, nu or alpha, offsets that decrease or
  * do not start at 0, t < 0 or bad Adam hyper-parameters; HRKAN_EUNSUPPORTED
- * on a handle without a fused shape ([2,W,1] or [2,W,W,1], W in 5, 10, 16;
- * m = 4; not HRKAN_FLAG_LAYERWISE), and for a problem kind whose residual
- * needs third derivatives.
+ * for a problem kind or shape without kernels on the handle's path.
  */
 int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, const float* x_int,
                              const int64_t* off_int, const float* x_bnd, const float* g_bnd,

@@ -56,6 +56,10 @@ struct hrkan_ctx {
     // multi-instance path 2: every layer's forward on the FP32 SIMT kernels (the
     // tensor cores for the weight gradient and the input adjoint only)
     bool batch_fwd_simt = false;
+    // the layer-wise multi-instance step runs the boundary set's kernels on
+    // this stream, forked from and joined back into the caller's stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     // layer-wise multi-instance layout: every instance's points in whole blocks
     // of LB_BLOCK (rebuilt only when the offsets, problems or chunk size change)
     struct LBatch {
@@ -766,7 +770,7 @@ int build_lbatch(hrkan_t h, hrkan_ctx::LBatch& b, int n_inst, const pinn_problem
 
 // One layer's forward over a block-padded multi-instance point set.
 int lb_forward_layer(hrkan_t h, const float* W, int l, const float* in, float* out, int64_t N, unsigned mask,
-                     const int* blk_inst, cudaStream_t s) {
+                     const int* blk_inst, cudaStream_t s, int wslot = 20) {
     if (N == 0) return HRKAN_OK;
     WideLayer p = wide_layer(h, W, l, N);
     p.z = in;
@@ -777,7 +781,7 @@ int lb_forward_layer(hrkan_t h, const float* W, int l, const float* in, float* o
     if (l > 0 && !h->batch_fwd_simt && tc_layer_supported(h->cfg.prec, p.I, p.O, h->n, mask)) {
         int rc = HRKAN_OK;
         const int64_t welems = tc_w_elems(p.O, p.I, h->n, h->cfg.prec) * n_inst;
-        float* wp = ws_get(h, 20, size_t(welems), &rc);
+        float* wp = ws_get(h, wslot, size_t(welems), &rc);
         if (!wp) return rc;
         cudaError_t e;
         {
@@ -806,7 +810,7 @@ int lb_forward_layer(hrkan_t h, const float* W, int l, const float* in, float* o
 // nlayers < L stops before layer nlayers (its input jets are then the last
 // ones the tape receives).
 int lb_forward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsigned mask, float* out, float* tape,
-                   const int* blk_inst, int zslot, cudaStream_t s, int nlayers = -1) {
+                   const int* blk_inst, int zslot, cudaStream_t s, int nlayers = -1, int wslot = 20) {
     if (N == 0) return HRKAN_OK;
     const int J = jets_of(mask), L = h->L;
     int rc = HRKAN_OK;
@@ -818,7 +822,7 @@ int lb_forward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsigne
         if (l == L - 1) y = out;
         else if (tape) y = tape + tape_offset(h, l + 1, N, J);
         else if (!(y = ws_get(h, zslot + (l % 2), size_t(J) * O * N, &rc))) return rc;
-        if ((rc = lb_forward_layer(h, W, l, in, y, N, mask, blk_inst, s))) return rc;
+        if ((rc = lb_forward_layer(h, W, l, in, y, N, mask, blk_inst, s, wslot))) return rc;
         in = y;
     }
     return HRKAN_OK;
@@ -842,7 +846,7 @@ bool lb_layer_takes_bf16(hrkan_t h, int l, unsigned mask) {
 
 int lb_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsigned mask, const float* tape,
                     const float* gy_out, const int* blk_inst, const int4* chunks, int nchunk, float* partial,
-                    cudaStream_t s, int l_top = -1, void* gy_bf_in = nullptr, int gy_bf_slot = 38) {
+                    cudaStream_t s, int l_top = -1, void* gy_bf_in = nullptr, int gy_bf_slot = 38, int shift = 0) {
     if (N == 0) return HRKAN_OK;
     const int J = jets_of(mask), L = h->L, n_inst = h->cfg.n_instances;
     int rc = HRKAN_OK;
@@ -871,9 +875,9 @@ int lb_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsign
         if (!tc_dw && !gy) return fail(HRKAN_EUNSUPPORTED, "layer %d: FP32 weight gradient without an FP32 gradient", l);
         void* gbf = gybf;
         if (tc_dw) {
-            if (!gbf) {   // convert the FP32 gradient into slot 21
+            if (!gbf) {   // convert the FP32 gradient into slot 21 (+ shift)
                 const int64_t el = tc_dw_gy_elems(J, d.O, N);
-                if (!(gbf = ws_get(h, 21, size_t((el + 1) / 2), &rc))) return rc;
+                if (!(gbf = ws_get(h, 21 + shift, size_t((el + 1) / 2), &rc))) return rc;
             }
             ProfScope ps(h, HRKAN_KERNEL_TENSOR, s);
             ProfScope pk(h, HRKAN_KERNEL_TC_DW, s);
@@ -902,7 +906,7 @@ int lb_backward_set(hrkan_t h, const float* W, const float* x, int64_t N, unsign
                 const int64_t el = tc_dw_gy_elems(J, a.I, N);
                 if (!(gz_bf = ws_get(h, bf_slot, size_t((el + 1) / 2), &rc))) return rc;
                 bf_slot = bf_slot == 38 ? 39 : 38;
-            } else if (!(gz = ws_get(h, 23 + (l % 2), size_t(J) * a.I * N, &rc))) {
+            } else if (!(gz = ws_get(h, 23 + shift + (l % 2), size_t(J) * a.I * N, &rc))) {
                 return rc;
             }
             a.gz = gz;
@@ -1015,6 +1019,37 @@ int lb_train_step_unfused(hrkan_t h, const pinn_problem* probs, float* W, const 
 // with the tape kept, the output layer with the residual/loss per instance and
 // its reverse in one launch per set, backward of the layers below into
 // per-chunk partial rows, then the per-instance fixed-order reduction and Adam.
+// The boundary set's chain of kernels runs on the handle's side stream,
+// forked from the caller's stream after nothing and joined back before the
+// per-instance reduction, so that its small launches overlap the interior
+// set's; the two chains share no buffer they write (own tape, gradient and
+// scratch slots, distinct partial and loss rows).  The join also runs on an
+// early error return, keeping the caller's stream ordered after the side
+// stream's work (and a stream capture closed).  With kernel timing on
+// (hrkan_profile_enable) both sets run in order on the caller's stream, so
+// that each launch's events time that launch alone.
+struct SideJoin {
+    hrkan_t h;
+    cudaStream_t s;
+    bool active = false;
+    void join() {
+        if (!active) return;
+        active = false;
+        cudaEventRecord(h->join_ev, h->side);
+        cudaStreamWaitEvent(s, h->join_ev, 0);
+    }
+    ~SideJoin() { join(); }
+};
+
+int side_stream(hrkan_t h) {
+    if (h->side) return HRKAN_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "side stream");
+    return HRKAN_OK;
+}
+
 int lb_train_step(hrkan_t h, const pinn_problem* probs, float* W, const float* x_int, const int64_t* off_int,
                   const float* x_bnd, const float* g_bnd, const int64_t* off_bnd, double lr, double b1, double b2,
                   double eps, int t, double* loss, float* dW, cudaStream_t s) {
@@ -1050,12 +1085,22 @@ int lb_train_step(hrkan_t h, const pinn_problem* probs, float* W, const float* x
     float* gzb = ws_get(h, 30, size_t(I_out) * std::max<int64_t>(Nb, 1), &rc);
     if (!gzb) return rc;
     const int64_t n0 = off_int[n_inst], n1 = off_bnd[n_inst];
+    // the boundary set on the side stream when both sets have points
+    cudaStream_t sb = s;
+    SideJoin sj{h, s};
+    if (Ni > 0 && Nb > 0 && !h->prof) {
+        if ((rc = side_stream(h))) return rc;
+        HR_CUDA(cudaEventRecord(h->fork_ev, s), "fork event");
+        HR_CUDA(cudaStreamWaitEvent(h->side, h->fork_ev, 0), "fork wait");
+        sb = h->side;
+        sj.active = true;
+    }
     HR_CUDA(lb_gather(x_int, n0, b.pt_src_i, xi, Ni, 2, s), "point gather");
-    HR_CUDA(lb_gather(x_bnd, n1, b.pt_src_b, xb, Nb, 2, s), "point gather");
-    HR_CUDA(lb_gather(g_bnd, n1, b.pt_src_b, gb, Nb, 1, s), "point gather");
+    HR_CUDA(lb_gather(x_bnd, n1, b.pt_src_b, xb, Nb, 2, sb), "point gather");
+    HR_CUDA(lb_gather(g_bnd, n1, b.pt_src_b, gb, Nb, 1, sb), "point gather");
     // layers below the output layer; their outputs (the output layer's inputs) go to the tape
     if ((rc = lb_forward_set(h, W, xi, Ni, mask, nullptr, ti, b.blk_inst_i, 0, s, L - 1))) return rc;
-    if ((rc = lb_forward_set(h, W, xb, Nb, 0x1u, nullptr, tb, b.blk_inst_b, 0, s, L - 1))) return rc;
+    if ((rc = lb_forward_set(h, W, xb, Nb, 0x1u, nullptr, tb, b.blk_inst_b, 0, sb, L - 1, 40))) return rc;
     // the output layer, residual / boundary misfit, its reverse: one launch per set
     LbTailParams tp{};
     tp.W = W + h->layer_off[L - 1];
@@ -1069,7 +1114,6 @@ int lb_train_step(hrkan_t h, const pinn_problem* probs, float* W, const float* x
     tp.col0 = h->layer_off[L - 1];
     tp.loss_partial = b.loss_partial;
     {
-        ProfScope ps(h, HRKAN_KERNEL_RESIDUAL, s);
         LbTailParams ti_p = tp;
         ti_p.z = ti + tape_offset(h, L - 1, Ni, J);
         ti_p.gz = gzi;
@@ -1080,7 +1124,10 @@ int lb_train_step(hrkan_t h, const pinn_problem* probs, float* W, const float* x
         ti_p.lrow = b.lrow_i;
         ti_p.chunks = b.chunks_i;
         ti_p.t_counter = t == 0 && b.nci > 0 ? h->t_counter : nullptr;
-        HR_CUDA(lb_tail(ti_p, mask, false, b.nci, s), "output-layer launch (batched)");
+        {
+            ProfScope ps(h, HRKAN_KERNEL_RESIDUAL, s);
+            HR_CUDA(lb_tail(ti_p, mask, false, b.nci, s), "output-layer launch (batched)");
+        }
         LbTailParams tb_p = tp;
         tb_p.z = tb + tape_offset(h, L - 1, Nb, 1);
         tb_p.gz = gzb;
@@ -1090,15 +1137,20 @@ int lb_train_step(hrkan_t h, const pinn_problem* probs, float* W, const float* x
         tb_p.lrow = b.lrow_b;
         tb_p.chunks = b.chunks_b;
         tb_p.t_counter = t == 0 && b.nci == 0 ? h->t_counter : nullptr;
-        HR_CUDA(lb_tail(tb_p, mask, true, b.ncb, s), "output-layer launch (batched)");
+        {
+            ProfScope ps(h, HRKAN_KERNEL_RESIDUAL, sb);
+            HR_CUDA(lb_tail(tb_p, mask, true, b.ncb, sb), "output-layer launch (batched)");
+        }
     }
     if (L >= 2) {
         if ((rc = lb_backward_set(h, W, xi, Ni, mask, ti, gzi, b.blk_inst_i, b.chunks_i, b.nci, b.partial, s, L - 2,
                                   gzi_b, 38)))
             return rc;
-        if ((rc = lb_backward_set(h, W, xb, Nb, 0x1u, tb, gzb, b.blk_inst_b, b.chunks_b, b.ncb, b.partial, s, L - 2)))
+        if ((rc = lb_backward_set(h, W, xb, Nb, 0x1u, tb, gzb, b.blk_inst_b, b.chunks_b, b.ncb, b.partial, sb, L - 2,
+                                  nullptr, 38, 20)))
             return rc;
     }
+    sj.join();
     BatchReduceParams q{};
     q.partial = b.partial;
     q.item_off = b.row_off;
@@ -1340,6 +1392,9 @@ void hrkan_destroy(hrkan_t h) {
     cudaGetDevice(&cur);
     if (cur != h->device) cudaSetDevice(h->device);
     cudaDeviceSynchronize();
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
     cudaFree(h->partial);
     cudaFree(h->loss_partial);
     cudaFree(h->m1);

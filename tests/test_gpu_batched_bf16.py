@@ -218,6 +218,31 @@ def test_path_2_runs_the_forward_in_fp32_and_the_backward_on_tensor_cores():
         capi.hrkan_destroy(h)
 
 
+@pytest.mark.parametrize("path", [1, 2])
+def test_boundary_set_on_the_side_stream_equals_the_step_in_order(path):
+    """The layer-wise step runs the boundary set's kernels on the handle's side stream, overlapping
+    the interior set's; with kernel timing on it runs both sets in order on one stream.  Three steps
+    either way give the same weights and losses bit for bit (the two chains write no common
+    buffer)."""
+    res = []
+    for timed in (False, True):
+        d, I, h, probs = _setup(capi.HRKAN_BF16)
+        try:
+            capi.hrkan_set_batch_path(h, path)
+            capi.hrkan_profile_enable(h, timed)
+            W = _dev(d["W"])
+            loss = torch.zeros((I, 3), dtype=torch.float64, device="cuda")
+            for t in (1, 2, 3):
+                _step(h, probs, d, W, t, loss)
+            torch.cuda.synchronize()
+            capi.hrkan_sync_status(h)
+            res.append((W.cpu().numpy(), loss.cpu().numpy()))
+        finally:
+            capi.hrkan_destroy(h)
+    np.testing.assert_array_equal(res[0][0], res[1][0])
+    np.testing.assert_array_equal(res[0][1], res[1][1])
+
+
 def test_layerwise_batched_chunk_size_changes_only_summation_order():
     """The weight-gradient chunk size (the knob hrkan_autotune_batch tunes on this path) moves the
     gradient only by the order of float32 sums; the loss not at all."""
