@@ -34,6 +34,7 @@ _lib = None
 POISSON = 0
 BURGERS = 1
 KDV = 2
+POISSON3 = 3   # three-input networks; the third frequency c travels in "lam"
 EXACT, BF16, TF32, BF16W2 = 0, 1, 2, 3   # BF16W2: BF16 operands, weights as bf16 hi + lo
 BF16X3 = 4   # both factors as bf16 hi + lo, products hi*hi + hi*lo + lo*hi
 

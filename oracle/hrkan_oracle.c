@@ -848,7 +848,7 @@ int orc_backward(int n_widths, const int* widths, int G, int k, int m, double lo
 
 /* ------------------------------------------------------------------- loss */
 
-enum { ORC_POISSON = 0, ORC_BURGERS = 1, ORC_KDV = 2 };
+enum { ORC_POISSON = 0, ORC_BURGERS = 1, ORC_KDV = 2, ORC_POISSON3 = 3 };
 
 static int row_of(unsigned mask, int bit)
 {
@@ -859,9 +859,12 @@ static int row_of(unsigned mask, int bit)
 }
 
 /*
- * PDE residual and loss, D = 2.
+ * PDE residual and loss, D = 2 (D = 3 for the three-dimensional Poisson kind).
  *   Poisson (Eq. 3-4, generalised to u* = sin(a pi x) sin(b pi y)):
  *       r = u_xx + u_yy + (a^2+b^2) pi^2 sin(a pi x) sin(b pi y)
+ *   Poisson in three dimensions (the same equation with a third coordinate z,
+ *   u* = sin(a pi x) sin(b pi y) sin(c pi z), c passed in lam; x_int [3][N]):
+ *       r = u_xx + u_yy + u_zz + (a^2+b^2+c^2) pi^2 sin(a pi x) sin(b pi y) sin(c pi z)
  *   Burgers (Eq. 6-8 form, coordinates (x, t)):
  *       r = u_t + lam u u_x - nu u_xx
  *   KdV (a third-order equation of the kind Section 3 picks a larger m for,
@@ -878,11 +881,29 @@ int orc_residual_loss(int kind, double a, double b, double lam, double nu, doubl
                       const double* u_bnd, const double* g_bnd, long N_bnd, double* loss,
                       double* dL_djets_int, double* dL_du_bnd)
 {
-    int D = 2, rows[16];
+    int D = kind == ORC_POISSON3 ? 3 : 2, rows[16];
     int J = mask_rows(mask, D, rows);
     double Lp = 0.0, Lb = 0.0;
     if (dL_djets_int) memset(dL_djets_int, 0, sizeof(double) * J * N_int);
-    if (kind == ORC_POISSON) {
+    if (kind == ORC_POISSON3) {
+        int rxx = row_of(mask, 1 + D + 0), ryy = row_of(mask, 1 + D + 1), rzz = row_of(mask, 1 + D + 2);
+        if (rxx < 0 || ryy < 0 || rzz < 0) return -1;
+        double c = lam;
+        for (long p = 0; p < N_int; ++p) {
+            double xx = x_int[p], yy = x_int[N_int + p], zz = x_int[2 * N_int + p];
+            double f = (a * a + b * b + c * c) * ORC_PI * ORC_PI * sin(a * ORC_PI * xx) * sin(b * ORC_PI * yy) *
+                       sin(c * ORC_PI * zz);
+            double r = jets_int[(long)rxx * N_int + p] + jets_int[(long)ryy * N_int + p] +
+                       jets_int[(long)rzz * N_int + p] + f;
+            Lp += r * r;
+            if (dL_djets_int) {
+                double g = 2.0 * alpha * r / (double)N_int;
+                dL_djets_int[(long)rxx * N_int + p] = g;
+                dL_djets_int[(long)ryy * N_int + p] = g;
+                dL_djets_int[(long)rzz * N_int + p] = g;
+            }
+        }
+    } else if (kind == ORC_POISSON) {
         int rxx = row_of(mask, 1 + D + 0), ryy = row_of(mask, 1 + D + 1);
         if (rxx < 0 || ryy < 0) return -1;
         for (long p = 0; p < N_int; ++p) {

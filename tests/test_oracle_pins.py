@@ -346,6 +346,85 @@ def test_poisson_residual_zero_on_manufactured_solution():
         assert np.abs(dj).max() < 1e-12
 
 
+def test_poisson3_residual_zero_on_manufactured_solution():
+    """The Poisson equation in three dimensions: the exact jets of
+    u* = sin(a pi x) sin(b pi y) sin(c pi z) (c in lam) give r = 0, rows u, u_x, u_y, u_z,
+    u_xx, u_yy, u_zz of mask 0x7F."""
+    rng = np.random.default_rng(41)
+    for a, b, c in [(1, 1, 1), (2, 1, 3)]:
+        x = rng.uniform(-1, 1, (3, 64))
+        s = [np.sin(k * np.pi * x[d]) for d, k in enumerate((a, b, c))]
+        co = [np.cos(k * np.pi * x[d]) for d, k in enumerate((a, b, c))]
+        u = s[0] * s[1] * s[2]
+        jets = np.stack([u, a * np.pi * co[0] * s[1] * s[2], b * np.pi * s[0] * co[1] * s[2],
+                         c * np.pi * s[0] * s[1] * co[2], -(a * np.pi) ** 2 * u, -(b * np.pi) ** 2 * u,
+                         -(c * np.pi) ** 2 * u])
+        prob = dict(kind=oracle.POISSON3, a=a, b=b, lam=c, alpha=0.5)
+        loss, dj, _ = oracle.residual_loss(prob, x, 0x7F, jets, np.zeros(4), np.zeros(4))
+        assert loss[1] < 1e-24
+        assert np.abs(dj).max() < 1e-12
+
+
+def test_poisson3_zero_network_loss_and_jet_gradient():
+    """u = 0 (zero jets): L_pde = mean(f^2) with f = (a^2+b^2+c^2) pi^2 sin sin sin written out,
+    L = alpha L_pde + mean(g^2); dL/d(u_xx) = dL/d(u_yy) = dL/d(u_zz) = 2 alpha f / N, and the other
+    rows get nothing.  Central differences of L in single jet entries agree (L is quadratic in
+    the jets, so a central difference is exact for any step)."""
+    rng = np.random.default_rng(42)
+    a, b, c, alpha, N = 2.0, 1.0, 3.0, 0.3, 40
+    x = rng.uniform(-1, 1, (3, N))
+    g = rng.normal(0, 1, 9)
+    f = (a * a + b * b + c * c) * np.pi ** 2 * np.sin(a * np.pi * x[0]) * np.sin(b * np.pi * x[1]) * \
+        np.sin(c * np.pi * x[2])
+    prob = dict(kind=oracle.POISSON3, a=a, b=b, lam=c, alpha=alpha)
+    jets = np.zeros((7, N))
+    loss, dj, du = oracle.residual_loss(prob, x, 0x7F, jets, np.zeros(9), g)
+    assert loss[1] == pytest.approx(np.mean(f * f), rel=1e-13)
+    assert loss[0] == pytest.approx(alpha * np.mean(f * f) + np.mean(g * g), rel=1e-13)
+    for r in (4, 5, 6):
+        np.testing.assert_allclose(dj[r], 2 * alpha * f / N, rtol=1e-13)
+    assert np.all(dj[:4] == 0.0)
+    np.testing.assert_allclose(du, -2 * g / 9, rtol=1e-13)
+    jets = rng.normal(0, 1, (7, N))
+    _, dj, _ = oracle.residual_loss(prob, x, 0x7F, jets, np.zeros(9), g)
+    h = 1e-2
+    for r, p in [(4, 3), (5, 17), (6, 29), (0, 5)]:
+        jp, jm = jets.copy(), jets.copy()
+        jp[r, p] += h; jm[r, p] -= h
+        fd = (oracle.residual_loss(prob, x, 0x7F, jp, np.zeros(9), g)[0][0] -
+              oracle.residual_loss(prob, x, 0x7F, jm, np.zeros(9), g)[0][0]) / (2 * h)
+        assert dj[r, p] == pytest.approx(fd, rel=1e-8, abs=1e-9)
+
+
+def test_poisson3_train_step_gradient_matches_central_differences():
+    """A D = 3 training step ([3,4,1], mask 0x7F): the gradient it applies equals central
+    differences of its loss in the weights, and its Adam update is the first-step closed form
+    w - lr g / (|g| + eps)."""
+    net = dict(widths=[3, 4, 1], G=4, k=3, m=4, lo=-1.0, hi=1.0)
+    rng = np.random.default_rng(43)
+    P = oracle.param_count(net)
+    W0 = rng.normal(0, 0.4, P)
+    xi = rng.uniform(-1, 1, (3, 30))
+    xb = rng.uniform(-1, 1, (3, 12))
+    gb = rng.normal(0, 0.5, 12)
+    prob = dict(kind=oracle.POISSON3, a=1.0, b=2.0, lam=1.0, alpha=0.7)
+    W = W0.copy()
+    loss, dW = oracle.train_step(net, prob, W, np.zeros(P), np.zeros(P), xi, 0x7F, xb, gb, 1e-3, 1)
+
+    def L(Wv):
+        jets = oracle.forward(net, Wv, xi, 0x7F)
+        ub = oracle.forward(net, Wv, xb, 0x1)[0]
+        return oracle.residual_loss(prob, xi, 0x7F, jets, ub, gb)[0][0]
+
+    assert loss[0] == pytest.approx(L(W0), rel=1e-13)
+    h = 1e-6
+    for i in rng.choice(P, 25, replace=False):
+        Wp, Wm = W0.copy(), W0.copy()
+        Wp[i] += h; Wm[i] -= h
+        assert dW[i] == pytest.approx((L(Wp) - L(Wm)) / (2 * h), rel=2e-5, abs=1e-8 * max(1.0, np.abs(dW).max()))
+    np.testing.assert_allclose(W, W0 - 1e-3 * dW / (np.abs(dW) + 1e-8), rtol=1e-12, atol=1e-15)
+
+
 def test_burgers_residual_zero_on_cole_hopf_solution():
     """Eq. 6-8 form: u = 2 nu pi e^{-nu pi^2 t} sin(pi x) / (a0 + e^{-nu pi^2 t} cos(pi x))
     solves u_t + u u_x = nu u_xx exactly (Cole-Hopf); sympy supplies its jets."""
