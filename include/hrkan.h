@@ -25,9 +25,11 @@
  *   i = 0..n-1, the same for every layer.  Inputs outside [s_0, e_{n-1}] touch
  *   no basis (all contributions are exactly zero).
  * - Coordinates x are structure-of-arrays float32 [D][N] (x[d*N + p]), D = 2,
- *   or D = 3 for FP32 single networks (hrkan_forward_jets and hrkan_backward
- *   only; their jet mask has bit 0 = u, bit 1+d = du/dx_d, bit 4+d =
- *   d2u/dx_d^2; the other calls return HRKAN_EUNSUPPORTED).
+ *   or D = 3 for FP32 single networks (hrkan_forward_jets, hrkan_backward, and
+ *   with the Poisson kind in three coordinates pinn_residual_loss,
+ *   hrkan_train_step and hrkan_train_step_partial; their jet mask has bit 0 =
+ *   u, bit 1+d = du/dx_d, bit 4+d = d2u/dx_d^2; the single-layer and
+ *   multi-instance calls return HRKAN_EUNSUPPORTED).
  * - Jet rows: bit 0 of a jet mask selects u, bit 1+d selects du/dx_d, bit 1+D+d
  *   selects d2u/dx_d^2, bit 1+2D+d selects d3u/dx_d^3, bit 1+3D = 7 selects
  *   the mixed d2u/dx_0dx_1 (D = 2: 0x1F = u,u_x,u_y,u_xx,u_yy; 0x0F =
@@ -76,7 +78,7 @@ enum hrkan_status {
 };
 
 enum hrkan_prec { HRKAN_FP32 = 0, HRKAN_BF16 = 1, HRKAN_TF32 = 2 };
-enum hrkan_pde { HRKAN_POISSON = 0, HRKAN_BURGERS = 1, HRKAN_KDV = 2 };
+enum hrkan_pde { HRKAN_POISSON = 0, HRKAN_BURGERS = 1, HRKAN_KDV = 2, HRKAN_POISSON3 = 3 };
 
 #define HRKAN_MAX_WIDTHS 8
 /* Use the layer-wise kernels even where a fused whole-network kernel exists. */
@@ -115,6 +117,11 @@ typedef struct hrkan_cfg {
  *                  (Eq. 3 with a = b = 1: u* = sin(pi x) sin(pi y))
  *   HRKAN_BURGERS: r = u_t + lam u u_x - nu u_xx, coordinates (x, t)
  *                  (Eq. 6 has lam = 1; the rescaled Eq. 7 has lam = 1/4, nu/16)
+ *   HRKAN_KDV:     r = u_t + lam u u_x + nu u_xxx, coordinates (x, t)
+ *   HRKAN_POISSON3 (three-input networks only, every other kind two-input
+ *                  only; else HRKAN_EUNSUPPORTED): Eq. 3 in three coordinates,
+ *                  r = u_xx + u_yy + u_zz + (a^2+b^2+c^2) pi^2 sin(a pi x)
+ *                  sin(b pi y) sin(c pi z) with c = lam, interior mask 0x7F
  * Loss (Eq. 4, Eq. 8): L = alpha mean_int(r^2) + mean_bnd((u - g)^2), the
  * boundary mean pooled over every boundary and initial-condition point.
  */
@@ -122,7 +129,8 @@ typedef struct pinn_problem {
     int kind;       /* enum hrkan_pde */
     int reserved;
     double a, b;    /* Poisson source frequencies */
-    double lam, nu; /* Burgers: r = u_t + lam u u_x - nu u_xx; KdV: r = u_t + lam u u_x + nu u_xxx */
+    double lam, nu; /* Burgers: r = u_t + lam u u_x - nu u_xx; KdV: r = u_t + lam u u_x + nu u_xxx;
+                       HRKAN_POISSON3: lam = c, the third source frequency */
     double alpha;   /* weight of the PDE term */
 } pinn_problem;
 
@@ -211,8 +219,9 @@ int hrkan_layer_adjoint(hrkan_t h, int layer, const float* W, const float* z, co
 
 /*
  * Residual and loss (Eq. 3-4 / Eq. 6-8) from precomputed jets.
- *   x_int [2][N_int], jets_int [J][N_int] under jet_mask (Poisson needs u_xx,
- *   u_yy; Burgers needs u, u_x, u_t, u_xx), u_bnd / g_bnd [N_bnd] network
+ *   x_int [D][N_int], jets_int [J][N_int] under jet_mask (Poisson needs u_xx,
+ *   u_yy; Burgers needs u, u_x, u_t, u_xx; the Poisson kind in three
+ *   coordinates takes exactly the mask 0x7F), u_bnd / g_bnd [N_bnd] network
  *   values and targets at the boundary/initial points.
  *   loss          [3] float64 device: L, mean r^2, mean (u-g)^2 (written).
  *   dL_djets_int  [J][N_int] (written; NULL to skip), dL_du_bnd [N_bnd]
@@ -282,8 +291,11 @@ int hrkan_reset_moments(hrkan_t h, hrkan_stream_t stream);
  * minimised by Adam), fused: forward jets at the interior and boundary
  * points, residual and loss, backward, cross-block reduction and Adam.  Same
  * arithmetic as hrkan_forward_jets + pinn_residual_loss + hrkan_backward +
- * adam_step; the interior mask is 0x1F for Poisson, 0x0F for Burgers and 0x2F
- * for KdV.
+ * adam_step; the interior mask is 0x1F for Poisson, 0x0F for Burgers, 0x2F
+ * for KdV and 0x7F for the Poisson kind in three coordinates (a three-input
+ * network: the two-pass forward and backward of hrkan_forward_jets /
+ * hrkan_backward with the layer inputs recomputed, a residual kernel, the
+ * reduction with Adam).
  *   W      [P] float32, updated in place.
  *   t      Adam step >= 1, or 0: take the step from a device-side counter of
  *          the handle (zeroed by hrkan_init / hrkan_reset_moments) and advance
@@ -295,8 +307,9 @@ int hrkan_reset_moments(hrkan_t h, hrkan_stream_t stream);
  * (with profiling disabled).
  * Errors: HRKAN_EINVAL for a NULL handle or pointer, a bad problem (kind,
  * non-finite coefficient), N_int + N_bnd = 0, t < 0 or bad Adam
- * hyper-parameters; HRKAN_EUNSUPPORTED on a three-input handle and for KdV on
- * the fused shapes.
+ * hyper-parameters; HRKAN_EUNSUPPORTED for a kind that does not match the
+ * network's input count (HRKAN_POISSON3 takes three inputs, the others two)
+ * and for KdV on the fused shapes.
  */
 int hrkan_train_step(hrkan_t h, const pinn_problem* prob, float* W, const float* x_int,
                      int64_t N_int, const float* x_bnd, const float* g_bnd, int64_t N_bnd,

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libhrkan.so")
 HRKAN_OK, HRKAN_EINVAL, HRKAN_ENOMEM, HRKAN_ECUDA, HRKAN_EUNSUPPORTED, HRKAN_ETIMEOUT, HRKAN_ENONFINITE, HRKAN_EIO = \
     0, -1, -2, -3, -4, -5, -6, -7
 HRKAN_FP32, HRKAN_BF16, HRKAN_TF32 = 0, 1, 2
-HRKAN_POISSON, HRKAN_BURGERS, HRKAN_KDV = 0, 1, 2
+HRKAN_POISSON, HRKAN_BURGERS, HRKAN_KDV, HRKAN_POISSON3 = 0, 1, 2, 3   # POISSON3: c in lam
 HRKAN_MAX_WIDTHS = 8
 
 # every symbol include/hrkan.h declares
@@ -238,7 +238,7 @@ def pinn_residual_loss(h, prob, x_int, N_int, jet_mask, jets_int, u_bnd, g_bnd, 
         J = _jets(jet_mask)
         _need(loss, 3, "loss")
         if N_int > 0:
-            _need(x_int, 2 * N_int, "x_int")
+            _need(x_int, h.D * N_int, "x_int")
             _need(jets_int, J * N_int, "jets_int")
             _need(dL_djets_int, J * N_int, "dL_djets_int")
         if N_bnd > 0:
@@ -341,9 +341,9 @@ def hrkan_train_step(h, prob, W, x_int, N_int, x_bnd, g_bnd, N_bnd, lr, b1, b2, 
         _need(dW, h.P, "dW")
         _need(loss, 3, "loss")
         if N_int > 0:
-            _need(x_int, 2 * N_int, "x_int")
+            _need(x_int, h.D * N_int, "x_int")
         if N_bnd > 0:
-            _need(x_bnd, 2 * N_bnd, "x_bnd")
+            _need(x_bnd, h.D * N_bnd, "x_bnd")
             _need(g_bnd, N_bnd, "g_bnd")
     _check(load_library().hrkan_train_step(h, ctypes.byref(prob), _ptr(W, f), _ptr(x_int, f), int(N_int),
                                            _ptr(x_bnd, f), _ptr(g_bnd, f), int(N_bnd), float(lr), float(b1),
@@ -361,9 +361,9 @@ def hrkan_train_step_partial(h, prob, W, x_int, N_int, x_bnd, g_bnd, N_bnd, N_in
         _need(dW, h.P, "dW")
         _need(loss, 3, "loss")
         if N_int > 0:
-            _need(x_int, 2 * N_int, "x_int")
+            _need(x_int, h.D * N_int, "x_int")
         if N_bnd > 0:
-            _need(x_bnd, 2 * N_bnd, "x_bnd")
+            _need(x_bnd, h.D * N_bnd, "x_bnd")
             _need(g_bnd, N_bnd, "g_bnd")
     _check(load_library().hrkan_train_step_partial(h, ctypes.byref(prob), _ptr(W, f), _ptr(x_int, f), int(N_int),
                                                    _ptr(x_bnd, f), _ptr(g_bnd, f), int(N_bnd), int(N_int_total),

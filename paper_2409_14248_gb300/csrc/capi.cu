@@ -177,7 +177,9 @@ PdeParams make_pde(const pinn_problem* p) {
     q.kind = p->kind;
     q.a = float(p->a);
     q.b = float(p->b);
-    q.src = float((p->a * p->a + p->b * p->b) * M_PI * M_PI);
+    // Poisson source factor (a^2 + b^2) pi^2; in three coordinates (kind 3) c = lam joins it
+    const double c2 = p->kind == HRKAN_POISSON3 ? p->lam * p->lam : 0.0;
+    q.src = float((p->a * p->a + p->b * p->b + c2) * M_PI * M_PI);
     q.lam = float(p->lam);
     q.nu = float(p->nu);
     q.alpha = float(p->alpha);
@@ -186,11 +188,20 @@ PdeParams make_pde(const pinn_problem* p) {
 
 int check_problem(const pinn_problem* p) {
     if (!p) return fail(HRKAN_EINVAL, "problem is NULL");
-    if (p->kind != HRKAN_POISSON && p->kind != HRKAN_BURGERS && p->kind != HRKAN_KDV)
+    if (p->kind != HRKAN_POISSON && p->kind != HRKAN_BURGERS && p->kind != HRKAN_KDV && p->kind != HRKAN_POISSON3)
         return fail(HRKAN_EINVAL, "problem kind %d", p->kind);
     if (!std::isfinite(p->a) || !std::isfinite(p->b) || !std::isfinite(p->lam) || !std::isfinite(p->nu) ||
         !std::isfinite(p->alpha))
         return fail(HRKAN_EINVAL, "non-finite problem coefficient");
+    return HRKAN_OK;
+}
+
+// The Poisson kind in three coordinates needs a three-input network, every other kind a
+// two-input one.
+int check_kind_inputs(const pinn_problem* p, int inputs) {
+    if ((p->kind == HRKAN_POISSON3) != (inputs == 3))
+        return fail(HRKAN_EUNSUPPORTED, "problem kind %d on a network of %d inputs (kind %d takes three inputs, the "
+                    "others two)", p->kind, inputs, HRKAN_POISSON3);
     return HRKAN_OK;
 }
 
@@ -1267,9 +1278,10 @@ int forward3(hrkan_t h, const float* W, const float* x, int64_t N, unsigned m, f
     return HRKAN_OK;
 }
 
-// Weight-gradient partial rows of both passes: [0, GP) and, with a z pass, [GP, 2 GP).
+// Weight-gradient partial rows of both passes: [row0, row0 + GP) and, with a z pass,
+// [row0 + GP, row0 + 2 GP).
 int backward3(hrkan_t h, const float* W, const float* x, int64_t N, unsigned m, const float* dL, int* rows,
-              cudaStream_t s) {
+              cudaStream_t s, int row0 = 0) {
     unsigned ma, mb;
     split3(m, &ma, &mb);
     int rc = HRKAN_OK;
@@ -1291,11 +1303,11 @@ int backward3(hrkan_t h, const float* W, const float* x, int64_t N, unsigned m, 
     }
     h->seed0 = 0;
     h->seed1 = 1;
-    rc = wide_backward_set(h, W, x, N, ma, nullptr, g[0], 0, s);
+    rc = wide_backward_set(h, W, x, N, ma, nullptr, g[0], row0, s);
     if (!rc && mb) {
         h->seed0 = 2;
         h->seed1 = -1;
-        rc = wide_backward_set(h, W, x, N, mb, nullptr, g[1], h->wide_gp, s);
+        rc = wide_backward_set(h, W, x, N, mb, nullptr, g[1], row0 + h->wide_gp, s);
     }
     h->seed0 = 0;
     h->seed1 = 1;
@@ -1362,7 +1374,9 @@ int hrkan_init(hrkan_t* out, const hrkan_cfg* cfg) {
     for (int l = 0; l < L; ++l)
         h->layer_off[l + 1] = h->layer_off[l] + int64_t(cfg->widths[l]) * cfg->widths[l + 1] * h->n;
     h->wide_gp = std::max(1, h->nsm * 2 / 8);
-    h->max_grid = net_id >= 0 ? h->nsm * 8 : 2 * h->wide_gp;
+    // layer-wise: two point sets of wide_gp partial rows each; three inputs: two passes
+    // for the interior set and one for the boundary set
+    h->max_grid = net_id >= 0 ? h->nsm * 8 : (cfg->widths[0] == 3 ? 3 : 2) * h->wide_gp;
     h->max_grid_l = h->nsm * 8;
     size_t bytes_partial = size_t(h->max_grid) * size_t(h->P) * sizeof(float);
     if ((e = cudaMalloc(&h->partial, bytes_partial)) != cudaSuccess ||
@@ -1458,13 +1472,15 @@ int pinn_residual_loss(hrkan_t h, const pinn_problem* prob, const float* x_int, 
                        const float* jets_int, const float* u_bnd, const float* g_bnd, int64_t N_bnd, double* loss,
                        float* dL_djets_int, float* dL_du_bnd, hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
-    if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: hrkan_forward_jets and hrkan_backward only");
     if (int rc = check_problem(prob)) return rc;
+    if (int rc = check_kind_inputs(prob, h->cfg.widths[0])) return rc;
+    const bool d3 = h->cfg.widths[0] == 3;
     if (N_int < 0 || N_bnd < 0) return fail(HRKAN_EINVAL, "negative point count");
-    if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
+    if (!(d3 ? valid_mask3(jet_mask) : valid_mask(jet_mask))) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
     if (!mask_has_rows(jet_mask, prob->kind))
         return fail(HRKAN_EINVAL, "jet mask 0x%x lacks rows the residual needs", jet_mask);
-    if (!residual_mask_supported(jet_mask)) return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x", jet_mask);
+    if (d3 ? jet_mask != pde_mask(HRKAN_POISSON3) : !residual_mask_supported(jet_mask))
+        return fail(HRKAN_EUNSUPPORTED, "jet mask 0x%x", jet_mask);
     if (!loss) return fail(HRKAN_EINVAL, "loss is NULL");
     if (N_int > 0 && (!x_int || !jets_int)) return fail(HRKAN_EINVAL, "NULL interior pointer");
     if (N_bnd > 0 && (!u_bnd || !g_bnd)) return fail(HRKAN_EINVAL, "NULL boundary pointer");
@@ -1490,7 +1506,7 @@ int pinn_residual_loss(hrkan_t h, const pinn_problem* prob, const float* x_int, 
     cudaStream_t s = (cudaStream_t)stream;
     {
         ProfScope ps(h, HRKAN_KERNEL_RESIDUAL, s);
-        HR_CUDA(launch_residual(r, (int)grid, s), "residual launch");
+        HR_CUDA(d3 ? launch_residual3(r, (int)grid, s) : launch_residual(r, (int)grid, s), "residual launch");
     }
     ReduceParams q{};
     q.P = 0;
@@ -1679,13 +1695,86 @@ namespace {
 // The training step of hrkan_train_step (adam = true) and of
 // hrkan_train_step_partial (adam = false: the loss contributions and the
 // gradient of this shard, means over Ni_tot / Nb_tot points).
+// One training step of a three-input network (the Poisson kind in three
+// coordinates): the jets by the two-pass forward (directions x, y, then z),
+// the residual and the boundary misfit, the two-pass backward of the interior
+// set (partial rows [0, 2 GP)) and the backward of the boundary set (rows
+// [2 GP, 3 GP)), then the reduction with Adam.  No tape: the backward
+// recomputes the layer inputs.
+int train_step3(hrkan_t h, const pinn_problem* prob, float* W, const float* x_int, int64_t N_int, const float* x_bnd,
+                const float* g_bnd, int64_t N_bnd, double lr, double b1, double b2, double eps, int t, double* loss,
+                float* dW, cudaStream_t s, int64_t Ni_tot, int64_t Nb_tot, bool adam) {
+    const unsigned mask = pde_mask(HRKAN_POISSON3);
+    const int J = __builtin_popcount(mask);
+    int rc = HRKAN_OK;
+    float* jets = ws_get(h, 4, size_t(J) * std::max<int64_t>(N_int, 1), &rc);
+    float* dli = jets ? ws_get(h, 5, size_t(J) * std::max<int64_t>(N_int, 1), &rc) : nullptr;
+    float* ub = dli ? ws_get(h, 6, size_t(std::max<int64_t>(N_bnd, 1)), &rc) : nullptr;
+    float* dlb = ub ? ws_get(h, 7, size_t(std::max<int64_t>(N_bnd, 1)), &rc) : nullptr;
+    if (!dlb) return rc;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_FORWARD, s);
+        if (N_int > 0 && (rc = forward3(h, W, x_int, N_int, mask, jets, s))) return rc;
+        if (N_bnd > 0 && (rc = forward3(h, W, x_bnd, N_bnd, 0x1u, ub, s))) return rc;
+    }
+    ResidualParams r{};
+    r.pde = make_pde(prob);
+    r.mask = mask;
+    r.x = x_int;
+    r.jets = jets;
+    r.N = N_int;
+    r.dL = dli;
+    r.u_bnd = ub;
+    r.g_bnd = g_bnd;
+    r.Nb = N_bnd;
+    r.dLb = dlb;
+    r.scale0 = Ni_tot > 0 ? float(2.0 * prob->alpha / double(Ni_tot)) : 0.0f;
+    r.scale1 = Nb_tot > 0 ? float(2.0 / double(Nb_tot)) : 0.0f;
+    r.loss_partial = h->loss_partial;
+    r.t_counter = adam && t == 0 ? h->t_counter : nullptr;
+    int64_t rg = (std::max(N_int, N_bnd) + 255) / 256;
+    rg = std::min<int64_t>(std::max<int64_t>(rg, 1), h->max_grid_l);
+    {
+        ProfScope ps(h, HRKAN_KERNEL_RESIDUAL, s);
+        HR_CUDA(launch_residual3(r, int(rg), s), "residual launch (three inputs)");
+    }
+    int rows_i = 0, rows_b = 0;
+    if (N_int > 0 && (rc = backward3(h, W, x_int, N_int, mask, dli, &rows_i, s, 0))) return rc;
+    if (N_bnd > 0 && (rc = backward3(h, W, x_bnd, N_bnd, 0x1u, dlb, &rows_b, s, rows_i))) return rc;
+    ReduceParams q{};
+    q.partial = h->partial;
+    q.G = rows_i + rows_b;
+    q.P = h->P;
+    q.dW = dW;
+    q.do_adam = adam ? 1 : 0;
+    q.W = W;
+    q.m1 = h->m1;
+    q.m2 = h->m2;
+    q.lr = lr; q.b1 = b1; q.b2 = b2; q.eps = eps;
+    q.c1 = 1.0 - std::pow(b1, t > 0 ? t : 1);
+    q.c2 = 1.0 - std::pow(b2, t > 0 ? t : 1);
+    q.t_counter = adam && t == 0 ? h->t_counter : nullptr;
+    q.loss_partial = h->loss_partial;
+    q.Gl = int(rg);
+    q.loss = loss;
+    q.status = h->status;
+    q.alpha = prob->alpha;
+    q.n0 = Ni_tot;
+    q.n1 = Nb_tot;
+    {
+        ProfScope ps(h, HRKAN_KERNEL_REDUCE, s);
+        HR_CUDA(launch_reduce(q, s), "reduce/Adam launch (three inputs)");
+    }
+    return HRKAN_OK;
+}
+
 int train_step_impl(hrkan_t h, const pinn_problem* prob, float* W, const float* x_int, int64_t N_int,
                     const float* x_bnd, const float* g_bnd, int64_t N_bnd, int64_t Ni_tot, int64_t Nb_tot, bool adam,
                     double lr, double b1, double b2, double eps, int t, double* loss, float* dW,
                     hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
-    if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: hrkan_forward_jets and hrkan_backward only");
     if (int rc = check_problem(prob)) return rc;
+    if (int rc = check_kind_inputs(prob, h->cfg.widths[0])) return rc;
     if (N_int < 0 || N_bnd < 0) return fail(HRKAN_EINVAL, "negative point count");
     if (N_int + N_bnd == 0) return fail(HRKAN_EINVAL, "no collocation points");
     if (!W || !loss) return fail(HRKAN_EINVAL, "NULL device pointer");
@@ -1697,6 +1786,9 @@ int train_step_impl(hrkan_t h, const pinn_problem* prob, float* W, const float* 
     if (int rc = use_device(h)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned mask = pde_mask(prob->kind);
+    if (h->cfg.widths[0] == 3)
+        return train_step3(h, prob, W, x_int, N_int, x_bnd, g_bnd, N_bnd, lr, b1, b2, eps, t, loss, dW, s, Ni_tot,
+                           Nb_tot, adam);
     if (h->net_id < 0) return wide_train_step(h, prob, W, x_int, N_int, x_bnd, g_bnd, N_bnd, lr, b1, b2, eps, t, loss,
                                               dW, s, Ni_tot, Nb_tot, adam);
     NarrowParams p = base_params(h, W);
@@ -1805,10 +1897,12 @@ int hrkan_train_step_batched(hrkan_t h, const pinn_problem* probs, float* W, con
                              double lr, double b1, double b2, double eps, int t, double* loss, float* dW,
                              hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: no multi-instance calls");
     const int n_inst = h->cfg.n_instances;
     if (!probs || !off_int || !off_bnd) return fail(HRKAN_EINVAL, "NULL host array");
     for (int i = 0; i < n_inst; ++i) {
         if (int rc = check_problem(&probs[i])) return rc;
+        if (int rc = check_kind_inputs(&probs[i], h->cfg.widths[0])) return rc;
         if (probs[i].kind != probs[0].kind || probs[i].lam != probs[0].lam || probs[i].nu != probs[0].nu ||
             probs[i].alpha != probs[0].alpha)
             return fail(HRKAN_EINVAL, "instance %d: kind, lam, nu and alpha must agree across instances", i);
@@ -1881,6 +1975,7 @@ int hrkan_autotune_batch(hrkan_t h, const pinn_problem* probs, float* W, const f
                          const float* x_bnd, const float* g_bnd, const int64_t* off_bnd, const int* candidates,
                          int n_candidates, int reps, int* chosen, double* ms_per_step, hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: no multi-instance calls");
     static const int kDefault[] = {256, 512, 1024, 2048, 4096};
     if (!candidates) {
         candidates = kDefault;
@@ -1967,6 +2062,7 @@ int hrkan_autotune_batch(hrkan_t h, const pinn_problem* probs, float* W, const f
 int hrkan_forward_jets_batched(hrkan_t h, const float* W, const float* x, const int64_t* offsets, unsigned jet_mask,
                                float* jets, hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
+    if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: no multi-instance calls");
     if (!offsets) return fail(HRKAN_EINVAL, "offsets is NULL");
     if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
     const int n_inst = h->cfg.n_instances;
@@ -2032,7 +2128,7 @@ int hrkan_set_wait_cycles(hrkan_t h, int64_t cycles) {
 int hrkan_layer_jets(hrkan_t h, int layer, const float* W, const float* z, int64_t N, unsigned jet_mask, float* y,
                      hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
-    if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: hrkan_forward_jets and hrkan_backward only");
+    if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: no single-layer calls");
     if (layer < 0 || layer >= h->L) return fail(HRKAN_EINVAL, "layer %d outside [0, %d)", layer, h->L);
     if (N < 0) return fail(HRKAN_EINVAL, "N=%lld", (long long)N);
     if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
@@ -2046,7 +2142,7 @@ int hrkan_layer_jets(hrkan_t h, int layer, const float* W, const float* z, int64
 int hrkan_layer_dw(hrkan_t h, int layer, const float* z, const float* gy, int64_t N, unsigned jet_mask, float* dW,
                    hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
-    if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: hrkan_forward_jets and hrkan_backward only");
+    if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: no single-layer calls");
     if (layer < 0 || layer >= h->L) return fail(HRKAN_EINVAL, "layer %d outside [0, %d)", layer, h->L);
     if (N < 0) return fail(HRKAN_EINVAL, "N=%lld", (long long)N);
     if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);
@@ -2079,7 +2175,7 @@ int hrkan_layer_dw(hrkan_t h, int layer, const float* z, const float* gy, int64_
 int hrkan_layer_adjoint(hrkan_t h, int layer, const float* W, const float* z, const float* gy, int64_t N,
                         unsigned jet_mask, float* gz, hrkan_stream_t stream) {
     if (!h) return fail(HRKAN_EINVAL, "handle is NULL");
-    if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: hrkan_forward_jets and hrkan_backward only");
+    if (h->cfg.widths[0] == 3) return fail(HRKAN_EUNSUPPORTED, "three-input networks: no single-layer calls");
     if (layer < 1 || layer >= h->L) return fail(HRKAN_EINVAL, "layer %d outside [1, %d)", layer, h->L);
     if (N < 0) return fail(HRKAN_EINVAL, "N=%lld", (long long)N);
     if (!valid_mask(jet_mask)) return fail(HRKAN_EINVAL, "jet mask 0x%x", jet_mask);

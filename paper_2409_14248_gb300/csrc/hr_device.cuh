@@ -488,10 +488,16 @@ __host__ __device__ __forceinline__ void pde_residual_grad(const PdeParams& P, f
 // Masks for which a residual exists: Poisson u_xx, u_yy; Burgers u, u_x, u_t,
 // u_xx; KdV u, u_x, u_t, u_xxx.
 __host__ __device__ constexpr bool mask_has_rows(unsigned mask, int kind) {
-    return kind == 0 ? ((mask & 0x18u) == 0x18u) : kind == 1 ? ((mask & 0x0Fu) == 0x0Fu) : ((mask & 0x27u) == 0x27u);
+    return kind == 0   ? ((mask & 0x18u) == 0x18u)
+           : kind == 1 ? ((mask & 0x0Fu) == 0x0Fu)
+           : kind == 2 ? ((mask & 0x27u) == 0x27u)
+                       : ((mask & 0x70u) == 0x70u);   // three inputs: u_xx, u_yy, u_zz
 }
 
 // The interior jet mask the training step uses for a problem kind.
-__host__ __device__ constexpr unsigned pde_mask(int kind) { return kind == 0 ? 0x1Fu : kind == 1 ? 0x0Fu : 0x2Fu; }
+// (three inputs, kind 3: every row up to the second derivatives, 0x7F)
+__host__ __device__ constexpr unsigned pde_mask(int kind) {
+    return kind == 0 ? 0x1Fu : kind == 1 ? 0x0Fu : kind == 2 ? 0x2Fu : 0x7Fu;
+}
 
 }  // namespace hrkan

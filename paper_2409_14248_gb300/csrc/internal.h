@@ -89,6 +89,9 @@ struct ResidualParams {
 };
 // Enqueue the residual kernel on `grid` blocks (grid must be <= the rows of loss_partial).
 cudaError_t launch_residual(const ResidualParams& p, int grid, cudaStream_t s);
+// The Poisson residual in three coordinates (kind 3): x [3][N], jets the seven rows of
+// mask 0x7F (u, u_x, u_y, u_z, u_xx, u_yy, u_zz), the third frequency in pde.lam.
+cudaError_t launch_residual3(const ResidualParams& p, int grid, cudaStream_t s);
 bool residual_mask_supported(unsigned mask);
 
 // ---- layer-wise multi-instance path (lbatch.cu) ------------------------------------

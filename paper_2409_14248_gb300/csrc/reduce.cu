@@ -166,6 +166,52 @@ __global__ void __launch_bounds__(RES_BLOCK) residual_kernel(ResidualParams p) {
     }
 }
 
+// Three coordinates, r = u_xx + u_yy + u_zz + (a^2 + b^2 + c^2) pi^2 sin(a pi x) sin(b pi y)
+// sin(c pi z) (pde.src holds the factor, pde.lam holds c); dL/d(u_xx, u_yy, u_zz) = scale0 r,
+// nothing for the lower rows.  Boundary misfit and the block's loss partials as residual_kernel.
+__global__ void __launch_bounds__(RES_BLOCK) residual3_kernel(ResidualParams p) {
+    if (p.t_counter && blockIdx.x == 0 && threadIdx.x == 0) p.t_counter[1] = p.t_counter[0] + 1;
+    double l0 = 0.0, l1 = 0.0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x, N = p.N;
+    for (int64_t pt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; pt < N; pt += stride) {
+        const float f = p.pde.src * sinpif(p.pde.a * p.x[pt]) * sinpif(p.pde.b * p.x[N + pt]) *
+                        sinpif(p.pde.lam * p.x[2 * N + pt]);
+        const float r = p.jets[4 * N + pt] + p.jets[5 * N + pt] + p.jets[6 * N + pt] + f;
+        l0 += double(r) * double(r);
+        if (p.dL) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) p.dL[q * N + pt] = 0.0f;
+#pragma unroll
+            for (int q = 4; q < 7; ++q) p.dL[q * N + pt] = p.scale0 * r;
+        }
+    }
+    for (int64_t pt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; pt < p.Nb; pt += stride) {
+        float d = p.u_bnd[pt] - p.g_bnd[pt];
+        l1 += double(d) * double(d);
+        if (p.dLb) p.dLb[pt] = p.scale1 * d;
+    }
+    __shared__ double red[2][RES_BLOCK / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        l0 += __shfl_down_sync(0xffffffffu, l0, o);
+        l1 += __shfl_down_sync(0xffffffffu, l1, o);
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = l0; red[1][threadIdx.x >> 5] = l1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int t = 0; t < RES_BLOCK / 32; ++t) { a += red[0][t]; b += red[1][t]; }
+        p.loss_partial[2 * blockIdx.x] = a;
+        p.loss_partial[2 * blockIdx.x + 1] = b;
+    }
+}
+
+cudaError_t launch_residual3(const ResidualParams& p, int grid, cudaStream_t s) {
+    if (p.mask != 0x7Fu) return cudaErrorInvalidValue;
+    residual3_kernel<<<grid, RES_BLOCK, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
 bool residual_mask_supported(unsigned mask) { return mask == 0x0Fu || mask == 0x1Fu || mask == 0x2Fu; }
 
 cudaError_t launch_residual(const ResidualParams& p, int grid, cudaStream_t s) {
