@@ -1031,9 +1031,9 @@ int lb_train_step_unfused(hrkan_t h, const pinn_problem* probs, float* W, const 
 // its reverse in one launch per set, backward of the layers below into
 // per-chunk partial rows, then the per-instance fixed-order reduction and Adam.
 // The boundary set's chain of kernels runs on the handle's side stream,
-// forked from the caller's stream after nothing and joined back before the
-// per-instance reduction, so that its small launches overlap the interior
-// set's; the two chains share no buffer they write (own tape, gradient and
+// forked from the caller's stream at the start of the step and joined back
+// before the per-instance reduction, so that its small launches overlap the
+// interior set's; the two chains share no buffer they write (own tape, gradient and
 // scratch slots, distinct partial and loss rows).  The join also runs on an
 // early error return, keeping the caller's stream ordered after the side
 // stream's work (and a stream capture closed).  With kernel timing on
