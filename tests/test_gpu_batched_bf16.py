@@ -130,14 +130,16 @@ def test_layerwise_batched_step_matches_oracle(prec):
         capi.hrkan_destroy(h)
 
 
-def test_layerwise_batched_bf16_graph_replay_equals_eager():
+@pytest.mark.parametrize("path", [1, 2])
+def test_layerwise_batched_bf16_graph_replay_equals_eager(path):
     """The BF16 multi-instance step with the device step counter (t = 0), captured once in a
-    CUDA graph and replayed, gives the same weights and losses as the same number of eager
-    steps."""
+    CUDA graph and replayed (the capture includes the boundary set's fork onto the side stream
+    and its join), gives the same weights and losses as the same number of eager steps."""
     res = []
     for graph in (False, True):
         d, I, h, probs = _setup(capi.HRKAN_BF16)
         try:
+            capi.hrkan_set_batch_path(h, path)
             W = _dev(d["W"])
             loss = torch.zeros((I, 3), dtype=torch.float64, device="cuda")
             xi, xb, gb = _dev(d["x_int"]), _dev(d["x_bnd"]), _dev(d["g_bnd"])
@@ -441,3 +443,45 @@ def test_fused_shape_runs_either_kernel_family_and_autotune_picks_one():
         assert ei.value.code == capi.HRKAN_EUNSUPPORTED
     finally:
         capi.hrkan_destroy(h)
+
+
+def test_full_batching_workload_step_on_sampled_instances():
+    """The full batching workload (256 instances, 4 603 954 interior + 575 384 boundary points)
+    in the launch configuration the bench times (BF16 handle, path 2, 2048-point weight-gradient
+    chunks, the boundary set on the side stream): one training step checked against the oracle
+    on three instances (the fewest points, the most, and one between: loss terms at the FP32 bar
+    1e-5, the forward being FP32 on this path; the weight gradient at the BF16 bar, normwise and
+    per point), every instance's loss and gradient finite, and the step repeated from the same
+    weights and moments bit-identical."""
+    d = inputs.make_batched(W_BATCH)
+    I, P = W_BATCH.instances, W_BATCH.n_params()
+    h = capi.hrkan_init(capi.make_cfg(W_BATCH.widths, W_BATCH.G, n_instances=I, prec=capi.HRKAN_BF16,
+                                      flags=capi.HRKAN_FLAG_LAYERWISE))
+    try:
+        capi.hrkan_set_batch_items(h, 2048)
+        capi.hrkan_set_batch_path(h, 2)
+        probs = [problem_of(W_BATCH, a, b) for a, b in d["ab"]]
+        xi, xb, gb = _dev(d["x_int"]), _dev(d["x_bnd"]), _dev(d["g_bnd"])
+        res = []
+        for _ in range(2):
+            capi.hrkan_reset_moments(h)
+            W = _dev(d["W"])
+            loss = torch.zeros((I, 3), dtype=torch.float64, device="cuda")
+            dW = torch.full((I * P,), float("nan"), device="cuda")
+            capi.hrkan_train_step_batched(h, probs, W, xi, d["off_int"], xb, gb, d["off_bnd"], W_BATCH.lr, 0.9,
+                                          0.999, 1e-8, 1, loss, dW)
+            capi.hrkan_sync_status(h)
+            res.append((loss.cpu().numpy(), dW.cpu().numpy(), W.cpu().numpy()))
+    finally:
+        capi.hrkan_destroy(h)
+    got_l, got_g, _ = res[0]
+    assert np.all(np.isfinite(got_l)) and np.all(np.isfinite(got_g))
+    for first, again in zip(res[0], res[1]):
+        np.testing.assert_array_equal(first, again)
+    counts = np.diff(d["off_int"])
+    for i in sorted({int(np.argmin(counts)), int(np.argmax(counts)), 137}):
+        Wi, x_i, x_b, g_b = _inst(d, i)
+        wl, wg = oracle.train_step(W_BATCH.net, W_BATCH.problem(*d["ab"][i]), Wi, np.zeros(P), np.zeros(P), x_i,
+                                   0x1F, x_b, g_b, W_BATCH.lr, 1)
+        np.testing.assert_allclose(got_l[i], wl, rtol=1e-5, atol=1e-12, err_msg=f"instance {i}")
+        assert_close(got_g[i * P:(i + 1) * P], wg, BAR, what=f"instance {i} gradient")
