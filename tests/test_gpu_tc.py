@@ -481,3 +481,59 @@ def test_tc_first_layer_dw_matches_rounding_aware_oracle(mask):
     e_impl, e_fmt = relerr(got, rounded), relerr(rounded, exact)
     assert e_impl < 2e-5 + FLIP * e_fmt, (e_impl, e_fmt)
     assert e_fmt > 4 * e_impl
+
+
+# ------------------------------------------------------------------ whole BF16 training steps
+
+def _bf16_and_fp32_steps(w, d):
+    """One training step (t = 1) of w's network on d's points on a BF16 handle and on an FP32
+    handle, from the same weights: (loss, dW) of each."""
+    from gpu_util import problem_of
+    Ni, Nb = d["x_int"].shape[1], d["x_bnd"].shape[1]
+    out = {}
+    for prec in (capi.HRKAN_BF16, capi.HRKAN_FP32):
+        h = capi.hrkan_init(capi.make_cfg(w.widths, w.G, w.k, w.m, w.lo, w.hi, prec=prec))
+        try:
+            loss = torch.zeros(3, dtype=torch.float64, device="cuda")
+            dW = torch.full((w.n_params(),), float("nan"), device="cuda")
+            capi.hrkan_train_step(h, problem_of(w), _dev(d["W"]), _dev(d["x_int"]), Ni, _dev(d["x_bnd"]),
+                                  _dev(d["g_bnd"]), Nb, w.lr, 0.9, 0.999, 1e-8, 1, loss, dW)
+            capi.hrkan_sync_status(h)
+            out[prec] = (loss.cpu().numpy(), dW.cpu().numpy())
+        finally:
+            capi.hrkan_destroy(h)
+    return out
+
+
+@pytest.mark.parametrize("wname", ["burgers_2_32_32_1", "poisson_2_64x3_1"])
+def test_bf16_train_step_matches_oracle(wname):
+    """A whole BF16 training step of a single network (the split forward on the tensor cores, the
+    weight gradient and input adjoint in BF16) against the oracle's step on the same 2000
+    interior and 250 boundary points: loss terms and every layer's weight gradient within the
+    BF16 bar, normwise and per point."""
+    from gpu_util import layer_slices, oracle_step
+    w = inputs.WORKLOADS[wname]
+    d = inputs.make(w, n_int=2000, n_bnd=250, n_ic=125, n_bc=125)
+    got = _bf16_and_fp32_steps(w, d)[capi.HRKAN_BF16]
+    want_l, want_g, _, _, _ = oracle_step(w, d["W"], d["x_int"], d["x_bnd"], d["g_bnd"], w.lr)
+    np.testing.assert_allclose(got[0], want_l, rtol=BAR)
+    for li, sl in enumerate(layer_slices(w.widths, w.G, w.k)):
+        e, m = assert_close(got[1][sl], want_g[sl], BAR, what=f"layer {li} gradient")
+        print(f"{wname} layer {li}: gradient normwise {e:.2e}, per point {m:.2e}")
+
+
+@pytest.mark.parametrize("wname", ["burgers_2_32_32_1", "poisson_2_64x3_1"])
+def test_bf16_train_step_at_full_size_tracks_fp32(wname):
+    """At the workload's full size, the launch shape the bench times (the gradient sums over every
+    point, so no point can be sampled), the BF16 step's loss terms and every layer's gradient stay
+    within the BF16 bar of the FP32 step's, which the FP32 tests pin to the oracle."""
+    from gpu_util import layer_slices
+    w = inputs.WORKLOADS[wname]
+    d = inputs.make(w)
+    out = _bf16_and_fp32_steps(w, d)
+    (l16, g16), (l32, g32) = out[capi.HRKAN_BF16], out[capi.HRKAN_FP32]
+    assert np.all(np.isfinite(g16))
+    np.testing.assert_allclose(l16, l32, rtol=BAR)
+    for li, sl in enumerate(layer_slices(w.widths, w.G, w.k)):
+        e, m = assert_close(g16[sl], g32[sl], BAR, what=f"layer {li} gradient")
+        print(f"{wname} full size layer {li}: gradient normwise {e:.2e}, per point {m:.2e}")
