@@ -230,15 +230,16 @@ cudaError_t launch_residual(const ResidualParams& p, int grid, cudaStream_t s) {
 
 namespace hrkan {
 
-// grid (ceil(P / 32), n_inst): block (x, i) sums instance i's partial rows for
-// 32 weights in a fixed order, applies Adam, and block (0, i) finishes the
-// instance's loss.
+// grid (ceil(P / 512), n_inst): block (x, i) sums instance i's partial rows for
+// 512 weights, one per thread, in a fixed order (per residue class of the row
+// index mod 16, then the classes in order; an instance has a few to a few
+// hundred rows), applies Adam, and block (0, i) finishes the instance's loss.
 __global__ void __launch_bounds__(RED_LANES * RED_WARPS) batch_reduce_kernel(BatchReduceParams p) {
-    __shared__ float part[RED_WARPS][RED_LANES];
     __shared__ float corr[2];
     const int lane = threadIdx.x, w = threadIdx.y;
     const int inst = blockIdx.y;
-    const int64_t k = int64_t(blockIdx.x) * RED_LANES + lane;
+    // one weight per thread, RED_LANES * RED_WARPS weights per block
+    const int64_t k = int64_t(blockIdx.x) * (RED_LANES * RED_WARPS) + w * RED_LANES + lane;
     const int r0 = p.item_off[inst], r1 = p.item_off[inst + 1];
     if (w == 0 && lane == 0) {
         double c1 = p.c1, c2 = p.c2;
@@ -250,16 +251,16 @@ __global__ void __launch_bounds__(RED_LANES * RED_WARPS) batch_reduce_kernel(Bat
         corr[0] = float(1.0 / c1);
         corr[1] = float(1.0 / sqrt(c2));
     }
-    if (k < p.P) {
-        float acc = 0.0f;
-        for (int g = r0 + w; g < r1; g += RED_WARPS) acc += p.partial[int64_t(g) * p.P + k];
-        part[w][lane] = acc;
-    }
     __syncthreads();
-    if (w == 0 && k < p.P) {
+    if (k < p.P) {
+        // fixed order: a partial sum per residue class of the row index (mod RED_WARPS),
+        // then the classes in order
         float gsum = 0.0f;
-#pragma unroll
-        for (int t = 0; t < RED_WARPS; ++t) gsum += part[t][lane];
+        for (int t = 0; t < RED_WARPS; ++t) {
+            float acc = 0.0f;
+            for (int g = r0 + t; g < r1; g += RED_WARPS) acc += p.partial[int64_t(g) * p.P + k];
+            gsum += acc;
+        }
         const int64_t i = int64_t(inst) * p.P + k;
         if (p.dW) p.dW[i] = gsum;
         const double gd = gsum;
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(RED_LANES * RED_WARPS) batch_reduce_kernel(Bat
 }
 
 cudaError_t launch_batch_reduce(const BatchReduceParams& p, cudaStream_t s) {
-    int64_t bx = (p.P + RED_LANES - 1) / RED_LANES;
+    int64_t bx = (p.P + RED_LANES * RED_WARPS - 1) / (RED_LANES * RED_WARPS);
     batch_reduce_kernel<<<dim3((unsigned)bx, (unsigned)p.n_inst), dim3(RED_LANES, RED_WARPS), 0, s>>>(p);
     return cudaGetLastError();
 }
