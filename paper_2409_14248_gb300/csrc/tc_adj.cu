@@ -13,13 +13,14 @@
 // Both operands are MN-major in the 128-byte swizzle (points / k contiguous,
 // o the MMA's K); D_r = 128 x N accumulates in one of two TMEM buffers so the
 // MMAs of jet row r+1 overlap the epilogue of row r.  The epilogue warps
-// (thread = point = TMEM lane; two warps per lane quarter, one unit each)
-// copy their lane's row of D to shared memory, read back the four entries of
-// the unit at its cell and add that row's share of the adjoint at once (the
-// map is linear in dA, so no row is kept); the next tile's jets arrive by
-// cp.async meanwhile.  Two units per CTA keep a thread at 96 registers, so two
-// CTAs share an SM (one CTA of four units per SM, at 168 registers with
-// spills, took 8% longer; the same two units at one CTA per SM 50% longer).
+// (thread = point = TMEM lane; two warps per lane quarter, each half of the
+// CTA's units) copy their lane's row of D to shared memory and read back the
+// four entries of each unit at its cell.  For NP = 16 (two units per CTA)
+// each row's share of the adjoint is added at once (the map is linear in dA,
+// so no row is kept) and the next tile's jets arrive by cp.async meanwhile:
+// 96 registers, two CTAs per SM (one CTA of four units per SM, at 168
+// registers with spills, took 8% longer; two units at one CTA per SM 50%
+// longer).  Wider units keep the J rows and apply the adjoint after the last.
 // Every wait is bounded as in the forward kernel.
 #include <cuda.h>
 
@@ -77,7 +78,13 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
 
 template <int NP>
 struct Shape {
-    static constexpr int UK = 2;                         // units per CTA (two epilogue halves)
+    // NP = 16: two units per CTA and the row-wise epilogue (96 registers, two CTAs per
+    // SM); wider units: four units per CTA (two for NP >= 48) with the rows kept, one
+    // CTA per SM (two units at two CTAs per SM spill there, and twice the K-ranges read
+    // every gy tile: 2.90 against 1.91 ms per step of [2,64,64,64,1] G=32)
+    static constexpr bool ROWWISE = NP == 16;
+    static constexpr int UK = ROWWISE ? 2 : ((NP * 4 <= 160) ? 4 : 2);   // units per CTA (two epilogue halves)
+    static constexpr int MINB = ROWWISE ? 2 : 1;         // resident CTAs per SM the registers allow
     static constexpr int UH = UK / 2;                    // units per epilogue warp
     static constexpr int NC = UK * NP;                   // D columns
     static constexpr int NBW = (NC + 63) / 64;           // W boxes of 64 k
@@ -132,7 +139,7 @@ __device__ __forceinline__ void row_adjoint(int r, const float* z, const float* 
 }
 
 template <unsigned MASK, int NP>
-__global__ void __launch_bounds__(THREADS, 2)
+__global__ void __launch_bounds__(THREADS, Shape<NP>::MINB)
     tc_adj_kernel(AdjParams p, const __grid_constant__ CUtensorMap gmap, const __grid_constant__ CUtensorMap wmap) {
     using JT = Jet<MASK>;
     using SH = Shape<NP>;
@@ -196,99 +203,182 @@ __global__ void __launch_bounds__(THREADS, 2)
         float* prow = pick + (half * TILE + row) * PS;
         const int ju = j0 + half * UH;                 // this warp's first unit
         const int64_t N = p.N;
-        // the next tile's jets go to shared memory by cp.async while this tile is
-        // processed (two buffers [2][UH * J][256 threads]; each thread reads back only
-        // its own entries, so its own wait_group orders them)
-        float* zbuf = pick + size_t(2 * TILE) * PS;
-        auto prefetch_z = [&](int ti) {
-            const int64_t pt = int64_t(t0 + ti) * TILE + row;
-            const float* zp = p.z + (pt < N ? pt : N - 1);
-            float* dst = zbuf + size_t(ti & 1) * (UH * J * 32 * EPI_WARPS) + tid;
+        if constexpr (SH::ROWWISE) {
+            // the next tile's jets go to shared memory by cp.async while this tile is
+            // processed (two buffers [2][UH * J][256 threads]; each thread reads back only
+            // its own entries, so its own wait_group orders them)
+            float* zbuf = pick + size_t(2 * TILE) * PS;
+            auto prefetch_z = [&](int ti) {
+                const int64_t pt = int64_t(t0 + ti) * TILE + row;
+                const float* zp = p.z + (pt < N ? pt : N - 1);
+                float* dst = zbuf + size_t(ti & 1) * (UH * J * 32 * EPI_WARPS) + tid;
 #pragma unroll
-            for (int u = 0; u < UH; ++u) {
-                const int j = min(ju + u, I - 1);
+                for (int u = 0; u < UH; ++u) {
+                    const int j = min(ju + u, I - 1);
 #pragma unroll
-                for (int r = 0; r < J; ++r)
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
-                                     smem_u32(dst + (u * J + r) * (32 * EPI_WARPS))),
-                                 "l"(zp + (int64_t(r) * I + j) * N)
-                                 : "memory");
+                    for (int r = 0; r < J; ++r)
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                                         smem_u32(dst + (u * J + r) * (32 * EPI_WARPS))),
+                                     "l"(zp + (int64_t(r) * I + j) * N)
+                                     : "memory");
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            };
+            if (nt > 0) prefetch_z(0);
+            int q = 0;
+            for (int ti = 0; ti < nt; ++ti) {
+                const int64_t pt = int64_t(t0 + ti) * TILE + row;
+                const bool valid = pt < N;
+                float z[UH][J];
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+                {
+                    const float* src = zbuf + size_t(ti & 1) * (UH * J * 32 * EPI_WARPS) + tid;
+#pragma unroll
+                    for (int u = 0; u < UH; ++u)
+#pragma unroll
+                        for (int r = 0; r < J; ++r) z[u][r] = src[(u * J + r) * (32 * EPI_WARPS)];
+                }
+                if (ti + 1 < nt) prefetch_z(ti + 1);   // next tile's jets, one tile ahead
+                // basis derivatives of each unit at its value (v', v'', v'''), and where its
+                // four active bases sit in a D row: basis i at element (i mod 4) * NP/4 + i/4
+                // of the unit; bases outside [0, n) read a clamped entry (their derivatives are 0)
+                float d1[UH][4], d2[UH][4], d3[UH][4], g[UH][J];
+                int pos[UH][4];
+#pragma unroll
+                for (int u = 0; u < UH; ++u) {
+                    Active<3, 4, 3> b;
+                    b.eval(z[u][0], p.g);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        d1[u][k] = b.d1[k];
+                        d2[u][k] = b.d2[k];
+                        d3[u][k] = b.d3[k];
+                        const int i = b.c + k;
+                        const int ps = (i & 3) * (NP / 4) + (i >> 2);
+                        pos[u][k] = u * NP + (ps < 0 ? 0 : (ps > NP - 1 ? NP - 1 : ps));
+                    }
+#pragma unroll
+                    for (int r = 0; r < J; ++r) g[u][r] = 0.0f;
+                }
+#pragma unroll
+                for (int r = 0; r < J; ++r, ++q) {
+                    const int b = q & 1;
+                    if (!__all_sync(0xffffffffu, mbar_wait(&bar_dfull[b], uint32_t(q >> 1) & 1u, abort, wl))) goto done;
+                    tc_fence_after();
+                    const uint32_t col0 = uint32_t(b * NC + half * UH * NP);
+#pragma unroll
+                    for (int c = 0; c < UH * NP; c += 8) {
+                        uint32_t v[8];
+                        tmem_ld8(tbase + lane_base + col0 + uint32_t(c), v);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        *reinterpret_cast<uint4*>(prow + c) = make_uint4(v[0], v[1], v[2], v[3]);
+                        *reinterpret_cast<uint4*>(prow + c + 4) = make_uint4(v[4], v[5], v[6], v[7]);
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    mbar_arrive_if(&bar_dempty[b], lane == 0);
+#pragma unroll
+                    for (int u = 0; u < UH; ++u) {
+                        float a[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) a[k] = prow[pos[u][k]];
+                        row_adjoint<MASK>(r, z[u], d1[u], d2[u], d3[u], a, g[u]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < UH; ++u) {
+                    if (ju + u >= I) break;
+                    if (p.gz_bf) {
+                        if (pt < p.npad)
+#pragma unroll
+                            for (int r = 0; r < J; ++r)
+                                p.gz_bf[(int64_t(r) * I + ju + u) * p.npad + pt] =
+                                    __bfloat16_as_ushort(__float2bfloat16_rn(valid ? g[u][r] : 0.0f));
+                    } else if (valid) {
+#pragma unroll
+                        for (int r = 0; r < J; ++r) p.gz[(int64_t(r) * I + ju + u) * N + pt] = g[u][r];
+                    }
+                }
             }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-        };
-        if (nt > 0) prefetch_z(0);
-        int q = 0;
-        for (int ti = 0; ti < nt; ++ti) {
-            const int64_t pt = int64_t(t0 + ti) * TILE + row;
-            const bool valid = pt < N;
-            float z[UH][J];
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-            {
-                const float* src = zbuf + size_t(ti & 1) * (UH * J * 32 * EPI_WARPS) + tid;
+        } else {
+            // the J rows of dA kept per unit, the reverse of the jet rows after the last
+            // one; the next tile's jets in registers
+            auto load_z = [&](int ti, float (&zz)[UH][J]) {
+                const int64_t pt = int64_t(t0 + ti) * TILE + row;
+                const float* zp = p.z + (pt < N ? pt : N - 1);
+#pragma unroll
+                for (int u = 0; u < UH; ++u) {
+                    const int j = min(ju + u, I - 1);
+#pragma unroll
+                    for (int r = 0; r < J; ++r) zz[u][r] = zp[(int64_t(r) * I + j) * N];
+                }
+            };
+            float zn[UH][J];
+            if (nt > 0) load_z(0, zn);
+            int q = 0;
+            for (int ti = 0; ti < nt; ++ti) {
+                const int64_t pt = int64_t(t0 + ti) * TILE + row;
+                const bool valid = pt < N;
+                float z[UH][J];
 #pragma unroll
                 for (int u = 0; u < UH; ++u)
 #pragma unroll
-                    for (int r = 0; r < J; ++r) z[u][r] = src[(u * J + r) * (32 * EPI_WARPS)];
-            }
-            if (ti + 1 < nt) prefetch_z(ti + 1);   // next tile's jets, one tile ahead
-            // basis derivatives of each unit at its value (v', v'', v'''), and where its
-            // four active bases sit in a D row: basis i at element (i mod 4) * NP/4 + i/4
-            // of the unit; bases outside [0, n) read a clamped entry (their derivatives are 0)
-            float d1[UH][4], d2[UH][4], d3[UH][4], g[UH][J];
-            int pos[UH][4];
-#pragma unroll
-            for (int u = 0; u < UH; ++u) {
-                Active<3, 4, 3> b;
-                b.eval(z[u][0], p.g);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    d1[u][k] = b.d1[k];
-                    d2[u][k] = b.d2[k];
-                    d3[u][k] = b.d3[k];
-                    const int i = b.c + k;
-                    const int ps = (i & 3) * (NP / 4) + (i >> 2);
-                    pos[u][k] = u * NP + (ps < 0 ? 0 : (ps > NP - 1 ? NP - 1 : ps));
-                }
-#pragma unroll
-                for (int r = 0; r < J; ++r) g[u][r] = 0.0f;
-            }
-#pragma unroll
-            for (int r = 0; r < J; ++r, ++q) {
-                const int b = q & 1;
-                if (!__all_sync(0xffffffffu, mbar_wait(&bar_dfull[b], uint32_t(q >> 1) & 1u, abort, wl))) goto done;
-                tc_fence_after();
-                const uint32_t col0 = uint32_t(b * NC + half * UH * NP);
-#pragma unroll
-                for (int c = 0; c < UH * NP; c += 8) {
-                    uint32_t v[8];
-                    tmem_ld8(tbase + lane_base + col0 + uint32_t(c), v);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    *reinterpret_cast<uint4*>(prow + c) = make_uint4(v[0], v[1], v[2], v[3]);
-                    *reinterpret_cast<uint4*>(prow + c + 4) = make_uint4(v[4], v[5], v[6], v[7]);
-                }
-                tc_fence_before();
-                __syncwarp();
-                mbar_arrive_if(&bar_dempty[b], lane == 0);
+                    for (int r = 0; r < J; ++r) z[u][r] = zn[u][r];
+                if (ti + 1 < nt) load_z(ti + 1, zn);   // next tile's jets, one tile ahead
+                int cell[UH];
 #pragma unroll
                 for (int u = 0; u < UH; ++u) {
-                    float a[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) a[k] = prow[pos[u][k]];
-                    row_adjoint<MASK>(r, z[u], d1[u], d2[u], d3[u], a, g[u]);
+                    Active<3, 4, 2> b;
+                    b.eval(z[u][0], p.g);
+                    cell[u] = b.c;
                 }
-            }
+                float dA[UH][J][4];
 #pragma unroll
-            for (int u = 0; u < UH; ++u) {
-                if (ju + u >= I) break;
-                if (p.gz_bf) {
-                    if (pt < p.npad)
+                for (int r = 0; r < J; ++r, ++q) {
+                    const int b = q & 1;
+                    if (!__all_sync(0xffffffffu, mbar_wait(&bar_dfull[b], uint32_t(q >> 1) & 1u, abort, wl))) goto done;
+                    tc_fence_after();
+                    const uint32_t col0 = uint32_t(b * NC + half * UH * NP);
 #pragma unroll
-                        for (int r = 0; r < J; ++r)
-                            p.gz_bf[(int64_t(r) * I + ju + u) * p.npad + pt] =
-                                __bfloat16_as_ushort(__float2bfloat16_rn(valid ? g[u][r] : 0.0f));
-                } else if (valid) {
+                    for (int c = 0; c < UH * NP; c += 8) {
+                        uint32_t v[8];
+                        tmem_ld8(tbase + lane_base + col0 + uint32_t(c), v);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        *reinterpret_cast<uint4*>(prow + c) = make_uint4(v[0], v[1], v[2], v[3]);
+                        *reinterpret_cast<uint4*>(prow + c + 4) = make_uint4(v[4], v[5], v[6], v[7]);
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    mbar_arrive_if(&bar_dempty[b], lane == 0);
 #pragma unroll
-                    for (int r = 0; r < J; ++r) p.gz[(int64_t(r) * I + ju + u) * N + pt] = g[u][r];
+                    for (int u = 0; u < UH; ++u)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            // basis i at element (i mod 4) * NP/4 + i/4 of the unit; bases outside
+                            // [0, n) read a clamped entry (their derivatives are 0)
+                            const int i = cell[u] + k;
+                            int pos = (i & 3) * (NP / 4) + (i >> 2);
+                            pos = pos < 0 ? 0 : (pos > NP - 1 ? NP - 1 : pos);
+                            dA[u][r][k] = prow[u * NP + pos];
+                        }
+                }
+#pragma unroll
+                for (int u = 0; u < UH; ++u) {
+                    if (ju + u >= I) break;
+                    Active<3, 4, 3> b;
+                    b.eval(z[u][0], p.g);
+                    float g[J];
+                    JT::template rows_adjoint<4>(z[u], b.d1, b.d2, b.d3, dA[u], g);
+                    if (p.gz_bf) {
+                        if (pt < p.npad)
+#pragma unroll
+                            for (int r = 0; r < J; ++r)
+                                p.gz_bf[(int64_t(r) * I + ju + u) * p.npad + pt] =
+                                    __bfloat16_as_ushort(__float2bfloat16_rn(valid ? g[r] : 0.0f));
+                    } else if (valid) {
+#pragma unroll
+                        for (int r = 0; r < J; ++r) p.gz[(int64_t(r) * I + ju + u) * N + pt] = g[r];
+                    }
                 }
             }
         }
@@ -416,7 +506,7 @@ cudaError_t launch(const AdjParams& p, const CUtensorMap& gm, const CUtensorMap&
     using SH = Shape<NP>;
     const size_t box = size_t(p.O) * 128;
     const size_t smem = size_t(SH::NBW) * box + size_t(NSB) * 2 * box + size_t(2 * TILE) * SH::PS * 4 +
-                        size_t(2 * SH::UH * Jet<MASK>::J * 32 * EPI_WARPS) * 4 + 1024;
+                        (SH::ROWWISE ? size_t(2 * SH::UH * Jet<MASK>::J * 32 * EPI_WARPS) * 4 : 0) + 1024;
     auto kern = tc_adj_kernel<MASK, NP>;
     static std::mutex mu;
     static std::unordered_map<const void*, size_t> set;
