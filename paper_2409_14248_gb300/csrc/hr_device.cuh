@@ -236,6 +236,43 @@ struct Jet {
         }
     }
 
+    // rows_adjoint() taken one row of dA at a time: the map is linear in dA, so
+    // row r's terms (a[q] = dA[r][q]) can be added to gz as soon as that row is
+    // known, and no row needs to be kept.  Summed over r = 0..J-1 it gives
+    // rows_adjoint() up to the order of the float additions.
+    template <int KP>
+    __host__ __device__ __forceinline__ static void row_adjoint(int r, const float* z, const float* d1,
+                                                       const float* d2, const float* d3, const float* a,
+                                                       float* gz) {
+        static_assert(!GENERAL, "value, first and second derivative rows only");
+#pragma unroll
+        for (int q = 0; q < KP; ++q) {
+            if (r == 0) gz[0] = fmaf(a[q], d1[q], gz[0]);
+            if constexpr (F0)
+                if (r == RF0) {
+                    gz[0] = fmaf(a[q] * d2[q], z[RF0], gz[0]);
+                    gz[RF0] = fmaf(a[q], d1[q], gz[RF0]);
+                }
+            if constexpr (F1)
+                if (r == RF1) {
+                    gz[0] = fmaf(a[q] * d2[q], z[RF1], gz[0]);
+                    gz[RF1] = fmaf(a[q], d1[q], gz[RF1]);
+                }
+            if constexpr (S0)
+                if (r == RS0) {
+                    gz[0] = fmaf(a[q], fmaf(d3[q] * z[RF0], z[RF0], d2[q] * z[RS0]), gz[0]);
+                    gz[RF0] = fmaf(a[q] * 2.0f * d2[q], z[RF0], gz[RF0]);
+                    gz[RS0] = fmaf(a[q], d1[q], gz[RS0]);
+                }
+            if constexpr (S1)
+                if (r == RS1) {
+                    gz[0] = fmaf(a[q], fmaf(d3[q] * z[RF1], z[RF1], d2[q] * z[RS1]), gz[0]);
+                    gz[RF1] = fmaf(a[q] * 2.0f * d2[q], z[RF1], gz[RF1]);
+                    gz[RS1] = fmaf(a[q], d1[q], gz[RS1]);
+                }
+        }
+    }
+
     // rows() plus the third-derivative rows (needs v''') and the mixed row:
     //   ddd-row    v''' z_d^3 + 3 v'' z_d z_dd + v' z_ddd
     //   01-row     v'' z_0 z_1 + v' z_01

@@ -102,42 +102,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
     return d;
 }
 
-// The reverse of the jet rows (Jet::rows_adjoint) taken one row of dA at a
-// time: the map is linear in dA, so row r's terms are added to gz as soon as
-// that row's four entries are picked, and no row is kept.
-template <unsigned MASK>
-__device__ __forceinline__ void row_adjoint(int r, const float* z, const float* d1, const float* d2, const float* d3,
-                                            const float* a, float* gz) {
-    using JT = Jet<MASK>;
-    static_assert(!JT::GENERAL, "value, first and second derivative rows only");
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if (r == 0) gz[0] = fmaf(a[q], d1[q], gz[0]);
-        if constexpr (JT::F0)
-            if (r == JT::RF0) {
-                gz[0] = fmaf(a[q] * d2[q], z[JT::RF0], gz[0]);
-                gz[JT::RF0] = fmaf(a[q], d1[q], gz[JT::RF0]);
-            }
-        if constexpr (JT::F1)
-            if (r == JT::RF1) {
-                gz[0] = fmaf(a[q] * d2[q], z[JT::RF1], gz[0]);
-                gz[JT::RF1] = fmaf(a[q], d1[q], gz[JT::RF1]);
-            }
-        if constexpr (JT::S0)
-            if (r == JT::RS0) {
-                gz[0] = fmaf(a[q], fmaf(d3[q] * z[JT::RF0], z[JT::RF0], d2[q] * z[JT::RS0]), gz[0]);
-                gz[JT::RF0] = fmaf(a[q] * 2.0f * d2[q], z[JT::RF0], gz[JT::RF0]);
-                gz[JT::RS0] = fmaf(a[q], d1[q], gz[JT::RS0]);
-            }
-        if constexpr (JT::S1)
-            if (r == JT::RS1) {
-                gz[0] = fmaf(a[q], fmaf(d3[q] * z[JT::RF1], z[JT::RF1], d2[q] * z[JT::RS1]), gz[0]);
-                gz[JT::RF1] = fmaf(a[q] * 2.0f * d2[q], z[JT::RF1], gz[JT::RF1]);
-                gz[JT::RS1] = fmaf(a[q], d1[q], gz[JT::RS1]);
-            }
-    }
-}
-
 template <unsigned MASK, int NP>
 __global__ void __launch_bounds__(THREADS, Shape<NP>::MINB)
     tc_adj_kernel(AdjParams p, const __grid_constant__ CUtensorMap gmap, const __grid_constant__ CUtensorMap wmap) {
@@ -282,7 +246,7 @@ __global__ void __launch_bounds__(THREADS, Shape<NP>::MINB)
                         float a[4];
 #pragma unroll
                         for (int k = 0; k < 4; ++k) a[k] = prow[pos[u][k]];
-                        row_adjoint<MASK>(r, z[u], d1[u], d2[u], d3[u], a, g[u]);
+                        JT::template row_adjoint<4>(r, z[u], d1[u], d2[u], d3[u], a, g[u]);
                     }
                 }
 #pragma unroll

@@ -4,6 +4,7 @@
 //   B m z c v0..v3 d1_0..d1_3 d2_.. d3_.. d4_.. d5_.. d6_..  (Active<3, m, 6>)
 //   R mask m z c <J rows x 4 entries> <J adjoint values>  (Jet rows and their reverse)
 //   P kind mask x0 x1 u r <J values of gu>               (pde_residual, pde_residual_grad)
+//   W mask m z c <J adjoint values>                      (the reverse row by row, row_adjoint)
 // Inputs of the R lines: jets z[r] = zr[r] (z[0] = the value), dA[r][q] =
 // gy[r] * w[c + q] with w[i] = wv(i) (a rank-1 gradient, as a one-output layer has).
 #include <cstdio>
@@ -71,6 +72,34 @@ static void rows() {
     }
 }
 
+// The reverse of the R lines' rows taken one row of dA at a time (Jet::row_adjoint,
+// as the tensor-core adjoint applies it), same inputs.
+template <unsigned MASK, int M>
+static void rows_rowwise() {
+    using JT = Jet<MASK>;
+    const Grid g = grid(M);
+    for (float z0 : ZS) {
+        Active<K, M, 6> a;
+        a.eval(z0, g);
+        float z[12], gz[12];
+        int r = 0;
+        for (int b = 0; b < 12; ++b)
+            if (MASK & (1u << b)) z[r++] = (b == 0) ? z0 : ZR[b];
+        for (int rr = 0; rr < JT::J; ++rr) gz[rr] = 0.0f;
+        for (int rr = 0; rr < JT::J; ++rr) {
+            float dA[K + 1];
+            for (int q = 0; q <= K; ++q) {
+                const int i = a.c + q;
+                dA[q] = (i >= 0 && i < g.n) ? GY[rr] * wv(i) : 0.0f;
+            }
+            JT::template row_adjoint<K + 1>(rr, z, a.d1, a.d2, a.d3, dA, gz);
+        }
+        printf("W %u %d %.9g %d", MASK, M, (double)z0, a.c);
+        for (int rr = 0; rr < JT::J; ++rr) printf(" %.9g", (double)gz[rr]);
+        printf("\n");
+    }
+}
+
 // Residual r of one interior point and gu = dL/d(jets) for L = alpha r^2
 // (scale 2 alpha: one point), with the point's jets taken from ZR and a
 // varying value row.  Problem constants as make_pde in csrc/capi.cu sets them.
@@ -112,5 +141,6 @@ int main() {
     rows<0x12Fu, 5>(); rows<0x52Fu, 6>(); rows<0x3FFu, 4>(); rows<0xFFFu, 6>();
     residual<0x1Fu>(0); residual<0xFFu>(0); residual<0x0Fu>(1); residual<0xFFu>(1); residual<0x2Fu>(2);
     residual<0x7Fu>(2);
+    rows_rowwise<0x1Fu, 4>(); rows_rowwise<0x0Fu, 4>(); rows_rowwise<0x07u, 3>(); rows_rowwise<0x01u, 4>();
     return 0;
 }

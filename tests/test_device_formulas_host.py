@@ -4,6 +4,8 @@ the host by nvcc and run on the CPU, against the FP64 oracle.
 tests/device_host/hr_device_host.cu prints, in float32:
 * B lines: the k + 1 active bases of Active<3, m, 6> (v and its first six
   derivatives) for m = 2..6 at points across and beyond the grid;
+* W lines: the same reverse taken one jet row of dA at a time (Jet::row_adjoint, the
+  tensor-core adjoint's form) for masks 0x1F, 0x0F (m = 4), 0x07 (m = 3) and 0x01;
 * R lines: the basis-matrix rows of one input unit (Jet<mask>::rows_b) and
   their reverse (adjoint_b) for masks 0x1F, 0x0F, 0xFF (m = 4 and 6), 0x2F
   (m = 3), 0x12F (fourth derivative along x0, m = 5), 0x52F (fourth and fifth,
@@ -156,3 +158,38 @@ def test_residuals_and_their_jet_gradients_match_the_oracle(lines):
         tol = 2.0 * alpha * (2e-6 * scale * dr + 2e-6 * abs(r_want) * dr) + 1e-30
         assert np.all(np.abs(gu - dj) <= tol), (kind, mask, gu, dj)
         assert np.all((gu == 0.0) == (dj == 0.0)), (kind, mask, gu, dj)
+
+
+def test_row_by_row_reverse_matches_the_oracle(lines):
+    """The reverse of the jet rows summed one row of dA at a time (as the tensor-core input
+    adjoint applies it, no row kept) equals the oracle's input adjoint of the same one-unit
+    layer, and the kernels' all-rows reverse (R lines) to float32 rounding."""
+    wlines = [ln for ln in lines if ln[0] == "W"]
+    assert len(wlines) == 4 * 15
+    rl = {(int(ln[1]), int(ln[2]), ln[3]): ln for ln in lines if ln[0] == "R"}
+    n = G + K
+    seen_r = 0
+    for ln in wlines:
+        mask, m, z0, c = int(ln[1]), int(ln[2]), float(ln[3]), int(ln[4])
+        bits = [b for b in range(12) if mask >> b & 1]
+        J = len(bits)
+        gz = np.array(ln[5: 5 + J], dtype=np.float64)
+        assert gz.size == J
+        order = {0: 0, 1: 1, 2: 1, 3: 2, 4: 2}
+        if 1 + max(order[b] for b in bits) >= m and near_knot(z0):
+            continue
+        zin = np.array([[[z0 if b == 0 else ZR[b]]] for b in bits], dtype=np.float64)
+        zin = zin.astype(np.float32).astype(np.float64)
+        w = np.array([wv(i) for i in range(n)], dtype=np.float64)
+        gy = np.array([[[np.float32(GY[r])]] for r in range(J)], dtype=np.float64)
+        want = oracle.layer_adjoint(1, 1, G, K, m, LO, HI, w, zin, gy, mask)[:, 0, 0]
+        scale = max(1.0, np.abs(want).max())
+        assert np.abs(gz - want).max() <= _tol(z0) * scale, (mask, m, z0, gz, want)
+        key = (mask, m, ln[3])
+        if key in rl:
+            seen_r += 1
+            r_ln = rl[key]
+            gz_r = np.array(r_ln[5 + J * (K + 1): 5 + J * (K + 1) + J], dtype=np.float64)
+            assert np.abs(gz - gz_r).max() <= 1e-5 * max(1.0, np.abs(gz_r).max()), (mask, z0, gz, gz_r)
+    assert seen_r == 2 * 15            # 0x1F and 0x0F at m = 4 are also R lines
+
